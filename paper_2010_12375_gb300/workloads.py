@@ -1,0 +1,285 @@
+"""Seeded synthetic inputs for the weakly-compressible SPH hot path.
+
+This module holds geometry and initial conditions only -- lattice particle
+placement, dummy-wall layers with their normals and volumes, the Taylor-Green
+initial velocity field and the seeded sampling of batched tank geometries. It
+contains none of the method's arithmetic (no kernel, no Riemann solver, no
+time stepping), so that the CUDA path and the plain CPU oracle can both be fed
+from it without sharing any of the computation they are compared on.
+
+Geometry follows the paper's validation cases (Sec. 7.1, 2D/3D dam break):
+a fluid block at rest in a tank whose walls are four layers of dummy
+particles on the same lattice as the fluid (lattice generator, Sec. 6.2).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+TANK_EXTENT = 5.366          # tank side length of the dam-break cases (multiples of H)
+WALL_LAYERS = 4              # dummy-particle wall thickness, in lattice spacings
+H_OVER_DP = 1.3              # smoothing length over lattice spacing
+
+
+@dataclass
+class Workload:
+    """One SPH problem: parameters plus the initial particle state (all float64).
+
+    Arrays are in particle-id order: row k holds particle id k.
+    """
+    name: str
+    dim: int
+    h: float
+    dp: float
+    rho0: float
+    c0: float
+    cfl_ad: float
+    cfl_ac: float
+    u_ref: float
+    nu: float
+    gravity: np.ndarray          # (3,)
+    lo: np.ndarray               # (3,) lower corner of the cell grid
+    hi: np.ndarray               # (3,) upper corner of the cell grid
+    periodic: np.ndarray         # (3,) int, 1 = periodic axis (period hi-lo)
+    free_surface: int
+    pos: np.ndarray              # (N, dim)
+    vel: np.ndarray              # (N, dim)
+    rho: np.ndarray              # (N,)
+    mass: np.ndarray             # (N,)
+    wall_pos: np.ndarray         # (Nw, dim)
+    wall_normal: np.ndarray      # (Nw, dim)
+    wall_vol: np.ndarray         # (Nw,)
+    t_end: float = 0.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_fluid(self) -> int:
+        return int(self.pos.shape[0])
+
+    @property
+    def n_wall(self) -> int:
+        return int(self.wall_pos.shape[0])
+
+
+def _lattice(lo, counts, dp):
+    """Points lo + (i + 1/2) dp for i over a regular grid with `counts` per axis."""
+    axes = [lo[a] + (np.arange(counts[a]) + 0.5) * dp for a in range(len(counts))]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    # x varies fastest in the returned order
+    pts = np.stack([m.transpose(tuple(reversed(range(len(counts))))).reshape(-1) for m in mesh], axis=1)
+    return pts
+
+
+def tank_walls(inner_lo, inner_hi, dp, layers=WALL_LAYERS):
+    """Dummy wall particles: lattice points of the outer box that lie outside the inner box.
+
+    The lattice is anchored at the outer corner (inner_lo - layers*dp), so fluid
+    placed at inner_lo + (i+1/2)dp sits on the same lattice. Each wall particle's
+    normal is the normalised sum of the unit normals of the inner faces it lies
+    beyond, pointing into the tank; its volume is dp**dim.
+    """
+    inner_lo = np.asarray(inner_lo, dtype=np.float64)
+    inner_hi = np.asarray(inner_hi, dtype=np.float64)
+    dim = inner_lo.shape[0]
+    outer_lo = inner_lo - layers * dp
+    outer_hi = inner_hi + layers * dp
+    counts = [int(math.floor((outer_hi[a] - outer_lo[a]) / dp + 1e-9)) for a in range(dim)]
+    pts = _lattice(outer_lo, counts, dp)
+    below = pts < inner_lo[None, :]
+    above = pts > inner_hi[None, :]
+    outside = np.any(below | above, axis=1)
+    pts = pts[outside]
+    normal = below[outside].astype(np.float64) - above[outside].astype(np.float64)
+    normal /= np.linalg.norm(normal, axis=1, keepdims=True)
+    vol = np.full(pts.shape[0], dp ** dim)
+    return pts, normal, vol
+
+
+def dam_break(dim=2, H=1.0, L=2.0, W=1.0, dp=None, n_per_H=40, tank=None, rho0=1.0, g=1.0,
+              t_end=None, name=None):
+    """Dam break: fluid block L (x) by H (y) [by W (z)] at rest in the corner of a tank.
+
+    2D: tank TANK_EXTENT*H square. 3D: tank TANK_EXTENT*H (x) by TANK_EXTENT*H (y) by W (z),
+    the fluid filling the full depth in z. c0 = 10 sqrt(g H) (weakly compressible,
+    Sec. 2.1), h = 1.3 dp, CFL_ad = 0.25, CFL_ac = 0.6 (Sec. 2.4).
+    """
+    if dp is None:
+        dp = H / n_per_H
+    nx = int(round(L / dp))
+    ny = int(round(H / dp))
+    if tank is None:
+        tank = TANK_EXTENT * H
+    if dim == 2:
+        fluid = _lattice(np.zeros(2), [nx, ny], dp)
+        inner_hi = np.array([tank, tank])
+    else:
+        nz = int(round(W / dp))
+        fluid = _lattice(np.zeros(3), [nx, ny, nz], dp)
+        inner_hi = np.array([tank, tank, nz * dp])
+    inner_lo = np.zeros(dim)
+    wpos, wnrm, wvol = tank_walls(inner_lo, inner_hi, dp)
+    c0 = 10.0 * math.sqrt(g * H)
+    grav = np.zeros(3)
+    grav[1] = -g
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    lo[:dim] = inner_lo - WALL_LAYERS * dp
+    hi[:dim] = inner_hi + WALL_LAYERS * dp
+    n = fluid.shape[0]
+    return Workload(
+        name=name or f"dam_break_{dim}d_{n}",
+        dim=dim, h=H_OVER_DP * dp, dp=dp, rho0=rho0, c0=c0, cfl_ad=0.25, cfl_ac=0.6,
+        u_ref=c0 / 10.0, nu=0.0, gravity=grav, lo=lo, hi=hi,
+        periodic=np.zeros(3, dtype=np.int32), free_surface=1,
+        pos=fluid, vel=np.zeros_like(fluid), rho=np.full(n, rho0),
+        mass=np.full(n, rho0 * dp ** dim),
+        wall_pos=wpos, wall_normal=wnrm, wall_vol=wvol,
+        t_end=t_end if t_end is not None else 5.0 * math.sqrt(H / g),
+        meta={"H": H, "L": nx * dp, "W": W if dim == 3 else None, "g": g},
+    )
+
+
+def dam_break_2d(n_per_H=40, **kw):
+    """2D dam break: H=1, L=2, tank 5.366, dp = H/40 gives 3200 fluid particles."""
+    return dam_break(dim=2, n_per_H=n_per_H, **kw)
+
+
+def dam_break_3d(n=80, **kw):
+    """3D dam break: fluid 2 (x) by 1 (y) by 1 (z), dp = 1/n, 2 n^3 fluid particles."""
+    return dam_break(dim=3, H=1.0, L=2.0, W=1.0, dp=1.0 / n, **kw)
+
+
+def still_tank(dim=2, H=0.5, width=None, height=None, dp=0.025, g=1.0, rho0=1.0):
+    """Fluid of depth H filling the full width of a tank, at rest (hydrostatic check)."""
+    width = width if width is not None else H
+    height = height if height is not None else 1.5 * H
+    nx = int(round(width / dp))
+    ny = int(round(H / dp))
+    if dim == 2:
+        fluid = _lattice(np.zeros(2), [nx, ny], dp)
+        inner_hi = np.array([nx * dp, height])
+    else:
+        fluid = _lattice(np.zeros(3), [nx, ny, nx], dp)
+        inner_hi = np.array([nx * dp, height, nx * dp])
+    wpos, wnrm, wvol = tank_walls(np.zeros(dim), inner_hi, dp)
+    c0 = 10.0 * math.sqrt(g * H)
+    grav = np.zeros(3)
+    grav[1] = -g
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    lo[:dim] = -WALL_LAYERS * dp
+    hi[:dim] = inner_hi + WALL_LAYERS * dp
+    n = fluid.shape[0]
+    return Workload(
+        name=f"still_tank_{dim}d_{n}", dim=dim, h=H_OVER_DP * dp, dp=dp, rho0=rho0, c0=c0,
+        cfl_ad=0.25, cfl_ac=0.6, u_ref=c0 / 10.0, nu=0.0, gravity=grav, lo=lo, hi=hi,
+        periodic=np.zeros(3, dtype=np.int32), free_surface=1,
+        pos=fluid, vel=np.zeros_like(fluid), rho=np.full(n, rho0),
+        mass=np.full(n, rho0 * dp ** dim), wall_pos=wpos, wall_normal=wnrm, wall_vol=wvol,
+        t_end=5.0 * math.sqrt(H / g), meta={"H": ny * dp, "g": g},
+    )
+
+
+def taylor_green(n=100, nu=0.01, c0=10.0, rho0=1.0):
+    """2D periodic Taylor-Green vortex on the unit square, n x n lattice, Re = 1/nu.
+
+    u = -cos(2 pi x) sin(2 pi y), v = sin(2 pi x) cos(2 pi y), rho = rho0, no gravity,
+    no walls; kinetic energy decays as exp(-16 pi^2 nu t).
+    """
+    dp = 1.0 / n
+    pos = _lattice(np.zeros(2), [n, n], dp)
+    x, y = pos[:, 0], pos[:, 1]
+    vel = np.stack([-np.cos(2 * np.pi * x) * np.sin(2 * np.pi * y),
+                    np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)], axis=1)
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    hi[:2] = 1.0
+    per = np.zeros(3, dtype=np.int32)
+    per[:2] = 1
+    N = pos.shape[0]
+    return Workload(
+        name=f"taylor_green_{n}x{n}", dim=2, h=H_OVER_DP * dp, dp=dp, rho0=rho0, c0=c0,
+        cfl_ad=0.25, cfl_ac=0.6, u_ref=c0 / 10.0, nu=nu, gravity=np.zeros(3), lo=lo, hi=hi,
+        periodic=per, free_surface=0, pos=pos, vel=vel, rho=np.full(N, rho0),
+        mass=np.full(N, rho0 * dp * dp), wall_pos=np.zeros((0, 2)), wall_normal=np.zeros((0, 2)),
+        wall_vol=np.zeros(0), t_end=1.0, meta={"U": 1.0, "L": 1.0},
+    )
+
+
+def periodic_box(dim=2, n=24, seed=0, vel_amp=0.3, rho_amp=0.01, jitter=0.1, c0=10.0):
+    """Periodic gravity-free wall-free box with seeded random velocity and density
+    perturbations and jittered lattice positions (momentum-conservation check)."""
+    rng = np.random.default_rng(seed)
+    dp = 1.0 / n
+    pos = _lattice(np.zeros(dim), [n] * dim, dp)
+    pos = pos + rng.uniform(-jitter, jitter, size=pos.shape) * dp
+    pos = np.mod(pos, 1.0)
+    N = pos.shape[0]
+    vel = rng.uniform(-vel_amp, vel_amp, size=(N, dim))
+    rho = 1.0 + rng.uniform(-rho_amp, rho_amp, size=N)
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    hi[:dim] = 1.0
+    per = np.zeros(3, dtype=np.int32)
+    per[:dim] = 1
+    return Workload(
+        name=f"periodic_box_{dim}d_{N}", dim=dim, h=H_OVER_DP * dp, dp=dp, rho0=1.0, c0=c0,
+        cfl_ad=0.25, cfl_ac=0.6, u_ref=c0 / 10.0, nu=0.0, gravity=np.zeros(3), lo=lo, hi=hi,
+        periodic=per, free_surface=0, pos=pos, vel=vel, rho=rho, mass=np.full(N, dp ** dim),
+        wall_pos=np.zeros((0, dim)), wall_normal=np.zeros((0, dim)), wall_vol=np.zeros(0),
+    )
+
+
+# ---------------------------------------------------------------------------------------
+# Seeded batched tanks.  splitmix64 (Steele, Lea, Flood 2014) drives the sampling so a
+# given seed always yields the same geometry.
+# ---------------------------------------------------------------------------------------
+_MASK64 = (1 << 64) - 1
+BATCH_BASE_SEED = 0x201012375
+
+
+def splitmix64(state: int):
+    """One splitmix64 step: returns (new_state, 64-bit output)."""
+    state = (state + 0x9E3779B97F4A7C15) & _MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return state, z ^ (z >> 31)
+
+
+def _uniforms(seed: int, k: int):
+    out = []
+    s = seed & _MASK64
+    for _ in range(k):
+        s, z = splitmix64(s)
+        out.append((z >> 11) * (1.0 / (1 << 53)))
+    return out
+
+
+def batched_dam_breaks(n_instances=256, n_min=2000, n_max=50000, base_seed=BATCH_BASE_SEED):
+    """Independent 2D dam breaks of seeded, uneven size.
+
+    Per instance s: H ~ U(0.5, 1.5), L/H ~ U(1, 3), target fluid count
+    exp(U(ln n_min, ln n_max)), dp = sqrt(L H / N_target) rounded to the lattice,
+    tank 5.366 H square, c0 = 10 sqrt(g H).
+    """
+    out = []
+    for s in range(n_instances):
+        u = _uniforms(base_seed ^ s, 3)
+        H = 0.5 + u[0]
+        L = H * (1.0 + 2.0 * u[1])
+        n_target = math.exp(math.log(n_min) + u[2] * (math.log(n_max) - math.log(n_min)))
+        dp = math.sqrt(L * H / n_target)
+        ny = max(2, int(round(H / dp)))
+        dp = H / ny
+        wl = dam_break(dim=2, H=H, L=L, dp=dp, name=f"batched_{s}")
+        out.append(wl)
+    return out
+
+
+def learned_dam_break(n_fluid=100_000):
+    """2D dam break H=1, L=2 at about n_fluid particles (447 x 224 for 1e5)."""
+    dp = math.sqrt(2.0 / n_fluid)
+    return dam_break(dim=2, H=1.0, L=2.0, dp=dp, name=f"dam_break_2d_learned")

@@ -1,0 +1,474 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed form,
+an invariant, brute force, or a value the paper prints (tests/golden/). The
+planted-mistake tests at the end show that plausible errors in the oracle
+(a dropped term, a wrong sign, a transposed operand) fail these pins.
+"""
+import json
+import math
+import os
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import wcsph as o
+from paper_2010_12375_gb300 import workloads as wk
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _free_block(dim, n, rho=None, vel=None, c0=10.0, gravity=None):
+    """A lattice block with no walls, no periodicity and no gravity (interior tests)."""
+    dp = 1.0 / n
+    pos = wk._lattice(np.zeros(dim), [n] * dim, dp)
+    N = pos.shape[0]
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    lo[:dim] = -0.5
+    hi[:dim] = 1.5
+    return SimpleNamespace(
+        dim=dim, h=1.3 * dp, dp=dp, rho0=1.0, c0=c0, cfl_ad=0.25, cfl_ac=0.6, u_ref=c0 / 10,
+        nu=0.0, gravity=np.zeros(3) if gravity is None else gravity, lo=lo, hi=hi,
+        periodic=np.zeros(3, dtype=int), free_surface=1, pos=pos,
+        vel=np.zeros_like(pos) if vel is None else vel,
+        rho=np.ones(N) if rho is None else rho, mass=np.full(N, dp ** dim),
+        wall_pos=np.zeros((0, dim)), wall_normal=np.zeros((0, dim)), wall_vol=np.zeros(0))
+
+
+def _interior(pos, margin):
+    return np.all((pos > margin) & (pos < 1.0 - margin), axis=1)
+
+
+# ---------------------------------------------------------------- kernel ------------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_wendland_normalisation(dim):
+    h = 0.37
+    if dim == 2:
+        val, _ = integrate.quad(lambda r: float(o.kernel_W(r, h, 2)) * 2 * math.pi * r, 0, 2 * h)
+    else:
+        val, _ = integrate.quad(lambda r: float(o.kernel_W(r, h, 3)) * 4 * math.pi * r * r, 0, 2 * h)
+    assert abs(val - 1.0) < 1e-10
+    assert float(o.kernel_W(2 * h, h, dim)) == 0.0
+    assert float(o.kernel_W(2.5 * h, h, dim)) == 0.0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_wendland_derivative_matches_finite_difference(dim):
+    h = 0.5
+    r = np.linspace(0.01, 1.99 * h, 57)
+    eps = 1e-6
+    fd = (o.kernel_W(r + eps, h, dim) - o.kernel_W(r - eps, h, dim)) / (2 * eps)
+    np.testing.assert_allclose(o.kernel_dW(r, h, dim), fd, rtol=1e-6, atol=1e-8)
+    assert np.all(o.kernel_dW(r, h, dim) < 0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_lattice_sum_is_partition_of_unity(dim):
+    # sum_j V_j W_ij -> 1 on a lattice (integral of W is 1); the error shrinks as h/dp grows
+    errs = [abs(o.lattice_sigma0(1.0, hr, dim) - 1.0) for hr in (1.3, 1.6, 2.0)]
+    assert errs[0] < 0.012
+    assert errs[0] > errs[1] > errs[2]
+
+
+# ---------------------------------------------------------------- neighbours --------
+def _random_problem(dim, n, seed, periodic):
+    rng = np.random.default_rng(seed)
+    h = 0.06 if dim == 2 else 0.12
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    hi[:dim] = 1.0
+    pos = rng.uniform(0, 1, size=(n, dim))
+    per = np.zeros(3, dtype=int)
+    if periodic:
+        per[:dim] = 1
+        wpos = np.zeros((0, dim))
+    else:
+        wpos = rng.uniform(0, 1, size=(n // 3, dim))
+    return SimpleNamespace(dim=dim, h=h, dp=h / 1.3, rho0=1.0, c0=10.0, cfl_ad=0.25, cfl_ac=0.6,
+                           u_ref=1.0, nu=0.0, gravity=np.zeros(3), lo=lo, hi=hi, periodic=per,
+                           free_surface=1), pos, wpos
+
+
+def _pairset(I, J):
+    return set(zip(I.tolist(), J.tolist()))
+
+
+@pytest.mark.parametrize("dim,periodic", [(2, False), (2, True), (3, False), (3, True)])
+def test_neighbour_sets_match_brute_force(dim, periodic):
+    prob, pos, wpos = _random_problem(dim, 1500 if dim == 2 else 900, 7 + dim, periodic)
+    prm = o.Params.from_problem(prob)
+    I, J, IW, KW = o.neighbour_sets(pos, wpos, prm)
+    bI, bJ = o.brute_force_pairs(pos, pos, 2 * prm.h, prm.period, same=True)
+    assert _pairset(I, J) == _pairset(bI, bJ)
+    if wpos.shape[0]:
+        bIW, bKW = o.brute_force_pairs(pos, wpos, 2 * prm.h, prm.period, same=False)
+        assert _pairset(IW, KW) == _pairset(bIW, bKW)
+    # the set is symmetric and never contains i itself
+    assert _pairset(I, J) == _pairset(J, I)
+    assert not np.any(I == J)
+
+
+@pytest.mark.parametrize("dim,periodic", [(2, False), (2, True), (3, False)])
+def test_quantised_neighbour_sets_agree_with_fp64(dim, periodic):
+    prob, pos, wpos = _random_problem(dim, 1500 if dim == 2 else 900, 3 + dim, periodic)
+    prm = o.Params.from_problem(prob)
+    a = o.neighbour_sets(pos, wpos, prm)
+    b = o.neighbour_sets_quantised(pos, wpos, prm)
+    assert _pairset(a[0], a[1]) == _pairset(b[0], b[1])
+    assert _pairset(a[2], a[3]) == _pairset(b[2], b[3])
+
+
+def test_quantisation_contract():
+    prm = o.Params.from_problem(wk.dam_break_2d())
+    cell, ncell, bits, dq, R2 = o.quantisation(prm)
+    assert cell == 2 * prm.h and bits == 22 and R2 == 2 ** 44
+    x = np.random.default_rng(1).uniform(0, 5, size=(1000, 2))
+    back = o.dequantise(o.quantise(x, prm), prm)
+    assert np.max(np.abs(back - x)) <= 0.5 * dq * (1 + 1e-9)
+    tg = o.Params.from_problem(wk.taylor_green(100))
+    cell, ncell, bits, dq, R2 = o.quantisation(tg)
+    assert ncell == [38, 38] and abs(cell * 38 - 1.0) < 1e-15 and cell >= 2 * tg.h
+
+
+def test_cell_permutation_orders_by_cell_then_id():
+    prob, pos, _ = _random_problem(2, 800, 11, False)
+    prm = o.Params.from_problem(prob)
+    ids = np.random.default_rng(2).permutation(800)
+    perm = o.cell_permutation(pos, ids, prm)
+    assert sorted(perm.tolist()) == sorted(ids.tolist())
+    cell = 2 * prm.h
+    ncx = int(math.ceil((prm.hi[0] - prm.lo[0]) / cell))
+    where = {int(i): k for k, i in enumerate(ids)}
+    c = np.floor((pos - prm.lo) / cell).astype(int)           # FP64 cell, away from edges
+    flat = c[:, 0] + ncx * c[:, 1]
+    fl = np.array([flat[where[int(i)]] for i in perm])
+    assert np.all(np.diff(fl) >= 0)
+    same = np.diff(fl) == 0
+    assert np.all(np.diff(perm)[same] > 0)
+
+
+# ---------------------------------------------------------------- Riemann solver ----
+def test_riemann_identities():
+    rng = np.random.default_rng(0)
+    rho = 1 + 0.01 * rng.uniform(-1, 1, 50)
+    U = rng.uniform(-1, 1, 50)
+    P = rng.uniform(0, 2, 50)
+    Us, Ps = o.riemann(rho, rho, U, U, P, P, 10.0)          # equal states
+    np.testing.assert_allclose(Us, U, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(Ps, P, rtol=0, atol=1e-15)
+    UL, UR = -np.abs(U), np.abs(U)                         # separating: no dissipation
+    _, Ps = o.riemann(rho, rho, UL, UR, P, P[::-1], 10.0)
+    np.testing.assert_allclose(Ps, 0.5 * (P + P[::-1]), atol=1e-15)
+
+
+def test_riemann_matches_linear_acoustic_solver_when_limiter_saturates():
+    # beta = 1 once U_L - U_R >= c/3: the textbook linearised acoustic Riemann solution
+    c, rhoL, rhoR = 10.0, 1.02, 0.99
+    UL, UR, PL, PR = 3.0, -1.0, 0.7, 0.2
+    Us, Ps = o.riemann(rhoL, rhoR, UL, UR, PL, PR, c)
+    Z = 0.5 * (rhoL + rhoR) * c                            # acoustic impedance
+    assert abs(Us - (0.5 * (UL + UR) + (PL - PR) / (2 * Z))) < 1e-14
+    assert abs(Ps - (0.5 * (PL + PR) + 0.5 * Z * (UL - UR))) < 1e-14
+    # below saturation the dissipation is reduced in proportion to 3 dU / c
+    Us2, Ps2 = o.riemann(1.0, 1.0, 0.5, 0.0, 0.0, 0.0, c)
+    assert abs(Ps2 - 0.5 * 1.0 * c * (3 * 0.5 / c) * 0.5) < 1e-14
+
+
+def test_riemann_mirror_symmetry():
+    rng = np.random.default_rng(3)
+    rL, rR = 1 + 0.01 * rng.uniform(-1, 1, (2, 40))
+    UL, UR = rng.uniform(-2, 2, (2, 40))
+    PL, PR = rng.uniform(0, 1, (2, 40))
+    Us, Ps = o.riemann(rL, rR, UL, UR, PL, PR, 10.0)
+    Us2, Ps2 = o.riemann(rR, rL, -UR, -UL, PR, PL, 10.0)   # same problem seen from j
+    np.testing.assert_allclose(Us2, -Us, atol=1e-14)
+    np.testing.assert_allclose(Ps2, Ps, atol=1e-14)
+
+
+# ---------------------------------------------------------------- operators ---------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_uniform_state_on_lattice_has_zero_acceleration(dim):
+    n = 24 if dim == 2 else 12
+    prob = wk.periodic_box(dim=dim, n=n, jitter=0.0, vel_amp=0.0, rho_amp=0.0)
+    prob.rho = np.full(prob.n_fluid, 1.003)                # uniform pressure p = c^2 0.003
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    nb = o.neighbour_sets(st.x, w.x, prm)
+    _, a = o.pressure_relaxation(st, w, nb, 0.0, 0.0, prm)
+    assert np.max(np.abs(a)) < 1e-10
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_linear_pressure_field_gives_minus_grad_p_over_rho(dim):
+    n = 40 if dim == 2 else 16
+    dp = 1.0 / n
+    pos = wk._lattice(np.zeros(dim), [n] * dim, dp)
+    k = np.array([0.3, -1.0, 0.5])[:dim]
+    c0 = 10.0
+    rho = 1.0 + (0.5 + pos @ k) / c0 ** 2
+    prob = _free_block(dim, n, rho=rho, c0=c0)
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    nb = o.neighbour_sets(st.x, w.x, prm)
+    _, a = o.pressure_relaxation(st, w, nb, 0.0, 0.0, prm)
+    inner = _interior(pos, 2.2 * prm.h)
+    got = a[inner].mean(axis=0)
+    want = -k / rho[inner].mean()
+    np.testing.assert_allclose(got, want, rtol=0.05)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_continuity_of_linear_expansion(dim):
+    # v = alpha (r - r_c): d rho/dt = -rho div v = -rho d alpha (Eq. governingeq)
+    n = 40 if dim == 2 else 16
+    dp = 1.0 / n
+    pos = wk._lattice(np.zeros(dim), [n] * dim, dp)
+    for alpha in (0.2, -0.2):
+        prob = _free_block(dim, n, vel=alpha * (pos - 0.5))
+        prm = o.Params.from_problem(prob)
+        st, w = o.state_from_problem(prob)
+        nb = o.neighbour_sets(st.x, w.x, prm)
+        out = o.density_relaxation(st, w, nb, 0.0, prm)
+        inner = _interior(pos, 2.2 * prm.h)
+        np.testing.assert_allclose(out.drho[inner], -dim * alpha, rtol=0.05)
+
+
+def test_viscous_term_matches_laplacian_of_shear_flow():
+    tg = wk.taylor_green(40, nu=0.01)
+    prm = o.Params.from_problem(tg)
+    st, w = o.state_from_problem(tg)
+    st.v[:, 0] = np.sin(2 * np.pi * st.x[:, 1])
+    st.v[:, 1] = 0.0
+    nb = o.neighbour_sets(st.x, w.x, prm)
+    a = o.viscous_acceleration(st, nb, prm)
+    expect = -0.01 * (2 * np.pi) ** 2 * np.sin(2 * np.pi * st.x[:, 1])  # nu d2u/dy2
+    ratio = np.sum(a[:, 0] * expect) / np.sum(expect * expect)
+    assert abs(ratio - 1.0) < 0.05
+    assert np.max(np.abs(a[:, 1])) < 1e-10
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_density_summation_on_lattice(dim):
+    n = 24 if dim == 2 else 10
+    prob = wk.periodic_box(dim=dim, n=n, jitter=0.0, vel_amp=0.0, rho_amp=0.0)
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    st.rho[:] = 0.5                                         # below the summation value
+    nb = o.neighbour_sets(st.x, w.x, prm)
+    rho = o.density_summation(st, w, nb, prm)
+    np.testing.assert_allclose(rho, 1.0, rtol=1e-12)
+    # uniformly compressed lattice: rho -> rho0 / s^d
+    s = 0.97
+    prob2 = _free_block(dim, 30 if dim == 2 else 14)
+    prob2.pos = prob2.pos * s
+    prob2.hi = prob2.hi * s
+    prm2 = o.Params.from_problem(prob2)
+    st2, w2 = o.state_from_problem(prob2)
+    nb2 = o.neighbour_sets(st2.x, w2.x, prm2)
+    r2 = o.density_summation(st2, w2, nb2, prm2)
+    inner = _interior(prob2.pos / s, 2.5 * prm2.h)
+    np.testing.assert_allclose(r2[inner], 1.0 / s ** dim, rtol=0.02)
+    # free surface: the max keeps the larger continuity density at the boundary
+    st2.rho[:] = 1.001
+    r3 = o.density_summation(st2, w2, nb2, prm2)
+    corner = np.argmin(np.sum(prob2.pos, axis=1))
+    assert r3[corner] == 1.001
+    prm2.free_surface = False
+    r4 = o.density_summation(st2, w2, nb2, prm2)
+    assert r4[corner] < 0.9
+
+
+# ---------------------------------------------------------------- invariants --------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_momentum_is_conserved_to_round_off(dim):
+    prob = wk.periodic_box(dim=dim, n=20 if dim == 2 else 9, seed=5)
+    prob.nu = 0.02
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    st.drho = np.random.default_rng(9).uniform(-0.1, 0.1, st.rho.shape)
+    nb = o.neighbour_sets(st.x, w.x, prm)
+    acc_prior = o.viscous_acceleration(st, nb, prm)
+    _, a = o.pressure_relaxation(st, w, nb, acc_prior, 1e-3, prm)
+    scale = np.sum(st.m[:, None] * np.abs(a))
+    assert np.max(np.abs(np.sum(st.m[:, None] * a, axis=0))) < 1e-12 * scale
+    p0 = np.sum(st.m[:, None] * st.v, axis=0)
+    st2, info = o.advection_step(st, w, prm)
+    p1 = np.sum(st2.m[:, None] * st2.v, axis=0)
+    assert info.substeps >= 3
+    assert np.max(np.abs(p1 - p0)) < 1e-13 * np.sum(st.m[:, None] * np.abs(st.v))
+    np.testing.assert_array_equal(st2.m, st.m)             # masses never change
+
+
+def test_two_particle_head_on_repels():
+    prob = _free_block(2, 2)
+    prob.pos = np.array([[0.40, 0.5], [0.40 + 1.2 * prob.h, 0.5]])
+    prob.vel = np.array([[1.0, 0.0], [-1.0, 0.0]])
+    prob.rho = np.array([1.0, 1.0])
+    prob.mass = np.array([prob.dp ** 2, prob.dp ** 2])
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    nb = o.neighbour_sets(st.x, w.x, prm)
+    _, a = o.pressure_relaxation(st, w, nb, 0.0, 0.0, prm)
+    assert a[0, 0] < 0 and a[1, 0] > 0                     # pushed apart
+    np.testing.assert_allclose(a[0], -a[1], atol=1e-14)
+    out = o.density_relaxation(st, w, nb, 0.0, prm)
+    assert np.all(out.drho > 0)                            # approaching pair compresses
+
+
+def test_free_particle_follows_ballistic_trajectory():
+    # position-based Verlet integrates a constant acceleration exactly
+    prob = _free_block(2, 20, gravity=np.array([0.0, -1.0, 0.0]))
+    prob.pos = np.array([[0.1, 0.9], [0.9, 0.1]])
+    prob.vel = np.array([[0.3, 0.2], [-0.1, 0.0]])
+    prob.rho = np.ones(2)
+    prob.mass = np.full(2, prob.dp ** 2)
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    x0, v0 = st.x.copy(), st.v.copy()
+    for _ in range(4):
+        st, _ = o.advection_step(st, w, prm)
+    t = st.t
+    g = np.array([0.0, -1.0])
+    np.testing.assert_allclose(st.x, x0 + v0 * t + 0.5 * g * t * t, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(st.v, v0 + g * t, rtol=0, atol=1e-14)
+
+
+def test_dual_criteria_time_steps_use_the_papers_constants():
+    with open(os.path.join(GOLDEN, "dual_criteria.json")) as f:
+        gold = json.load(f)
+    for case in gold["cases"]:
+        prob = _free_block(2, 2)
+        prob.h, prob.c0, prob.u_ref, prob.nu = case["h"], case["c0"], case["u_ref"], case["nu"]
+        prob.cfl_ad, prob.cfl_ac = gold["cfl_ad"], gold["cfl_ac"]
+        prm = o.Params.from_problem(prob)
+        v = np.array([[case["vmax"], 0.0], [0.0, 0.1 * case["vmax"]]])
+        assert abs(o.dt_advection(v, prm) - case["dt_ad"]) < 1e-15
+        assert abs(o.dt_acoustic(v, prm) - case["dt_ac"]) < 1e-15
+
+
+def test_substeps_cover_the_advection_step_exactly():
+    prob = wk.dam_break_2d(n_per_H=10)
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    st2, info = o.advection_step(st, w, prm)
+    assert abs(sum(info.dts) - info.dt_ad) < 1e-15
+    assert abs(st2.t - info.dt_ad) < 1e-15
+    ratio = (0.25 / max(0.0, prm.u_ref)) * (prm.c0 / 0.6)  # Dt_ad / Dt_ac at rest
+    assert info.substeps == math.ceil(ratio)
+
+
+def test_diagnostics_closed_forms():
+    prob = _free_block(2, 4, gravity=np.array([0.0, -2.0, 0.0]))
+    prm = o.Params.from_problem(prob)
+    st, _ = o.state_from_problem(prob)
+    st.v[:] = [3.0, -4.0]
+    d = o.diagnostics(st, prm)
+    M = np.sum(st.m)
+    assert abs(d["mass"] - M) < 1e-15
+    assert abs(d["kinetic"] - 0.5 * M * 25.0) < 1e-13
+    assert abs(d["potential"] - 2.0 * np.sum(st.m * st.x[:, 1])) < 1e-13
+    assert d["internal"] == 0.0 and d["max_rho_dev"] == 0.0
+    st.rho[:] = 1.01                                        # e(rho) = c^2 (ln r + 1/r - 1)
+    d = o.diagnostics(st, prm)
+    e = 100.0 * (math.log(1.01) + 1 / 1.01 - 1)
+    assert abs(d["internal"] - M * e) < 1e-15 and e > 0
+
+
+# ---------------------------------------------------------------- physics -----------
+@pytest.mark.slow
+def test_hydrostatic_still_tank():
+    tank = wk.still_tank()
+    prm = o.Params.from_problem(tank)
+    H = tank.meta["H"]
+    samples = []
+
+    def cb(k, st, info):
+        if st.t > 3.0:
+            y = st.x[:, 1]
+            mid = np.abs(y - 0.5 * H) < 0.05
+            samples.append(np.mean(o.eos_pressure(st.rho[mid], prm)))
+    o.run(tank, t_end=6.0, callback=cb)
+    p_mid = float(np.mean(samples))
+    assert abs(p_mid - prm.rho0 * 1.0 * 0.5 * H) < 0.05 * 0.5 * H
+
+
+@pytest.mark.slow
+def test_taylor_green_decay_converges_to_closed_form():
+    errs = []
+    for n in (32, 64):
+        tg = wk.taylor_green(n)
+        _, series = o.run(tg, t_end=0.1)
+        ke = np.array([s["kinetic"] for s in series])
+        t = np.array([s["t"] for s in series])
+        errs.append(np.max(np.abs(ke / ke[0] - np.exp(-16 * np.pi ** 2 * 0.01 * t))))
+    assert errs[1] < errs[0] < 0.06
+
+
+@pytest.mark.slow
+def test_dam_break_front_and_density_variation():
+    prob = wk.dam_break_2d(n_per_H=20)
+    H, g = prob.meta["H"], prob.meta["g"]
+    _, series = o.run(prob, t_end=1.2)
+    t = np.array([s["t"] for s in series])
+    front = np.array([s["front_x"] for s in series])
+    # the front stays behind the shallow-water (Ritter) front x = L + 2 sqrt(gH) t
+    assert np.all(front <= prob.meta["L"] + 2 * math.sqrt(g * H) * t + 2 * prob.dp)
+    # and has surged forward by a sizeable fraction of it
+    assert front[-1] - front[0] > 0.5 * math.sqrt(g * H) * t[-1]
+    # c0 = 10 sqrt(gH) keeps the density variation near 1 percent (Sec. 2.1)
+    with open(os.path.join(GOLDEN, "dual_criteria.json")) as f:
+        gold = json.load(f)
+    assert max(s["max_rho_dev"] for s in series) < 3 * gold["density_variation"]
+    mass = [s["mass"] for s in series]
+    assert max(mass) == min(mass)
+
+
+# ---------------------------------------------------------------- planted mistakes --
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Each plausible mistake in the oracle fails at least one pin above."""
+    # 1. wrong sign of the gradient (R2) -> head-on pair attracts
+    orig = o.kernel_dW
+    monkeypatch.setattr(o, "kernel_dW", lambda r, h, d: -orig(r, h, d))
+    with pytest.raises(AssertionError):
+        test_two_particle_head_on_repels()
+    monkeypatch.setattr(o, "kernel_dW", orig)
+    # 2. P* built from the left pressure instead of the pair average -> mirror symmetry fails
+    orig_r = o.riemann
+
+    def bad_riemann(rL, rR, UL, UR, PL, PR, c0):
+        Us, Ps = orig_r(rL, rR, UL, UR, PL, PR, c0)
+        return Us, Ps + 0.5 * (PL - PR)
+    monkeypatch.setattr(o, "riemann", bad_riemann)
+    with pytest.raises(AssertionError):
+        test_riemann_mirror_symmetry()
+    monkeypatch.setattr(o, "riemann", orig_r)
+    # 3. missing factor 2 in the momentum equation -> pressure-gradient pin fails
+    monkeypatch.setattr(o, "LIMITER", 3.0)
+    orig_pr = o.pressure_relaxation
+
+    def half_force(st, w, nb, acc_prior, dt, prm):
+        out, a = orig_pr(st, w, nb, acc_prior, dt, prm)
+        return out, 0.5 * (a - prm.gravity[None, :]) + prm.gravity[None, :]
+    monkeypatch.setattr(o, "pressure_relaxation", half_force)
+    with pytest.raises(AssertionError):
+        test_linear_pressure_field_gives_minus_grad_p_over_rho(2)
+    monkeypatch.setattr(o, "pressure_relaxation", orig_pr)
+    # 4. transposed Wendland constant (3D alpha in 2D) -> normalisation pin fails
+    orig_a = o.wendland_alpha
+    monkeypatch.setattr(o, "wendland_alpha", lambda h, d: orig_a(h, 5 - d) * h ** ((5 - d) - d))
+    with pytest.raises(AssertionError):
+        test_wendland_normalisation(2)
+    monkeypatch.setattr(o, "wendland_alpha", orig_a)
+    # 5. half step using v^n instead of v^{n+1} (R9) -> ballistic pin fails
+    orig_dr = o.density_relaxation
+
+    def stale_velocity(st, w, nb, dt, prm):
+        out = orig_dr(st, w, nb, dt, prm)
+        out.x = out.x - 0.5 * dt * dt * prm.gravity[None, :]     # v^n = v^{n+1} - dt g
+        return out
+    monkeypatch.setattr(o, "density_relaxation", stale_velocity)
+    with pytest.raises(AssertionError):
+        test_free_particle_follows_ballistic_trajectory()
