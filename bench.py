@@ -1,0 +1,335 @@
+"""Benchmark of the WCSPH hot path on the 3D dam break (one JSON line on stdout).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 159]
+
+A step is one dual-criteria advection step of the whole hot path: cell hash,
+sort, offsets, reorder, neighbour sets, Dt_ad, density re-initialisation, then
+acoustic substeps (pressure + density relaxation) until Dt_ad is covered. The
+metric is particle-substeps per second (fluid particles x acoustic substeps /
+time). Inputs are resident in HBM when the timed region starts; the particle
+state (8M particles, 256 MB) and the neighbour table (GBs) exceed the 129 MB L2.
+The e2e figure drives the same steps through the public C ABI with the state in
+pinned host memory, copied in and out every step.
+Under torchrun each rank runs an independent replica (the single dam break is
+not sharded): value = all ranks' particle-substeps / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-substeps/s, 3D dam break"
+UNIT = "particle-substeps/s"
+
+# DRAM traffic of the pressure-relaxation kernel per fluid particle, from the ncu
+# capture summarised in profiles/ (None until captured). Valid only for the kernel
+# sources whose hash is recorded with it.
+TRAFFIC_BYTES_PER_PARTICLE = None
+TRAFFIC_SOURCE_HASH = None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("sph_common.cuh", "sph_physics.cu"):
+        with open(os.path.join(ROOT, "paper_2010_12375_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"sph_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ CPU legs
+CPU_SAMPLE_N = 16      # 3D dam break at dp = 1/16: 8,192 fluid particles
+
+
+def cpu_sample_workload():
+    from paper_2010_12375_gb300 import workloads as wk
+    return wk.dam_break_3d(CPU_SAMPLE_N)
+
+
+def oracle_steps(n_steps, problem=None):
+    """Time the FP64 oracle on the bounded sample; returns (particle-substeps/s, seconds, substeps)."""
+    from oracle import wcsph as o
+    prob = problem or cpu_sample_workload()
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    sub = 0
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        st, info = o.advection_step(st, w, prm)
+        sub += info.substeps
+    dt = time.perf_counter() - t0
+    return prob.n_fluid * sub / dt, dt, sub
+
+
+def cpu_sample_text(steps):
+    return (f"3D dam break at dp = 1/{CPU_SAMPLE_N} (8,192 fluid + walls, same physics as the "
+            f"GPU workload), {steps} advection step(s) of the FP64 numpy oracle on one core")
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, as it stands."""
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_steps(1)
+    rates, secs, subs = [], 0.0, 0
+    for _ in range(args.steps):
+        r, s, k = oracle_steps(1)
+        rates.append(r)
+        secs += s
+        subs += k
+    value = CPU_SAMPLE_N ** 3 * 2 * subs / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"3D dam break, bounded CPU sample (dp = 1/{CPU_SAMPLE_N})",
+                   "n_fluid": 2 * CPU_SAMPLE_N ** 3},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": cpu_sample_text(args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2010_12375_gb300 import sph, workloads as wk
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    prob = wk.dam_break_3d(args.n)
+    N = prob.n_fluid
+    sim = sph.Simulation(prob, flags=(sph.SPH_FLAG_GRAPH if args.graph else 0), stream=stream)
+    info = sim.info()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: device-resident state
+    sph.sph_set_kernel_timing(sim.handle, not args.graph)
+    d0 = sim.diagnostics()
+    l0 = sim.kernel_launches()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t_wall = time.perf_counter()
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = sim.kernel_launches() - l0
+    d1 = sim.diagnostics()
+    ktimes, kcount = sph.sph_kernel_times(sim.handle)
+    sph.sph_set_kernel_timing(sim.handle, False)
+    substeps = d1["substeps"] - d0["substeps"]
+    fluid_pairs, wall_pairs = sim.pair_count()
+
+    # ---------------- e2e: host state in and out every step through the C ABI
+    dim = prob.dim
+    pin = lambda *shape: torch.empty(*shape, dtype=torch.float64).pin_memory()
+    h_pos, h_vel, h_rho, h_drho = pin(N, dim), pin(N, dim), pin(N), pin(N)
+    sph.sph_get_state(sim.handle, N, dim, stream, out=(h_pos, h_vel, h_rho, h_drho))
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    de0 = sim.diagnostics()
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        t_now = sim.diagnostics()["t"] if False else -1.0
+        sph.sph_set_state(sim.handle, h_pos, h_vel, h_rho, h_drho, t_now, stream)
+        sim.step(1)
+        sph.sph_get_state(sim.handle, N, dim, stream, out=(h_pos, h_vel, h_rho, h_drho))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_sub = sim.diagnostics()["substeps"] - de0["substeps"]
+    bytes_io = N * (2 * dim + 2) * 8
+
+    # ---------------- aggregate over ranks
+    per_rank = torch.tensor([ms, N * substeps, e2e_ms, N * e2e_sub], dtype=torch.float64, device=dev)
+    if world > 1:
+        ms_t = per_rank.clone()
+        dist.all_reduce(ms_t, op=dist.ReduceOp.SUM)
+        mx = per_rank.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        total_units, total_e2e_units = float(ms_t[1]), float(ms_t[3])
+        ms_max, e2e_ms_max = float(mx[0]), float(mx[2])
+    else:
+        total_units, total_e2e_units = float(per_rank[1]), float(per_rank[3])
+        ms_max, e2e_ms_max = ms, e2e_ms
+    value = total_units / (ms_max * 1e-3)
+    e2e_value = total_e2e_units / (e2e_ms_max * 1e-3)
+
+    # ---------------- roofline of the dominant kernel (pressure relaxation)
+    peak, peak_kind = measured_peaks()
+    k7_ms = ktimes[0] / max(kcount[0], 1)
+    # algorithmic bytes per launch: state read 32 B + write 28 B per particle, neighbour
+    # count 4 B, neighbour index 4 B per pair (frozen set read once)
+    k7_bytes = N * (32 + 28 + 4) + 4 * (fluid_pairs + wall_pairs)
+    achieved = k7_bytes / (k7_ms * 1e-3) / 1e9 if kcount[0] else None
+    traffic = None
+    if TRAFFIC_BYTES_PER_PARTICLE is not None and TRAFFIC_SOURCE_HASH == kernel_source_hash():
+        traffic = TRAFFIC_BYTES_PER_PARTICLE * N
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "kernel": "k_pressure_relaxation<3>", "peak_kind": peak_kind,
+            "launch_ms": k7_ms, "algorithmic_bytes_per_launch": k7_bytes,
+            "density_relaxation_ms": ktimes[1] / max(kcount[1], 1)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs, sub = oracle_steps(args.cpu_steps)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": cpu_sample_text(args.cpu_steps) + f" ({secs:.1f} s, {sub} substeps)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": f"3D dam break, fluid 2x1x1 in a 5.366x5.366x1 tank, dp = 1/{args.n}",
+                "n_fluid": N, "n_wall": prob.n_wall, "h_over_dp": 1.3,
+                "substeps": substeps, "neighbour_pairs": fluid_pairs + wall_pairs,
+                "mean_neighbours": (fluid_pairs + wall_pairs) / N,
+                "l2": "inputs larger than L2 (state 256 MB, neighbour table %.1f GB)"
+                      % (4 * N * info.capacity / 1e9),
+                "loop": "graph" if args.graph else "host-driven, one sync per substep",
+                "parallelism": f"replicas x{world}",
+            },
+            "clocks": clk,
+            "gpu_launches": launches,
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+                    "d2h_bytes_per_step": bytes_io, "steps": e2e_steps},
+            "cpu_baseline": cpu,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=159, help="3D dam break resolution: dp = 1/n, 2n^3 fluid")
+    ap.add_argument("--graph", action="store_true", help="time the CUDA-graph loop instead")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

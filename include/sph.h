@@ -1,0 +1,219 @@
+/*
+ * sph.h -- C ABI of the GB300 weakly-compressible SPH hot path (libsph.so).
+ *
+ * The library advances fluid particles with the Riemann-solver WCSPH scheme of
+ * SPHinXsys (Zhang et al., arXiv 2010.12375): a cell-linked-list neighbour
+ * search once per advection step, density re-initialisation (Eq. eqrhosum /
+ * Eq. eqrhosumnosurface), the dual-criteria time steps (Eq. dt-advection,
+ * Eq. dt-relax) and, per acoustic substep, the pressure and density relaxations
+ * of the position-based Verlet scheme (Eqs. verlet-first-half,
+ * verlet-first-mediate, verlet-first-final with Eq. riemannsph, Eq. eqeos and
+ * the one-sided wall problem of Eqs. eqriepartial, eqrienoslip, eqriepright),
+ * with a Wendland C2 kernel, dummy-particle walls and gravity.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: SPH_OK (0) or a negative SPH_E_* code. No call aborts the
+ *    process or traps the GPU. After SPH_E_DOMAIN..SPH_E_TIMEOUT the handle
+ *    stays valid for inspection (sph_get_state, sph_last_error).
+ *  - Array arguments are plain pointers to host or device memory (unified
+ *    addressing decides which); the library copies what it needs and never
+ *    keeps a caller pointer beyond the call. Vectors are interleaved per
+ *    particle: pos[k*dim + a].
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *    asynchronous on it, except those that return host values, which
+ *    synchronise that stream before returning.
+ *  - Particle order at the boundary is always the caller's order ("id" order:
+ *    row k is particle k). Inside, particles are re-sorted by cell every
+ *    advection step.
+ *  - The handle is not thread safe; calls on one handle must be serialised.
+ *
+ * Position representation (part of the contract, so results can be checked
+ * bit for bit): positions are held as fixed-point integers per axis,
+ * q = rint((x - lo) / dq), with dq = cell / 2^bits, cell = 2h (or, when axes
+ * are periodic, period / floor(period / 2h), all periodic axes sharing one
+ * period), bits = min(22, 31 - bitlength(max cells per axis)). The cell of a
+ * particle is q >> bits per axis, flattened with x fastest. Particles j != i
+ * are neighbours when sum_a (q_i,a - q_j,a)^2 < R2 (minimum image on periodic
+ * axes), R2 = ceil((2h/dq)^2) evaluated in double precision: the integer
+ * form of |r_i - r_j| < 2h.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define SPH_OK          0
+#define SPH_E_INVALID  -1   /* bad argument or parameter (h <= 0, dim not 2/3, CFL <= 0, ...) */
+#define SPH_E_CUDA     -2   /* a CUDA runtime call failed (message in sph_last_error)        */
+#define SPH_E_OOM      -3   /* device allocation failed                                     */
+#define SPH_E_DOMAIN   -4   /* a particle left the cell grid [lo, hi) on a non-periodic axis */
+#define SPH_E_UNSTABLE -5   /* NaN/Inf in the state, or a time step below 1e-12 h/c0          */
+#define SPH_E_CAPACITY -6   /* a particle has more neighbours than the per-particle capacity */
+#define SPH_E_TIMEOUT  -7   /* a bounded device-side wait expired                            */
+
+/* ---- flags (sph_params.flags) ----------------------------------------------------- */
+#define SPH_FLAG_GRAPH     1u  /* sph_step runs each advection step as one CUDA graph whose
+                                  acoustic-substep loop is a device-side conditional WHILE node */
+#define SPH_FLAG_KEEP_ACC  2u  /* keep the last dv/dt of every particle for sph_get_acceleration */
+
+typedef struct sph_handle sph_handle;   /* opaque, library-owned */
+
+/* Problem parameters (one per tank). The paper's statement of the problem:
+ * smoothing length h (Sec. 1.1), reference density rho0 and artificial sound
+ * speed c0 of the EoS p = c0^2 (rho - rho0) (Eq. eqeos), advection and acoustic
+ * CFL numbers (Sec. 2.4: 0.25 and 0.6), kinematic viscosity nu (Eq. eqviscous,
+ * eta = rho0 nu; 0 = inviscid), gravity g (Eq. governingeq). */
+typedef struct {
+  int32_t  dim;           /* 2 or 3 */
+  int32_t  free_surface;  /* 1: rho = max(rho*, rho0 sumW/sumW0) (Eq. eqrhosum); 0: without max */
+  double   h;             /* smoothing length; kernel support radius is 2h                 */
+  double   dp;            /* initial lattice spacing: sumW0 is the lattice sum at dp       */
+  double   rho0, c0;      /* reference density, artificial sound speed                    */
+  double   cfl_ad, cfl_ac;/* advection / acoustic CFL numbers                             */
+  double   u_ref;         /* speed floor in Dt_ad = cfl_ad min(h / max(|v|max, u_ref), h^2/nu) */
+  double   nu;            /* kinematic viscosity                                          */
+  double   gravity[3];
+  double   lo[3], hi[3];  /* cell-grid box (tank including its wall layers); unused axes ignored */
+  int32_t  periodic[3];   /* 1 = periodic axis with period hi - lo (>= 3 cells)             */
+  int32_t  capacity;      /* max neighbours (fluid + wall) per particle; 0 = 48 (2D) / 128 (3D) */
+  uint32_t flags;         /* SPH_FLAG_* (taken from the first instance)                    */
+} sph_params;
+
+/* FP64 conservation and bulk diagnostics of one tank. */
+typedef struct {
+  double  mass;           /* sum m                                                       */
+  double  momentum[3];    /* sum m v                                                     */
+  double  kinetic;        /* sum m |v|^2 / 2                                             */
+  double  potential;      /* -sum m g . r                                                */
+  double  internal;       /* sum m c0^2 (ln(rho/rho0) + rho0/rho - 1), the EoS energy     */
+  double  energy;         /* kinetic + potential + internal                              */
+  double  max_rho_dev;    /* max |rho/rho0 - 1|                                          */
+  double  mean_rho_dev;   /* mean |rho/rho0 - 1|                                         */
+  double  front_x;        /* max x over fluid particles                                  */
+  double  t;              /* simulated time (FP64 accumulator)                           */
+  double  dt_ad;          /* last advection step                                         */
+  int64_t n_fluid;
+  int64_t advection_steps;
+  int64_t substeps;       /* acoustic substeps taken so far                              */
+} sph_diag;
+
+/* Sizes and derived constants of a handle. */
+typedef struct {
+  int32_t dim, n_instances, capacity, bits;
+  int64_t n_fluid, n_wall, n_cells;
+  double  cell, dq, sigma0;        /* cell size, position quantum, lattice sumW0 (instance 0) */
+  int64_t R2;                      /* integer neighbour threshold (instance 0)               */
+  int64_t device_bytes;            /* device memory held by the handle                       */
+} sph_info;
+
+/* Check parameters on the host only (no GPU needed). SPH_OK or SPH_E_INVALID. */
+int sph_params_check(const sph_params* p);
+
+/* Create a handle holding n_instances independent tanks (1 = a single tank).
+ * On failure *out may still receive a handle carrying the message for
+ * sph_last_error; the caller destroys it.
+ * Instance k owns fluid rows [fluid_offsets[k], fluid_offsets[k+1]) and wall rows
+ * [wall_offsets[k], wall_offsets[k+1]); offsets may be NULL when n_instances = 1.
+ * pos, vel: [n_fluid*dim] double; rho, mass: [n_fluid] double;
+ * wall_pos, wall_normal: [n_wall*dim] double (unit normal pointing into the fluid);
+ * wall_vol: [n_wall] double. All dims equal across instances. The walls are
+ * static (wall velocity 0). d rho/dt starts at 0 and the simulated time at 0.
+ * Walls are sorted into cells once here. *out receives the handle. */
+int sph_create(const sph_params* params, int32_t n_instances,
+               const int64_t* fluid_offsets, const int64_t* wall_offsets,
+               int64_t n_fluid, const double* pos, const double* vel,
+               const double* rho, const double* mass,
+               int64_t n_wall, const double* wall_pos, const double* wall_normal,
+               const double* wall_vol, void* stream, sph_handle** out);
+
+void sph_destroy(sph_handle* h);
+
+/* Message of the last failure on this handle ("" if none). */
+const char* sph_last_error(const sph_handle* h);
+
+int sph_get_info(const sph_handle* h, sph_info* out);
+
+/* Configuration update (paper Sec. 2.4 / Sec. 6.2 mesh_cell_linked_list): hash
+ * particles to cells, sort by (cell, id), cell offsets, reorder the state, and
+ * build the neighbour set {j != i : |r_i - r_j| < 2h} of every fluid particle
+ * (fluid and wall neighbours), frozen until the next call. */
+int sph_build_cells(sph_handle* h, void* stream);
+
+/* Start an advection step: Dt_ad (Eq. dt-advection, speed floor u_ref), density
+ * re-initialisation (Eq. eqrhosum / Eq. eqrhosumnosurface; walls count in sum W,
+ * sumW0 = lattice sum at dp including self) and the viscous acceleration
+ * (Eq. eqviscous, fluid pairs, held over the substeps). Requires sph_build_cells
+ * after the last position change. dt_ad_out (host, may be NULL) receives Dt_ad
+ * of instance 0 and makes the call synchronous. */
+int sph_advection_step(sph_handle* h, double* dt_ad_out, void* stream);
+
+/* One acoustic substep for every instance whose advection step is not yet
+ * covered: dt = min(cfl_ac h / (c0 + |v|max) (Eq. dt-relax), Dt_ad - tau), then
+ * the pressure relaxation (Eq. verlet-first-half, Eq. eqeos, Eq. riemannsph
+ * momentum with the wall problem, Eq. verlet-first-mediate) and the density
+ * relaxation (Eq. verlet-first-final with Eq. riemannsph continuity).
+ * Pair geometry is recomputed from the current positions; neighbours are the
+ * frozen set. done_out (host, may be NULL) receives 1 once every instance has
+ * covered its Dt_ad; dt_out (host, may be NULL) receives instance 0's dt. Either
+ * makes the call synchronous. */
+int sph_acoustic_substep(sph_handle* h, int32_t* done_out, double* dt_out, void* stream);
+
+/* n_advection_steps complete dual-criteria steps: build cells, advection step,
+ * substeps until Dt_ad is covered. With SPH_FLAG_GRAPH each step is one CUDA
+ * graph launch (the substep loop is a device-side WHILE node); otherwise the
+ * host drives the loop, synchronising once per substep. Synchronous. */
+int sph_step(sph_handle* h, int32_t n_advection_steps, void* stream);
+
+/* FP64 diagnostics, one sph_diag per instance into out[0..n_instances) (host). */
+int sph_diagnostics(sph_handle* h, sph_diag* out, void* stream);
+
+/* Copy the state out in id order: pos, vel [n_fluid*dim], rho, drho_dt [n_fluid]
+ * (double; any pointer may be NULL). Positions are lo + q dq exactly. */
+int sph_get_state(sph_handle* h, double* pos, double* vel, double* rho, double* drho_dt,
+                  void* stream);
+
+/* Replace the state (id order, same sizes as sph_create; drho_dt may be NULL = 0)
+ * and, if t >= 0, instance 0's simulated time. Call sph_build_cells before
+ * the next advection step (sph_step does). */
+int sph_set_state(sph_handle* h, const double* pos, const double* vel, const double* rho,
+                  const double* drho_dt, double t, void* stream);
+
+/* dv/dt of the last pressure relaxation in id order [n_fluid*dim] (needs
+ * SPH_FLAG_KEEP_ACC). */
+int sph_get_acceleration(sph_handle* h, double* acc, void* stream);
+
+/* Fluid ids in cell-sorted order after the last sph_build_cells [n_fluid]. */
+int sph_get_permutation(sph_handle* h, int32_t* ids, void* stream);
+
+/* Neighbour sets of the last sph_build_cells in id order: for fluid id i,
+ * fluid_ids[i*stride .. +fluid_count[i]) holds fluid neighbour ids and
+ * wall_ids[i*stride .. +wall_count[i]) wall row indices (caller order).
+ * stride >= capacity. Order within a row is the library's traversal order. */
+int sph_get_neighbours(sph_handle* h, int32_t* fluid_count, int32_t* wall_count,
+                       int32_t* fluid_ids, int32_t* wall_ids, int32_t stride, void* stream);
+
+/* Directed fluid-fluid and fluid-wall pairs in the neighbour sets of the last
+ * sph_build_cells (host outputs; synchronous). */
+int sph_pair_count(sph_handle* h, int64_t* fluid_pairs, int64_t* wall_pairs, void* stream);
+
+/* Kernel launches the library has issued on this handle (graph nodes counted
+ * once per execution, the substep loop by the device-side substep counter). */
+int sph_kernel_launches(sph_handle* h, int64_t* out);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * each launch of the pressure and density relaxation kernels (host-driven loop
+ * only; off by default). sph_kernel_times returns accumulated milliseconds and
+ * launch counts since the last reset: [0] pressure relaxation, [1] density
+ * relaxation. */
+int sph_set_kernel_timing(sph_handle* h, int32_t enable);
+int sph_kernel_times(sph_handle* h, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_GB300_H */

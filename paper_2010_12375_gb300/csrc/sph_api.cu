@@ -1,0 +1,776 @@
+// C ABI of libsph.so: handle lifetime, parameter checks, per-tank constants,
+// the host-driven and graph-driven advection loops, state import/export.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sph.h"
+#include "sph_kernels.h"
+
+using sph::Buffers;
+using sph::Ctrl;
+using sph::Global;
+using sph::Inst;
+
+struct sph_handle {
+  Buffers b;
+  std::vector<sph_params> params;
+  std::vector<Inst> hinst;
+  uint32_t flags = 0;
+  std::string err;
+  std::vector<void*> allocs;
+  int64_t device_bytes = 0;
+  int64_t launches = 0;            // kernels launched directly by the host
+  int64_t graph_kernels = 0;       // kernels executed by graph launches
+  // graph of one advection step
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  int64_t graph_fixed = 0, graph_body = 0;
+  cudaStream_t cap_stream = nullptr;
+  // staging and host mirrors
+  double* stage = nullptr;
+  size_t stage_elems = 0;
+  double* diag_scratch = nullptr;
+  double* diag_out = nullptr;
+  Global* hglob = nullptr;         // pinned host mirror of the device status
+  // kernel timing
+  bool timing = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  double ms[2] = {0.0, 0.0};
+  int64_t timed[2] = {0, 0};
+  bool cells_valid = false;
+};
+
+namespace {
+
+constexpr int kQuantBits = 22;
+
+int fail(sph_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(sph_handle* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return fail(h, e == cudaErrorMemoryAllocation ? SPH_E_OOM : SPH_E_CUDA, m);
+}
+
+#define CK(h, call)                                            \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);   \
+  } while (0)
+
+template <typename T>
+int dalloc(sph_handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+  h->allocs.push_back((void*)*p);
+  h->device_bytes += (int64_t)(sizeof(T) * count);
+  return SPH_OK;
+}
+
+#define DALLOC(h, p, n)                    \
+  do {                                     \
+    int r_ = dalloc((h), &(p), (n));       \
+    if (r_ != SPH_OK) return r_;           \
+  } while (0)
+
+int bitlength(long long v) {
+  int b = 0;
+  while (v > 0) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
+// Wendland C2 in double (host): W(r) = alpha (1 - q/2)^4 (1 + 2q), q = r/h < 2.
+double wendland_alpha(double h, int dim) {
+  const double pi = 3.14159265358979323846;
+  return dim == 2 ? 7.0 / (4.0 * pi * h * h) : 21.0 / (16.0 * pi * h * h * h);
+}
+
+double wendland_W(double r, double h, int dim) {
+  double q = r / h;
+  if (q >= 2.0) return 0.0;
+  double t = 1.0 - 0.5 * q;
+  return wendland_alpha(h, dim) * t * t * t * t * (1.0 + 2.0 * q);
+}
+
+// sum_k W(|k| dp) over the square / cubic lattice, self included.
+double lattice_sum(double dp, double h, int dim) {
+  int kmax = (int)std::ceil(2.0 * h / dp) + 1;
+  double s = 0.0;
+  for (int kz = (dim == 3 ? -kmax : 0); kz <= (dim == 3 ? kmax : 0); ++kz)
+    for (int ky = -kmax; ky <= kmax; ++ky)
+      for (int kx = -kmax; kx <= kmax; ++kx) {
+        double r = dp * std::sqrt((double)kx * kx + (double)ky * ky + (double)kz * kz);
+        s += wendland_W(r, h, dim);
+      }
+  return s;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int check_params(const sph_params* p, std::string* why) {
+  auto bad = [&](const char* m) {
+    if (why) *why = m;
+    return SPH_E_INVALID;
+  };
+  if (!p) return bad("params is NULL");
+  if (p->dim != 2 && p->dim != 3) return bad("dim must be 2 or 3");
+  if (!finite_pos(p->h)) return bad("h must be positive");
+  if (!finite_pos(p->dp)) return bad("dp must be positive");
+  if (!finite_pos(p->rho0)) return bad("rho0 must be positive");
+  if (!finite_pos(p->c0)) return bad("c0 must be positive");
+  if (!finite_pos(p->cfl_ad) || !finite_pos(p->cfl_ac)) return bad("CFL numbers must be positive");
+  if (!(std::isfinite(p->u_ref) && p->u_ref >= 0.0)) return bad("u_ref must be >= 0");
+  if (!(std::isfinite(p->nu) && p->nu >= 0.0)) return bad("nu must be >= 0");
+  if (p->u_ref == 0.0 && !(p->nu > 0.0)) return bad("u_ref = 0 needs nu > 0 to bound Dt_ad");
+  if (p->capacity < 0 || p->capacity > 65535) return bad("capacity must be in [0, 65535]");
+  if (p->free_surface != 0 && p->free_surface != 1) return bad("free_surface must be 0 or 1");
+  double period = 0.0;
+  for (int a = 0; a < p->dim; ++a) {
+    if (!std::isfinite(p->gravity[a])) return bad("gravity must be finite");
+    if (!(std::isfinite(p->lo[a]) && std::isfinite(p->hi[a]) && p->hi[a] > p->lo[a]))
+      return bad("need lo < hi on every axis");
+    if (p->periodic[a] != 0 && p->periodic[a] != 1) return bad("periodic must be 0 or 1");
+    if (p->periodic[a]) {
+      double L = p->hi[a] - p->lo[a];
+      if (period == 0.0) period = L;
+      else if (L != period) return bad("all periodic axes must share one period");
+      if (std::floor(L / (2.0 * p->h)) < 3.0) return bad("a periodic axis needs at least 3 cells");
+    }
+  }
+  double cell = period > 0.0 ? period / std::floor(period / (2.0 * p->h)) : 2.0 * p->h;
+  for (int a = 0; a < p->dim; ++a) {
+    double nc = p->periodic[a] ? std::floor(period / (2.0 * p->h)) : std::ceil((p->hi[a] - p->lo[a]) / cell);
+    if (nc > 32768.0) return bad("more than 32768 cells on an axis");
+  }
+  return SPH_OK;
+}
+
+// Per-tank constants, following the position contract in sph.h.
+Inst make_inst(const sph_params& p) {
+  Inst I;
+  std::memset(&I, 0, sizeof(I));
+  const int d = p.dim;
+  double period = 0.0;
+  for (int a = 0; a < d; ++a)
+    if (p.periodic[a]) period = p.hi[a] - p.lo[a];
+  double cell = period > 0.0 ? period / std::floor(period / (2.0 * p.h)) : 2.0 * p.h;
+  int ncell[3] = {1, 1, 1};
+  int nmax = 1;
+  for (int a = 0; a < d; ++a) {
+    if (p.periodic[a]) ncell[a] = (int)std::floor(period / (2.0 * p.h));
+    else ncell[a] = std::max(1, (int)std::ceil((p.hi[a] - p.lo[a]) / cell));
+    nmax = std::max(nmax, ncell[a]);
+  }
+  int bits = std::min(kQuantBits, 31 - bitlength(nmax));
+  double dq = cell / (double)(1u << bits);
+  double x = 2.0 * p.h / dq;
+  long long R2 = (long long)std::ceil(x * x);
+  const double alpha = wendland_alpha(p.h, d);
+  const double sigma0 = lattice_sum(p.dp, p.h, d);
+  const double sig = alpha - sigma0;        // W(0) - sumW0
+  I.h = (float)p.h;
+  I.inv_h = (float)(1.0 / p.h);
+  I.four_h2 = (float)(4.0 * p.h * p.h);
+  I.dq = (float)dq;
+  I.inv_dq = (float)(1.0 / dq);
+  I.c0 = (float)p.c0;
+  I.c0sq = (float)(p.c0 * p.c0);
+  I.rho0 = (float)p.rho0;
+  I.w_a = (float)alpha;
+  I.dwr_a = (float)(-5.0 * alpha / (p.h * p.h));
+  I.sig_hi = (float)sig;
+  I.sig_lo = (float)(sig - (double)I.sig_hi);
+  I.rho0_over_sigma0 = (float)(p.rho0 / sigma0);
+  for (int a = 0; a < 3; ++a) I.g[a] = a < d ? (float)p.gravity[a] : 0.0f;
+  I.eta = (float)(p.rho0 * p.nu);
+  I.mass = 0.0f;
+  for (int a = 0; a < 3; ++a) {
+    I.ncell[a] = ncell[a];
+    I.period[a] = (a < d && p.periodic[a]) ? (ncell[a] << bits) : 0;
+    I.lo[a] = a < d ? p.lo[a] : 0.0;
+  }
+  I.bits = bits;
+  I.free_surface = p.free_surface;
+  I.R2 = R2;
+  I.h_d = p.h;
+  I.c0_d = p.c0;
+  I.u_ref = p.u_ref;
+  I.nu = p.nu;
+  I.cfl_ad = p.cfl_ad;
+  I.cfl_ac = p.cfl_ac;
+  I.dq_d = dq;
+  I.rho0_d = p.rho0;
+  return I;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int status_code(const Global& g) {
+  if (g.err & sph::ERR_DOMAIN) return SPH_E_DOMAIN;
+  if (g.err & sph::ERR_CAPACITY) return SPH_E_CAPACITY;
+  if (g.err & (sph::ERR_NAN | sph::ERR_DT)) return SPH_E_UNSTABLE;
+  if (g.err & sph::ERR_TIMEOUT) return SPH_E_TIMEOUT;
+  return SPH_OK;
+}
+
+// Synchronise `s`, read the device status and turn error bits into a code.
+int sync_status(sph_handle* h, cudaStream_t s) {
+  CK(h, cudaMemcpyAsync(h->hglob, h->b.glob, sizeof(Global), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  int code = status_code(*h->hglob);
+  if (code != SPH_OK) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "device error bits 0x%x (first at slot %lld)", h->hglob->err,
+                  (long long)h->hglob->bad_index);
+    h->err = buf;
+  }
+  return code;
+}
+
+void enqueue_build(sph_handle* h, cudaStream_t s, int64_t* n) {
+  sph::launch_hash(h->b, s, n);
+  sph::launch_sort_fluid(h->b, s, n);
+  sph::launch_neighbours(h->b, s, n);
+}
+
+void enqueue_advection(sph_handle* h, cudaStream_t s, int64_t* n) {
+  sph::launch_dt_advection(h->b, s, n);
+  sph::launch_density(h->b, s, n);
+  sph::launch_viscous(h->b, s, n);
+}
+
+void enqueue_substep(sph_handle* h, cudaStream_t s, bool use_cond, int64_t* n) {
+  sph::launch_dt_acoustic(h->b, s, h->cond, use_cond, n);
+  if (h->timing && !use_cond) cudaEventRecord(h->ev[0], s);
+  sph::launch_pressure_relaxation(h->b, s, n);
+  if (h->timing && !use_cond) cudaEventRecord(h->ev[1], s);
+  sph::launch_density_relaxation(h->b, s, n);
+  if (h->timing && !use_cond) cudaEventRecord(h->ev[2], s);
+}
+
+int build_graph(sph_handle* h) {
+  if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = h->cap_stream;
+  cudaGraph_t g = nullptr;
+  CK(h, cudaGraphCreate(&g, 0));
+  CK(h, cudaGraphConditionalHandleCreate(&h->cond, g, 1, cudaGraphCondAssignDefault));
+  int64_t fixed = 0, body_n = 0;
+  CK(h, cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_build(h, cs, &fixed);
+  enqueue_advection(h, cs, &fixed);
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(h, cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h->cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CK(h, cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(h, cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CK(h, cudaStreamEndCapture(cs, &g));
+  CK(h, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_substep(h, cs, true, &body_n);
+  CK(h, cudaStreamEndCapture(cs, &body));
+  CK(h, cudaGraphInstantiate(&h->gexec, g, 0));
+  h->graph = g;
+  h->graph_fixed = fixed;
+  h->graph_body = body_n;
+  return SPH_OK;
+}
+
+int ensure_stage(sph_handle* h, size_t elems) {
+  if (h->stage_elems >= elems) return SPH_OK;
+  if (h->stage) {
+    cudaFree(h->stage);
+    h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)h->stage), h->allocs.end());
+    h->device_bytes -= (int64_t)(h->stage_elems * sizeof(double));
+    h->stage = nullptr;
+  }
+  DALLOC(h, h->stage, elems);
+  h->stage_elems = elems;
+  return SPH_OK;
+}
+
+// Bring caller arrays onto the device: device pointers are used as they are,
+// host arrays go through the staging buffer at offset `off`.
+const double* device_view(sph_handle* h, const double* p, size_t elems, size_t off, cudaStream_t s,
+                          cudaError_t* e) {
+  *e = cudaSuccess;
+  if (!p || is_device_ptr(p)) return p;
+  *e = cudaMemcpyAsync(h->stage + off, p, sizeof(double) * elems, cudaMemcpyHostToDevice, s);
+  return h->stage + off;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sph_params_check(const sph_params* p) { return check_params(p, nullptr); }
+
+const char* sph_last_error(const sph_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+void sph_destroy(sph_handle* h) {
+  if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->hglob) cudaFreeHost(h->hglob);
+  delete h;
+}
+
+int sph_create(const sph_params* params, int32_t n_instances, const int64_t* fluid_offsets,
+               const int64_t* wall_offsets, int64_t n_fluid, const double* pos, const double* vel,
+               const double* rho, const double* mass, int64_t n_wall, const double* wall_pos,
+               const double* wall_normal, const double* wall_vol, void* stream, sph_handle** out) {
+  if (!out) return SPH_E_INVALID;
+  *out = nullptr;
+  if (!params || n_instances < 1 || n_fluid < 0 || n_wall < 0) return SPH_E_INVALID;
+  if (n_fluid > 0 && (!pos || !vel || !rho || !mass)) return SPH_E_INVALID;
+  if (n_wall > 0 && (!wall_pos || !wall_normal || !wall_vol)) return SPH_E_INVALID;
+  if (n_instances > 1 && (!fluid_offsets || !wall_offsets)) return SPH_E_INVALID;
+  if (n_fluid >= (1ll << 31) || n_wall >= (1ll << 31)) return SPH_E_INVALID;
+  for (int k = 0; k < n_instances; ++k) {
+    if (check_params(&params[k], nullptr) != SPH_OK) return SPH_E_INVALID;
+    if (params[k].dim != params[0].dim) return SPH_E_INVALID;
+  }
+  std::vector<int64_t> fo(n_instances + 1), wo(n_instances + 1);
+  if (n_instances == 1) {
+    fo[0] = 0; fo[1] = n_fluid; wo[0] = 0; wo[1] = n_wall;
+  } else {
+    for (int k = 0; k <= n_instances; ++k) {
+      fo[k] = fluid_offsets[k];
+      wo[k] = wall_offsets[k];
+    }
+  }
+  if (fo[0] != 0 || fo[n_instances] != n_fluid || wo[0] != 0 || wo[n_instances] != n_wall)
+    return SPH_E_INVALID;
+  for (int k = 0; k < n_instances; ++k)
+    if (fo[k + 1] < fo[k] || wo[k + 1] < wo[k]) return SPH_E_INVALID;
+
+  sph_handle* h = new sph_handle();
+  *out = h;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int dim = params[0].dim;
+  h->params.assign(params, params + n_instances);
+  h->flags = params[0].flags;
+  Buffers& b = h->b;
+  b.n = n_fluid;
+  b.nw = n_wall;
+  b.n_inst = n_instances;
+  b.dim = dim;
+  b.cap = params[0].capacity > 0 ? params[0].capacity : (dim == 2 ? 48 : 128);
+  int64_t n_cells = 0;
+  bool any_visc = false;
+  for (int k = 0; k < n_instances; ++k) {
+    Inst I = make_inst(params[k]);
+    I.cell_base = n_cells;
+    long long nc = 1;
+    for (int a = 0; a < dim; ++a) nc *= I.ncell[a];
+    n_cells += nc;
+    I.fluid_begin = fo[k];
+    I.fluid_end = fo[k + 1];
+    I.wall_begin = wo[k];
+    I.wall_end = wo[k + 1];
+    if (params[k].nu > 0.0) any_visc = true;
+    h->hinst.push_back(I);
+  }
+  if (n_cells >= (1ll << 32) - 1) return fail(h, SPH_E_INVALID, "too many cells");
+  b.n_cells = n_cells;
+
+  // masses: one value per tank when uniform, else a per-particle array
+  std::vector<double> hm(n_fluid);
+  if (n_fluid) {
+    cudaError_t e = cudaMemcpy(hm.data(), mass, sizeof(double) * n_fluid, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy masses");
+  }
+  bool uniform = true;
+  for (int k = 0; k < n_instances; ++k) {
+    for (int64_t i = fo[k]; i < fo[k + 1]; ++i)
+      if (hm[i] != hm[fo[k]]) uniform = false;
+    if (fo[k + 1] > fo[k]) h->hinst[k].mass = (float)hm[fo[k]];
+  }
+
+  const int64_t nmax = std::max<int64_t>(n_fluid, n_wall);
+  DALLOC(h, b.inst, n_instances);
+  DALLOC(h, b.ctrl, n_instances);
+  DALLOC(h, b.glob, 1);
+  DALLOC(h, b.PS, n_fluid);
+  DALLOC(h, b.VS, n_fluid);
+  DALLOC(h, b.PH, nmax);
+  DALLOC(h, b.VH, nmax);
+  DALLOC(h, b.id, n_fluid);
+  DALLOC(h, b.cell, nmax);
+  DALLOC(h, b.rank, nmax);
+  DALLOC(h, b.key, nmax);
+  DALLOC(h, b.src, nmax);
+  DALLOC(h, b.count, n_cells);
+  DALLOC(h, b.fstart, n_cells + 1);
+  DALLOC(h, b.wstart, n_cells + 1);
+  DALLOC(h, b.scan_tmp, sph::scan_tmp_elems(n_cells));
+  DALLOC(h, b.WP, n_wall);
+  DALLOC(h, b.WN, n_wall);
+  DALLOC(h, b.wid, n_wall);
+  DALLOC(h, b.nbr, (size_t)n_fluid * b.cap);
+  DALLOC(h, b.nbc, n_fluid);
+  if (!uniform) {
+    DALLOC(h, b.mass, n_fluid);
+    DALLOC(h, b.mass_tmp, n_fluid);
+    std::vector<float> fm(hm.begin(), hm.end());
+    CK(h, cudaMemcpy(b.mass, fm.data(), sizeof(float) * n_fluid, cudaMemcpyHostToDevice));
+  }
+  if (any_visc) {
+    DALLOC(h, b.acc_prior, n_fluid);
+    CK(h, cudaMemset(b.acc_prior, 0, sizeof(float4) * std::max<int64_t>(n_fluid, 1)));
+  }
+  if (h->flags & SPH_FLAG_KEEP_ACC) {
+    DALLOC(h, b.acc_keep, n_fluid);
+    CK(h, cudaMemset(b.acc_keep, 0, sizeof(float4) * std::max<int64_t>(n_fluid, 1)));
+  }
+  if (n_instances > 1) {
+    std::vector<int> io(n_fluid), wio(n_wall);
+    for (int k = 0; k < n_instances; ++k) {
+      for (int64_t i = fo[k]; i < fo[k + 1]; ++i) io[i] = k;
+      for (int64_t i = wo[k]; i < wo[k + 1]; ++i) wio[i] = k;
+    }
+    int *dio = nullptr, *dwio = nullptr;
+    DALLOC(h, dio, n_fluid);
+    DALLOC(h, dwio, n_wall);
+    if (n_fluid) CK(h, cudaMemcpy(dio, io.data(), sizeof(int) * n_fluid, cudaMemcpyHostToDevice));
+    if (n_wall) CK(h, cudaMemcpy(dwio, wio.data(), sizeof(int) * n_wall, cudaMemcpyHostToDevice));
+    b.inst_of = dio;
+    b.winst_of = dwio;
+  }
+  DALLOC(h, h->diag_scratch, sph::diag_scratch_elems(b));
+  DALLOC(h, h->diag_out, (size_t)n_instances * sph::kDiagFields);
+  CK(h, cudaMallocHost((void**)&h->hglob, sizeof(Global)));
+  {
+    int r = ensure_stage(h, std::max<size_t>((size_t)n_fluid * (2 * dim + 2), (size_t)n_wall * (2 * dim + 1)));
+    if (r != SPH_OK) return r;
+  }
+  CK(h, cudaMemcpy(b.inst, h->hinst.data(), sizeof(Inst) * n_instances, cudaMemcpyHostToDevice));
+  std::vector<Ctrl> hc(n_instances);
+  std::memset(hc.data(), 0, sizeof(Ctrl) * n_instances);
+  CK(h, cudaMemcpy(b.ctrl, hc.data(), sizeof(Ctrl) * n_instances, cudaMemcpyHostToDevice));
+  CK(h, cudaMemset(b.glob, 0, sizeof(Global)));
+  for (auto& e : h->ev) CK(h, cudaEventCreate(&e));
+
+  // walls: import and sort into cells once
+  if (n_wall) {
+    cudaError_t e1, e2, e3;
+    const double* wp = device_view(h, wall_pos, (size_t)n_wall * dim, 0, s, &e1);
+    const double* wn = device_view(h, wall_normal, (size_t)n_wall * dim, (size_t)n_wall * dim, s, &e2);
+    const double* wv = device_view(h, wall_vol, (size_t)n_wall, (size_t)n_wall * dim * 2, s, &e3);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+      return cuda_fail(h, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "copy walls");
+    sph::launch_import_walls(b, wp, wn, wv, s);
+    CK(h, cudaStreamSynchronize(s));
+  }
+  sph::sort_walls(b, b.PH, b.VH, b.wid, s);
+  CK(h, cudaGetLastError());
+  int r = sph_set_state(h, pos, vel, rho, nullptr, 0.0, stream);
+  if (r != SPH_OK) return r;
+  return sync_status(h, s);
+}
+
+int sph_get_info(const sph_handle* h, sph_info* out) {
+  if (!h || !out) return SPH_E_INVALID;
+  const Inst& I = h->hinst[0];
+  out->dim = h->b.dim;
+  out->n_instances = h->b.n_inst;
+  out->capacity = h->b.cap;
+  out->bits = I.bits;
+  out->n_fluid = h->b.n;
+  out->n_wall = h->b.nw;
+  out->n_cells = h->b.n_cells;
+  out->cell = I.dq_d * (double)(1u << I.bits);
+  out->dq = I.dq_d;
+  out->sigma0 = lattice_sum(h->params[0].dp, h->params[0].h, h->b.dim);
+  out->R2 = I.R2;
+  out->device_bytes = h->device_bytes;
+  return SPH_OK;
+}
+
+int sph_set_state(sph_handle* h, const double* pos, const double* vel, const double* rho,
+                  const double* drho_dt, double t, void* stream) {
+  if (!h) return SPH_E_INVALID;
+  Buffers& b = h->b;
+  if (b.n > 0 && (!pos || !vel || !rho)) return fail(h, SPH_E_INVALID, "pos, vel and rho are required");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)b.n, d = (size_t)b.dim;
+  if (b.n > 0) {
+    cudaError_t e[4];
+    const double* p = device_view(h, pos, n * d, 0, s, &e[0]);
+    const double* v = device_view(h, vel, n * d, n * d, s, &e[1]);
+    const double* r = device_view(h, rho, n, 2 * n * d, s, &e[2]);
+    const double* dr = device_view(h, drho_dt, n, 2 * n * d + n, s, &e[3]);
+    for (auto ee : e)
+      if (ee != cudaSuccess) return cuda_fail(h, ee, "copy state");
+    sph::launch_import(b, p, v, r, dr, s);
+    ++h->launches;
+  }
+  // slot k holds caller row k until the next cell build
+  std::vector<int> iota(b.n);
+  for (int64_t i = 0; i < b.n; ++i) iota[i] = (int)i;
+  if (b.n) CK(h, cudaMemcpyAsync(b.id, iota.data(), sizeof(int) * b.n, cudaMemcpyHostToDevice, s));
+  sph::launch_vmax(b, s, &h->launches);
+  if (t >= 0.0) {
+    CK(h, cudaMemcpyAsync(&b.ctrl[0].t, &t, sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  CK(h, cudaStreamSynchronize(s));          // the host vectors above must outlive the copies
+  h->cells_valid = false;
+  CK(h, cudaGetLastError());
+  return SPH_OK;
+}
+
+int sph_build_cells(sph_handle* h, void* stream) {
+  if (!h) return SPH_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  enqueue_build(h, s, &h->launches);
+  CK(h, cudaGetLastError());
+  h->cells_valid = true;
+  return SPH_OK;
+}
+
+int sph_advection_step(sph_handle* h, double* dt_ad_out, void* stream) {
+  if (!h) return SPH_E_INVALID;
+  if (!h->cells_valid) return fail(h, SPH_E_INVALID, "sph_build_cells must run after a state change");
+  cudaStream_t s = (cudaStream_t)stream;
+  enqueue_advection(h, s, &h->launches);
+  CK(h, cudaGetLastError());
+  if (dt_ad_out) {
+    CK(h, cudaMemcpyAsync(dt_ad_out, &h->b.ctrl[0].dt_ad, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return sync_status(h, s);
+  }
+  return SPH_OK;
+}
+
+int sph_acoustic_substep(sph_handle* h, int32_t* done_out, double* dt_out, void* stream) {
+  if (!h) return SPH_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  enqueue_substep(h, s, false, &h->launches);
+  CK(h, cudaGetLastError());
+  if (done_out || dt_out || h->timing) {
+    if (dt_out) CK(h, cudaMemcpyAsync(dt_out, &h->b.ctrl[0].dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    int r = sync_status(h, s);
+    if (done_out) *done_out = h->hglob->active ? 0 : 1;
+    if (h->timing && h->b.n > 0) {
+      float a = 0.f, c = 0.f;
+      cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+      cudaEventElapsedTime(&c, h->ev[1], h->ev[2]);
+      h->ms[0] += a;
+      h->ms[1] += c;
+      h->timed[0] += 1;
+      h->timed[1] += 1;
+    }
+    return r;
+  }
+  return SPH_OK;
+}
+
+int sph_step(sph_handle* h, int32_t n_advection_steps, void* stream) {
+  if (!h || n_advection_steps < 0) return SPH_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((h->flags & SPH_FLAG_GRAPH) && !h->timing) {
+    if (!h->gexec) {
+      int r = build_graph(h);
+      if (r != SPH_OK) return r;
+    }
+    CK(h, cudaMemcpyAsync(h->hglob, h->b.glob, sizeof(Global), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    long long sub0 = h->hglob->substeps;
+    for (int k = 0; k < n_advection_steps; ++k) CK(h, cudaGraphLaunch(h->gexec, s));
+    int r = sync_status(h, s);
+    h->graph_kernels += (int64_t)n_advection_steps * h->graph_fixed +
+                        (int64_t)(h->hglob->substeps - sub0) * h->graph_body;
+    h->cells_valid = true;
+    return r;
+  }
+  for (int k = 0; k < n_advection_steps; ++k) {
+    enqueue_build(h, s, &h->launches);
+    h->cells_valid = true;
+    enqueue_advection(h, s, &h->launches);
+    for (int guard = 0;; ++guard) {
+      int32_t done = 0;
+      int r = sph_acoustic_substep(h, &done, nullptr, stream);
+      if (r != SPH_OK) return r;
+      if (done) break;
+      if (guard > 1000000) return fail(h, SPH_E_UNSTABLE, "substep loop did not finish");
+    }
+  }
+  return sync_status(h, s);
+}
+
+int sph_diagnostics(sph_handle* h, sph_diag* out, void* stream) {
+  if (!h || !out) return SPH_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = h->b.n_inst;
+  sph::launch_diagnostics(h->b, h->diag_scratch, h->diag_out, s, &h->launches);
+  std::vector<double> f((size_t)K * sph::kDiagFields);
+  std::vector<Ctrl> c(K);
+  CK(h, cudaMemcpyAsync(f.data(), h->diag_out, sizeof(double) * f.size(), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaMemcpyAsync(c.data(), h->b.ctrl, sizeof(Ctrl) * K, cudaMemcpyDeviceToHost, s));
+  int r = sync_status(h, s);
+  for (int k = 0; k < K; ++k) {
+    const double* v = &f[(size_t)k * sph::kDiagFields];
+    sph_diag& d = out[k];
+    std::memset(&d, 0, sizeof(d));
+    d.mass = v[0];
+    d.momentum[0] = v[1];
+    d.momentum[1] = v[2];
+    d.momentum[2] = v[3];
+    d.kinetic = v[4];
+    d.potential = v[5];
+    d.internal = v[6];
+    d.energy = v[4] + v[5] + v[6];
+    d.n_fluid = (int64_t)v[10];
+    d.mean_rho_dev = d.n_fluid ? v[7] / (double)d.n_fluid : 0.0;
+    d.max_rho_dev = v[8];
+    d.front_x = d.n_fluid ? v[9] : 0.0;
+    d.t = c[k].t;
+    d.dt_ad = c[k].dt_ad;
+    d.advection_steps = c[k].adv_steps;
+    d.substeps = c[k].substeps;
+  }
+  return r;
+}
+
+int sph_get_state(sph_handle* h, double* pos, double* vel, double* rho, double* drho_dt,
+                  void* stream) {
+  if (!h) return SPH_E_INVALID;
+  Buffers& b = h->b;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)b.n, d = (size_t)b.dim;
+  if (n == 0) return SPH_OK;
+  double* dst[4] = {pos, vel, rho, drho_dt};
+  size_t sz[4] = {n * d, n * d, n, n};
+  size_t off[4] = {0, n * d, 2 * n * d, 2 * n * d + n};
+  double* tgt[4];
+  bool dev[4];
+  for (int k = 0; k < 4; ++k) {
+    dev[k] = dst[k] && is_device_ptr(dst[k]);
+    tgt[k] = dst[k] ? (dev[k] ? dst[k] : h->stage + off[k]) : nullptr;
+  }
+  sph::launch_export(b, tgt[0], tgt[1], tgt[2], tgt[3], s);
+  ++h->launches;
+  for (int k = 0; k < 4; ++k)
+    if (dst[k] && !dev[k])
+      CK(h, cudaMemcpyAsync(dst[k], tgt[k], sizeof(double) * sz[k], cudaMemcpyDeviceToHost, s));
+  return sync_status(h, s);
+}
+
+int sph_get_acceleration(sph_handle* h, double* acc, void* stream) {
+  if (!h || !acc) return SPH_E_INVALID;
+  if (!h->b.acc_keep) return fail(h, SPH_E_INVALID, "create the handle with SPH_FLAG_KEEP_ACC");
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t e = (size_t)h->b.n * h->b.dim;
+  bool dev = is_device_ptr(acc);
+  double* tgt = dev ? acc : h->stage;
+  sph::launch_export_acc(h->b, tgt, s);
+  ++h->launches;
+  if (!dev && e) CK(h, cudaMemcpyAsync(acc, tgt, sizeof(double) * e, cudaMemcpyDeviceToHost, s));
+  return sync_status(h, s);
+}
+
+int sph_get_permutation(sph_handle* h, int32_t* ids, void* stream) {
+  if (!h || !ids) return SPH_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->b.n) CK(h, cudaMemcpyAsync(ids, h->b.id, sizeof(int) * h->b.n, cudaMemcpyDefault, s));
+  return sync_status(h, s);
+}
+
+int sph_get_neighbours(sph_handle* h, int32_t* fluid_count, int32_t* wall_count, int32_t* fluid_ids,
+                       int32_t* wall_ids, int32_t stride, void* stream) {
+  if (!h || !fluid_count || !wall_count || !fluid_ids || !wall_ids) return SPH_E_INVALID;
+  if (stride < h->b.cap) return fail(h, SPH_E_INVALID, "stride must be >= capacity");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)h->b.n;
+  if (n == 0) return SPH_OK;
+  int32_t *fc, *wc, *fi, *wi;
+  CK(h, cudaMalloc(&fc, sizeof(int32_t) * n));
+  CK(h, cudaMalloc(&wc, sizeof(int32_t) * n));
+  CK(h, cudaMalloc(&fi, sizeof(int32_t) * n * stride));
+  CK(h, cudaMalloc(&wi, sizeof(int32_t) * n * stride));
+  sph::launch_export_neighbours(h->b, fc, wc, fi, wi, stride, s);
+  ++h->launches;
+  cudaMemcpyAsync(fluid_count, fc, sizeof(int32_t) * n, cudaMemcpyDefault, s);
+  cudaMemcpyAsync(wall_count, wc, sizeof(int32_t) * n, cudaMemcpyDefault, s);
+  cudaMemcpyAsync(fluid_ids, fi, sizeof(int32_t) * n * stride, cudaMemcpyDefault, s);
+  cudaMemcpyAsync(wall_ids, wi, sizeof(int32_t) * n * stride, cudaMemcpyDefault, s);
+  int r = sync_status(h, s);
+  cudaFree(fc);
+  cudaFree(wc);
+  cudaFree(fi);
+  cudaFree(wi);
+  return r;
+}
+
+int sph_pair_count(sph_handle* h, int64_t* fluid_pairs, int64_t* wall_pairs, void* stream) {
+  if (!h || !fluid_pairs || !wall_pairs) return SPH_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(h->diag_out);
+  unsigned long long hv[2] = {0, 0};
+  sph::launch_pair_count(h->b, d, s);
+  ++h->launches;
+  CK(h, cudaMemcpyAsync(hv, d, sizeof(hv), cudaMemcpyDeviceToHost, s));
+  int r = sync_status(h, s);
+  *fluid_pairs = (int64_t)hv[0];
+  *wall_pairs = (int64_t)hv[1];
+  return r;
+}
+
+int sph_kernel_launches(sph_handle* h, int64_t* out) {
+  if (!h || !out) return SPH_E_INVALID;
+  *out = h->launches + h->graph_kernels;
+  return SPH_OK;
+}
+
+int sph_set_kernel_timing(sph_handle* h, int32_t enable) {
+  if (!h) return SPH_E_INVALID;
+  h->timing = enable != 0;
+  h->ms[0] = h->ms[1] = 0.0;
+  h->timed[0] = h->timed[1] = 0;
+  return SPH_OK;
+}
+
+int sph_kernel_times(sph_handle* h, double* ms, int64_t* launches) {
+  if (!h) return SPH_E_INVALID;
+  if (ms) {
+    ms[0] = h->ms[0];
+    ms[1] = h->ms[1];
+  }
+  if (launches) {
+    launches[0] = h->timed[0];
+    launches[1] = h->timed[1];
+  }
+  return SPH_OK;
+}
+
+}  // extern "C"

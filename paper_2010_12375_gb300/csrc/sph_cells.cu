@@ -1,0 +1,361 @@
+// Configuration update of the WCSPH hot path (cell-linked list, paper Sec. 6.2
+// mesh_cell_linked_list, refreshed once per advection step as Sec. 2.4 fixes):
+//   hash      particle -> cell (integer: cell = q >> bits per axis, flattened x fastest)
+//   sort      counting sort on the cell digit (a one-digit radix sort with radix =
+//             number of cells) followed by an in-cell sort by caller id, which makes
+//             the order the unique (cell, id) order, independent of history
+//   offsets   exclusive scan of the cell counts
+//   reorder   gather of the 32-byte particle records into cell order
+//   neighbours frozen set {j != i : |r_i - r_j| < 2h}, column-major ELL rows
+#include <cstdio>
+
+#include "sph_kernels.h"
+
+namespace sph {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+inline unsigned grid_for(int64_t n, int block = kBlock) {
+  return (unsigned)((n + block - 1) / block);
+}
+
+__device__ __forceinline__ void raise_error(Global* g, int bit, long long idx) {
+  int old = atomicOr(&g->err, bit);
+  if (old == 0) g->bad_index = idx;
+}
+
+// ---------------------------------------------------------------- scan ---------------
+// Block-level exclusive scan of kScanTile elements; block totals to `sums`.
+__global__ void k_scan_tile(const uint32_t* in, uint32_t* out,   // may alias (in-place)
+                            int64_t n, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t local = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t idx = base + k;
+    v[k] = idx < n ? in[idx] : 0u;
+    local += v[k];
+  }
+  // inclusive scan of per-thread totals inside the warp
+  unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (unsigned)o) incl += y;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= (unsigned)o) wi += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;   // exclusive warp offsets
+    if (lane == 31 && sums) sums[blockIdx.x] = wi;           // block total
+  }
+  __syncthreads();
+  uint32_t run = warp_tot[warp] + incl - local;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t idx = base + k;
+    if (idx < n) out[idx] = run;
+    run += v[k];
+  }
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, int64_t n, const uint32_t* __restrict__ offs) {
+  int64_t idx = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+  uint32_t add = offs[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t j = idx + (int64_t)k * kScanThreads;
+    if (j < n) out[j] += add;
+  }
+}
+
+__global__ void k_scan_total(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n) {
+  out[n] = n ? out[n - 1] + in[n - 1] : 0u;
+}
+
+}  // namespace
+
+size_t scan_tmp_elems(int64_t n) {
+  size_t total = 0;
+  int64_t m = n;
+  while (m > kScanTile) {
+    m = (m + kScanTile - 1) / kScanTile;
+    total += (size_t)m;
+  }
+  return total + 1;
+}
+
+static void scan_rec(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s,
+                     int64_t* launches) {
+  int64_t blocks = (n + kScanTile - 1) / kScanTile;
+  if (blocks <= 1) {
+    k_scan_tile<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    ++*launches;
+    return;
+  }
+  uint32_t* sums = tmp;
+  k_scan_tile<<<(unsigned)blocks, kScanThreads, 0, s>>>(in, out, n, sums);
+  scan_rec(sums, sums, blocks, tmp + blocks, s, launches);
+  k_scan_add<<<(unsigned)blocks, kScanThreads, 0, s>>>(out, n, sums);
+  *launches += 2;
+}
+
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total.
+void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s,
+                    int64_t* launches) {
+  if (n > 0) scan_rec(in, out, n, tmp, s, launches);
+  k_scan_total<<<1, 1, 0, s>>>(in, out, n);
+  ++*launches;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- hash ---------------
+template <int D>
+__global__ void k_hash(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst_of,
+                       const Inst* __restrict__ inst, uint32_t* __restrict__ cell,
+                       uint32_t* __restrict__ count, uint32_t* __restrict__ rank, Global* g) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Inst& I = inst[inst_of ? inst_of[i] : 0];
+  int4 p = P[i];
+  int q[3] = {p.x, p.y, p.z};
+  long long c = 0, stride = 1;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    int ca = q[a] >> I.bits;
+    if (ca < 0 || ca >= I.ncell[a]) {
+      raise_error(g, ERR_DOMAIN, i);
+      ca = ca < 0 ? 0 : I.ncell[a] - 1;
+    }
+    c += (long long)ca * stride;
+    stride *= I.ncell[a];
+  }
+  c += I.cell_base;
+  cell[i] = (uint32_t)c;
+  rank[i] = atomicAdd(&count[c], 1u);
+}
+
+__global__ void k_scatter(int64_t n, const uint32_t* __restrict__ cell, const uint32_t* __restrict__ rank,
+                          const uint32_t* __restrict__ start, const int* __restrict__ id,
+                          int* __restrict__ key, int* __restrict__ src) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t d = start[cell[i]] + rank[i];
+  key[d] = id[i];
+  src[d] = (int)i;
+}
+
+// Insertion sort of each cell's slots by id (cells hold a few tens of particles).
+__global__ void k_cell_sort(int64_t n_cells, const uint32_t* __restrict__ start, int* __restrict__ key,
+                            int* __restrict__ src) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  uint32_t b = start[c], e = start[c + 1];
+  for (uint32_t k = b + 1; k < e; ++k) {
+    int kk = key[k], ss = src[k];
+    uint32_t m = k;
+    while (m > b && key[m - 1] > kk) {
+      key[m] = key[m - 1];
+      src[m] = src[m - 1];
+      --m;
+    }
+    key[m] = kk;
+    src[m] = ss;
+  }
+}
+
+__global__ void k_reorder(int64_t n, const int* __restrict__ src, const int4* __restrict__ Pin,
+                          const float4* __restrict__ Vin, int4* __restrict__ Pout,
+                          float4* __restrict__ Vout, const float* __restrict__ min,
+                          float* __restrict__ mout) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = src[i];
+  Pout[i] = Pin[s];
+  Vout[i] = Vin[s];
+  if (min) mout[i] = min[s];
+}
+
+__global__ void k_copy_back(int64_t n, const int4* __restrict__ Pin, const float4* __restrict__ Vin,
+                            const int* __restrict__ key, int4* __restrict__ Pout,
+                            float4* __restrict__ Vout, int* __restrict__ id,
+                            const float* __restrict__ min, float* __restrict__ mout) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Pout[i] = Pin[i];
+  Vout[i] = Vin[i];
+  id[i] = key[i];
+  if (min) mout[i] = min[i];
+}
+
+// ---------------------------------------------------------------- neighbours ---------
+// Visit the 3^D cells around (cx, cy, cz) of one grid; within each (dy, dz) row the
+// cells cx-1..cx+1 are one contiguous slot range unless the x axis wraps.
+template <int D, typename F>
+__device__ __forceinline__ void for_neighbour_cells(const Inst& I, int cx, int cy, int cz,
+                                                    const uint32_t* __restrict__ start, F&& visit) {
+  const int nx = I.ncell[0], ny = I.ncell[1], nz = D == 3 ? I.ncell[2] : 1;
+  const long long base = I.cell_base;
+  for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
+    int z = cz + dz;
+    if (D == 3) {
+      if (I.period[2]) z = (z + nz) % nz;
+      else if (z < 0 || z >= nz) continue;
+    }
+    for (int dy = -1; dy <= 1; ++dy) {
+      int y = cy + dy;
+      if (I.period[1]) y = (y + ny) % ny;
+      else if (y < 0 || y >= ny) continue;
+      long long row = base + ((long long)z * ny + y) * nx;
+      int x0 = cx - 1, x1 = cx + 1;
+      if (I.period[0] && (x0 < 0 || x1 >= nx)) {
+        for (int dx = -1; dx <= 1; ++dx) {
+          int x = (cx + dx + nx) % nx;
+          visit(start[row + x], start[row + x + 1]);
+        }
+      } else {
+        if (x0 < 0) x0 = 0;
+        if (x1 >= nx) x1 = nx - 1;
+        visit(start[row + x0], start[row + x1 + 1]);
+      }
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock)
+k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst_of,
+             const Inst* __restrict__ inst, const uint32_t* __restrict__ fstart,
+             const int4* __restrict__ WP, const uint32_t* __restrict__ wstart, int cap,
+             int* __restrict__ nbr, uint32_t* __restrict__ nbc, Global* g) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Inst& I = inst[inst_of ? inst_of[i] : 0];
+  const int4 pi = P[i];
+  int cx = min(max(pi.x >> I.bits, 0), I.ncell[0] - 1);
+  int cy = min(max(pi.y >> I.bits, 0), I.ncell[1] - 1);
+  int cz = D == 3 ? min(max(pi.z >> I.bits, 0), I.ncell[2] - 1) : 0;
+  int nf = 0, nw = 0;
+  bool overflow = false;
+  for_neighbour_cells<D>(I, cx, cy, cz, fstart, [&](uint32_t b, uint32_t e) {
+    for (uint32_t j = b; j < e; ++j) {
+      if ((int64_t)j == i) continue;
+      if (within<D>(pi, P[j], I)) {
+        if (nf < cap) nbr[(int64_t)nf * n + i] = (int)j;
+        else overflow = true;
+        ++nf;
+      }
+    }
+  });
+  if (nf > cap) nf = cap;
+  if (WP) {
+    for_neighbour_cells<D>(I, cx, cy, cz, wstart, [&](uint32_t b, uint32_t e) {
+      for (uint32_t j = b; j < e; ++j) {
+        if (within<D>(pi, WP[j], I)) {
+          int k = nf + nw;
+          if (k < cap) {
+            nbr[(int64_t)k * n + i] = (int)j;
+            ++nw;
+          } else {
+            overflow = true;
+          }
+        }
+      }
+    });
+  }
+  if (overflow) raise_error(g, ERR_CAPACITY, i);
+  nbc[i] = (uint32_t)nf | ((uint32_t)nw << 16);
+}
+
+// ---------------------------------------------------------------- walls ---------------
+__global__ void k_wall_reorder(int64_t n, const int* __restrict__ src, const int4* __restrict__ Pin,
+                               const float4* __restrict__ Nin, int4* __restrict__ Pout,
+                               float4* __restrict__ Nout) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = src[i];
+  Pout[i] = Pin[s];
+  Nout[i] = Nin[s];
+}
+
+__global__ void k_iota(int64_t n, int* __restrict__ a) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (int)i;
+}
+
+}  // namespace
+
+void launch_hash(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * b.n_cells, s);
+  if (b.n == 0) return;
+  if (b.dim == 2)
+    k_hash<2><<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.cell, b.count, b.rank, b.glob);
+  else
+    k_hash<3><<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.cell, b.count, b.rank, b.glob);
+  ++*launches;
+}
+
+void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  scan_exclusive(b.count, b.fstart, b.n_cells, b.scan_tmp, s, launches);
+  if (b.n == 0) return;
+  k_scatter<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.cell, b.rank, b.fstart, b.id, b.key, b.src);
+  k_cell_sort<<<grid_for(b.n_cells), kBlock, 0, s>>>(b.n_cells, b.fstart, b.key, b.src);
+  k_reorder<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.src, b.PS, b.VS, b.PH, b.VH, b.mass, b.mass_tmp);
+  k_copy_back<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PH, b.VH, b.key, b.PS, b.VS, b.id, b.mass_tmp,
+                                               b.mass);
+  *launches += 4;
+}
+
+void launch_neighbours(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  if (b.n == 0) return;
+  const int4* wp = b.nw ? b.WP : nullptr;
+  if (b.dim == 2)
+    k_neighbours<2><<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.fstart, wp,
+                                                     b.wstart, b.cap, b.nbr, b.nbc, b.glob);
+  else
+    k_neighbours<3><<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.fstart, wp,
+                                                     b.wstart, b.cap, b.nbr, b.nbc, b.glob);
+  ++*launches;
+}
+
+// Walls are static: sort them into cells once. Uses the fluid build scratch
+// (cell/rank/count/key/src sized for max(n, nw)); wid_tmp may be b.wid.
+void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStream_t s) {
+  int64_t dummy = 0;
+  cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * b.n_cells, s);
+  if (b.nw > 0) {
+    if (b.dim == 2)
+      k_hash<2><<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, b.WP, b.winst_of, b.inst, b.cell, b.count,
+                                                  b.rank, b.glob);
+    else
+      k_hash<3><<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, b.WP, b.winst_of, b.inst, b.cell, b.count,
+                                                  b.rank, b.glob);
+  }
+  scan_exclusive(b.count, b.wstart, b.n_cells, b.scan_tmp, s, &dummy);
+  if (b.nw == 0) return;
+  k_iota<<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, wid_tmp);
+  k_scatter<<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, b.cell, b.rank, b.wstart, wid_tmp, b.key, b.src);
+  k_cell_sort<<<grid_for(b.n_cells), kBlock, 0, s>>>(b.n_cells, b.wstart, b.key, b.src);
+  k_wall_reorder<<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, b.src, b.WP, b.WN, WP_tmp, WN_tmp);
+  cudaMemcpyAsync(b.WP, WP_tmp, sizeof(int4) * b.nw, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(b.WN, WN_tmp, sizeof(float4) * b.nw, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(b.wid, b.key, sizeof(int) * b.nw, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace sph

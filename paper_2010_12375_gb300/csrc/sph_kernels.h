@@ -1,0 +1,81 @@
+// Host-side launch interface of the WCSPH kernels (internal to libsph.so).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph_common.cuh"
+
+namespace sph {
+
+// Device buffers of one handle. Fluid arrays are indexed in cell-sorted order.
+struct Buffers {
+  int64_t n = 0, nw = 0, n_cells = 0;
+  int n_inst = 1, dim = 2, cap = 0;
+  Inst* inst = nullptr;           // [n_inst]
+  Ctrl* ctrl = nullptr;           // [n_inst]
+  Global* glob = nullptr;         // [1]
+  const int* inst_of = nullptr;   // [n] instance of each fluid slot (NULL when n_inst == 1)
+  const int* winst_of = nullptr;  // [nw]
+  int4* PS = nullptr;  float4* VS = nullptr;   // state between substeps
+  int4* PH = nullptr;  float4* VH = nullptr;   // half step / reorder scratch
+  float* mass = nullptr;          // [n] non-uniform masses, NULL when uniform per instance
+  float* mass_tmp = nullptr;
+  int* id = nullptr;              // [n] caller id of each sorted slot
+  float4* acc_prior = nullptr;    // [n] viscous acceleration (NULL when inviscid)
+  float4* acc_keep = nullptr;     // [n] last dv/dt (NULL unless kept)
+  // cell build
+  uint32_t* cell = nullptr;       // [n]
+  uint32_t* rank = nullptr;       // [n]
+  uint32_t* count = nullptr;      // [n_cells]
+  uint32_t* fstart = nullptr;     // [n_cells + 1]
+  int* key = nullptr;             // [n]
+  int* src = nullptr;             // [n]
+  uint32_t* scan_tmp = nullptr;   // scan block sums
+  // walls
+  int4* WP = nullptr;  float4* WN = nullptr;
+  int* wid = nullptr;             // [nw] caller row of each sorted wall slot
+  uint32_t* wstart = nullptr;     // [n_cells + 1]
+  // neighbours (column-major ELL: nbr[k * n + i])
+  int* nbr = nullptr;
+  uint32_t* nbc = nullptr;        // [n] fluid count | wall count << 16
+};
+
+size_t scan_tmp_elems(int64_t n);
+void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s,
+                    int64_t* launches);
+
+// cell build
+void launch_hash(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_neighbours(const Buffers& b, cudaStream_t s, int64_t* launches);
+void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStream_t s);
+
+// import / export
+void launch_import(const Buffers& b, const double* pos, const double* vel, const double* rho,
+                   const double* drho, cudaStream_t s);
+void launch_import_walls(const Buffers& b, const double* pos, const double* nrm, const double* vol,
+                         cudaStream_t s);
+void launch_export(const Buffers& b, double* pos, double* vel, double* rho, double* drho,
+                   cudaStream_t s);
+void launch_export_acc(const Buffers& b, double* acc, cudaStream_t s);
+void launch_export_neighbours(const Buffers& b, int32_t* fc, int32_t* wc, int32_t* fids,
+                              int32_t* wids, int32_t stride, cudaStream_t s);
+
+// physics
+void launch_pair_count(const Buffers& b, unsigned long long* out2, cudaStream_t s);
+void launch_vmax(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_dt_advection(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_density(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_viscous(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_dt_acoustic(const Buffers& b, cudaStream_t s, cudaGraphConditionalHandle cond,
+                        bool use_cond, int64_t* launches);
+void launch_pressure_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_density_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches);
+
+// diagnostics: out[n_inst * kDiagFields] doubles on the device
+constexpr int kDiagFields = 16;
+size_t diag_scratch_elems(const Buffers& b);
+void launch_diagnostics(const Buffers& b, double* scratch, double* out, cudaStream_t s,
+                        int64_t* launches);
+
+}  // namespace sph

@@ -1,0 +1,644 @@
+// Pair-interaction kernels and time-step control of the WCSPH hot path.
+//
+//   k_density              Eq. eqrhosum / Eq. eqrhosumnosurface (once per advection step)
+//   k_viscous              Eq. eqviscous (once per advection step, fluid pairs)
+//   k_dt_advection         Eq. dt-advection (one thread per instance, FP64)
+//   k_dt_acoustic          Eq. dt-relax clamped to the advection step (one thread per instance)
+//   k_pressure_relaxation  Eq. verlet-first-half, Eq. eqeos, Eq. riemannsph (momentum),
+//                          wall problem Eqs. eqriepartial/eqrienoslip/eqriepright,
+//                          Eq. verlet-first-mediate
+//   k_density_relaxation   Eq. verlet-first-final with Eq. riemannsph (continuity)
+//
+// Conventions: r_ij = r_i - r_j, e_ij = -r_ij/|r_ij| points from i to j, and
+// grad_i W_ij = (dW/dr) r_ij/|r_ij|. Interface states of the low-dissipation
+// solver: U* = (U_L+U_R)/2 + (P_L-P_R)/(2 rho_bar c0),
+// P* = (P_L+P_R)/2 + rho_bar c0 beta (U_L-U_R)/2, beta = min(3 max(U_L-U_R,0)/c0, 1).
+// One thread per fluid particle walks its frozen neighbour row (column-major
+// ELL, so a warp's 32 index loads per row position are one 128-byte line) and
+// recomputes the pair geometry from the current positions; pairs at or beyond
+// 2h, or at zero distance, contribute nothing.
+#include <cmath>
+
+#include "sph_kernels.h"
+
+namespace sph {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+inline unsigned grid_for(int64_t n, int block = kBlock) {
+  return (unsigned)((n + block - 1) / block);
+}
+
+__device__ __forceinline__ void raise_error(Global* g, int bit, long long idx) {
+  int old = atomicOr(&g->err, bit);
+  if (old == 0) g->bad_index = idx;
+}
+
+__device__ __forceinline__ int inst_index(const int* inst_of, int64_t i) {
+  return inst_of ? inst_of[i] : 0;
+}
+
+// Block-wide max of |v|^2 into the instance's slot: one atomic per block when the
+// whole block belongs to one instance, else one per lane.
+__device__ __forceinline__ void reduce_vmax(float v2, bool valid, int k, bool uniform_block,
+                                            Ctrl* ctrl) {
+  __shared__ float red[kBlock / 32];
+  if (!uniform_block) {
+    if (valid) atomicMax(&ctrl[k].vmax2, __float_as_uint(v2));
+    return;
+  }
+  float m = valid ? v2 : 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(&ctrl[k].vmax2, __float_as_uint(m));
+  }
+}
+
+__device__ __forceinline__ bool block_one_instance(const int* inst_of, int64_t n, int* k_out) {
+  int64_t first = (int64_t)blockIdx.x * blockDim.x;
+  int64_t last = min(first + (int64_t)blockDim.x, n) - 1;
+  int a = inst_index(inst_of, first), b = inst_index(inst_of, last);
+  *k_out = a;
+  return a == b;
+}
+
+// ---------------------------------------------------------------- import / export ----
+template <int D>
+__global__ void k_import(int64_t n, const double* __restrict__ pos, const double* __restrict__ vel,
+                         const double* __restrict__ rho, const double* __restrict__ drho,
+                         const int* __restrict__ inst_of, const Inst* __restrict__ inst,
+                         int4* __restrict__ P, float4* __restrict__ V, Global* g) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Inst& I = inst[inst_index(inst_of, i)];
+  int q[3] = {0, 0, 0};
+  float v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    double s = (pos[i * D + a] - I.lo[a]) / I.dq_d;
+    double lim = 2147483000.0;
+    if (!(s > -lim && s < lim)) {          // also catches NaN
+      raise_error(g, ERR_DOMAIN, i);
+      s = 0.0;
+    }
+    int qa = __double2int_rn(s);
+    if (I.period[a]) {
+      qa %= I.period[a];
+      if (qa < 0) qa += I.period[a];
+    }
+    q[a] = qa;
+    v[a] = (float)vel[i * D + a];
+  }
+  float dev = (float)(rho[i] - I.rho0_d);
+  float dr = drho ? (float)drho[i] : 0.0f;
+  P[i] = make_int4(q[0], q[1], q[2], f2i(dev));
+  V[i] = make_float4(v[0], v[1], v[2], dr);
+}
+
+template <int D>
+__global__ void k_import_walls(int64_t n, const double* __restrict__ pos, const double* __restrict__ nrm,
+                               const double* __restrict__ vol, const int* __restrict__ inst_of,
+                               const Inst* __restrict__ inst, int4* __restrict__ P,
+                               float4* __restrict__ N, Global* g) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Inst& I = inst[inst_index(inst_of, i)];
+  int q[3] = {0, 0, 0};
+  float nv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    double s = (pos[i * D + a] - I.lo[a]) / I.dq_d;
+    if (!(s > -2147483000.0 && s < 2147483000.0)) {
+      raise_error(g, ERR_DOMAIN, i);
+      s = 0.0;
+    }
+    int qa = __double2int_rn(s);
+    if (I.period[a]) {
+      qa %= I.period[a];
+      if (qa < 0) qa += I.period[a];
+    }
+    q[a] = qa;
+    nv[a] = (float)nrm[i * D + a];
+  }
+  P[i] = make_int4(q[0], q[1], q[2], f2i((float)vol[i]));
+  N[i] = make_float4(nv[0], nv[1], nv[2], 0.0f);
+}
+
+template <int D>
+__global__ void k_export(int64_t n, const int4* __restrict__ P, const float4* __restrict__ V,
+                         const int* __restrict__ id, const int* __restrict__ inst_of,
+                         const Inst* __restrict__ inst, double* __restrict__ pos,
+                         double* __restrict__ vel, double* __restrict__ rho,
+                         double* __restrict__ drho) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Inst& I = inst[inst_index(inst_of, i)];
+  int4 p = P[i];
+  float4 v = V[i];
+  int64_t row = id[i];
+  int q[3] = {p.x, p.y, p.z};
+  float vv[3] = {v.x, v.y, v.z};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (pos) pos[row * D + a] = I.lo[a] + (double)q[a] * I.dq_d;
+    if (vel) vel[row * D + a] = (double)vv[a];
+  }
+  if (rho) rho[row] = I.rho0_d + (double)i2f(p.w);
+  if (drho) drho[row] = (double)v.w;
+}
+
+template <int D>
+__global__ void k_export_acc(int64_t n, const float4* __restrict__ A, const int* __restrict__ id,
+                             double* __restrict__ acc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 a = A[i];
+  int64_t row = id[i];
+  acc[row * D + 0] = a.x;
+  acc[row * D + 1] = a.y;
+  if (D == 3) acc[row * D + 2] = a.z;
+}
+
+__global__ void k_export_neighbours(int64_t n, int cap, const int* __restrict__ nbr,
+                                    const uint32_t* __restrict__ nbc, const int* __restrict__ id,
+                                    const int* __restrict__ wid, int stride, int32_t* __restrict__ fc,
+                                    int32_t* __restrict__ wc, int32_t* __restrict__ fids,
+                                    int32_t* __restrict__ wids) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t c = nbc[i];
+  int nf = (int)(c & 0xffffu), nw = (int)(c >> 16);
+  int64_t row = id[i];
+  fc[row] = nf;
+  wc[row] = nw;
+  for (int k = 0; k < nf; ++k) fids[row * stride + k] = id[nbr[(int64_t)k * n + i]];
+  for (int k = 0; k < nw; ++k) wids[row * stride + k] = wid[nbr[(int64_t)(nf + k) * n + i]];
+}
+
+__global__ void k_pair_count(int64_t n, const uint32_t* __restrict__ nbc, unsigned long long* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long f = 0, w = 0;
+  if (i < n) {
+    f = nbc[i] & 0xffffu;
+    w = nbc[i] >> 16;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    f += __shfl_xor_sync(0xffffffffu, f, o);
+    w += __shfl_xor_sync(0xffffffffu, w, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], f);
+    atomicAdd(&out[1], w);
+  }
+}
+
+// ---------------------------------------------------------------- reductions / steps -
+template <int D>
+__global__ void k_vmax(int64_t n, const float4* __restrict__ V, const int* __restrict__ inst_of,
+                       Ctrl* ctrl) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int k;
+  bool uni = block_one_instance(inst_of, n, &k);
+  float v2 = 0.f;
+  bool valid = i < n;
+  if (valid) {
+    float4 v = V[i];
+    v2 = v.x * v.x + v.y * v.y + (D == 3 ? v.z * v.z : 0.f);
+    if (!uni) k = inst_index(inst_of, i);
+  }
+  reduce_vmax(v2, valid, k, uni, ctrl);
+}
+
+__global__ void k_reset_vmax(int n_inst, Ctrl* ctrl) {
+  for (int k = threadIdx.x; k < n_inst; k += blockDim.x) ctrl[k].vmax2 = 0u;
+}
+
+// Eq. dt-advection: Dt_ad = CFL_ad min(h / max(|v|max, U_ref), h^2 / nu).
+__global__ void k_dt_advection(int n_inst, const Inst* __restrict__ inst, Ctrl* ctrl, Global* g) {
+  for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
+    const Inst& I = inst[k];
+    Ctrl& C = ctrl[k];
+    double vmax = sqrt((double)__uint_as_float(C.vmax2));
+    double dt = I.h_d / fmax(vmax, I.u_ref);
+    if (I.nu > 0.0) dt = fmin(dt, I.h_d * I.h_d / I.nu);
+    C.dt_ad = I.cfl_ad * dt;
+    C.tau = 0.0;
+    C.done = 0;
+    C.dt = 0.0;
+    C.sub_in_step = 0;
+    C.adv_steps += 1;
+  }
+  if (threadIdx.x == 0) g->active = 1;
+}
+
+// Eq. dt-relax, clamped to the remainder of the advection step. Sets the
+// condition of the device-side substep loop when launched inside a graph.
+__global__ void k_dt_acoustic(int n_inst, const Inst* __restrict__ inst, Ctrl* ctrl, Global* g,
+                              cudaGraphConditionalHandle cond, int use_cond) {
+  int any = 0;
+  for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
+    const Inst& I = inst[k];
+    Ctrl& C = ctrl[k];
+    if (C.done) {
+      C.dt = 0.0;
+      continue;
+    }
+    double vmax = sqrt((double)__uint_as_float(C.vmax2));
+    C.vmax2 = 0u;                                   // refilled by the pressure relaxation
+    double dt_ac = I.cfl_ac * I.h_d / (I.c0_d + vmax);
+    double rem = C.dt_ad - C.tau;
+    double dt = fmin(dt_ac, rem);
+    // a non-finite or vanishing step, or a runaway substep count, ends the loop with an
+    // error instead of letting the device-side loop spin
+    if (!(dt_ac > 1e-12 * I.h_d / I.c0_d) || !(rem > 0.0) || !(dt > 0.0) ||
+        C.sub_in_step >= kMaxSubstepsPerStep) {
+      atomicOr(&g->err, ERR_DT);
+      C.dt = 0.0;
+      C.done = 1;
+      continue;
+    }
+    C.dt = dt;
+    C.tau += dt;
+    C.t += dt;
+    C.substeps += 1;
+    C.sub_in_step += 1;
+    if (C.tau >= C.dt_ad * (1.0 - kLoopSlack)) C.done = 1;
+    else any = 1;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    g->active = any;
+    g->substeps += 1;
+    if (use_cond) cudaGraphSetConditional(cond, any ? 1u : 0u);
+  }
+}
+
+// ---------------------------------------------------------------- density -------------
+template <int D>
+__global__ void __launch_bounds__(kBlock)
+k_density(int64_t n, int4* P, const int* __restrict__ inst_of, const Inst* __restrict__ inst,
+          const int* __restrict__ nbr, const uint32_t* __restrict__ nbc, const int4* __restrict__ WP) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Inst& I = inst[inst_index(inst_of, i)];
+  const int4 pi = P[i];
+  uint32_t c = nbc[i];
+  int nf = (int)(c & 0xffffu), nw = (int)(c >> 16);
+  // sum W - sumW0, started from W(0) - sumW0 so the deviation keeps its precision
+  float s = I.sig_hi, comp = 0.0f;
+  kahan_add(s, comp, I.sig_lo);
+  for (int k = 0; k < nf; ++k) {
+    const int4 pj = P[nbr[(int64_t)k * n + i]];
+    float dx = (float)wrap_diff(pi.x - pj.x, I.period[0]) * I.dq;
+    float dy = (float)wrap_diff(pi.y - pj.y, I.period[1]) * I.dq;
+    float r2 = dx * dx + dy * dy;
+    if (D == 3) {
+      float dz = (float)wrap_diff(pi.z - pj.z, I.period[2]) * I.dq;
+      r2 += dz * dz;
+    }
+    if (r2 < I.four_h2) kahan_add(s, comp, kernel_W(sqrtf(r2), I));
+  }
+  for (int k = 0; k < nw; ++k) {
+    const int4 pw = WP[nbr[(int64_t)(nf + k) * n + i]];
+    float dx = (float)wrap_diff(pi.x - pw.x, I.period[0]) * I.dq;
+    float dy = (float)wrap_diff(pi.y - pw.y, I.period[1]) * I.dq;
+    float r2 = dx * dx + dy * dy;
+    if (D == 3) {
+      float dz = (float)wrap_diff(pi.z - pw.z, I.period[2]) * I.dq;
+      r2 += dz * dz;
+    }
+    if (r2 < I.four_h2) kahan_add(s, comp, kernel_W(sqrtf(r2), I));
+  }
+  float dev = I.rho0_over_sigma0 * (s - comp);       // rho0 sumW/sumW0 - rho0
+  if (I.free_surface) dev = fmaxf(i2f(pi.w), dev);
+  reinterpret_cast<int*>(P + i)[3] = f2i(dev);        // only .w changes; others read .xyz
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock)
+k_viscous(int64_t n, const int4* __restrict__ P, const float4* __restrict__ V,
+          const float* __restrict__ mass, const int* __restrict__ inst_of,
+          const Inst* __restrict__ inst, const int* __restrict__ nbr,
+          const uint32_t* __restrict__ nbc, float4* __restrict__ acc_prior) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Inst& I = inst[inst_index(inst_of, i)];
+  const int4 pi = P[i];
+  const float4 vi = V[i];
+  float rho_i = I.rho0 + i2f(pi.w);
+  int nf = (int)(nbc[i] & 0xffffu);
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  if (I.eta > 0.0f) {
+    for (int k = 0; k < nf; ++k) {
+      int j = nbr[(int64_t)k * n + i];
+      const int4 pj = P[j];
+      const float4 vj = V[j];
+      float dx = (float)wrap_diff(pi.x - pj.x, I.period[0]) * I.dq;
+      float dy = (float)wrap_diff(pi.y - pj.y, I.period[1]) * I.dq;
+      float r2 = dx * dx + dy * dy;
+      if (D == 3) {
+        float dz = (float)wrap_diff(pi.z - pj.z, I.period[2]) * I.dq;
+        r2 += dz * dz;
+      }
+      if (!(r2 < I.four_h2) || r2 == 0.0f) continue;
+      float fw = kernel_dW_over_r(sqrtf(r2), I);            // (dW/dr)/r
+      float mj = mass ? mass[j] : I.mass;
+      float f = mj / (I.rho0 + i2f(pj.w)) * fw;
+      ax += f * (vi.x - vj.x);
+      ay += f * (vi.y - vj.y);
+      if (D == 3) az += f * (vi.z - vj.z);
+    }
+  }
+  float s = 2.0f * I.eta / rho_i;
+  acc_prior[i] = make_float4(s * ax, s * ay, s * az, 0.0f);
+}
+
+// ---------------------------------------------------------------- relaxations ---------
+template <int D>
+__global__ void __launch_bounds__(kBlock)
+k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __restrict__ VS,
+                      int4* __restrict__ PH, float4* __restrict__ VH,
+                      const float* __restrict__ mass, const int* __restrict__ inst_of,
+                      const Inst* __restrict__ inst, Ctrl* ctrl, const int* __restrict__ nbr,
+                      const uint32_t* __restrict__ nbc, const int4* __restrict__ WP,
+                      const float4* __restrict__ WN, const float4* __restrict__ acc_prior,
+                      float4* __restrict__ acc_keep, Global* g) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int kb;
+  const bool uni = block_one_instance(inst_of, n, &kb);
+  bool valid = i < n;
+  int k = valid ? inst_index(inst_of, i) : kb;
+  const double dtd = ctrl[k].dt;
+  if (dtd == 0.0) valid = false;                 // instance idle for this substep
+  float v2 = 0.0f;
+  if (valid) {
+    const Inst& I = inst[k];
+    const float dt = (float)dtd, hdt = 0.5f * dt;
+    const int4 pi = PS[i];
+    const float4 vi = VS[i];
+    const float dev_i = i2f(pi.w) + hdt * vi.w;       // Eq. verlet-first-half (density)
+    const float rho_i = I.rho0 + dev_i;
+    const float pr_i = I.c0sq * dev_i;                // Eq. eqeos
+    float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    const uint32_t cnt = nbc[i];
+    const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
+    for (int kk = 0; kk < nf; ++kk) {
+      const int j = nbr[(int64_t)kk * n + i];
+      const int4 pj = PS[j];
+      const float4 vj = VS[j];
+      // half-step pair vector r_ij^{n+1/2} = r_ij^n + dt/2 (v_i - v_j)
+      float rx = fmaf(hdt, vi.x - vj.x, (float)wrap_diff(pi.x - pj.x, I.period[0]) * I.dq);
+      float ry = fmaf(hdt, vi.y - vj.y, (float)wrap_diff(pi.y - pj.y, I.period[1]) * I.dq);
+      float rz = D == 3 ? fmaf(hdt, vi.z - vj.z, (float)wrap_diff(pi.z - pj.z, I.period[2]) * I.dq) : 0.f;
+      float r2 = rx * rx + ry * ry + rz * rz;
+      if (!(r2 < I.four_h2) || r2 == 0.0f) continue;
+      const float inv_r = rsqrtf(r2);
+      const float r = r2 * inv_r;
+      const float fw = kernel_dW_over_r(r, I);        // (dW/dr)/r
+      const float dev_j = i2f(pj.w) + hdt * vj.w;
+      const float rho_j = I.rho0 + dev_j;
+      const float pr_j = I.c0sq * dev_j;
+      // U_L = v_i.e_ij, U_R = v_j.e_ij with e_ij = -r_ij/r
+      const float UL = -(vi.x * rx + vi.y * ry + vi.z * rz) * inv_r;
+      const float UR = -(vj.x * rx + vj.y * ry + vj.z * rz) * inv_r;
+      const float dU = UL - UR;
+      const float rho_bar = 0.5f * (rho_i + rho_j);
+      const float beta = fminf(kLimiter * fmaxf(dU, 0.0f) / I.c0, 1.0f);
+      const float Pstar = 0.5f * (pr_i + pr_j) + 0.5f * rho_bar * I.c0 * beta * dU;
+      const float mj = mass ? mass[j] : I.mass;
+      const float f = mj / rho_j * Pstar * fw;        // V_j P* (dW/dr)/r
+      kahan_add(ax, cx, f * rx);
+      kahan_add(ay, cy, f * ry);
+      if (D == 3) kahan_add(az, cz, f * rz);
+    }
+    for (int kk = 0; kk < nw; ++kk) {
+      const int w = nbr[(int64_t)(nf + kk) * n + i];
+      const int4 pw = WP[w];
+      const float4 nwv = WN[w];
+      float rx = fmaf(hdt, vi.x, (float)wrap_diff(pi.x - pw.x, I.period[0]) * I.dq);
+      float ry = fmaf(hdt, vi.y, (float)wrap_diff(pi.y - pw.y, I.period[1]) * I.dq);
+      float rz = D == 3 ? fmaf(hdt, vi.z, (float)wrap_diff(pi.z - pw.z, I.period[2]) * I.dq) : 0.f;
+      float r2 = rx * rx + ry * ry + rz * rz;
+      if (!(r2 < I.four_h2) || r2 == 0.0f) continue;
+      const float inv_r = rsqrtf(r2);
+      const float fw = kernel_dW_over_r(r2 * inv_r, I);
+      // one-sided problem along the wall normal: U_L = -n.v_i, U_R = -U_L,
+      // P_R = P_L + rho_i g.(r_w - r_i), rho_R from the EoS
+      const float UL = -(nwv.x * vi.x + nwv.y * vi.y + nwv.z * vi.z);
+      const float PR = pr_i - rho_i * (I.g[0] * rx + I.g[1] * ry + I.g[2] * rz);
+      const float rho_bar = 0.5f * (rho_i + I.rho0 + PR / I.c0sq);
+      const float dU = 2.0f * UL;
+      const float beta = fminf(kLimiter * fmaxf(dU, 0.0f) / I.c0, 1.0f);
+      const float Pstar = 0.5f * (pr_i + PR) + 0.5f * rho_bar * I.c0 * beta * dU;
+      const float f = i2f(pw.w) * Pstar * fw;         // V_w P* (dW/dr)/r
+      kahan_add(ax, cx, f * rx);
+      kahan_add(ay, cy, f * ry);
+      if (D == 3) kahan_add(az, cz, f * rz);
+    }
+    // dv/dt = acc_prior + g - 2/rho_i sum V_j P* grad_i W_ij
+    const float s = -2.0f / rho_i;
+    float4 ap = acc_prior ? acc_prior[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float a0 = ap.x + I.g[0] + s * (ax - cx);
+    float a1 = ap.y + I.g[1] + s * (ay - cy);
+    float a2 = D == 3 ? ap.z + I.g[2] + s * (az - cz) : 0.f;
+    float4 vn = make_float4(vi.x + dt * a0, vi.y + dt * a1, vi.z + dt * a2, vi.w);  // verlet-first-mediate
+    // Eq. verlet-first-half (position), fixed point
+    int qx = pi.x + __float2int_rn(hdt * vi.x * I.inv_dq);
+    int qy = pi.y + __float2int_rn(hdt * vi.y * I.inv_dq);
+    int qz = D == 3 ? pi.z + __float2int_rn(hdt * vi.z * I.inv_dq) : 0;
+    qx = wrap_coord(qx, I.period[0]);
+    qy = wrap_coord(qy, I.period[1]);
+    if (D == 3) qz = wrap_coord(qz, I.period[2]);
+    PH[i] = make_int4(qx, qy, qz, f2i(dev_i));
+    VH[i] = vn;
+    if (acc_keep) acc_keep[i] = make_float4(a0, a1, a2, 0.f);
+    v2 = vn.x * vn.x + vn.y * vn.y + vn.z * vn.z;
+    if (!isfinite(v2)) raise_error(g, ERR_NAN, i);
+  }
+  reduce_vmax(v2, valid, k, uni, ctrl);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock)
+k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __restrict__ VH,
+                     int4* __restrict__ PS, float4* __restrict__ VS,
+                     const float* __restrict__ mass, const int* __restrict__ inst_of,
+                     const Inst* __restrict__ inst, const Ctrl* __restrict__ ctrl,
+                     const int* __restrict__ nbr, const uint32_t* __restrict__ nbc,
+                     const int4* __restrict__ WP, const float4* __restrict__ WN, Global* g) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = inst_index(inst_of, i);
+  const double dtd = ctrl[k].dt;
+  if (dtd == 0.0) return;
+  const Inst& I = inst[k];
+  const float hdt = 0.5f * (float)dtd;
+  const int4 pi = PH[i];
+  const float4 vi = VH[i];                            // v^{n+1}
+  const float dev_i = i2f(pi.w);
+  const float rho_i = I.rho0 + dev_i;
+  float s = 0.f, comp = 0.f;
+  const uint32_t cnt = nbc[i];
+  const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
+  for (int kk = 0; kk < nf; ++kk) {
+    const int j = nbr[(int64_t)kk * n + i];
+    const int4 pj = PH[j];
+    const float4 vj = VH[j];
+    // r_ij^{n+1} = r_ij^{n+1/2} + dt/2 (v_i - v_j)^{n+1}
+    float rx = fmaf(hdt, vi.x - vj.x, (float)wrap_diff(pi.x - pj.x, I.period[0]) * I.dq);
+    float ry = fmaf(hdt, vi.y - vj.y, (float)wrap_diff(pi.y - pj.y, I.period[1]) * I.dq);
+    float rz = D == 3 ? fmaf(hdt, vi.z - vj.z, (float)wrap_diff(pi.z - pj.z, I.period[2]) * I.dq) : 0.f;
+    float r2 = rx * rx + ry * ry + rz * rz;
+    if (!(r2 < I.four_h2) || r2 == 0.0f) continue;
+    const float inv_r = rsqrtf(r2);
+    const float r = r2 * inv_r;
+    const float dW = kernel_dW_over_r(r, I) * r;
+    const float dev_j = i2f(pj.w);
+    const float rho_j = I.rho0 + dev_j;
+    const float UL = -(vi.x * rx + vi.y * ry + vi.z * rz) * inv_r;
+    const float UR = -(vj.x * rx + vj.y * ry + vj.z * rz) * inv_r;
+    const float rho_bar = 0.5f * (rho_i + rho_j);
+    // U* - U_L = (U_R - U_L)/2 + (P_L - P_R)/(2 rho_bar c0), P_L - P_R = c0^2 (dev_i - dev_j)
+    const float dUs = 0.5f * (UR - UL) + I.c0 * (dev_i - dev_j) / (2.0f * rho_bar);
+    const float mj = mass ? mass[j] : I.mass;
+    kahan_add(s, comp, mj / rho_j * dUs * dW);
+  }
+  for (int kk = 0; kk < nw; ++kk) {
+    const int w = nbr[(int64_t)(nf + kk) * n + i];
+    const int4 pw = WP[w];
+    const float4 nwv = WN[w];
+    float rx = fmaf(hdt, vi.x, (float)wrap_diff(pi.x - pw.x, I.period[0]) * I.dq);
+    float ry = fmaf(hdt, vi.y, (float)wrap_diff(pi.y - pw.y, I.period[1]) * I.dq);
+    float rz = D == 3 ? fmaf(hdt, vi.z, (float)wrap_diff(pi.z - pw.z, I.period[2]) * I.dq) : 0.f;
+    float r2 = rx * rx + ry * ry + rz * rz;
+    if (!(r2 < I.four_h2) || r2 == 0.0f) continue;
+    const float inv_r = rsqrtf(r2);
+    const float r = r2 * inv_r;
+    const float dW = kernel_dW_over_r(r, I) * r;
+    const float UL = -(nwv.x * vi.x + nwv.y * vi.y + nwv.z * vi.z);
+    const float gr = I.g[0] * rx + I.g[1] * ry + I.g[2] * rz;
+    const float PR = I.c0sq * dev_i - rho_i * gr;
+    const float rho_bar = 0.5f * (rho_i + I.rho0 + PR / I.c0sq);
+    // U_R = -U_L so the mean is 0; P_L - P_R = rho_i g.r_iw
+    const float Us = rho_i * gr / (2.0f * rho_bar * I.c0);
+    kahan_add(s, comp, i2f(pw.w) * (Us - UL) * dW);
+  }
+  const float drho = 2.0f * rho_i * (s - comp);
+  const float dev_n = dev_i + hdt * drho;             // Eq. verlet-first-final (density)
+  int qx = pi.x + __float2int_rn(hdt * vi.x * I.inv_dq);
+  int qy = pi.y + __float2int_rn(hdt * vi.y * I.inv_dq);
+  int qz = D == 3 ? pi.z + __float2int_rn(hdt * vi.z * I.inv_dq) : 0;
+  qx = wrap_coord(qx, I.period[0]);
+  qy = wrap_coord(qy, I.period[1]);
+  if (D == 3) qz = wrap_coord(qz, I.period[2]);
+  if (!isfinite(dev_n)) raise_error(g, ERR_NAN, i);
+  PS[i] = make_int4(qx, qy, qz, f2i(dev_n));
+  VS[i] = make_float4(vi.x, vi.y, vi.z, drho);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers -----------
+#define SPH_DIM_LAUNCH(b, kern, grid, block, stream, ...)                          \
+  do {                                                                             \
+    if ((b).dim == 2) kern<2><<<grid, block, 0, stream>>>(__VA_ARGS__);            \
+    else kern<3><<<grid, block, 0, stream>>>(__VA_ARGS__);                         \
+  } while (0)
+
+void launch_import(const Buffers& b, const double* pos, const double* vel, const double* rho,
+                   const double* drho, cudaStream_t s) {
+  if (b.n == 0) return;
+  SPH_DIM_LAUNCH(b, k_import, grid_for(b.n), kBlock, s, b.n, pos, vel, rho, drho, b.inst_of, b.inst,
+                 b.PS, b.VS, b.glob);
+}
+
+void launch_import_walls(const Buffers& b, const double* pos, const double* nrm, const double* vol,
+                         cudaStream_t s) {
+  if (b.nw == 0) return;
+  SPH_DIM_LAUNCH(b, k_import_walls, grid_for(b.nw), kBlock, s, b.nw, pos, nrm, vol, b.winst_of, b.inst,
+                 b.WP, b.WN, b.glob);
+}
+
+void launch_export(const Buffers& b, double* pos, double* vel, double* rho, double* drho,
+                   cudaStream_t s) {
+  if (b.n == 0) return;
+  SPH_DIM_LAUNCH(b, k_export, grid_for(b.n), kBlock, s, b.n, b.PS, b.VS, b.id, b.inst_of, b.inst, pos,
+                 vel, rho, drho);
+}
+
+void launch_export_acc(const Buffers& b, double* acc, cudaStream_t s) {
+  if (b.n == 0 || !b.acc_keep) return;
+  SPH_DIM_LAUNCH(b, k_export_acc, grid_for(b.n), kBlock, s, b.n, b.acc_keep, b.id, acc);
+}
+
+void launch_export_neighbours(const Buffers& b, int32_t* fc, int32_t* wc, int32_t* fids,
+                              int32_t* wids, int32_t stride, cudaStream_t s) {
+  if (b.n == 0) return;
+  k_export_neighbours<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.cap, b.nbr, b.nbc, b.id, b.wid, stride,
+                                                        fc, wc, fids, wids);
+}
+
+void launch_pair_count(const Buffers& b, unsigned long long* out2, cudaStream_t s) {
+  cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), s);
+  if (b.n == 0) return;
+  k_pair_count<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.nbc, out2);
+}
+
+void launch_vmax(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  k_reset_vmax<<<1, 256, 0, s>>>(b.n_inst, b.ctrl);
+  ++*launches;
+  if (b.n == 0) return;
+  SPH_DIM_LAUNCH(b, k_vmax, grid_for(b.n), kBlock, s, b.n, b.VS, b.inst_of, b.ctrl);
+  ++*launches;
+}
+
+void launch_dt_advection(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  k_dt_advection<<<1, 256, 0, s>>>(b.n_inst, b.inst, b.ctrl, b.glob);
+  ++*launches;
+}
+
+void launch_density(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  if (b.n == 0) return;
+  SPH_DIM_LAUNCH(b, k_density, grid_for(b.n), kBlock, s, b.n, b.PS, b.inst_of, b.inst, b.nbr, b.nbc,
+                 b.WP);
+  ++*launches;
+}
+
+void launch_viscous(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  if (b.n == 0 || !b.acc_prior) return;
+  SPH_DIM_LAUNCH(b, k_viscous, grid_for(b.n), kBlock, s, b.n, b.PS, b.VS, b.mass, b.inst_of, b.inst,
+                 b.nbr, b.nbc, b.acc_prior);
+  ++*launches;
+}
+
+void launch_dt_acoustic(const Buffers& b, cudaStream_t s, cudaGraphConditionalHandle cond,
+                        bool use_cond, int64_t* launches) {
+  k_dt_acoustic<<<1, 256, 0, s>>>(b.n_inst, b.inst, b.ctrl, b.glob, cond, use_cond ? 1 : 0);
+  ++*launches;
+}
+
+void launch_pressure_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  if (b.n == 0) return;
+  SPH_DIM_LAUNCH(b, k_pressure_relaxation, grid_for(b.n), kBlock, s, b.n, b.PS, b.VS, b.PH, b.VH,
+                 b.mass, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, b.WP, b.WN, b.acc_prior,
+                 b.acc_keep, b.glob);
+  ++*launches;
+}
+
+void launch_density_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  if (b.n == 0) return;
+  SPH_DIM_LAUNCH(b, k_density_relaxation, grid_for(b.n), kBlock, s, b.n, b.PH, b.VH, b.PS, b.VS,
+                 b.mass, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, b.WP, b.WN, b.glob);
+  ++*launches;
+}
+
+}  // namespace sph

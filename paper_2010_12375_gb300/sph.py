@@ -1,0 +1,404 @@
+"""Thin ctypes binding of libsph.so (include/sph.h). Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels. Functions
+keep the C names; arrays may be numpy arrays (host) or torch tensors (host or
+CUDA), converted to float64 / int32 contiguous buffers as the ABI requires.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+SPH_OK = 0
+SPH_E_INVALID = -1
+SPH_E_CUDA = -2
+SPH_E_OOM = -3
+SPH_E_DOMAIN = -4
+SPH_E_UNSTABLE = -5
+SPH_E_CAPACITY = -6
+SPH_E_TIMEOUT = -7
+SPH_FLAG_GRAPH = 1
+SPH_FLAG_KEEP_ACC = 2
+
+ERROR_NAMES = {0: "SPH_OK", -1: "SPH_E_INVALID", -2: "SPH_E_CUDA", -3: "SPH_E_OOM",
+               -4: "SPH_E_DOMAIN", -5: "SPH_E_UNSTABLE", -6: "SPH_E_CAPACITY", -7: "SPH_E_TIMEOUT"}
+
+# every function declared in include/sph.h
+EXPORTS = [
+    "sph_params_check", "sph_create", "sph_destroy", "sph_last_error", "sph_get_info",
+    "sph_build_cells", "sph_advection_step", "sph_acoustic_substep", "sph_step",
+    "sph_diagnostics", "sph_get_state", "sph_set_state", "sph_get_acceleration",
+    "sph_get_permutation", "sph_get_neighbours", "sph_pair_count", "sph_kernel_launches",
+    "sph_set_kernel_timing", "sph_kernel_times",
+]
+
+
+class SphParams(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32), ("free_surface", ctypes.c_int32),
+        ("h", ctypes.c_double), ("dp", ctypes.c_double),
+        ("rho0", ctypes.c_double), ("c0", ctypes.c_double),
+        ("cfl_ad", ctypes.c_double), ("cfl_ac", ctypes.c_double),
+        ("u_ref", ctypes.c_double), ("nu", ctypes.c_double),
+        ("gravity", ctypes.c_double * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+        ("periodic", ctypes.c_int32 * 3), ("capacity", ctypes.c_int32), ("flags", ctypes.c_uint32),
+    ]
+
+
+class SphDiag(ctypes.Structure):
+    _fields_ = [
+        ("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3),
+        ("kinetic", ctypes.c_double), ("potential", ctypes.c_double),
+        ("internal", ctypes.c_double), ("energy", ctypes.c_double),
+        ("max_rho_dev", ctypes.c_double), ("mean_rho_dev", ctypes.c_double),
+        ("front_x", ctypes.c_double), ("t", ctypes.c_double), ("dt_ad", ctypes.c_double),
+        ("n_fluid", ctypes.c_int64), ("advection_steps", ctypes.c_int64),
+        ("substeps", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {"mass": self.mass, "momentum": np.array(self.momentum[:]), "kinetic": self.kinetic,
+                "potential": self.potential, "internal": self.internal, "energy": self.energy,
+                "max_rho_dev": self.max_rho_dev, "mean_rho_dev": self.mean_rho_dev,
+                "front_x": self.front_x, "t": self.t, "dt_ad": self.dt_ad,
+                "n_fluid": self.n_fluid, "advection_steps": self.advection_steps,
+                "substeps": self.substeps}
+
+
+class SphInfo(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32), ("n_instances", ctypes.c_int32), ("capacity", ctypes.c_int32),
+        ("bits", ctypes.c_int32), ("n_fluid", ctypes.c_int64), ("n_wall", ctypes.c_int64),
+        ("n_cells", ctypes.c_int64), ("cell", ctypes.c_double), ("dq", ctypes.c_double),
+        ("sigma0", ctypes.c_double), ("R2", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+class SphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load():
+    """Load libsph.so; raise if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libsph.so not built at {LIB_PATH}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "sph_params_check": (i32, [ctypes.POINTER(SphParams)]),
+        "sph_create": (i32, [ctypes.POINTER(SphParams), i32, P, P, i64, P, P, P, P, i64, P, P, P, P,
+                             ctypes.POINTER(P)]),
+        "sph_destroy": (None, [P]),
+        "sph_last_error": (ctypes.c_char_p, [P]),
+        "sph_get_info": (i32, [P, ctypes.POINTER(SphInfo)]),
+        "sph_build_cells": (i32, [P, P]),
+        "sph_advection_step": (i32, [P, ctypes.POINTER(dbl), P]),
+        "sph_acoustic_substep": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(dbl), P]),
+        "sph_step": (i32, [P, i32, P]),
+        "sph_diagnostics": (i32, [P, ctypes.POINTER(SphDiag), P]),
+        "sph_get_state": (i32, [P, P, P, P, P, P]),
+        "sph_set_state": (i32, [P, P, P, P, P, dbl, P]),
+        "sph_get_acceleration": (i32, [P, P, P]),
+        "sph_get_permutation": (i32, [P, P, P]),
+        "sph_get_neighbours": (i32, [P, P, P, P, P, i32, P]),
+        "sph_pair_count": (i32, [P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),
+        "sph_kernel_launches": (i32, [P, ctypes.POINTER(i64)]),
+        "sph_set_kernel_timing": (i32, [P, i32]),
+        "sph_kernel_times": (i32, [P, ctypes.POINTER(dbl), ctypes.POINTER(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------------------ helpers
+def _ptr(a):
+    """Raw address of a contiguous numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()            # torch tensor (host or device)
+
+
+def _f64(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float64)
+    import torch
+    return a.to(torch.float64).contiguous()
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream       # torch.cuda.Stream
+
+
+def params_from(problem, flags=0, capacity=0) -> SphParams:
+    """Build the C parameter struct from any object carrying the problem's attributes."""
+    p = SphParams()
+    p.dim = int(problem.dim)
+    p.free_surface = int(problem.free_surface)
+    p.h, p.dp = float(problem.h), float(problem.dp)
+    p.rho0, p.c0 = float(problem.rho0), float(problem.c0)
+    p.cfl_ad, p.cfl_ac = float(problem.cfl_ad), float(problem.cfl_ac)
+    p.u_ref, p.nu = float(problem.u_ref), float(problem.nu)
+    for a in range(3):
+        p.gravity[a] = float(problem.gravity[a])
+        p.lo[a] = float(problem.lo[a])
+        p.hi[a] = float(problem.hi[a])
+        p.periodic[a] = int(problem.periodic[a])
+    p.capacity = int(capacity)
+    p.flags = int(flags)
+    return p
+
+
+def check(lib, h, code):
+    if code != SPH_OK:
+        msg = lib.sph_last_error(h).decode() if h else ""
+        raise SphError(code, msg)
+
+
+# ------------------------------------------------------------------------------ C names
+def sph_params_check(params: SphParams) -> int:
+    return load().sph_params_check(ctypes.byref(params))
+
+
+def sph_create(params, pos, vel, rho, mass, wall_pos, wall_normal, wall_vol,
+               fluid_offsets=None, wall_offsets=None, stream=None):
+    """params: one SphParams or a list (one per tank). Returns the opaque handle."""
+    lib = load()
+    plist = params if isinstance(params, (list, tuple)) else [params]
+    arr = (SphParams * len(plist))(*plist)
+    pos, vel, rho, mass = _f64(pos), _f64(vel), _f64(rho), _f64(mass)
+    wall_pos, wall_normal, wall_vol = _f64(wall_pos), _f64(wall_normal), _f64(wall_vol)
+    fo = None if fluid_offsets is None else np.ascontiguousarray(fluid_offsets, dtype=np.int64)
+    wo = None if wall_offsets is None else np.ascontiguousarray(wall_offsets, dtype=np.int64)
+    n = int(rho.shape[0])
+    nw = int(wall_vol.shape[0])
+    h = ctypes.c_void_p()
+    code = lib.sph_create(arr, len(plist), _ptr(fo), _ptr(wo), n, _ptr(pos), _ptr(vel), _ptr(rho),
+                          _ptr(mass), nw, _ptr(wall_pos), _ptr(wall_normal), _ptr(wall_vol),
+                          _stream(stream), ctypes.byref(h))
+    if code != SPH_OK:
+        msg = lib.sph_last_error(h).decode() if h.value else ""
+        if h.value:
+            lib.sph_destroy(h)
+        raise SphError(code, msg)
+    return h
+
+
+def sph_destroy(h):
+    load().sph_destroy(h)
+
+
+def sph_get_info(h) -> SphInfo:
+    lib = load()
+    info = SphInfo()
+    check(lib, h, lib.sph_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def sph_build_cells(h, stream=None):
+    lib = load()
+    check(lib, h, lib.sph_build_cells(h, _stream(stream)))
+
+
+def sph_advection_step(h, stream=None, want_dt=True):
+    lib = load()
+    dt = ctypes.c_double(0.0)
+    check(lib, h, lib.sph_advection_step(h, ctypes.byref(dt) if want_dt else None, _stream(stream)))
+    return dt.value
+
+
+def sph_acoustic_substep(h, stream=None, sync=True):
+    lib = load()
+    done = ctypes.c_int32(0)
+    dt = ctypes.c_double(0.0)
+    if sync:
+        check(lib, h, lib.sph_acoustic_substep(h, ctypes.byref(done), ctypes.byref(dt), _stream(stream)))
+        return bool(done.value), dt.value
+    check(lib, h, lib.sph_acoustic_substep(h, None, None, _stream(stream)))
+    return None, None
+
+
+def sph_step(h, n_advection_steps=1, stream=None):
+    lib = load()
+    check(lib, h, lib.sph_step(h, int(n_advection_steps), _stream(stream)))
+
+
+def sph_diagnostics(h, n_instances=1, stream=None):
+    lib = load()
+    out = (SphDiag * n_instances)()
+    check(lib, h, lib.sph_diagnostics(h, out, _stream(stream)))
+    return [d.as_dict() for d in out]
+
+
+def sph_get_state(h, n, dim, stream=None, out=None):
+    """Returns (pos, vel, rho, drho_dt) float64 numpy arrays in id order (or fills `out`)."""
+    lib = load()
+    if out is None:
+        out = (np.empty((n, dim)), np.empty((n, dim)), np.empty(n), np.empty(n))
+    check(lib, h, lib.sph_get_state(h, *[_ptr(a) for a in out], _stream(stream)))
+    return out
+
+
+def sph_set_state(h, pos, vel, rho, drho_dt=None, t=-1.0, stream=None):
+    lib = load()
+    pos, vel, rho, drho_dt = _f64(pos), _f64(vel), _f64(rho), _f64(drho_dt)
+    check(lib, h, lib.sph_set_state(h, _ptr(pos), _ptr(vel), _ptr(rho), _ptr(drho_dt), float(t),
+                                    _stream(stream)))
+
+
+def sph_get_acceleration(h, n, dim, stream=None):
+    lib = load()
+    acc = np.empty((n, dim))
+    check(lib, h, lib.sph_get_acceleration(h, _ptr(acc), _stream(stream)))
+    return acc
+
+
+def sph_get_permutation(h, n, stream=None):
+    lib = load()
+    ids = np.empty(n, dtype=np.int32)
+    check(lib, h, lib.sph_get_permutation(h, _ptr(ids), _stream(stream)))
+    return ids
+
+
+def sph_get_neighbours(h, n, stride, stream=None):
+    """Returns (fluid_count, wall_count, fluid_ids[n, stride], wall_ids[n, stride])."""
+    lib = load()
+    fc = np.empty(n, dtype=np.int32)
+    wc = np.empty(n, dtype=np.int32)
+    fi = np.empty((n, stride), dtype=np.int32)
+    wi = np.empty((n, stride), dtype=np.int32)
+    check(lib, h, lib.sph_get_neighbours(h, _ptr(fc), _ptr(wc), _ptr(fi), _ptr(wi), int(stride),
+                                         _stream(stream)))
+    return fc, wc, fi, wi
+
+
+def sph_pair_count(h, stream=None):
+    lib = load()
+    f = ctypes.c_int64(0)
+    w = ctypes.c_int64(0)
+    check(lib, h, lib.sph_pair_count(h, ctypes.byref(f), ctypes.byref(w), _stream(stream)))
+    return int(f.value), int(w.value)
+
+
+def sph_kernel_launches(h) -> int:
+    lib = load()
+    v = ctypes.c_int64(0)
+    check(lib, h, lib.sph_kernel_launches(h, ctypes.byref(v)))
+    return int(v.value)
+
+
+def sph_set_kernel_timing(h, enable=True):
+    lib = load()
+    check(lib, h, lib.sph_set_kernel_timing(h, 1 if enable else 0))
+
+
+def sph_kernel_times(h):
+    lib = load()
+    ms = (ctypes.c_double * 2)()
+    cnt = (ctypes.c_int64 * 2)()
+    check(lib, h, lib.sph_kernel_times(h, ms, cnt))
+    return list(ms), list(cnt)
+
+
+# ------------------------------------------------------------------------------ convenience
+class Simulation:
+    """One handle over one or more tanks built from workload objects (marshalling only)."""
+
+    def __init__(self, problems, flags=0, capacity=0, stream=None):
+        probs = problems if isinstance(problems, (list, tuple)) else [problems]
+        self.problems = probs
+        self.dim = int(probs[0].dim)
+        self.stream = stream
+        params = [params_from(p, flags=flags, capacity=capacity) for p in probs]
+        pos = np.concatenate([np.asarray(p.pos, dtype=np.float64).reshape(-1, self.dim) for p in probs])
+        vel = np.concatenate([np.asarray(p.vel, dtype=np.float64).reshape(-1, self.dim) for p in probs])
+        rho = np.concatenate([np.asarray(p.rho, dtype=np.float64) for p in probs])
+        mass = np.concatenate([np.asarray(p.mass, dtype=np.float64) for p in probs])
+        wpos = np.concatenate([np.asarray(p.wall_pos, dtype=np.float64).reshape(-1, self.dim) for p in probs])
+        wnrm = np.concatenate([np.asarray(p.wall_normal, dtype=np.float64).reshape(-1, self.dim) for p in probs])
+        wvol = np.concatenate([np.asarray(p.wall_vol, dtype=np.float64) for p in probs])
+        fo = np.cumsum([0] + [len(p.rho) for p in probs])
+        wo = np.cumsum([0] + [len(p.wall_vol) for p in probs])
+        self.n = int(rho.shape[0])
+        self.n_wall = int(wvol.shape[0])
+        self.n_instances = len(probs)
+        self.fluid_offsets = fo
+        self.handle = sph_create(params, pos, vel, rho, mass, wpos, wnrm, wvol,
+                                 fo if len(probs) > 1 else None, wo if len(probs) > 1 else None,
+                                 stream=stream)
+
+    def close(self):
+        if self.handle is not None:
+            sph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return sph_get_info(self.handle)
+
+    def build_cells(self):
+        sph_build_cells(self.handle, self.stream)
+
+    def advection_step(self):
+        return sph_advection_step(self.handle, self.stream)
+
+    def acoustic_substep(self):
+        return sph_acoustic_substep(self.handle, self.stream)
+
+    def step(self, n=1):
+        sph_step(self.handle, n, self.stream)
+
+    def diagnostics(self):
+        d = sph_diagnostics(self.handle, self.n_instances, self.stream)
+        return d if self.n_instances > 1 else d[0]
+
+    def state(self):
+        return sph_get_state(self.handle, self.n, self.dim, self.stream)
+
+    def set_state(self, pos, vel, rho, drho_dt=None, t=-1.0):
+        sph_set_state(self.handle, pos, vel, rho, drho_dt, t, self.stream)
+
+    def acceleration(self):
+        return sph_get_acceleration(self.handle, self.n, self.dim, self.stream)
+
+    def permutation(self):
+        return sph_get_permutation(self.handle, self.n, self.stream)
+
+    def neighbours(self):
+        cap = self.info().capacity
+        return sph_get_neighbours(self.handle, self.n, cap, self.stream)
+
+    def kernel_launches(self):
+        return sph_kernel_launches(self.handle)
+
+    def pair_count(self):
+        return sph_pair_count(self.handle, self.stream)

@@ -78,7 +78,8 @@ def tank_walls(inner_lo, inner_hi, dp, layers=WALL_LAYERS):
     The lattice is anchored at the outer corner (inner_lo - layers*dp), so fluid
     placed at inner_lo + (i+1/2)dp sits on the same lattice. Each wall particle's
     normal is the normalised sum of the unit normals of the inner faces it lies
-    beyond, pointing into the tank; its volume is dp**dim.
+    beyond, pointing into the tank; its volume is dp**dim. Points are ordered with
+    x varying fastest over the outer box.
     """
     inner_lo = np.asarray(inner_lo, dtype=np.float64)
     inner_hi = np.asarray(inner_hi, dtype=np.float64)
@@ -86,12 +87,29 @@ def tank_walls(inner_lo, inner_hi, dp, layers=WALL_LAYERS):
     outer_lo = inner_lo - layers * dp
     outer_hi = inner_hi + layers * dp
     counts = [int(math.floor((outer_hi[a] - outer_lo[a]) / dp + 1e-9)) for a in range(dim)]
-    pts = _lattice(outer_lo, counts, dp)
-    below = pts < inner_lo[None, :]
-    above = pts > inner_hi[None, :]
-    outside = np.any(below | above, axis=1)
-    pts = pts[outside]
-    normal = below[outside].astype(np.float64) - above[outside].astype(np.float64)
+    coord = [outer_lo[a] + (np.arange(counts[a]) + 0.5) * dp for a in range(dim)]
+    side = [(coord[a] > inner_hi[a]).astype(np.int8) - (coord[a] < inner_lo[a]).astype(np.int8)
+            for a in range(dim)]
+    # flat index x + nx (y + ny z) of every outside point, built from slabs that do not overlap
+    strides = [1, counts[0], counts[0] * counts[1]][:dim]
+    idx = [np.arange(counts[a], dtype=np.int64) * strides[a] for a in range(dim)]
+    out_ = [idx[a][side[a] != 0] for a in range(dim)]
+    in_ = [idx[a][side[a] == 0] for a in range(dim)]
+    pieces = []
+    for a in range(dim):          # outside on axis a, inside on the axes before it
+        parts = [in_[b] if b < a else (out_[b] if b == a else idx[b]) for b in range(dim)]
+        flat = parts[0]
+        for b in range(1, dim):
+            flat = (flat[None, :] + parts[b][:, None]).reshape(-1)
+        pieces.append(flat)
+    flat = np.sort(np.concatenate(pieces))
+    ijk = []
+    rem = flat
+    for a in range(dim):
+        ijk.append(rem % counts[a])
+        rem = rem // counts[a]
+    pts = np.stack([coord[a][ijk[a]] for a in range(dim)], axis=1)
+    normal = np.stack([side[a][ijk[a]].astype(np.float64) * -1.0 for a in range(dim)], axis=1)
     normal /= np.linalg.norm(normal, axis=1, keepdims=True)
     vol = np.full(pts.shape[0], dp ** dim)
     return pts, normal, vol

@@ -1,0 +1,419 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Neighbour sets and cell permutations are compared bit for bit; densities,
+accelerations and velocities after one acoustic substep within 1e-5 relative
+L2 from an identical, representable starting state; trajectories on bulk
+quantities (energy, front) within 0.5 %.
+"""
+import copy
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import wcsph as o
+from paper_2010_12375_gb300 import workloads as wk
+from tests.parity import REL_L2_TOL, perturbed_state, rel_l2, representable, walls_representable
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def sph():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_12375_gb300 import sph as s
+    s.load()
+    return s
+
+
+def _with_walls_on_grid(problem):
+    p = copy.copy(problem)
+    p.wall_pos = walls_representable(problem)
+    return p
+
+
+def _rowsets(count, ids):
+    return [set(ids[i, :count[i]].tolist()) for i in range(len(count))]
+
+
+def _oracle_rowsets(n, I, J):
+    rows = [set() for _ in range(n)]
+    for i, j in zip(I.tolist(), J.tolist()):
+        rows[i].add(j)
+    return rows
+
+
+# ------------------------------------------------------------------ cells and neighbours
+@pytest.mark.parametrize("case", ["dam2d", "tg", "dam3d", "ragged"])
+def test_neighbour_sets_and_permutation_bit_exact(sph, case):
+    if case == "dam2d":
+        prob = wk.dam_break_2d()
+        x, v, rho, drho = perturbed_state(prob, 1, 0.3, 0.0)
+        x = x + np.random.default_rng(2).uniform(-0.2, 0.2, size=x.shape) * prob.dp
+    elif case == "tg":
+        prob = wk.taylor_green(64)
+        x = prob.pos + np.random.default_rng(3).uniform(-0.3, 0.3, size=prob.pos.shape) * prob.dp
+        x = np.mod(x, 1.0)
+        v, rho = prob.vel, prob.rho
+    elif case == "dam3d":
+        prob = wk.dam_break_3d(16)
+        x = prob.pos + np.random.default_rng(4).uniform(-0.2, 0.2, size=prob.pos.shape) * prob.dp
+        v, rho = prob.vel, prob.rho
+    else:   # a count that is not a multiple of the block size, with a ragged free surface
+        prob = wk.dam_break(dim=2, H=1.0, L=1.37, n_per_H=33)
+        keep = np.random.default_rng(5).uniform(size=prob.n_fluid) > 0.05
+        prob.pos, prob.vel, prob.rho, prob.mass = prob.pos[keep], prob.vel[keep], prob.rho[keep], prob.mass[keep]
+        x, v, rho = prob.pos, prob.vel, prob.rho
+    prob = _with_walls_on_grid(prob)
+    xq, v32, rho32, _ = representable(prob, x, v, rho)
+    prob.pos, prob.vel, prob.rho = xq, v32, rho32
+    sim = sph.Simulation(prob)
+    sim.build_cells()
+    fc, wc, fi, wi = sim.neighbours()
+    perm = sim.permutation()
+    prm = o.Params.from_problem(prob)
+    I, J, IW, KW = o.neighbour_sets_quantised(xq, prob.wall_pos, prm)
+    assert _rowsets(fc, fi) == _oracle_rowsets(prob.n_fluid, I, J)
+    assert _rowsets(wc, wi) == _oracle_rowsets(prob.n_fluid, IW, KW)
+    np.testing.assert_array_equal(perm, o.cell_permutation(xq, np.arange(prob.n_fluid), prm))
+    # the FP64 definition |r_i - r_j| < 2h agrees with the fixed-point decision
+    a = o.neighbour_sets(xq, prob.wall_pos, prm)
+    assert a[0].size == I.size and a[2].size == IW.size
+    sim.close()
+
+
+# ------------------------------------------------------------------ density summation
+@pytest.mark.parametrize("case", ["dam2d", "tg", "dam3d"])
+def test_density_summation(sph, case):
+    if case == "dam2d":
+        prob = wk.dam_break_2d()
+    elif case == "tg":
+        prob = wk.taylor_green(100)
+    else:
+        prob = wk.dam_break_3d(20)
+    prob = _with_walls_on_grid(prob)
+    rng = np.random.default_rng(7)
+    x = prob.pos + rng.uniform(-0.15, 0.15, size=prob.pos.shape) * prob.dp
+    if case == "tg":
+        x = np.mod(x, 1.0)
+    rho = np.full(prob.n_fluid, prob.rho0 * 0.999)      # below the summation in the bulk
+    xq, v32, rho32, _ = representable(prob, x, prob.vel, rho)
+    prob.pos, prob.vel, prob.rho = xq, v32, rho32
+    sim = sph.Simulation(prob)
+    sim.build_cells()
+    dt_ad = sim.advection_step()
+    _, _, rho_gpu, _ = sim.state()
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    nb = o.neighbour_sets_quantised(st.x, w.x, prm)
+    rho_or = o.density_summation(st, w, nb, prm)
+    assert rel_l2(rho_gpu, rho_or) < REL_L2_TOL
+    # the deviation rho - rho0 itself is accurate to FP32 rounding of W terms
+    assert np.max(np.abs(rho_gpu - rho_or)) < 2e-6 * prm.rho0
+    assert abs(dt_ad - o.dt_advection(st.v, prm)) < 1e-6 * dt_ad
+    sim.close()
+
+
+# ------------------------------------------------------------------ one acoustic substep
+def _substep_case(case):
+    if case == "dam2d":
+        prob = wk.dam_break_2d()
+        vel_amp, rho_amp = 0.3, 0.01
+    elif case == "tg":
+        prob = wk.taylor_green(64)
+        vel_amp, rho_amp = 0.05, 0.005
+    elif case == "dam3d":
+        prob = wk.dam_break_3d(16)
+        vel_amp, rho_amp = 0.3, 0.01
+    else:
+        prob = wk.periodic_box(dim=3, n=12, seed=3)
+        vel_amp, rho_amp = 0.1, 0.01
+    return prob, vel_amp, rho_amp
+
+
+@pytest.mark.parametrize("case", ["dam2d", "tg", "dam3d", "box3d"])
+def test_one_substep_matches_oracle(sph, case):
+    prob, vel_amp, rho_amp = _substep_case(case)
+    prob = _with_walls_on_grid(prob)
+    x, v, rho, drho = perturbed_state(prob, 11, vel_amp, rho_amp)
+    rng = np.random.default_rng(12)
+    x = x + rng.uniform(-0.1, 0.1, size=x.shape) * prob.dp
+    if np.any(prob.periodic[:prob.dim]):
+        x = np.mod(x, 1.0)
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    nb = o.neighbour_sets(x, w.x, prm)
+    if prm.free_surface:
+        # make density re-initialisation an identity on both sides: rho* above the sum
+        st.x = x
+        rho = np.maximum(rho, o.density_summation(st, w, nb, prm)) + 1e-5 * prm.rho0
+    xq, v32, rho32, d32 = representable(prob, x, v, rho, drho)
+    sim = sph.Simulation(prob, flags=sph.SPH_FLAG_KEEP_ACC)
+    sim.set_state(xq, v32, rho32, d32, t=0.0)
+    sim.build_cells()
+    sim.advection_step()
+    _, _, rho_mid, _ = sim.state()
+    done, dt_gpu = sim.acoustic_substep()
+    acc_gpu = sim.acceleration()
+    pos_gpu, vel_gpu, rho_gpu, drho_gpu = sim.state()
+    sim.close()
+
+    st = o.State(xq, v32, rho32, d32, np.asarray(prob.mass, dtype=np.float64), 0.0)
+    nb = o.neighbour_sets_quantised(st.x, w.x, prm)
+    Dt = o.dt_advection(st.v, prm)
+    st.rho = o.density_summation(st, w, nb, prm)
+    if prm.free_surface:
+        np.testing.assert_array_equal(rho_mid, st.rho)      # identity on both sides
+    acc_prior = o.viscous_acceleration(st, nb, prm)
+    dt = min(o.dt_acoustic(st.v, prm), Dt)
+    assert abs(dt_gpu - dt) < 1e-6 * dt
+    half, dvdt = o.pressure_relaxation(st, w, nb, acc_prior, dt, prm)
+    out = o.density_relaxation(half, w, nb, dt, prm)
+    assert rel_l2(acc_gpu, dvdt) < REL_L2_TOL, rel_l2(acc_gpu, dvdt)
+    assert rel_l2(vel_gpu, out.v) < REL_L2_TOL
+    assert rel_l2(rho_gpu, out.rho) < REL_L2_TOL
+    assert rel_l2(drho_gpu, out.drho) < 1e-3 * max(1.0, np.linalg.norm(out.drho)) or \
+        np.max(np.abs(drho_gpu - out.drho)) < 1e-4 * max(np.max(np.abs(out.drho)), 1.0)
+    dx = o.min_image(pos_gpu - out.x, prm.period)
+    _, _, _, dq, _ = o.quantisation(prm)
+    assert np.max(np.abs(dx)) < 8 * dq + 1e-7 * prm.dp
+
+
+# ------------------------------------------------------------------ invariants on the GPU
+def test_momentum_and_mass_conservation(sph):
+    prob = wk.periodic_box(dim=3, n=16, seed=21, vel_amp=0.3, rho_amp=0.01)
+    sim = sph.Simulation(prob)
+    d0 = sim.diagnostics()
+    sim.step(3)
+    d1 = sim.diagnostics()
+    scale = np.sum(prob.mass[:, None] * np.abs(prob.vel))
+    assert np.max(np.abs(d1["momentum"] - d0["momentum"])) < 1e-6 * scale
+    assert d1["mass"] == d0["mass"]
+    assert d1["substeps"] >= 9
+    sim.close()
+
+
+def test_graph_and_host_loop_agree_bit_for_bit(sph):
+    prob = wk.dam_break_2d(n_per_H=20)
+    a = sph.Simulation(prob)
+    b = sph.Simulation(prob, flags=sph.SPH_FLAG_GRAPH)
+    a.step(6)
+    b.step(6)
+    for u, v in zip(a.state(), b.state()):
+        np.testing.assert_array_equal(u, v)
+    da, db = a.diagnostics(), b.diagnostics()
+    assert da["substeps"] == db["substeps"] and da["t"] == db["t"]
+    assert b.kernel_launches() > 0
+    a.close()
+    b.close()
+
+
+def test_restart_is_bit_identical(sph):
+    prob = wk.dam_break_2d(n_per_H=20)
+    a = sph.Simulation(prob)
+    a.step(8)
+    ref = a.state()
+    b = sph.Simulation(prob)
+    b.step(4)
+    pos, vel, rho, drho = b.state()
+    t = b.diagnostics()["t"]
+    b.close()
+    c = sph.Simulation(prob)
+    c.set_state(pos, vel, rho, drho, t=t)
+    c.step(4)
+    for u, v in zip(ref, c.state()):
+        np.testing.assert_array_equal(u, v)
+    assert c.diagnostics()["t"] == a.diagnostics()["t"]
+    a.close()
+    c.close()
+
+
+def test_batched_instances_match_single_runs(sph):
+    tanks = wk.batched_dam_breaks(n_instances=6, n_min=300, n_max=3000)
+    multi = sph.Simulation(tanks)
+    multi.step(3)
+    pos_m, vel_m, rho_m, _ = multi.state()
+    dm = multi.diagnostics()
+    off = multi.fluid_offsets
+    for k, t in enumerate(tanks):
+        single = sph.Simulation(t)
+        single.step(3)
+        pos_s, vel_s, rho_s, _ = single.state()
+        sl = slice(off[k], off[k + 1])
+        np.testing.assert_array_equal(pos_m[sl], pos_s)
+        np.testing.assert_array_equal(vel_m[sl], vel_s)
+        np.testing.assert_array_equal(rho_m[sl], rho_s)
+        ds = single.diagnostics()
+        assert dm[k]["substeps"] == ds["substeps"] and dm[k]["t"] == ds["t"]
+        assert abs(dm[k]["energy"] - ds["energy"]) <= 1e-12 * abs(ds["energy"])
+        single.close()
+    multi.close()
+
+
+# ------------------------------------------------------------------ trajectories
+def _interp(t, ts, ys):
+    return np.interp(t, ts, ys)
+
+
+@pytest.mark.slow
+def test_dam_break_2d_trajectory_energy_and_front(sph):
+    with open(os.path.join(GOLDEN, "dam_break_2d_trajectory.json")) as f:
+        gold = json.load(f)
+    prob = wk.dam_break_2d()
+    sim = sph.Simulation(prob, flags=sph.SPH_FLAG_GRAPH)
+    ts, es, fs = [], [], []
+    d = sim.diagnostics()
+    ts.append(d["t"]); es.append(d["energy"]); fs.append(d["front_x"])
+    while d["t"] < gold["t_end"] * (1 - 1e-12):
+        sim.step(5)
+        d = sim.diagnostics()
+        ts.append(d["t"]); es.append(d["energy"]); fs.append(d["front_x"])
+    sim.close()
+    gt, ge, gf = np.array(gold["t"]), np.array(gold["energy"]), np.array(gold["front_x"])
+    ts = np.array(ts)
+    E0 = ge[0]
+    mask = ts <= gt[-1]
+    err_e = np.max(np.abs(np.array(es)[mask] - _interp(ts[mask], gt, ge))) / abs(E0)
+    assert err_e < 5e-3, err_e
+    L = prob.meta["L"]
+    pre = ts[mask] < gold["t_impact"]
+    err_f = np.max(np.abs(np.array(fs)[mask][pre] - _interp(ts[mask][pre], gt, gf))) / L
+    assert err_f < 5e-3, err_f
+
+
+def test_taylor_green_kinetic_energy(sph):
+    prob = wk.taylor_green(64)
+    sim = sph.Simulation(prob, flags=sph.SPH_FLAG_GRAPH)
+    ts, kes = [], []
+    d = sim.diagnostics()
+    while d["t"] < 0.1:
+        ts.append(d["t"]); kes.append(d["kinetic"])
+        sim.step(1)
+        d = sim.diagnostics()
+    ts.append(d["t"]); kes.append(d["kinetic"])
+    sim.close()
+    _, series = o.run(prob, t_end=0.1)
+    ot = np.array([s["t"] for s in series])
+    ok = np.array([s["kinetic"] for s in series])
+    kes = np.array(kes)
+    assert np.max(np.abs(kes - _interp(np.array(ts), ot, ok))) / ok[0] < 5e-3
+    exact = np.exp(-16 * np.pi ** 2 * 0.01 * np.array(ts))
+    assert np.max(np.abs(kes / kes[0] - exact)) < 0.06
+
+
+# ------------------------------------------------------------------ edge cases and errors
+def test_empty_fluid_and_single_particle(sph):
+    prob = wk.dam_break_2d(n_per_H=10)
+    empty = copy.copy(prob)
+    empty.pos = np.zeros((0, 2)); empty.vel = np.zeros((0, 2))
+    empty.rho = np.zeros(0); empty.mass = np.zeros(0)
+    sim = sph.Simulation(empty)
+    sim.step(2)
+    d = sim.diagnostics()
+    assert d["n_fluid"] == 0 and d["mass"] == 0.0
+    sim.close()
+    one = copy.copy(prob)
+    one.pos = np.array([[2.6, 3.0]]); one.vel = np.array([[0.1, 0.0]])
+    one.rho = np.array([1.0]); one.mass = np.array([prob.dp ** 2])
+    sim = sph.Simulation(one)
+    sim.step(3)
+    pos, vel, _, _ = sim.state()
+    t = sim.diagnostics()["t"]
+    assert abs(pos[0, 1] - (3.0 - 0.5 * t * t)) < 1e-6 and abs(vel[0, 1] + t) < 1e-6
+    sim.close()
+
+
+def test_errors_are_reported_not_trapped(sph):
+    prob = wk.dam_break_2d(n_per_H=10)
+    with pytest.raises(sph.SphError) as e:
+        p = sph.params_from(prob)
+        p.h = -1.0
+        sph.sph_create(p, prob.pos, prob.vel, prob.rho, prob.mass, prob.wall_pos,
+                       prob.wall_normal, prob.wall_vol)
+    assert e.value.code == sph.SPH_E_INVALID
+    # neighbour capacity overflow
+    sim = sph.Simulation(prob, capacity=4)
+    sim.build_cells()
+    with pytest.raises(sph.SphError) as e:
+        sim.advection_step()
+    assert e.value.code == sph.SPH_E_CAPACITY
+    sim.close()
+    # a particle outside the cell grid
+    bad = copy.copy(prob)
+    bad.pos = prob.pos.copy()
+    bad.pos[0] = [100.0, 100.0]
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(bad).step(1)
+    assert e.value.code == sph.SPH_E_DOMAIN
+    # NaN velocity
+    nan = copy.copy(prob)
+    nan.vel = prob.vel.copy()
+    nan.vel[3] = [np.nan, 0.0]
+    s2 = sph.Simulation(nan)
+    with pytest.raises(sph.SphError) as e:
+        s2.step(1)
+    assert e.value.code == sph.SPH_E_UNSTABLE
+    s2.close()
+
+
+# ------------------------------------------------------------------ full size, sampled
+def _local_problem(prob, x, v, rho, drho, centres, radius):
+    """Particles (fluid and wall) within `radius` of any centre: an oracle-sized sub-problem."""
+    from scipy.spatial import cKDTree
+    tf = cKDTree(x)
+    near = np.unique(np.concatenate(tf.query_ball_point(centres, radius)))
+    tw = cKDTree(prob.wall_pos)
+    wnear = np.unique(np.concatenate(tw.query_ball_point(centres, radius))).astype(np.int64)
+    sub = copy.copy(prob)
+    sub.pos, sub.vel, sub.rho, sub.mass = x[near], v[near], rho[near], prob.mass[near]
+    sub.wall_pos, sub.wall_normal, sub.wall_vol = (prob.wall_pos[wnear], prob.wall_normal[wnear],
+                                                    prob.wall_vol[wnear])
+    return sub, near, drho[near]
+
+
+@pytest.mark.slow
+def test_full_size_3d_first_substep_sampled(sph):
+    """3D dam break at 8.04M fluid particles (the benchmark workload), launched as the
+    benchmark launches it; one advection step's density summation and first substep
+    checked on sampled particles against the oracle run on their neighbourhoods."""
+    prob = wk.dam_break_3d(159)
+    x, v, rho, drho = perturbed_state(prob, 31, 0.2, 0.005)
+    xq, v32, rho32, d32 = representable(prob, x, v, rho, drho)
+    prob.wall_pos = walls_representable(prob)
+    prm = o.Params.from_problem(prob)
+    vmax_all = v32
+    sim = sph.Simulation(prob, flags=sph.SPH_FLAG_KEEP_ACC)
+    sim.set_state(xq, v32, rho32, d32, t=0.0)
+    sim.build_cells()
+    sim.advection_step()
+    _, _, rho_mid, _ = sim.state()
+    sim.acoustic_substep()
+    acc_gpu = sim.acceleration()
+    _, vel_gpu, _, _ = sim.state()
+    sim.close()
+    rng = np.random.default_rng(5)
+    samples = rng.choice(prob.n_fluid, size=400, replace=False)
+    # include particles next to the walls and at the free surface
+    samples = np.unique(np.concatenate([samples, np.argsort(xq[:, 1])[:50], np.argsort(-xq[:, 1])[:50],
+                                        np.argsort(xq[:, 0])[:50], np.argsort(xq[:, 2])[:50]]))
+    sub, near, dsub = _local_problem(prob, xq, v32, rho32, d32, xq[samples], 4.5 * prob.h)
+    sprm = o.Params.from_problem(sub)
+    st, w = o.state_from_problem(sub)
+    st.drho = dsub
+    nb = o.neighbour_sets_quantised(st.x, w.x, sprm)
+    Dt = o.dt_advection(vmax_all, prm)                # global |v|max from the input
+    st.rho = o.density_summation(st, w, nb, sprm)
+    local = np.searchsorted(near, samples)
+    assert rel_l2(rho_mid[samples], st.rho[local]) < REL_L2_TOL
+    dt = min(o.dt_acoustic(vmax_all, prm), Dt)
+    # the oracle's own summed densities feed its substep: only pairs whose 1-hop
+    # neighbourhood is complete are compared
+    half, dvdt = o.pressure_relaxation(st, w, nb, 0.0, dt, sprm)
+    assert rel_l2(acc_gpu[samples], dvdt[local]) < 1e-4
+    assert rel_l2(vel_gpu[samples], half.v[local]) < REL_L2_TOL
