@@ -400,6 +400,8 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
     I.wall_begin = wo[k];
     I.wall_end = wo[k + 1];
     if (params[k].nu > 0.0) any_visc = true;
+    for (int a = 0; a < dim; ++a)
+      if (params[k].periodic[a]) b.any_periodic = true;
     h->hinst.push_back(I);
   }
   if (n_cells >= (1ll << 32) - 1) return fail(h, SPH_E_INVALID, "too many cells");

@@ -238,7 +238,25 @@ __device__ __forceinline__ void for_neighbour_cells(const Inst& I, int cx, int c
   }
 }
 
-template <int D>
+// Candidate test: the squared distance in FP32 from exactly converted integer
+// differences (error < 3 ulp), with the exact integer test only inside a
+// +-2^-20 band around the threshold, so the decision is always the integer one.
+template <int D, bool PER>
+__device__ __forceinline__ bool within_fast(const int4& a, const int4& b, const Inst& I, float lo,
+                                            float hi) {
+  const float dx = biased_diff<PER>(a.x, b.x, I.period[0]) - kMagic;
+  const float dy = biased_diff<PER>(a.y, b.y, I.period[1]) - kMagic;
+  float d2 = fmaf(dx, dx, dy * dy);
+  if (D == 3) {
+    const float dz = biased_diff<PER>(a.z, b.z, I.period[2]) - kMagic;
+    d2 = fmaf(dz, dz, d2);
+  }
+  if (d2 < lo) return true;
+  if (d2 >= hi) return false;
+  return within<D>(a, b, I);
+}
+
+template <int D, bool PER>
 __global__ void __launch_bounds__(kBlock)
 k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst_of,
              const Inst* __restrict__ inst, const uint32_t* __restrict__ fstart,
@@ -247,6 +265,8 @@ k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Inst& I = inst[inst_of ? inst_of[i] : 0];
+  const float R2f = (float)I.R2;
+  const float lo = R2f * (1.0f - 9.5367431640625e-07f), hi = R2f * (1.0f + 9.5367431640625e-07f);
   const int4 pi = P[i];
   int cx = min(max(pi.x >> I.bits, 0), I.ncell[0] - 1);
   int cy = min(max(pi.y >> I.bits, 0), I.ncell[1] - 1);
@@ -254,9 +274,9 @@ k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst
   int nf = 0, nw = 0;
   bool overflow = false;
   for_neighbour_cells<D>(I, cx, cy, cz, fstart, [&](uint32_t b, uint32_t e) {
+#pragma unroll 2
     for (uint32_t j = b; j < e; ++j) {
-      if ((int64_t)j == i) continue;
-      if (within<D>(pi, P[j], I)) {
+      if (within_fast<D, PER>(pi, P[j], I, lo, hi) && (int64_t)j != i) {
         if (nf < cap) nbr[(int64_t)nf * n + i] = (int)j;
         else overflow = true;
         ++nf;
@@ -266,8 +286,9 @@ k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst
   if (nf > cap) nf = cap;
   if (WP) {
     for_neighbour_cells<D>(I, cx, cy, cz, wstart, [&](uint32_t b, uint32_t e) {
+#pragma unroll 2
       for (uint32_t j = b; j < e; ++j) {
-        if (within<D>(pi, WP[j], I)) {
+        if (within_fast<D, PER>(pi, WP[j], I, lo, hi)) {
           int k = nf + nw;
           if (k < cap) {
             nbr[(int64_t)k * n + i] = (int)j;
@@ -325,12 +346,10 @@ void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches) {
 void launch_neighbours(const Buffers& b, cudaStream_t s, int64_t* launches) {
   if (b.n == 0) return;
   const int4* wp = b.nw ? b.WP : nullptr;
-  if (b.dim == 2)
-    k_neighbours<2><<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.fstart, wp,
-                                                     b.wstart, b.cap, b.nbr, b.nbc, b.glob);
-  else
-    k_neighbours<3><<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.fstart, wp,
-                                                     b.wstart, b.cap, b.nbr, b.nbc, b.glob);
+  auto kern = b.dim == 2 ? (b.any_periodic ? k_neighbours<2, true> : k_neighbours<2, false>)
+                         : (b.any_periodic ? k_neighbours<3, true> : k_neighbours<3, false>);
+  kern<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.fstart, wp, b.wstart, b.cap,
+                                        b.nbr, b.nbc, b.glob);
   ++*launches;
 }
 

@@ -131,3 +131,46 @@ __device__ __forceinline__ float kernel_dW_over_r(float r, const Inst& I) {
 }
 
 }  // namespace sph
+
+// ---- packed FP32 (two lanes per instruction) -------------------------------------------
+// The relaxation kernels evaluate two neighbour pairs at a time in the .x/.y lanes
+// of float2 values with sm_100+ packed FP32 instructions.
+namespace sph {
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // a - b, one rounding
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 max2(float2 a, float b) { return make_float2(fmaxf(a.x, b), fmaxf(a.y, b)); }
+__device__ __forceinline__ float2 min2(float2 a, float b) { return make_float2(fminf(a.x, b), fminf(a.y, b)); }
+__device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ float2 rcp2(float2 a) {
+  return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y));
+}
+
+// s += a*b with Kahan compensation kept negated in nc (the product is fused).
+__device__ __forceinline__ void kahan2(float2& s, float2& nc, float2 a, float2 b) {
+  float2 y = fma2(a, b, nc);
+  float2 t = add2(s, y);
+  nc = sub2(y, sub2(t, s));
+  s = t;
+}
+
+// Exact int -> float of a fixed-point difference |d| < 2^22 with integer and FP32
+// adds only: the bits of 1.5*2^23 + d, read as a float, minus 1.5*2^23. Larger |d|
+// map to values of magnitude >= 2^22 quanta (>= 2h), which contribute nothing.
+constexpr unsigned kMagicBits = 0x4B400000u;
+constexpr float kMagic = 12582912.0f;
+
+template <bool PER>
+__device__ __forceinline__ float biased_diff(int qi, int qj, int period) {
+  unsigned d;
+  if (PER) d = (unsigned)wrap_diff(qi - qj, period) + kMagicBits;
+  else d = (unsigned)qi - (unsigned)qj + kMagicBits;
+  return __uint_as_float(d);
+}
+
+}  // namespace sph

@@ -11,6 +11,7 @@ namespace sph {
 struct Buffers {
   int64_t n = 0, nw = 0, n_cells = 0;
   int n_inst = 1, dim = 2, cap = 0;
+  bool any_periodic = false;      // some tank has a periodic axis
   Inst* inst = nullptr;           // [n_inst]
   Ctrl* ctrl = nullptr;           // [n_inst]
   Global* glob = nullptr;         // [1]

@@ -4,10 +4,7 @@
 //   k_viscous              Eq. eqviscous (once per advection step, fluid pairs)
 //   k_dt_advection         Eq. dt-advection (one thread per instance, FP64)
 //   k_dt_acoustic          Eq. dt-relax clamped to the advection step (one thread per instance)
-//   k_pressure_relaxation  Eq. verlet-first-half, Eq. eqeos, Eq. riemannsph (momentum),
-//                          wall problem Eqs. eqriepartial/eqrienoslip/eqriepright,
-//                          Eq. verlet-first-mediate
-//   k_density_relaxation   Eq. verlet-first-final with Eq. riemannsph (continuity)
+//   (the acoustic-substep relaxation kernels live in sph_relax.cu)
 //
 // Conventions: r_ij = r_i - r_j, e_ij = -r_ij/|r_ij| points from i to j, and
 // grad_i W_ij = (dW/dr) r_ij/|r_ij|. Interface states of the low-dissipation
@@ -362,189 +359,6 @@ k_viscous(int64_t n, const int4* __restrict__ P, const float4* __restrict__ V,
   acc_prior[i] = make_float4(s * ax, s * ay, s * az, 0.0f);
 }
 
-// ---------------------------------------------------------------- relaxations ---------
-template <int D>
-__global__ void __launch_bounds__(kBlock)
-k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __restrict__ VS,
-                      int4* __restrict__ PH, float4* __restrict__ VH,
-                      const float* __restrict__ mass, const int* __restrict__ inst_of,
-                      const Inst* __restrict__ inst, Ctrl* ctrl, const int* __restrict__ nbr,
-                      const uint32_t* __restrict__ nbc, const int4* __restrict__ WP,
-                      const float4* __restrict__ WN, const float4* __restrict__ acc_prior,
-                      float4* __restrict__ acc_keep, Global* g) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int kb;
-  const bool uni = block_one_instance(inst_of, n, &kb);
-  bool valid = i < n;
-  int k = valid ? inst_index(inst_of, i) : kb;
-  const double dtd = ctrl[k].dt;
-  if (dtd == 0.0) valid = false;                 // instance idle for this substep
-  float v2 = 0.0f;
-  if (valid) {
-    const Inst& I = inst[k];
-    const float dt = (float)dtd, hdt = 0.5f * dt;
-    const int4 pi = PS[i];
-    const float4 vi = VS[i];
-    const float dev_i = i2f(pi.w) + hdt * vi.w;       // Eq. verlet-first-half (density)
-    const float rho_i = I.rho0 + dev_i;
-    const float pr_i = I.c0sq * dev_i;                // Eq. eqeos
-    float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-    const uint32_t cnt = nbc[i];
-    const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
-    for (int kk = 0; kk < nf; ++kk) {
-      const int j = nbr[(int64_t)kk * n + i];
-      const int4 pj = PS[j];
-      const float4 vj = VS[j];
-      // half-step pair vector r_ij^{n+1/2} = r_ij^n + dt/2 (v_i - v_j)
-      float rx = fmaf(hdt, vi.x - vj.x, (float)wrap_diff(pi.x - pj.x, I.period[0]) * I.dq);
-      float ry = fmaf(hdt, vi.y - vj.y, (float)wrap_diff(pi.y - pj.y, I.period[1]) * I.dq);
-      float rz = D == 3 ? fmaf(hdt, vi.z - vj.z, (float)wrap_diff(pi.z - pj.z, I.period[2]) * I.dq) : 0.f;
-      float r2 = rx * rx + ry * ry + rz * rz;
-      if (!(r2 < I.four_h2) || r2 == 0.0f) continue;
-      const float inv_r = rsqrtf(r2);
-      const float r = r2 * inv_r;
-      const float fw = kernel_dW_over_r(r, I);        // (dW/dr)/r
-      const float dev_j = i2f(pj.w) + hdt * vj.w;
-      const float rho_j = I.rho0 + dev_j;
-      const float pr_j = I.c0sq * dev_j;
-      // U_L = v_i.e_ij, U_R = v_j.e_ij with e_ij = -r_ij/r
-      const float UL = -(vi.x * rx + vi.y * ry + vi.z * rz) * inv_r;
-      const float UR = -(vj.x * rx + vj.y * ry + vj.z * rz) * inv_r;
-      const float dU = UL - UR;
-      const float rho_bar = 0.5f * (rho_i + rho_j);
-      const float beta = fminf(kLimiter * fmaxf(dU, 0.0f) / I.c0, 1.0f);
-      const float Pstar = 0.5f * (pr_i + pr_j) + 0.5f * rho_bar * I.c0 * beta * dU;
-      const float mj = mass ? mass[j] : I.mass;
-      const float f = mj / rho_j * Pstar * fw;        // V_j P* (dW/dr)/r
-      kahan_add(ax, cx, f * rx);
-      kahan_add(ay, cy, f * ry);
-      if (D == 3) kahan_add(az, cz, f * rz);
-    }
-    for (int kk = 0; kk < nw; ++kk) {
-      const int w = nbr[(int64_t)(nf + kk) * n + i];
-      const int4 pw = WP[w];
-      const float4 nwv = WN[w];
-      float rx = fmaf(hdt, vi.x, (float)wrap_diff(pi.x - pw.x, I.period[0]) * I.dq);
-      float ry = fmaf(hdt, vi.y, (float)wrap_diff(pi.y - pw.y, I.period[1]) * I.dq);
-      float rz = D == 3 ? fmaf(hdt, vi.z, (float)wrap_diff(pi.z - pw.z, I.period[2]) * I.dq) : 0.f;
-      float r2 = rx * rx + ry * ry + rz * rz;
-      if (!(r2 < I.four_h2) || r2 == 0.0f) continue;
-      const float inv_r = rsqrtf(r2);
-      const float fw = kernel_dW_over_r(r2 * inv_r, I);
-      // one-sided problem along the wall normal: U_L = -n.v_i, U_R = -U_L,
-      // P_R = P_L + rho_i g.(r_w - r_i), rho_R from the EoS
-      const float UL = -(nwv.x * vi.x + nwv.y * vi.y + nwv.z * vi.z);
-      const float PR = pr_i - rho_i * (I.g[0] * rx + I.g[1] * ry + I.g[2] * rz);
-      const float rho_bar = 0.5f * (rho_i + I.rho0 + PR / I.c0sq);
-      const float dU = 2.0f * UL;
-      const float beta = fminf(kLimiter * fmaxf(dU, 0.0f) / I.c0, 1.0f);
-      const float Pstar = 0.5f * (pr_i + PR) + 0.5f * rho_bar * I.c0 * beta * dU;
-      const float f = i2f(pw.w) * Pstar * fw;         // V_w P* (dW/dr)/r
-      kahan_add(ax, cx, f * rx);
-      kahan_add(ay, cy, f * ry);
-      if (D == 3) kahan_add(az, cz, f * rz);
-    }
-    // dv/dt = acc_prior + g - 2/rho_i sum V_j P* grad_i W_ij
-    const float s = -2.0f / rho_i;
-    float4 ap = acc_prior ? acc_prior[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float a0 = ap.x + I.g[0] + s * (ax - cx);
-    float a1 = ap.y + I.g[1] + s * (ay - cy);
-    float a2 = D == 3 ? ap.z + I.g[2] + s * (az - cz) : 0.f;
-    float4 vn = make_float4(vi.x + dt * a0, vi.y + dt * a1, vi.z + dt * a2, vi.w);  // verlet-first-mediate
-    // Eq. verlet-first-half (position), fixed point
-    int qx = pi.x + __float2int_rn(hdt * vi.x * I.inv_dq);
-    int qy = pi.y + __float2int_rn(hdt * vi.y * I.inv_dq);
-    int qz = D == 3 ? pi.z + __float2int_rn(hdt * vi.z * I.inv_dq) : 0;
-    qx = wrap_coord(qx, I.period[0]);
-    qy = wrap_coord(qy, I.period[1]);
-    if (D == 3) qz = wrap_coord(qz, I.period[2]);
-    PH[i] = make_int4(qx, qy, qz, f2i(dev_i));
-    VH[i] = vn;
-    if (acc_keep) acc_keep[i] = make_float4(a0, a1, a2, 0.f);
-    v2 = vn.x * vn.x + vn.y * vn.y + vn.z * vn.z;
-    if (!isfinite(v2)) raise_error(g, ERR_NAN, i);
-  }
-  reduce_vmax(v2, valid, k, uni, ctrl);
-}
-
-template <int D>
-__global__ void __launch_bounds__(kBlock)
-k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __restrict__ VH,
-                     int4* __restrict__ PS, float4* __restrict__ VS,
-                     const float* __restrict__ mass, const int* __restrict__ inst_of,
-                     const Inst* __restrict__ inst, const Ctrl* __restrict__ ctrl,
-                     const int* __restrict__ nbr, const uint32_t* __restrict__ nbc,
-                     const int4* __restrict__ WP, const float4* __restrict__ WN, Global* g) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int k = inst_index(inst_of, i);
-  const double dtd = ctrl[k].dt;
-  if (dtd == 0.0) return;
-  const Inst& I = inst[k];
-  const float hdt = 0.5f * (float)dtd;
-  const int4 pi = PH[i];
-  const float4 vi = VH[i];                            // v^{n+1}
-  const float dev_i = i2f(pi.w);
-  const float rho_i = I.rho0 + dev_i;
-  float s = 0.f, comp = 0.f;
-  const uint32_t cnt = nbc[i];
-  const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
-  for (int kk = 0; kk < nf; ++kk) {
-    const int j = nbr[(int64_t)kk * n + i];
-    const int4 pj = PH[j];
-    const float4 vj = VH[j];
-    // r_ij^{n+1} = r_ij^{n+1/2} + dt/2 (v_i - v_j)^{n+1}
-    float rx = fmaf(hdt, vi.x - vj.x, (float)wrap_diff(pi.x - pj.x, I.period[0]) * I.dq);
-    float ry = fmaf(hdt, vi.y - vj.y, (float)wrap_diff(pi.y - pj.y, I.period[1]) * I.dq);
-    float rz = D == 3 ? fmaf(hdt, vi.z - vj.z, (float)wrap_diff(pi.z - pj.z, I.period[2]) * I.dq) : 0.f;
-    float r2 = rx * rx + ry * ry + rz * rz;
-    if (!(r2 < I.four_h2) || r2 == 0.0f) continue;
-    const float inv_r = rsqrtf(r2);
-    const float r = r2 * inv_r;
-    const float dW = kernel_dW_over_r(r, I) * r;
-    const float dev_j = i2f(pj.w);
-    const float rho_j = I.rho0 + dev_j;
-    const float UL = -(vi.x * rx + vi.y * ry + vi.z * rz) * inv_r;
-    const float UR = -(vj.x * rx + vj.y * ry + vj.z * rz) * inv_r;
-    const float rho_bar = 0.5f * (rho_i + rho_j);
-    // U* - U_L = (U_R - U_L)/2 + (P_L - P_R)/(2 rho_bar c0), P_L - P_R = c0^2 (dev_i - dev_j)
-    const float dUs = 0.5f * (UR - UL) + I.c0 * (dev_i - dev_j) / (2.0f * rho_bar);
-    const float mj = mass ? mass[j] : I.mass;
-    kahan_add(s, comp, mj / rho_j * dUs * dW);
-  }
-  for (int kk = 0; kk < nw; ++kk) {
-    const int w = nbr[(int64_t)(nf + kk) * n + i];
-    const int4 pw = WP[w];
-    const float4 nwv = WN[w];
-    float rx = fmaf(hdt, vi.x, (float)wrap_diff(pi.x - pw.x, I.period[0]) * I.dq);
-    float ry = fmaf(hdt, vi.y, (float)wrap_diff(pi.y - pw.y, I.period[1]) * I.dq);
-    float rz = D == 3 ? fmaf(hdt, vi.z, (float)wrap_diff(pi.z - pw.z, I.period[2]) * I.dq) : 0.f;
-    float r2 = rx * rx + ry * ry + rz * rz;
-    if (!(r2 < I.four_h2) || r2 == 0.0f) continue;
-    const float inv_r = rsqrtf(r2);
-    const float r = r2 * inv_r;
-    const float dW = kernel_dW_over_r(r, I) * r;
-    const float UL = -(nwv.x * vi.x + nwv.y * vi.y + nwv.z * vi.z);
-    const float gr = I.g[0] * rx + I.g[1] * ry + I.g[2] * rz;
-    const float PR = I.c0sq * dev_i - rho_i * gr;
-    const float rho_bar = 0.5f * (rho_i + I.rho0 + PR / I.c0sq);
-    // U_R = -U_L so the mean is 0; P_L - P_R = rho_i g.r_iw
-    const float Us = rho_i * gr / (2.0f * rho_bar * I.c0);
-    kahan_add(s, comp, i2f(pw.w) * (Us - UL) * dW);
-  }
-  const float drho = 2.0f * rho_i * (s - comp);
-  const float dev_n = dev_i + hdt * drho;             // Eq. verlet-first-final (density)
-  int qx = pi.x + __float2int_rn(hdt * vi.x * I.inv_dq);
-  int qy = pi.y + __float2int_rn(hdt * vi.y * I.inv_dq);
-  int qz = D == 3 ? pi.z + __float2int_rn(hdt * vi.z * I.inv_dq) : 0;
-  qx = wrap_coord(qx, I.period[0]);
-  qy = wrap_coord(qy, I.period[1]);
-  if (D == 3) qz = wrap_coord(qz, I.period[2]);
-  if (!isfinite(dev_n)) raise_error(g, ERR_NAN, i);
-  PS[i] = make_int4(qx, qy, qz, f2i(dev_n));
-  VS[i] = make_float4(vi.x, vi.y, vi.z, drho);
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------- launchers -----------
@@ -623,21 +437,6 @@ void launch_viscous(const Buffers& b, cudaStream_t s, int64_t* launches) {
 void launch_dt_acoustic(const Buffers& b, cudaStream_t s, cudaGraphConditionalHandle cond,
                         bool use_cond, int64_t* launches) {
   k_dt_acoustic<<<1, 256, 0, s>>>(b.n_inst, b.inst, b.ctrl, b.glob, cond, use_cond ? 1 : 0);
-  ++*launches;
-}
-
-void launch_pressure_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches) {
-  if (b.n == 0) return;
-  SPH_DIM_LAUNCH(b, k_pressure_relaxation, grid_for(b.n), kBlock, s, b.n, b.PS, b.VS, b.PH, b.VH,
-                 b.mass, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, b.WP, b.WN, b.acc_prior,
-                 b.acc_keep, b.glob);
-  ++*launches;
-}
-
-void launch_density_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches) {
-  if (b.n == 0) return;
-  SPH_DIM_LAUNCH(b, k_density_relaxation, grid_for(b.n), kBlock, s, b.n, b.PH, b.VH, b.PS, b.VS,
-                 b.mass, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, b.WP, b.WN, b.glob);
   ++*launches;
 }
 

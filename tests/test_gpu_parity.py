@@ -113,6 +113,7 @@ def test_density_summation(sph, case):
     st, w = o.state_from_problem(prob)
     nb = o.neighbour_sets_quantised(st.x, w.x, prm)
     rho_or = o.density_summation(st, w, nb, prm)
+    print(f"{case}: density rel L2 {rel_l2(rho_gpu, rho_or):.2e} max abs {np.max(np.abs(rho_gpu - rho_or)):.2e}")
     assert rel_l2(rho_gpu, rho_or) < REL_L2_TOL
     # the deviation rho - rho0 itself is accurate to FP32 rounding of W terms
     assert np.max(np.abs(rho_gpu - rho_or)) < 2e-6 * prm.rho0
@@ -175,6 +176,8 @@ def test_one_substep_matches_oracle(sph, case):
     assert abs(dt_gpu - dt) < 1e-6 * dt
     half, dvdt = o.pressure_relaxation(st, w, nb, acc_prior, dt, prm)
     out = o.density_relaxation(half, w, nb, dt, prm)
+    print(f"{case}: rel L2 dv/dt {rel_l2(acc_gpu, dvdt):.2e} v {rel_l2(vel_gpu, out.v):.2e} "
+          f"rho {rel_l2(rho_gpu, out.rho):.2e}")
     assert rel_l2(acc_gpu, dvdt) < REL_L2_TOL, rel_l2(acc_gpu, dvdt)
     assert rel_l2(vel_gpu, out.v) < REL_L2_TOL
     assert rel_l2(rho_gpu, out.rho) < REL_L2_TOL
@@ -280,10 +283,12 @@ def test_dam_break_2d_trajectory_energy_and_front(sph):
     E0 = ge[0]
     mask = ts <= gt[-1]
     err_e = np.max(np.abs(np.array(es)[mask] - _interp(ts[mask], gt, ge))) / abs(E0)
+    print(f"dam break 2D: energy err {err_e:.2e} of E0")
     assert err_e < 5e-3, err_e
     L = prob.meta["L"]
     pre = ts[mask] < gold["t_impact"]
     err_f = np.max(np.abs(np.array(fs)[mask][pre] - _interp(ts[mask][pre], gt, gf))) / L
+    print(f"dam break 2D: front err before impact {err_f:.2e} of L")
     assert err_f < 5e-3, err_f
 
 
@@ -415,5 +420,7 @@ def test_full_size_3d_first_substep_sampled(sph):
     # the oracle's own summed densities feed its substep: only pairs whose 1-hop
     # neighbourhood is complete are compared
     half, dvdt = o.pressure_relaxation(st, w, nb, 0.0, dt, sprm)
+    print(f"8M sampled: rho {rel_l2(rho_mid[samples], st.rho[local]):.2e} "
+          f"dv/dt {rel_l2(acc_gpu[samples], dvdt[local]):.2e} v {rel_l2(vel_gpu[samples], half.v[local]):.2e}")
     assert rel_l2(acc_gpu[samples], dvdt[local]) < 1e-4
     assert rel_l2(vel_gpu[samples], half.v[local]) < REL_L2_TOL
