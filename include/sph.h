@@ -133,7 +133,8 @@ int sph_create(const sph_params* params, int32_t n_instances,
 
 void sph_destroy(sph_handle* h);
 
-/* Message of the last failure on this handle ("" if none). */
+/* Message of the last failure on this handle ("" if none); with h = NULL, the
+ * message of this thread's last failed sph_diagnostics_noalloc call. */
 const char* sph_last_error(const sph_handle* h);
 
 int sph_get_info(const sph_handle* h, sph_info* out);
@@ -212,6 +213,25 @@ int sph_kernel_launches(sph_handle* h, int64_t* out);
  * relaxation. */
 int sph_set_kernel_timing(sph_handle* h, int32_t enable);
 int sph_kernel_times(sph_handle* h, double* ms, int64_t* launches);
+
+/* Allocation-free diagnostics. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory (code running inside
+ * another framework's device memory pool or under a fixed device-memory budget,
+ * and hosts that forbid runtime allocation after start-up), for whom creating a
+ * handle is not an option. It computes the same FP64 fields as sph_diagnostics
+ * (t, dt_ad and the step counters are 0) from the caller's arrays in caller order:
+ * pos, vel [n*dim], rho, mass [n], all double and all in DEVICE memory; p supplies
+ * dim, rho0, c0 and gravity. out is a host struct; the call synchronises stream.
+ * It calls no cudaMalloc, cudaFree or allocating library routine. Its scratch is
+ * a fixed 131,200-byte array in the library's device image (1024 blocks of 16
+ * partial sums plus the result row), which every GPU that loads the library holds
+ * until exit. The first call on each device looks up that array's address with the
+ * device current; make that first call before any stream capture begins. Calls
+ * share the array and overwrite all of it that they read, so calls that overlap on
+ * the GPU race. n above 2^31 - 1, dim not 2 or 3, host pointers or a missing array
+ * return SPH_E_INVALID with a message in sph_last_error(NULL). */
+int sph_diagnostics_noalloc(const sph_params* p, int64_t n, const double* pos, const double* vel,
+                            const double* rho, const double* mass, sph_diag* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -10,6 +10,8 @@
 #include "sph.h"
 #include "sph_kernels.h"
 
+const char* sph_noalloc_last_error();   // message of the last failed handle-less call (sph_noalloc.cu)
+
 using sph::Buffers;
 using sph::Ctrl;
 using sph::Global;
@@ -332,7 +334,7 @@ extern "C" {
 
 int sph_params_check(const sph_params* p) { return check_params(p, nullptr); }
 
-const char* sph_last_error(const sph_handle* h) { return h ? h->err.c_str() : "null handle"; }
+const char* sph_last_error(const sph_handle* h) { return h ? h->err.c_str() : sph_noalloc_last_error(); }
 
 void sph_destroy(sph_handle* h) {
   if (!h) return;

@@ -32,7 +32,7 @@ EXPORTS = [
     "sph_build_cells", "sph_advection_step", "sph_acoustic_substep", "sph_step",
     "sph_diagnostics", "sph_get_state", "sph_set_state", "sph_get_acceleration",
     "sph_get_permutation", "sph_get_neighbours", "sph_pair_count", "sph_kernel_launches",
-    "sph_set_kernel_timing", "sph_kernel_times",
+    "sph_set_kernel_timing", "sph_kernel_times", "sph_diagnostics_noalloc",
 ]
 
 
@@ -117,6 +117,8 @@ def load():
         "sph_kernel_launches": (i32, [P, ctypes.POINTER(i64)]),
         "sph_set_kernel_timing": (i32, [P, i32]),
         "sph_kernel_times": (i32, [P, ctypes.POINTER(dbl), ctypes.POINTER(i64)]),
+        "sph_diagnostics_noalloc": (i32, [ctypes.POINTER(SphParams), i64, P, P, P, P,
+                                          ctypes.POINTER(SphDiag), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -322,6 +324,20 @@ def sph_kernel_times(h):
     cnt = (ctypes.c_int64 * 2)()
     check(lib, h, lib.sph_kernel_times(h, ms, cnt))
     return list(ms), list(cnt)
+
+
+def sph_diagnostics_noalloc(params: SphParams, pos, vel, rho, mass, stream=None):
+    """FP64 diagnostics of caller-owned DEVICE arrays (torch CUDA float64 tensors, caller
+    order) without any device allocation by the library. Returns a dict like
+    sph_diagnostics."""
+    lib = load()
+    out = SphDiag()
+    n = int(rho.shape[0])
+    code = lib.sph_diagnostics_noalloc(ctypes.byref(params), n, _ptr(pos), _ptr(vel), _ptr(rho),
+                                       _ptr(mass), ctypes.byref(out), _stream(stream))
+    if code != SPH_OK:
+        raise SphError(code, lib.sph_last_error(None).decode())
+    return out.as_dict()
 
 
 # ------------------------------------------------------------------------------ convenience
