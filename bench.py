@@ -33,16 +33,19 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-substeps/s, 3D dam break"
 UNIT = "particle-substeps/s"
 
-# DRAM traffic of the pressure-relaxation kernel per fluid particle, from the ncu
-# capture summarised in profiles/ (None until captured). Valid only for the kernel
-# sources whose hash is recorded with it.
-TRAFFIC_BYTES_PER_PARTICLE = None
-TRAFFIC_SOURCE_HASH = None
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pressure-relaxation
+# launch per fluid particle, from the ncu capture of the 3D dam break at dp = 1/80
+# (1,024,000 particles, neighbour table 0.5 GB > L2) summarised in
+# profiles/pressure_relaxation_dam_break_3d.md; it is scaled to the benchmark's particle
+# count (the traffic is per particle: state records plus its neighbour row). Valid only
+# for the kernel sources whose hash is recorded with it.
+TRAFFIC_BYTES_PER_PARTICLE = 389.54
+TRAFFIC_SOURCE_HASH = "dcc5d2380bd3ce82"
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sph_common.cuh", "sph_physics.cu"):
+    for f in ("sph_common.cuh", "sph_relax.cu"):
         with open(os.path.join(ROOT, "paper_2010_12375_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -111,7 +114,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ CPU legs
-CPU_SAMPLE_N = 16      # 3D dam break at dp = 1/16: 8,192 fluid particles
+CPU_SAMPLE_N = 20      # 3D dam break at dp = 1/20: 16,000 fluid particles
 
 
 def cpu_sample_workload():
@@ -135,8 +138,9 @@ def oracle_steps(n_steps, problem=None):
 
 
 def cpu_sample_text(steps):
-    return (f"3D dam break at dp = 1/{CPU_SAMPLE_N} (8,192 fluid + walls, same physics as the "
-            f"GPU workload), {steps} advection step(s) of the FP64 numpy oracle on one core")
+    return (f"3D dam break at dp = 1/{CPU_SAMPLE_N} ({2 * CPU_SAMPLE_N ** 3:,} fluid + walls, same "
+            f"physics as the GPU workload), {steps} advection step(s) of the FP64 numpy oracle "
+            f"on one core")
 
 
 def run_reference(args, rank, world):
@@ -145,10 +149,9 @@ def run_reference(args, rank, world):
         return
     for _ in range(args.warmup):
         oracle_steps(1)
-    rates, secs, subs = [], 0.0, 0
+    secs, subs = 0.0, 0
     for _ in range(args.steps):
-        r, s, k = oracle_steps(1)
-        rates.append(r)
+        _, s, k = oracle_steps(1)
         secs += s
         subs += k
     value = CPU_SAMPLE_N ** 3 * 2 * subs / secs
@@ -311,7 +314,7 @@ def main():
     ap.add_argument("--n", type=int, default=159, help="3D dam break resolution: dp = 1/n, 2n^3 fluid")
     ap.add_argument("--graph", action="store_true", help="time the CUDA-graph loop instead")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

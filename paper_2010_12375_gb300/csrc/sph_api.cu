@@ -389,6 +389,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
   b.n_inst = n_instances;
   b.dim = dim;
   b.cap = params[0].capacity > 0 ? params[0].capacity : (dim == 2 ? 48 : 128);
+  b.cap = (b.cap + 3) & ~3;                  // whole quads of neighbour slots
   int64_t n_cells = 0;
   bool any_visc = false;
   for (int k = 0; k < n_instances; ++k) {

@@ -174,3 +174,15 @@ __device__ __forceinline__ float biased_diff(int qi, int qj, int period) {
 }
 
 }  // namespace sph
+
+// ---- neighbour table layout ---------------------------------------------------------------
+// Slot s of particle i lives at int index ((s >> 2) * n + i) * 4 + (s & 3): quads of four
+// slots are interleaved over particles, so a warp reads one quad row as 32 contiguous
+// 16-byte loads. Fluid neighbours occupy slots [0, nf); wall neighbours start at the next
+// quad boundary, wall_slot0(nf) = 4 ceil(nf / 4).
+namespace sph {
+__device__ __forceinline__ int64_t slot_index(int64_t n, int64_t i, int s) {
+  return ((int64_t)(s >> 2) * n + i) * 4 + (s & 3);
+}
+__device__ __forceinline__ int wall_slot0(int nf) { return (nf + 3) & ~3; }
+}  // namespace sph

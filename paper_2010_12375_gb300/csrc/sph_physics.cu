@@ -176,8 +176,9 @@ __global__ void k_export_neighbours(int64_t n, int cap, const int* __restrict__ 
   int64_t row = id[i];
   fc[row] = nf;
   wc[row] = nw;
-  for (int k = 0; k < nf; ++k) fids[row * stride + k] = id[nbr[(int64_t)k * n + i]];
-  for (int k = 0; k < nw; ++k) wids[row * stride + k] = wid[nbr[(int64_t)(nf + k) * n + i]];
+  for (int k = 0; k < nf; ++k) fids[row * stride + k] = id[nbr[slot_index(n, i, k)]];
+  const int w0 = wall_slot0(nf);
+  for (int k = 0; k < nw; ++k) wids[row * stride + k] = wid[nbr[slot_index(n, i, w0 + k)]];
 }
 
 __global__ void k_pair_count(int64_t n, const uint32_t* __restrict__ nbc, unsigned long long* out) {
@@ -280,7 +281,31 @@ __global__ void k_dt_acoustic(int n_inst, const Inst* __restrict__ inst, Ctrl* c
 }
 
 // ---------------------------------------------------------------- density -------------
-template <int D>
+// W of two pairs at once from their packed squared distances; lanes with mask 0 add 0.
+__device__ __forceinline__ float2 kernel_W2(float2 r2, float inv_h, float w_a) {
+  const float2 q = mul2(mul2(r2, rsqrt2(fma2(r2, f2(1.0f), f2(1e-30f)))), f2(inv_h));
+  const float2 t = max2(fma2(q, f2(-0.5f), f2(1.0f)), 0.0f);
+  const float2 t2 = mul2(t, t);
+  return mul2(mul2(f2(w_a), mul2(t2, t2)), fma2(q, f2(2.0f), f2(1.0f)));
+}
+
+template <int D, bool PER>
+__device__ __forceinline__ float2 pair_r2(const int4& p, const int4& a, const int4& b, const Inst& I) {
+  const float2 M = f2(-kMagic), DQ = f2(I.dq);
+  const float2 dx = mul2(add2(make_float2(biased_diff<PER>(p.x, a.x, I.period[0]), biased_diff<PER>(p.x, b.x, I.period[0])), M), DQ);
+  const float2 dy = mul2(add2(make_float2(biased_diff<PER>(p.y, a.y, I.period[1]), biased_diff<PER>(p.y, b.y, I.period[1])), M), DQ);
+  float2 r2 = fma2(dx, dx, mul2(dy, dy));
+  if (D == 3) {
+    const float2 dz = mul2(add2(make_float2(biased_diff<PER>(p.z, a.z, I.period[2]), biased_diff<PER>(p.z, b.z, I.period[2])), M), DQ);
+    r2 = fma2(dz, dz, r2);
+  }
+  return r2;
+}
+
+// Eq. eqrhosum / Eq. eqrhosumnosurface: rho = rho0 sum W / sum W0 (with max(rho*, .) for a
+// free surface), sum over self, fluid and wall neighbours. The Kahan sum starts from
+// W(0) - sumW0 so it holds the deviation rho/rho0 - 1 with its own relative precision.
+template <int D, bool PER>
 __global__ void __launch_bounds__(kBlock)
 k_density(int64_t n, int4* P, const int* __restrict__ inst_of, const Inst* __restrict__ inst,
           const int* __restrict__ nbr, const uint32_t* __restrict__ nbc, const int4* __restrict__ WP) {
@@ -288,34 +313,34 @@ k_density(int64_t n, int4* P, const int* __restrict__ inst_of, const Inst* __res
   if (i >= n) return;
   const Inst& I = inst[inst_index(inst_of, i)];
   const int4 pi = P[i];
-  uint32_t c = nbc[i];
-  int nf = (int)(c & 0xffffu), nw = (int)(c >> 16);
-  // sum W - sumW0, started from W(0) - sumW0 so the deviation keeps its precision
-  float s = I.sig_hi, comp = 0.0f;
-  kahan_add(s, comp, I.sig_lo);
-  for (int k = 0; k < nf; ++k) {
-    const int4 pj = P[nbr[(int64_t)k * n + i]];
-    float dx = (float)wrap_diff(pi.x - pj.x, I.period[0]) * I.dq;
-    float dy = (float)wrap_diff(pi.y - pj.y, I.period[1]) * I.dq;
-    float r2 = dx * dx + dy * dy;
-    if (D == 3) {
-      float dz = (float)wrap_diff(pi.z - pj.z, I.period[2]) * I.dq;
-      r2 += dz * dz;
-    }
-    if (r2 < I.four_h2) kahan_add(s, comp, kernel_W(sqrtf(r2), I));
+  const uint32_t c = nbc[i];
+  const int nf = (int)(c & 0xffffu), nw = (int)(c >> 16);
+  float2 s = make_float2(I.sig_hi, 0.0f), nc = f2(0.0f);
+  kahan2(s, nc, make_float2(I.sig_lo, 0.0f), f2(1.0f));
+  const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
+  const int nq = (nf + 3) >> 2;
+  for (int q = 0; q < nq; ++q) {
+    const int4 cq = nb4[(int64_t)q * n + i];
+    const int sl = q << 2;
+    const int j1 = sl + 1 < nf ? cq.y : cq.x, j2 = sl + 2 < nf ? cq.z : cq.x, j3 = sl + 3 < nf ? cq.w : cq.x;
+    const int4 a0 = P[cq.x], a1 = P[j1], a2 = P[j2], a3 = P[j3];
+    const float2 m01 = make_float2(1.0f, sl + 1 < nf ? 1.0f : 0.0f);
+    const float2 m23 = make_float2(sl + 2 < nf ? 1.0f : 0.0f, sl + 3 < nf ? 1.0f : 0.0f);
+    kahan2(s, nc, kernel_W2(pair_r2<D, PER>(pi, a0, a1, I), I.inv_h, I.w_a), m01);
+    kahan2(s, nc, kernel_W2(pair_r2<D, PER>(pi, a2, a3, I), I.inv_h, I.w_a), m23);
   }
-  for (int k = 0; k < nw; ++k) {
-    const int4 pw = WP[nbr[(int64_t)(nf + k) * n + i]];
-    float dx = (float)wrap_diff(pi.x - pw.x, I.period[0]) * I.dq;
-    float dy = (float)wrap_diff(pi.y - pw.y, I.period[1]) * I.dq;
-    float r2 = dx * dx + dy * dy;
-    if (D == 3) {
-      float dz = (float)wrap_diff(pi.z - pw.z, I.period[2]) * I.dq;
-      r2 += dz * dz;
-    }
-    if (r2 < I.four_h2) kahan_add(s, comp, kernel_W(sqrtf(r2), I));
+  const int q0 = wall_slot0(nf) >> 2, nwq = (nw + 3) >> 2;
+  for (int q = 0; q < nwq; ++q) {
+    const int4 cq = nb4[(int64_t)(q0 + q) * n + i];
+    const int sl = q << 2;
+    const int w1 = sl + 1 < nw ? cq.y : cq.x, w2 = sl + 2 < nw ? cq.z : cq.x, w3 = sl + 3 < nw ? cq.w : cq.x;
+    const int4 a0 = WP[cq.x], a1 = WP[w1], a2 = WP[w2], a3 = WP[w3];
+    const float2 m01 = make_float2(1.0f, sl + 1 < nw ? 1.0f : 0.0f);
+    const float2 m23 = make_float2(sl + 2 < nw ? 1.0f : 0.0f, sl + 3 < nw ? 1.0f : 0.0f);
+    kahan2(s, nc, kernel_W2(pair_r2<D, PER>(pi, a0, a1, I), I.inv_h, I.w_a), m01);
+    kahan2(s, nc, kernel_W2(pair_r2<D, PER>(pi, a2, a3, I), I.inv_h, I.w_a), m23);
   }
-  float dev = I.rho0_over_sigma0 * (s - comp);       // rho0 sumW/sumW0 - rho0
+  float dev = I.rho0_over_sigma0 * ((s.x + nc.x) + (s.y + nc.y));   // rho0 sumW/sumW0 - rho0
   if (I.free_surface) dev = fmaxf(i2f(pi.w), dev);
   reinterpret_cast<int*>(P + i)[3] = f2i(dev);        // only .w changes; others read .xyz
 }
@@ -336,7 +361,7 @@ k_viscous(int64_t n, const int4* __restrict__ P, const float4* __restrict__ V,
   float ax = 0.f, ay = 0.f, az = 0.f;
   if (I.eta > 0.0f) {
     for (int k = 0; k < nf; ++k) {
-      int j = nbr[(int64_t)k * n + i];
+      int j = nbr[slot_index(n, i, k)];
       const int4 pj = P[j];
       const float4 vj = V[j];
       float dx = (float)wrap_diff(pi.x - pj.x, I.period[0]) * I.dq;
@@ -422,8 +447,9 @@ void launch_dt_advection(const Buffers& b, cudaStream_t s, int64_t* launches) {
 
 void launch_density(const Buffers& b, cudaStream_t s, int64_t* launches) {
   if (b.n == 0) return;
-  SPH_DIM_LAUNCH(b, k_density, grid_for(b.n), kBlock, s, b.n, b.PS, b.inst_of, b.inst, b.nbr, b.nbc,
-                 b.WP);
+  auto kern = b.dim == 2 ? (b.any_periodic ? k_density<2, true> : k_density<2, false>)
+                         : (b.any_periodic ? k_density<3, true> : k_density<3, false>);
+  kern<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.nbr, b.nbc, b.WP);
   ++*launches;
 }
 

@@ -12,10 +12,12 @@
 // U_L = v_i.e_ij, U_R = v_j.e_ij, U* = (U_L+U_R)/2 + (P_L-P_R)/(2 rho_bar c0),
 // P* = (P_L+P_R)/2 + rho_bar c0 beta (U_L-U_R)/2, beta = min(3 max(U_L-U_R,0)/c0, 1).
 //
-// One thread per fluid particle walks its frozen neighbour row two entries at a
-// time: the two pairs occupy the .x and .y lanes of packed FP32 instructions
-// (__ffma2_rn and friends), which halves the instruction count of the pair
-// arithmetic. An odd row is padded with the particle itself, a pair at zero
+// One thread per fluid particle walks its frozen neighbour row one quad (four
+// slots, one 16-byte load, the next quad already in flight) at a time; the eight
+// neighbour records of a quad are gathered together and evaluated as two packed
+// pairs in the .x and .y lanes of sm_100 packed FP32 instructions (__ffma2_rn and
+// friends), which halves the instruction count of the pair arithmetic. Unused
+// slots of the last quad are padded with the particle itself, a pair at zero
 // distance whose contribution is exactly zero. Pairs that drifted past 2h get
 // t = max(1 - q/2, 0) = 0 and contribute nothing, with no branch. Sums are
 // Kahan-compensated per lane and the two lanes are added at the end.
@@ -83,6 +85,75 @@ __device__ __forceinline__ Geo2 geometry2(float2 rx, float2 ry, float2 rz, float
   return g;
 }
 
+// Exactly converted, packed pair vector: dq (q_i - q_j) + add, lanes (a, b).
+template <bool PER>
+__device__ __forceinline__ float2 pair_axis(int qi, int qa, int qb, int period, float2 DQ, float2 add) {
+  return fma2(add2(make_float2(biased_diff<PER>(qi, qa, period), biased_diff<PER>(qi, qb, period)),
+                   f2(-kMagic)),
+              DQ, add);
+}
+
+// Shared per-particle context of the pressure relaxation.
+struct PrCtx {
+  float hdt, inv_h, dwr, rho0, c0sq, kc, qc0, dev_i, rho_i, pr_i;
+  int px, py, pz;
+  float2 sx, sy, sz, nx, ny, nz;      // Kahan sums (per lane) and negated compensations
+};
+
+// Two fluid pairs (a, b) of the pressure relaxation: V_j P* (dW/dr)/r r_ij accumulated.
+template <int D, bool PER>
+__device__ __forceinline__ void pr_fluid2(PrCtx& C, const int4& pi, const float4& vi, const int4& pa,
+                                          const int4& pb, const float4& va, const float4& vb, float2 mj,
+                                          float2 DQ) {
+  const float2 HDT = f2(C.hdt);
+  const float2 rx = pair_axis<PER>(pi.x, pa.x, pb.x, C.px, DQ, mul2(HDT, sub2(f2(vi.x), make_float2(va.x, vb.x))));
+  const float2 ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(HDT, sub2(f2(vi.y), make_float2(va.y, vb.y))));
+  float2 rz = f2(0.f);
+  if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(HDT, sub2(f2(vi.z), make_float2(va.z, vb.z))));
+  const Geo2 G = geometry2(rx, ry, rz, C.inv_h, C.dwr);
+  const float2 dev_j = fma2(HDT, make_float2(va.w, vb.w), make_float2(i2f(pa.w), i2f(pb.w)));
+  const float2 rho_j = add2(f2(C.rho0), dev_j);
+  // U_L - U_R = (v_j - v_i).r_ij / |r_ij|
+  const float2 dvx = sub2(make_float2(va.x, vb.x), f2(vi.x));
+  const float2 dvy = sub2(make_float2(va.y, vb.y), f2(vi.y));
+  const float2 dvz = sub2(make_float2(va.z, vb.z), f2(vi.z));
+  const float2 dU = mul2(fma2(dvx, rx, fma2(dvy, ry, mul2(dvz, rz))), G.inv_r);
+  const float2 beta = min2(mul2(f2(C.kc), max2(dU, 0.0f)), 1.0f);
+  // P* = (p_i + p_j)/2 + (c0/4)(rho_i + rho_j) beta (U_L - U_R)
+  const float2 pbar = mul2(f2(0.5f * C.c0sq), add2(f2(C.dev_i), dev_j));
+  const float2 pstar = fma2(mul2(f2(C.qc0), add2(f2(C.rho_i), rho_j)), mul2(beta, dU), pbar);
+  const float2 f = mul2(mul2(mul2(mj, rcp2(rho_j)), pstar), G.fw);       // V_j P* (dW/dr)/r
+  kahan2(C.sx, C.nx, f, rx);
+  kahan2(C.sy, C.ny, f, ry);
+  if (D == 3) kahan2(C.sz, C.nz, f, rz);
+}
+
+// Two wall pairs of the pressure relaxation (one-sided problem along the wall normal).
+template <int D, bool PER>
+__device__ __forceinline__ void pr_wall2(PrCtx& C, const int4& pi, const float4& vi, const int4& qa,
+                                         const int4& qb, const float4& na, const float4& nb, float2 Vw,
+                                         float2 DQ, float g0, float g1, float g2, float inv_c0sq) {
+  const float2 rx = pair_axis<PER>(pi.x, qa.x, qb.x, C.px, DQ, f2(C.hdt * vi.x));
+  const float2 ry = pair_axis<PER>(pi.y, qa.y, qb.y, C.py, DQ, f2(C.hdt * vi.y));
+  float2 rz = f2(0.f);
+  if (D == 3) rz = pair_axis<PER>(pi.z, qa.z, qb.z, C.pz, DQ, f2(C.hdt * vi.z));
+  const Geo2 G = geometry2(rx, ry, rz, C.inv_h, C.dwr);
+  // U_L = -n.v_i, U_R = -U_L, P_R = P_L + rho_i g.(r_w - r_i), rho_R from the EoS
+  const float2 UL = mul2(f2(-1.0f), fma2(make_float2(na.x, nb.x), f2(vi.x),
+                                         fma2(make_float2(na.y, nb.y), f2(vi.y), mul2(make_float2(na.z, nb.z), f2(vi.z)))));
+  const float2 gr = fma2(f2(g0), rx, fma2(f2(g1), ry, mul2(f2(g2), rz)));
+  const float2 PR = fma2(f2(-C.rho_i), gr, f2(C.pr_i));
+  const float2 rhoR = fma2(PR, f2(inv_c0sq), f2(C.rho0));
+  const float2 dU = add2(UL, UL);
+  const float2 beta = min2(mul2(f2(C.kc), max2(dU, 0.0f)), 1.0f);
+  const float2 pstar = fma2(mul2(f2(C.qc0), add2(f2(C.rho_i), rhoR)), mul2(beta, dU),
+                            mul2(f2(0.5f), add2(f2(C.pr_i), PR)));
+  const float2 f = mul2(mul2(Vw, pstar), G.fw);
+  kahan2(C.sx, C.nx, f, rx);
+  kahan2(C.sy, C.ny, f, ry);
+  if (D == 3) kahan2(C.sz, C.nz, f, rz);
+}
+
 // ---------------------------------------------------------------- pressure relaxation --
 template <int D, bool PER>
 __global__ void __launch_bounds__(kBlock, 2)
@@ -103,108 +174,85 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
   float v2 = 0.0f;
   if (valid) {
     const Inst& I = inst[k];
-    const float dt = (float)dtd, hdt = 0.5f * dt;
-    const float dq = I.dq, inv_h = I.inv_h, dwr = I.dwr_a, rho0 = I.rho0, c0sq = I.c0sq;
-    const float c0 = I.c0, kc = kLimiter / c0, qc0 = 0.25f * c0;
-    const int px = PER ? I.period[0] : 0, py = PER ? I.period[1] : 0, pz = PER ? I.period[2] : 0;
+    const float dt = (float)dtd;
+    PrCtx C;
+    C.hdt = 0.5f * dt;
+    C.inv_h = I.inv_h;
+    C.dwr = I.dwr_a;
+    C.rho0 = I.rho0;
+    C.c0sq = I.c0sq;
+    C.kc = kLimiter / I.c0;
+    C.qc0 = 0.25f * I.c0;
+    C.px = PER ? I.period[0] : 0;
+    C.py = PER ? I.period[1] : 0;
+    C.pz = PER ? I.period[2] : 0;
+    C.sx = C.sy = C.sz = C.nx = C.ny = C.nz = f2(0.f);
     const int4 pi = PS[i];
     const float4 vi = VS[i];
-    const float dev_i = i2f(pi.w) + hdt * vi.w;       // Eq. verlet-first-half (density)
-    const float rho_i = rho0 + dev_i;
-    const float pr_i = c0sq * dev_i;                  // Eq. eqeos
-    const float2 HDT = f2(hdt), DQ = f2(dq), MAG = f2(-kMagic);
-    const float2 VIX = f2(vi.x), VIY = f2(vi.y), VIZ = f2(vi.z);
-    float2 sx = f2(0.f), sy = f2(0.f), sz = f2(0.f), nx = f2(0.f), ny = f2(0.f), nz = f2(0.f);
+    C.dev_i = i2f(pi.w) + C.hdt * vi.w;               // Eq. verlet-first-half (density)
+    C.rho_i = C.rho0 + C.dev_i;
+    C.pr_i = C.c0sq * C.dev_i;                        // Eq. eqeos
+    const float2 DQ = f2(I.dq);
     const uint32_t cnt = nbc[i];
     const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
-    const float mi = mass ? 0.0f : I.mass;
-    for (int kk = 0; kk < nf; kk += 2) {
-      const int ja = nbr[(int64_t)kk * n + i];
-      const int jb = kk + 1 < nf ? nbr[(int64_t)(kk + 1) * n + i] : (int)i;   // self pad: zero term
-      const int4 pa = PS[ja], pb = PS[jb];
-      const float4 va = VS[ja], vb = VS[jb];
-      // half-step pair vector r_ij = dq (q_i - q_j) + dt/2 (v_i - v_j)
-      const float2 rx = fma2(add2(make_float2(biased_diff<PER>(pi.x, pa.x, px), biased_diff<PER>(pi.x, pb.x, px)), MAG),
-                             DQ, mul2(HDT, sub2(VIX, make_float2(va.x, vb.x))));
-      const float2 ry = fma2(add2(make_float2(biased_diff<PER>(pi.y, pa.y, py), biased_diff<PER>(pi.y, pb.y, py)), MAG),
-                             DQ, mul2(HDT, sub2(VIY, make_float2(va.y, vb.y))));
-      float2 rz = f2(0.f);
-      if (D == 3)
-        rz = fma2(add2(make_float2(biased_diff<PER>(pi.z, pa.z, pz), biased_diff<PER>(pi.z, pb.z, pz)), MAG),
-                  DQ, mul2(HDT, sub2(VIZ, make_float2(va.z, vb.z))));
-      const Geo2 G = geometry2(rx, ry, rz, inv_h, dwr);
-      const float2 dev_j = fma2(HDT, make_float2(va.w, vb.w), make_float2(i2f(pa.w), i2f(pb.w)));
-      const float2 rho_j = add2(f2(rho0), dev_j);
-      // U_L - U_R = (v_j - v_i).r_ij / |r_ij|
-      const float2 vjr = fma2(make_float2(va.x, vb.x), rx, fma2(make_float2(va.y, vb.y), ry,
-                              mul2(make_float2(va.z, vb.z), rz)));
-      const float2 vir = fma2(VIX, rx, fma2(VIY, ry, mul2(VIZ, rz)));
-      const float2 dU = mul2(sub2(vjr, vir), G.inv_r);
-      const float2 beta = min2(mul2(f2(kc), max2(dU, 0.0f)), 1.0f);
-      // P* = (p_i + p_j)/2 + (c0/4)(rho_i + rho_j) beta (U_L - U_R)
-      const float2 pbar = mul2(f2(0.5f * c0sq), add2(f2(dev_i), dev_j));
-      const float2 pstar = fma2(mul2(f2(qc0), add2(f2(rho_i), rho_j)), mul2(beta, dU), pbar);
-      float2 mj = f2(mi);
-      if (mass) mj = make_float2(mass[ja], mass[jb]);
-      const float2 f = mul2(mul2(mul2(mj, rcp2(rho_j)), pstar), G.fw);   // V_j P* (dW/dr)/r
-      kahan2(sx, nx, f, rx);
-      kahan2(sy, ny, f, ry);
-      if (D == 3) kahan2(sz, nz, f, rz);
+    const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
+    const int nq = (nf + 3) >> 2;
+    int4 cur = nq ? nb4[i] : make_int4(0, 0, 0, 0);
+    for (int q = 0; q < nq; ++q) {
+      int4 nxt = cur;
+      if (q + 1 < nq) nxt = nb4[(int64_t)(q + 1) * n + i];      // next quad in flight
+      const int s = q << 2;
+      const int j0 = cur.x;
+      const int j1 = s + 1 < nf ? cur.y : (int)i;                // self pads: zero terms
+      const int j2 = s + 2 < nf ? cur.z : (int)i;
+      const int j3 = s + 3 < nf ? cur.w : (int)i;
+      const int4 p0 = PS[j0], p1 = PS[j1], p2 = PS[j2], p3 = PS[j3];
+      const float4 v0 = VS[j0], v1 = VS[j1], v2v = VS[j2], v3 = VS[j3];
+      float2 m01 = f2(I.mass), m23 = f2(I.mass);
+      if (mass) {
+        m01 = make_float2(mass[j0], mass[j1]);
+        m23 = make_float2(mass[j2], mass[j3]);
+      }
+      pr_fluid2<D, PER>(C, pi, vi, p0, p1, v0, v1, m01, DQ);
+      pr_fluid2<D, PER>(C, pi, vi, p2, p3, v2v, v3, m23, DQ);
+      cur = nxt;
     }
     if (nw) {
       const float g0 = I.g[0], g1 = I.g[1], g2 = I.g[2];
-      const float inv_c0sq = 1.0f / c0sq;
-      for (int kk = 0; kk < nw; kk += 2) {
-        const int wa = nbr[(int64_t)(nf + kk) * n + i];
-        const bool has_b = kk + 1 < nw;
-        const int wb = has_b ? nbr[(int64_t)(nf + kk + 1) * n + i] : wa;
-        const int4 qa = WP[wa], qb = WP[wb];
-        const float4 na = WN[wa], nb = WN[wb];
-        const float2 rx = fma2(add2(make_float2(biased_diff<PER>(pi.x, qa.x, px), biased_diff<PER>(pi.x, qb.x, px)), MAG),
-                               DQ, f2(hdt * vi.x));
-        const float2 ry = fma2(add2(make_float2(biased_diff<PER>(pi.y, qa.y, py), biased_diff<PER>(pi.y, qb.y, py)), MAG),
-                               DQ, f2(hdt * vi.y));
-        float2 rz = f2(0.f);
-        if (D == 3)
-          rz = fma2(add2(make_float2(biased_diff<PER>(pi.z, qa.z, pz), biased_diff<PER>(pi.z, qb.z, pz)), MAG),
-                    DQ, f2(hdt * vi.z));
-        const Geo2 G = geometry2(rx, ry, rz, inv_h, dwr);
-        // one-sided problem: U_L = -n.v_i, U_R = -U_L, P_R = P_L + rho_i g.(r_w - r_i)
-        const float2 UL = mul2(f2(-1.0f), fma2(make_float2(na.x, nb.x), VIX,
-                                               fma2(make_float2(na.y, nb.y), VIY, mul2(make_float2(na.z, nb.z), VIZ))));
-        const float2 gr = fma2(f2(g0), rx, fma2(f2(g1), ry, mul2(f2(g2), rz)));
-        const float2 PR = fma2(f2(-rho_i), gr, f2(pr_i));
-        const float2 rhoR = fma2(PR, f2(inv_c0sq), f2(rho0));
-        const float2 dU = add2(UL, UL);
-        const float2 beta = min2(mul2(f2(kc), max2(dU, 0.0f)), 1.0f);
-        const float2 pstar = fma2(mul2(f2(qc0), add2(f2(rho_i), rhoR)), mul2(beta, dU),
-                                  mul2(f2(0.5f), add2(f2(pr_i), PR)));
-        float2 Vw = make_float2(i2f(qa.w), has_b ? i2f(qb.w) : 0.0f);   // duplicate pad carries no volume
-        const float2 f = mul2(mul2(Vw, pstar), G.fw);
-        kahan2(sx, nx, f, rx);
-        kahan2(sy, ny, f, ry);
-        if (D == 3) kahan2(sz, nz, f, rz);
+      const float inv_c0sq = 1.0f / I.c0sq;
+      const int q0 = wall_slot0(nf) >> 2, nwq = (nw + 3) >> 2;
+      for (int q = 0; q < nwq; ++q) {
+        const int4 c = nb4[(int64_t)(q0 + q) * n + i];
+        const int s = q << 2;
+        const int w1 = s + 1 < nw ? c.y : c.x, w2 = s + 2 < nw ? c.z : c.x, w3 = s + 3 < nw ? c.w : c.x;
+        const int4 a0 = WP[c.x], a1 = WP[w1], a2 = WP[w2], a3 = WP[w3];
+        const float4 n0 = WN[c.x], n1 = WN[w1], n2 = WN[w2], n3 = WN[w3];
+        const float2 V01 = make_float2(i2f(a0.w), s + 1 < nw ? i2f(a1.w) : 0.0f);   // pads carry no volume
+        const float2 V23 = make_float2(s + 2 < nw ? i2f(a2.w) : 0.0f, s + 3 < nw ? i2f(a3.w) : 0.0f);
+        pr_wall2<D, PER>(C, pi, vi, a0, a1, n0, n1, V01, DQ, g0, g1, g2, inv_c0sq);
+        pr_wall2<D, PER>(C, pi, vi, a2, a3, n2, n3, V23, DQ, g0, g1, g2, inv_c0sq);
       }
     }
     // dv/dt = acc_prior + g - (2/rho_i) sum V_j P* grad_i W_ij
-    const float s = -2.0f / rho_i;
-    const float ax = (sx.x + nx.x) + (sx.y + nx.y);
-    const float ay = (sy.x + ny.x) + (sy.y + ny.y);
-    const float az = (sz.x + nz.x) + (sz.y + nz.y);
+    const float sc = -2.0f / C.rho_i;
+    const float ax = (C.sx.x + C.nx.x) + (C.sx.y + C.nx.y);
+    const float ay = (C.sy.x + C.ny.x) + (C.sy.y + C.ny.y);
+    const float az = (C.sz.x + C.nz.x) + (C.sz.y + C.nz.y);
     const float4 ap = acc_prior ? acc_prior[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float a0 = ap.x + I.g[0] + s * ax;
-    const float a1 = ap.y + I.g[1] + s * ay;
-    const float a2 = D == 3 ? ap.z + I.g[2] + s * az : 0.f;
+    const float a0 = ap.x + I.g[0] + sc * ax;
+    const float a1 = ap.y + I.g[1] + sc * ay;
+    const float a2 = D == 3 ? ap.z + I.g[2] + sc * az : 0.f;
     const float4 vn = make_float4(vi.x + dt * a0, vi.y + dt * a1, vi.z + dt * a2, vi.w);  // verlet-first-mediate
+    const float hdt = C.hdt;
     int qx = pi.x + __float2int_rn(hdt * vi.x * I.inv_dq);                              // verlet-first-half
     int qy = pi.y + __float2int_rn(hdt * vi.y * I.inv_dq);
     int qz = D == 3 ? pi.z + __float2int_rn(hdt * vi.z * I.inv_dq) : 0;
     if (PER) {
-      qx = wrap_coord(qx, px);
-      qy = wrap_coord(qy, py);
-      if (D == 3) qz = wrap_coord(qz, pz);
+      qx = wrap_coord(qx, C.px);
+      qy = wrap_coord(qy, C.py);
+      if (D == 3) qz = wrap_coord(qz, C.pz);
     }
-    PH[i] = make_int4(qx, qy, qz, f2i(dev_i));
+    PH[i] = make_int4(qx, qy, qz, f2i(C.dev_i));
     VH[i] = vn;
     if (acc_keep) acc_keep[i] = make_float4(a0, a1, a2, 0.f);
     v2 = vn.x * vn.x + vn.y * vn.y + vn.z * vn.z;
@@ -214,6 +262,55 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
 }
 
 // ---------------------------------------------------------------- density relaxation ---
+struct DrCtx {
+  float hdt, inv_h, dwr, rho0, c0, dev_i, rho_i;
+  int px, py, pz;
+  float2 s, nc;
+};
+
+template <int D, bool PER>
+__device__ __forceinline__ void dr_fluid2(DrCtx& C, const int4& pi, const float4& vi, const int4& pa,
+                                          const int4& pb, const float4& va, const float4& vb, float2 mj,
+                                          float2 DQ) {
+  const float2 HDT = f2(C.hdt);
+  // r_ij^{n+1} = r_ij^{n+1/2} + dt/2 (v_i - v_j)^{n+1}
+  const float2 rx = pair_axis<PER>(pi.x, pa.x, pb.x, C.px, DQ, mul2(HDT, sub2(f2(vi.x), make_float2(va.x, vb.x))));
+  const float2 ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(HDT, sub2(f2(vi.y), make_float2(va.y, vb.y))));
+  float2 rz = f2(0.f);
+  if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(HDT, sub2(f2(vi.z), make_float2(va.z, vb.z))));
+  const Geo2 G = geometry2(rx, ry, rz, C.inv_h, C.dwr);
+  const float2 dev_j = make_float2(i2f(pa.w), i2f(pb.w));
+  const float2 rho_j = add2(f2(C.rho0), dev_j);
+  // (U_R - U_L)/2 = (v_i - v_j).r_ij / (2 |r_ij|)
+  const float2 dvx = sub2(f2(vi.x), make_float2(va.x, vb.x));
+  const float2 dvy = sub2(f2(vi.y), make_float2(va.y, vb.y));
+  const float2 dvz = sub2(f2(vi.z), make_float2(va.z, vb.z));
+  const float2 half_dUR = mul2(fma2(dvx, rx, fma2(dvy, ry, mul2(dvz, rz))), mul2(G.inv_r, f2(0.5f)));
+  // U* - U_L = (U_R - U_L)/2 + c0 (dev_i - dev_j)/(rho_i + rho_j)
+  const float2 dUs = fma2(mul2(f2(C.c0), sub2(f2(C.dev_i), dev_j)), rcp2(add2(f2(C.rho_i), rho_j)), half_dUR);
+  kahan2(C.s, C.nc, mul2(mul2(mj, rcp2(rho_j)), dUs), mul2(G.fw, G.r));
+}
+
+template <int D, bool PER>
+__device__ __forceinline__ void dr_wall2(DrCtx& C, const int4& pi, const float4& vi, const int4& qa,
+                                         const int4& qb, const float4& na, const float4& nb, float2 Vw,
+                                         float2 DQ, float g0, float g1, float g2, float inv_c0sq,
+                                         float pr_i) {
+  const float2 rx = pair_axis<PER>(pi.x, qa.x, qb.x, C.px, DQ, f2(C.hdt * vi.x));
+  const float2 ry = pair_axis<PER>(pi.y, qa.y, qb.y, C.py, DQ, f2(C.hdt * vi.y));
+  float2 rz = f2(0.f);
+  if (D == 3) rz = pair_axis<PER>(pi.z, qa.z, qb.z, C.pz, DQ, f2(C.hdt * vi.z));
+  const Geo2 G = geometry2(rx, ry, rz, C.inv_h, C.dwr);
+  const float2 UL = mul2(f2(-1.0f), fma2(make_float2(na.x, nb.x), f2(vi.x),
+                                         fma2(make_float2(na.y, nb.y), f2(vi.y), mul2(make_float2(na.z, nb.z), f2(vi.z)))));
+  const float2 gr = fma2(f2(g0), rx, fma2(f2(g1), ry, mul2(f2(g2), rz)));
+  const float2 PR = fma2(f2(-C.rho_i), gr, f2(pr_i));
+  const float2 rhoR = fma2(PR, f2(inv_c0sq), f2(C.rho0));
+  // U_R = -U_L: U* = (P_L - P_R)/(2 rho_bar c0) = rho_i g.r_iw / (c0 (rho_i + rho_R))
+  const float2 Us = mul2(mul2(f2(C.rho_i), gr), rcp2(mul2(f2(C.c0), add2(f2(C.rho_i), rhoR))));
+  kahan2(C.s, C.nc, mul2(Vw, sub2(Us, UL)), mul2(G.fw, G.r));
+}
+
 template <int D, bool PER>
 __global__ void __launch_bounds__(kBlock, 2)
 k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __restrict__ VH,
@@ -228,85 +325,71 @@ k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __res
   const double dtd = ctrl[k].dt;
   if (dtd == 0.0) return;
   const Inst& I = inst[k];
-  const float hdt = 0.5f * (float)dtd;
-  const float dq = I.dq, inv_h = I.inv_h, dwr = I.dwr_a, rho0 = I.rho0, c0 = I.c0;
-  const int px = PER ? I.period[0] : 0, py = PER ? I.period[1] : 0, pz = PER ? I.period[2] : 0;
+  DrCtx C;
+  C.hdt = 0.5f * (float)dtd;
+  C.inv_h = I.inv_h;
+  C.dwr = I.dwr_a;
+  C.rho0 = I.rho0;
+  C.c0 = I.c0;
+  C.px = PER ? I.period[0] : 0;
+  C.py = PER ? I.period[1] : 0;
+  C.pz = PER ? I.period[2] : 0;
+  C.s = C.nc = f2(0.f);
   const int4 pi = PH[i];
   const float4 vi = VH[i];                            // v^{n+1}
-  const float dev_i = i2f(pi.w);
-  const float rho_i = rho0 + dev_i;
-  const float2 HDT = f2(hdt), DQ = f2(dq), MAG = f2(-kMagic);
-  const float2 VIX = f2(vi.x), VIY = f2(vi.y), VIZ = f2(vi.z);
-  float2 s = f2(0.f), nc = f2(0.f);
+  C.dev_i = i2f(pi.w);
+  C.rho_i = C.rho0 + C.dev_i;
+  const float2 DQ = f2(I.dq);
   const uint32_t cnt = nbc[i];
   const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
-  const float mi = mass ? 0.0f : I.mass;
-  for (int kk = 0; kk < nf; kk += 2) {
-    const int ja = nbr[(int64_t)kk * n + i];
-    const int jb = kk + 1 < nf ? nbr[(int64_t)(kk + 1) * n + i] : (int)i;
-    const int4 pa = PH[ja], pb = PH[jb];
-    const float4 va = VH[ja], vb = VH[jb];
-    // r_ij^{n+1} = r_ij^{n+1/2} + dt/2 (v_i - v_j)^{n+1}
-    const float2 rx = fma2(add2(make_float2(biased_diff<PER>(pi.x, pa.x, px), biased_diff<PER>(pi.x, pb.x, px)), MAG),
-                           DQ, mul2(HDT, sub2(VIX, make_float2(va.x, vb.x))));
-    const float2 ry = fma2(add2(make_float2(biased_diff<PER>(pi.y, pa.y, py), biased_diff<PER>(pi.y, pb.y, py)), MAG),
-                           DQ, mul2(HDT, sub2(VIY, make_float2(va.y, vb.y))));
-    float2 rz = f2(0.f);
-    if (D == 3)
-      rz = fma2(add2(make_float2(biased_diff<PER>(pi.z, pa.z, pz), biased_diff<PER>(pi.z, pb.z, pz)), MAG),
-                DQ, mul2(HDT, sub2(VIZ, make_float2(va.z, vb.z))));
-    const Geo2 G = geometry2(rx, ry, rz, inv_h, dwr);
-    const float2 dev_j = make_float2(i2f(pa.w), i2f(pb.w));
-    const float2 rho_j = add2(f2(rho0), dev_j);
-    const float2 vjr = fma2(make_float2(va.x, vb.x), rx, fma2(make_float2(va.y, vb.y), ry,
-                            mul2(make_float2(va.z, vb.z), rz)));
-    const float2 vir = fma2(VIX, rx, fma2(VIY, ry, mul2(VIZ, rz)));
-    // U* - U_L = (U_R - U_L)/2 + c0 (dev_i - dev_j)/(rho_i + rho_j)
-    const float2 half_dUR = mul2(mul2(sub2(vir, vjr), G.inv_r), f2(0.5f));
-    const float2 dUs = fma2(mul2(f2(c0), sub2(f2(dev_i), dev_j)), rcp2(add2(f2(rho_i), rho_j)), half_dUR);
-    float2 mj = f2(mi);
-    if (mass) mj = make_float2(mass[ja], mass[jb]);
-    const float2 dW = mul2(G.fw, G.r);
-    kahan2(s, nc, mul2(mul2(mj, rcp2(rho_j)), dUs), dW);
+  const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
+  const int nq = (nf + 3) >> 2;
+  int4 cur = nq ? nb4[i] : make_int4(0, 0, 0, 0);
+  for (int q = 0; q < nq; ++q) {
+    int4 nxt = cur;
+    if (q + 1 < nq) nxt = nb4[(int64_t)(q + 1) * n + i];
+    const int s = q << 2;
+    const int j0 = cur.x;
+    const int j1 = s + 1 < nf ? cur.y : (int)i;
+    const int j2 = s + 2 < nf ? cur.z : (int)i;
+    const int j3 = s + 3 < nf ? cur.w : (int)i;
+    const int4 p0 = PH[j0], p1 = PH[j1], p2 = PH[j2], p3 = PH[j3];
+    const float4 v0 = VH[j0], v1 = VH[j1], v2 = VH[j2], v3 = VH[j3];
+    float2 m01 = f2(I.mass), m23 = f2(I.mass);
+    if (mass) {
+      m01 = make_float2(mass[j0], mass[j1]);
+      m23 = make_float2(mass[j2], mass[j3]);
+    }
+    dr_fluid2<D, PER>(C, pi, vi, p0, p1, v0, v1, m01, DQ);
+    dr_fluid2<D, PER>(C, pi, vi, p2, p3, v2, v3, m23, DQ);
+    cur = nxt;
   }
   if (nw) {
     const float g0 = I.g[0], g1 = I.g[1], g2 = I.g[2];
-    const float inv_c0sq = 1.0f / I.c0sq, pr_i = I.c0sq * dev_i;
-    for (int kk = 0; kk < nw; kk += 2) {
-      const int wa = nbr[(int64_t)(nf + kk) * n + i];
-      const bool has_b = kk + 1 < nw;
-      const int wb = has_b ? nbr[(int64_t)(nf + kk + 1) * n + i] : wa;
-      const int4 qa = WP[wa], qb = WP[wb];
-      const float4 na = WN[wa], nb = WN[wb];
-      const float2 rx = fma2(add2(make_float2(biased_diff<PER>(pi.x, qa.x, px), biased_diff<PER>(pi.x, qb.x, px)), MAG),
-                             DQ, f2(hdt * vi.x));
-      const float2 ry = fma2(add2(make_float2(biased_diff<PER>(pi.y, qa.y, py), biased_diff<PER>(pi.y, qb.y, py)), MAG),
-                             DQ, f2(hdt * vi.y));
-      float2 rz = f2(0.f);
-      if (D == 3)
-        rz = fma2(add2(make_float2(biased_diff<PER>(pi.z, qa.z, pz), biased_diff<PER>(pi.z, qb.z, pz)), MAG),
-                  DQ, f2(hdt * vi.z));
-      const Geo2 G = geometry2(rx, ry, rz, inv_h, dwr);
-      const float2 UL = mul2(f2(-1.0f), fma2(make_float2(na.x, nb.x), VIX,
-                                             fma2(make_float2(na.y, nb.y), VIY, mul2(make_float2(na.z, nb.z), VIZ))));
-      const float2 gr = fma2(f2(g0), rx, fma2(f2(g1), ry, mul2(f2(g2), rz)));
-      const float2 PR = fma2(f2(-rho_i), gr, f2(pr_i));
-      const float2 rhoR = fma2(PR, f2(inv_c0sq), f2(rho0));
-      // U_R = -U_L: U* = (P_L - P_R)/(2 rho_bar c0) = rho_i g.r_iw / (c0 (rho_i + rho_R))
-      const float2 Us = mul2(mul2(f2(rho_i), gr), rcp2(mul2(f2(c0), add2(f2(rho_i), rhoR))));
-      const float2 Vw = make_float2(i2f(qa.w), has_b ? i2f(qb.w) : 0.0f);
-      kahan2(s, nc, mul2(Vw, sub2(Us, UL)), mul2(G.fw, G.r));
+    const float inv_c0sq = 1.0f / I.c0sq, pr_i = I.c0sq * C.dev_i;
+    const int q0 = wall_slot0(nf) >> 2, nwq = (nw + 3) >> 2;
+    for (int q = 0; q < nwq; ++q) {
+      const int4 c = nb4[(int64_t)(q0 + q) * n + i];
+      const int s = q << 2;
+      const int w1 = s + 1 < nw ? c.y : c.x, w2 = s + 2 < nw ? c.z : c.x, w3 = s + 3 < nw ? c.w : c.x;
+      const int4 a0 = WP[c.x], a1 = WP[w1], a2 = WP[w2], a3 = WP[w3];
+      const float4 n0 = WN[c.x], n1 = WN[w1], n2 = WN[w2], n3 = WN[w3];
+      const float2 V01 = make_float2(i2f(a0.w), s + 1 < nw ? i2f(a1.w) : 0.0f);
+      const float2 V23 = make_float2(s + 2 < nw ? i2f(a2.w) : 0.0f, s + 3 < nw ? i2f(a3.w) : 0.0f);
+      dr_wall2<D, PER>(C, pi, vi, a0, a1, n0, n1, V01, DQ, g0, g1, g2, inv_c0sq, pr_i);
+      dr_wall2<D, PER>(C, pi, vi, a2, a3, n2, n3, V23, DQ, g0, g1, g2, inv_c0sq, pr_i);
     }
   }
-  const float drho = 2.0f * rho_i * ((s.x + nc.x) + (s.y + nc.y));
-  const float dev_n = dev_i + hdt * drho;             // Eq. verlet-first-final (density)
+  const float drho = 2.0f * C.rho_i * ((C.s.x + C.nc.x) + (C.s.y + C.nc.y));
+  const float dev_n = C.dev_i + C.hdt * drho;         // Eq. verlet-first-final (density)
+  const float hdt = C.hdt;
   int qx = pi.x + __float2int_rn(hdt * vi.x * I.inv_dq);
   int qy = pi.y + __float2int_rn(hdt * vi.y * I.inv_dq);
   int qz = D == 3 ? pi.z + __float2int_rn(hdt * vi.z * I.inv_dq) : 0;
   if (PER) {
-    qx = wrap_coord(qx, px);
-    qy = wrap_coord(qy, py);
-    if (D == 3) qz = wrap_coord(qz, pz);
+    qx = wrap_coord(qx, C.px);
+    qy = wrap_coord(qy, C.py);
+    if (D == 3) qz = wrap_coord(qz, C.pz);
   }
   if (!isfinite(dev_n)) raise_error(g, ERR_NAN, i);
   PS[i] = make_int4(qx, qy, qz, f2i(dev_n));
