@@ -189,6 +189,12 @@ def run_ours(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         sim.step(1)
+    tuned = None
+    if not args.no_autotune:
+        # one extra (untimed) advection step that times the launch variants
+        cfg, times = sph.sph_autotune(sim.handle, stream)
+        tuned = {"pressure_relaxation": {"threads_per_particle": cfg[0], "block": cfg[1]},
+                 "density_relaxation": {"threads_per_particle": cfg[2], "block": cfg[3]}}
     torch.cuda.synchronize()
 
     # ---------------- timed region: device-resident state
@@ -292,6 +298,7 @@ def run_ours(args, rank, world, local_rank):
                       % (4 * N * info.capacity / 1e9),
                 "loop": "graph" if args.graph else "host-driven, one sync per substep",
                 "parallelism": f"replicas x{world}",
+                "launch": tuned or {"autotune": "off"},
             },
             "clocks": clk,
             "gpu_launches": launches,
@@ -305,6 +312,78 @@ def run_ours(args, rank, world, local_rank):
     sim.close()
 
 
+# ------------------------------------------------------------------------------ other workloads
+def _timed_steps(sim, steps, stream):
+    """Advection steps timed with CUDA events on the launching stream; returns (ms, diags)."""
+    import torch
+    d0 = sim.diagnostics()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    sim.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), d0, sim.diagnostics()
+
+
+def _units(problems, d0, d1):
+    if len(problems) == 1:
+        d0, d1 = [d0], [d1]
+    return sum(p.n_fluid * (b["substeps"] - a["substeps"]) for p, a, b in zip(problems, d0, d1))
+
+
+def run_workload(args):
+    """Secondary workloads: the batched tanks, the 2D dam break and the Taylor-Green vortex."""
+    import torch
+    from paper_2010_12375_gb300 import sph, workloads as wk
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    if args.workload == "batched":
+        problems = wk.batched_dam_breaks(256)
+        name = "256 independent 2D dam breaks (2k-50k fluid each), one handle"
+    elif args.workload == "dam2d":
+        problems = [wk.dam_break_2d()]
+        name = "2D dam break, 3,200 fluid particles (dp = H/40)"
+    else:
+        problems = [wk.taylor_green(400)]
+        name = "2D periodic Taylor-Green vortex, 400 x 400, Re = 100"
+    out = {"metric": f"particle-substeps/s, {args.workload}", "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+           "data": "synthetic", "config": {"workload": name,
+                                           "n_fluid": sum(p.n_fluid for p in problems),
+                                           "tanks": len(problems)}}
+    results = {}
+    for loop, flags in (("graph", sph.SPH_FLAG_GRAPH), ("host", 0)):
+        sim = sph.Simulation(problems if len(problems) > 1 else problems[0], flags=flags, stream=stream)
+        for _ in range(args.warmup):
+            sim.step(1)
+        if not args.no_autotune:
+            sph.sph_autotune(sim.handle, stream)
+        ms, d0, d1 = _timed_steps(sim, args.steps, stream)
+        results[loop] = {"value": _units(problems, d0, d1) / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                         "launch": sph.sph_get_launch_config(sim.handle)}
+        sim.close()
+    out["value"] = results["graph"]["value"]
+    out["ms_per_step"] = results["graph"]["ms_per_step"]
+    out["loops"] = results
+    if args.workload == "batched":
+        # the same tanks one after another, each its own handle and graph: the plain solver
+        total_ms, units = 0.0, 0
+        for p in problems:
+            sim = sph.Simulation(p, flags=sph.SPH_FLAG_GRAPH, stream=stream)
+            sim.step(1)
+            ms, d0, d1 = _timed_steps(sim, args.steps, stream)
+            total_ms += ms
+            units += p.n_fluid * (d1["substeps"] - d0["substeps"])
+            sim.close()
+        plain = units / (total_ms * 1e-3)
+        out["plain_gpu"] = {"value": plain, "ms_per_step_all_tanks": total_ms / args.steps,
+                            "what": "each tank in its own handle, one after another, graph loop"}
+        out["speedup_vs_plain_gpu"] = out["value"] / plain
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,6 +395,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg"],
+                    help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -324,6 +406,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "dam3d":
+        run_workload(args)
         return
     if world > 1:
         import torch.distributed as dist

@@ -202,6 +202,24 @@ int sph_get_neighbours(sph_handle* h, int32_t* fluid_count, int32_t* wall_count,
  * sph_build_cells (host outputs; synchronous). */
 int sph_pair_count(sph_handle* h, int64_t* fluid_pairs, int64_t* wall_pairs, void* stream);
 
+/* Launch configuration of the two acoustic-substep kernels: cfg[0] threads per particle
+ * and cfg[1] block size of the pressure relaxation, cfg[2], cfg[3] the same for the
+ * density relaxation. Threads per particle 1, 2 or 4 (the lanes of a particle split its
+ * neighbour row and add their sums in a fixed order); block 128, 256 or 512. Set
+ * returns SPH_E_INVALID for other values. */
+int sph_get_launch_config(const sph_handle* h, int32_t* cfg);
+int sph_set_launch_config(sph_handle* h, const int32_t* cfg);
+
+/* Autotuner: runs one advection step, timing every launch variant (3 x 3 per kernel)
+ * of the two relaxation kernels on its first substep (each variant recomputes the same
+ * substep; the chosen one writes the result), keeps the fastest, and records it in the
+ * cache file $SPH_AUTOTUNE_CACHE (default $HOME/.cache/sph_gb300_autotune.json) under
+ * (GPU name, dim, particle-count power of two, batched or single). sph_create applies a
+ * cached entry for the same key. cfg_out (may be NULL) receives the chosen cfg;
+ * ms_out (may be NULL) the mean launch times [kernel][tpp index][block index] (18).
+ * Synchronous. */
+int sph_autotune(sph_handle* h, int32_t* cfg_out, double* ms_out, void* stream);
+
 /* Kernel launches the library has issued on this handle (graph nodes counted
  * once per execution, the substep loop by the device-side substep counter). */
 int sph_kernel_launches(sph_handle* h, int64_t* out);

@@ -3,9 +3,16 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
 #include <string>
 #include <vector>
+
+#include <sys/stat.h>
+#include <sys/types.h>
 
 #include "sph.h"
 #include "sph_kernels.h"
@@ -50,6 +57,8 @@ struct sph_handle {
 namespace {
 
 constexpr int kQuantBits = 22;
+
+int make_dir(const std::string& dir) { return mkdir(dir.c_str(), 0755); }
 
 int fail(sph_handle* h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -328,6 +337,101 @@ const double* device_view(sph_handle* h, const double* p, size_t elems, size_t o
   return h->stage + off;
 }
 
+// ---------------------------------------------------------------- autotuner ----------
+// Launch variants of the two acoustic-substep kernels: threads per particle x block size.
+// The choice is cached per (GPU, dimension, particle-count bucket, batched or not) in a
+// small JSON file: $SPH_AUTOTUNE_CACHE, else $HOME/.cache/sph_gb300_autotune.json.
+const int kTppChoices[3] = {1, 2, 4};
+const int kBlockChoices[3] = {128, 256, 512};
+
+std::string autotune_path() {
+  const char* env = std::getenv("SPH_AUTOTUNE_CACHE");
+  if (env && *env) return env;
+  const char* home = std::getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/sph_gb300_autotune.json";
+}
+
+std::string autotune_key(const sph_handle* h) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::memset(&prop, 0, sizeof(prop));
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) cudaGetLastError();
+  int bucket = 0;
+  for (int64_t v = std::max<int64_t>(h->b.n, 1); v > 1; v >>= 1) ++bucket;
+  std::ostringstream k;
+  k << prop.name << "|d" << h->b.dim << "|n2^" << bucket << "|" << (h->b.n_inst > 1 ? "batched" : "single");
+  return k.str();
+}
+
+// The cache is a flat JSON object {"key": "pr_tpp,pr_block,dr_tpp,dr_block", ...}.
+std::map<std::string, std::string> read_autotune_cache() {
+  std::map<std::string, std::string> m;
+  std::ifstream f(autotune_path());
+  if (!f) return m;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string t = ss.str();
+  size_t p = 0;
+  while (true) {
+    size_t a = t.find('"', p);
+    if (a == std::string::npos) break;
+    size_t b = t.find('"', a + 1);
+    if (b == std::string::npos) break;
+    size_t c = t.find('"', b + 1);
+    if (c == std::string::npos) break;
+    size_t d = t.find('"', c + 1);
+    if (d == std::string::npos) break;
+    m[t.substr(a + 1, b - a - 1)] = t.substr(c + 1, d - c - 1);
+    p = d + 1;
+  }
+  return m;
+}
+
+void write_autotune_cache(const std::map<std::string, std::string>& m) {
+  const std::string path = autotune_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {
+    const std::string dir = path.substr(0, slash);
+    for (size_t i = 1; i <= dir.size(); ++i)          // mkdir -p, component by component
+      if (i == dir.size() || dir[i] == '/') (void)make_dir(dir.substr(0, i));
+  }
+  std::ofstream f(path + ".tmp");
+  if (!f) return;
+  f << "{\n";
+  size_t k = 0;
+  for (const auto& kv : m) f << "  \"" << kv.first << "\": \"" << kv.second << "\"" << (++k < m.size() ? ",\n" : "\n");
+  f << "}\n";
+  f.close();
+  std::rename((path + ".tmp").c_str(), path.c_str());
+}
+
+bool parse_cfg(const std::string& v, sph::LaunchCfg* c) {
+  int a[4];
+  if (std::sscanf(v.c_str(), "%d,%d,%d,%d", &a[0], &a[1], &a[2], &a[3]) != 4) return false;
+  auto ok_t = [](int t) { return t == 1 || t == 2 || t == 4; };
+  auto ok_b = [](int b) { return b == 128 || b == 256 || b == 512; };
+  if (!ok_t(a[0]) || !ok_b(a[1]) || !ok_t(a[2]) || !ok_b(a[3])) return false;
+  c->pr_tpp = a[0];
+  c->pr_block = a[1];
+  c->dr_tpp = a[2];
+  c->dr_block = a[3];
+  return true;
+}
+
+std::string format_cfg(const sph::LaunchCfg& c) {
+  std::ostringstream o;
+  o << c.pr_tpp << "," << c.pr_block << "," << c.dr_tpp << "," << c.dr_block;
+  return o.str();
+}
+
+void drop_graph(sph_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -499,6 +603,11 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
     CK(h, cudaStreamSynchronize(s));
   }
   sph::sort_walls(b, b.PH, b.VH, b.wid, s);
+  {
+    const auto cache = read_autotune_cache();
+    const auto it = cache.find(autotune_key(h));
+    if (it != cache.end()) parse_cfg(it->second, &b.cfg);
+  }
   CK(h, cudaGetLastError());
   int r = sph_set_state(h, pos, vel, rho, nullptr, 0.0, stream);
   if (r != SPH_OK) return r;
@@ -749,6 +858,84 @@ int sph_pair_count(sph_handle* h, int64_t* fluid_pairs, int64_t* wall_pairs, voi
   *fluid_pairs = (int64_t)hv[0];
   *wall_pairs = (int64_t)hv[1];
   return r;
+}
+
+int sph_get_launch_config(const sph_handle* h, int32_t* cfg) {
+  if (!h || !cfg) return SPH_E_INVALID;
+  cfg[0] = h->b.cfg.pr_tpp;
+  cfg[1] = h->b.cfg.pr_block;
+  cfg[2] = h->b.cfg.dr_tpp;
+  cfg[3] = h->b.cfg.dr_block;
+  return SPH_OK;
+}
+
+int sph_set_launch_config(sph_handle* h, const int32_t* cfg) {
+  if (!h || !cfg) return SPH_E_INVALID;
+  std::ostringstream o;
+  o << cfg[0] << "," << cfg[1] << "," << cfg[2] << "," << cfg[3];
+  sph::LaunchCfg c;
+  if (!parse_cfg(o.str(), &c)) return fail(h, SPH_E_INVALID, "threads per particle must be 1, 2 or 4 and blocks 128, 256 or 512");
+  h->b.cfg = c;
+  drop_graph(h);
+  return SPH_OK;
+}
+
+int sph_autotune(sph_handle* h, int32_t* cfg_out, double* ms_out, void* stream) {
+  if (!h) return SPH_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  enqueue_build(h, s, &h->launches);
+  h->cells_valid = true;
+  enqueue_advection(h, s, &h->launches);
+  sph::launch_dt_acoustic(h->b, s, h->cond, false, &h->launches);
+  cudaEvent_t e0 = h->ev[0], e1 = h->ev[1];
+  const int reps = 3;
+  // repeated launches of either kernel are idempotent: same inputs, same outputs
+  for (int kernel = 0; kernel < 2; ++kernel) {
+    float best = 1e30f;
+    sph::LaunchCfg best_cfg = h->b.cfg;
+    for (int t : kTppChoices)
+      for (int blk : kBlockChoices) {
+        sph::LaunchCfg c = h->b.cfg;
+        if (kernel == 0) { c.pr_tpp = t; c.pr_block = blk; } else { c.dr_tpp = t; c.dr_block = blk; }
+        sph::Buffers bb = h->b;
+        bb.cfg = c;
+        CK(h, cudaEventRecord(e0, s));
+        for (int r = 0; r < reps; ++r) {
+          if (kernel == 0) sph::launch_pressure_relaxation(bb, s, &h->launches);
+          else sph::launch_density_relaxation(bb, s, &h->launches);
+        }
+        CK(h, cudaEventRecord(e1, s));
+        CK(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, e0, e1));
+        ms /= reps;
+        if (ms_out) ms_out[kernel * 9 + (t == 1 ? 0 : t == 2 ? 1 : 2) * 3 + (blk == 128 ? 0 : blk == 256 ? 1 : 2)] = ms;
+        if (ms < best) {
+          best = ms;
+          best_cfg = c;
+        }
+      }
+    h->b.cfg = best_cfg;
+    // the stored result comes from the chosen variant
+    if (kernel == 0) sph::launch_pressure_relaxation(h->b, s, &h->launches);
+    else sph::launch_density_relaxation(h->b, s, &h->launches);
+  }
+  drop_graph(h);
+  int r = sync_status(h, s);
+  if (r != SPH_OK) return r;
+  // finish the advection step with the chosen configuration
+  for (int guard = 0; h->hglob->active; ++guard) {
+    int32_t done = 0;
+    r = sph_acoustic_substep(h, &done, nullptr, stream);
+    if (r != SPH_OK) return r;
+    if (done) break;
+    if (guard > 1000000) return fail(h, SPH_E_UNSTABLE, "substep loop did not finish");
+  }
+  auto cache = read_autotune_cache();
+  cache[autotune_key(h)] = format_cfg(h->b.cfg);
+  write_autotune_cache(cache);
+  if (cfg_out) sph_get_launch_config(h, cfg_out);
+  return SPH_OK;
 }
 
 int sph_kernel_launches(sph_handle* h, int64_t* out) {

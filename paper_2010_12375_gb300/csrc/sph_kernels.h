@@ -7,8 +7,16 @@
 
 namespace sph {
 
+// Launch configuration of the acoustic-substep kernels (chosen by the autotuner):
+// threads per particle (1, 2, 4) and block size (128, 256, 512).
+struct LaunchCfg {
+  int pr_tpp = 1, pr_block = 256;   // pressure relaxation
+  int dr_tpp = 1, dr_block = 256;   // density relaxation
+};
+
 // Device buffers of one handle. Fluid arrays are indexed in cell-sorted order.
 struct Buffers {
+  LaunchCfg cfg;
   int64_t n = 0, nw = 0, n_cells = 0;
   int n_inst = 1, dim = 2, cap = 0;
   bool any_periodic = false;      // some tank has a periodic axis

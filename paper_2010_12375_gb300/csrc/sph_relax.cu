@@ -27,11 +27,20 @@ namespace sph {
 
 namespace {
 
-constexpr int kBlock = 256;
+constexpr int kMaxBlock = 512;         // launch variants use 128, 256 or 512 threads
 constexpr float kTinyR2 = 1e-30f;     // keeps rsqrt finite for a pair at zero distance
 
-inline unsigned grid_for(int64_t n, int block = kBlock) {
-  return (unsigned)((n + block - 1) / block);
+inline unsigned grid_for(int64_t threads, int block) {
+  return (unsigned)((threads + block - 1) / block);
+}
+
+// Sum of a value over the TPP consecutive lanes that share a particle, in a fixed
+// butterfly order: every lane of the group gets the same, deterministic total.
+template <int TPP>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = 1; o < TPP; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 __device__ __forceinline__ void raise_error(Global* g, int bit, long long idx) {
@@ -43,16 +52,19 @@ __device__ __forceinline__ int inst_index(const int* inst_of, int64_t i) {
   return inst_of ? inst_of[i] : 0;
 }
 
+// Whether the particles [first, last] of this block (TPP threads each) share one tank.
+template <int TPP>
 __device__ __forceinline__ bool block_one_instance(const int* inst_of, int64_t n, int* k_out) {
-  int64_t first = (int64_t)blockIdx.x * blockDim.x;
-  int64_t last = min(first + (int64_t)blockDim.x, n) - 1;
-  int a = inst_index(inst_of, first), b = inst_index(inst_of, last);
+  int64_t first = (int64_t)blockIdx.x * (blockDim.x / TPP);
+  int64_t last = min(first + (int64_t)(blockDim.x / TPP), n) - 1;
+  if (first > last) last = first;
+  int a = inst_index(inst_of, min(first, n - 1)), b = inst_index(inst_of, max(last, (int64_t)0));
   *k_out = a;
   return a == b;
 }
 
 __device__ __forceinline__ void reduce_vmax(float v2, bool valid, int k, bool uniform_block, Ctrl* ctrl) {
-  __shared__ float red[kBlock / 32];
+  __shared__ float red[kMaxBlock / 32];
   if (!uniform_block) {
     if (valid) atomicMax(&ctrl[k].vmax2, __float_as_uint(v2));
     return;
@@ -155,8 +167,11 @@ __device__ __forceinline__ void pr_wall2(PrCtx& C, const int4& pi, const float4&
 }
 
 // ---------------------------------------------------------------- pressure relaxation --
-template <int D, bool PER>
-__global__ void __launch_bounds__(kBlock, 2)
+// TPP threads share one particle: lane `sub` takes quads sub, sub + TPP, ... of its row,
+// and the lanes' compensated sums are combined in a fixed order. TPP = 1 is one thread per
+// particle; 2 and 4 trade per-thread work for more threads in flight.
+template <int D, bool PER, int TPP>
+__global__ void __launch_bounds__(kMaxBlock, 1)
 k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __restrict__ VS,
                       int4* __restrict__ PH, float4* __restrict__ VH,
                       const float* __restrict__ mass, const int* __restrict__ inst_of,
@@ -164,18 +179,22 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
                       const uint32_t* __restrict__ nbc, const int4* __restrict__ WP,
                       const float4* __restrict__ WN, const float4* __restrict__ acc_prior,
                       float4* __restrict__ acc_keep, Global* g) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+  const int sub = TPP > 1 ? (int)(threadIdx.x % TPP) : 0;
   int kb;
-  const bool uni = block_one_instance(inst_of, n, &kb);
+  const bool uni = block_one_instance<TPP>(inst_of, n, &kb);
   bool valid = i < n;
   const int k = valid ? inst_index(inst_of, i) : kb;
   const double dtd = ctrl[k].dt;
   if (dtd == 0.0) valid = false;                 // tank idle for this substep
   float v2 = 0.0f;
+  PrCtx C;
+  C.sx = C.sy = C.sz = C.nx = C.ny = C.nz = f2(0.f);
+  const Inst& I = inst[k];
+  const float dt = (float)dtd;
+  int4 pi = make_int4(0, 0, 0, 0);
+  float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
   if (valid) {
-    const Inst& I = inst[k];
-    const float dt = (float)dtd;
-    PrCtx C;
     C.hdt = 0.5f * dt;
     C.inv_h = I.inv_h;
     C.dwr = I.dwr_a;
@@ -186,9 +205,8 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
     C.px = PER ? I.period[0] : 0;
     C.py = PER ? I.period[1] : 0;
     C.pz = PER ? I.period[2] : 0;
-    C.sx = C.sy = C.sz = C.nx = C.ny = C.nz = f2(0.f);
-    const int4 pi = PS[i];
-    const float4 vi = VS[i];
+    pi = PS[i];
+    vi = VS[i];
     C.dev_i = i2f(pi.w) + C.hdt * vi.w;               // Eq. verlet-first-half (density)
     C.rho_i = C.rho0 + C.dev_i;
     C.pr_i = C.c0sq * C.dev_i;                        // Eq. eqeos
@@ -197,10 +215,10 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
     const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
     const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
     const int nq = (nf + 3) >> 2;
-    int4 cur = nq ? nb4[i] : make_int4(0, 0, 0, 0);
-    for (int q = 0; q < nq; ++q) {
+    int4 cur = sub < nq ? nb4[(int64_t)sub * n + i] : make_int4(0, 0, 0, 0);
+    for (int q = sub; q < nq; q += TPP) {
       int4 nxt = cur;
-      if (q + 1 < nq) nxt = nb4[(int64_t)(q + 1) * n + i];      // next quad in flight
+      if (q + TPP < nq) nxt = nb4[(int64_t)(q + TPP) * n + i];  // next quad in flight
       const int s = q << 2;
       const int j0 = cur.x;
       const int j1 = s + 1 < nf ? cur.y : (int)i;                // self pads: zero terms
@@ -221,7 +239,7 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
       const float g0 = I.g[0], g1 = I.g[1], g2 = I.g[2];
       const float inv_c0sq = 1.0f / I.c0sq;
       const int q0 = wall_slot0(nf) >> 2, nwq = (nw + 3) >> 2;
-      for (int q = 0; q < nwq; ++q) {
+      for (int q = sub; q < nwq; q += TPP) {
         const int4 c = nb4[(int64_t)(q0 + q) * n + i];
         const int s = q << 2;
         const int w1 = s + 1 < nw ? c.y : c.x, w2 = s + 2 < nw ? c.z : c.x, w3 = s + 3 < nw ? c.w : c.x;
@@ -233,11 +251,20 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
         pr_wall2<D, PER>(C, pi, vi, a2, a3, n2, n3, V23, DQ, g0, g1, g2, inv_c0sq);
       }
     }
+  }
+  // per-lane compensated sums, then the group total (all lanes take part in the shuffles)
+  float ax = (C.sx.x + C.nx.x) + (C.sx.y + C.nx.y);
+  float ay = (C.sy.x + C.ny.x) + (C.sy.y + C.ny.y);
+  float az = (C.sz.x + C.nz.x) + (C.sz.y + C.nz.y);
+  if (TPP > 1) {
+    ax = group_sum<TPP>(ax);
+    ay = group_sum<TPP>(ay);
+    if (D == 3) az = group_sum<TPP>(az);
+  }
+  const bool writer = valid && sub == 0;
+  if (writer) {
     // dv/dt = acc_prior + g - (2/rho_i) sum V_j P* grad_i W_ij
     const float sc = -2.0f / C.rho_i;
-    const float ax = (C.sx.x + C.nx.x) + (C.sx.y + C.nx.y);
-    const float ay = (C.sy.x + C.ny.x) + (C.sy.y + C.ny.y);
-    const float az = (C.sz.x + C.nz.x) + (C.sz.y + C.nz.y);
     const float4 ap = acc_prior ? acc_prior[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float a0 = ap.x + I.g[0] + sc * ax;
     const float a1 = ap.y + I.g[1] + sc * ay;
@@ -258,7 +285,7 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
     v2 = vn.x * vn.x + vn.y * vn.y + vn.z * vn.z;
     if (!isfinite(v2)) raise_error(g, ERR_NAN, i);
   }
-  reduce_vmax(v2, valid, k, uni, ctrl);
+  reduce_vmax(v2, writer, k, uni, ctrl);
 }
 
 // ---------------------------------------------------------------- density relaxation ---
@@ -311,76 +338,86 @@ __device__ __forceinline__ void dr_wall2(DrCtx& C, const int4& pi, const float4&
   kahan2(C.s, C.nc, mul2(Vw, sub2(Us, UL)), mul2(G.fw, G.r));
 }
 
-template <int D, bool PER>
-__global__ void __launch_bounds__(kBlock, 2)
+template <int D, bool PER, int TPP>
+__global__ void __launch_bounds__(kMaxBlock, 1)
 k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __restrict__ VH,
                      int4* __restrict__ PS, float4* __restrict__ VS,
                      const float* __restrict__ mass, const int* __restrict__ inst_of,
                      const Inst* __restrict__ inst, const Ctrl* __restrict__ ctrl,
                      const int* __restrict__ nbr, const uint32_t* __restrict__ nbc,
                      const int4* __restrict__ WP, const float4* __restrict__ WN, Global* g) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int k = inst_index(inst_of, i);
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+  const int sub = TPP > 1 ? (int)(threadIdx.x % TPP) : 0;
+  if (TPP == 1 && i >= n) return;                     // no group shuffles to take part in
+  bool valid = i < n;
+  const int k = valid ? inst_index(inst_of, i) : 0;
   const double dtd = ctrl[k].dt;
-  if (dtd == 0.0) return;
+  if (TPP == 1 && dtd == 0.0) return;
+  if (dtd == 0.0) valid = false;
   const Inst& I = inst[k];
   DrCtx C;
-  C.hdt = 0.5f * (float)dtd;
-  C.inv_h = I.inv_h;
-  C.dwr = I.dwr_a;
-  C.rho0 = I.rho0;
-  C.c0 = I.c0;
-  C.px = PER ? I.period[0] : 0;
-  C.py = PER ? I.period[1] : 0;
-  C.pz = PER ? I.period[2] : 0;
   C.s = C.nc = f2(0.f);
-  const int4 pi = PH[i];
-  const float4 vi = VH[i];                            // v^{n+1}
-  C.dev_i = i2f(pi.w);
-  C.rho_i = C.rho0 + C.dev_i;
-  const float2 DQ = f2(I.dq);
-  const uint32_t cnt = nbc[i];
-  const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
-  const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
-  const int nq = (nf + 3) >> 2;
-  int4 cur = nq ? nb4[i] : make_int4(0, 0, 0, 0);
-  for (int q = 0; q < nq; ++q) {
-    int4 nxt = cur;
-    if (q + 1 < nq) nxt = nb4[(int64_t)(q + 1) * n + i];
-    const int s = q << 2;
-    const int j0 = cur.x;
-    const int j1 = s + 1 < nf ? cur.y : (int)i;
-    const int j2 = s + 2 < nf ? cur.z : (int)i;
-    const int j3 = s + 3 < nf ? cur.w : (int)i;
-    const int4 p0 = PH[j0], p1 = PH[j1], p2 = PH[j2], p3 = PH[j3];
-    const float4 v0 = VH[j0], v1 = VH[j1], v2 = VH[j2], v3 = VH[j3];
-    float2 m01 = f2(I.mass), m23 = f2(I.mass);
-    if (mass) {
-      m01 = make_float2(mass[j0], mass[j1]);
-      m23 = make_float2(mass[j2], mass[j3]);
-    }
-    dr_fluid2<D, PER>(C, pi, vi, p0, p1, v0, v1, m01, DQ);
-    dr_fluid2<D, PER>(C, pi, vi, p2, p3, v2, v3, m23, DQ);
-    cur = nxt;
-  }
-  if (nw) {
-    const float g0 = I.g[0], g1 = I.g[1], g2 = I.g[2];
-    const float inv_c0sq = 1.0f / I.c0sq, pr_i = I.c0sq * C.dev_i;
-    const int q0 = wall_slot0(nf) >> 2, nwq = (nw + 3) >> 2;
-    for (int q = 0; q < nwq; ++q) {
-      const int4 c = nb4[(int64_t)(q0 + q) * n + i];
+  int4 pi = make_int4(0, 0, 0, 0);
+  float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
+  C.hdt = 0.5f * (float)dtd;
+  if (valid) {
+    C.inv_h = I.inv_h;
+    C.dwr = I.dwr_a;
+    C.rho0 = I.rho0;
+    C.c0 = I.c0;
+    C.px = PER ? I.period[0] : 0;
+    C.py = PER ? I.period[1] : 0;
+    C.pz = PER ? I.period[2] : 0;
+    pi = PH[i];
+    vi = VH[i];                                       // v^{n+1}
+    C.dev_i = i2f(pi.w);
+    C.rho_i = C.rho0 + C.dev_i;
+    const float2 DQ = f2(I.dq);
+    const uint32_t cnt = nbc[i];
+    const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
+    const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
+    const int nq = (nf + 3) >> 2;
+    int4 cur = sub < nq ? nb4[(int64_t)sub * n + i] : make_int4(0, 0, 0, 0);
+    for (int q = sub; q < nq; q += TPP) {
+      int4 nxt = cur;
+      if (q + TPP < nq) nxt = nb4[(int64_t)(q + TPP) * n + i];
       const int s = q << 2;
-      const int w1 = s + 1 < nw ? c.y : c.x, w2 = s + 2 < nw ? c.z : c.x, w3 = s + 3 < nw ? c.w : c.x;
-      const int4 a0 = WP[c.x], a1 = WP[w1], a2 = WP[w2], a3 = WP[w3];
-      const float4 n0 = WN[c.x], n1 = WN[w1], n2 = WN[w2], n3 = WN[w3];
-      const float2 V01 = make_float2(i2f(a0.w), s + 1 < nw ? i2f(a1.w) : 0.0f);
-      const float2 V23 = make_float2(s + 2 < nw ? i2f(a2.w) : 0.0f, s + 3 < nw ? i2f(a3.w) : 0.0f);
-      dr_wall2<D, PER>(C, pi, vi, a0, a1, n0, n1, V01, DQ, g0, g1, g2, inv_c0sq, pr_i);
-      dr_wall2<D, PER>(C, pi, vi, a2, a3, n2, n3, V23, DQ, g0, g1, g2, inv_c0sq, pr_i);
+      const int j0 = cur.x;
+      const int j1 = s + 1 < nf ? cur.y : (int)i;
+      const int j2 = s + 2 < nf ? cur.z : (int)i;
+      const int j3 = s + 3 < nf ? cur.w : (int)i;
+      const int4 p0 = PH[j0], p1 = PH[j1], p2 = PH[j2], p3 = PH[j3];
+      const float4 v0 = VH[j0], v1 = VH[j1], v2 = VH[j2], v3 = VH[j3];
+      float2 m01 = f2(I.mass), m23 = f2(I.mass);
+      if (mass) {
+        m01 = make_float2(mass[j0], mass[j1]);
+        m23 = make_float2(mass[j2], mass[j3]);
+      }
+      dr_fluid2<D, PER>(C, pi, vi, p0, p1, v0, v1, m01, DQ);
+      dr_fluid2<D, PER>(C, pi, vi, p2, p3, v2, v3, m23, DQ);
+      cur = nxt;
+    }
+    if (nw) {
+      const float g0 = I.g[0], g1 = I.g[1], g2 = I.g[2];
+      const float inv_c0sq = 1.0f / I.c0sq, pr_i = I.c0sq * C.dev_i;
+      const int q0 = wall_slot0(nf) >> 2, nwq = (nw + 3) >> 2;
+      for (int q = sub; q < nwq; q += TPP) {
+        const int4 c = nb4[(int64_t)(q0 + q) * n + i];
+        const int s = q << 2;
+        const int w1 = s + 1 < nw ? c.y : c.x, w2 = s + 2 < nw ? c.z : c.x, w3 = s + 3 < nw ? c.w : c.x;
+        const int4 a0 = WP[c.x], a1 = WP[w1], a2 = WP[w2], a3 = WP[w3];
+        const float4 n0 = WN[c.x], n1 = WN[w1], n2 = WN[w2], n3 = WN[w3];
+        const float2 V01 = make_float2(i2f(a0.w), s + 1 < nw ? i2f(a1.w) : 0.0f);
+        const float2 V23 = make_float2(s + 2 < nw ? i2f(a2.w) : 0.0f, s + 3 < nw ? i2f(a3.w) : 0.0f);
+        dr_wall2<D, PER>(C, pi, vi, a0, a1, n0, n1, V01, DQ, g0, g1, g2, inv_c0sq, pr_i);
+        dr_wall2<D, PER>(C, pi, vi, a2, a3, n2, n3, V23, DQ, g0, g1, g2, inv_c0sq, pr_i);
+      }
     }
   }
-  const float drho = 2.0f * C.rho_i * ((C.s.x + C.nc.x) + (C.s.y + C.nc.y));
+  float sum = (C.s.x + C.nc.x) + (C.s.y + C.nc.y);
+  if (TPP > 1) sum = group_sum<TPP>(sum);
+  if (!valid || sub != 0) return;
+  const float drho = 2.0f * C.rho_i * sum;
   const float dev_n = C.dev_i + C.hdt * drho;         // Eq. verlet-first-final (density)
   const float hdt = C.hdt;
   int qx = pi.x + __float2int_rn(hdt * vi.x * I.inv_dq);
@@ -396,37 +433,56 @@ k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __res
   VS[i] = make_float4(vi.x, vi.y, vi.z, drho);
 }
 
-template <typename K2P, typename K2N, typename K3P, typename K3N, typename... A>
-void dispatch(const Buffers& b, cudaStream_t s, K2P k2p, K2N k2n, K3P k3p, K3N k3n, A... args) {
-  const unsigned grid = grid_for(b.n);
-  if (b.dim == 2) {
-    if (b.any_periodic) k2p<<<grid, kBlock, 0, s>>>(args...);
-    else k2n<<<grid, kBlock, 0, s>>>(args...);
-  } else {
-    if (b.any_periodic) k3p<<<grid, kBlock, 0, s>>>(args...);
-    else k3n<<<grid, kBlock, 0, s>>>(args...);
-  }
+// Launch variants: (threads per particle, block size) per kernel, indexed by kTpp / kBlk.
+template <int D, bool PER>
+void launch_pr(int tpp, int block, const Buffers& b, cudaStream_t s) {
+  const unsigned grid = grid_for(b.n * tpp, block);
+#define SPH_PR_ARGS b.n, (const int4*)b.PS, (const float4*)b.VS, b.PH, b.VH, (const float*)b.mass, \
+    b.inst_of, (const Inst*)b.inst, b.ctrl, (const int*)b.nbr, (const uint32_t*)b.nbc,                 \
+    (const int4*)b.WP, (const float4*)b.WN, (const float4*)b.acc_prior, b.acc_keep, b.glob
+  if (tpp == 4) k_pressure_relaxation<D, PER, 4><<<grid, block, 0, s>>>(SPH_PR_ARGS);
+  else if (tpp == 2) k_pressure_relaxation<D, PER, 2><<<grid, block, 0, s>>>(SPH_PR_ARGS);
+  else k_pressure_relaxation<D, PER, 1><<<grid, block, 0, s>>>(SPH_PR_ARGS);
+#undef SPH_PR_ARGS
+}
+
+template <int D, bool PER>
+void launch_dr(int tpp, int block, const Buffers& b, cudaStream_t s) {
+  const unsigned grid = grid_for(b.n * tpp, block);
+#define SPH_DR_ARGS b.n, (const int4*)b.PH, (const float4*)b.VH, b.PS, b.VS, (const float*)b.mass, \
+    b.inst_of, (const Inst*)b.inst, (const Ctrl*)b.ctrl, (const int*)b.nbr, (const uint32_t*)b.nbc,   \
+    (const int4*)b.WP, (const float4*)b.WN, b.glob
+  if (tpp == 4) k_density_relaxation<D, PER, 4><<<grid, block, 0, s>>>(SPH_DR_ARGS);
+  else if (tpp == 2) k_density_relaxation<D, PER, 2><<<grid, block, 0, s>>>(SPH_DR_ARGS);
+  else k_density_relaxation<D, PER, 1><<<grid, block, 0, s>>>(SPH_DR_ARGS);
+#undef SPH_DR_ARGS
 }
 
 }  // namespace
 
 void launch_pressure_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches) {
   if (b.n == 0) return;
-  dispatch(b, s, k_pressure_relaxation<2, true>, k_pressure_relaxation<2, false>,
-           k_pressure_relaxation<3, true>, k_pressure_relaxation<3, false>, b.n, (const int4*)b.PS,
-           (const float4*)b.VS, b.PH, b.VH, (const float*)b.mass, b.inst_of, (const Inst*)b.inst, b.ctrl,
-           (const int*)b.nbr, (const uint32_t*)b.nbc, (const int4*)b.WP, (const float4*)b.WN,
-           (const float4*)b.acc_prior, b.acc_keep, b.glob);
+  const int tpp = b.cfg.pr_tpp, block = b.cfg.pr_block;
+  if (b.dim == 2) {
+    if (b.any_periodic) launch_pr<2, true>(tpp, block, b, s);
+    else launch_pr<2, false>(tpp, block, b, s);
+  } else {
+    if (b.any_periodic) launch_pr<3, true>(tpp, block, b, s);
+    else launch_pr<3, false>(tpp, block, b, s);
+  }
   ++*launches;
 }
 
 void launch_density_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches) {
   if (b.n == 0) return;
-  dispatch(b, s, k_density_relaxation<2, true>, k_density_relaxation<2, false>,
-           k_density_relaxation<3, true>, k_density_relaxation<3, false>, b.n, (const int4*)b.PH,
-           (const float4*)b.VH, b.PS, b.VS, (const float*)b.mass, b.inst_of, (const Inst*)b.inst,
-           (const Ctrl*)b.ctrl, (const int*)b.nbr, (const uint32_t*)b.nbc, (const int4*)b.WP,
-           (const float4*)b.WN, b.glob);
+  const int tpp = b.cfg.dr_tpp, block = b.cfg.dr_block;
+  if (b.dim == 2) {
+    if (b.any_periodic) launch_dr<2, true>(tpp, block, b, s);
+    else launch_dr<2, false>(tpp, block, b, s);
+  } else {
+    if (b.any_periodic) launch_dr<3, true>(tpp, block, b, s);
+    else launch_dr<3, false>(tpp, block, b, s);
+  }
   ++*launches;
 }
 

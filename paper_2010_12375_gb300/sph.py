@@ -33,6 +33,7 @@ EXPORTS = [
     "sph_diagnostics", "sph_get_state", "sph_set_state", "sph_get_acceleration",
     "sph_get_permutation", "sph_get_neighbours", "sph_pair_count", "sph_kernel_launches",
     "sph_set_kernel_timing", "sph_kernel_times", "sph_diagnostics_noalloc",
+    "sph_get_launch_config", "sph_set_launch_config", "sph_autotune",
 ]
 
 
@@ -119,6 +120,9 @@ def load():
         "sph_kernel_times": (i32, [P, ctypes.POINTER(dbl), ctypes.POINTER(i64)]),
         "sph_diagnostics_noalloc": (i32, [ctypes.POINTER(SphParams), i64, P, P, P, P,
                                           ctypes.POINTER(SphDiag), P]),
+        "sph_get_launch_config": (i32, [P, ctypes.POINTER(i32)]),
+        "sph_set_launch_config": (i32, [P, ctypes.POINTER(i32)]),
+        "sph_autotune": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(dbl), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -324,6 +328,29 @@ def sph_kernel_times(h):
     cnt = (ctypes.c_int64 * 2)()
     check(lib, h, lib.sph_kernel_times(h, ms, cnt))
     return list(ms), list(cnt)
+
+
+def sph_get_launch_config(h):
+    lib = load()
+    cfg = (ctypes.c_int32 * 4)()
+    check(lib, h, lib.sph_get_launch_config(h, cfg))
+    return list(cfg)
+
+
+def sph_set_launch_config(h, cfg):
+    lib = load()
+    arr = (ctypes.c_int32 * 4)(*[int(c) for c in cfg])
+    check(lib, h, lib.sph_set_launch_config(h, arr))
+
+
+def sph_autotune(h, stream=None):
+    """Tune the relaxation kernels' launch variants during one advection step; returns
+    (cfg, times[kernel][tpp][block] in ms)."""
+    lib = load()
+    cfg = (ctypes.c_int32 * 4)()
+    ms = (ctypes.c_double * 18)()
+    check(lib, h, lib.sph_autotune(h, cfg, ms, _stream(stream)))
+    return list(cfg), np.array(ms[:]).reshape(2, 3, 3)
 
 
 def sph_diagnostics_noalloc(params: SphParams, pos, vel, rho, mass, stream=None):

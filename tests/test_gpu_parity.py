@@ -424,3 +424,72 @@ def test_full_size_3d_first_substep_sampled(sph):
           f"dv/dt {rel_l2(acc_gpu[samples], dvdt[local]):.2e} v {rel_l2(vel_gpu[samples], half.v[local]):.2e}")
     assert rel_l2(acc_gpu[samples], dvdt[local]) < 1e-4
     assert rel_l2(vel_gpu[samples], half.v[local]) < REL_L2_TOL
+
+
+# ------------------------------------------------------------------ launch variants / autotuner
+@pytest.mark.parametrize("cfg", [[2, 128, 4, 512], [4, 512, 2, 128], [1, 512, 1, 128]])
+@pytest.mark.parametrize("case", ["dam3d", "tg"])
+def test_launch_variants_match_oracle(sph, case, cfg):
+    prob, vel_amp, rho_amp = _substep_case(case)
+    prob = _with_walls_on_grid(prob)
+    x, v, rho, drho = perturbed_state(prob, 13, vel_amp, rho_amp)
+    x = x + np.random.default_rng(14).uniform(-0.1, 0.1, size=x.shape) * prob.dp
+    if np.any(prob.periodic[:prob.dim]):
+        x = np.mod(x, 1.0)
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    if prm.free_surface:
+        st.x = x
+        rho = np.maximum(rho, o.density_summation(st, w, o.neighbour_sets(x, w.x, prm), prm)) + 1e-5
+    xq, v32, rho32, d32 = representable(prob, x, v, rho, drho)
+    sim = sph.Simulation(prob, flags=sph.SPH_FLAG_KEEP_ACC)
+    sph.sph_set_launch_config(sim.handle, cfg)
+    assert sph.sph_get_launch_config(sim.handle) == cfg
+    sim.set_state(xq, v32, rho32, d32, t=0.0)
+    sim.build_cells()
+    sim.advection_step()
+    sim.acoustic_substep()
+    acc_gpu = sim.acceleration()
+    _, vel_gpu, rho_gpu, _ = sim.state()
+    sim.close()
+    st = o.State(xq, v32, rho32, d32, np.asarray(prob.mass, dtype=np.float64), 0.0)
+    nb = o.neighbour_sets_quantised(st.x, w.x, prm)
+    Dt = o.dt_advection(st.v, prm)
+    st.rho = o.density_summation(st, w, nb, prm)
+    acc_prior = o.viscous_acceleration(st, nb, prm)
+    dt = min(o.dt_acoustic(st.v, prm), Dt)
+    half, dvdt = o.pressure_relaxation(st, w, nb, acc_prior, dt, prm)
+    out = o.density_relaxation(half, w, nb, dt, prm)
+    assert rel_l2(acc_gpu, dvdt) < REL_L2_TOL
+    assert rel_l2(vel_gpu, out.v) < REL_L2_TOL
+    assert rel_l2(rho_gpu, out.rho) < REL_L2_TOL
+
+
+def test_invalid_launch_config_is_rejected(sph):
+    sim = sph.Simulation(wk.dam_break_2d(n_per_H=10))
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_set_launch_config(sim.handle, [3, 256, 1, 256])
+    assert e.value.code == sph.SPH_E_INVALID
+    sim.close()
+
+
+def test_autotune_chooses_caches_and_equals_a_plain_step(sph, tmp_path, monkeypatch):
+    monkeypatch.setenv("SPH_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    prob = wk.dam_break_3d(24)
+    a = sph.Simulation(prob)
+    cfg, times = sph.sph_autotune(a.handle)
+    assert cfg[0] in (1, 2, 4) and cfg[1] in (128, 256, 512)
+    assert np.all(times > 0)
+    assert abs(times[0].min() - times[0][[1, 2, 4].index(cfg[0])][[128, 256, 512].index(cfg[1])]) < 1e-12
+    text = (tmp_path / "tune.json").read_text()
+    assert "|d3|" in text and ",".join(map(str, cfg)) in text
+    # a new handle for the same problem size picks the cached choice up
+    b = sph.Simulation(prob)
+    assert sph.sph_get_launch_config(b.handle) == cfg
+    # the tuned step is an ordinary advection step with the chosen variants
+    b.step(1)
+    for u, v in zip(a.state(), b.state()):
+        np.testing.assert_array_equal(u, v)
+    assert a.diagnostics()["substeps"] == b.diagnostics()["substeps"]
+    a.close()
+    b.close()
