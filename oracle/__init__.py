@@ -8,4 +8,4 @@ library; both are fed from the seeded input generators alone.
 Every function follows the paper's equations in the paper's order (cited per
 function). Parity status per function is listed in `oracle.wcsph`'s header.
 """
-from . import wcsph  # noqa: F401
+from . import mpnn, wcsph  # noqa: F401
