@@ -339,6 +339,9 @@ def run_workload(args):
     from paper_2010_12375_gb300 import sph, workloads as wk
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
+    if args.workload == "learned":
+        run_learned(args, stream)
+        return
     if args.workload == "batched":
         problems = wk.batched_dam_breaks(256)
         name = "256 independent 2D dam breaks (2k-50k fluid each), one handle"
@@ -384,6 +387,41 @@ def run_workload(args):
     print(json.dumps(out), flush=True)
 
 
+def run_learned(args, stream):
+    """Train the learned stand-in on solver trajectories of 200 seeded tanks, then step the
+    2D dam break at 100,128 particles with it (fallback on) and without it."""
+    import torch
+    from paper_2010_12375_gb300 import learned, sph, workloads as wk
+    t0 = time.perf_counter()
+    tanks = learned.training_tanks(n_tanks=200, n_per_H=40)
+    data = learned.record(tanks, steps=300, every=30, stream=stream)
+    t_rec = time.perf_counter() - t0
+    net = sph.sph_learned_create(2, learned.initial_weights(2, seed=0))
+    t0 = time.perf_counter()
+    losses = learned.train(net, data, epochs=3, lr=2e-3, lr_final=2e-4, stream=stream)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    prob = wk.learned_dam_break()
+    runs = {}
+    for name, drift in (("per_step_drift_0.5pct", 0.005), ("per_step_drift_0.01pct", 0.0001)):
+        runs[name] = learned.compare_stepping(net, prob, steps=args.steps, max_mean_rho_dev=0.01,
+                                              max_energy_drift=drift, stream=stream)
+    best = min(runs.values(), key=lambda r: r["energy_rel_diff"])
+    out = {"metric": "learned vs plain advection steps, 2D dam break 100,128 particles",
+           "unit": "speedup (plain ms per step / learned ms per step)", "value": best["speedup"],
+           "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "dtype": "bf16 network, f32 solver",
+           "data": "synthetic",
+           "config": {"workload": f"2D dam break H=1, L=2, {prob.n_fluid} fluid particles",
+                      "training": f"{len(data.samples)} pairs from 200 seeded tanks (H ~ U(0.5,1.5), "
+                                  f"L/H ~ U(1,3), dp = H/40), 3 epochs of Adam",
+                      "record_s": t_rec, "train_s": t_train, "train_steps": len(losses),
+                      "loss_first_epoch": float(np.mean(losses[:len(data.samples)])),
+                      "loss_last_epoch": float(np.mean(losses[-len(data.samples):]))},
+           "runs": runs}
+    sph.sph_learned_destroy(net)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,7 +434,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg"],
+    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned"],
                     help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()
     if args.warmup < 3:

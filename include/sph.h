@@ -232,6 +232,50 @@ int sph_kernel_launches(sph_handle* h, int64_t* out);
 int sph_set_kernel_timing(sph_handle* h, int32_t enable);
 int sph_kernel_times(sph_handle* h, double* ms, int64_t* launches);
 
+/* ---- learned stand-in for the acoustic substeps ------------------------------------ */
+/* A message-passing network over the frozen neighbour graph of an advection step that
+ * predicts each fluid particle's velocity and density change over the whole step (the
+ * paper has no learned component; this is the project's own addition). Definition:
+ * node input u_i = [v_i/c0, 100 (rho_i/rho0 - 1), Dt_ad c0/h, 1]; edge input
+ * x_ij = [r_ij/h, (v_i - v_j)/c0, 100 dev_i, 100 dev_j, wall] over fluid and wall
+ * neighbours (walls: v_j = 0, dev_j = 0); h_i = relu(W_enc u_i); three rounds with shared
+ * weights of z_ij = relu(W_e1 [x_ij, h_j, 1]), m_ij = W_e2 [z_ij, 1],
+ * a_i = (1/NBAR) sum_j m_ij (NBAR = 20 in 2D, 80 in 3D), h_i += W_n2 [relu(W_n1 [h_i, a_i, 1]), 1];
+ * output y_i = W_d2 [relu(W_d1 [h_i, 1]), 1], whose first dim + 1 entries are
+ * [(dv_i - g Dt_ad)/V_S, 100 drho_i/rho0] with V_S = |g| Dt_ad (u_ref when g = 0). Every
+ * matrix product rounds both operands to
+ * bfloat16 and accumulates in FP32 on the tensor cores. Weights: 32,000 floats, matrices
+ * enc (64x16), e1 (64x80), e2 (64x80), n1 (64x144), n2 (64x80), d1 (64x80), d2 (16x80),
+ * each row-major with inputs zero-padded and the bias in the column after the inputs. */
+typedef struct sph_learned sph_learned;
+
+int sph_learned_weight_count(int64_t* count);
+/* weights: host or device, 32,000 floats (NULL = zeros). */
+int sph_learned_create(int32_t dim, const float* weights, sph_learned** out);
+void sph_learned_destroy(sph_learned* net);
+const char* sph_learned_last_error(const sph_learned* net);
+/* Replace the weights (resets the Adam moments) / read them (host or device pointer). */
+int sph_learned_set_weights(sph_learned* net, const float* weights);
+int sph_learned_get_weights(sph_learned* net, float* weights);
+/* Network output for the handle's current state, which must be the start of an advection
+ * step (sph_build_cells then sph_advection_step). y: [n_fluid * (dim+1)] double, id order,
+ * host or device (may be NULL). Synchronous. */
+int sph_learned_predict(sph_handle* h, sph_learned* net, double* y, void* stream);
+/* One training step on the handle's current state (as for predict): forward, mean squared
+ * error against target [n_fluid * (dim+1)] (id order, host or device), hand-written
+ * backward and, if lr > 0, one Adam step (beta 0.9/0.999, eps 1e-8) on FP32 master
+ * weights. loss_out and grad_out (32,000 floats, host or device) may be NULL. */
+int sph_learned_train_step(sph_handle* h, sph_learned* net, const double* target, double lr,
+                           double* loss_out, float* grad_out, void* stream);
+/* One advection step with the network in place of the acoustic substeps: build cells,
+ * Dt_ad and density re-initialisation, prediction, then v += g Dt_ad + V_S y_v,
+ * rho += rho0 y_rho/100, r += Dt_ad (v + v')/2. If afterwards any tank's mean
+ * |rho/rho0 - 1| exceeds max_mean_rho_dev or its energy changed by more than
+ * max_energy_drift (relative), the step is undone and the plain acoustic substeps run
+ * instead. *used_learned = 1 when the network's step was kept. Synchronous. */
+int sph_learned_step(sph_handle* h, sph_learned* net, double max_mean_rho_dev,
+                     double max_energy_drift, int32_t* used_learned, void* stream);
+
 /* Allocation-free diagnostics. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory (code running inside
  * another framework's device memory pool or under a fixed device-memory budget,

@@ -21,12 +21,13 @@ are zero-padded to the matrix widths K below):
                h_i += W_n2 [relu(W_n1 [h_i, a_i, 1]), 1]   (K = 144, 80)
   decoder      y_i = W_d2 [relu(W_d1 [h_i, 1]), 1]     (K = 80, 80; the first d + 1 of its
                                                        16 output rows are used)
-  targets      y_i = [(dv_i - g dt_ad) / U_ref, S_RHO drho_i / rho0]
+  targets      y_i = [(dv_i - g dt_ad) / V_S, S_RHO drho_i / rho0], V_S = |g| dt_ad
+               (U_ref when g = 0): the velocity change is measured in units of gravity's
   loss         mean over particles and outputs of (y_i - target_i)^2
 Every matrix product rounds both operands to bfloat16 (round to nearest even) and
 accumulates exactly; backward treats the rounding as the identity. With `bf16=False`
 the network is plain FP64 (used for the finite-difference pin). Weights are stored in the
-order enc, e1, e2, n1, n2, d1, d2, each row-major (outputs x padded inputs): 32,384 floats.
+order enc, e1, e2, n1, n2, d1, d2, each row-major (outputs x padded inputs): 32,000 floats.
 """
 from __future__ import annotations
 
@@ -232,10 +233,15 @@ def backward(W, g: Graph, cache, Y, T, q: bool = True):
     return dW
 
 
+def velocity_scale(gravity, dt_ad, u_ref):
+    g = float(np.linalg.norm(np.asarray(gravity, dtype=np.float64)))
+    return g * dt_ad if g > 0.0 else u_ref
+
+
 def targets(dim, vel0, vel1, rho0_arr, rho1_arr, gravity, dt_ad, u_ref, rho0):
     """Normalised targets of one advection step (see the module header)."""
     T = np.zeros((vel0.shape[0], dim + 1))
-    T[:, :dim] = (vel1 - vel0 - np.asarray(gravity)[:dim] * dt_ad) / u_ref
+    T[:, :dim] = (vel1 - vel0 - np.asarray(gravity)[:dim] * dt_ad) / velocity_scale(gravity, dt_ad, u_ref)
     T[:, dim] = S_RHO * (rho1_arr - rho0_arr) / rho0
     return T
 

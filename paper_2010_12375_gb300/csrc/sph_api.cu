@@ -15,6 +15,7 @@
 #include <sys/types.h>
 
 #include "sph.h"
+#include "sph_handle.h"
 #include "sph_kernels.h"
 
 const char* sph_noalloc_last_error();   // message of the last failed handle-less call (sph_noalloc.cu)
@@ -24,35 +25,6 @@ using sph::Ctrl;
 using sph::Global;
 using sph::Inst;
 
-struct sph_handle {
-  Buffers b;
-  std::vector<sph_params> params;
-  std::vector<Inst> hinst;
-  uint32_t flags = 0;
-  std::string err;
-  std::vector<void*> allocs;
-  int64_t device_bytes = 0;
-  int64_t launches = 0;            // kernels launched directly by the host
-  int64_t graph_kernels = 0;       // kernels executed by graph launches
-  // graph of one advection step
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  cudaGraphConditionalHandle cond = 0;
-  int64_t graph_fixed = 0, graph_body = 0;
-  cudaStream_t cap_stream = nullptr;
-  // staging and host mirrors
-  double* stage = nullptr;
-  size_t stage_elems = 0;
-  double* diag_scratch = nullptr;
-  double* diag_out = nullptr;
-  Global* hglob = nullptr;         // pinned host mirror of the device status
-  // kernel timing
-  bool timing = false;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-  double ms[2] = {0.0, 0.0};
-  int64_t timed[2] = {0, 0};
-  bool cells_valid = false;
-};
 
 namespace {
 
@@ -433,6 +405,8 @@ void drop_graph(sph_handle* h) {
 }
 
 }  // namespace
+
+int sph_sync_status(sph_handle* h, cudaStream_t s) { return sync_status(h, s); }
 
 extern "C" {
 

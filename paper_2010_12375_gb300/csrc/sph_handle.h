@@ -1,0 +1,40 @@
+// Library-side definition of the opaque sph_handle (shared by the C-ABI translation units).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "sph.h"
+#include "sph_kernels.h"
+
+struct sph_handle {
+  sph::Buffers b;
+  std::vector<sph_params> params;
+  std::vector<sph::Inst> hinst;
+  uint32_t flags = 0;
+  std::string err;
+  std::vector<void*> allocs;
+  int64_t device_bytes = 0;
+  int64_t launches = 0;            // kernels launched directly by the host
+  int64_t graph_kernels = 0;       // kernels executed by graph launches
+  // graph of one advection step
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  int64_t graph_fixed = 0, graph_body = 0;
+  cudaStream_t cap_stream = nullptr;
+  // staging and host mirrors
+  double* stage = nullptr;
+  size_t stage_elems = 0;
+  double* diag_scratch = nullptr;
+  double* diag_out = nullptr;
+  sph::Global* hglob = nullptr;         // pinned host mirror of the device status
+  // kernel timing
+  bool timing = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  double ms[2] = {0.0, 0.0};
+  int64_t timed[2] = {0, 0};
+  bool cells_valid = false;
+};
+
+// Host-side helpers of sph_api.cu used by the other C-ABI translation units.
+int sph_sync_status(sph_handle* h, cudaStream_t s);

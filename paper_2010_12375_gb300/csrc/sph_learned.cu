@@ -1,0 +1,887 @@
+// Learned stand-in for the acoustic substeps of an advection step.
+//
+// A message-passing network over the frozen neighbour graph of the step predicts each
+// fluid particle's velocity and density change over Dt_ad (the network is the project's
+// own; the paper has none). Definition, shared with the FP64 reference (oracle/mpnn.py):
+//   u_i  = [v_i/c0, 100 (rho_i/rho0 - 1), Dt_ad c0/h, 1]                      K = 16
+//   x_ij = [r_ij/h, (v_i - v_j)/c0, 100 dev_i, 100 dev_j, wall]  (walls: v_j = 0, dev_j = 0)
+//   h_i  = relu(W_enc u_i)
+//   3 rounds, shared weights:
+//     z_ij = relu(W_e1 [x_ij, h_j, 1])     m_ij = W_e2 [z_ij, 1]            K = 80, 80
+//     a_i  = (1/NBAR) sum_j m_ij           h_i += W_n2 [relu(W_n1 [h_i, a_i, 1]), 1]   K = 144, 80
+//   y_i  = W_d2 [relu(W_d1 [h_i, 1]), 1]                                     K = 80, 80
+//   targets [(dv_i - g Dt_ad)/V_S, 100 drho_i/rho0], V_S = |g| Dt_ad (U_ref when g = 0),
+//   loss = mean squared error.
+// Every product rounds its operands to bfloat16 and accumulates in FP32 on the tensor
+// cores (mma.sync m16n8k16). These layers are skinny (64 outputs, K <= 144: ~34 FLOP per
+// byte moved, far below the tensor-core ridge of ~285), so they are bound by HBM and the
+// warp-level MMA is not their limiter. Weight gradients are summed per block and then over
+// blocks in a fixed order (deterministic); node-embedding gradients of the gather are
+// scattered with FP32 atomics.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sph.h"
+#include "sph_handle.h"
+#include "sph_kernels.h"
+
+using bf16 = __nv_bfloat16;
+
+namespace sph {
+namespace learned {
+
+constexpr int F = 64;
+constexpr int ROUNDS = 3;
+constexpr float S_RHO = 100.0f;
+enum { L_ENC = 0, L_E1, L_E2, L_N1, L_N2, L_D1, L_D2, L_COUNT };
+constexpr int kRows[L_COUNT] = {64, 64, 64, 64, 64, 64, 16};
+constexpr int kCols[L_COUNT] = {16, 80, 80, 144, 80, 80, 80};
+__constant__ int c_rows[L_COUNT] = {64, 64, 64, 64, 64, 64, 16};
+__constant__ int c_cols[L_COUNT] = {16, 80, 80, 144, 80, 80, 80};
+constexpr int kWeights = 32000;
+constexpr int kTile = 64;                 // rows per dense block (4 warps x 16)
+constexpr int kDwRows = 2048;             // rows per weight-gradient block
+
+inline int w_offset(int l) {
+  int o = 0;
+  for (int k = 0; k < l; ++k) o += kRows[k] * kCols[k];
+  return o;
+}
+
+inline float nbar(int dim) { return dim == 2 ? 20.0f : 80.0f; }
+
+__device__ __forceinline__ uint32_t ld_u32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma16816(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// ------------------------------------------------------------------ dense forward
+// Y = X W^T for M rows. X bf16 [M x K] (row stride ldx), W bf16 [NO x K] row-major. Epilogue
+// per element (m, n < NO): y = acc; y = 0 where mask[m, n] <= 0 (ReLU backward) if mask;
+// y = max(y, 0) if relu; out_f32[m, n] = y (or += y with accum) for n < nf_store;
+// out_b[m, col0 + n] = bf16(y) for n < nb_store.
+template <int NO>
+__global__ void __launch_bounds__(128)
+k_dense(int64_t M, int K, const bf16* __restrict__ X, int ldx, const bf16* __restrict__ W,
+        float* __restrict__ out_f32, int ldf, int nf_store, int accum, bf16* __restrict__ out_b, int ldo,
+        int col0, int nb_store, int relu, const bf16* __restrict__ mask, int ldm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LD = K + 8;                       // padded row: conflict-free fragment loads
+  bf16* sW = reinterpret_cast<bf16*>(smem_raw);
+  bf16* sX = sW + NO * LD;
+  const int64_t m0 = (int64_t)blockIdx.x * kTile;
+  for (int idx = threadIdx.x; idx < NO * K / 2; idx += blockDim.x) {
+    const int r = (2 * idx) / K, c = (2 * idx) % K;
+    *reinterpret_cast<uint32_t*>(&sW[r * LD + c]) = ld_u32(&W[r * K + c]);
+  }
+  for (int idx = threadIdx.x; idx < kTile * K / 2; idx += blockDim.x) {
+    const int r = (2 * idx) / K, c = (2 * idx) % K;
+    const int64_t m = m0 + r;
+    *reinterpret_cast<uint32_t*>(&sX[r * LD + c]) = m < M ? ld_u32(&X[m * ldx + c]) : 0u;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float acc[NO / 8][4];
+#pragma unroll
+  for (int nt = 0; nt < NO / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+  const bf16* xr0 = sX + (warp * 16 + g) * LD;
+  const bf16* xr1 = xr0 + 8 * LD;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const uint32_t a0 = ld_u32(xr0 + k0 + 2 * t), a1 = ld_u32(xr1 + k0 + 2 * t);
+    const uint32_t a2 = ld_u32(xr0 + k0 + 2 * t + 8), a3 = ld_u32(xr1 + k0 + 2 * t + 8);
+#pragma unroll
+    for (int nt = 0; nt < NO / 8; ++nt) {
+      const bf16* wr = sW + (nt * 8 + g) * LD + k0 + 2 * t;
+      mma16816(acc[nt], a0, a1, a2, a3, ld_u32(wr), ld_u32(wr + 8));
+    }
+  }
+#pragma unroll
+  for (int nt = 0; nt < NO / 8; ++nt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t m = m0 + warp * 16 + g + 8 * h;
+      if (m >= M) continue;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int n = nt * 8 + 2 * t + e;
+        float y = acc[nt][2 * h + e];
+        if (mask) y = __bfloat162float(mask[m * ldm + n]) > 0.f ? y : 0.f;
+        if (relu) y = fmaxf(y, 0.f);
+        if (out_f32 && n < nf_store) {
+          if (accum) out_f32[m * ldf + n] += y;
+          else out_f32[m * ldf + n] = y;
+        }
+        if (out_b && n < nb_store) out_b[m * ldo + col0 + n] = __float2bfloat16_rn(y);
+      }
+    }
+}
+
+// ------------------------------------------------------------------ weight gradient
+// partial[block][no][k] = sum over this block's rows m of dY[m, no] X[m, k] (tensor cores,
+// the row index is the MMA reduction dimension).
+template <int NO>
+__global__ void __launch_bounds__(128)
+k_dense_dw(int64_t M, int K, const bf16* __restrict__ dY, int ldy, const bf16* __restrict__ X, int ldx,
+           float* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LDY = NO + 8, LDX = K + 8;
+  bf16* sY = reinterpret_cast<bf16*>(smem_raw);
+  bf16* sX = sY + kTile * LDY;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int mt_n = NO / 16, nt_n = K / 8, tiles = mt_n * nt_n;
+  constexpr int kMaxT = (NO / 16) * 18 / 4 + 1;   // K <= 144 -> at most 18 column tiles
+  float acc[kMaxT][4];
+#pragma unroll
+  for (int q = 0; q < kMaxT; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+  const int64_t r_begin = (int64_t)blockIdx.x * kDwRows;
+  const int64_t r_end = min(r_begin + (int64_t)kDwRows, M);
+  for (int64_t c0 = r_begin; c0 < r_end; c0 += kTile) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kTile * NO; idx += blockDim.x) {
+      const int r = idx / NO, c = idx % NO;
+      const int64_t m = c0 + r;
+      sY[r * LDY + c] = m < r_end ? dY[m * ldy + c] : __float2bfloat16_rn(0.f);
+    }
+    for (int idx = threadIdx.x; idx < kTile * K; idx += blockDim.x) {
+      const int r = idx / K, c = idx % K;
+      const int64_t m = c0 + r;
+      sX[r * LDX + c] = m < r_end ? X[m * ldx + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int ks = 0; ks < kTile; ks += 16) {
+      int q = 0;
+      for (int tile = warp; tile < tiles; tile += 4, ++q) {
+        const int mt = tile / nt_n, nt = tile % nt_n;
+        const int rr = ks + 2 * t;
+        const int c_lo = mt * 16 + g, c_hi = c_lo + 8;
+        const uint32_t a0 = pack2(sY[rr * LDY + c_lo], sY[(rr + 1) * LDY + c_lo]);
+        const uint32_t a1 = pack2(sY[rr * LDY + c_hi], sY[(rr + 1) * LDY + c_hi]);
+        const uint32_t a2 = pack2(sY[(rr + 8) * LDY + c_lo], sY[(rr + 9) * LDY + c_lo]);
+        const uint32_t a3 = pack2(sY[(rr + 8) * LDY + c_hi], sY[(rr + 9) * LDY + c_hi]);
+        const int kc = nt * 8 + g;
+        const uint32_t b0 = pack2(sX[rr * LDX + kc], sX[(rr + 1) * LDX + kc]);
+        const uint32_t b1 = pack2(sX[(rr + 8) * LDX + kc], sX[(rr + 9) * LDX + kc]);
+        mma16816(acc[q], a0, a1, a2, a3, b0, b1);
+      }
+    }
+  }
+  float* out = partial + (size_t)blockIdx.x * NO * K;
+  int q = 0;
+  for (int tile = warp; tile < tiles; tile += 4, ++q) {
+    const int mt = tile / nt_n, nt = tile % nt_n;
+    const int r0 = mt * 16 + g, col = nt * 8 + 2 * t;
+    out[r0 * K + col] = acc[q][0];
+    out[r0 * K + col + 1] = acc[q][1];
+    out[(r0 + 8) * K + col] = acc[q][2];
+    out[(r0 + 8) * K + col + 1] = acc[q][3];
+  }
+}
+
+// grad[o] += sum over blocks b (in order) of partial[b][o]
+__global__ void k_reduce_partials(int blocks, int count, const float* __restrict__ partial, float* __restrict__ grad) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= count) return;
+  float s = 0.f;
+  for (int b = 0; b < blocks; ++b) s += partial[(size_t)b * count + o];
+  grad[o] += s;
+}
+
+// ------------------------------------------------------------------ graph and features
+// Edge CSR of the frozen neighbour table: node i owns edges [off[i], off[i+1]), fluid
+// neighbours first, then walls; nbr >= 0 is a fluid slot, nbr < 0 encodes wall -1 - w.
+__global__ void k_edge_count(int64_t n, const uint32_t* __restrict__ nbc, uint32_t* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) cnt[i] = (nbc[i] & 0xffffu) + (nbc[i] >> 16);
+}
+
+template <int D>
+__global__ void k_features(int64_t n, const int4* __restrict__ P, const float4* __restrict__ V,
+                           const int* __restrict__ inst_of, const Inst* __restrict__ inst,
+                           const Ctrl* __restrict__ ctrl, const int* __restrict__ nbr,
+                           const uint32_t* __restrict__ nbc, const uint32_t* __restrict__ off,
+                           const int4* __restrict__ WP, int* __restrict__ esrc, int* __restrict__ enbr,
+                           bf16* __restrict__ U, bf16* XE0, bf16* XE1, bf16* XE2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = inst_of ? inst_of[i] : 0;
+  const Inst& I = inst[k];
+  const int4 pi = P[i];
+  const float4 vi = V[i];
+  const float inv_c0 = 1.0f / I.c0, inv_h = I.inv_h;
+  const float dev_i = i2f(pi.w) / I.rho0;
+  const float dt_ad = (float)ctrl[k].dt_ad;
+  bf16* u = U + i * 16;
+  const float uv[3] = {vi.x, vi.y, vi.z};
+  for (int c = 0; c < 16; ++c) u[c] = __float2bfloat16_rn(0.f);
+  for (int a = 0; a < D; ++a) u[a] = __float2bfloat16_rn(uv[a] * inv_c0);
+  u[D] = __float2bfloat16_rn(S_RHO * dev_i);
+  u[D + 1] = __float2bfloat16_rn(dt_ad * I.c0 * inv_h);
+  u[D + 2] = __float2bfloat16_rn(1.0f);
+  const uint32_t cnt = nbc[i];
+  const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
+  const int fe = 2 * D + 3;
+  uint32_t e = off[i];
+  for (int s = 0; s < nf + nw; ++s, ++e) {
+    const bool wall = s >= nf;
+    const int j = nbr[slot_index(n, i, wall ? wall_slot0(nf) + (s - nf) : s)];
+    const int4 pj = wall ? WP[j] : P[j];
+    float feat[9];
+    const int qi[3] = {pi.x, pi.y, pi.z}, qj[3] = {pj.x, pj.y, pj.z};
+    float vj[3] = {0.f, 0.f, 0.f};
+    float dev_j = 0.f;
+    if (!wall) {
+      const float4 v4 = V[j];
+      vj[0] = v4.x; vj[1] = v4.y; vj[2] = v4.z;
+      dev_j = i2f(pj.w) / I.rho0;
+    }
+    for (int a = 0; a < D; ++a) {
+      const float d = (float)wrap_diff(qi[a] - qj[a], I.period[a]) * I.dq;
+      feat[a] = d * inv_h;
+      feat[D + a] = (uv[a] - vj[a]) * inv_c0;
+    }
+    feat[2 * D] = S_RHO * dev_i;
+    feat[2 * D + 1] = S_RHO * dev_j;
+    feat[2 * D + 2] = wall ? 1.0f : 0.0f;
+    esrc[e] = (int)i;
+    enbr[e] = wall ? -1 - j : j;
+    bf16* rows[3] = {XE0 + (size_t)e * 80, XE1 + (size_t)e * 80, XE2 + (size_t)e * 80};
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < fe; ++c) rows[r][c] = __float2bfloat16_rn(feat[c]);
+      for (int c = fe; c < 80; ++c) rows[r][c] = __float2bfloat16_rn(0.f);
+      rows[r][fe + F] = __float2bfloat16_rn(1.0f);
+    }
+  }
+}
+
+// XE[e, fe + f] = bf16(h[nbr(e), f]) for fluid neighbours (walls keep 0)
+__global__ void k_gather_h(int64_t E, int fe, const int* __restrict__ enbr, const float* __restrict__ H,
+                           bf16* __restrict__ XE) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= E * F) return;
+  const int64_t e = idx / F;
+  const int f = (int)(idx % F);
+  const int j = enbr[e];
+  if (j >= 0) XE[e * 80 + fe + f] = __float2bfloat16_rn(H[(int64_t)j * F + f]);
+}
+
+// XN[i] = [bf16(h_i), bf16(a_i), 1], a_i = (1/nbar) sum over node i's edges of M
+__global__ void k_segsum(int64_t n, const uint32_t* __restrict__ off, const float* __restrict__ Mm,
+                         const float* __restrict__ H, float inv_nbar, bf16* __restrict__ XN) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  const int64_t i = idx / F;
+  const int f = (int)(idx % F);
+  float s = 0.f;
+  for (uint32_t e = off[i]; e < off[i + 1]; ++e) s += Mm[(int64_t)e * F + f];
+  XN[i * 144 + f] = __float2bfloat16_rn(H[i * F + f]);
+  XN[i * 144 + F + f] = __float2bfloat16_rn(s * inv_nbar);
+}
+
+__global__ void k_rows_bf16(int64_t n, int cols, const float* __restrict__ src, int lds, bf16* __restrict__ dst,
+                            int ldd) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * cols) return;
+  const int64_t r = idx / cols;
+  const int c = (int)(idx % cols);
+  dst[r * ldd + c] = __float2bfloat16_rn(src[r * lds + c]);
+}
+
+// constant columns of an activation buffer: column `one` = 1, [pad_from, ld) = 0
+__global__ void k_const_cols(int64_t rows, int ld, int one, int pad_from, bf16* __restrict__ A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  A[r * ld + one] = __float2bfloat16_rn(1.0f);
+  for (int c = pad_from; c < ld; ++c) A[r * ld + c] = __float2bfloat16_rn(0.f);
+}
+
+// loss and its gradient: dY = 2 (y - target) / (n (d+1)) on the first d+1 columns
+__global__ void k_loss(int64_t n, int dout, const float* __restrict__ Y, const double* __restrict__ T,
+                       const int* __restrict__ id, bf16* __restrict__ dY, double* __restrict__ loss) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (i < n) {
+    const int64_t row = id[i];
+    const double scale = 2.0 / ((double)n * dout);
+    for (int c = 0; c < 16; ++c) {
+      float gval = 0.f;
+      if (c < dout) {
+        const double d = (double)Y[i * 16 + c] - T[row * dout + c];
+        l += d * d;
+        gval = (float)(scale * d);
+      }
+      dY[i * 16 + c] = __float2bfloat16_rn(gval);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, l / ((double)n * dout));
+}
+
+// dh += dXN[:, :F]; dM[e] = bf16(dXN[src(e), F + f] / nbar)
+__global__ void k_node_back(int64_t n, const float* __restrict__ dXN, float* __restrict__ dH) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  const int64_t i = idx / F;
+  const int f = (int)(idx % F);
+  dH[i * F + f] += dXN[i * 144 + f];
+}
+
+__global__ void k_edge_back(int64_t E, const int* __restrict__ esrc, const float* __restrict__ dXN, float inv_nbar,
+                            bf16* __restrict__ dM) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= E * F) return;
+  const int64_t e = idx / F;
+  const int f = (int)(idx % F);
+  dM[e * F + f] = __float2bfloat16_rn(dXN[(int64_t)esrc[e] * 144 + F + f] * inv_nbar);
+}
+
+// dh[nbr(e)] += dXE[e, fe + f] for fluid neighbours (gather transpose)
+__global__ void k_scatter_dh(int64_t E, int fe, const int* __restrict__ enbr, const float* __restrict__ dXE,
+                             float* __restrict__ dH) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= E * F) return;
+  const int64_t e = idx / F;
+  const int f = (int)(idx % F);
+  const int j = enbr[e];
+  if (j >= 0) atomicAdd(&dH[(int64_t)j * F + f], dXE[e * 80 + fe + f]);
+}
+
+// dZ0 = bf16(dh * (h0 > 0))
+__global__ void k_relu_back(int64_t n, const float* __restrict__ dH, const float* __restrict__ H0,
+                            bf16* __restrict__ dZ) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * F) return;
+  dZ[idx] = __float2bfloat16_rn(H0[idx] > 0.f ? dH[idx] : 0.f);
+}
+
+// Adam (beta1 0.9, beta2 0.999, eps 1e-8); b1pow = beta1^t, b2pow = beta2^t
+__global__ void k_adam(int count, float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, float lr, float b1pow, float b2pow) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= count) return;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  m[o] = b1 * m[o] + (1.f - b1) * g[o];
+  v[o] = b2 * v[o] + (1.f - b2) * g[o] * g[o];
+  const float mh = m[o] / (1.f - b1pow), vh = v[o] / (1.f - b2pow);
+  w[o] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// bf16 copies of the weights: row-major and, per matrix, transposed
+__global__ void k_weights_bf16(const float* __restrict__ w, bf16* __restrict__ wb, bf16* __restrict__ wbt) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= kWeights) return;
+  int base = 0, l = 0;
+  while (l < L_COUNT - 1 && o >= base + c_rows[l] * c_cols[l]) {
+    base += c_rows[l] * c_cols[l];
+    ++l;
+  }
+  const int r = (o - base) / c_cols[l], c = (o - base) % c_cols[l];
+  const bf16 b = __float2bfloat16_rn(w[o]);
+  wb[o] = b;
+  wbt[base + c * c_rows[l] + r] = b;
+}
+
+// Apply a prediction: v' = v + g Dt_ad + V_S y_v, rho' = rho + rho0 y_rho / 100,
+// r' = r + Dt_ad (v + v')/2, d rho/dt = (rho' - rho)/Dt_ad; the tank's clock advances by Dt_ad.
+template <int D>
+__global__ void k_apply(int64_t n, int4* __restrict__ P, float4* __restrict__ V, const int* __restrict__ inst_of,
+                        const Inst* __restrict__ inst, const Ctrl* __restrict__ ctrl, const float* __restrict__ Y,
+                        Global* g) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = inst_of ? inst_of[i] : 0;
+  const Inst& I = inst[k];
+  const float dt = (float)ctrl[k].dt_ad;
+  const float gmag = sqrtf(I.g[0] * I.g[0] + I.g[1] * I.g[1] + I.g[2] * I.g[2]);
+  const float vs = gmag > 0.f ? gmag * dt : (float)I.u_ref;
+  int4 p = P[i];
+  const float4 v = V[i];
+  const float* y = Y + i * 16;
+  const float vn[3] = {v.x + I.g[0] * dt + vs * y[0], v.y + I.g[1] * dt + vs * y[1],
+                       D == 3 ? v.z + I.g[2] * dt + vs * y[2] : 0.f};
+  const float drho = I.rho0 * y[D] / S_RHO;
+  const float dev = i2f(p.w) + drho;
+  const float vo[3] = {v.x, v.y, v.z};
+  int q[3] = {p.x, p.y, p.z};
+  for (int a = 0; a < D; ++a) q[a] = wrap_coord(q[a] + __float2int_rn(0.5f * dt * (vo[a] + vn[a]) * I.inv_dq), I.period[a]);
+  if (!isfinite(dev) || !isfinite(vn[0]) || !isfinite(vn[1])) atomicOr(&g->err, ERR_NAN);
+  P[i] = make_int4(q[0], q[1], q[2], f2i(dev));
+  V[i] = make_float4(vn[0], vn[1], vn[2], dt > 0.f ? drho / dt : 0.f);
+}
+
+__global__ void k_learned_clock(int n_inst, Ctrl* ctrl) {
+  for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
+    ctrl[k].t += ctrl[k].dt_ad;
+    ctrl[k].tau = ctrl[k].dt_ad;
+    ctrl[k].done = 1;
+    ctrl[k].dt = 0.0;
+  }
+}
+
+template <int NO>
+size_t dense_smem(int K) { return (size_t)(NO + kTile) * (K + 8) * sizeof(bf16); }
+
+template <int NO>
+size_t dw_smem(int K) { return (size_t)kTile * ((NO + 8) + (K + 8)) * sizeof(bf16); }
+
+template <int NO>
+void set_smem_attrs() {
+  cudaFuncSetAttribute(k_dense<NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem<NO>(144));
+}
+
+template <int NO>
+void set_dw_attrs() {
+  cudaFuncSetAttribute(k_dense_dw<NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem<NO>(144));
+}
+
+}  // namespace learned
+}  // namespace sph
+
+using namespace sph::learned;
+
+struct sph_learned {
+  int dim = 2;
+  float* w32 = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* grad = nullptr;
+  bf16* wb = nullptr;
+  bf16* wbt = nullptr;
+  int64_t adam_t = 0;
+  // workspace
+  int64_t cap_n = 0, cap_e = 0;
+  uint32_t* cnt = nullptr;
+  uint32_t* off = nullptr;
+  uint32_t* scan_tmp = nullptr;
+  int* esrc = nullptr;
+  int* enbr = nullptr;
+  bf16* U = nullptr;
+  bf16* XE[ROUNDS] = {nullptr};
+  bf16* A1[ROUNDS] = {nullptr};
+  bf16* XN[ROUNDS] = {nullptr};
+  bf16* A2[ROUNDS] = {nullptr};
+  float* Mbuf = nullptr;
+  float* H = nullptr;
+  float* H0 = nullptr;
+  bf16* XD = nullptr;
+  bf16* A3 = nullptr;
+  float* Y = nullptr;
+  float* dH = nullptr;
+  float* dXN = nullptr;
+  bf16* dYb = nullptr;
+  bf16* dZn = nullptr;
+  bf16* dM = nullptr;
+  bf16* dZe = nullptr;
+  float* dXE = nullptr;
+  float* partial = nullptr;
+  size_t partial_elems = 0;
+  double* loss = nullptr;
+  int64_t E = 0;
+  // saved state for the fallback
+  int4* saveP = nullptr;
+  float4* saveV = nullptr;
+  sph::Ctrl* saveC = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace {
+
+template <typename T>
+bool nalloc(sph_learned* L, T** p, size_t count) {
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  L->allocs.push_back((void*)*p);
+  return true;
+}
+
+inline unsigned blocks_for(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+int ensure_workspace(sph_learned* L, int64_t n, int64_t E) {
+  if (n <= L->cap_n && E <= L->cap_e) return SPH_OK;
+  // grow: free the old workspace (not the weights) and allocate anew
+  void* keep[6] = {L->w32, L->m, L->v, L->grad, L->wb, L->wbt};
+  std::vector<void*> rest;
+  for (void* p : L->allocs) {
+    bool k = false;
+    for (void* q : keep) k |= (p == q);
+    if (k) rest.push_back(p);
+    else cudaFree(p);
+  }
+  L->allocs = rest;
+  L->saveC = nullptr;                        // freed above with the rest of the workspace
+  n = std::max<int64_t>(n, L->cap_n);
+  E = std::max<int64_t>(E, L->cap_e);
+  bool ok = nalloc(L, &L->cnt, n) && nalloc(L, &L->off, n + 1) &&
+            nalloc(L, &L->scan_tmp, sph::scan_tmp_elems(n)) && nalloc(L, &L->esrc, E) && nalloc(L, &L->enbr, E) &&
+            nalloc(L, &L->U, n * 16) && nalloc(L, &L->Mbuf, E * F) && nalloc(L, &L->H, n * F) &&
+            nalloc(L, &L->H0, n * F) && nalloc(L, &L->XD, n * 80) && nalloc(L, &L->A3, n * 80) &&
+            nalloc(L, &L->Y, n * 16) && nalloc(L, &L->dH, n * F) && nalloc(L, &L->dXN, n * 144) &&
+            nalloc(L, &L->dYb, n * 16) && nalloc(L, &L->dZn, n * F) && nalloc(L, &L->dM, E * F) &&
+            nalloc(L, &L->dZe, std::max(E, n) * F) && nalloc(L, &L->dXE, E * 80) && nalloc(L, &L->loss, 1) &&
+            nalloc(L, &L->saveP, n) && nalloc(L, &L->saveV, n);
+  for (int r = 0; r < ROUNDS && ok; ++r)
+    ok = nalloc(L, &L->XE[r], E * 80) && nalloc(L, &L->A1[r], E * 80) && nalloc(L, &L->XN[r], n * 144) &&
+         nalloc(L, &L->A2[r], n * 80);
+  L->partial_elems = (size_t)((std::max(n, E) + kDwRows - 1) / kDwRows + 1) * 64 * 144;
+  ok = ok && nalloc(L, &L->partial, L->partial_elems);
+  if (!ok) {
+    L->err = "device allocation of the network workspace failed";
+    return SPH_E_OOM;
+  }
+  L->cap_n = n;
+  L->cap_e = E;
+  return SPH_OK;
+}
+
+template <int NO>
+void dense(int64_t M, int K, const bf16* X, int ldx, const bf16* W, float* of, int ldf, int nf, int accum,
+           bf16* ob, int ldo, int col0, int nb, int relu, const bf16* mask, int ldm, cudaStream_t s) {
+  if (M == 0) return;
+  k_dense<NO><<<blocks_for(M, kTile), 128, dense_smem<NO>(K), s>>>(M, K, X, ldx, W, of, ldf, nf, accum, ob, ldo,
+                                                                   col0, nb, relu, mask, ldm);
+}
+
+// grad[layer] += dY^T X over M rows
+template <int NO>
+void dense_dw(sph_learned* L, int layer, int64_t M, int K, const bf16* dY, int ldy, const bf16* X, int ldx,
+              cudaStream_t s) {
+  if (M == 0) return;
+  const int blocks = (int)((M + kDwRows - 1) / kDwRows);
+  k_dense_dw<NO><<<blocks, 128, dw_smem<NO>(K), s>>>(M, K, dY, ldy, X, ldx, L->partial);
+  const int count = NO * K;
+  k_reduce_partials<<<blocks_for(count), 256, 0, s>>>(blocks, count, L->partial, L->grad + w_offset(layer));
+}
+
+const bf16* Wl(const sph_learned* L, int l) { return L->wb + w_offset(l); }
+const bf16* WTl(const sph_learned* L, int l) { return L->wbt + w_offset(l); }
+
+// Graph and features of the handle's current (post density re-initialisation) state.
+int build_inputs(sph_handle* h, sph_learned* L, cudaStream_t s) {
+  const sph::Buffers& b = h->b;
+  const int64_t n = b.n;
+  // edge count first (host needs E to size the workspace)
+  if (ensure_workspace(L, n, std::max<int64_t>(L->cap_e, 1)) != SPH_OK) return SPH_E_OOM;
+  k_edge_count<<<blocks_for(n), 256, 0, s>>>(n, b.nbc, L->cnt);
+  int64_t dummy = 0;
+  sph::scan_exclusive(L->cnt, L->off, n, L->scan_tmp, s, &dummy);
+  uint32_t E32 = 0;
+  if (cudaMemcpyAsync(&E32, L->off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return SPH_E_CUDA;
+  }
+  const int64_t E = E32;
+  if (E > L->cap_e) {
+    if (ensure_workspace(L, n, E) != SPH_OK) return SPH_E_OOM;
+    k_edge_count<<<blocks_for(n), 256, 0, s>>>(n, b.nbc, L->cnt);
+    sph::scan_exclusive(L->cnt, L->off, n, L->scan_tmp, s, &dummy);
+  }
+  L->E = E;
+  if (b.dim == 2)
+    k_features<2><<<blocks_for(n), 256, 0, s>>>(n, b.PS, b.VS, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, L->off, b.WP,
+                                                L->esrc, L->enbr, L->U, L->XE[0], L->XE[1], L->XE[2]);
+  else
+    k_features<3><<<blocks_for(n), 256, 0, s>>>(n, b.PS, b.VS, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, L->off, b.WP,
+                                                L->esrc, L->enbr, L->U, L->XE[0], L->XE[1], L->XE[2]);
+  for (int r = 0; r < ROUNDS; ++r) {
+    k_const_cols<<<blocks_for(E), 256, 0, s>>>(E, 80, F, F + 1, L->A1[r]);
+    k_const_cols<<<blocks_for(n), 256, 0, s>>>(n, 144, 2 * F, 2 * F + 1, L->XN[r]);
+    k_const_cols<<<blocks_for(n), 256, 0, s>>>(n, 80, F, F + 1, L->A2[r]);
+  }
+  k_const_cols<<<blocks_for(n), 256, 0, s>>>(n, 80, F, F + 1, L->XD);
+  k_const_cols<<<blocks_for(n), 256, 0, s>>>(n, 80, F, F + 1, L->A3);
+  return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_E_CUDA;
+}
+
+void forward(sph_handle* h, sph_learned* L, cudaStream_t s) {
+  const int64_t n = h->b.n, E = L->E;
+  const int d = h->b.dim, fe = 2 * d + 3;
+  const float inv_nbar = 1.0f / nbar(d);
+  // encoder: H = relu(U W_enc^T); H0 keeps h0 for the encoder's backward
+  dense<64>(n, 16, L->U, 16, Wl(L, L_ENC), L->H, F, F, 0, nullptr, 0, 0, 0, 1, nullptr, 0, s);
+  cudaMemcpyAsync(L->H0, L->H, sizeof(float) * n * F, cudaMemcpyDeviceToDevice, s);
+  for (int r = 0; r < ROUNDS; ++r) {
+    k_gather_h<<<blocks_for(E * F), 256, 0, s>>>(E, fe, L->enbr, L->H, L->XE[r]);
+    dense<64>(E, 80, L->XE[r], 80, Wl(L, L_E1), nullptr, 0, 0, 0, L->A1[r], 80, 0, F, 1, nullptr, 0, s);
+    dense<64>(E, 80, L->A1[r], 80, Wl(L, L_E2), L->Mbuf, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+    k_segsum<<<blocks_for(n * F), 256, 0, s>>>(n, L->off, L->Mbuf, L->H, inv_nbar, L->XN[r]);
+    dense<64>(n, 144, L->XN[r], 144, Wl(L, L_N1), nullptr, 0, 0, 0, L->A2[r], 80, 0, F, 1, nullptr, 0, s);
+    dense<64>(n, 80, L->A2[r], 80, Wl(L, L_N2), L->H, F, F, 1, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+  }
+  k_rows_bf16<<<blocks_for(n * F), 256, 0, s>>>(n, F, L->H, F, L->XD, 80);
+  dense<64>(n, 80, L->XD, 80, Wl(L, L_D1), nullptr, 0, 0, 0, L->A3, 80, 0, F, 1, nullptr, 0, s);
+  dense<16>(n, 80, L->A3, 80, Wl(L, L_D2), L->Y, 16, 16, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+}
+
+void backward(sph_handle* h, sph_learned* L, cudaStream_t s) {
+  const int64_t n = h->b.n, E = L->E;
+  const int d = h->b.dim, fe = 2 * d + 3;
+  const float inv_nbar = 1.0f / nbar(d);
+  cudaMemsetAsync(L->grad, 0, sizeof(float) * kWeights, s);
+  // decoder
+  dense_dw<16>(L, L_D2, n, 80, L->dYb, 16, L->A3, 80, s);
+  dense<80>(n, 16, L->dYb, 16, WTl(L, L_D2), nullptr, 0, 0, 0, L->dZn, F, 0, F, 0, L->A3, 80, s);
+  dense_dw<64>(L, L_D1, n, 80, L->dZn, F, L->XD, 80, s);
+  dense<80>(n, 64, L->dZn, F, WTl(L, L_D1), L->dH, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+  for (int r = ROUNDS - 1; r >= 0; --r) {
+    // h_new = h + W_n2 [relu(W_n1 XN), 1]
+    k_rows_bf16<<<blocks_for(n * F), 256, 0, s>>>(n, F, L->dH, F, L->dZn, F);
+    dense_dw<64>(L, L_N2, n, 80, L->dZn, F, L->A2[r], 80, s);
+    bf16* dZ2 = L->dZe;   // reuse the edge buffer (E >= n)
+    dense<80>(n, 64, L->dZn, F, WTl(L, L_N2), nullptr, 0, 0, 0, dZ2, F, 0, F, 0, L->A2[r], 80, s);
+    dense_dw<64>(L, L_N1, n, 144, dZ2, F, L->XN[r], 144, s);
+    dense<144>(n, 64, dZ2, F, WTl(L, L_N1), L->dXN, 144, 144, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+    k_node_back<<<blocks_for(n * F), 256, 0, s>>>(n, L->dXN, L->dH);
+    k_edge_back<<<blocks_for(E * F), 256, 0, s>>>(E, L->esrc, L->dXN, inv_nbar, L->dM);
+    dense_dw<64>(L, L_E2, E, 80, L->dM, F, L->A1[r], 80, s);
+    dense<80>(E, 64, L->dM, F, WTl(L, L_E2), nullptr, 0, 0, 0, L->dZe, F, 0, F, 0, L->A1[r], 80, s);
+    dense_dw<64>(L, L_E1, E, 80, L->dZe, F, L->XE[r], 80, s);
+    dense<80>(E, 64, L->dZe, F, WTl(L, L_E1), L->dXE, 80, 80, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+    k_scatter_dh<<<blocks_for(E * F), 256, 0, s>>>(E, fe, L->enbr, L->dXE, L->dH);
+  }
+  k_relu_back<<<blocks_for(n * F), 256, 0, s>>>(n, L->dH, L->H0, L->dZn);
+  dense_dw<64>(L, L_ENC, n, 16, L->dZn, F, L->U, 16, s);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+namespace {
+
+__global__ void k_export_y(int64_t n, int dout, const float* __restrict__ Y, const int* __restrict__ id,
+                           double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t row = id[i];
+  for (int c = 0; c < dout; ++c) y[row * dout + c] = (double)Y[i * 16 + c];
+}
+
+bool device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int lfail(sph_learned* L, int code, const char* msg) {
+  if (L) L->err = msg;
+  return code;
+}
+
+void upload_weights_bf16(sph_learned* L, cudaStream_t s) {
+  k_weights_bf16<<<blocks_for(kWeights), 256, 0, s>>>(L->w32, L->wb, L->wbt);
+}
+
+int ready(sph_handle* h, sph_learned* L) {
+  if (!h || !L) return SPH_E_INVALID;
+  if (h->b.dim != L->dim) return lfail(L, SPH_E_INVALID, "network and handle dimensions differ");
+  if (!h->cells_valid) return lfail(L, SPH_E_INVALID, "run sph_build_cells and sph_advection_step first");
+  return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sph_learned_weight_count(int64_t* count) {
+  if (!count) return SPH_E_INVALID;
+  *count = kWeights;
+  return SPH_OK;
+}
+
+const char* sph_learned_last_error(const sph_learned* L) { return L ? L->err.c_str() : "null network"; }
+
+void sph_learned_destroy(sph_learned* L) {
+  if (!L) return;
+  for (void* p : L->allocs) cudaFree(p);
+  delete L;
+}
+
+int sph_learned_create(int32_t dim, const float* weights, sph_learned** out) {
+  if (!out || (dim != 2 && dim != 3)) return SPH_E_INVALID;
+  sph_learned* L = new sph_learned();
+  *out = L;
+  L->dim = dim;
+  if (!nalloc(L, &L->w32, kWeights) || !nalloc(L, &L->m, kWeights) || !nalloc(L, &L->v, kWeights) ||
+      !nalloc(L, &L->grad, kWeights) || !nalloc(L, &L->wb, kWeights) || !nalloc(L, &L->wbt, kWeights))
+    return lfail(L, SPH_E_OOM, "device allocation of the weights failed");
+  set_smem_attrs<16>();
+  set_smem_attrs<64>();
+  set_smem_attrs<80>();
+  set_smem_attrs<144>();
+  set_dw_attrs<16>();
+  set_dw_attrs<64>();
+  cudaMemset(L->m, 0, sizeof(float) * kWeights);
+  cudaMemset(L->v, 0, sizeof(float) * kWeights);
+  cudaMemset(L->w32, 0, sizeof(float) * kWeights);
+  if (weights && cudaMemcpy(L->w32, weights, sizeof(float) * kWeights, cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return lfail(L, SPH_E_CUDA, "copy of the weights failed");
+  }
+  upload_weights_bf16(L, 0);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return lfail(L, SPH_E_CUDA, "network set-up failed");
+  }
+  return SPH_OK;
+}
+
+int sph_learned_set_weights(sph_learned* L, const float* w) {
+  if (!L || !w) return SPH_E_INVALID;
+  if (cudaMemcpy(L->w32, w, sizeof(float) * kWeights, cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return lfail(L, SPH_E_CUDA, "copy of the weights failed");
+  }
+  cudaMemset(L->m, 0, sizeof(float) * kWeights);
+  cudaMemset(L->v, 0, sizeof(float) * kWeights);
+  L->adam_t = 0;
+  upload_weights_bf16(L, 0);
+  return cudaDeviceSynchronize() == cudaSuccess ? SPH_OK : SPH_E_CUDA;
+}
+
+int sph_learned_get_weights(sph_learned* L, float* w) {
+  if (!L || !w) return SPH_E_INVALID;
+  if (cudaMemcpy(w, L->w32, sizeof(float) * kWeights, cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return lfail(L, SPH_E_CUDA, "copy of the weights failed");
+  }
+  return SPH_OK;
+}
+
+int sph_learned_predict(sph_handle* h, sph_learned* L, double* y, void* stream) {
+  int r = ready(h, L);
+  if (r != SPH_OK) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  r = build_inputs(h, L, s);
+  if (r != SPH_OK) return lfail(L, r, "building the network inputs failed");
+  forward(h, L, s);
+  if (y) {
+    const int dout = h->b.dim + 1;
+    const bool dev = device_ptr(y);
+    double* tgt = dev ? y : h->stage;
+    k_export_y<<<blocks_for(h->b.n), 256, 0, s>>>(h->b.n, dout, L->Y, h->b.id, tgt);
+    if (!dev && cudaMemcpyAsync(y, tgt, sizeof(double) * h->b.n * dout, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+      cudaGetLastError();
+      return lfail(L, SPH_E_CUDA, "copy of the prediction failed");
+    }
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return lfail(L, SPH_E_CUDA, "network forward pass failed");
+  }
+  return SPH_OK;
+}
+
+int sph_learned_train_step(sph_handle* h, sph_learned* L, const double* target, double lr, double* loss_out,
+                           float* grad_out, void* stream) {
+  int r = ready(h, L);
+  if (r != SPH_OK) return r;
+  if (!target) return lfail(L, SPH_E_INVALID, "target is required");
+  cudaStream_t s = (cudaStream_t)stream;
+  r = build_inputs(h, L, s);
+  if (r != SPH_OK) return lfail(L, r, "building the network inputs failed");
+  forward(h, L, s);
+  const int64_t n = h->b.n;
+  const int dout = h->b.dim + 1;
+  const double* T = target;
+  if (!device_ptr(target)) {
+    if (cudaMemcpyAsync(h->stage, target, sizeof(double) * n * dout, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      return lfail(L, SPH_E_CUDA, "copy of the target failed");
+    }
+    T = h->stage;
+  }
+  cudaMemsetAsync(L->loss, 0, sizeof(double), s);
+  k_loss<<<blocks_for(n), 256, 0, s>>>(n, dout, L->Y, T, h->b.id, L->dYb, L->loss);
+  backward(h, L, s);
+  if (lr > 0.0) {
+    ++L->adam_t;
+    const float b1pow = (float)std::pow(0.9, (double)L->adam_t), b2pow = (float)std::pow(0.999, (double)L->adam_t);
+    k_adam<<<blocks_for(kWeights), 256, 0, s>>>(kWeights, L->w32, L->m, L->v, L->grad, (float)lr, b1pow, b2pow);
+    upload_weights_bf16(L, s);
+  }
+  double loss = 0.0;
+  cudaMemcpyAsync(&loss, L->loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (grad_out) cudaMemcpyAsync(grad_out, L->grad, sizeof(float) * kWeights, cudaMemcpyDefault, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return lfail(L, SPH_E_CUDA, "training step failed");
+  }
+  if (loss_out) *loss_out = loss;
+  return SPH_OK;
+}
+
+int sph_learned_step(sph_handle* h, sph_learned* L, double max_mean_rho_dev, double max_energy_drift,
+                     int32_t* used_learned, void* stream) {
+  if (!h || !L) return SPH_E_INVALID;
+  if (h->b.dim != L->dim) return lfail(L, SPH_E_INVALID, "network and handle dimensions differ");
+  cudaStream_t s = (cudaStream_t)stream;
+  int r = sph_build_cells(h, stream);
+  if (r == SPH_OK) r = sph_advection_step(h, nullptr, stream);
+  if (r != SPH_OK) return r;
+  const int K = h->b.n_inst;
+  std::vector<sph_diag> d0(K), d1(K);
+  r = sph_diagnostics(h, d0.data(), stream);
+  if (r != SPH_OK) return r;
+  const int64_t n = h->b.n;
+  r = build_inputs(h, L, s);
+  if (r != SPH_OK) return lfail(L, r, "building the network inputs failed");
+  if (!L->saveC && !nalloc(L, &L->saveC, K)) return lfail(L, SPH_E_OOM, "allocation failed");
+  cudaMemcpyAsync(L->saveP, h->b.PS, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(L->saveV, h->b.VS, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(L->saveC, h->b.ctrl, sizeof(sph::Ctrl) * K, cudaMemcpyDeviceToDevice, s);
+  forward(h, L, s);
+  if (h->b.dim == 2)
+    k_apply<2><<<blocks_for(n), 256, 0, s>>>(n, h->b.PS, h->b.VS, h->b.inst_of, h->b.inst, h->b.ctrl, L->Y, h->b.glob);
+  else
+    k_apply<3><<<blocks_for(n), 256, 0, s>>>(n, h->b.PS, h->b.VS, h->b.inst_of, h->b.inst, h->b.ctrl, L->Y, h->b.glob);
+  k_learned_clock<<<1, 256, 0, s>>>(K, h->b.ctrl);
+  sph::launch_vmax(h->b, s, &h->launches);
+  h->cells_valid = false;
+  r = sph_diagnostics(h, d1.data(), stream);
+  bool ok = (r == SPH_OK);
+  for (int k = 0; k < K && ok; ++k) {
+    const double drift = std::fabs(d1[k].energy - d0[k].energy) / std::max(std::fabs(d0[k].energy), 1e-300);
+    if (!(d1[k].mean_rho_dev <= max_mean_rho_dev) || !(drift <= max_energy_drift)) ok = false;
+  }
+  if (used_learned) *used_learned = ok ? 1 : 0;
+  if (ok) return SPH_OK;
+  // fall back: restore the step's start and run the acoustic substeps
+  h->err.clear();
+  cudaMemsetAsync(h->b.glob, 0, sizeof(int), s);                    // clear error bits of the trial
+  cudaMemcpyAsync(h->b.PS, L->saveP, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(h->b.VS, L->saveV, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(h->b.ctrl, L->saveC, sizeof(sph::Ctrl) * K, cudaMemcpyDeviceToDevice, s);
+  h->cells_valid = true;
+  for (int guard = 0;; ++guard) {
+    int32_t done = 0;
+    r = sph_acoustic_substep(h, &done, nullptr, stream);
+    if (r != SPH_OK) return r;
+    if (done) break;
+    if (guard > 1000000) return SPH_E_UNSTABLE;
+  }
+  return SPH_OK;
+}
+
+}  // extern "C"

@@ -34,6 +34,9 @@ EXPORTS = [
     "sph_get_permutation", "sph_get_neighbours", "sph_pair_count", "sph_kernel_launches",
     "sph_set_kernel_timing", "sph_kernel_times", "sph_diagnostics_noalloc",
     "sph_get_launch_config", "sph_set_launch_config", "sph_autotune",
+    "sph_learned_weight_count", "sph_learned_create", "sph_learned_destroy",
+    "sph_learned_last_error", "sph_learned_set_weights", "sph_learned_get_weights",
+    "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
 ]
 
 
@@ -123,6 +126,15 @@ def load():
         "sph_get_launch_config": (i32, [P, ctypes.POINTER(i32)]),
         "sph_set_launch_config": (i32, [P, ctypes.POINTER(i32)]),
         "sph_autotune": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(dbl), P]),
+        "sph_learned_weight_count": (i32, [ctypes.POINTER(i64)]),
+        "sph_learned_create": (i32, [i32, P, ctypes.POINTER(P)]),
+        "sph_learned_destroy": (None, [P]),
+        "sph_learned_last_error": (ctypes.c_char_p, [P]),
+        "sph_learned_set_weights": (i32, [P, P]),
+        "sph_learned_get_weights": (i32, [P, P]),
+        "sph_learned_predict": (i32, [P, P, P, P]),
+        "sph_learned_train_step": (i32, [P, P, P, dbl, ctypes.POINTER(dbl), P, P]),
+        "sph_learned_step": (i32, [P, P, dbl, dbl, ctypes.POINTER(i32), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -365,6 +377,79 @@ def sph_diagnostics_noalloc(params: SphParams, pos, vel, rho, mass, stream=None)
     if code != SPH_OK:
         raise SphError(code, lib.sph_last_error(None).decode())
     return out.as_dict()
+
+
+# ------------------------------------------------------------------------------ learned
+def _lcheck(lib, net, code):
+    if code != SPH_OK:
+        msg = lib.sph_learned_last_error(net).decode() if net else ""
+        raise SphError(code, msg)
+
+
+def sph_learned_weight_count() -> int:
+    lib = load()
+    v = ctypes.c_int64(0)
+    check(lib, None, lib.sph_learned_weight_count(ctypes.byref(v)))
+    return int(v.value)
+
+
+def sph_learned_create(dim, weights=None):
+    lib = load()
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+    net = ctypes.c_void_p()
+    code = lib.sph_learned_create(int(dim), _ptr(w), ctypes.byref(net))
+    if code != SPH_OK:
+        msg = lib.sph_learned_last_error(net).decode() if net.value else ""
+        if net.value:
+            lib.sph_learned_destroy(net)
+        raise SphError(code, msg)
+    return net
+
+
+def sph_learned_destroy(net):
+    load().sph_learned_destroy(net)
+
+
+def sph_learned_set_weights(net, weights):
+    lib = load()
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _lcheck(lib, net, lib.sph_learned_set_weights(net, _ptr(w)))
+
+
+def sph_learned_get_weights(net):
+    lib = load()
+    w = np.empty(sph_learned_weight_count(), dtype=np.float32)
+    _lcheck(lib, net, lib.sph_learned_get_weights(net, _ptr(w)))
+    return w
+
+
+def sph_learned_predict(h, net, n, dim, stream=None):
+    lib = load()
+    y = np.empty((n, dim + 1))
+    _lcheck(lib, net, lib.sph_learned_predict(h, net, _ptr(y), _stream(stream)))
+    return y
+
+
+def sph_learned_train_step(h, net, target, lr, want_grad=False, stream=None):
+    """Returns (loss, gradient or None)."""
+    lib = load()
+    t = _f64(target)
+    loss = ctypes.c_double(0.0)
+    g = np.empty(sph_learned_weight_count(), dtype=np.float32) if want_grad else None
+    _lcheck(lib, net, lib.sph_learned_train_step(h, net, _ptr(t), float(lr), ctypes.byref(loss), _ptr(g),
+                                                 _stream(stream)))
+    return loss.value, g
+
+
+def sph_learned_step(h, net, max_mean_rho_dev=0.01, max_energy_drift=0.005, stream=None):
+    lib = load()
+    used = ctypes.c_int32(0)
+    code = lib.sph_learned_step(h, net, float(max_mean_rho_dev), float(max_energy_drift),
+                                ctypes.byref(used), _stream(stream))
+    if code != SPH_OK:
+        msg = lib.sph_learned_last_error(net).decode() or lib.sph_last_error(h).decode()
+        raise SphError(code, msg)
+    return bool(used.value)
 
 
 # ------------------------------------------------------------------------------ convenience
