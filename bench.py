@@ -39,8 +39,8 @@ UNIT = "particle-substeps/s"
 # profiles/pressure_relaxation_dam_break_3d.md; it is scaled to the benchmark's particle
 # count (the traffic is per particle: state records plus its neighbour row). Valid only
 # for the kernel sources whose hash is recorded with it.
-TRAFFIC_BYTES_PER_PARTICLE = 389.54
-TRAFFIC_SOURCE_HASH = "dcc5d2380bd3ce82"
+TRAFFIC_BYTES_PER_PARTICLE = 389.66
+TRAFFIC_SOURCE_HASH = "a11ba06d4e15d3b4"
 
 
 def kernel_source_hash():
@@ -187,12 +187,17 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
+    tuned = None
+    cfg = None
+    if args.launch_config:
+        cfg = [int(v) for v in args.launch_config.split(",")]
+        sph.sph_set_launch_config(sim.handle, cfg)
     for _ in range(args.warmup):
         sim.step(1)
-    tuned = None
-    if not args.no_autotune:
+    if cfg is None and not args.no_autotune:
         # one extra (untimed) advection step that times the launch variants
         cfg, times = sph.sph_autotune(sim.handle, stream)
+    if cfg is not None:
         tuned = {"pressure_relaxation": {"threads_per_particle": cfg[0], "block": cfg[1]},
                  "density_relaxation": {"threads_per_particle": cfg[2], "block": cfg[3]}}
     torch.cuda.synchronize()
@@ -272,11 +277,16 @@ def run_ours(args, rank, world, local_rank):
     traffic = None
     if TRAFFIC_BYTES_PER_PARTICLE is not None and TRAFFIC_SOURCE_HASH == kernel_source_hash():
         traffic = TRAFFIC_BYTES_PER_PARTICLE * N
+    # the same table walk with the 32-byte neighbour records gathered and no pair arithmetic:
+    # the device's floor for gathering them this way (the kernels are gather-bound, not HBM-bound)
+    gather_ms = sph.sph_gather_ceiling(sim.handle, 10, stream)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "kernel": "k_pressure_relaxation<3>", "peak_kind": peak_kind,
             "launch_ms": k7_ms, "algorithmic_bytes_per_launch": k7_bytes,
-            "density_relaxation_ms": ktimes[1] / max(kcount[1], 1)}
+            "density_relaxation_ms": ktimes[1] / max(kcount[1], 1),
+            "gather_ceiling_ms": gather_ms,
+            "frac_of_gather_ceiling": (gather_ms / k7_ms) if kcount[0] else None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -294,8 +304,9 @@ def run_ours(args, rank, world, local_rank):
                 "n_fluid": N, "n_wall": prob.n_wall, "h_over_dp": 1.3,
                 "substeps": substeps, "neighbour_pairs": fluid_pairs + wall_pairs,
                 "mean_neighbours": (fluid_pairs + wall_pairs) / N,
-                "l2": "inputs larger than L2 (state 256 MB, neighbour table %.1f GB)"
-                      % (4 * N * info.capacity / 1e9),
+                "l2": "inputs larger than L2 (state %d MB, neighbour table %.1f GB)"
+                      % (32 * N // 10**6, 4 * N * info.capacity / 1e9),
+                "pair_interactions_per_s": 2 * (fluid_pairs + wall_pairs) * total_units / N / (ms_max * 1e-3),
                 "loop": "graph" if args.graph else "host-driven, one sync per substep",
                 "parallelism": f"replicas x{world}",
                 "launch": tuned or {"autotune": "off"},
@@ -434,6 +445,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch-config", default=None,
+                    help="pr_tpp,pr_block,dr_tpp,dr_block: fixed launch variants instead of autotuning")
     ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned"],
                     help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()

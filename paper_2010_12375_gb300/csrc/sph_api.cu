@@ -912,6 +912,22 @@ int sph_autotune(sph_handle* h, int32_t* cfg_out, double* ms_out, void* stream) 
   return SPH_OK;
 }
 
+int sph_gather_ceiling(sph_handle* h, int32_t reps, double* ms_out, void* stream) {
+  if (!h || !ms_out || reps < 1) return SPH_E_INVALID;
+  if (!h->cells_valid) return fail(h, SPH_E_INVALID, "sph_build_cells must run first");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* sink = reinterpret_cast<unsigned*>(h->diag_out);
+  sph::launch_gather_ceiling(h->b, sink, s, &h->launches);        // warm-up
+  CK(h, cudaEventRecord(h->ev[0], s));
+  for (int r = 0; r < reps; ++r) sph::launch_gather_ceiling(h->b, sink, s, &h->launches);
+  CK(h, cudaEventRecord(h->ev[1], s));
+  CK(h, cudaEventSynchronize(h->ev[1]));
+  float ms = 0.f;
+  CK(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+  *ms_out = (double)ms / reps;
+  return sync_status(h, s);
+}
+
 int sph_kernel_launches(sph_handle* h, int64_t* out) {
   if (!h || !out) return SPH_E_INVALID;
   *out = h->launches + h->graph_kernels;

@@ -80,6 +80,8 @@ void launch_dt_acoustic(const Buffers& b, cudaStream_t s, cudaGraphConditionalHa
                         bool use_cond, int64_t* launches);
 void launch_pressure_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_density_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches);
+// gather-only walk of the neighbour table (diagnostic); sink: one device word
+void launch_gather_ceiling(const Buffers& b, unsigned* sink, cudaStream_t s, int64_t* launches);
 
 // diagnostics: out[n_inst * kDiagFields] doubles on the device
 constexpr int kDiagFields = 16;

@@ -33,7 +33,7 @@ EXPORTS = [
     "sph_diagnostics", "sph_get_state", "sph_set_state", "sph_get_acceleration",
     "sph_get_permutation", "sph_get_neighbours", "sph_pair_count", "sph_kernel_launches",
     "sph_set_kernel_timing", "sph_kernel_times", "sph_diagnostics_noalloc",
-    "sph_get_launch_config", "sph_set_launch_config", "sph_autotune",
+    "sph_get_launch_config", "sph_set_launch_config", "sph_autotune", "sph_gather_ceiling",
     "sph_learned_weight_count", "sph_learned_create", "sph_learned_destroy",
     "sph_learned_last_error", "sph_learned_set_weights", "sph_learned_get_weights",
     "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
@@ -126,6 +126,7 @@ def load():
         "sph_get_launch_config": (i32, [P, ctypes.POINTER(i32)]),
         "sph_set_launch_config": (i32, [P, ctypes.POINTER(i32)]),
         "sph_autotune": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(dbl), P]),
+        "sph_gather_ceiling": (i32, [P, i32, ctypes.POINTER(dbl), P]),
         "sph_learned_weight_count": (i32, [ctypes.POINTER(i64)]),
         "sph_learned_create": (i32, [i32, P, ctypes.POINTER(P)]),
         "sph_learned_destroy": (None, [P]),
@@ -363,6 +364,14 @@ def sph_autotune(h, stream=None):
     ms = (ctypes.c_double * 18)()
     check(lib, h, lib.sph_autotune(h, cfg, ms, _stream(stream)))
     return list(cfg), np.array(ms[:]).reshape(2, 3, 3)
+
+
+def sph_gather_ceiling(h, reps=10, stream=None) -> float:
+    """Mean ms of the gather-only walk of the current neighbour table."""
+    lib = load()
+    ms = ctypes.c_double(0)
+    check(lib, h, lib.sph_gather_ceiling(h, int(reps), ctypes.byref(ms), _stream(stream)))
+    return float(ms.value)
 
 
 def sph_diagnostics_noalloc(params: SphParams, pos, vel, rho, mass, stream=None):

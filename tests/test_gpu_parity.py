@@ -493,3 +493,20 @@ def test_autotune_chooses_caches_and_equals_a_plain_step(sph, tmp_path, monkeypa
     assert a.diagnostics()["substeps"] == b.diagnostics()["substeps"]
     a.close()
     b.close()
+
+
+def test_gather_ceiling_runs_and_changes_nothing(sph):
+    prob = wk.dam_break_3d(24)
+    sim = sph.Simulation(prob)
+    sim.step(1)
+    before = sim.state()
+    sim.build_cells()
+    ms = sph.sph_gather_ceiling(sim.handle, 3)
+    assert ms > 0.0
+    for u, v in zip(before, sim.state()):
+        np.testing.assert_array_equal(u, v)
+    # after a state change the table is stale: the call is refused, not run
+    sim.set_state(*before)
+    with pytest.raises(sph.SphError):
+        sph.sph_gather_ceiling(sim.handle, 3)
+    sim.close()
