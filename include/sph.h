@@ -31,8 +31,9 @@
  * bit for bit): positions are held as fixed-point integers per axis,
  * q = rint((x - lo) / dq), with dq = cell / 2^bits, cell = 2h (or, when axes
  * are periodic, period / floor(period / 2h), all periodic axes sharing one
- * period), bits = min(22, 31 - bitlength(max cells per axis)). The cell of a
- * particle is q >> bits per axis, flattened with x fastest. Particles j != i
+ * period), bits = min(22, 31 - bitlength(max cells per axis)). Particles are
+ * stored by search cell, q >> (bits - 1) per axis (the cell halved on every axis),
+ * flattened with x fastest, then by id. Particles j != i
  * are neighbours when sum_a (q_i,a - q_j,a)^2 < R2 (minimum image on periodic
  * axes), R2 = ceil((2h/dq)^2) evaluated in double precision: the integer
  * form of |r_i - r_j| < 2h.
@@ -105,7 +106,7 @@ typedef struct {
 /* Sizes and derived constants of a handle. */
 typedef struct {
   int32_t dim, n_instances, capacity, bits;
-  int64_t n_fluid, n_wall, n_cells;
+  int64_t n_fluid, n_wall, n_cells;  /* n_cells: search cells over all instances       */
   double  cell, dq, sigma0;        /* cell size, position quantum, lattice sumW0 (instance 0) */
   int64_t R2;                      /* integer neighbour threshold (instance 0)               */
   int64_t device_bytes;            /* device memory held by the handle                       */
@@ -140,7 +141,7 @@ const char* sph_last_error(const sph_handle* h);
 int sph_get_info(const sph_handle* h, sph_info* out);
 
 /* Configuration update (paper Sec. 2.4 / Sec. 6.2 mesh_cell_linked_list): hash
- * particles to cells, sort by (cell, id), cell offsets, reorder the state, and
+ * particles to search cells, sort by (search cell, id), cell offsets, reorder the state, and
  * build the neighbour set {j != i : |r_i - r_j| < 2h} of every fluid particle
  * (fluid and wall neighbours), frozen until the next call. */
 int sph_build_cells(sph_handle* h, void* stream);

@@ -304,14 +304,16 @@ def neighbour_sets_quantised(x: np.ndarray, xw: np.ndarray, prm: Params):
 
 
 def cell_permutation(x: np.ndarray, ids: np.ndarray, prm: Params) -> np.ndarray:
-    """Particle ids in (cell, id) order, cells flattened with x fastest."""
+    """Particle ids in (search cell, id) order. Search cells halve the position cell on
+    every axis (cell index q >> (bits - 1), about h wide) and are flattened with x fastest;
+    the order is the one the cell-linked list of Sec. 6.2 is stored in (reading R10)."""
     cell, ncell, bits, dq, _ = quantisation(prm)
-    c = quantise(x, prm) >> bits
+    c = quantise(x, prm) >> (bits - 1)
     flat = np.zeros(x.shape[0], dtype=np.int64)
     stride = 1
     for a in range(prm.dim):
         flat += c[:, a] * stride
-        stride *= ncell[a]
+        stride *= 2 * ncell[a]
     order = np.lexsort((ids, flat))
     return ids[order]
 

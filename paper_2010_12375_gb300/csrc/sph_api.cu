@@ -182,10 +182,12 @@ Inst make_inst(const sph_params& p) {
   I.mass = 0.0f;
   for (int a = 0; a < 3; ++a) {
     I.ncell[a] = ncell[a];
+    I.scell[a] = a < d ? 2 * ncell[a] : 1;
     I.period[a] = (a < d && p.periodic[a]) ? (ncell[a] << bits) : 0;
     I.lo[a] = a < d ? p.lo[a] : 0.0;
   }
   I.bits = bits;
+  I.sbits = bits - 1;
   I.free_surface = p.free_surface;
   I.R2 = R2;
   I.h_d = p.h;
@@ -474,7 +476,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
     Inst I = make_inst(params[k]);
     I.cell_base = n_cells;
     long long nc = 1;
-    for (int a = 0; a < dim; ++a) nc *= I.ncell[a];
+    for (int a = 0; a < dim; ++a) nc *= I.scell[a];
     n_cells += nc;
     I.fluid_begin = fo[k];
     I.fluid_end = fo[k + 1];

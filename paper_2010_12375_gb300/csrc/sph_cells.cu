@@ -1,12 +1,16 @@
 // Configuration update of the WCSPH hot path (cell-linked list, paper Sec. 6.2
 // mesh_cell_linked_list, refreshed once per advection step as Sec. 2.4 fixes):
-//   hash      particle -> cell (integer: cell = q >> bits per axis, flattened x fastest)
+//   hash      particle -> search cell (integer: q >> (bits - 1) per axis, i.e. cells of
+//             half the 2h position cell, about h; flattened x fastest)
 //   sort      counting sort on the cell digit (a one-digit radix sort with radix =
 //             number of cells) followed by an in-cell sort by caller id, which makes
 //             the order the unique (cell, id) order, independent of history
 //   offsets   exclusive scan of the cell counts
 //   reorder   gather of the 32-byte particle records into cell order
-//   neighbours frozen set {j != i : |r_i - r_j| < 2h}, column-major ELL rows
+//   neighbours frozen set {j != i : |r_i - r_j| < 2h}, quad-interleaved ELL rows; the
+//             search visits the 5^D cells around a particle clipped to its 2h sphere
+//             (rows whose slab lies at >= 2h are skipped, row runs cut to the
+//             sphere's chord), about 42 % of the candidates of a 3^D scan of 2h cells
 #include <cstdio>
 
 #include "sph_kernels.h"
@@ -138,13 +142,13 @@ __global__ void k_hash(int64_t n, const int4* __restrict__ P, const int* __restr
   long long c = 0, stride = 1;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    int ca = q[a] >> I.bits;
-    if (ca < 0 || ca >= I.ncell[a]) {
+    int ca = q[a] >> I.sbits;                       // search cell: half a cell per axis
+    if (ca < 0 || ca >= I.scell[a]) {
       raise_error(g, ERR_DOMAIN, i);
-      ca = ca < 0 ? 0 : I.ncell[a] - 1;
+      ca = ca < 0 ? 0 : I.scell[a] - 1;
     }
     c += (long long)ca * stride;
-    stride *= I.ncell[a];
+    stride *= I.scell[a];
   }
   c += I.cell_base;
   cell[i] = (uint32_t)c;
@@ -205,35 +209,74 @@ __global__ void k_copy_back(int64_t n, const int4* __restrict__ Pin, const float
 }
 
 // ---------------------------------------------------------------- neighbours ---------
-// Visit the 3^D cells around (cx, cy, cz) of one grid; within each (dy, dz) row the
-// cells cx-1..cx+1 are one contiguous slot range unless the x axis wraps.
-template <int D, typename F>
-__device__ __forceinline__ void for_neighbour_cells(const Inst& I, int cx, int cy, int cz,
-                                                    const uint32_t* __restrict__ start, F&& visit) {
-  const int nx = I.ncell[0], ny = I.ncell[1], nz = D == 3 ? I.ncell[2] : 1;
+// Largest x with x^2 < v (v >= 1), exact in integers.
+__device__ __forceinline__ long long isqrt_below(long long v) {
+  long long x = (long long)sqrtf((float)(v - 1));
+  while (x > 0 && x * x > v - 1) --x;
+  while ((x + 1) * (x + 1) <= v - 1) ++x;
+  return x;
+}
+
+// Squared distance (quanta) from coordinate q to the slab of search cell c (unwrapped).
+__device__ __forceinline__ long long slab_d2(int q, int c, int sbits) {
+  const long long lo = (long long)c << sbits, hi = lo + (1ll << sbits) - 1;
+  const long long d = q < lo ? lo - q : (q > hi ? q - hi : 0);
+  return d * d;
+}
+
+__device__ __forceinline__ int wrap_cell(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+// Visit the search-cell runs that can hold a neighbour of the particle at p: for every
+// row (dy, dz) in [-2, 2]^(D-1) whose slab lies closer than 2h, the x cells that meet the
+// sphere's chord in that slab. Within a row the cells of a run are one contiguous slot
+// range; a periodic x axis splits a run that crosses the edge into two. No neighbour is
+// skipped: a particle j in a skipped row or cell has sum (q_i - q_j)^2 >= R2.
+template <int D, bool PER, typename F>
+__device__ __forceinline__ void for_neighbour_runs(const Inst& I, const int4& p,
+                                                   const uint32_t* __restrict__ start, F&& visit) {
+  const int sb = I.sbits;
+  const int nx = I.scell[0], ny = I.scell[1], nz = D == 3 ? I.scell[2] : 1;
+  const int cy = min(max(p.y >> sb, 0), ny - 1);
+  const int cz = D == 3 ? min(max(p.z >> sb, 0), nz - 1) : 0;
   const long long base = I.cell_base;
-  for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
-    int z = cz + dz;
+  for (int dz = (D == 3 ? -2 : 0); dz <= (D == 3 ? 2 : 0); ++dz) {
+    const int zu = cz + dz;
+    int z = 0;
+    long long dz2 = 0;
     if (D == 3) {
-      if (I.period[2]) z = (z + nz) % nz;
-      else if (z < 0 || z >= nz) continue;
+      if (PER && I.period[2]) z = wrap_cell(zu, nz);
+      else if (zu < 0 || zu >= nz) continue;
+      else z = zu;
+      dz2 = slab_d2(p.z, zu, sb);
+      if (dz2 >= I.R2) continue;
     }
-    for (int dy = -1; dy <= 1; ++dy) {
-      int y = cy + dy;
-      if (I.period[1]) y = (y + ny) % ny;
-      else if (y < 0 || y >= ny) continue;
-      long long row = base + ((long long)z * ny + y) * nx;
-      int x0 = cx - 1, x1 = cx + 1;
-      if (I.period[0] && (x0 < 0 || x1 >= nx)) {
-        for (int dx = -1; dx <= 1; ++dx) {
-          int x = (cx + dx + nx) % nx;
-          visit(start[row + x], start[row + x + 1]);
+    for (int dy = -2; dy <= 2; ++dy) {
+      const int yu = cy + dy;
+      int y;
+      if (PER && I.period[1]) y = wrap_cell(yu, ny);
+      else if (yu < 0 || yu >= ny) continue;
+      else y = yu;
+      const long long rem = I.R2 - dz2 - slab_d2(p.y, yu, sb);
+      if (rem <= 0) continue;
+      const long long xr = isqrt_below(rem);
+      int xa = (int)(((long long)p.x - xr) >> sb), xb = (int)(((long long)p.x + xr) >> sb);
+      const long long row = base + ((long long)z * ny + y) * nx;
+      if (PER && I.period[0]) {
+        if (xa < 0) {
+          visit(start[row + xa + nx], start[row + nx]);
+          xa = 0;
+        }
+        if (xb >= nx) {
+          visit(start[row + xa], start[row + nx]);
+          visit(start[row], start[row + xb - nx + 1]);
+          continue;
         }
       } else {
-        if (x0 < 0) x0 = 0;
-        if (x1 >= nx) x1 = nx - 1;
-        visit(start[row + x0], start[row + x1 + 1]);
+        xa = max(xa, 0);
+        xb = min(xb, nx - 1);
+        if (xa > xb) continue;
       }
+      visit(start[row + xa], start[row + xb + 1]);
     }
   }
 }
@@ -269,12 +312,9 @@ k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst
   const float R2f = (float)I.R2;
   const float lo = R2f * (1.0f - 9.5367431640625e-07f), hi = R2f * (1.0f + 9.5367431640625e-07f);
   const int4 pi = P[i];
-  int cx = min(max(pi.x >> I.bits, 0), I.ncell[0] - 1);
-  int cy = min(max(pi.y >> I.bits, 0), I.ncell[1] - 1);
-  int cz = D == 3 ? min(max(pi.z >> I.bits, 0), I.ncell[2] - 1) : 0;
   int nf = 0, nw = 0;
   bool overflow = false;
-  for_neighbour_cells<D>(I, cx, cy, cz, fstart, [&](uint32_t b, uint32_t e) {
+  for_neighbour_runs<D, PER>(I, pi, fstart, [&](uint32_t b, uint32_t e) {
     for (uint32_t j = b; j < e; j += 2) {
       const uint32_t j2 = j + 1 < e ? j + 1 : j;     // odd tail: test j twice, keep once
       bool in_a, in_b;
@@ -294,7 +334,7 @@ k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst
   if (nf > cap) nf = cap;
   const int w0 = wall_slot0(nf);
   if (WP) {
-    for_neighbour_cells<D>(I, cx, cy, cz, wstart, [&](uint32_t b, uint32_t e) {
+    for_neighbour_runs<D, PER>(I, pi, wstart, [&](uint32_t b, uint32_t e) {
       for (uint32_t j = b; j < e; j += 2) {
         const uint32_t j2 = j + 1 < e ? j + 1 : j;
         bool in_a, in_b;

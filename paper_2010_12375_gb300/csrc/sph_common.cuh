@@ -37,9 +37,11 @@ struct Inst {
   float g[3];
   float eta;                     // rho0 * nu
   float mass;                    // uniform particle mass
-  int   ncell[3];
+  int   ncell[3];                // cells per axis (position frame: q >> bits)
+  int   scell[3];                // search cells per axis, 2 ncell (1 on an unused axis)
   int   period[3];               // period in quanta on periodic axes, else 0
   int   bits;
+  int   sbits;                   // search cell of a particle: q >> sbits, sbits = bits - 1
   int   free_surface;
   long long R2;                  // integer neighbour threshold
   long long cell_base;           // first global cell of this instance

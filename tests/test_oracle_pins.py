@@ -133,14 +133,14 @@ def test_quantisation_contract():
     assert ncell == [38, 38] and abs(cell * 38 - 1.0) < 1e-15 and cell >= 2 * tg.h
 
 
-def test_cell_permutation_orders_by_cell_then_id():
+def test_cell_permutation_orders_by_search_cell_then_id():
     prob, pos, _ = _random_problem(2, 800, 11, False)
     prm = o.Params.from_problem(prob)
     ids = np.random.default_rng(2).permutation(800)
     perm = o.cell_permutation(pos, ids, prm)
     assert sorted(perm.tolist()) == sorted(ids.tolist())
-    cell = 2 * prm.h
-    ncx = int(math.ceil((prm.hi[0] - prm.lo[0]) / cell))
+    cell = prm.h                                               # half of the 2h cell
+    ncx = 2 * int(math.ceil((prm.hi[0] - prm.lo[0]) / (2 * prm.h)))
     where = {int(i): k for k, i in enumerate(ids)}
     c = np.floor((pos - prm.lo) / cell).astype(int)           # FP64 cell, away from edges
     flat = c[:, 0] + ncx * c[:, 1]
