@@ -209,46 +209,44 @@ __global__ void k_copy_back(int64_t n, const int4* __restrict__ Pin, const float
 }
 
 // ---------------------------------------------------------------- neighbours ---------
-// Largest x with x^2 < v (v >= 1), exact in integers.
-__device__ __forceinline__ long long isqrt_below(long long v) {
-  long long x = (long long)sqrtf((float)(v - 1));
-  while (x > 0 && x * x > v - 1) --x;
-  while ((x + 1) * (x + 1) <= v - 1) ++x;
-  return x;
-}
-
-// Squared distance (quanta) from coordinate q to the slab of search cell c (unwrapped).
-__device__ __forceinline__ long long slab_d2(int q, int c, int sbits) {
-  const long long lo = (long long)c << sbits, hi = lo + (1ll << sbits) - 1;
-  const long long d = q < lo ? lo - q : (q > hi ? q - hi : 0);
-  return d * d;
-}
-
 __device__ __forceinline__ int wrap_cell(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+// Distance (quanta) from a point at offset o inside its search cell (width S) to the
+// slab of the cell d rows away; exact integers below 2^23, so exact in FP32.
+__device__ __forceinline__ float slab_gap(int d, float o, float S) {
+  return d > 0 ? (float)d * S - o : (d < 0 ? o + (float)(-d - 1) * S + 1.0f : 0.0f);
+}
 
 // Visit the search-cell runs that can hold a neighbour of the particle at p: for every
 // row (dy, dz) in [-2, 2]^(D-1) whose slab lies closer than 2h, the x cells that meet the
 // sphere's chord in that slab. Within a row the cells of a run are one contiguous slot
-// range; a periodic x axis splits a run that crosses the edge into two. No neighbour is
-// skipped: a particle j in a skipped row or cell has sum (q_i - q_j)^2 >= R2.
+// range; a periodic x axis splits a run that crosses the edge into two. The row test and
+// the chord are evaluated in FP32 against R2 (1 + 2^-20), a margin above every rounding
+// error of the squares, so they only ever err towards visiting more: a particle j in a
+// skipped row or cell has sum (q_i - q_j)^2 >= R2 and is not a neighbour.
 template <int D, bool PER, typename F>
 __device__ __forceinline__ void for_neighbour_runs(const Inst& I, const int4& p,
                                                    const uint32_t* __restrict__ start, F&& visit) {
   const int sb = I.sbits;
+  const float S = (float)(1 << sb);
   const int nx = I.scell[0], ny = I.scell[1], nz = D == 3 ? I.scell[2] : 1;
   const int cy = min(max(p.y >> sb, 0), ny - 1);
   const int cz = D == 3 ? min(max(p.z >> sb, 0), nz - 1) : 0;
+  const float oy = (float)(p.y - (cy << sb));
+  const float oz = D == 3 ? (float)(p.z - (cz << sb)) : 0.0f;
+  const float R2m = (float)I.R2 * (1.0f + 9.5367431640625e-07f);
   const long long base = I.cell_base;
   for (int dz = (D == 3 ? -2 : 0); dz <= (D == 3 ? 2 : 0); ++dz) {
-    const int zu = cz + dz;
     int z = 0;
-    long long dz2 = 0;
+    float gz2 = 0.0f;
     if (D == 3) {
+      const int zu = cz + dz;
       if (PER && I.period[2]) z = wrap_cell(zu, nz);
       else if (zu < 0 || zu >= nz) continue;
       else z = zu;
-      dz2 = slab_d2(p.z, zu, sb);
-      if (dz2 >= I.R2) continue;
+      const float gz = fmaxf(slab_gap(dz, oz, S), 0.0f);
+      gz2 = gz * gz;
+      if (gz2 >= R2m) continue;
     }
     for (int dy = -2; dy <= 2; ++dy) {
       const int yu = cy + dy;
@@ -256,9 +254,11 @@ __device__ __forceinline__ void for_neighbour_runs(const Inst& I, const int4& p,
       if (PER && I.period[1]) y = wrap_cell(yu, ny);
       else if (yu < 0 || yu >= ny) continue;
       else y = yu;
-      const long long rem = I.R2 - dz2 - slab_d2(p.y, yu, sb);
-      if (rem <= 0) continue;
-      const long long xr = isqrt_below(rem);
+      const float gy = fmaxf(slab_gap(dy, oy, S), 0.0f);
+      const float rem = R2m - gz2 - gy * gy;
+      if (rem <= 0.0f) continue;
+      // |dx| of a neighbour is below sqrt(rem); rsqrt-based root within 2 quanta
+      const long long xr = (long long)(rem * rsqrtf(rem)) + 2;
       int xa = (int)(((long long)p.x - xr) >> sb), xb = (int)(((long long)p.x + xr) >> sb);
       const long long row = base + ((long long)z * ny + y) * nx;
       if (PER && I.period[0]) {
@@ -280,6 +280,28 @@ __device__ __forceinline__ void for_neighbour_runs(const Inst& I, const int4& p,
     }
   }
 }
+
+// Appends neighbour indices to one particle's quad-interleaved row (slot s of particle i
+// at ((s >> 2) n + i) 4 + (s & 3)) with a running pointer instead of a product per slot.
+struct RowWriter {
+  int* p;
+  int64_t stride;   // 4n ints between consecutive quads of one particle
+  int sub, count, cap;
+  __device__ __forceinline__ RowWriter(int* nbr, int64_t n, int64_t i, int slot0, int cap_)
+      : p(nbr + ((int64_t)(slot0 >> 2) * n + i) * 4), stride(4 * n), sub(slot0 & 3), count(0), cap(cap_ - slot0) {}
+  __device__ __forceinline__ void push(int j, bool& overflow) {
+    if (count < cap) {
+      p[sub] = j;
+      if (++sub == 4) {
+        sub = 0;
+        p += stride;
+      }
+    } else {
+      overflow = true;
+    }
+    ++count;
+  }
+};
 
 // Candidate test: the squared distance in FP32 from exactly converted integer
 // differences (error < 3 ulp); only inside a +-2^-20 band around the threshold is
@@ -312,53 +334,31 @@ k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst
   const float R2f = (float)I.R2;
   const float lo = R2f * (1.0f - 9.5367431640625e-07f), hi = R2f * (1.0f + 9.5367431640625e-07f);
   const int4 pi = P[i];
-  int nf = 0, nw = 0;
   bool overflow = false;
+  RowWriter fw(nbr, n, i, 0, cap);
   for_neighbour_runs<D, PER>(I, pi, fstart, [&](uint32_t b, uint32_t e) {
     for (uint32_t j = b; j < e; j += 2) {
       const uint32_t j2 = j + 1 < e ? j + 1 : j;     // odd tail: test j twice, keep once
       bool in_a, in_b;
       within_fast2<D, PER>(pi, P[j], P[j2], I, lo, hi, in_a, in_b);
-      if (in_a && (int64_t)j != i) {
-        if (nf < cap) nbr[slot_index(n, i, nf)] = (int)j;
-        else overflow = true;
-        ++nf;
-      }
-      if (in_b && j2 != j && (int64_t)j2 != i) {
-        if (nf < cap) nbr[slot_index(n, i, nf)] = (int)j2;
-        else overflow = true;
-        ++nf;
-      }
+      if (in_a && (int64_t)j != i) fw.push((int)j, overflow);
+      if (in_b && j2 != j && (int64_t)j2 != i) fw.push((int)j2, overflow);
     }
   });
-  if (nf > cap) nf = cap;
-  const int w0 = wall_slot0(nf);
+  const int nf = min(fw.count, cap);
+  int nw = 0;
   if (WP) {
+    RowWriter ww(nbr, n, i, wall_slot0(nf), cap);
     for_neighbour_runs<D, PER>(I, pi, wstart, [&](uint32_t b, uint32_t e) {
       for (uint32_t j = b; j < e; j += 2) {
         const uint32_t j2 = j + 1 < e ? j + 1 : j;
         bool in_a, in_b;
         within_fast2<D, PER>(pi, WP[j], WP[j2], I, lo, hi, in_a, in_b);
-        if (in_a) {
-          const int k = w0 + nw;
-          if (k < cap) {
-            nbr[slot_index(n, i, k)] = (int)j;
-            ++nw;
-          } else {
-            overflow = true;
-          }
-        }
-        if (in_b && j2 != j) {
-          const int k = w0 + nw;
-          if (k < cap) {
-            nbr[slot_index(n, i, k)] = (int)j2;
-            ++nw;
-          } else {
-            overflow = true;
-          }
-        }
+        if (in_a) ww.push((int)j, overflow);
+        if (in_b && j2 != j) ww.push((int)j2, overflow);
       }
     });
+    nw = min(ww.count, max(cap - wall_slot0(nf), 0));
   }
   if (overflow) raise_error(g, ERR_CAPACITY, i);
   nbc[i] = (uint32_t)nf | ((uint32_t)nw << 16);
