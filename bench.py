@@ -39,8 +39,8 @@ UNIT = "particle-substeps/s"
 # profiles/pressure_relaxation_dam_break_3d.md; it is scaled to the benchmark's particle
 # count (the traffic is per particle: state records plus its neighbour row). Valid only
 # for the kernel sources whose hash is recorded with it.
-TRAFFIC_BYTES_PER_PARTICLE = 389.66
-TRAFFIC_SOURCE_HASH = "a11ba06d4e15d3b4"
+TRAFFIC_BYTES_PER_PARTICLE = 390.32
+TRAFFIC_SOURCE_HASH = "bd5f5ba2ecb13557"
 
 
 def kernel_source_hash():

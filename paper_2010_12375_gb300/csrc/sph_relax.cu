@@ -28,6 +28,13 @@ namespace sph {
 namespace {
 
 constexpr int kMaxBlock = 512;         // launch variants use 128, 256 or 512 threads
+
+// Resident blocks per SM each launch variant is compiled for (its register budget):
+// 768 threads per SM for the pressure relaxation (80 registers) and 896 for the density
+// relaxation (72) at 128-thread blocks, measured fastest on the 8M 3D dam break (more
+// warps in flight hide the neighbour gathers better than a larger register budget).
+constexpr int pr_min_blocks(int block) { return block == 128 ? 6 : (block == 256 ? 3 : 1); }
+constexpr int dr_min_blocks(int block) { return block == 128 ? 7 : (block == 256 ? 3 : 1); }
 constexpr float kTinyR2 = 1e-30f;     // keeps rsqrt finite for a pair at zero distance
 
 inline unsigned grid_for(int64_t threads, int block) {
@@ -170,8 +177,8 @@ __device__ __forceinline__ void pr_wall2(PrCtx& C, const int4& pi, const float4&
 // TPP threads share one particle: lane `sub` takes quads sub, sub + TPP, ... of its row,
 // and the lanes' compensated sums are combined in a fixed order. TPP = 1 is one thread per
 // particle; 2 and 4 trade per-thread work for more threads in flight.
-template <int D, bool PER, int TPP>
-__global__ void __launch_bounds__(kMaxBlock, 1)
+template <int D, bool PER, int TPP, int BLK>
+__global__ void __launch_bounds__(BLK, pr_min_blocks(BLK))
 k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __restrict__ VS,
                       int4* __restrict__ PH, float4* __restrict__ VH,
                       const float* __restrict__ mass, const int* __restrict__ inst_of,
@@ -338,8 +345,8 @@ __device__ __forceinline__ void dr_wall2(DrCtx& C, const int4& pi, const float4&
   kahan2(C.s, C.nc, mul2(Vw, sub2(Us, UL)), mul2(G.fw, G.r));
 }
 
-template <int D, bool PER, int TPP>
-__global__ void __launch_bounds__(kMaxBlock, 1)
+template <int D, bool PER, int TPP, int BLK>
+__global__ void __launch_bounds__(BLK, dr_min_blocks(BLK))
 k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __restrict__ VH,
                      int4* __restrict__ PS, float4* __restrict__ VS,
                      const float* __restrict__ mass, const int* __restrict__ inst_of,
@@ -440,9 +447,14 @@ void launch_pr(int tpp, int block, const Buffers& b, cudaStream_t s) {
 #define SPH_PR_ARGS b.n, (const int4*)b.PS, (const float4*)b.VS, b.PH, b.VH, (const float*)b.mass, \
     b.inst_of, (const Inst*)b.inst, b.ctrl, (const int*)b.nbr, (const uint32_t*)b.nbc,                 \
     (const int4*)b.WP, (const float4*)b.WN, (const float4*)b.acc_prior, b.acc_keep, b.glob
-  if (tpp == 4) k_pressure_relaxation<D, PER, 4><<<grid, block, 0, s>>>(SPH_PR_ARGS);
-  else if (tpp == 2) k_pressure_relaxation<D, PER, 2><<<grid, block, 0, s>>>(SPH_PR_ARGS);
-  else k_pressure_relaxation<D, PER, 1><<<grid, block, 0, s>>>(SPH_PR_ARGS);
+  // one instantiation per (threads per particle, block) pair, each with its own bounds
+#define SPH_PR(T, B) k_pressure_relaxation<D, PER, T, B><<<grid, B, 0, s>>>(SPH_PR_ARGS)
+#define SPH_PR_T(T) (block == 512 ? SPH_PR(T, 512) : block == 256 ? SPH_PR(T, 256) : SPH_PR(T, 128))
+  if (tpp == 4) SPH_PR_T(4);
+  else if (tpp == 2) SPH_PR_T(2);
+  else SPH_PR_T(1);
+#undef SPH_PR_T
+#undef SPH_PR
 #undef SPH_PR_ARGS
 }
 
@@ -452,9 +464,13 @@ void launch_dr(int tpp, int block, const Buffers& b, cudaStream_t s) {
 #define SPH_DR_ARGS b.n, (const int4*)b.PH, (const float4*)b.VH, b.PS, b.VS, (const float*)b.mass, \
     b.inst_of, (const Inst*)b.inst, (const Ctrl*)b.ctrl, (const int*)b.nbr, (const uint32_t*)b.nbc,   \
     (const int4*)b.WP, (const float4*)b.WN, b.glob
-  if (tpp == 4) k_density_relaxation<D, PER, 4><<<grid, block, 0, s>>>(SPH_DR_ARGS);
-  else if (tpp == 2) k_density_relaxation<D, PER, 2><<<grid, block, 0, s>>>(SPH_DR_ARGS);
-  else k_density_relaxation<D, PER, 1><<<grid, block, 0, s>>>(SPH_DR_ARGS);
+#define SPH_DR(T, B) k_density_relaxation<D, PER, T, B><<<grid, B, 0, s>>>(SPH_DR_ARGS)
+#define SPH_DR_T(T) (block == 512 ? SPH_DR(T, 512) : block == 256 ? SPH_DR(T, 256) : SPH_DR(T, 128))
+  if (tpp == 4) SPH_DR_T(4);
+  else if (tpp == 2) SPH_DR_T(2);
+  else SPH_DR_T(1);
+#undef SPH_DR_T
+#undef SPH_DR
 #undef SPH_DR_ARGS
 }
 
