@@ -170,6 +170,21 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def aggregate_ranks(ms, units, e2e_ms, e2e_units, world, device):
+    """Replicas: units add over ranks, the job takes as long as its slowest rank.
+    Returns (total units, max ms, total e2e units, max e2e ms)."""
+    import torch
+    if world <= 1:
+        return float(units), float(ms), float(e2e_units), float(e2e_ms)
+    import torch.distributed as dist
+    per_rank = torch.tensor([ms, units, e2e_ms, e2e_units], dtype=torch.float64, device=device)
+    total = per_rank.clone()
+    dist.all_reduce(total, op=dist.ReduceOp.SUM)
+    mx = per_rank.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    return float(total[1]), float(mx[0]), float(total[3]), float(mx[2])
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -253,17 +268,8 @@ def run_ours(args, rank, world, local_rank):
     bytes_io = N * (2 * dim + 2) * 8
 
     # ---------------- aggregate over ranks
-    per_rank = torch.tensor([ms, N * substeps, e2e_ms, N * e2e_sub], dtype=torch.float64, device=dev)
-    if world > 1:
-        ms_t = per_rank.clone()
-        dist.all_reduce(ms_t, op=dist.ReduceOp.SUM)
-        mx = per_rank.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        total_units, total_e2e_units = float(ms_t[1]), float(ms_t[3])
-        ms_max, e2e_ms_max = float(mx[0]), float(mx[2])
-    else:
-        total_units, total_e2e_units = float(per_rank[1]), float(per_rank[3])
-        ms_max, e2e_ms_max = ms, e2e_ms
+    total_units, ms_max, total_e2e_units, e2e_ms_max = aggregate_ranks(
+        ms, N * substeps, e2e_ms, N * e2e_sub, world, dev)
     value = total_units / (ms_max * 1e-3)
     e2e_value = total_e2e_units / (e2e_ms_max * 1e-3)
 

@@ -124,18 +124,19 @@ template <int D, bool PER>
 __device__ __forceinline__ void pr_fluid2(PrCtx& C, const int4& pi, const float4& vi, const int4& pa,
                                           const int4& pb, const float4& va, const float4& vb, float2 mj,
                                           float2 DQ) {
-  const float2 HDT = f2(C.hdt);
-  const float2 rx = pair_axis<PER>(pi.x, pa.x, pb.x, C.px, DQ, mul2(HDT, sub2(f2(vi.x), make_float2(va.x, vb.x))));
-  const float2 ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(HDT, sub2(f2(vi.y), make_float2(va.y, vb.y))));
+  const float2 HDT = f2(C.hdt), MHDT = f2(-C.hdt);
+  // v_j - v_i; hdt (v_i - v_j) = (-hdt)(v_j - v_i) exactly, so one difference serves both
+  const float2 dvx = sub2(make_float2(va.x, vb.x), f2(vi.x));
+  const float2 dvy = sub2(make_float2(va.y, vb.y), f2(vi.y));
+  const float2 dvz = D == 3 ? sub2(make_float2(va.z, vb.z), f2(vi.z)) : f2(0.f);
+  const float2 rx = pair_axis<PER>(pi.x, pa.x, pb.x, C.px, DQ, mul2(MHDT, dvx));
+  const float2 ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(MHDT, dvy));
   float2 rz = f2(0.f);
-  if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(HDT, sub2(f2(vi.z), make_float2(va.z, vb.z))));
+  if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(MHDT, dvz));
   const Geo2 G = geometry2(rx, ry, rz, C.inv_h, C.dwr);
   const float2 dev_j = fma2(HDT, make_float2(va.w, vb.w), make_float2(i2f(pa.w), i2f(pb.w)));
   const float2 rho_j = add2(f2(C.rho0), dev_j);
   // U_L - U_R = (v_j - v_i).r_ij / |r_ij|
-  const float2 dvx = sub2(make_float2(va.x, vb.x), f2(vi.x));
-  const float2 dvy = sub2(make_float2(va.y, vb.y), f2(vi.y));
-  const float2 dvz = sub2(make_float2(va.z, vb.z), f2(vi.z));
   const float2 dU = mul2(fma2(dvx, rx, fma2(dvy, ry, mul2(dvz, rz))), G.inv_r);
   const float2 beta = min2(mul2(f2(C.kc), max2(dU, 0.0f)), 1.0f);
   // P* = (p_i + p_j)/2 + (c0/4)(rho_i + rho_j) beta (U_L - U_R)
