@@ -39,13 +39,13 @@ UNIT = "particle-substeps/s"
 # profiles/pressure_relaxation_dam_break_3d.md; it is scaled to the benchmark's particle
 # count (the traffic is per particle: state records plus its neighbour row). Valid only
 # for the kernel sources whose hash is recorded with it.
-TRAFFIC_BYTES_PER_PARTICLE = 390.32
-TRAFFIC_SOURCE_HASH = "bd5f5ba2ecb13557"
+TRAFFIC_BYTES_PER_PARTICLE = 390.91
+TRAFFIC_SOURCE_HASH = "ee5ab61ffcc66fdc"
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sph_common.cuh", "sph_relax.cu"):
+    for f in ("sph_common.cuh", "sph_relax.cuh", "sph_relax_pr.cu"):
         with open(os.path.join(ROOT, "paper_2010_12375_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -202,6 +202,10 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
+    # the sampler starts before the warm-up so nvidia-smi's own start-up stays outside the
+    # timed region; its samples cover the warm-up and the timed steps
+    clocks = ClockSampler(local_rank)
+    clocks.start()
     tuned = None
     cfg = None
     if args.launch_config:
@@ -221,21 +225,22 @@ def run_ours(args, rank, world, local_rank):
     sph.sph_set_kernel_timing(sim.handle, not args.graph)
     d0 = sim.diagnostics()
     l0 = sim.kernel_launches()
-    clocks = ClockSampler(local_rank)
-    clocks.start()
     barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    # one event per advection-step boundary: the region is first to last, and the
+    # per-step split shows any outlier step
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
     t_wall = time.perf_counter()
-    sim.step(args.steps)
-    ev1.record(stream)
+    for k in range(args.steps):
+        sim.step(1)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
     launches = sim.kernel_launches() - l0
     d1 = sim.diagnostics()
     ktimes, kcount = sph.sph_kernel_times(sim.handle)
@@ -324,6 +329,7 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": bytes_io, "steps": e2e_steps},
             "cpu_baseline": cpu,
             "wall_s_timed": t_wall,
+            "step_ms": {"min": step_ms[0], "median": step_ms[len(step_ms) // 2], "max": step_ms[-1]},
         }
         print(json.dumps(line), flush=True)
     sim.close()

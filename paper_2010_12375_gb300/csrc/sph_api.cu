@@ -177,6 +177,10 @@ Inst make_inst(const sph_params& p) {
   I.sig_hi = (float)sig;
   I.sig_lo = (float)(sig - (double)I.sig_hi);
   I.rho0_over_sigma0 = (float)(p.rho0 / sigma0);
+  I.kc = sph::kLimiter / I.c0;                   // FP32 operations, as on the device
+  I.qc0 = 0.25f * I.c0;
+  I.hc0sq = 0.5f * I.c0sq;
+  I.inv_c0sq = 1.0f / I.c0sq;
   for (int a = 0; a < 3; ++a) I.g[a] = a < d ? (float)p.gravity[a] : 0.0f;
   I.eta = (float)(p.rho0 * p.nu);
   I.mass = 0.0f;
@@ -519,6 +523,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
   DALLOC(h, b.count, n_cells);
   DALLOC(h, b.fstart, n_cells + 1);
   DALLOC(h, b.wstart, n_cells + 1);
+  DALLOC(h, b.wnear, n_cells);
   DALLOC(h, b.scan_tmp, sph::scan_tmp_elems(n_cells));
   DALLOC(h, b.WP, n_wall);
   DALLOC(h, b.WN, n_wall);
@@ -561,6 +566,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
     if (r != SPH_OK) return r;
   }
   CK(h, cudaMemcpy(b.inst, h->hinst.data(), sizeof(Inst) * n_instances, cudaMemcpyHostToDevice));
+  b.inst0 = h->hinst[0];
   std::vector<Ctrl> hc(n_instances);
   std::memset(hc.data(), 0, sizeof(Ctrl) * n_instances);
   CK(h, cudaMemcpy(b.ctrl, hc.data(), sizeof(Ctrl) * n_instances, cudaMemcpyHostToDevice));
@@ -579,6 +585,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
     CK(h, cudaStreamSynchronize(s));
   }
   sph::sort_walls(b, b.PH, b.VH, b.wid, s);
+  sph::flag_near_wall_cells(b, reinterpret_cast<uint8_t*>(b.count), s);   // count: scratch here
   {
     const auto cache = read_autotune_cache();
     const auto it = cache.find(autotune_key(h));

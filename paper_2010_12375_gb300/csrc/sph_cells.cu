@@ -217,6 +217,16 @@ __device__ __forceinline__ float slab_gap(int d, float o, float S) {
   return d > 0 ? (float)d * S - o : (d < 0 ? o + (float)(-d - 1) * S + 1.0f : 0.0f);
 }
 
+// Flattened search cell of a particle (clamped to its tank's grid).
+template <int D>
+__device__ __forceinline__ long long search_cell(const Inst& I, const int4& p) {
+  const int sb = I.sbits;
+  const int cx = min(max(p.x >> sb, 0), I.scell[0] - 1);
+  const int cy = min(max(p.y >> sb, 0), I.scell[1] - 1);
+  const int cz = D == 3 ? min(max(p.z >> sb, 0), I.scell[2] - 1) : 0;
+  return I.cell_base + ((long long)cz * I.scell[1] + cy) * I.scell[0] + cx;
+}
+
 // Visit the search-cell runs that can hold a neighbour of the particle at p: for every
 // row (dy, dz) in [-2, 2]^(D-1) whose slab lies closer than 2h, the x cells that meet the
 // sphere's chord in that slab. Within a row the cells of a run are one contiguous slot
@@ -326,8 +336,9 @@ template <int D, bool PER>
 __global__ void __launch_bounds__(kBlock)
 k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst_of,
              const Inst* __restrict__ inst, const uint32_t* __restrict__ fstart,
-             const int4* __restrict__ WP, const uint32_t* __restrict__ wstart, int cap,
-             int* __restrict__ nbr, uint32_t* __restrict__ nbc, Global* g) {
+             const int4* __restrict__ WP, const uint32_t* __restrict__ wstart,
+             const uint8_t* __restrict__ wnear, int cap, int* __restrict__ nbr,
+             uint32_t* __restrict__ nbc, Global* g) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Inst& I = inst[inst_of ? inst_of[i] : 0];
@@ -347,7 +358,7 @@ k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst
   });
   const int nf = min(fw.count, cap);
   int nw = 0;
-  if (WP) {
+  if (WP && wnear[search_cell<D>(I, pi)]) {           // no wall within reach: skip the pass
     RowWriter ww(nbr, n, i, wall_slot0(nf), cap);
     for_neighbour_runs<D, PER>(I, pi, wstart, [&](uint32_t b, uint32_t e) {
       for (uint32_t j = b; j < e; j += 2) {
@@ -380,6 +391,43 @@ __global__ void k_iota(int64_t n, int* __restrict__ a) {
   if (i < n) a[i] = (int)i;
 }
 
+// Near-wall flags of the search cells: a cell is flagged when a wall particle lies within
+// two search cells on every axis, i.e. in the 5^d block the neighbour search visits. The
+// occupancy of the wall grid is dilated by +-2 cells one axis at a time.
+__device__ __forceinline__ int cell_instance(const Inst* __restrict__ inst, int n_inst, long long c) {
+  int lo = 0, hi = n_inst - 1;                 // last instance whose first cell is <= c
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].cell_base <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_wall_occupied(int64_t n_cells, const uint32_t* __restrict__ wstart, uint8_t* __restrict__ out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n_cells) out[c] = wstart[c + 1] > wstart[c] ? 1 : 0;
+}
+
+__global__ void k_dilate_axis(int64_t n_cells, int axis, const Inst* __restrict__ inst, int n_inst,
+                              const uint8_t* __restrict__ in, uint8_t* __restrict__ out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const Inst& I = inst[cell_instance(inst, n_inst, c)];
+  long long stride = 1;
+  for (int a = 0; a < axis; ++a) stride *= I.scell[a];
+  const int len = I.scell[axis];
+  const int pos = (int)(((c - I.cell_base) / stride) % len);
+  uint8_t v = 0;
+  for (int d = -2; d <= 2; ++d) {
+    int p = pos + d;
+    if (I.period[axis]) p = p < 0 ? p + len : (p >= len ? p - len : p);
+    else if (p < 0 || p >= len) continue;
+    v |= in[c + (long long)(p - pos) * stride];
+  }
+  out[c] = v;
+}
+
 }  // namespace
 
 void launch_hash(const Buffers& b, cudaStream_t s, int64_t* launches) {
@@ -408,8 +456,8 @@ void launch_neighbours(const Buffers& b, cudaStream_t s, int64_t* launches) {
   const int4* wp = b.nw ? b.WP : nullptr;
   auto kern = b.dim == 2 ? (b.any_periodic ? k_neighbours<2, true> : k_neighbours<2, false>)
                          : (b.any_periodic ? k_neighbours<3, true> : k_neighbours<3, false>);
-  kern<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.fstart, wp, b.wstart, b.cap,
-                                        b.nbr, b.nbc, b.glob);
+  kern<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.fstart, wp, b.wstart, b.wnear,
+                                        b.cap, b.nbr, b.nbc, b.glob);
   ++*launches;
 }
 
@@ -435,6 +483,17 @@ void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStre
   cudaMemcpyAsync(b.WP, WP_tmp, sizeof(int4) * b.nw, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(b.WN, WN_tmp, sizeof(float4) * b.nw, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(b.wid, b.key, sizeof(int) * b.nw, cudaMemcpyDeviceToDevice, s);
+}
+
+// b.wnear from the sorted walls; tmp holds n_cells bytes of scratch.
+void flag_near_wall_cells(const Buffers& b, uint8_t* tmp, cudaStream_t s) {
+  if (b.n_cells == 0) return;
+  const unsigned grid = grid_for(b.n_cells);
+  uint8_t* bufs[2] = {b.wnear, tmp};
+  k_wall_occupied<<<grid, kBlock, 0, s>>>(b.n_cells, b.wstart, bufs[b.dim & 1]);
+  for (int a = 0; a < b.dim; ++a)       // ping-pong so the last pass writes b.wnear
+    k_dilate_axis<<<grid, kBlock, 0, s>>>(b.n_cells, a, b.inst, b.n_inst, bufs[(b.dim + a) & 1],
+                                          bufs[(b.dim + a + 1) & 1]);
 }
 
 }  // namespace sph

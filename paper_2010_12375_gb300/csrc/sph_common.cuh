@@ -34,6 +34,10 @@ struct Inst {
   float dwr_a;                   // -5 alpha_d / h^2 : (dW/dr)/r = dwr_a (1 - q/2)^3
   float sig_hi, sig_lo;          // W(0) - sumW0 as a float pair (hi + lo)
   float rho0_over_sigma0;
+  float kc;                      // limiter / c0 (low-dissipation solver)
+  float qc0;                     // c0 / 4
+  float hc0sq;                   // c0^2 / 2
+  float inv_c0sq;                // 1 / c0^2
   float g[3];
   float eta;                     // rho0 * nu
   float mass;                    // uniform particle mass

@@ -21,6 +21,7 @@ struct Buffers {
   int n_inst = 1, dim = 2, cap = 0;
   bool any_periodic = false;      // some tank has a periodic axis
   Inst* inst = nullptr;           // [n_inst]
+  Inst inst0{};                   // host copy of instance 0 (kernel argument when n_inst == 1)
   Ctrl* ctrl = nullptr;           // [n_inst]
   Global* glob = nullptr;         // [1]
   const int* inst_of = nullptr;   // [n] instance of each fluid slot (NULL when n_inst == 1)
@@ -44,6 +45,7 @@ struct Buffers {
   int4* WP = nullptr;  float4* WN = nullptr;
   int* wid = nullptr;             // [nw] caller row of each sorted wall slot
   uint32_t* wstart = nullptr;     // [n_cells + 1]
+  uint8_t* wnear = nullptr;       // [n_cells] 1: a wall particle lies within two search cells
   // neighbours (column-major ELL: nbr[k * n + i])
   int* nbr = nullptr;
   uint32_t* nbc = nullptr;        // [n] fluid count | wall count << 16
@@ -58,6 +60,7 @@ void launch_hash(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_neighbours(const Buffers& b, cudaStream_t s, int64_t* launches);
 void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStream_t s);
+void flag_near_wall_cells(const Buffers& b, uint8_t* tmp, cudaStream_t s);
 
 // import / export
 void launch_import(const Buffers& b, const double* pos, const double* vel, const double* rho,

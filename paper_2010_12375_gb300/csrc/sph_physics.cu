@@ -4,7 +4,7 @@
 //   k_viscous              Eq. eqviscous (once per advection step, fluid pairs)
 //   k_dt_advection         Eq. dt-advection (one thread per instance, FP64)
 //   k_dt_acoustic          Eq. dt-relax clamped to the advection step (one thread per instance)
-//   (the acoustic-substep relaxation kernels live in sph_relax.cu)
+//   (the acoustic-substep relaxation kernels live in sph_relax.cuh)
 //
 // Conventions: r_ij = r_i - r_j, e_ij = -r_ij/|r_ij| points from i to j, and
 // grad_i W_ij = (dW/dr) r_ij/|r_ij|. Interface states of the low-dissipation

@@ -21,6 +21,8 @@
 // distance whose contribution is exactly zero. Pairs that drifted past 2h get
 // t = max(1 - q/2, 0) = 0 and contribute nothing, with no branch. Sums are
 // Kahan-compensated per lane and the two lanes are added at the end.
+#pragma once
+
 #include "sph_kernels.h"
 
 namespace sph {
@@ -30,10 +32,10 @@ namespace {
 constexpr int kMaxBlock = 512;         // launch variants use 128, 256 or 512 threads
 
 // Resident blocks per SM each launch variant is compiled for (its register budget):
-// 768 threads per SM for the pressure relaxation (80 registers) and 896 for the density
-// relaxation (72) at 128-thread blocks, measured fastest on the 8M 3D dam break (more
-// warps in flight hide the neighbour gathers better than a larger register budget).
-constexpr int pr_min_blocks(int block) { return block == 128 ? 6 : (block == 256 ? 3 : 1); }
+// 896 threads per SM (72 registers) for both relaxation kernels at 128-thread blocks,
+// measured fastest on the 8M 3D dam break (more warps in flight hide the neighbour
+// gathers better than a larger register budget).
+constexpr int pr_min_blocks(int block) { return block == 128 ? 7 : (block == 256 ? 3 : 1); }
 constexpr int dr_min_blocks(int block) { return block == 128 ? 7 : (block == 256 ? 3 : 1); }
 constexpr float kTinyR2 = 1e-30f;     // keeps rsqrt finite for a pair at zero distance
 
@@ -114,14 +116,14 @@ __device__ __forceinline__ float2 pair_axis(int qi, int qa, int qb, int period, 
 
 // Shared per-particle context of the pressure relaxation.
 struct PrCtx {
-  float hdt, inv_h, dwr, rho0, c0sq, kc, qc0, dev_i, rho_i, pr_i;
+  float hdt, dev_i, rho_i, pr_i;
   int px, py, pz;
   float2 sx, sy, sz, nx, ny, nz;      // Kahan sums (per lane) and negated compensations
 };
 
 // Two fluid pairs (a, b) of the pressure relaxation: V_j P* (dW/dr)/r r_ij accumulated.
 template <int D, bool PER>
-__device__ __forceinline__ void pr_fluid2(PrCtx& C, const int4& pi, const float4& vi, const int4& pa,
+__device__ __forceinline__ void pr_fluid2(const Inst& I, PrCtx& C, const int4& pi, const float4& vi, const int4& pa,
                                           const int4& pb, const float4& va, const float4& vb, float2 mj,
                                           float2 DQ) {
   const float2 HDT = f2(C.hdt), MHDT = f2(-C.hdt);
@@ -133,15 +135,15 @@ __device__ __forceinline__ void pr_fluid2(PrCtx& C, const int4& pi, const float4
   const float2 ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(MHDT, dvy));
   float2 rz = f2(0.f);
   if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(MHDT, dvz));
-  const Geo2 G = geometry2(rx, ry, rz, C.inv_h, C.dwr);
+  const Geo2 G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
   const float2 dev_j = fma2(HDT, make_float2(va.w, vb.w), make_float2(i2f(pa.w), i2f(pb.w)));
-  const float2 rho_j = add2(f2(C.rho0), dev_j);
+  const float2 rho_j = add2(f2(I.rho0), dev_j);
   // U_L - U_R = (v_j - v_i).r_ij / |r_ij|
   const float2 dU = mul2(fma2(dvx, rx, fma2(dvy, ry, mul2(dvz, rz))), G.inv_r);
-  const float2 beta = min2(mul2(f2(C.kc), max2(dU, 0.0f)), 1.0f);
+  const float2 beta = min2(mul2(f2(I.kc), max2(dU, 0.0f)), 1.0f);
   // P* = (p_i + p_j)/2 + (c0/4)(rho_i + rho_j) beta (U_L - U_R)
-  const float2 pbar = mul2(f2(0.5f * C.c0sq), add2(f2(C.dev_i), dev_j));
-  const float2 pstar = fma2(mul2(f2(C.qc0), add2(f2(C.rho_i), rho_j)), mul2(beta, dU), pbar);
+  const float2 pbar = mul2(f2(I.hc0sq), add2(f2(C.dev_i), dev_j));
+  const float2 pstar = fma2(mul2(f2(I.qc0), add2(f2(C.rho_i), rho_j)), mul2(beta, dU), pbar);
   const float2 f = mul2(mul2(mul2(mj, rcp2(rho_j)), pstar), G.fw);       // V_j P* (dW/dr)/r
   kahan2(C.sx, C.nx, f, rx);
   kahan2(C.sy, C.ny, f, ry);
@@ -150,23 +152,23 @@ __device__ __forceinline__ void pr_fluid2(PrCtx& C, const int4& pi, const float4
 
 // Two wall pairs of the pressure relaxation (one-sided problem along the wall normal).
 template <int D, bool PER>
-__device__ __forceinline__ void pr_wall2(PrCtx& C, const int4& pi, const float4& vi, const int4& qa,
-                                         const int4& qb, const float4& na, const float4& nb, float2 Vw,
-                                         float2 DQ, float g0, float g1, float g2, float inv_c0sq) {
+__device__ __forceinline__ void pr_wall2(const Inst& I, PrCtx& C, const int4& pi, const float4& vi,
+                                         const int4& qa, const int4& qb, const float4& na,
+                                         const float4& nb, float2 Vw, float2 DQ) {
   const float2 rx = pair_axis<PER>(pi.x, qa.x, qb.x, C.px, DQ, f2(C.hdt * vi.x));
   const float2 ry = pair_axis<PER>(pi.y, qa.y, qb.y, C.py, DQ, f2(C.hdt * vi.y));
   float2 rz = f2(0.f);
   if (D == 3) rz = pair_axis<PER>(pi.z, qa.z, qb.z, C.pz, DQ, f2(C.hdt * vi.z));
-  const Geo2 G = geometry2(rx, ry, rz, C.inv_h, C.dwr);
+  const Geo2 G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
   // U_L = -n.v_i, U_R = -U_L, P_R = P_L + rho_i g.(r_w - r_i), rho_R from the EoS
   const float2 UL = mul2(f2(-1.0f), fma2(make_float2(na.x, nb.x), f2(vi.x),
                                          fma2(make_float2(na.y, nb.y), f2(vi.y), mul2(make_float2(na.z, nb.z), f2(vi.z)))));
-  const float2 gr = fma2(f2(g0), rx, fma2(f2(g1), ry, mul2(f2(g2), rz)));
+  const float2 gr = fma2(f2(I.g[0]), rx, fma2(f2(I.g[1]), ry, mul2(f2(I.g[2]), rz)));
   const float2 PR = fma2(f2(-C.rho_i), gr, f2(C.pr_i));
-  const float2 rhoR = fma2(PR, f2(inv_c0sq), f2(C.rho0));
+  const float2 rhoR = fma2(PR, f2(I.inv_c0sq), f2(I.rho0));
   const float2 dU = add2(UL, UL);
-  const float2 beta = min2(mul2(f2(C.kc), max2(dU, 0.0f)), 1.0f);
-  const float2 pstar = fma2(mul2(f2(C.qc0), add2(f2(C.rho_i), rhoR)), mul2(beta, dU),
+  const float2 beta = min2(mul2(f2(I.kc), max2(dU, 0.0f)), 1.0f);
+  const float2 pstar = fma2(mul2(f2(I.qc0), add2(f2(C.rho_i), rhoR)), mul2(beta, dU),
                             mul2(f2(0.5f), add2(f2(C.pr_i), PR)));
   const float2 f = mul2(mul2(Vw, pstar), G.fw);
   kahan2(C.sx, C.nx, f, rx);
@@ -178,9 +180,9 @@ __device__ __forceinline__ void pr_wall2(PrCtx& C, const int4& pi, const float4&
 // TPP threads share one particle: lane `sub` takes quads sub, sub + TPP, ... of its row,
 // and the lanes' compensated sums are combined in a fixed order. TPP = 1 is one thread per
 // particle; 2 and 4 trade per-thread work for more threads in flight.
-template <int D, bool PER, int TPP, int BLK>
+template <int D, bool PER, int TPP, int BLK, bool UNI>
 __global__ void __launch_bounds__(BLK, pr_min_blocks(BLK))
-k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __restrict__ VS,
+k_pressure_relaxation(const Inst Ip, int64_t n, const int4* __restrict__ PS, const float4* __restrict__ VS,
                       int4* __restrict__ PH, float4* __restrict__ VH,
                       const float* __restrict__ mass, const int* __restrict__ inst_of,
                       const Inst* __restrict__ inst, Ctrl* ctrl, const int* __restrict__ nbr,
@@ -198,26 +200,20 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
   float v2 = 0.0f;
   PrCtx C;
   C.sx = C.sy = C.sz = C.nx = C.ny = C.nz = f2(0.f);
-  const Inst& I = inst[k];
+  const Inst& I = UNI ? Ip : inst[k];        // one tank: constants straight from the argument
   const float dt = (float)dtd;
   int4 pi = make_int4(0, 0, 0, 0);
   float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
   if (valid) {
     C.hdt = 0.5f * dt;
-    C.inv_h = I.inv_h;
-    C.dwr = I.dwr_a;
-    C.rho0 = I.rho0;
-    C.c0sq = I.c0sq;
-    C.kc = kLimiter / I.c0;
-    C.qc0 = 0.25f * I.c0;
     C.px = PER ? I.period[0] : 0;
     C.py = PER ? I.period[1] : 0;
     C.pz = PER ? I.period[2] : 0;
     pi = PS[i];
     vi = VS[i];
     C.dev_i = i2f(pi.w) + C.hdt * vi.w;               // Eq. verlet-first-half (density)
-    C.rho_i = C.rho0 + C.dev_i;
-    C.pr_i = C.c0sq * C.dev_i;                        // Eq. eqeos
+    C.rho_i = I.rho0 + C.dev_i;
+    C.pr_i = I.c0sq * C.dev_i;                        // Eq. eqeos
     const float2 DQ = f2(I.dq);
     const uint32_t cnt = nbc[i];
     const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
@@ -239,13 +235,11 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
         m01 = make_float2(mass[j0], mass[j1]);
         m23 = make_float2(mass[j2], mass[j3]);
       }
-      pr_fluid2<D, PER>(C, pi, vi, p0, p1, v0, v1, m01, DQ);
-      pr_fluid2<D, PER>(C, pi, vi, p2, p3, v2v, v3, m23, DQ);
+      pr_fluid2<D, PER>(I, C, pi, vi, p0, p1, v0, v1, m01, DQ);
+      pr_fluid2<D, PER>(I, C, pi, vi, p2, p3, v2v, v3, m23, DQ);
       cur = nxt;
     }
     if (nw) {
-      const float g0 = I.g[0], g1 = I.g[1], g2 = I.g[2];
-      const float inv_c0sq = 1.0f / I.c0sq;
       const int q0 = wall_slot0(nf) >> 2, nwq = (nw + 3) >> 2;
       for (int q = sub; q < nwq; q += TPP) {
         const int4 c = nb4[(int64_t)(q0 + q) * n + i];
@@ -255,8 +249,8 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
         const float4 n0 = WN[c.x], n1 = WN[w1], n2 = WN[w2], n3 = WN[w3];
         const float2 V01 = make_float2(i2f(a0.w), s + 1 < nw ? i2f(a1.w) : 0.0f);   // pads carry no volume
         const float2 V23 = make_float2(s + 2 < nw ? i2f(a2.w) : 0.0f, s + 3 < nw ? i2f(a3.w) : 0.0f);
-        pr_wall2<D, PER>(C, pi, vi, a0, a1, n0, n1, V01, DQ, g0, g1, g2, inv_c0sq);
-        pr_wall2<D, PER>(C, pi, vi, a2, a3, n2, n3, V23, DQ, g0, g1, g2, inv_c0sq);
+        pr_wall2<D, PER>(I, C, pi, vi, a0, a1, n0, n1, V01, DQ);
+        pr_wall2<D, PER>(I, C, pi, vi, a2, a3, n2, n3, V23, DQ);
       }
     }
   }
@@ -298,13 +292,13 @@ k_pressure_relaxation(int64_t n, const int4* __restrict__ PS, const float4* __re
 
 // ---------------------------------------------------------------- density relaxation ---
 struct DrCtx {
-  float hdt, inv_h, dwr, rho0, c0, dev_i, rho_i;
+  float hdt, dev_i, rho_i;
   int px, py, pz;
   float2 s, nc;
 };
 
 template <int D, bool PER>
-__device__ __forceinline__ void dr_fluid2(DrCtx& C, const int4& pi, const float4& vi, const int4& pa,
+__device__ __forceinline__ void dr_fluid2(const Inst& I, DrCtx& C, const int4& pi, const float4& vi, const int4& pa,
                                           const int4& pb, const float4& va, const float4& vb, float2 mj,
                                           float2 DQ) {
   const float2 HDT = f2(C.hdt);
@@ -313,42 +307,41 @@ __device__ __forceinline__ void dr_fluid2(DrCtx& C, const int4& pi, const float4
   const float2 ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(HDT, sub2(f2(vi.y), make_float2(va.y, vb.y))));
   float2 rz = f2(0.f);
   if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(HDT, sub2(f2(vi.z), make_float2(va.z, vb.z))));
-  const Geo2 G = geometry2(rx, ry, rz, C.inv_h, C.dwr);
+  const Geo2 G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
   const float2 dev_j = make_float2(i2f(pa.w), i2f(pb.w));
-  const float2 rho_j = add2(f2(C.rho0), dev_j);
+  const float2 rho_j = add2(f2(I.rho0), dev_j);
   // (U_R - U_L)/2 = (v_i - v_j).r_ij / (2 |r_ij|)
   const float2 dvx = sub2(f2(vi.x), make_float2(va.x, vb.x));
   const float2 dvy = sub2(f2(vi.y), make_float2(va.y, vb.y));
   const float2 dvz = sub2(f2(vi.z), make_float2(va.z, vb.z));
   const float2 half_dUR = mul2(fma2(dvx, rx, fma2(dvy, ry, mul2(dvz, rz))), mul2(G.inv_r, f2(0.5f)));
   // U* - U_L = (U_R - U_L)/2 + c0 (dev_i - dev_j)/(rho_i + rho_j)
-  const float2 dUs = fma2(mul2(f2(C.c0), sub2(f2(C.dev_i), dev_j)), rcp2(add2(f2(C.rho_i), rho_j)), half_dUR);
+  const float2 dUs = fma2(mul2(f2(I.c0), sub2(f2(C.dev_i), dev_j)), rcp2(add2(f2(C.rho_i), rho_j)), half_dUR);
   kahan2(C.s, C.nc, mul2(mul2(mj, rcp2(rho_j)), dUs), mul2(G.fw, G.r));
 }
 
 template <int D, bool PER>
-__device__ __forceinline__ void dr_wall2(DrCtx& C, const int4& pi, const float4& vi, const int4& qa,
-                                         const int4& qb, const float4& na, const float4& nb, float2 Vw,
-                                         float2 DQ, float g0, float g1, float g2, float inv_c0sq,
-                                         float pr_i) {
+__device__ __forceinline__ void dr_wall2(const Inst& I, DrCtx& C, const int4& pi, const float4& vi,
+                                         const int4& qa, const int4& qb, const float4& na,
+                                         const float4& nb, float2 Vw, float2 DQ, float pr_i) {
   const float2 rx = pair_axis<PER>(pi.x, qa.x, qb.x, C.px, DQ, f2(C.hdt * vi.x));
   const float2 ry = pair_axis<PER>(pi.y, qa.y, qb.y, C.py, DQ, f2(C.hdt * vi.y));
   float2 rz = f2(0.f);
   if (D == 3) rz = pair_axis<PER>(pi.z, qa.z, qb.z, C.pz, DQ, f2(C.hdt * vi.z));
-  const Geo2 G = geometry2(rx, ry, rz, C.inv_h, C.dwr);
+  const Geo2 G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
   const float2 UL = mul2(f2(-1.0f), fma2(make_float2(na.x, nb.x), f2(vi.x),
                                          fma2(make_float2(na.y, nb.y), f2(vi.y), mul2(make_float2(na.z, nb.z), f2(vi.z)))));
-  const float2 gr = fma2(f2(g0), rx, fma2(f2(g1), ry, mul2(f2(g2), rz)));
+  const float2 gr = fma2(f2(I.g[0]), rx, fma2(f2(I.g[1]), ry, mul2(f2(I.g[2]), rz)));
   const float2 PR = fma2(f2(-C.rho_i), gr, f2(pr_i));
-  const float2 rhoR = fma2(PR, f2(inv_c0sq), f2(C.rho0));
+  const float2 rhoR = fma2(PR, f2(I.inv_c0sq), f2(I.rho0));
   // U_R = -U_L: U* = (P_L - P_R)/(2 rho_bar c0) = rho_i g.r_iw / (c0 (rho_i + rho_R))
-  const float2 Us = mul2(mul2(f2(C.rho_i), gr), rcp2(mul2(f2(C.c0), add2(f2(C.rho_i), rhoR))));
+  const float2 Us = mul2(mul2(f2(C.rho_i), gr), rcp2(mul2(f2(I.c0), add2(f2(C.rho_i), rhoR))));
   kahan2(C.s, C.nc, mul2(Vw, sub2(Us, UL)), mul2(G.fw, G.r));
 }
 
-template <int D, bool PER, int TPP, int BLK>
+template <int D, bool PER, int TPP, int BLK, bool UNI>
 __global__ void __launch_bounds__(BLK, dr_min_blocks(BLK))
-k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __restrict__ VH,
+k_density_relaxation(const Inst Ip, int64_t n, const int4* __restrict__ PH, const float4* __restrict__ VH,
                      int4* __restrict__ PS, float4* __restrict__ VS,
                      const float* __restrict__ mass, const int* __restrict__ inst_of,
                      const Inst* __restrict__ inst, const Ctrl* __restrict__ ctrl,
@@ -362,24 +355,20 @@ k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __res
   const double dtd = ctrl[k].dt;
   if (TPP == 1 && dtd == 0.0) return;
   if (dtd == 0.0) valid = false;
-  const Inst& I = inst[k];
+  const Inst& I = UNI ? Ip : inst[k];        // one tank: constants straight from the argument
   DrCtx C;
   C.s = C.nc = f2(0.f);
   int4 pi = make_int4(0, 0, 0, 0);
   float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
   C.hdt = 0.5f * (float)dtd;
   if (valid) {
-    C.inv_h = I.inv_h;
-    C.dwr = I.dwr_a;
-    C.rho0 = I.rho0;
-    C.c0 = I.c0;
     C.px = PER ? I.period[0] : 0;
     C.py = PER ? I.period[1] : 0;
     C.pz = PER ? I.period[2] : 0;
     pi = PH[i];
     vi = VH[i];                                       // v^{n+1}
     C.dev_i = i2f(pi.w);
-    C.rho_i = C.rho0 + C.dev_i;
+    C.rho_i = I.rho0 + C.dev_i;
     const float2 DQ = f2(I.dq);
     const uint32_t cnt = nbc[i];
     const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
@@ -401,13 +390,12 @@ k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __res
         m01 = make_float2(mass[j0], mass[j1]);
         m23 = make_float2(mass[j2], mass[j3]);
       }
-      dr_fluid2<D, PER>(C, pi, vi, p0, p1, v0, v1, m01, DQ);
-      dr_fluid2<D, PER>(C, pi, vi, p2, p3, v2, v3, m23, DQ);
+      dr_fluid2<D, PER>(I, C, pi, vi, p0, p1, v0, v1, m01, DQ);
+      dr_fluid2<D, PER>(I, C, pi, vi, p2, p3, v2, v3, m23, DQ);
       cur = nxt;
     }
     if (nw) {
-      const float g0 = I.g[0], g1 = I.g[1], g2 = I.g[2];
-      const float inv_c0sq = 1.0f / I.c0sq, pr_i = I.c0sq * C.dev_i;
+      const float pr_i = I.c0sq * C.dev_i;
       const int q0 = wall_slot0(nf) >> 2, nwq = (nw + 3) >> 2;
       for (int q = sub; q < nwq; q += TPP) {
         const int4 c = nb4[(int64_t)(q0 + q) * n + i];
@@ -417,8 +405,8 @@ k_density_relaxation(int64_t n, const int4* __restrict__ PH, const float4* __res
         const float4 n0 = WN[c.x], n1 = WN[w1], n2 = WN[w2], n3 = WN[w3];
         const float2 V01 = make_float2(i2f(a0.w), s + 1 < nw ? i2f(a1.w) : 0.0f);
         const float2 V23 = make_float2(s + 2 < nw ? i2f(a2.w) : 0.0f, s + 3 < nw ? i2f(a3.w) : 0.0f);
-        dr_wall2<D, PER>(C, pi, vi, a0, a1, n0, n1, V01, DQ, g0, g1, g2, inv_c0sq, pr_i);
-        dr_wall2<D, PER>(C, pi, vi, a2, a3, n2, n3, V23, DQ, g0, g1, g2, inv_c0sq, pr_i);
+        dr_wall2<D, PER>(I, C, pi, vi, a0, a1, n0, n1, V01, DQ, pr_i);
+        dr_wall2<D, PER>(I, C, pi, vi, a2, a3, n2, n3, V23, DQ, pr_i);
       }
     }
   }
@@ -449,7 +437,9 @@ void launch_pr(int tpp, int block, const Buffers& b, cudaStream_t s) {
     b.inst_of, (const Inst*)b.inst, b.ctrl, (const int*)b.nbr, (const uint32_t*)b.nbc,                 \
     (const int4*)b.WP, (const float4*)b.WN, (const float4*)b.acc_prior, b.acc_keep, b.glob
   // one instantiation per (threads per particle, block) pair, each with its own bounds
-#define SPH_PR(T, B) k_pressure_relaxation<D, PER, T, B><<<grid, B, 0, s>>>(SPH_PR_ARGS)
+#define SPH_PR(T, B) (b.n_inst == 1                                                                 \
+      ? k_pressure_relaxation<D, PER, T, B, true><<<grid, B, 0, s>>>(b.inst0, SPH_PR_ARGS)           \
+      : k_pressure_relaxation<D, PER, T, B, false><<<grid, B, 0, s>>>(b.inst0, SPH_PR_ARGS))
 #define SPH_PR_T(T) (block == 512 ? SPH_PR(T, 512) : block == 256 ? SPH_PR(T, 256) : SPH_PR(T, 128))
   if (tpp == 4) SPH_PR_T(4);
   else if (tpp == 2) SPH_PR_T(2);
@@ -465,7 +455,9 @@ void launch_dr(int tpp, int block, const Buffers& b, cudaStream_t s) {
 #define SPH_DR_ARGS b.n, (const int4*)b.PH, (const float4*)b.VH, b.PS, b.VS, (const float*)b.mass, \
     b.inst_of, (const Inst*)b.inst, (const Ctrl*)b.ctrl, (const int*)b.nbr, (const uint32_t*)b.nbc,   \
     (const int4*)b.WP, (const float4*)b.WN, b.glob
-#define SPH_DR(T, B) k_density_relaxation<D, PER, T, B><<<grid, B, 0, s>>>(SPH_DR_ARGS)
+#define SPH_DR(T, B) (b.n_inst == 1                                                                 \
+      ? k_density_relaxation<D, PER, T, B, true><<<grid, B, 0, s>>>(b.inst0, SPH_DR_ARGS)            \
+      : k_density_relaxation<D, PER, T, B, false><<<grid, B, 0, s>>>(b.inst0, SPH_DR_ARGS))
 #define SPH_DR_T(T) (block == 512 ? SPH_DR(T, 512) : block == 256 ? SPH_DR(T, 256) : SPH_DR(T, 128))
   if (tpp == 4) SPH_DR_T(4);
   else if (tpp == 2) SPH_DR_T(2);
@@ -476,31 +468,5 @@ void launch_dr(int tpp, int block, const Buffers& b, cudaStream_t s) {
 }
 
 }  // namespace
-
-void launch_pressure_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches) {
-  if (b.n == 0) return;
-  const int tpp = b.cfg.pr_tpp, block = b.cfg.pr_block;
-  if (b.dim == 2) {
-    if (b.any_periodic) launch_pr<2, true>(tpp, block, b, s);
-    else launch_pr<2, false>(tpp, block, b, s);
-  } else {
-    if (b.any_periodic) launch_pr<3, true>(tpp, block, b, s);
-    else launch_pr<3, false>(tpp, block, b, s);
-  }
-  ++*launches;
-}
-
-void launch_density_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches) {
-  if (b.n == 0) return;
-  const int tpp = b.cfg.dr_tpp, block = b.cfg.dr_block;
-  if (b.dim == 2) {
-    if (b.any_periodic) launch_dr<2, true>(tpp, block, b, s);
-    else launch_dr<2, false>(tpp, block, b, s);
-  } else {
-    if (b.any_periodic) launch_dr<3, true>(tpp, block, b, s);
-    else launch_dr<3, false>(tpp, block, b, s);
-  }
-  ++*launches;
-}
 
 }  // namespace sph
