@@ -634,14 +634,13 @@ int sph_set_state(sph_handle* h, const double* pos, const double* vel, const dou
     ++h->launches;
   }
   // slot k holds caller row k until the next cell build
-  std::vector<int> iota(b.n);
-  for (int64_t i = 0; i < b.n; ++i) iota[i] = (int)i;
-  if (b.n) CK(h, cudaMemcpyAsync(b.id, iota.data(), sizeof(int) * b.n, cudaMemcpyHostToDevice, s));
+  sph::launch_iota(b.id, b.n, s);
+  if (b.n) ++h->launches;
   sph::launch_vmax(b, s, &h->launches);
   if (t >= 0.0) {
     CK(h, cudaMemcpyAsync(&b.ctrl[0].t, &t, sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  CK(h, cudaStreamSynchronize(s));          // the host vectors above must outlive the copies
+  CK(h, cudaStreamSynchronize(s));          // the caller's arrays may be reused on return
   h->cells_valid = false;
   CK(h, cudaGetLastError());
   return SPH_OK;

@@ -485,6 +485,10 @@ void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStre
   cudaMemcpyAsync(b.wid, b.key, sizeof(int) * b.nw, cudaMemcpyDeviceToDevice, s);
 }
 
+void launch_iota(int* a, int64_t n, cudaStream_t s) {
+  if (n > 0) k_iota<<<grid_for(n), kBlock, 0, s>>>(n, a);
+}
+
 // b.wnear from the sorted walls; tmp holds n_cells bytes of scratch.
 void flag_near_wall_cells(const Buffers& b, uint8_t* tmp, cudaStream_t s) {
   if (b.n_cells == 0) return;

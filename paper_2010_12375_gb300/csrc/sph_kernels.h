@@ -61,6 +61,7 @@ void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_neighbours(const Buffers& b, cudaStream_t s, int64_t* launches);
 void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStream_t s);
 void flag_near_wall_cells(const Buffers& b, uint8_t* tmp, cudaStream_t s);
+void launch_iota(int* a, int64_t n, cudaStream_t s);     // a[i] = i
 
 // import / export
 void launch_import(const Buffers& b, const double* pos, const double* vel, const double* rho,
