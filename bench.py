@@ -365,6 +365,9 @@ def run_workload(args):
     if args.workload == "learned":
         run_learned(args, stream)
         return
+    if args.workload == "sizes":
+        run_sizes(args)
+        return
     if args.workload == "batched":
         problems = wk.batched_dam_breaks(256)
         name = "256 independent 2D dam breaks (2k-50k fluid each), one handle"
@@ -407,6 +410,41 @@ def run_workload(args):
         out["plain_gpu"] = {"value": plain, "ms_per_step_all_tanks": total_ms / args.steps,
                             "what": "each tank in its own handle, one after another, graph loop"}
         out["speedup_vs_plain_gpu"] = out["value"] / plain
+    print(json.dumps(out), flush=True)
+
+
+def run_sizes(args):
+    """The 3D dam break at the three resolutions dp = 1/80, 1/126, 1/159 (1.02M, 4.0M, 8.04M
+    fluid), each run for --steps advection steps (200 by default here) in the CUDA-graph loop
+    after the warm-up and autotuning: throughput, and the energy, mass and front over the run."""
+    import torch
+    from paper_2010_12375_gb300 import sph, workloads as wk
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    steps = args.steps if args.steps != 20 else 200
+    rows = []
+    for n in (80, 126, 159):
+        prob = wk.dam_break_3d(n)
+        sim = sph.Simulation(prob, flags=sph.SPH_FLAG_GRAPH, stream=stream)
+        for _ in range(args.warmup):
+            sim.step(1)
+        if not args.no_autotune:
+            sph.sph_autotune(sim.handle, stream)
+        ms, d0, d1 = _timed_steps(sim, steps, stream)
+        sub = d1["substeps"] - d0["substeps"]
+        rows.append({"n": n, "n_fluid": prob.n_fluid, "value": prob.n_fluid * sub / (ms * 1e-3),
+                     "ms_per_step": ms / steps, "substeps": sub, "t": [d0["t"], d1["t"]],
+                     "energy_rel_change": (d1["energy"] - d0["energy"]) / abs(d0["energy"]),
+                     "mass_rel_change": (d1["mass"] - d0["mass"]) / d0["mass"],
+                     "front_x": [d0["front_x"], d1["front_x"]],
+                     "launch": sph.sph_get_launch_config(sim.handle)})
+        sim.close()
+        torch.cuda.empty_cache()
+    out = {"metric": "particle-substeps/s, 3D dam break at three resolutions", "unit": UNIT,
+           "n_gpus": 1, "steps": steps, "warmup": args.warmup, "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic", "loop": "graph",
+           "config": {"workload": "3D dam break 2x1x1 in a 5.366x5.366x1 tank, dp = 1/80, 1/126, 1/159"},
+           "value": rows[-1]["value"], "sizes": rows}
     print(json.dumps(out), flush=True)
 
 
@@ -459,7 +497,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch-config", default=None,
                     help="pr_tpp,pr_block,dr_tpp,dr_block: fixed launch variants instead of autotuning")
-    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned"],
+    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "sizes"],
                     help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()
     if args.warmup < 3:
