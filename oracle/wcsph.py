@@ -343,6 +343,24 @@ def _geometry(xa, xb, prm: Params):
     return rij, r, e
 
 
+def _from_rij(rij):
+    """|r_ij| and e_ij = -r_ij/|r_ij| of given pair vectors (as _geometry returns them)."""
+    r = np.sqrt(np.sum(rij * rij, axis=1))
+    safe = np.where(r > 0.0, r, 1.0)
+    e = np.where((r > 0.0)[:, None], -rij / safe[:, None], 0.0)
+    return rij, r, e
+
+
+def frozen_geometry(st: State, w: Walls, nb, prm: Params):
+    """Pair vectors r_i - r_j (minimum image) of the fluid and the wall pairs at the
+    configuration update, kept for the whole advection step (reading R11: Sec. 2.4 and
+    Sec. 6.2 store the pair geometry in the neighbour relation when it is built)."""
+    I, J, IW, KW = nb
+    rij = _geometry(st.x[I], st.x[J], prm)[0]
+    rfw = _geometry(st.x[IW], w.x[KW], prm)[0]
+    return rij, rfw
+
+
 def _scatter_add(idx, vals, n):
     if vals.ndim == 1:
         return np.bincount(idx, weights=vals, minlength=n)
@@ -398,13 +416,16 @@ def dt_acoustic(v: np.ndarray, prm: Params) -> float:
     return prm.cfl_ac * prm.h / (prm.c0 + vmax)
 
 
-def pressure_relaxation(st: State, w: Walls, nb, acc_prior, dt: float, prm: Params):
+def pressure_relaxation(st: State, w: Walls, nb, acc_prior, dt: float, prm: Params,
+                        geometry=None):
     """First half of the position-based Verlet substep.
 
     Eq. verlet-first-half: rho and r to the mid point; Eq. eqeos: pressure;
     Eq. riemannsph (momentum) for fluid pairs and the one-sided wall problem
     (Eqs. eqriepartial, eqrienoslip, eqriepright) for wall pairs;
     Eq. verlet-first-mediate: v to the new step. Returns (state, dv/dt).
+    With `geometry` (from frozen_geometry) the pair vectors are those of the
+    configuration update instead of the mid-point positions (reading R11).
     """
     I, J, IW, KW = nb
     N = st.x.shape[0]
@@ -414,7 +435,7 @@ def pressure_relaxation(st: State, w: Walls, nb, acc_prior, dt: float, prm: Para
     p = eos_pressure(rho, prm)
     acc = np.zeros((N, prm.dim))
     if I.size:
-        rij, r, e = _geometry(x[I], x[J], prm)
+        rij, r, e = _geometry(x[I], x[J], prm) if geometry is None else _from_rij(geometry[0])
         dW = kernel_dW(r, prm.h, prm.dim)
         UL = np.sum(st.v[I] * e, axis=1)
         UR = np.sum(st.v[J] * e, axis=1)
@@ -423,12 +444,15 @@ def pressure_relaxation(st: State, w: Walls, nb, acc_prior, dt: float, prm: Para
         Vj = st.m[J] / rho[J]
         acc += _scatter_add(I, (-2.0 * Vj * Ps / rho[I])[:, None] * grad, N)
     if IW.size:
-        rfw, r, e = _geometry(x[IW], w.x[KW], prm)
+        if geometry is None:
+            rfw, r, e = _geometry(x[IW], w.x[KW], prm)
+        else:
+            rfw, r, e = _from_rij(geometry[1])
         dW = kernel_dW(r, prm.h, prm.dim)
         UL = -np.sum(w.n[KW] * st.v[IW], axis=1)
         UR = -UL
         PL = p[IW]
-        PR = PL + rho[IW] * ((w.x[KW] - x[IW]) @ g)
+        PR = PL + rho[IW] * ((-rfw) @ g)              # r_w - r_f = -(r_f - r_w)
         rhoR = prm.rho0 + PR / c0 ** 2
         _, Ps = riemann(rho[IW], rhoR, UL, UR, PL, PR, c0)
         grad = (-e) * dW[:, None]
@@ -439,9 +463,10 @@ def pressure_relaxation(st: State, w: Walls, nb, acc_prior, dt: float, prm: Para
     return out, dvdt
 
 
-def density_relaxation(st: State, w: Walls, nb, dt: float, prm: Params):
+def density_relaxation(st: State, w: Walls, nb, dt: float, prm: Params, geometry=None):
     """Second half of the substep: Eq. verlet-first-final with the continuity equation
-    of Eq. riemannsph (fluid pairs) and its one-sided wall form (R4). Returns state."""
+    of Eq. riemannsph (fluid pairs) and its one-sided wall form (R4). Returns state.
+    With `geometry` the pair vectors are the frozen ones (reading R11)."""
     I, J, IW, KW = nb
     N = st.x.shape[0]
     c0, g = prm.c0, prm.gravity
@@ -450,7 +475,7 @@ def density_relaxation(st: State, w: Walls, nb, dt: float, prm: Params):
     p = eos_pressure(rho, prm)
     drho = np.zeros(N)
     if I.size:
-        _, r, e = _geometry(x[I], x[J], prm)
+        _, r, e = _geometry(x[I], x[J], prm) if geometry is None else _from_rij(geometry[0])
         dW = kernel_dW(r, prm.h, prm.dim)
         UL = np.sum(st.v[I] * e, axis=1)
         UR = np.sum(st.v[J] * e, axis=1)
@@ -458,12 +483,15 @@ def density_relaxation(st: State, w: Walls, nb, dt: float, prm: Params):
         Vj = st.m[J] / rho[J]
         drho += _scatter_add(I, 2.0 * rho[I] * Vj * (Us - UL) * dW, N)
     if IW.size:
-        _, r, e = _geometry(x[IW], w.x[KW], prm)
+        if geometry is None:
+            rfw, r, e = _geometry(x[IW], w.x[KW], prm)
+        else:
+            rfw, r, e = _from_rij(geometry[1])
         dW = kernel_dW(r, prm.h, prm.dim)
         UL = -np.sum(w.n[KW] * st.v[IW], axis=1)
         UR = -UL
         PL = p[IW]
-        PR = PL + rho[IW] * ((w.x[KW] - x[IW]) @ g)
+        PR = PL + rho[IW] * ((-rfw) @ g)
         rhoR = prm.rho0 + PR / c0 ** 2
         Us, _ = riemann(rho[IW], rhoR, UL, UR, PL, PR, c0)
         drho += _scatter_add(IW, 2.0 * rho[IW] * w.V[KW] * (Us - UL) * dW, N)
@@ -471,10 +499,10 @@ def density_relaxation(st: State, w: Walls, nb, dt: float, prm: Params):
     return State(x, st.v.copy(), rho_new, drho, st.m, st.t)
 
 
-def acoustic_substep(st: State, w: Walls, nb, acc_prior, dt: float, prm: Params):
+def acoustic_substep(st: State, w: Walls, nb, acc_prior, dt: float, prm: Params, geometry=None):
     """One pressure relaxation followed by one density relaxation with step dt."""
-    half, dvdt = pressure_relaxation(st, w, nb, acc_prior, dt, prm)
-    out = density_relaxation(half, w, nb, dt, prm)
+    half, dvdt = pressure_relaxation(st, w, nb, acc_prior, dt, prm, geometry)
+    out = density_relaxation(half, w, nb, dt, prm, geometry)
     out.t = st.t + dt
     return out, dvdt, half
 
@@ -487,19 +515,21 @@ class StepInfo:
     pairs: int = 0
 
 
-def advection_step(st: State, w: Walls, prm: Params, neighbours=neighbour_sets):
+def advection_step(st: State, w: Walls, prm: Params, neighbours=neighbour_sets, frozen=False):
     """One dual-criteria step: neighbour set, Dt_ad, density re-initialisation, viscous
-    acceleration, then acoustic substeps until Dt_ad is covered (Sec. 2.3-2.4, R7)."""
+    acceleration, then acoustic substeps until Dt_ad is covered (Sec. 2.3-2.4, R7).
+    frozen=True keeps the pair geometry of the configuration update (reading R11)."""
     st = st.copy()
     nb = neighbours(st.x, w.x, prm)
     Dt = dt_advection(st.v, prm)
     st.rho = density_summation(st, w, nb, prm)
     acc_prior = viscous_acceleration(st, nb, prm)
+    geometry = frozen_geometry(st, w, nb, prm) if frozen else None
     tau = 0.0
     info = StepInfo(dt_ad=Dt, substeps=0, pairs=int(nb[0].size + nb[2].size))
     while tau < Dt * (1.0 - LOOP_SLACK):
         dt = min(dt_acoustic(st.v, prm), Dt - tau)
-        st, _, _ = acoustic_substep(st, w, nb, acc_prior, dt, prm)
+        st, _, _ = acoustic_substep(st, w, nb, acc_prior, dt, prm, geometry)
         tau += dt
         info.substeps += 1
         info.dts.append(dt)

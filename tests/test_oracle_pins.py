@@ -449,8 +449,8 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(o, "LIMITER", 3.0)
     orig_pr = o.pressure_relaxation
 
-    def half_force(st, w, nb, acc_prior, dt, prm):
-        out, a = orig_pr(st, w, nb, acc_prior, dt, prm)
+    def half_force(st, w, nb, acc_prior, dt, prm, geometry=None):
+        out, a = orig_pr(st, w, nb, acc_prior, dt, prm, geometry)
         return out, 0.5 * (a - prm.gravity[None, :]) + prm.gravity[None, :]
     monkeypatch.setattr(o, "pressure_relaxation", half_force)
     with pytest.raises(AssertionError):
@@ -465,8 +465,8 @@ def test_planted_mistakes_are_caught(monkeypatch):
     # 5. half step using v^n instead of v^{n+1} (R9) -> ballistic pin fails
     orig_dr = o.density_relaxation
 
-    def stale_velocity(st, w, nb, dt, prm):
-        out = orig_dr(st, w, nb, dt, prm)
+    def stale_velocity(st, w, nb, dt, prm, geometry=None):
+        out = orig_dr(st, w, nb, dt, prm, geometry)
         out.x = out.x - 0.5 * dt * dt * prm.gravity[None, :]     # v^n = v^{n+1} - dt g
         return out
     monkeypatch.setattr(o, "density_relaxation", stale_velocity)
