@@ -195,7 +195,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     prob = wk.dam_break_3d(args.n)
     N = prob.n_fluid
-    sim = sph.Simulation(prob, flags=(sph.SPH_FLAG_GRAPH if args.graph else 0), stream=stream)
+    flags = (sph.SPH_FLAG_GRAPH if args.graph else 0) | (sph.SPH_FLAG_FROZEN_GEOMETRY if args.frozen else 0)
+    sim = sph.Simulation(prob, flags=flags, stream=stream)
     info = sim.info()
 
     def barrier():
@@ -284,9 +285,13 @@ def run_ours(args, rank, world, local_rank):
     # algorithmic bytes per launch: state read 32 B + write 28 B per particle, neighbour
     # count 4 B, neighbour index 4 B per pair (frozen set read once)
     k7_bytes = N * (32 + 28 + 4) + 4 * (fluid_pairs + wall_pairs)
+    if args.frozen:
+        # the frozen reading also streams one 16-byte pair record per neighbour slot
+        k7_bytes += 16 * (fluid_pairs + wall_pairs)
     achieved = k7_bytes / (k7_ms * 1e-3) / 1e9 if kcount[0] else None
     traffic = None
-    if TRAFFIC_BYTES_PER_PARTICLE is not None and TRAFFIC_SOURCE_HASH == kernel_source_hash():
+    if (TRAFFIC_BYTES_PER_PARTICLE is not None and TRAFFIC_SOURCE_HASH == kernel_source_hash()
+            and not args.frozen):
         traffic = TRAFFIC_BYTES_PER_PARTICLE * N
     # the same table walk with the 32-byte neighbour records gathered and no pair arithmetic:
     # the device's floor for gathering them this way (the kernels are gather-bound, not HBM-bound)
@@ -311,7 +316,8 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {
-                "workload": f"3D dam break, fluid 2x1x1 in a 5.366x5.366x1 tank, dp = 1/{args.n}",
+                "workload": f"3D dam break, fluid 2x1x1 in a 5.366x5.366x1 tank, dp = 1/{args.n}"
+                            + (", frozen pair geometry" if args.frozen else ""),
                 "n_fluid": N, "n_wall": prob.n_wall, "h_over_dp": 1.3,
                 "substeps": substeps, "neighbour_pairs": fluid_pairs + wall_pairs,
                 "mean_neighbours": (fluid_pairs + wall_pairs) / N,
@@ -495,6 +501,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--frozen", action="store_true",
+                    help="the frozen-pair-geometry reading (pair vectors kept from the configuration update)")
     ap.add_argument("--launch-config", default=None,
                     help="pr_tpp,pr_block,dr_tpp,dr_block: fixed launch variants instead of autotuning")
     ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "sizes"],

@@ -61,6 +61,13 @@ extern "C" {
 #define SPH_FLAG_GRAPH     1u  /* sph_step runs each advection step as one CUDA graph whose
                                   acoustic-substep loop is a device-side conditional WHILE node */
 #define SPH_FLAG_KEEP_ACC  2u  /* keep the last dv/dt of every particle for sph_get_acceleration */
+#define SPH_FLAG_FROZEN_GEOMETRY 4u  /* keep each pair's vector r_i - r_j and (dW/dr)/r from the
+                                      * configuration update (after sph_advection_step's density
+                                      * re-initialisation) for every half step of the advection
+                                      * step, as the neighbour relation of Sec. 6.2 stores them;
+                                      * without it they are recomputed from the current
+                                      * positions in every half step. Costs 16 B per neighbour
+                                      * slot of device memory (n_fluid x capacity). */
 
 typedef struct sph_handle sph_handle;   /* opaque, library-owned */
 

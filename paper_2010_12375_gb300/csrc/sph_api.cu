@@ -247,6 +247,7 @@ void enqueue_advection(sph_handle* h, cudaStream_t s, int64_t* n) {
   sph::launch_dt_advection(h->b, s, n);
   sph::launch_density(h->b, s, n);
   sph::launch_viscous(h->b, s, n);
+  sph::launch_pair_geometry(h->b, s, n);     // frozen-geometry reading only (b.geo set)
 }
 
 void enqueue_substep(sph_handle* h, cudaStream_t s, bool use_cond, int64_t* n) {
@@ -540,6 +541,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
     DALLOC(h, b.acc_prior, n_fluid);
     CK(h, cudaMemset(b.acc_prior, 0, sizeof(float4) * std::max<int64_t>(n_fluid, 1)));
   }
+  if (h->flags & SPH_FLAG_FROZEN_GEOMETRY) DALLOC(h, b.geo, (size_t)n_fluid * b.cap);
   if (h->flags & SPH_FLAG_KEEP_ACC) {
     DALLOC(h, b.acc_keep, n_fluid);
     CK(h, cudaMemset(b.acc_keep, 0, sizeof(float4) * std::max<int64_t>(n_fluid, 1)));

@@ -49,6 +49,7 @@ struct Buffers {
   // neighbours (column-major ELL: nbr[k * n + i])
   int* nbr = nullptr;
   uint32_t* nbc = nullptr;        // [n] fluid count | wall count << 16
+  float4* geo = nullptr;          // [cap][n] frozen r_i - r_j and (dW/dr)/r per slot (or NULL)
 };
 
 size_t scan_tmp_elems(int64_t n);
@@ -84,6 +85,8 @@ void launch_dt_acoustic(const Buffers& b, cudaStream_t s, cudaGraphConditionalHa
                         bool use_cond, int64_t* launches);
 void launch_pressure_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_density_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches);
+// per-slot pair geometry at the current positions, for the frozen-geometry reading
+void launch_pair_geometry(const Buffers& b, cudaStream_t s, int64_t* launches);
 // gather-only walk of the neighbour table (diagnostic); sink: one device word
 void launch_gather_ceiling(const Buffers& b, unsigned* sink, cudaStream_t s, int64_t* launches);
 

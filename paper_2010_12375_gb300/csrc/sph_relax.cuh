@@ -106,6 +106,17 @@ __device__ __forceinline__ Geo2 geometry2(float2 rx, float2 ry, float2 rz, float
   return g;
 }
 
+// The same factors from a stored pair vector and (dW/dr)/r (frozen-geometry reading):
+// 1/|r| and |r| come out of the same operations as in geometry2.
+__device__ __forceinline__ Geo2 stored_geometry2(float2 rx, float2 ry, float2 rz, float2 fw) {
+  Geo2 g;
+  float2 r2 = fma2(rx, rx, fma2(ry, ry, fma2(rz, rz, f2(kTinyR2))));
+  g.inv_r = rsqrt2(r2);
+  g.r = mul2(r2, g.inv_r);
+  g.fw = fw;
+  return g;
+}
+
 // Exactly converted, packed pair vector: dq (q_i - q_j) + add, lanes (a, b).
 template <bool PER>
 __device__ __forceinline__ float2 pair_axis(int qi, int qa, int qb, int period, float2 DQ, float2 add) {
@@ -122,20 +133,30 @@ struct PrCtx {
 };
 
 // Two fluid pairs (a, b) of the pressure relaxation: V_j P* (dW/dr)/r r_ij accumulated.
-template <int D, bool PER>
+// FG: the pair vectors and (dW/dr)/r come from the frozen table (ga, gb), else from the
+// mid-point positions.
+template <int D, bool PER, bool FG = false>
 __device__ __forceinline__ void pr_fluid2(const Inst& I, PrCtx& C, const int4& pi, const float4& vi, const int4& pa,
                                           const int4& pb, const float4& va, const float4& vb, float2 mj,
-                                          float2 DQ) {
+                                          float2 DQ, float4 ga = float4(), float4 gb = float4()) {
   const float2 HDT = f2(C.hdt), MHDT = f2(-C.hdt);
   // v_j - v_i; hdt (v_i - v_j) = (-hdt)(v_j - v_i) exactly, so one difference serves both
   const float2 dvx = sub2(make_float2(va.x, vb.x), f2(vi.x));
   const float2 dvy = sub2(make_float2(va.y, vb.y), f2(vi.y));
   const float2 dvz = D == 3 ? sub2(make_float2(va.z, vb.z), f2(vi.z)) : f2(0.f);
-  const float2 rx = pair_axis<PER>(pi.x, pa.x, pb.x, C.px, DQ, mul2(MHDT, dvx));
-  const float2 ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(MHDT, dvy));
-  float2 rz = f2(0.f);
-  if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(MHDT, dvz));
-  const Geo2 G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
+  float2 rx, ry, rz = f2(0.f);
+  Geo2 G;
+  if (FG) {
+    rx = make_float2(ga.x, gb.x);
+    ry = make_float2(ga.y, gb.y);
+    if (D == 3) rz = make_float2(ga.z, gb.z);
+    G = stored_geometry2(rx, ry, rz, make_float2(ga.w, gb.w));
+  } else {
+    rx = pair_axis<PER>(pi.x, pa.x, pb.x, C.px, DQ, mul2(MHDT, dvx));
+    ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(MHDT, dvy));
+    if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(MHDT, dvz));
+    G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
+  }
   const float2 dev_j = fma2(HDT, make_float2(va.w, vb.w), make_float2(i2f(pa.w), i2f(pb.w)));
   const float2 rho_j = add2(f2(I.rho0), dev_j);
   // U_L - U_R = (v_j - v_i).r_ij / |r_ij|
@@ -151,15 +172,24 @@ __device__ __forceinline__ void pr_fluid2(const Inst& I, PrCtx& C, const int4& p
 }
 
 // Two wall pairs of the pressure relaxation (one-sided problem along the wall normal).
-template <int D, bool PER>
+template <int D, bool PER, bool FG = false>
 __device__ __forceinline__ void pr_wall2(const Inst& I, PrCtx& C, const int4& pi, const float4& vi,
                                          const int4& qa, const int4& qb, const float4& na,
-                                         const float4& nb, float2 Vw, float2 DQ) {
-  const float2 rx = pair_axis<PER>(pi.x, qa.x, qb.x, C.px, DQ, f2(C.hdt * vi.x));
-  const float2 ry = pair_axis<PER>(pi.y, qa.y, qb.y, C.py, DQ, f2(C.hdt * vi.y));
-  float2 rz = f2(0.f);
-  if (D == 3) rz = pair_axis<PER>(pi.z, qa.z, qb.z, C.pz, DQ, f2(C.hdt * vi.z));
-  const Geo2 G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
+                                         const float4& nb, float2 Vw, float2 DQ,
+                                         float4 ga = float4(), float4 gb = float4()) {
+  float2 rx, ry, rz = f2(0.f);
+  Geo2 G;
+  if (FG) {
+    rx = make_float2(ga.x, gb.x);
+    ry = make_float2(ga.y, gb.y);
+    if (D == 3) rz = make_float2(ga.z, gb.z);
+    G = stored_geometry2(rx, ry, rz, make_float2(ga.w, gb.w));
+  } else {
+    rx = pair_axis<PER>(pi.x, qa.x, qb.x, C.px, DQ, f2(C.hdt * vi.x));
+    ry = pair_axis<PER>(pi.y, qa.y, qb.y, C.py, DQ, f2(C.hdt * vi.y));
+    if (D == 3) rz = pair_axis<PER>(pi.z, qa.z, qb.z, C.pz, DQ, f2(C.hdt * vi.z));
+    G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
+  }
   // U_L = -n.v_i, U_R = -U_L, P_R = P_L + rho_i g.(r_w - r_i), rho_R from the EoS
   const float2 UL = mul2(f2(-1.0f), fma2(make_float2(na.x, nb.x), f2(vi.x),
                                          fma2(make_float2(na.y, nb.y), f2(vi.y), mul2(make_float2(na.z, nb.z), f2(vi.z)))));
@@ -180,9 +210,11 @@ __device__ __forceinline__ void pr_wall2(const Inst& I, PrCtx& C, const int4& pi
 // TPP threads share one particle: lane `sub` takes quads sub, sub + TPP, ... of its row,
 // and the lanes' compensated sums are combined in a fixed order. TPP = 1 is one thread per
 // particle; 2 and 4 trade per-thread work for more threads in flight.
-template <int D, bool PER, int TPP, int BLK, bool UNI>
+// FG: pair geometry from the frozen table geo ([slot][n]) instead of the positions.
+template <int D, bool PER, int TPP, int BLK, bool UNI, bool FG>
 __global__ void __launch_bounds__(BLK, pr_min_blocks(BLK))
-k_pressure_relaxation(const Inst Ip, int64_t n, const int4* __restrict__ PS, const float4* __restrict__ VS,
+k_pressure_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, const int4* __restrict__ PS,
+                      const float4* __restrict__ VS,
                       int4* __restrict__ PH, float4* __restrict__ VH,
                       const float* __restrict__ mass, const int* __restrict__ inst_of,
                       const Inst* __restrict__ inst, Ctrl* ctrl, const int* __restrict__ nbr,
@@ -228,15 +260,33 @@ k_pressure_relaxation(const Inst Ip, int64_t n, const int4* __restrict__ PS, con
       const int j1 = s + 1 < nf ? cur.y : (int)i;                // self pads: zero terms
       const int j2 = s + 2 < nf ? cur.z : (int)i;
       const int j3 = s + 3 < nf ? cur.w : (int)i;
-      const int4 p0 = PS[j0], p1 = PS[j1], p2 = PS[j2], p3 = PS[j3];
+      int4 p0, p1, p2, p3;
+      float4 g0 = float4(), g1 = float4(), g2 = float4(), g3 = float4();
+      if (FG) {                                  // the frozen table holds the geometry: only dev_j here
+        const int* __restrict__ dw = reinterpret_cast<const int*>(PS) + 3;
+        p0 = make_int4(0, 0, 0, dw[4 * (int64_t)j0]);
+        p1 = make_int4(0, 0, 0, dw[4 * (int64_t)j1]);
+        p2 = make_int4(0, 0, 0, dw[4 * (int64_t)j2]);
+        p3 = make_int4(0, 0, 0, dw[4 * (int64_t)j3]);
+        const float4* __restrict__ gq = geo + (int64_t)s * n + i;
+        g0 = gq[0];
+        g1 = gq[n];
+        g2 = gq[2 * n];
+        g3 = gq[3 * n];
+      } else {
+        p0 = PS[j0];
+        p1 = PS[j1];
+        p2 = PS[j2];
+        p3 = PS[j3];
+      }
       const float4 v0 = VS[j0], v1 = VS[j1], v2v = VS[j2], v3 = VS[j3];
       float2 m01 = f2(I.mass), m23 = f2(I.mass);
       if (mass) {
         m01 = make_float2(mass[j0], mass[j1]);
         m23 = make_float2(mass[j2], mass[j3]);
       }
-      pr_fluid2<D, PER>(I, C, pi, vi, p0, p1, v0, v1, m01, DQ);
-      pr_fluid2<D, PER>(I, C, pi, vi, p2, p3, v2v, v3, m23, DQ);
+      pr_fluid2<D, PER, FG>(I, C, pi, vi, p0, p1, v0, v1, m01, DQ, g0, g1);
+      pr_fluid2<D, PER, FG>(I, C, pi, vi, p2, p3, v2v, v3, m23, DQ, g2, g3);
       cur = nxt;
     }
     if (nw) {
@@ -249,8 +299,16 @@ k_pressure_relaxation(const Inst Ip, int64_t n, const int4* __restrict__ PS, con
         const float4 n0 = WN[c.x], n1 = WN[w1], n2 = WN[w2], n3 = WN[w3];
         const float2 V01 = make_float2(i2f(a0.w), s + 1 < nw ? i2f(a1.w) : 0.0f);   // pads carry no volume
         const float2 V23 = make_float2(s + 2 < nw ? i2f(a2.w) : 0.0f, s + 3 < nw ? i2f(a3.w) : 0.0f);
-        pr_wall2<D, PER>(I, C, pi, vi, a0, a1, n0, n1, V01, DQ);
-        pr_wall2<D, PER>(I, C, pi, vi, a2, a3, n2, n3, V23, DQ);
+        float4 g0 = float4(), g1 = float4(), g2 = float4(), g3 = float4();
+        if (FG) {
+          const float4* __restrict__ gq = geo + (int64_t)((q0 + q) << 2) * n + i;
+          g0 = gq[0];
+          g1 = gq[n];
+          g2 = gq[2 * n];
+          g3 = gq[3 * n];
+        }
+        pr_wall2<D, PER, FG>(I, C, pi, vi, a0, a1, n0, n1, V01, DQ, g0, g1);
+        pr_wall2<D, PER, FG>(I, C, pi, vi, a2, a3, n2, n3, V23, DQ, g2, g3);
       }
     }
   }
@@ -297,17 +355,25 @@ struct DrCtx {
   float2 s, nc;
 };
 
-template <int D, bool PER>
+template <int D, bool PER, bool FG = false>
 __device__ __forceinline__ void dr_fluid2(const Inst& I, DrCtx& C, const int4& pi, const float4& vi, const int4& pa,
                                           const int4& pb, const float4& va, const float4& vb, float2 mj,
-                                          float2 DQ) {
+                                          float2 DQ, float4 ga = float4(), float4 gb = float4()) {
   const float2 HDT = f2(C.hdt);
-  // r_ij^{n+1} = r_ij^{n+1/2} + dt/2 (v_i - v_j)^{n+1}
-  const float2 rx = pair_axis<PER>(pi.x, pa.x, pb.x, C.px, DQ, mul2(HDT, sub2(f2(vi.x), make_float2(va.x, vb.x))));
-  const float2 ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(HDT, sub2(f2(vi.y), make_float2(va.y, vb.y))));
-  float2 rz = f2(0.f);
-  if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(HDT, sub2(f2(vi.z), make_float2(va.z, vb.z))));
-  const Geo2 G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
+  float2 rx, ry, rz = f2(0.f);
+  Geo2 G;
+  if (FG) {
+    rx = make_float2(ga.x, gb.x);
+    ry = make_float2(ga.y, gb.y);
+    if (D == 3) rz = make_float2(ga.z, gb.z);
+    G = stored_geometry2(rx, ry, rz, make_float2(ga.w, gb.w));
+  } else {
+    // r_ij^{n+1} = r_ij^{n+1/2} + dt/2 (v_i - v_j)^{n+1}
+    rx = pair_axis<PER>(pi.x, pa.x, pb.x, C.px, DQ, mul2(HDT, sub2(f2(vi.x), make_float2(va.x, vb.x))));
+    ry = pair_axis<PER>(pi.y, pa.y, pb.y, C.py, DQ, mul2(HDT, sub2(f2(vi.y), make_float2(va.y, vb.y))));
+    if (D == 3) rz = pair_axis<PER>(pi.z, pa.z, pb.z, C.pz, DQ, mul2(HDT, sub2(f2(vi.z), make_float2(va.z, vb.z))));
+    G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
+  }
   const float2 dev_j = make_float2(i2f(pa.w), i2f(pb.w));
   const float2 rho_j = add2(f2(I.rho0), dev_j);
   // (U_R - U_L)/2 = (v_i - v_j).r_ij / (2 |r_ij|)
@@ -320,15 +386,24 @@ __device__ __forceinline__ void dr_fluid2(const Inst& I, DrCtx& C, const int4& p
   kahan2(C.s, C.nc, mul2(mul2(mj, rcp2(rho_j)), dUs), mul2(G.fw, G.r));
 }
 
-template <int D, bool PER>
+template <int D, bool PER, bool FG = false>
 __device__ __forceinline__ void dr_wall2(const Inst& I, DrCtx& C, const int4& pi, const float4& vi,
                                          const int4& qa, const int4& qb, const float4& na,
-                                         const float4& nb, float2 Vw, float2 DQ, float pr_i) {
-  const float2 rx = pair_axis<PER>(pi.x, qa.x, qb.x, C.px, DQ, f2(C.hdt * vi.x));
-  const float2 ry = pair_axis<PER>(pi.y, qa.y, qb.y, C.py, DQ, f2(C.hdt * vi.y));
-  float2 rz = f2(0.f);
-  if (D == 3) rz = pair_axis<PER>(pi.z, qa.z, qb.z, C.pz, DQ, f2(C.hdt * vi.z));
-  const Geo2 G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
+                                         const float4& nb, float2 Vw, float2 DQ, float pr_i,
+                                         float4 ga = float4(), float4 gb = float4()) {
+  float2 rx, ry, rz = f2(0.f);
+  Geo2 G;
+  if (FG) {
+    rx = make_float2(ga.x, gb.x);
+    ry = make_float2(ga.y, gb.y);
+    if (D == 3) rz = make_float2(ga.z, gb.z);
+    G = stored_geometry2(rx, ry, rz, make_float2(ga.w, gb.w));
+  } else {
+    rx = pair_axis<PER>(pi.x, qa.x, qb.x, C.px, DQ, f2(C.hdt * vi.x));
+    ry = pair_axis<PER>(pi.y, qa.y, qb.y, C.py, DQ, f2(C.hdt * vi.y));
+    if (D == 3) rz = pair_axis<PER>(pi.z, qa.z, qb.z, C.pz, DQ, f2(C.hdt * vi.z));
+    G = geometry2(rx, ry, rz, I.inv_h, I.dwr_a);
+  }
   const float2 UL = mul2(f2(-1.0f), fma2(make_float2(na.x, nb.x), f2(vi.x),
                                          fma2(make_float2(na.y, nb.y), f2(vi.y), mul2(make_float2(na.z, nb.z), f2(vi.z)))));
   const float2 gr = fma2(f2(I.g[0]), rx, fma2(f2(I.g[1]), ry, mul2(f2(I.g[2]), rz)));
@@ -339,9 +414,10 @@ __device__ __forceinline__ void dr_wall2(const Inst& I, DrCtx& C, const int4& pi
   kahan2(C.s, C.nc, mul2(Vw, sub2(Us, UL)), mul2(G.fw, G.r));
 }
 
-template <int D, bool PER, int TPP, int BLK, bool UNI>
+template <int D, bool PER, int TPP, int BLK, bool UNI, bool FG>
 __global__ void __launch_bounds__(BLK, dr_min_blocks(BLK))
-k_density_relaxation(const Inst Ip, int64_t n, const int4* __restrict__ PH, const float4* __restrict__ VH,
+k_density_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, const int4* __restrict__ PH,
+                     const float4* __restrict__ VH,
                      int4* __restrict__ PS, float4* __restrict__ VS,
                      const float* __restrict__ mass, const int* __restrict__ inst_of,
                      const Inst* __restrict__ inst, const Ctrl* __restrict__ ctrl,
@@ -383,15 +459,33 @@ k_density_relaxation(const Inst Ip, int64_t n, const int4* __restrict__ PH, cons
       const int j1 = s + 1 < nf ? cur.y : (int)i;
       const int j2 = s + 2 < nf ? cur.z : (int)i;
       const int j3 = s + 3 < nf ? cur.w : (int)i;
-      const int4 p0 = PH[j0], p1 = PH[j1], p2 = PH[j2], p3 = PH[j3];
+      int4 p0, p1, p2, p3;
+      float4 g0 = float4(), g1 = float4(), g2 = float4(), g3 = float4();
+      if (FG) {                                  // the frozen table holds the geometry: only dev_j here
+        const int* __restrict__ dw = reinterpret_cast<const int*>(PH) + 3;
+        p0 = make_int4(0, 0, 0, dw[4 * (int64_t)j0]);
+        p1 = make_int4(0, 0, 0, dw[4 * (int64_t)j1]);
+        p2 = make_int4(0, 0, 0, dw[4 * (int64_t)j2]);
+        p3 = make_int4(0, 0, 0, dw[4 * (int64_t)j3]);
+        const float4* __restrict__ gq = geo + (int64_t)s * n + i;
+        g0 = gq[0];
+        g1 = gq[n];
+        g2 = gq[2 * n];
+        g3 = gq[3 * n];
+      } else {
+        p0 = PH[j0];
+        p1 = PH[j1];
+        p2 = PH[j2];
+        p3 = PH[j3];
+      }
       const float4 v0 = VH[j0], v1 = VH[j1], v2 = VH[j2], v3 = VH[j3];
       float2 m01 = f2(I.mass), m23 = f2(I.mass);
       if (mass) {
         m01 = make_float2(mass[j0], mass[j1]);
         m23 = make_float2(mass[j2], mass[j3]);
       }
-      dr_fluid2<D, PER>(I, C, pi, vi, p0, p1, v0, v1, m01, DQ);
-      dr_fluid2<D, PER>(I, C, pi, vi, p2, p3, v2, v3, m23, DQ);
+      dr_fluid2<D, PER, FG>(I, C, pi, vi, p0, p1, v0, v1, m01, DQ, g0, g1);
+      dr_fluid2<D, PER, FG>(I, C, pi, vi, p2, p3, v2, v3, m23, DQ, g2, g3);
       cur = nxt;
     }
     if (nw) {
@@ -405,8 +499,16 @@ k_density_relaxation(const Inst Ip, int64_t n, const int4* __restrict__ PH, cons
         const float4 n0 = WN[c.x], n1 = WN[w1], n2 = WN[w2], n3 = WN[w3];
         const float2 V01 = make_float2(i2f(a0.w), s + 1 < nw ? i2f(a1.w) : 0.0f);
         const float2 V23 = make_float2(s + 2 < nw ? i2f(a2.w) : 0.0f, s + 3 < nw ? i2f(a3.w) : 0.0f);
-        dr_wall2<D, PER>(I, C, pi, vi, a0, a1, n0, n1, V01, DQ, pr_i);
-        dr_wall2<D, PER>(I, C, pi, vi, a2, a3, n2, n3, V23, DQ, pr_i);
+        float4 g0 = float4(), g1 = float4(), g2 = float4(), g3 = float4();
+        if (FG) {
+          const float4* __restrict__ gq = geo + (int64_t)((q0 + q) << 2) * n + i;
+          g0 = gq[0];
+          g1 = gq[n];
+          g2 = gq[2 * n];
+          g3 = gq[3 * n];
+        }
+        dr_wall2<D, PER, FG>(I, C, pi, vi, a0, a1, n0, n1, V01, DQ, pr_i, g0, g1);
+        dr_wall2<D, PER, FG>(I, C, pi, vi, a2, a3, n2, n3, V23, DQ, pr_i, g2, g3);
       }
     }
   }
@@ -438,8 +540,14 @@ void launch_pr(int tpp, int block, const Buffers& b, cudaStream_t s) {
     (const int4*)b.WP, (const float4*)b.WN, (const float4*)b.acc_prior, b.acc_keep, b.glob
   // one instantiation per (threads per particle, block) pair, each with its own bounds
 #define SPH_PR(T, B) (b.n_inst == 1                                                                 \
-      ? k_pressure_relaxation<D, PER, T, B, true><<<grid, B, 0, s>>>(b.inst0, SPH_PR_ARGS)           \
-      : k_pressure_relaxation<D, PER, T, B, false><<<grid, B, 0, s>>>(b.inst0, SPH_PR_ARGS))
+      ? k_pressure_relaxation<D, PER, T, B, true, false><<<grid, B, 0, s>>>(b.inst0, nullptr, SPH_PR_ARGS) \
+      : k_pressure_relaxation<D, PER, T, B, false, false><<<grid, B, 0, s>>>(b.inst0, nullptr, SPH_PR_ARGS))
+  if (b.geo) {               // frozen geometry: one variant, one thread per particle
+    const unsigned g1 = grid_for(b.n, 128);
+    if (b.n_inst == 1) k_pressure_relaxation<D, PER, 1, 128, true, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_PR_ARGS);
+    else k_pressure_relaxation<D, PER, 1, 128, false, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_PR_ARGS);
+    return;
+  }
 #define SPH_PR_T(T) (block == 512 ? SPH_PR(T, 512) : block == 256 ? SPH_PR(T, 256) : SPH_PR(T, 128))
   if (tpp == 4) SPH_PR_T(4);
   else if (tpp == 2) SPH_PR_T(2);
@@ -456,8 +564,14 @@ void launch_dr(int tpp, int block, const Buffers& b, cudaStream_t s) {
     b.inst_of, (const Inst*)b.inst, (const Ctrl*)b.ctrl, (const int*)b.nbr, (const uint32_t*)b.nbc,   \
     (const int4*)b.WP, (const float4*)b.WN, b.glob
 #define SPH_DR(T, B) (b.n_inst == 1                                                                 \
-      ? k_density_relaxation<D, PER, T, B, true><<<grid, B, 0, s>>>(b.inst0, SPH_DR_ARGS)            \
-      : k_density_relaxation<D, PER, T, B, false><<<grid, B, 0, s>>>(b.inst0, SPH_DR_ARGS))
+      ? k_density_relaxation<D, PER, T, B, true, false><<<grid, B, 0, s>>>(b.inst0, nullptr, SPH_DR_ARGS) \
+      : k_density_relaxation<D, PER, T, B, false, false><<<grid, B, 0, s>>>(b.inst0, nullptr, SPH_DR_ARGS))
+  if (b.geo) {
+    const unsigned g1 = grid_for(b.n, 128);
+    if (b.n_inst == 1) k_density_relaxation<D, PER, 1, 128, true, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_DR_ARGS);
+    else k_density_relaxation<D, PER, 1, 128, false, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_DR_ARGS);
+    return;
+  }
 #define SPH_DR_T(T) (block == 512 ? SPH_DR(T, 512) : block == 256 ? SPH_DR(T, 256) : SPH_DR(T, 128))
   if (tpp == 4) SPH_DR_T(4);
   else if (tpp == 2) SPH_DR_T(2);

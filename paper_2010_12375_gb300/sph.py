@@ -22,6 +22,7 @@ SPH_E_CAPACITY = -6
 SPH_E_TIMEOUT = -7
 SPH_FLAG_GRAPH = 1
 SPH_FLAG_KEEP_ACC = 2
+SPH_FLAG_FROZEN_GEOMETRY = 4
 
 ERROR_NAMES = {0: "SPH_OK", -1: "SPH_E_INVALID", -2: "SPH_E_CUDA", -3: "SPH_E_OOM",
                -4: "SPH_E_DOMAIN", -5: "SPH_E_UNSTABLE", -6: "SPH_E_CAPACITY", -7: "SPH_E_TIMEOUT"}
