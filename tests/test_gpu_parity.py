@@ -385,7 +385,8 @@ def _local_problem(prob, x, v, rho, drho, centres, radius):
 @pytest.mark.slow
 def test_full_size_3d_first_substep_sampled(sph):
     """3D dam break at 8.04M fluid particles (the benchmark workload), launched as the
-    benchmark launches it; one advection step's density summation and first substep
+    benchmark launches it (the autotuner's pick there: one thread per particle, 128-thread
+    blocks); one advection step's density summation and first substep, both relaxations,
     checked on sampled particles against the oracle run on their neighbourhoods."""
     prob = wk.dam_break_3d(159)
     x, v, rho, drho = perturbed_state(prob, 31, 0.2, 0.005)
@@ -394,20 +395,23 @@ def test_full_size_3d_first_substep_sampled(sph):
     prm = o.Params.from_problem(prob)
     vmax_all = v32
     sim = sph.Simulation(prob, flags=sph.SPH_FLAG_KEEP_ACC)
+    sph.sph_set_launch_config(sim.handle, [1, 128, 1, 128])
     sim.set_state(xq, v32, rho32, d32, t=0.0)
     sim.build_cells()
     sim.advection_step()
     _, _, rho_mid, _ = sim.state()
     sim.acoustic_substep()
     acc_gpu = sim.acceleration()
-    _, vel_gpu, _, _ = sim.state()
+    _, vel_gpu, rho_gpu, drho_gpu = sim.state()
     sim.close()
     rng = np.random.default_rng(5)
-    samples = rng.choice(prob.n_fluid, size=400, replace=False)
+    samples = rng.choice(prob.n_fluid, size=200, replace=False)
     # include particles next to the walls and at the free surface
-    samples = np.unique(np.concatenate([samples, np.argsort(xq[:, 1])[:50], np.argsort(-xq[:, 1])[:50],
-                                        np.argsort(xq[:, 0])[:50], np.argsort(xq[:, 2])[:50]]))
-    sub, near, dsub = _local_problem(prob, xq, v32, rho32, d32, xq[samples], 4.5 * prob.h)
+    samples = np.unique(np.concatenate([samples, np.argsort(xq[:, 1])[:25], np.argsort(-xq[:, 1])[:25],
+                                        np.argsort(xq[:, 0])[:25], np.argsort(xq[:, 2])[:25]]))
+    # 6.5 h: a sample's density relaxation needs its neighbours' new velocities, theirs
+    # their neighbours' summed densities, and those their neighbours (three hops of 2h)
+    sub, near, dsub = _local_problem(prob, xq, v32, rho32, d32, xq[samples], 6.5 * prob.h)
     sprm = o.Params.from_problem(sub)
     st, w = o.state_from_problem(sub)
     st.drho = dsub
@@ -417,13 +421,15 @@ def test_full_size_3d_first_substep_sampled(sph):
     local = np.searchsorted(near, samples)
     assert rel_l2(rho_mid[samples], st.rho[local]) < REL_L2_TOL
     dt = min(o.dt_acoustic(vmax_all, prm), Dt)
-    # the oracle's own summed densities feed its substep: only pairs whose 1-hop
-    # neighbourhood is complete are compared
     half, dvdt = o.pressure_relaxation(st, w, nb, 0.0, dt, sprm)
-    print(f"8M sampled: rho {rel_l2(rho_mid[samples], st.rho[local]):.2e} "
-          f"dv/dt {rel_l2(acc_gpu[samples], dvdt[local]):.2e} v {rel_l2(vel_gpu[samples], half.v[local]):.2e}")
+    out = o.density_relaxation(half, w, nb, dt, sprm)
+    print(f"8M sampled ({samples.size}): rho {rel_l2(rho_mid[samples], st.rho[local]):.2e} "
+          f"dv/dt {rel_l2(acc_gpu[samples], dvdt[local]):.2e} v {rel_l2(vel_gpu[samples], half.v[local]):.2e} "
+          f"rho' {rel_l2(rho_gpu[samples], out.rho[local]):.2e} drho {rel_l2(drho_gpu[samples], out.drho[local]):.2e}")
     assert rel_l2(acc_gpu[samples], dvdt[local]) < REL_L2_TOL
     assert rel_l2(vel_gpu[samples], half.v[local]) < REL_L2_TOL
+    assert rel_l2(rho_gpu[samples], out.rho[local]) < REL_L2_TOL
+    assert np.max(np.abs(drho_gpu[samples] - out.drho[local])) < 1e-3 * max(np.abs(out.drho[local]).max(), 1.0)
 
 
 # ------------------------------------------------------------------ launch variants / autotuner
