@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -74,6 +75,18 @@ __device__ __forceinline__ void mma16816(float* c, uint32_t a0, uint32_t a1, uin
 // per element (m, n < NO): y = acc; y = 0 where mask[m, n] <= 0 (ReLU backward) if mask;
 // y = max(y, 0) if relu; out_f32[m, n] = y (or += y with accum) for n < nf_store;
 // out_b[m, col0 + n] = bf16(y) for n < nb_store.
+// Each block keeps W in shared memory and walks row tiles of 64 (grid-stride), the next
+// tile's rows streaming in with 16-byte cp.async copies while the current one is
+// multiplied. K, ldx, ldf, ldo, ldm, col0, nf_store and nb_store are multiples of 8 / 2
+// (checked by the host wrapper), so rows move in 16-byte pieces and results in pairs.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;                       // 0: fill the 16 bytes with zeros
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 template <int NO>
 __global__ void __launch_bounds__(128)
 k_dense(int64_t M, int K, const bf16* __restrict__ X, int ldx, const bf16* __restrict__ W,
@@ -82,52 +95,77 @@ k_dense(int64_t M, int K, const bf16* __restrict__ X, int ldx, const bf16* __res
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LD = K + 8;                       // padded row: conflict-free fragment loads
   bf16* sW = reinterpret_cast<bf16*>(smem_raw);
-  bf16* sX = sW + NO * LD;
-  const int64_t m0 = (int64_t)blockIdx.x * kTile;
-  for (int idx = threadIdx.x; idx < NO * K / 2; idx += blockDim.x) {
-    const int r = (2 * idx) / K, c = (2 * idx) % K;
-    *reinterpret_cast<uint32_t*>(&sW[r * LD + c]) = ld_u32(&W[r * K + c]);
-  }
-  for (int idx = threadIdx.x; idx < kTile * K / 2; idx += blockDim.x) {
-    const int r = (2 * idx) / K, c = (2 * idx) % K;
-    const int64_t m = m0 + r;
-    *reinterpret_cast<uint32_t*>(&sX[r * LD + c]) = m < M ? ld_u32(&X[m * ldx + c]) : 0u;
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float acc[NO / 8][4];
-#pragma unroll
-  for (int nt = 0; nt < NO / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-  const bf16* xr0 = sX + (warp * 16 + g) * LD;
-  const bf16* xr1 = xr0 + 8 * LD;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    const uint32_t a0 = ld_u32(xr0 + k0 + 2 * t), a1 = ld_u32(xr1 + k0 + 2 * t);
-    const uint32_t a2 = ld_u32(xr0 + k0 + 2 * t + 8), a3 = ld_u32(xr1 + k0 + 2 * t + 8);
-#pragma unroll
-    for (int nt = 0; nt < NO / 8; ++nt) {
-      const bf16* wr = sW + (nt * 8 + g) * LD + k0 + 2 * t;
-      mma16816(acc[nt], a0, a1, a2, a3, ld_u32(wr), ld_u32(wr + 8));
+  bf16* const sX0 = sW + NO * LD;            // two row-tile buffers of kTile x LD
+  const int64_t tiles = (M + kTile - 1) / kTile;
+  const int chunks = K / 8;                   // 16-byte pieces per row
+  auto load_tile = [&](int64_t tile, bf16* dst) {
+    const int64_t m0 = tile * kTile;
+    for (int idx = threadIdx.x; idx < kTile * chunks; idx += blockDim.x) {
+      const int r = idx / chunks, c = (idx % chunks) * 8;
+      const int64_t m = m0 + r;
+      cp_async16(dst + r * LD + c, X + (m < M ? m : 0) * ldx + c, m < M);
     }
+    cp_async_commit();
+  };
+  int64_t tile = blockIdx.x;
+  if (tile < tiles) load_tile(tile, sX0);
+  for (int idx = threadIdx.x; idx < NO * chunks; idx += blockDim.x) {
+    const int r = idx / chunks, c = (idx % chunks) * 8;
+    *reinterpret_cast<uint4*>(&sW[r * LD + c]) = *reinterpret_cast<const uint4*>(&W[r * K + c]);
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int buf = 0; tile < tiles; tile += gridDim.x, buf ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();                          // this tile (and W) in place; the other buffer free
+    if (tile + gridDim.x < tiles) load_tile(tile + gridDim.x, sX0 + (buf ^ 1) * kTile * LD);
+    const bf16* sX = sX0 + buf * kTile * LD;
+    float acc[NO / 8][4];
 #pragma unroll
-  for (int nt = 0; nt < NO / 8; ++nt)
+    for (int nt = 0; nt < NO / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+    const bf16* xr0 = sX + (warp * 16 + g) * LD;
+    const bf16* xr1 = xr0 + 8 * LD;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+      const uint32_t a0 = ld_u32(xr0 + k0 + 2 * t), a1 = ld_u32(xr1 + k0 + 2 * t);
+      const uint32_t a2 = ld_u32(xr0 + k0 + 2 * t + 8), a3 = ld_u32(xr1 + k0 + 2 * t + 8);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t m = m0 + warp * 16 + g + 8 * h;
-      if (m >= M) continue;
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int n = nt * 8 + 2 * t + e;
-        float y = acc[nt][2 * h + e];
-        if (mask) y = __bfloat162float(mask[m * ldm + n]) > 0.f ? y : 0.f;
-        if (relu) y = fmaxf(y, 0.f);
-        if (out_f32 && n < nf_store) {
-          if (accum) out_f32[m * ldf + n] += y;
-          else out_f32[m * ldf + n] = y;
-        }
-        if (out_b && n < nb_store) out_b[m * ldo + col0 + n] = __float2bfloat16_rn(y);
+      for (int nt = 0; nt < NO / 8; ++nt) {
+        const bf16* wr = sW + (nt * 8 + g) * LD + k0 + 2 * t;
+        mma16816(acc[nt], a0, a1, a2, a3, ld_u32(wr), ld_u32(wr + 8));
       }
     }
+    const int64_t m0 = tile * kTile;
+#pragma unroll
+    for (int nt = 0; nt < NO / 8; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t m = m0 + warp * 16 + g + 8 * h;
+        if (m >= M) continue;
+        const int n = nt * 8 + 2 * t;         // this thread's pair of columns (n, n + 1)
+        float y0 = acc[nt][2 * h], y1 = acc[nt][2 * h + 1];
+        if (mask) {
+          const uint32_t mk = ld_u32(&mask[m * ldm + n]);
+          y0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk & 0xffffu))) > 0.f ? y0 : 0.f;
+          y1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk >> 16))) > 0.f ? y1 : 0.f;
+        }
+        if (relu) {
+          y0 = fmaxf(y0, 0.f);
+          y1 = fmaxf(y1, 0.f);
+        }
+        if (out_f32 && n < nf_store) {
+          float2* o = reinterpret_cast<float2*>(&out_f32[m * ldf + n]);
+          if (accum) {
+            const float2 p = *o;
+            *o = make_float2(p.x + y0, p.y + y1);
+          } else {
+            *o = make_float2(y0, y1);
+          }
+        }
+        if (out_b && n < nb_store)
+          *reinterpret_cast<uint32_t*>(&out_b[m * ldo + col0 + n]) =
+              pack2(__float2bfloat16_rn(y0), __float2bfloat16_rn(y1));
+      }
+  }
+  cp_async_wait_all();                        // no copy left in flight at exit
 }
 
 // ------------------------------------------------------------------ weight gradient
@@ -208,74 +246,101 @@ __global__ void k_edge_count(int64_t n, const uint32_t* __restrict__ nbc, uint32
   if (i < n) cnt[i] = (nbc[i] & 0xffffu) + (nbc[i] >> 16);
 }
 
+// Node features (one 32-byte row per particle) and the edge list of the frozen table.
 template <int D>
-__global__ void k_features(int64_t n, const int4* __restrict__ P, const float4* __restrict__ V,
-                           const int* __restrict__ inst_of, const Inst* __restrict__ inst,
-                           const Ctrl* __restrict__ ctrl, const int* __restrict__ nbr,
-                           const uint32_t* __restrict__ nbc, const uint32_t* __restrict__ off,
-                           const int4* __restrict__ WP, int* __restrict__ esrc, int* __restrict__ enbr,
-                           bf16* __restrict__ U, bf16* XE0, bf16* XE1, bf16* XE2) {
+__global__ void k_node_features(int64_t n, const int4* __restrict__ P, const float4* __restrict__ V,
+                                const int* __restrict__ inst_of, const Inst* __restrict__ inst,
+                                const Ctrl* __restrict__ ctrl, const int* __restrict__ nbr,
+                                const uint32_t* __restrict__ nbc, const uint32_t* __restrict__ off,
+                                int* __restrict__ esrc, int* __restrict__ enbr, bf16* __restrict__ U) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int k = inst_of ? inst_of[i] : 0;
   const Inst& I = inst[k];
   const int4 pi = P[i];
   const float4 vi = V[i];
-  const float inv_c0 = 1.0f / I.c0, inv_h = I.inv_h;
-  const float dev_i = i2f(pi.w) / I.rho0;
-  const float dt_ad = (float)ctrl[k].dt_ad;
-  bf16* u = U + i * 16;
+  const float inv_c0 = 1.0f / I.c0;
   const float uv[3] = {vi.x, vi.y, vi.z};
+  __align__(16) bf16 u[16];
   for (int c = 0; c < 16; ++c) u[c] = __float2bfloat16_rn(0.f);
   for (int a = 0; a < D; ++a) u[a] = __float2bfloat16_rn(uv[a] * inv_c0);
-  u[D] = __float2bfloat16_rn(S_RHO * dev_i);
-  u[D + 1] = __float2bfloat16_rn(dt_ad * I.c0 * inv_h);
+  u[D] = __float2bfloat16_rn(S_RHO * (i2f(pi.w) / I.rho0));
+  u[D + 1] = __float2bfloat16_rn((float)ctrl[k].dt_ad * I.c0 * I.inv_h);
   u[D + 2] = __float2bfloat16_rn(1.0f);
+  uint4* dst = reinterpret_cast<uint4*>(U + i * 16);
+  dst[0] = reinterpret_cast<const uint4*>(u)[0];
+  dst[1] = reinterpret_cast<const uint4*>(u)[1];
   const uint32_t cnt = nbc[i];
   const int nf = (int)(cnt & 0xffffu), nw = (int)(cnt >> 16);
-  const int fe = 2 * D + 3;
   uint32_t e = off[i];
   for (int s = 0; s < nf + nw; ++s, ++e) {
     const bool wall = s >= nf;
     const int j = nbr[slot_index(n, i, wall ? wall_slot0(nf) + (s - nf) : s)];
-    const int4 pj = wall ? WP[j] : P[j];
-    float feat[9];
-    const int qi[3] = {pi.x, pi.y, pi.z}, qj[3] = {pj.x, pj.y, pj.z};
-    float vj[3] = {0.f, 0.f, 0.f};
-    float dev_j = 0.f;
-    if (!wall) {
-      const float4 v4 = V[j];
-      vj[0] = v4.x; vj[1] = v4.y; vj[2] = v4.z;
-      dev_j = i2f(pj.w) / I.rho0;
-    }
-    for (int a = 0; a < D; ++a) {
-      const float d = (float)wrap_diff(qi[a] - qj[a], I.period[a]) * I.dq;
-      feat[a] = d * inv_h;
-      feat[D + a] = (uv[a] - vj[a]) * inv_c0;
-    }
-    feat[2 * D] = S_RHO * dev_i;
-    feat[2 * D + 1] = S_RHO * dev_j;
-    feat[2 * D + 2] = wall ? 1.0f : 0.0f;
     esrc[e] = (int)i;
     enbr[e] = wall ? -1 - j : j;
-    bf16* rows[3] = {XE0 + (size_t)e * 80, XE1 + (size_t)e * 80, XE2 + (size_t)e * 80};
-    for (int r = 0; r < 3; ++r) {
-      for (int c = 0; c < fe; ++c) rows[r][c] = __float2bfloat16_rn(feat[c]);
-      for (int c = fe; c < 80; ++c) rows[r][c] = __float2bfloat16_rn(0.f);
-      rows[r][fe + F] = __float2bfloat16_rn(1.0f);
-    }
   }
 }
 
-// XE[e, fe + f] = bf16(h[nbr(e), f]) for fluid neighbours (walls keep 0)
-__global__ void k_gather_h(int64_t E, int fe, const int* __restrict__ enbr, const float* __restrict__ H,
-                           bf16* __restrict__ XE) {
+// Static features of edge e, 16 bf16 per edge: [r_ij/h, (v_i - v_j)/c0, 100 dev_i,
+// 100 dev_j, is_wall, 0...]; the rounds' input rows are assembled from them by k_edge_rows.
+template <int D>
+__global__ void k_edge_features(int64_t E, const int4* __restrict__ P, const float4* __restrict__ V,
+                                const int* __restrict__ inst_of, const Inst* __restrict__ inst,
+                                const int* __restrict__ esrc, const int* __restrict__ enbr,
+                                const int4* __restrict__ WP, bf16* __restrict__ XS) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int i = esrc[e], jj = enbr[e];
+  const bool wall = jj < 0;
+  const int j = wall ? -1 - jj : jj;
+  const Inst& I = inst[inst_of ? inst_of[i] : 0];
+  const int4 pi = P[i];
+  const float4 vi = V[i];
+  const int4 pj = wall ? WP[j] : P[j];
+  float4 vj = make_float4(0.f, 0.f, 0.f, 0.f);
+  float dev_j = 0.f;
+  if (!wall) {
+    vj = V[j];
+    dev_j = i2f(pj.w) / I.rho0;
+  }
+  const float inv_c0 = 1.0f / I.c0;
+  const int qi[3] = {pi.x, pi.y, pi.z}, qj[3] = {pj.x, pj.y, pj.z};
+  const float ui[3] = {vi.x, vi.y, vi.z}, uj[3] = {vj.x, vj.y, vj.z};
+  __align__(16) bf16 row[16];
+  for (int c = 0; c < 16; ++c) row[c] = __float2bfloat16_rn(0.f);
+  for (int a = 0; a < D; ++a) {
+    row[a] = __float2bfloat16_rn((float)wrap_diff(qi[a] - qj[a], I.period[a]) * I.dq * I.inv_h);
+    row[D + a] = __float2bfloat16_rn((ui[a] - uj[a]) * inv_c0);
+  }
+  row[2 * D] = __float2bfloat16_rn(S_RHO * (i2f(pi.w) / I.rho0));
+  row[2 * D + 1] = __float2bfloat16_rn(S_RHO * dev_j);
+  row[2 * D + 2] = __float2bfloat16_rn(wall ? 1.0f : 0.0f);
+  uint4* dst = reinterpret_cast<uint4*>(XS + e * 16);
+  dst[0] = reinterpret_cast<const uint4*>(row)[0];
+  dst[1] = reinterpret_cast<const uint4*>(row)[1];
+}
+
+// Round input row of edge e: XE[e] = [static features (fe) | bf16(h_j) (64, zero for a
+// wall) | 1 | 0...] (80 columns). One thread per 16-byte piece: consecutive threads write
+// consecutive pieces.
+__global__ void k_edge_rows(int64_t E, int fe, const bf16* __restrict__ XS, const int* __restrict__ enbr,
+                            const float* __restrict__ H, bf16* __restrict__ XE) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= E * F) return;
-  const int64_t e = idx / F;
-  const int f = (int)(idx % F);
+  if (idx >= E * 10) return;
+  const int64_t e = idx / 10;
+  const int c0 = (int)(idx - e * 10) * 8;
   const int j = enbr[e];
-  if (j >= 0) XE[e * 80 + fe + f] = __float2bfloat16_rn(H[(int64_t)j * F + f]);
+  __align__(16) bf16 v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int c = c0 + k;
+    float x = 0.f;
+    if (c < fe) x = __bfloat162float(XS[e * 16 + c]);
+    else if (c < fe + F) x = j >= 0 ? H[(int64_t)j * F + (c - fe)] : 0.f;
+    else if (c == fe + F) x = 1.0f;
+    v[k] = __float2bfloat16_rn(x);
+  }
+  *reinterpret_cast<uint4*>(XE + e * 80 + c0) = *reinterpret_cast<const uint4*>(v);
 }
 
 // XN[i] = [bf16(h_i), bf16(a_i), 1], a_i = (1/nbar) sum over node i's edges of M
@@ -433,7 +498,7 @@ __global__ void k_learned_clock(int n_inst, Ctrl* ctrl) {
 }
 
 template <int NO>
-size_t dense_smem(int K) { return (size_t)(NO + kTile) * (K + 8) * sizeof(bf16); }
+size_t dense_smem(int K) { return (size_t)(NO + 2 * kTile) * (K + 8) * sizeof(bf16); }
 
 template <int NO>
 size_t dw_smem(int K) { return (size_t)kTile * ((NO + 8) + (K + 8)) * sizeof(bf16); }
@@ -470,6 +535,7 @@ struct sph_learned {
   int* esrc = nullptr;
   int* enbr = nullptr;
   bf16* U = nullptr;
+  bf16* XS = nullptr;                        // [E][16] static edge features
   bf16* XE[ROUNDS] = {nullptr};
   bf16* A1[ROUNDS] = {nullptr};
   bf16* XN[ROUNDS] = {nullptr};
@@ -531,7 +597,7 @@ int ensure_workspace(sph_learned* L, int64_t n, int64_t E) {
   n = std::max<int64_t>(n, L->cap_n);
   E = std::max<int64_t>(E, L->cap_e);
   bool ok = nalloc(L, &L->cnt, n) && nalloc(L, &L->off, n + 1) &&
-            nalloc(L, &L->scan_tmp, sph::scan_tmp_elems(n)) && nalloc(L, &L->esrc, E) && nalloc(L, &L->enbr, E) &&
+            nalloc(L, &L->scan_tmp, sph::scan_tmp_elems(n)) && nalloc(L, &L->esrc, E) && nalloc(L, &L->enbr, E) && nalloc(L, &L->XS, E * 16) &&
             nalloc(L, &L->U, n * 16) && nalloc(L, &L->Mbuf, E * F) && nalloc(L, &L->H, n * F) &&
             nalloc(L, &L->H0, n * F) && nalloc(L, &L->XD, n * 80) && nalloc(L, &L->A3, n * 80) &&
             nalloc(L, &L->Y, n * 16) && nalloc(L, &L->dH, n * F) && nalloc(L, &L->dXN, n * 144) &&
@@ -549,6 +615,22 @@ int ensure_workspace(sph_learned* L, int64_t n, int64_t E) {
   }
   L->cap_n = n;
   L->cap_e = E;
+  // constant columns of the activation buffers (bias 1 and zero padding): no kernel writes
+  // them afterwards, so they are set once for every row the workspace holds
+  auto consts = [](int64_t rows, int ld, int one, int pad_from, bf16* A) {
+    if (rows > 0) k_const_cols<<<blocks_for(rows), 256>>>(rows, ld, one, pad_from, A);
+  };
+  for (int r = 0; r < ROUNDS; ++r) {
+    consts(E, 80, F, F + 1, L->A1[r]);
+    consts(n, 144, 2 * F, 2 * F + 1, L->XN[r]);
+    consts(n, 80, F, F + 1, L->A2[r]);
+  }
+  consts(n, 80, F, F + 1, L->XD);
+  consts(n, 80, F, F + 1, L->A3);
+  if (cudaDeviceSynchronize() != cudaSuccess) {   // before work on the caller's stream uses them
+    L->err = "initialising the network workspace failed";
+    return SPH_E_CUDA;
+  }
   return SPH_OK;
 }
 
@@ -556,8 +638,16 @@ template <int NO>
 void dense(int64_t M, int K, const bf16* X, int ldx, const bf16* W, float* of, int ldf, int nf, int accum,
            bf16* ob, int ldo, int col0, int nb, int relu, const bf16* mask, int ldm, cudaStream_t s) {
   if (M == 0) return;
-  k_dense<NO><<<blocks_for(M, kTile), 128, dense_smem<NO>(K), s>>>(M, K, X, ldx, W, of, ldf, nf, accum, ob, ldo,
-                                                                   col0, nb, relu, mask, ldm);
+  // rows move as 16-byte pieces and results as pairs: strides and column ranges must allow it
+  if (K % 8 || ldx % 8 || (of && (ldf % 2 || nf % 2)) || (ob && (ldo % 2 || col0 % 2 || nb % 2)) ||
+      (mask && ldm % 2)) {
+    std::fprintf(stderr, "sph_learned: dense layer with unaligned shape\n");
+    return;
+  }
+  const int64_t tiles = (M + kTile - 1) / kTile;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 4);
+  k_dense<NO><<<grid, 128, dense_smem<NO>(K), s>>>(M, K, X, ldx, W, of, ldf, nf, accum, ob, ldo, col0, nb, relu,
+                                                   mask, ldm);
 }
 
 // grad[layer] += dY^T X over M rows
@@ -596,19 +686,19 @@ int build_inputs(sph_handle* h, sph_learned* L, cudaStream_t s) {
     sph::scan_exclusive(L->cnt, L->off, n, L->scan_tmp, s, &dummy);
   }
   L->E = E;
-  if (b.dim == 2)
-    k_features<2><<<blocks_for(n), 256, 0, s>>>(n, b.PS, b.VS, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, L->off, b.WP,
-                                                L->esrc, L->enbr, L->U, L->XE[0], L->XE[1], L->XE[2]);
-  else
-    k_features<3><<<blocks_for(n), 256, 0, s>>>(n, b.PS, b.VS, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, L->off, b.WP,
-                                                L->esrc, L->enbr, L->U, L->XE[0], L->XE[1], L->XE[2]);
-  for (int r = 0; r < ROUNDS; ++r) {
-    k_const_cols<<<blocks_for(E), 256, 0, s>>>(E, 80, F, F + 1, L->A1[r]);
-    k_const_cols<<<blocks_for(n), 256, 0, s>>>(n, 144, 2 * F, 2 * F + 1, L->XN[r]);
-    k_const_cols<<<blocks_for(n), 256, 0, s>>>(n, 80, F, F + 1, L->A2[r]);
+  if (b.dim == 2) {
+    k_node_features<2><<<blocks_for(n), 256, 0, s>>>(n, b.PS, b.VS, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, L->off,
+                                                     L->esrc, L->enbr, L->U);
+    if (E > 0)
+      k_edge_features<2><<<blocks_for(E), 256, 0, s>>>(E, b.PS, b.VS, b.inst_of, b.inst, L->esrc, L->enbr, b.WP,
+                                                     L->XS);
+  } else {
+    k_node_features<3><<<blocks_for(n), 256, 0, s>>>(n, b.PS, b.VS, b.inst_of, b.inst, b.ctrl, b.nbr, b.nbc, L->off,
+                                                     L->esrc, L->enbr, L->U);
+    if (E > 0)
+      k_edge_features<3><<<blocks_for(E), 256, 0, s>>>(E, b.PS, b.VS, b.inst_of, b.inst, L->esrc, L->enbr, b.WP,
+                                                     L->XS);
   }
-  k_const_cols<<<blocks_for(n), 256, 0, s>>>(n, 80, F, F + 1, L->XD);
-  k_const_cols<<<blocks_for(n), 256, 0, s>>>(n, 80, F, F + 1, L->A3);
   return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_E_CUDA;
 }
 
@@ -620,7 +710,7 @@ void forward(sph_handle* h, sph_learned* L, cudaStream_t s) {
   dense<64>(n, 16, L->U, 16, Wl(L, L_ENC), L->H, F, F, 0, nullptr, 0, 0, 0, 1, nullptr, 0, s);
   cudaMemcpyAsync(L->H0, L->H, sizeof(float) * n * F, cudaMemcpyDeviceToDevice, s);
   for (int r = 0; r < ROUNDS; ++r) {
-    k_gather_h<<<blocks_for(E * F), 256, 0, s>>>(E, fe, L->enbr, L->H, L->XE[r]);
+    if (E > 0) k_edge_rows<<<blocks_for(E * 10), 256, 0, s>>>(E, fe, L->XS, L->enbr, L->H, L->XE[r]);
     dense<64>(E, 80, L->XE[r], 80, Wl(L, L_E1), nullptr, 0, 0, 0, L->A1[r], 80, 0, F, 1, nullptr, 0, s);
     dense<64>(E, 80, L->A1[r], 80, Wl(L, L_E2), L->Mbuf, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
     k_segsum<<<blocks_for(n * F), 256, 0, s>>>(n, L->off, L->Mbuf, L->H, inv_nbar, L->XN[r]);
@@ -651,12 +741,12 @@ void backward(sph_handle* h, sph_learned* L, cudaStream_t s) {
     dense_dw<64>(L, L_N1, n, 144, dZ2, F, L->XN[r], 144, s);
     dense<144>(n, 64, dZ2, F, WTl(L, L_N1), L->dXN, 144, 144, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
     k_node_back<<<blocks_for(n * F), 256, 0, s>>>(n, L->dXN, L->dH);
-    k_edge_back<<<blocks_for(E * F), 256, 0, s>>>(E, L->esrc, L->dXN, inv_nbar, L->dM);
+    if (E > 0) k_edge_back<<<blocks_for(E * F), 256, 0, s>>>(E, L->esrc, L->dXN, inv_nbar, L->dM);
     dense_dw<64>(L, L_E2, E, 80, L->dM, F, L->A1[r], 80, s);
     dense<80>(E, 64, L->dM, F, WTl(L, L_E2), nullptr, 0, 0, 0, L->dZe, F, 0, F, 0, L->A1[r], 80, s);
     dense_dw<64>(L, L_E1, E, 80, L->dZe, F, L->XE[r], 80, s);
     dense<80>(E, 64, L->dZe, F, WTl(L, L_E1), L->dXE, 80, 80, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
-    k_scatter_dh<<<blocks_for(E * F), 256, 0, s>>>(E, fe, L->enbr, L->dXE, L->dH);
+    if (E > 0) k_scatter_dh<<<blocks_for(E * F), 256, 0, s>>>(E, fe, L->enbr, L->dXE, L->dH);
   }
   k_relu_back<<<blocks_for(n * F), 256, 0, s>>>(n, L->dH, L->H0, L->dZn);
   dense_dw<64>(L, L_ENC, n, 16, L->dZn, F, L->U, 16, s);
