@@ -371,6 +371,9 @@ def run_workload(args):
     if args.workload == "learned":
         run_learned(args, stream)
         return
+    if args.workload == "learned_step":
+        run_learned_step(args, stream)
+        return
     if args.workload == "sizes":
         run_sizes(args)
         return
@@ -454,6 +457,43 @@ def run_sizes(args):
     print(json.dumps(out), flush=True)
 
 
+def run_learned_step(args, stream):
+    """Cost of one learned advection step against one plain step on the 2D dam break at
+    100,128 particles, with the network's initial weights (no training: timing only)."""
+    import torch
+    from paper_2010_12375_gb300 import learned, sph, workloads as wk
+    prob = wk.learned_dam_break()
+    sim = sph.Simulation(prob, flags=sph.SPH_FLAG_GRAPH, stream=stream)
+    for _ in range(args.warmup):
+        sim.step(1)
+    ms, _, _ = _timed_steps(sim, args.steps, stream)          # plain steps first, graph loop
+    net = sph.sph_learned_create(2, learned.initial_weights(2, seed=0))
+    # every learned step starts from the same state (the untrained network is not meant to be
+    # stepped on its own output); only the learned steps are inside the events
+    start = sim.state()
+    t0 = sim.diagnostics()["t"]
+    total = 0.0
+    for k in range(args.warmup + args.steps):
+        sim.set_state(*start, t=t0)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sph.sph_learned_step(sim.handle, net, 1.0, 1.0, stream=stream)   # guard open: always kept
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            total += ev0.elapsed_time(ev1)
+    learned_ms = total / args.steps
+    sph.sph_learned_destroy(net)
+    sim.close()
+    out = {"metric": "learned advection step time, 2D dam break 100,128 particles", "unit": "ms",
+           "value": learned_ms, "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "dtype": "bf16 network, f32 solver", "data": "synthetic",
+           "config": {"workload": f"2D dam break H=1, L=2, {prob.n_fluid} fluid particles, initial weights"},
+           "plain_ms_per_step": ms / args.steps}
+    print(json.dumps(out), flush=True)
+
+
 def run_learned(args, stream):
     """Train the learned stand-in on solver trajectories of 200 seeded tanks, then step the
     2D dam break at 100,128 particles with it (fallback on) and without it."""
@@ -505,7 +545,7 @@ def main():
                     help="the frozen-pair-geometry reading (pair vectors kept from the configuration update)")
     ap.add_argument("--launch-config", default=None,
                     help="pr_tpp,pr_block,dr_tpp,dr_block: fixed launch variants instead of autotuning")
-    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "sizes"],
+    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes"],
                     help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()
     if args.warmup < 3:
