@@ -16,8 +16,9 @@
 // cores (mma.sync m16n8k16). These layers are skinny (64 outputs, K <= 144: ~34 FLOP per
 // byte moved, far below the tensor-core ridge of ~285), so they are bound by HBM and the
 // warp-level MMA is not their limiter. Weight gradients are summed per block and then over
-// blocks in a fixed order (deterministic); node-embedding gradients of the gather are
-// scattered with FP32 atomics.
+// blocks in a fixed order and node-embedding gradients of the neighbour gather are summed
+// per node over its reverse edges in edge order, so a training step is deterministic (only
+// the reported loss value is accumulated with atomics).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -414,15 +415,37 @@ __global__ void k_edge_back(int64_t E, const int* __restrict__ esrc, const float
   dM[e * F + f] = __float2bfloat16_rn(dXN[(int64_t)esrc[e] * 144 + F + f] * inv_nbar);
 }
 
-// dh[nbr(e)] += dXE[e, fe + f] for fluid neighbours (gather transpose)
-__global__ void k_scatter_dh(int64_t E, int fe, const int* __restrict__ enbr, const float* __restrict__ dXE,
-                             float* __restrict__ dH) {
+// Reverse of each fluid edge: erev[e] for e = (i -> j) is the edge (j -> i) (the frozen
+// fluid neighbour relation is symmetric: |r_i - r_j| < 2h either way); -1 for walls.
+__global__ void k_reverse_edges(int64_t E, const int* __restrict__ esrc, const int* __restrict__ enbr,
+                                const uint32_t* __restrict__ off, int* __restrict__ erev) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int i = esrc[e], j = enbr[e];
+  int r = -1;
+  if (j >= 0)
+    for (uint32_t e2 = off[j]; e2 < off[j + 1]; ++e2)
+      if (enbr[e2] == i) {
+        r = (int)e2;
+        break;
+      }
+  erev[e] = r;
+}
+
+// Transpose of the gather h_j -> x_ij: dh[j] += sum over edges (i -> j) of dXE[e, fe + f],
+// taken over j's own fluid edges (j -> i) through their reverses, in edge order.
+__global__ void k_gather_dh(int64_t n, int fe, const uint32_t* __restrict__ off, const int* __restrict__ enbr,
+                            const int* __restrict__ erev, const float* __restrict__ dXE, float* __restrict__ dH) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= E * F) return;
-  const int64_t e = idx / F;
+  if (idx >= n * F) return;
+  const int64_t j = idx / F;
   const int f = (int)(idx % F);
-  const int j = enbr[e];
-  if (j >= 0) atomicAdd(&dH[(int64_t)j * F + f], dXE[e * 80 + fe + f]);
+  float acc = 0.f;
+  for (uint32_t e2 = off[j]; e2 < off[j + 1] && enbr[e2] >= 0; ++e2) {
+    const int r = erev[e2];
+    if (r >= 0) acc += dXE[(int64_t)r * 80 + fe + f];
+  }
+  dH[j * F + f] += acc;
 }
 
 // dZ0 = bf16(dh * (h0 > 0))
@@ -536,6 +559,7 @@ struct sph_learned {
   int* enbr = nullptr;
   bf16* U = nullptr;
   bf16* XS = nullptr;                        // [E][16] static edge features
+  int* erev = nullptr;                       // [E] reverse of each fluid edge, -1 for walls
   bf16* XE[ROUNDS] = {nullptr};
   bf16* A1[ROUNDS] = {nullptr};
   bf16* XN[ROUNDS] = {nullptr};
@@ -597,7 +621,7 @@ int ensure_workspace(sph_learned* L, int64_t n, int64_t E) {
   n = std::max<int64_t>(n, L->cap_n);
   E = std::max<int64_t>(E, L->cap_e);
   bool ok = nalloc(L, &L->cnt, n) && nalloc(L, &L->off, n + 1) &&
-            nalloc(L, &L->scan_tmp, sph::scan_tmp_elems(n)) && nalloc(L, &L->esrc, E) && nalloc(L, &L->enbr, E) && nalloc(L, &L->XS, E * 16) &&
+            nalloc(L, &L->scan_tmp, sph::scan_tmp_elems(n)) && nalloc(L, &L->esrc, E) && nalloc(L, &L->enbr, E) && nalloc(L, &L->XS, E * 16) && nalloc(L, &L->erev, E) &&
             nalloc(L, &L->U, n * 16) && nalloc(L, &L->Mbuf, E * F) && nalloc(L, &L->H, n * F) &&
             nalloc(L, &L->H0, n * F) && nalloc(L, &L->XD, n * 80) && nalloc(L, &L->A3, n * 80) &&
             nalloc(L, &L->Y, n * 16) && nalloc(L, &L->dH, n * F) && nalloc(L, &L->dXN, n * 144) &&
@@ -727,6 +751,7 @@ void backward(sph_handle* h, sph_learned* L, cudaStream_t s) {
   const int d = h->b.dim, fe = 2 * d + 3;
   const float inv_nbar = 1.0f / nbar(d);
   cudaMemsetAsync(L->grad, 0, sizeof(float) * kWeights, s);
+  if (E > 0) k_reverse_edges<<<blocks_for(E), 256, 0, s>>>(E, L->esrc, L->enbr, L->off, L->erev);
   // decoder
   dense_dw<16>(L, L_D2, n, 80, L->dYb, 16, L->A3, 80, s);
   dense<80>(n, 16, L->dYb, 16, WTl(L, L_D2), nullptr, 0, 0, 0, L->dZn, F, 0, F, 0, L->A3, 80, s);
@@ -746,7 +771,7 @@ void backward(sph_handle* h, sph_learned* L, cudaStream_t s) {
     dense<80>(E, 64, L->dM, F, WTl(L, L_E2), nullptr, 0, 0, 0, L->dZe, F, 0, F, 0, L->A1[r], 80, s);
     dense_dw<64>(L, L_E1, E, 80, L->dZe, F, L->XE[r], 80, s);
     dense<80>(E, 64, L->dZe, F, WTl(L, L_E1), L->dXE, 80, 80, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
-    if (E > 0) k_scatter_dh<<<blocks_for(E * F), 256, 0, s>>>(E, fe, L->enbr, L->dXE, L->dH);
+    if (E > 0) k_gather_dh<<<blocks_for(n * F), 256, 0, s>>>(n, fe, L->off, L->enbr, L->erev, L->dXE, L->dH);
   }
   k_relu_back<<<blocks_for(n * F), 256, 0, s>>>(n, L->dH, L->H0, L->dZn);
   dense_dw<64>(L, L_ENC, n, 16, L->dZn, F, L->U, 16, s);

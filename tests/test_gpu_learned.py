@@ -184,3 +184,22 @@ def test_trained_network_gains_over_the_untrained_predictor(sph):
     assert cmp["kept_fraction"] >= 0.0 and cmp["plain_ms_per_step"] > 0
     sph.sph_learned_destroy(net)
     sph.sph_learned_destroy(zero)
+
+
+def test_training_steps_are_bit_reproducible(sph):
+    # every reduction of forward, backward and Adam runs in a fixed order
+    prob, state = _case(2, seed=6)
+    W0 = pack(mpnn.init_weights(2, seed=2))
+    a = sph.sph_learned_create(2, W0)
+    b = sph.sph_learned_create(2, W0)
+    sim, dt_ad, pos, vel, rho = _start_of_step(sph, prob, state)
+    T = np.random.default_rng(3).normal(0, 0.5, (prob.n_fluid, 3))
+    for _ in range(3):
+        sph.sph_learned_train_step(sim.handle, a, T, 2e-3)
+        sph.sph_learned_train_step(sim.handle, b, T, 2e-3)
+    wa, wb = sph.sph_learned_get_weights(a), sph.sph_learned_get_weights(b)
+    assert np.any(wa != W0)
+    np.testing.assert_array_equal(wa, wb)
+    sph.sph_learned_destroy(a)
+    sph.sph_learned_destroy(b)
+    sim.close()
