@@ -510,10 +510,13 @@ def run_learned(args, stream):
     t_train = time.perf_counter() - t0
     prob = wk.learned_dam_break()
     runs = {}
-    for name, drift in (("per_step_drift_0.5pct", 0.005), ("per_step_drift_0.01pct", 0.0001)):
+    for name, drift in (("per_step_drift_0.5pct", 0.005), ("per_step_drift_0.01pct", 0.0001),
+                        ("per_step_drift_0.001pct", 0.00001)):
         runs[name] = learned.compare_stepping(net, prob, steps=args.steps, max_mean_rho_dev=0.01,
                                               max_energy_drift=drift, stream=stream)
-    best = min(runs.values(), key=lambda r: r["energy_rel_diff"])
+    # the headline: the fastest run within 1 % of the plain run's energy, else the closest one
+    within = [r for r in runs.values() if r["energy_rel_diff"] <= 0.01]
+    best = max(within, key=lambda r: r["speedup"]) if within else min(runs.values(), key=lambda r: r["energy_rel_diff"])
     out = {"metric": "learned vs plain advection steps, 2D dam break 100,128 particles",
            "unit": "speedup (plain ms per step / learned ms per step)", "value": best["speedup"],
            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "dtype": "bf16 network, f32 solver",
