@@ -40,14 +40,19 @@ UNIT = "particle-substeps/s"
 # count (the traffic is per particle: state records plus its neighbour row). Valid only
 # for the kernel sources whose hash is recorded with it.
 TRAFFIC_BYTES_PER_PARTICLE = 391.25
-TRAFFIC_SOURCE_HASH = "02e35a01d689949f"
+TRAFFIC_SOURCE_HASH = "c691de2bc1df65bd"
 
 
 def kernel_source_hash():
+    """Hash of the pressure relaxation's sources with comments and blank lines removed, so
+    the stored traffic figure stays valid across comment edits and lapses on code edits."""
     h = hashlib.sha256()
     for f in ("sph_common.cuh", "sph_relax.cuh", "sph_relax_pr.cu"):
-        with open(os.path.join(ROOT, "paper_2010_12375_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2010_12375_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

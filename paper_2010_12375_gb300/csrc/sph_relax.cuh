@@ -21,6 +21,12 @@
 // distance whose contribution is exactly zero. Pairs that drifted past 2h get
 // t = max(1 - q/2, 0) = 0 and contribute nothing, with no branch. Sums are
 // Kahan-compensated per lane and the two lanes are added at the end.
+//
+// Template switches: TPP threads per particle and BLK threads per block (launch
+// variants, each with its own register budget); UNI, a single-tank handle whose constant
+// record arrives as the kernel argument; FG, the frozen-geometry reading, where each
+// pair's vector r_i - r_j and (dW/dr)/r come from the table written at the configuration
+// update instead of from the current positions.
 #pragma once
 
 #include "sph_kernels.h"

@@ -1,5 +1,6 @@
-// Pressure relaxation launches (kernels and pair terms in sph_relax.cuh). Its own
-// translation unit so the two relaxation kernels compile in parallel.
+// Pressure relaxation launches (kernels and pair terms in sph_relax.cuh) and the
+// frozen-geometry table. Its own translation unit so the two relaxation kernels compile
+// in parallel.
 #include "sph_relax.cuh"
 
 namespace sph {
