@@ -214,7 +214,8 @@ int sph_pair_count(sph_handle* h, int64_t* fluid_pairs, int64_t* wall_pairs, voi
  * and cfg[1] block size of the pressure relaxation, cfg[2], cfg[3] the same for the
  * density relaxation. Threads per particle 1, 2 or 4 (the lanes of a particle split its
  * neighbour row and add their sums in a fixed order); block 128, 256 or 512. Set
- * returns SPH_E_INVALID for other values. */
+ * returns SPH_E_INVALID for other values. Handles created with SPH_FLAG_FROZEN_GEOMETRY
+ * run one thread per particle in 128-thread blocks whatever the configuration says. */
 int sph_get_launch_config(const sph_handle* h, int32_t* cfg);
 int sph_set_launch_config(sph_handle* h, const int32_t* cfg);
 
