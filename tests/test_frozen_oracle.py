@@ -5,6 +5,7 @@ Where positions do not move relative to one another over a half step, both readi
 give the same result; over a whole step the frozen pair terms stay antisymmetric, so
 momentum is conserved; and the difference between the readings shrinks with the step."""
 import numpy as np
+import pytest
 
 from oracle import wcsph as o
 from paper_2010_12375_gb300 import workloads as wk
@@ -92,3 +93,10 @@ def test_readings_differ_by_a_first_order_term_in_the_step():
         gaps.append(np.abs(a_frz - a_rec).max())
     assert gaps[0] > 0
     assert 1.8 < gaps[0] / gaps[1] < 2.2 and 1.8 < gaps[1] / gaps[2] < 2.2
+
+
+def test_planted_sign_flip_of_the_frozen_vectors_is_caught(monkeypatch):
+    orig = o.frozen_geometry
+    monkeypatch.setattr(o, "frozen_geometry", lambda st, w, nb, prm: tuple(-g for g in orig(st, w, nb, prm)))
+    with pytest.raises(AssertionError):
+        test_at_rest_the_first_half_step_is_the_same_in_both_readings()

@@ -472,3 +472,32 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(o, "density_relaxation", stale_velocity)
     with pytest.raises(AssertionError):
         test_free_particle_follows_ballistic_trajectory()
+    monkeypatch.setattr(o, "density_relaxation", orig_dr)
+    # 6. density summation without the particle's own W(0) -> lattice density pin fails
+    orig_ds = o.density_summation
+
+    def no_self(st, w, nb, prm):
+        return orig_ds(st, w, nb, prm) - prm.rho0 * o.kernel_W(0.0, prm.h, prm.dim) / prm.sigma0
+    monkeypatch.setattr(o, "density_summation", no_self)
+    with pytest.raises(AssertionError):
+        test_density_summation_on_lattice(2)
+    monkeypatch.setattr(o, "density_summation", orig_ds)
+    # 7. viscous term with the wrong sign -> shear-flow Laplacian pin fails
+    orig_visc = o.viscous_acceleration
+    monkeypatch.setattr(o, "viscous_acceleration", lambda st, nb, prm: -orig_visc(st, nb, prm))
+    with pytest.raises(AssertionError):
+        test_viscous_term_matches_laplacian_of_shear_flow()
+    monkeypatch.setattr(o, "viscous_acceleration", orig_visc)
+    # 8. advection step without the U_ref speed floor (R7) -> the paper's CFL pin fails
+    orig_dta = o.dt_advection
+
+    def no_floor(v, prm):
+        vmax = float(np.sqrt(np.max(np.sum(v * v, axis=1)))) if v.size else 0.0
+        dt = prm.h / max(vmax, 1e-300)
+        if prm.nu > 0.0:
+            dt = min(dt, prm.h * prm.h / prm.nu)
+        return prm.cfl_ad * dt
+    monkeypatch.setattr(o, "dt_advection", no_floor)
+    with pytest.raises(AssertionError):
+        test_dual_criteria_time_steps_use_the_papers_constants()
+    monkeypatch.setattr(o, "dt_advection", orig_dta)
