@@ -23,7 +23,7 @@
  *    asynchronous on it, except those that return host values, which
  *    synchronise that stream before returning.
  *  - Particle order at the boundary is always the caller's order ("id" order:
- *    row k is particle k). Inside, particles are re-sorted by cell every
+ *    row k is particle k). Inside, particles are re-sorted by search cell every
  *    advection step.
  *  - The handle is not thread safe; calls on one handle must be serialised.
  *
