@@ -124,3 +124,23 @@ def test_frozen_graph_loop_equals_host_loop(sph):
         np.testing.assert_array_equal(u, v)
     a.close()
     b.close()
+
+
+def test_frozen_batched_tanks_match_single_runs(sph):
+    # the multi-tank launches (tank constants read per particle) against one tank per handle
+    tanks = wk.batched_dam_breaks(n_instances=4, n_min=300, n_max=2000)
+    flags = sph.SPH_FLAG_FROZEN_GEOMETRY
+    multi = sph.Simulation(tanks, flags=flags)
+    multi.step(3)
+    pos_m, vel_m, rho_m, _ = multi.state()
+    off = multi.fluid_offsets
+    for k, t in enumerate(tanks):
+        single = sph.Simulation(t, flags=flags)
+        single.step(3)
+        pos_s, vel_s, rho_s, _ = single.state()
+        sl = slice(off[k], off[k + 1])
+        np.testing.assert_array_equal(pos_m[sl], pos_s)
+        np.testing.assert_array_equal(vel_m[sl], vel_s)
+        np.testing.assert_array_equal(rho_m[sl], rho_s)
+        single.close()
+    multi.close()
