@@ -56,37 +56,49 @@ k_diag_partial(const int4* __restrict__ P, const float4* __restrict__ V, const f
     maxx = fmax(maxx, x);
     cnt += 1.0;
   }
-  __shared__ double red[kDiagBlock];
-  double* out = part + ((size_t)k * gridDim.x + blockIdx.x) * kDiagFields;
+  // block total per field: a fixed butterfly in each warp, then the warp totals in order
+  __shared__ double red[kDiagFields][kDiagBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int f = 0; f < kDiagFields; ++f) {
+    const bool is_max = (f == F_MAXDEV || f == F_MAXX);
     double val = f < kSumFields ? acc[f] : (f == F_MAXDEV ? maxdev : (f == F_MAXX ? maxx : (f == F_COUNT ? cnt : 0.0)));
-    red[threadIdx.x] = val;
-    __syncthreads();
-    for (int s = kDiagBlock / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        double o = red[threadIdx.x + s];
-        if (f == F_MAXDEV || f == F_MAXX) red[threadIdx.x] = fmax(red[threadIdx.x], o);
-        else red[threadIdx.x] += o;
-      }
-      __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_xor_sync(0xffffffffu, val, o);
+      val = is_max ? fmax(val, other) : val + other;
     }
-    if (threadIdx.x == 0) out[f] = red[0];
-    __syncthreads();
+    if (lane == 0) red[f][warp] = val;
+  }
+  __syncthreads();
+  if (threadIdx.x < kDiagFields) {
+    const int f = threadIdx.x;
+    const bool is_max = (f == F_MAXDEV || f == F_MAXX);
+    double r = red[f][0];
+    for (int w = 1; w < kDiagBlock / 32; ++w) r = is_max ? fmax(r, red[f][w]) : r + red[f][w];
+    part[((size_t)k * gridDim.x + blockIdx.x) * kDiagFields + f] = r;
   }
 }
 
-__global__ void k_diag_final(int n_inst, int bpi, const double* __restrict__ part, double* __restrict__ out) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_inst; k += gridDim.x * blockDim.x) {
-    double r[kDiagFields];
-    for (int f = 0; f < kDiagFields; ++f) r[f] = (f == F_MAXX) ? -1e300 : 0.0;
-    for (int b = 0; b < bpi; ++b) {
-      const double* p = part + ((size_t)k * bpi + b) * kDiagFields;
-      for (int f = 0; f < kDiagFields; ++f) {
-        if (f == F_MAXDEV || f == F_MAXX) r[f] = fmax(r[f], p[f]);
-        else r[f] += p[f];
-      }
-    }
-    for (int f = 0; f < kDiagFields; ++f) out[(size_t)k * kDiagFields + f] = r[f];
+// Per instance: one 256-thread block; thread t sums field t % 16 over the blocks
+// t / 16, t / 16 + 16, ... in order, then the 16 group sums of each field are added in
+// order: a fixed summation order, independent of scheduling.
+__global__ void __launch_bounds__(256)
+k_diag_final(int n_inst, int bpi, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double grp[16][kDiagFields];
+  const int k = blockIdx.x;
+  const int f = threadIdx.x % kDiagFields, g = threadIdx.x / kDiagFields;
+  const bool is_max = (f == F_MAXDEV || f == F_MAXX);
+  double r = f == F_MAXX ? -1e300 : 0.0;
+  for (int b = g; b < bpi; b += 16) {
+    const double v = part[((size_t)k * bpi + b) * kDiagFields + f];
+    r = is_max ? fmax(r, v) : r + v;
+  }
+  grp[g][f] = r;
+  __syncthreads();
+  if (threadIdx.x < kDiagFields) {
+    double t = grp[0][f];
+    for (int q = 1; q < 16; ++q) t = is_max ? fmax(t, grp[q][f]) : t + grp[q][f];
+    out[(size_t)k * kDiagFields + f] = t;
   }
 }
 
@@ -104,7 +116,7 @@ void launch_diagnostics(const Buffers& b, double* scratch, double* out, cudaStre
     k_diag_partial<2><<<grid, kDiagBlock, 0, s>>>(b.PS, b.VS, b.mass, b.inst, scratch);
   else
     k_diag_partial<3><<<grid, kDiagBlock, 0, s>>>(b.PS, b.VS, b.mass, b.inst, scratch);
-  k_diag_final<<<(b.n_inst + 127) / 128, 128, 0, s>>>(b.n_inst, bpi, scratch, out);
+  k_diag_final<<<b.n_inst, 256, 0, s>>>(b.n_inst, bpi, scratch, out);
   *launches += 2;
 }
 
