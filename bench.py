@@ -267,8 +267,8 @@ def run_ours(args, rank, world, local_rank):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
-        t_now = sim.diagnostics()["t"] if False else -1.0
-        sph.sph_set_state(sim.handle, h_pos, h_vel, h_rho, h_drho, t_now, stream)
+        # t < 0 leaves the simulated time as it is
+        sph.sph_set_state(sim.handle, h_pos, h_vel, h_rho, h_drho, -1.0, stream)
         sim.step(1)
         sph.sph_get_state(sim.handle, N, dim, stream, out=(h_pos, h_vel, h_rho, h_drho))
     e1.record(stream)

@@ -24,6 +24,17 @@ int blocks_per_inst(const Buffers& b) {
   return (int)want;
 }
 
+// ln(1 + e) - e / (1 + e), the EoS energy per unit mass over c0^2 at rho/rho0 = 1 + e:
+// for |e| <= 1/20 its Taylor series sum_{k>=2} (-1)^k (k-1)/k e^k to k = 16 (the remainder
+// is below 1e-18 of the sum), else the closed form.
+__device__ __forceinline__ double eos_energy(double e) {
+  if (fabs(e) > 0.05) return log1p(e) - e / (1.0 + e);
+  double s = -15.0 / 16.0;                            // coefficient of e^16
+#pragma unroll
+  for (int k = 15; k >= 2; --k) s = fma(s, e, (k & 1 ? -1.0 : 1.0) * (double)(k - 1) / (double)k);
+  return s * e * e;
+}
+
 template <int D>
 __global__ void __launch_bounds__(kDiagBlock)
 k_diag_partial(const int4* __restrict__ P, const float4* __restrict__ V, const float* __restrict__ mass,
@@ -50,7 +61,7 @@ k_diag_partial(const int4* __restrict__ P, const float4* __restrict__ V, const f
     acc[F_PZ] += m * vz;
     acc[F_KE] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
     acc[F_PE] -= m * ((double)I.g[0] * x + (double)I.g[1] * y + (double)I.g[2] * z);
-    acc[F_IE] += m * I.c0_d * I.c0_d * (log1p(dev) - dev / (1.0 + dev));
+    acc[F_IE] += m * I.c0_d * I.c0_d * eos_energy(dev);
     acc[F_SUMDEV] += fabs(dev);
     maxdev = fmax(maxdev, fabs(dev));
     maxx = fmax(maxx, x);
