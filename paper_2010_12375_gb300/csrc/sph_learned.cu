@@ -357,6 +357,195 @@ __global__ void k_segsum(int64_t n, const uint32_t* __restrict__ off, const floa
   XN[i * 144 + F + f] = __float2bfloat16_rn(s * inv_nbar);
 }
 
+// Edge network of one round, fused for inference. Each warp takes a run of kFuseNodes
+// nodes and walks their edges in 16-row tiles. A lane holds, for its two rows of the MMA
+// fragments, exactly the twenty input columns it multiplies: static features from XS,
+// bf16(h_j) from H (zero for a wall), the bias 1 and zero padding, as k_edge_rows lays a
+// round input row out; the next tile's values are loaded while the current tile is
+// multiplied (and the neighbour indices one tile ahead of that). Both edge layers run on
+// the tensor cores (mma.sync m16n8k16, k-steps in k_dense's order; the first layer's
+// accumulators become the second layer's A fragments after k_dense's ReLU and bfloat16
+// rounding), and the messages are added per node in edge order as k_segsum does. XN is
+// therefore bit-identical to the unfused path's, and no per-edge row, activation or
+// message goes to memory.
+constexpr int kFuseWarps = 8;
+constexpr int kFuseNodes = 8;
+constexpr int kFuseLd = 88;                   // padded weight row of 80 bf16
+
+inline size_t fused_smem() {
+  return (size_t)2 * 64 * kFuseLd * sizeof(bf16) + (size_t)kFuseWarps * 16 * F * sizeof(float);
+}
+
+// One fragment row's inputs: the values of its twenty columns as k_edge_rows lays the row
+// out (static feature, h value, bias 1 or zero padding; all zero past the last edge).
+struct FuseRow {
+  float v[20];
+};
+
+// column of slot q (0..19) of a lane with quad index t: k-step q / 4, position q % 4 in
+// {0, 1, 8, 9}
+__device__ __forceinline__ int fuse_col(int q, int t) { return (q >> 2) * 16 + 2 * t + (q & 1) + ((q >> 1) & 1) * 8; }
+
+// Column kinds of a lane's twenty slots as bit masks: h columns, static columns, bias.
+struct FuseKinds {
+  uint32_t h, st, bias;
+};
+
+template <int FE>
+__device__ __forceinline__ FuseKinds fuse_kinds(int t) {
+  FuseKinds k{0u, 0u, 0u};
+#pragma unroll
+  for (int q = 0; q < 20; ++q) {
+    const int c = fuse_col(q, t);
+    if (c < FE) k.st |= 1u << q;
+    else if (c < FE + F) k.h |= 1u << q;
+    else if (c == FE + F) k.bias |= 1u << q;
+  }
+  return k;
+}
+
+template <int FE>
+__device__ __forceinline__ void fuse_load(FuseRow& R, const FuseKinds& K, int64_t e, bool valid, int j, int t,
+                                          const bf16* __restrict__ XS, const float* __restrict__ H) {
+  // static columns occur only in k-step 0 (slots 0..3: XS columns 2t, 2t+1, 2t+8, 2t+9)
+  const uint32_t x0 = valid && (K.st & 3u) ? ld_u32(XS + e * 16 + 2 * t) : 0u;
+  const uint32_t x1 = valid && (K.st & 12u) ? ld_u32(XS + e * 16 + 2 * t + 8) : 0u;
+  const bool hj = valid && j >= 0;
+#pragma unroll
+  for (int q = 0; q < 20; ++q) {
+    const int c = fuse_col(q, t);
+    float x = 0.f;
+    if ((K.h >> q) & 1u) {
+      if (hj) x = __ldg(&H[(int64_t)j * F + (c - FE)]);
+    } else if (q < 4 && ((K.st >> q) & 1u)) {
+      const uint32_t w = q < 2 ? x0 : x1;
+      x = __bfloat162float(__ushort_as_bfloat16((unsigned short)((q & 1) ? (w >> 16) : (w & 0xffffu))));
+    } else if (((K.bias >> q) & 1u) && valid) {
+      x = 1.0f;
+    }
+    R.v[q] = x;
+  }
+}
+
+template <int FE>
+__global__ void __launch_bounds__(kFuseWarps * 32)
+k_edge_round_fused(int64_t n, const uint32_t* __restrict__ off, const bf16* __restrict__ XS,
+                   const int* __restrict__ enbr, const float* __restrict__ H, const bf16* __restrict__ W1,
+                   const bf16* __restrict__ W2, float inv_nbar, bf16* __restrict__ XN) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  bf16* sW1 = reinterpret_cast<bf16*>(smem_raw);
+  bf16* sW2 = sW1 + 64 * kFuseLd;
+  float* sM = reinterpret_cast<float*>(sW2 + 64 * kFuseLd) + warp * 16 * F;
+  for (int idx = threadIdx.x; idx < 64 * 10; idx += blockDim.x) {
+    const int r = idx / 10, c = (idx % 10) * 8;
+    *reinterpret_cast<uint4*>(&sW1[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&W1[r * 80 + c]);
+    *reinterpret_cast<uint4*>(&sW2[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&W2[r * 80 + c]);
+  }
+  __syncthreads();
+  const FuseKinds K = fuse_kinds<FE>(t);
+  const int64_t chunks = (n + kFuseNodes - 1) / kFuseNodes;
+  for (int64_t ch = (int64_t)blockIdx.x * kFuseWarps + warp; ch < chunks; ch += (int64_t)gridDim.x * kFuseWarps) {
+    const int64_t i0 = ch * kFuseNodes, i1 = min(i0 + (int64_t)kFuseNodes, n);
+    const uint32_t e_begin = off[i0], e_end = off[i1];
+    int64_t cur = i0;                         // node whose sum is open
+    uint32_t cur_end = off[cur + 1];
+    float s0 = 0.f, s1 = 0.f;                 // this lane's columns 2 lane, 2 lane + 1
+    // close every node whose edges end at or before edge e (edgeless nodes included)
+    auto close_until = [&](uint32_t e) {
+      while (cur < i1 && cur_end <= e) {
+        const int f = 2 * lane;
+        const float2 hv = *reinterpret_cast<const float2*>(&H[cur * F + f]);
+        *reinterpret_cast<uint32_t*>(&XN[cur * 144 + f]) = pack2(__float2bfloat16_rn(hv.x), __float2bfloat16_rn(hv.y));
+        *reinterpret_cast<uint32_t*>(&XN[cur * 144 + F + f]) =
+            pack2(__float2bfloat16_rn(s0 * inv_nbar), __float2bfloat16_rn(s1 * inv_nbar));
+        s0 = s1 = 0.f;
+        ++cur;
+        if (cur < i1) cur_end = off[cur + 1];
+      }
+    };
+    close_until(e_begin);
+    // pipeline: inputs of the current tile, neighbour indices of the next
+    auto idx_of = [&](uint32_t t0, int r) { return t0 + r < e_end ? __ldg(&enbr[t0 + r]) : -1; };
+    FuseRow ra, rb;
+    {
+      const int ja = idx_of(e_begin, g), jb = idx_of(e_begin, g + 8);
+      fuse_load<FE>(ra, K, (int64_t)e_begin + g, e_begin + g < e_end, ja, t, XS, H);
+      fuse_load<FE>(rb, K, (int64_t)e_begin + g + 8, e_begin + g + 8 < e_end, jb, t, XS, H);
+    }
+    int ja_n = idx_of(e_begin + 16, g), jb_n = idx_of(e_begin + 16, g + 8);
+    for (uint32_t t0 = e_begin; t0 < e_end; t0 += 16) {
+      // the current tile's A fragments of the first layer
+      uint32_t A[5][4];
+#pragma unroll
+      for (int kk = 0; kk < 5; ++kk) {
+        A[kk][0] = pack2(__float2bfloat16_rn(ra.v[4 * kk]), __float2bfloat16_rn(ra.v[4 * kk + 1]));
+        A[kk][1] = pack2(__float2bfloat16_rn(rb.v[4 * kk]), __float2bfloat16_rn(rb.v[4 * kk + 1]));
+        A[kk][2] = pack2(__float2bfloat16_rn(ra.v[4 * kk + 2]), __float2bfloat16_rn(ra.v[4 * kk + 3]));
+        A[kk][3] = pack2(__float2bfloat16_rn(rb.v[4 * kk + 2]), __float2bfloat16_rn(rb.v[4 * kk + 3]));
+      }
+      // next tile's inputs in flight during this tile's products
+      const uint32_t t1 = t0 + 16;
+      if (t1 < e_end) {
+        fuse_load<FE>(ra, K, (int64_t)t1 + g, t1 + g < e_end, ja_n, t, XS, H);
+        fuse_load<FE>(rb, K, (int64_t)t1 + g + 8, t1 + g + 8 < e_end, jb_n, t, XS, H);
+        ja_n = idx_of(t1 + 16, g);
+        jb_n = idx_of(t1 + 16, g + 8);
+      }
+      float acc[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 5; ++kk)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+          const bf16* wr = sW1 + (nt * 8 + g) * kFuseLd + kk * 16 + 2 * t;
+          mma16816(acc[nt], A[kk][0], A[kk][1], A[kk][2], A[kk][3], ld_u32(wr), ld_u32(wr + 8));
+        }
+      // second layer: A = [bf16(relu(z)) | 1 | 0...], z's fragments reused in place
+      float acc2[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) acc2[nt][0] = acc2[nt][1] = acc2[nt][2] = acc2[nt][3] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 5; ++kk) {
+        uint32_t a0, a1, a2, a3;
+        if (kk < 4) {
+          const float* lo = acc[2 * kk];
+          const float* hi = acc[2 * kk + 1];
+          a0 = pack2(__float2bfloat16_rn(fmaxf(lo[0], 0.f)), __float2bfloat16_rn(fmaxf(lo[1], 0.f)));
+          a1 = pack2(__float2bfloat16_rn(fmaxf(lo[2], 0.f)), __float2bfloat16_rn(fmaxf(lo[3], 0.f)));
+          a2 = pack2(__float2bfloat16_rn(fmaxf(hi[0], 0.f)), __float2bfloat16_rn(fmaxf(hi[1], 0.f)));
+          a3 = pack2(__float2bfloat16_rn(fmaxf(hi[2], 0.f)), __float2bfloat16_rn(fmaxf(hi[3], 0.f)));
+        } else {                              // columns 64..79: the bias column, then zeros
+          a0 = a1 = t == 0 ? pack2(__float2bfloat16_rn(1.0f), __float2bfloat16_rn(0.f)) : 0u;
+          a2 = a3 = 0u;
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+          const bf16* wr = sW2 + (nt * 8 + g) * kFuseLd + kk * 16 + 2 * t;
+          mma16816(acc2[nt], a0, a1, a2, a3, ld_u32(wr), ld_u32(wr + 8));
+        }
+      }
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        *reinterpret_cast<float2*>(&sM[g * F + c]) = make_float2(acc2[nt][0], acc2[nt][1]);
+        *reinterpret_cast<float2*>(&sM[(g + 8) * F + c]) = make_float2(acc2[nt][2], acc2[nt][3]);
+      }
+      __syncwarp();
+      const int rows = (int)min(16u, e_end - t0);
+      for (int r = 0; r < rows; ++r) {
+        close_until(t0 + (uint32_t)r);
+        const float2 m = *reinterpret_cast<const float2*>(&sM[r * F + 2 * lane]);
+        s0 += m.x;
+        s1 += m.y;
+      }
+      __syncwarp();                           // sM free for the next tile
+    }
+    close_until(e_end);
+  }
+}
+
 __global__ void k_rows_bf16(int64_t n, int cols, const float* __restrict__ src, int lds, bf16* __restrict__ dst,
                             int ldd) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -550,6 +739,7 @@ struct sph_learned {
   bf16* wb = nullptr;
   bf16* wbt = nullptr;
   int64_t adam_t = 0;
+  bool fused = true;                         // fused edge rounds for inference
   // workspace
   int64_t cap_n = 0, cap_e = 0;
   uint32_t* cnt = nullptr;
@@ -726,18 +916,35 @@ int build_inputs(sph_handle* h, sph_learned* L, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_E_CUDA;
 }
 
-void forward(sph_handle* h, sph_learned* L, cudaStream_t s) {
+// train: keep every round's edge rows and activations for the backward pass; otherwise
+// (inference) the edge network of each round runs fused when the network allows it.
+void forward(sph_handle* h, sph_learned* L, cudaStream_t s, bool train) {
   const int64_t n = h->b.n, E = L->E;
   const int d = h->b.dim, fe = 2 * d + 3;
   const float inv_nbar = 1.0f / nbar(d);
+  const bool fused = L->fused && !train;
   // encoder: H = relu(U W_enc^T); H0 keeps h0 for the encoder's backward
   dense<64>(n, 16, L->U, 16, Wl(L, L_ENC), L->H, F, F, 0, nullptr, 0, 0, 0, 1, nullptr, 0, s);
-  cudaMemcpyAsync(L->H0, L->H, sizeof(float) * n * F, cudaMemcpyDeviceToDevice, s);
+  if (train) cudaMemcpyAsync(L->H0, L->H, sizeof(float) * n * F, cudaMemcpyDeviceToDevice, s);
   for (int r = 0; r < ROUNDS; ++r) {
-    if (E > 0) k_edge_rows<<<blocks_for(E * 10), 256, 0, s>>>(E, fe, L->XS, L->enbr, L->H, L->XE[r]);
-    dense<64>(E, 80, L->XE[r], 80, Wl(L, L_E1), nullptr, 0, 0, 0, L->A1[r], 80, 0, F, 1, nullptr, 0, s);
-    dense<64>(E, 80, L->A1[r], 80, Wl(L, L_E2), L->Mbuf, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
-    k_segsum<<<blocks_for(n * F), 256, 0, s>>>(n, L->off, L->Mbuf, L->H, inv_nbar, L->XN[r]);
+    if (fused) {
+      const int64_t chunks = (n + kFuseNodes - 1) / kFuseNodes;
+      int per_sm = 1, sms = 1, dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      auto kern = d == 2 ? k_edge_round_fused<7> : k_edge_round_fused<9>;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFuseWarps * 32, fused_smem());
+      const unsigned grid = (unsigned)std::min<int64_t>((chunks + kFuseWarps - 1) / kFuseWarps,
+                                                        (int64_t)std::max(per_sm, 1) * sms);
+      if (n > 0)
+        kern<<<grid, kFuseWarps * 32, fused_smem(), s>>>(n, L->off, L->XS, L->enbr, L->H, Wl(L, L_E1), Wl(L, L_E2),
+                                                         inv_nbar, L->XN[r]);
+    } else {
+      if (E > 0) k_edge_rows<<<blocks_for(E * 10), 256, 0, s>>>(E, fe, L->XS, L->enbr, L->H, L->XE[r]);
+      dense<64>(E, 80, L->XE[r], 80, Wl(L, L_E1), nullptr, 0, 0, 0, L->A1[r], 80, 0, F, 1, nullptr, 0, s);
+      dense<64>(E, 80, L->A1[r], 80, Wl(L, L_E2), L->Mbuf, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+      k_segsum<<<blocks_for(n * F), 256, 0, s>>>(n, L->off, L->Mbuf, L->H, inv_nbar, L->XN[r]);
+    }
     dense<64>(n, 144, L->XN[r], 144, Wl(L, L_N1), nullptr, 0, 0, 0, L->A2[r], 80, 0, F, 1, nullptr, 0, s);
     dense<64>(n, 80, L->A2[r], 80, Wl(L, L_N2), L->H, F, F, 1, nullptr, 0, 0, 0, 0, nullptr, 0, s);
   }
@@ -841,6 +1048,8 @@ int sph_learned_create(int32_t dim, const float* weights, sph_learned** out) {
   if (!nalloc(L, &L->w32, kWeights) || !nalloc(L, &L->m, kWeights) || !nalloc(L, &L->v, kWeights) ||
       !nalloc(L, &L->grad, kWeights) || !nalloc(L, &L->wb, kWeights) || !nalloc(L, &L->wbt, kWeights))
     return lfail(L, SPH_E_OOM, "device allocation of the weights failed");
+  cudaFuncSetAttribute(k_edge_round_fused<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem());
+  cudaFuncSetAttribute(k_edge_round_fused<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem());
   set_smem_attrs<16>();
   set_smem_attrs<64>();
   set_smem_attrs<80>();
@@ -884,13 +1093,19 @@ int sph_learned_get_weights(sph_learned* L, float* w) {
   return SPH_OK;
 }
 
+int sph_learned_set_fused(sph_learned* L, int32_t enabled) {
+  if (!L) return SPH_E_INVALID;
+  L->fused = enabled != 0;
+  return SPH_OK;
+}
+
 int sph_learned_predict(sph_handle* h, sph_learned* L, double* y, void* stream) {
   int r = ready(h, L);
   if (r != SPH_OK) return r;
   cudaStream_t s = (cudaStream_t)stream;
   r = build_inputs(h, L, s);
   if (r != SPH_OK) return lfail(L, r, "building the network inputs failed");
-  forward(h, L, s);
+  forward(h, L, s, false);
   if (y) {
     const int dout = h->b.dim + 1;
     const bool dev = device_ptr(y);
@@ -916,7 +1131,7 @@ int sph_learned_train_step(sph_handle* h, sph_learned* L, const double* target, 
   cudaStream_t s = (cudaStream_t)stream;
   r = build_inputs(h, L, s);
   if (r != SPH_OK) return lfail(L, r, "building the network inputs failed");
-  forward(h, L, s);
+  forward(h, L, s, true);
   const int64_t n = h->b.n;
   const int dout = h->b.dim + 1;
   const double* T = target;
@@ -966,7 +1181,7 @@ int sph_learned_step(sph_handle* h, sph_learned* L, double max_mean_rho_dev, dou
   cudaMemcpyAsync(L->saveP, h->b.PS, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(L->saveV, h->b.VS, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(L->saveC, h->b.ctrl, sizeof(sph::Ctrl) * K, cudaMemcpyDeviceToDevice, s);
-  forward(h, L, s);
+  forward(h, L, s, false);
   if (h->b.dim == 2)
     k_apply<2><<<blocks_for(n), 256, 0, s>>>(n, h->b.PS, h->b.VS, h->b.inst_of, h->b.inst, h->b.ctrl, L->Y, h->b.glob);
   else

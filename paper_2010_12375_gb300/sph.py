@@ -37,7 +37,7 @@ EXPORTS = [
     "sph_get_launch_config", "sph_set_launch_config", "sph_autotune", "sph_gather_ceiling",
     "sph_learned_weight_count", "sph_learned_create", "sph_learned_destroy",
     "sph_learned_last_error", "sph_learned_set_weights", "sph_learned_get_weights",
-    "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
+    "sph_learned_set_fused", "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
 ]
 
 
@@ -134,6 +134,7 @@ def load():
         "sph_learned_last_error": (ctypes.c_char_p, [P]),
         "sph_learned_set_weights": (i32, [P, P]),
         "sph_learned_get_weights": (i32, [P, P]),
+        "sph_learned_set_fused": (i32, [P, i32]),
         "sph_learned_predict": (i32, [P, P, P, P]),
         "sph_learned_train_step": (i32, [P, P, P, dbl, ctypes.POINTER(dbl), P, P]),
         "sph_learned_step": (i32, [P, P, dbl, dbl, ctypes.POINTER(i32), P]),
@@ -431,6 +432,11 @@ def sph_learned_get_weights(net):
     w = np.empty(sph_learned_weight_count(), dtype=np.float32)
     _lcheck(lib, net, lib.sph_learned_get_weights(net, _ptr(w)))
     return w
+
+
+def sph_learned_set_fused(net, enabled):
+    lib = load()
+    _lcheck(lib, net, lib.sph_learned_set_fused(net, 1 if enabled else 0))
 
 
 def sph_learned_predict(h, net, n, dim, stream=None):

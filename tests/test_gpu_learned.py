@@ -83,6 +83,21 @@ def test_forward_matches_reference(sph, dim):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+def test_fused_inference_equals_the_unfused_layers(sph, dim):
+    # the fused edge rounds make the same products, roundings and sums in the same order
+    prob, state = _case(dim, seed=2)
+    net = sph.sph_learned_create(dim, pack(mpnn.init_weights(dim, seed=6)))
+    sim, _, _, _, _ = _start_of_step(sph, prob, state)
+    y_fused = sph.sph_learned_predict(sim.handle, net, prob.n_fluid, dim)
+    sph.sph_learned_set_fused(net, False)
+    y_plain = sph.sph_learned_predict(sim.handle, net, prob.n_fluid, dim)
+    assert np.abs(y_plain).max() > 0
+    np.testing.assert_array_equal(y_fused, y_plain)
+    sph.sph_learned_destroy(net)
+    sim.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 def test_gradients_match_reference(sph, dim):
     prob, state = _case(dim, seed=3)
     W = mpnn.init_weights(dim, seed=7)
