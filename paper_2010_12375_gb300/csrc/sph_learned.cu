@@ -358,73 +358,54 @@ __global__ void k_segsum(int64_t n, const uint32_t* __restrict__ off, const floa
 }
 
 // Edge network of one round, fused for inference. Each warp takes a run of kFuseNodes
-// nodes and walks their edges in 16-row tiles. A lane holds, for its two rows of the MMA
-// fragments, exactly the twenty input columns it multiplies: static features from XS,
-// bf16(h_j) from H (zero for a wall), the bias 1 and zero padding, as k_edge_rows lays a
-// round input row out; the next tile's values are loaded while the current tile is
-// multiplied (and the neighbour indices one tile ahead of that). Both edge layers run on
-// the tensor cores (mma.sync m16n8k16, k-steps in k_dense's order; the first layer's
-// accumulators become the second layer's A fragments after k_dense's ReLU and bfloat16
-// rounding), and the messages are added per node in edge order as k_segsum does. XN is
-// therefore bit-identical to the unfused path's, and no per-edge row, activation or
-// message goes to memory.
+// nodes and walks their edges in 16-row tiles. The next tile's h_j rows and static edge
+// features are loaded (whole rows, 16-byte pieces) while the current tile is multiplied,
+// and the neighbour indices one tile ahead of that. A tile's A fragments are read from a
+// per-warp staging copy of those rows, column by column as k_edge_rows lays a round input
+// row out (static features, bf16(h_j) or zero for a wall, the bias 1, zero padding). Both
+// edge layers run on the tensor cores (mma.sync m16n8k16, k-steps in k_dense's order; the
+// first layer's accumulators become the second layer's A fragments after k_dense's ReLU
+// and bfloat16 rounding), and the messages are added per node in edge order as k_segsum
+// does. XN is therefore bit-identical to the unfused path's, and no per-edge row,
+// activation or message goes to memory.
 constexpr int kFuseWarps = 8;
 constexpr int kFuseNodes = 8;
 constexpr int kFuseLd = 88;                   // padded weight row of 80 bf16
+constexpr int kStageLd = 68;                  // staged h row: 64 floats + pad (16-byte rows)
+constexpr int kStageWords = 16 * kStageLd + 16 * 8;   // h rows, then the static features (bf16 pairs)
+constexpr int kMsgLd = 72;                    // message row stride: conflict-free float2 stores
+
+static_assert(16 * kMsgLd <= kStageWords, "messages must fit the staging area");
 
 inline size_t fused_smem() {
-  return (size_t)2 * 64 * kFuseLd * sizeof(bf16) + (size_t)kFuseWarps * 16 * F * sizeof(float);
+  return (size_t)2 * 64 * kFuseLd * sizeof(bf16) + (size_t)kFuseWarps * kStageWords * sizeof(float);
 }
-
-// One fragment row's inputs: the values of its twenty columns as k_edge_rows lays the row
-// out (static feature, h value, bias 1 or zero padding; all zero past the last edge).
-struct FuseRow {
-  float v[20];
-};
 
 // column of slot q (0..19) of a lane with quad index t: k-step q / 4, position q % 4 in
 // {0, 1, 8, 9}
 __device__ __forceinline__ int fuse_col(int q, int t) { return (q >> 2) * 16 + 2 * t + (q & 1) + ((q >> 1) & 1) * 8; }
 
-// Column kinds of a lane's twenty slots as bit masks: h columns, static columns, bias.
-struct FuseKinds {
-  uint32_t h, st, bias;
-};
-
-template <int FE>
-__device__ __forceinline__ FuseKinds fuse_kinds(int t) {
-  FuseKinds k{0u, 0u, 0u};
-#pragma unroll
-  for (int q = 0; q < 20; ++q) {
-    const int c = fuse_col(q, t);
-    if (c < FE) k.st |= 1u << q;
-    else if (c < FE + F) k.h |= 1u << q;
-    else if (c == FE + F) k.bias |= 1u << q;
-  }
-  return k;
+// B fragments of two n-tiles (nt, nt + 1) at k-step k0 from a row-major [n][kFuseLd] weight
+// copy: lane i addresses row i % 8 of 8x8 matrix i / 8 (matrices: (nt, k0), (nt, k0 + 8),
+// (nt + 1, k0), (nt + 1, k0 + 8)), and receives row lane / 4, columns 2 (lane % 4), +1 of
+// each, which is the m16n8k16 B fragment.
+__device__ __forceinline__ void ldsm_b4(const bf16* W, int nt, int k0, int lane, uint32_t& b0, uint32_t& b1,
+                                        uint32_t& c0, uint32_t& c1) {
+  const int m = lane >> 3;
+  const bf16* p = W + ((nt + (m >> 1)) * 8 + (lane & 7)) * kFuseLd + k0 + (m & 1) * 8;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(b0), "=r"(b1), "=r"(c0), "=r"(c1)
+               : "r"(a));
 }
 
+// bf16 of column c of a staged row: static feature, h value, bias or zero padding
 template <int FE>
-__device__ __forceinline__ void fuse_load(FuseRow& R, const FuseKinds& K, int64_t e, bool valid, int j, int t,
-                                          const bf16* __restrict__ XS, const float* __restrict__ H) {
-  // static columns occur only in k-step 0 (slots 0..3: XS columns 2t, 2t+1, 2t+8, 2t+9)
-  const uint32_t x0 = valid && (K.st & 3u) ? ld_u32(XS + e * 16 + 2 * t) : 0u;
-  const uint32_t x1 = valid && (K.st & 12u) ? ld_u32(XS + e * 16 + 2 * t + 8) : 0u;
-  const bool hj = valid && j >= 0;
-#pragma unroll
-  for (int q = 0; q < 20; ++q) {
-    const int c = fuse_col(q, t);
-    float x = 0.f;
-    if ((K.h >> q) & 1u) {
-      if (hj) x = __ldg(&H[(int64_t)j * F + (c - FE)]);
-    } else if (q < 4 && ((K.st >> q) & 1u)) {
-      const uint32_t w = q < 2 ? x0 : x1;
-      x = __bfloat162float(__ushort_as_bfloat16((unsigned short)((q & 1) ? (w >> 16) : (w & 0xffffu))));
-    } else if (((K.bias >> q) & 1u) && valid) {
-      x = 1.0f;
-    }
-    R.v[q] = x;
-  }
+__device__ __forceinline__ bf16 fuse_elem(const float* __restrict__ hrow, const bf16* __restrict__ xrow, int c,
+                                          bool valid) {
+  if (c < FE) return xrow[c];
+  if (c < FE + F) return __float2bfloat16_rn(hrow[c - FE]);
+  return __float2bfloat16_rn(valid && c == FE + F ? 1.0f : 0.f);
 }
 
 template <int FE>
@@ -436,14 +417,15 @@ k_edge_round_fused(int64_t n, const uint32_t* __restrict__ off, const bf16* __re
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   bf16* sW1 = reinterpret_cast<bf16*>(smem_raw);
   bf16* sW2 = sW1 + 64 * kFuseLd;
-  float* sM = reinterpret_cast<float*>(sW2 + 64 * kFuseLd) + warp * 16 * F;
+  float* stage = reinterpret_cast<float*>(sW2 + 64 * kFuseLd) + warp * kStageWords;   // h rows
+  bf16* xstage = reinterpret_cast<bf16*>(stage + 16 * kStageLd);                       // [16][16]
+  float* sM = stage;                          // the messages reuse the staging rows (16 x kMsgLd)
   for (int idx = threadIdx.x; idx < 64 * 10; idx += blockDim.x) {
     const int r = idx / 10, c = (idx % 10) * 8;
     *reinterpret_cast<uint4*>(&sW1[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&W1[r * 80 + c]);
     *reinterpret_cast<uint4*>(&sW2[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&W2[r * 80 + c]);
   }
   __syncthreads();
-  const FuseKinds K = fuse_kinds<FE>(t);
   const int64_t chunks = (n + kFuseNodes - 1) / kFuseNodes;
   for (int64_t ch = (int64_t)blockIdx.x * kFuseWarps + warp; ch < chunks; ch += (int64_t)gridDim.x * kFuseWarps) {
     const int64_t i0 = ch * kFuseNodes, i1 = min(i0 + (int64_t)kFuseNodes, n);
@@ -465,32 +447,52 @@ k_edge_round_fused(int64_t n, const uint32_t* __restrict__ off, const bf16* __re
       }
     };
     close_until(e_begin);
-    // pipeline: inputs of the current tile, neighbour indices of the next
-    auto idx_of = [&](uint32_t t0, int r) { return t0 + r < e_end ? __ldg(&enbr[t0 + r]) : -1; };
-    FuseRow ra, rb;
-    {
-      const int ja = idx_of(e_begin, g), jb = idx_of(e_begin, g + 8);
-      fuse_load<FE>(ra, K, (int64_t)e_begin + g, e_begin + g < e_end, ja, t, XS, H);
-      fuse_load<FE>(rb, K, (int64_t)e_begin + g + 8, e_begin + g + 8 < e_end, jb, t, XS, H);
-    }
-    int ja_n = idx_of(e_begin + 16, g), jb_n = idx_of(e_begin + 16, g + 8);
+    // neighbour index of row `lane` (lanes 0..15) of the tile at t0, -1 past the end
+    auto idx_of = [&](uint32_t t0) { return lane < 16 && t0 + lane < e_end ? __ldg(&enbr[t0 + lane]) : -1; };
+    // the tile's rows: piece p of lane l is row 2p + l / 16, floats 4 (l % 16) .. + 3
+    float4 hq[8];
+    uint4 xq;
+    auto load_tile = [&](uint32_t t0, int jrow) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const int row = 2 * p + (lane >> 4);
+        const int j = __shfl_sync(0xffffffffu, jrow, row);
+        hq[p] = (t0 + row < e_end && j >= 0) ? __ldg(reinterpret_cast<const float4*>(&H[(int64_t)j * F]) + (lane & 15))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const int xrow = lane >> 1;
+      xq = t0 + xrow < e_end ? __ldg(reinterpret_cast<const uint4*>(&XS[((int64_t)t0 + xrow) * 16]) + (lane & 1))
+                             : make_uint4(0u, 0u, 0u, 0u);
+    };
+    load_tile(e_begin, idx_of(e_begin));
+    int jn = idx_of(e_begin + 16);
     for (uint32_t t0 = e_begin; t0 < e_end; t0 += 16) {
-      // the current tile's A fragments of the first layer
+      // stage the current tile's rows and read this lane's A fragments of the first layer
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+        *reinterpret_cast<float4*>(&stage[(2 * p + (lane >> 4)) * kStageLd + 4 * (lane & 15)]) = hq[p];
+      *reinterpret_cast<uint4*>(&xstage[(lane >> 1) * 16 + 8 * (lane & 1)]) = xq;
+      __syncwarp();
+      const bool va = t0 + g < e_end, vb = t0 + g + 8 < e_end;
+      const float* ha = stage + g * kStageLd;
+      const float* hb = ha + 8 * kStageLd;
+      const bf16* xa = xstage + g * 16;
+      const bf16* xb = xa + 8 * 16;
       uint32_t A[5][4];
 #pragma unroll
       for (int kk = 0; kk < 5; ++kk) {
-        A[kk][0] = pack2(__float2bfloat16_rn(ra.v[4 * kk]), __float2bfloat16_rn(ra.v[4 * kk + 1]));
-        A[kk][1] = pack2(__float2bfloat16_rn(rb.v[4 * kk]), __float2bfloat16_rn(rb.v[4 * kk + 1]));
-        A[kk][2] = pack2(__float2bfloat16_rn(ra.v[4 * kk + 2]), __float2bfloat16_rn(ra.v[4 * kk + 3]));
-        A[kk][3] = pack2(__float2bfloat16_rn(rb.v[4 * kk + 2]), __float2bfloat16_rn(rb.v[4 * kk + 3]));
+        const int c = kk * 16 + 2 * t;
+        A[kk][0] = pack2(fuse_elem<FE>(ha, xa, c, va), fuse_elem<FE>(ha, xa, c + 1, va));
+        A[kk][1] = pack2(fuse_elem<FE>(hb, xb, c, vb), fuse_elem<FE>(hb, xb, c + 1, vb));
+        A[kk][2] = pack2(fuse_elem<FE>(ha, xa, c + 8, va), fuse_elem<FE>(ha, xa, c + 9, va));
+        A[kk][3] = pack2(fuse_elem<FE>(hb, xb, c + 8, vb), fuse_elem<FE>(hb, xb, c + 9, vb));
       }
-      // next tile's inputs in flight during this tile's products
+      __syncwarp();                           // staging read: free for the messages
+      // next tile's rows in flight during this tile's products
       const uint32_t t1 = t0 + 16;
       if (t1 < e_end) {
-        fuse_load<FE>(ra, K, (int64_t)t1 + g, t1 + g < e_end, ja_n, t, XS, H);
-        fuse_load<FE>(rb, K, (int64_t)t1 + g + 8, t1 + g + 8 < e_end, jb_n, t, XS, H);
-        ja_n = idx_of(t1 + 16, g);
-        jb_n = idx_of(t1 + 16, g + 8);
+        load_tile(t1, jn);
+        jn = idx_of(t1 + 16);
       }
       float acc[8][4];
 #pragma unroll
@@ -498,9 +500,11 @@ k_edge_round_fused(int64_t n, const uint32_t* __restrict__ off, const bf16* __re
 #pragma unroll
       for (int kk = 0; kk < 5; ++kk)
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-          const bf16* wr = sW1 + (nt * 8 + g) * kFuseLd + kk * 16 + 2 * t;
-          mma16816(acc[nt], A[kk][0], A[kk][1], A[kk][2], A[kk][3], ld_u32(wr), ld_u32(wr + 8));
+        for (int nt = 0; nt < 8; nt += 2) {
+          uint32_t b0, b1, c0, c1;
+          ldsm_b4(sW1, nt, kk * 16, lane, b0, b1, c0, c1);
+          mma16816(acc[nt], A[kk][0], A[kk][1], A[kk][2], A[kk][3], b0, b1);
+          mma16816(acc[nt + 1], A[kk][0], A[kk][1], A[kk][2], A[kk][3], c0, c1);
         }
       // second layer: A = [bf16(relu(z)) | 1 | 0...], z's fragments reused in place
       float acc2[8][4];
@@ -521,26 +525,28 @@ k_edge_round_fused(int64_t n, const uint32_t* __restrict__ off, const bf16* __re
           a2 = a3 = 0u;
         }
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-          const bf16* wr = sW2 + (nt * 8 + g) * kFuseLd + kk * 16 + 2 * t;
-          mma16816(acc2[nt], a0, a1, a2, a3, ld_u32(wr), ld_u32(wr + 8));
+        for (int nt = 0; nt < 8; nt += 2) {
+          uint32_t b0, b1, c0, c1;
+          ldsm_b4(sW2, nt, kk * 16, lane, b0, b1, c0, c1);
+          mma16816(acc2[nt], a0, a1, a2, a3, b0, b1);
+          mma16816(acc2[nt + 1], a0, a1, a2, a3, c0, c1);
         }
       }
 #pragma unroll
       for (int nt = 0; nt < 8; ++nt) {
         const int c = nt * 8 + 2 * t;
-        *reinterpret_cast<float2*>(&sM[g * F + c]) = make_float2(acc2[nt][0], acc2[nt][1]);
-        *reinterpret_cast<float2*>(&sM[(g + 8) * F + c]) = make_float2(acc2[nt][2], acc2[nt][3]);
+        *reinterpret_cast<float2*>(&sM[g * kMsgLd + c]) = make_float2(acc2[nt][0], acc2[nt][1]);
+        *reinterpret_cast<float2*>(&sM[(g + 8) * kMsgLd + c]) = make_float2(acc2[nt][2], acc2[nt][3]);
       }
       __syncwarp();
       const int rows = (int)min(16u, e_end - t0);
       for (int r = 0; r < rows; ++r) {
         close_until(t0 + (uint32_t)r);
-        const float2 m = *reinterpret_cast<const float2*>(&sM[r * F + 2 * lane]);
+        const float2 m = *reinterpret_cast<const float2*>(&sM[r * kMsgLd + 2 * lane]);
         s0 += m.x;
         s1 += m.y;
       }
-      __syncwarp();                           // sM free for the next tile
+      __syncwarp();                           // sM free for the next tile's staging
     }
     close_until(e_end);
   }
