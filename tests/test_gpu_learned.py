@@ -97,6 +97,48 @@ def test_fused_inference_equals_the_unfused_layers(sph, dim):
     sim.close()
 
 
+def test_fused_inference_with_edgeless_nodes(sph):
+    # five particles lifted into the empty upper tank, > 2h from everything: nodes without
+    # edges between nodes with edges, in the fused kernel's node runs and edge tiles
+    prob, (x, v, rho, drho) = _case(2, seed=4)
+    x = x.copy()
+    for k in range(5):
+        x[7 * k + 3] = (0.1 + 0.15 * k, 0.8)
+    state = representable(prob, x, v, rho, drho)
+    net = sph.sph_learned_create(2, pack(mpnn.init_weights(2, seed=8)))
+    sim, _, _, _, _ = _start_of_step(sph, prob, state)
+    fc, wc, _, _ = sim.neighbours()
+    assert np.count_nonzero(fc + wc == 0) >= 5
+    y_fused = sph.sph_learned_predict(sim.handle, net, prob.n_fluid, 2)
+    sph.sph_learned_set_fused(net, False)
+    y_plain = sph.sph_learned_predict(sim.handle, net, prob.n_fluid, 2)
+    np.testing.assert_array_equal(y_fused, y_plain)
+    sph.sph_learned_destroy(net)
+    sim.close()
+
+
+def test_fused_inference_single_particle(sph):
+    # no edges at all: every round's messages are zero
+    prob = wk.dam_break(dim=2, H=0.3, L=0.4, dp=0.02, tank=1.0)
+    prob.wall_pos = walls_representable(prob)
+    single = copy.copy(prob)
+    single.pos = np.array([[0.5, 0.5]])
+    single.vel = np.array([[0.1, -0.2]])
+    single.rho = np.array([prob.rho0])
+    single.mass = prob.mass[:1]
+    net = sph.sph_learned_create(2, pack(mpnn.init_weights(2, seed=9)))
+    sim = sph.Simulation(single)
+    sim.build_cells()
+    sim.advection_step()
+    y_fused = sph.sph_learned_predict(sim.handle, net, 1, 2)
+    sph.sph_learned_set_fused(net, False)
+    y_plain = sph.sph_learned_predict(sim.handle, net, 1, 2)
+    assert np.all(np.isfinite(y_fused))
+    np.testing.assert_array_equal(y_fused, y_plain)
+    sph.sph_learned_destroy(net)
+    sim.close()
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_gradients_match_reference(sph, dim):
     prob, state = _case(dim, seed=3)
