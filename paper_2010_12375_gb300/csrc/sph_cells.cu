@@ -3,10 +3,11 @@
 //   hash      particle -> search cell (integer: q >> (bits - 1) per axis, i.e. cells of
 //             half the 2h position cell, about h; flattened x fastest)
 //   sort      counting sort on the cell digit (a one-digit radix sort with radix =
-//             number of cells) followed by an in-cell sort by caller id, which makes
-//             the order the unique (cell, id) order, independent of history
+//             number of cells), then each particle's rank among its cell mates by
+//             caller id, which makes the order the unique (cell, id) order,
+//             independent of history
 //   offsets   exclusive scan of the cell counts
-//   reorder   gather of the 32-byte particle records into cell order
+//   reorder   the 32-byte particle records moved to their (cell, id) slots
 //   neighbours frozen set {j != i : |r_i - r_j| < 2h}, quad-interleaved ELL rows; the
 //             search visits the 5^D cells around a particle clipped to its 2h sphere
 //             (rows whose slab lies at >= 2h are skipped, row runs cut to the
@@ -165,35 +166,37 @@ __global__ void k_scatter(int64_t n, const uint32_t* __restrict__ cell, const ui
   src[d] = (int)i;
 }
 
-// Insertion sort of each cell's slots by id (cells hold a few tens of particles).
-__global__ void k_cell_sort(int64_t n_cells, const uint32_t* __restrict__ start, int* __restrict__ key,
-                            int* __restrict__ src) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_cells) return;
-  uint32_t b = start[c], e = start[c + 1];
-  for (uint32_t k = b + 1; k < e; ++k) {
-    int kk = key[k], ss = src[k];
-    uint32_t m = k;
-    while (m > b && key[m - 1] > kk) {
-      key[m] = key[m - 1];
-      src[m] = src[m - 1];
-      --m;
-    }
-    key[m] = kk;
-    src[m] = ss;
-  }
+// Final slot of every particle: the counting sort left each cell's particles in arbitrary
+// order; a particle's place within its cell is the number of cell mates with a smaller id,
+// which makes the order the unique (cell, id) order. One thread per particle (cells hold
+// a few particles), instead of one per cell.
+__global__ void k_cell_rank(int64_t n, const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
+                            const int* __restrict__ key, const int* __restrict__ src, uint32_t* __restrict__ dst) {
+  int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const uint32_t c = cell[src[d]];
+  const uint32_t b = start[c], e = start[c + 1];
+  const int k = key[d];
+  uint32_t r = 0;
+  for (uint32_t m = b; m < e; ++m) r += key[m] < k ? 1u : 0u;
+  dst[d] = b + r;
 }
 
-__global__ void k_reorder(int64_t n, const int* __restrict__ src, const int4* __restrict__ Pin,
+// Records moved to their final slots (writes stay within each cell's slot range); the
+// ids in the new order go to id_out.
+__global__ void k_reorder(int64_t n, const int* __restrict__ src, const uint32_t* __restrict__ dst,
+                          const int* __restrict__ key, const int4* __restrict__ Pin,
                           const float4* __restrict__ Vin, int4* __restrict__ Pout,
                           float4* __restrict__ Vout, const float* __restrict__ min,
-                          float* __restrict__ mout) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int s = src[i];
-  Pout[i] = Pin[s];
-  Vout[i] = Vin[s];
-  if (min) mout[i] = min[s];
+                          float* __restrict__ mout, int* __restrict__ id_out) {
+  int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const int s = src[d];
+  const uint32_t t = dst[d];
+  Pout[t] = Pin[s];
+  Vout[t] = Vin[s];
+  id_out[t] = key[d];
+  if (min) mout[t] = min[s];
 }
 
 __global__ void k_copy_back(int64_t n, const int4* __restrict__ Pin, const float4* __restrict__ Vin,
@@ -316,7 +319,9 @@ struct RowWriter {
 // Candidate test: the squared distance in FP32 from exactly converted integer
 // differences (error < 3 ulp); only inside a +-2^-20 band around the threshold is
 // the exact integer test needed, so the decision is always the integer one.
-// Two candidates at once in the lanes of packed FP32 instructions.
+// Two candidates at once in the lanes of packed FP32 instructions. The exact test sits
+// behind a warp vote: a warp takes it only when one of its candidates falls in the band
+// (measured 0.1 ms faster per build at 8M than selecting between the two tests).
 template <int D, bool PER>
 __device__ __forceinline__ void within_fast2(const int4& p, const int4& a, const int4& b, const Inst& I,
                                              float lo, float hi, bool& in_a, bool& in_b) {
@@ -328,8 +333,13 @@ __device__ __forceinline__ void within_fast2(const int4& p, const int4& a, const
     const float2 dz = add2(make_float2(biased_diff<PER>(p.z, a.z, I.period[2]), biased_diff<PER>(p.z, b.z, I.period[2])), M);
     d2 = fma2(dz, dz, d2);
   }
-  in_a = d2.x < lo ? true : (d2.x >= hi ? false : within<D>(p, a, I));
-  in_b = d2.y < lo ? true : (d2.y >= hi ? false : within<D>(p, b, I));
+  in_a = d2.x < lo;
+  in_b = d2.y < lo;
+  const bool ea = !in_a && d2.x < hi, eb = !in_b && d2.y < hi;
+  if (__any_sync(__activemask(), ea || eb)) {
+    if (ea) in_a = within<D>(p, a, I);
+    if (eb) in_b = within<D>(p, b, I);
+  }
 }
 
 template <int D, bool PER>
@@ -376,14 +386,17 @@ k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst
 }
 
 // ---------------------------------------------------------------- walls ---------------
-__global__ void k_wall_reorder(int64_t n, const int* __restrict__ src, const int4* __restrict__ Pin,
+__global__ void k_wall_reorder(int64_t n, const int* __restrict__ src, const uint32_t* __restrict__ dst,
+                               const int* __restrict__ key, const int4* __restrict__ Pin,
                                const float4* __restrict__ Nin, int4* __restrict__ Pout,
-                               float4* __restrict__ Nout) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int s = src[i];
-  Pout[i] = Pin[s];
-  Nout[i] = Nin[s];
+                               float4* __restrict__ Nout, int* __restrict__ id_out) {
+  int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const int s = src[d];
+  const uint32_t t = dst[d];
+  Pout[t] = Pin[s];
+  Nout[t] = Nin[s];
+  id_out[t] = key[d];
 }
 
 __global__ void k_iota(int64_t n, int* __restrict__ a) {
@@ -444,9 +457,12 @@ void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches) {
   scan_exclusive(b.count, b.fstart, b.n_cells, b.scan_tmp, s, launches);
   if (b.n == 0) return;
   k_scatter<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.cell, b.rank, b.fstart, b.id, b.key, b.src);
-  k_cell_sort<<<grid_for(b.n_cells), kBlock, 0, s>>>(b.n_cells, b.fstart, b.key, b.src);
-  k_reorder<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.src, b.PS, b.VS, b.PH, b.VH, b.mass, b.mass_tmp);
-  k_copy_back<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PH, b.VH, b.key, b.PS, b.VS, b.id, b.mass_tmp,
+  // final slots into rank (free after the scatter); sorted ids into cell (free after the rank)
+  k_cell_rank<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.cell, b.fstart, b.key, b.src, b.rank);
+  int* ids_sorted = reinterpret_cast<int*>(b.cell);
+  k_reorder<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.src, b.rank, b.key, b.PS, b.VS, b.PH, b.VH, b.mass,
+                                             b.mass_tmp, ids_sorted);
+  k_copy_back<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PH, b.VH, ids_sorted, b.PS, b.VS, b.id, b.mass_tmp,
                                                b.mass);
   *launches += 4;
 }
@@ -478,11 +494,13 @@ void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStre
   if (b.nw == 0) return;
   k_iota<<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, wid_tmp);
   k_scatter<<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, b.cell, b.rank, b.wstart, wid_tmp, b.key, b.src);
-  k_cell_sort<<<grid_for(b.n_cells), kBlock, 0, s>>>(b.n_cells, b.wstart, b.key, b.src);
-  k_wall_reorder<<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, b.src, b.WP, b.WN, WP_tmp, WN_tmp);
+  k_cell_rank<<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, b.cell, b.wstart, b.key, b.src, b.rank);
+  int* wids_sorted = reinterpret_cast<int*>(b.cell);
+  k_wall_reorder<<<grid_for(b.nw), kBlock, 0, s>>>(b.nw, b.src, b.rank, b.key, b.WP, b.WN, WP_tmp, WN_tmp,
+                                                   wids_sorted);
   cudaMemcpyAsync(b.WP, WP_tmp, sizeof(int4) * b.nw, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(b.WN, WN_tmp, sizeof(float4) * b.nw, cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(b.wid, b.key, sizeof(int) * b.nw, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(b.wid, wids_sorted, sizeof(int) * b.nw, cudaMemcpyDeviceToDevice, s);
 }
 
 void launch_iota(int* a, int64_t n, cudaStream_t s) {
