@@ -17,8 +17,8 @@ constexpr int kSumFields = 8;   // fields 0..7 are sums, 8..9 maxima, 10 count
 
 int blocks_per_inst(const Buffers& b) {
   int64_t per = b.n_inst ? (b.n + b.n_inst - 1) / b.n_inst : 0;
-  int64_t want = (per + kDiagBlock * 8 - 1) / (kDiagBlock * 8);
-  if (b.n_inst == 1) want = (b.n + kDiagBlock * 8 - 1) / (kDiagBlock * 8);
+  int64_t want = (per + kDiagBlock * 2 - 1) / (kDiagBlock * 2);
+  if (b.n_inst == 1) want = (b.n + kDiagBlock * 2 - 1) / (kDiagBlock * 2);
   if (want < 1) want = 1;
   if (want > kMaxBlocksPerInst) want = kMaxBlocksPerInst;
   return (int)want;

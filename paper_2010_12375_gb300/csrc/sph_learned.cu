@@ -366,7 +366,9 @@ __global__ void k_segsum(int64_t n, const uint32_t* __restrict__ off, const floa
 // edge layers run on the tensor cores (mma.sync m16n8k16, k-steps in k_dense's order; the
 // first layer's accumulators become the second layer's A fragments after k_dense's ReLU
 // and bfloat16 rounding), and the messages are added per node in edge order as k_segsum
-// does. XN is therefore bit-identical to the unfused path's, and no per-edge row,
+// does. After its edges, the run's node rows go through the node network (both node
+// layers, the update added to h) into the other node-state buffer. XN and the new node
+// states are therefore bit-identical to the unfused path's, and no per-edge row,
 // activation or message goes to memory.
 constexpr int kFuseWarps = 8;
 constexpr int kFuseNodes = 8;
@@ -377,8 +379,10 @@ constexpr int kMsgLd = 72;                    // message row stride: conflict-fr
 
 static_assert(16 * kMsgLd <= kStageWords, "messages must fit the staging area");
 
+constexpr int kNodeLd = 152;                  // padded weight row of 144 bf16 (node layer 1)
+
 inline size_t fused_smem() {
-  return (size_t)2 * 64 * kFuseLd * sizeof(bf16) + (size_t)kFuseWarps * kStageWords * sizeof(float);
+  return (size_t)(3 * 64 * kFuseLd + 64 * kNodeLd) * sizeof(bf16) + (size_t)kFuseWarps * kStageWords * sizeof(float);
 }
 
 // column of slot q (0..19) of a lane with quad index t: k-step q / 4, position q % 4 in
@@ -389,10 +393,11 @@ __device__ __forceinline__ int fuse_col(int q, int t) { return (q >> 2) * 16 + 2
 // copy: lane i addresses row i % 8 of 8x8 matrix i / 8 (matrices: (nt, k0), (nt, k0 + 8),
 // (nt + 1, k0), (nt + 1, k0 + 8)), and receives row lane / 4, columns 2 (lane % 4), +1 of
 // each, which is the m16n8k16 B fragment.
+template <int LD = kFuseLd>
 __device__ __forceinline__ void ldsm_b4(const bf16* W, int nt, int k0, int lane, uint32_t& b0, uint32_t& b1,
                                         uint32_t& c0, uint32_t& c1) {
   const int m = lane >> 3;
-  const bf16* p = W + ((nt + (m >> 1)) * 8 + (lane & 7)) * kFuseLd + k0 + (m & 1) * 8;
+  const bf16* p = W + ((nt + (m >> 1)) * 8 + (lane & 7)) * LD + k0 + (m & 1) * 8;
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(b0), "=r"(b1), "=r"(c0), "=r"(c1)
@@ -409,21 +414,29 @@ __device__ __forceinline__ bf16 fuse_elem(const float* __restrict__ hrow, const 
 }
 
 template <int FE>
-__global__ void __launch_bounds__(kFuseWarps * 32)
+__global__ void __launch_bounds__(kFuseWarps * 32, 2)
 k_edge_round_fused(int64_t n, const uint32_t* __restrict__ off, const bf16* __restrict__ XS,
                    const int* __restrict__ enbr, const float* __restrict__ H, const bf16* __restrict__ W1,
-                   const bf16* __restrict__ W2, float inv_nbar, bf16* __restrict__ XN) {
+                   const bf16* __restrict__ W2, const bf16* __restrict__ Wn1, const bf16* __restrict__ Wn2,
+                   float inv_nbar, bf16* __restrict__ XN, float* __restrict__ Hout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   bf16* sW1 = reinterpret_cast<bf16*>(smem_raw);
   bf16* sW2 = sW1 + 64 * kFuseLd;
-  float* stage = reinterpret_cast<float*>(sW2 + 64 * kFuseLd) + warp * kStageWords;   // h rows
+  bf16* sN2 = sW2 + 64 * kFuseLd;             // node layer 2, rows of kFuseLd
+  bf16* sN1 = sN2 + 64 * kFuseLd;             // node layer 1, rows of kNodeLd
+  float* stage = reinterpret_cast<float*>(sN1 + 64 * kNodeLd) + warp * kStageWords;   // h rows
   bf16* xstage = reinterpret_cast<bf16*>(stage + 16 * kStageLd);                       // [16][16]
   float* sM = stage;                          // the messages reuse the staging rows (16 x kMsgLd)
   for (int idx = threadIdx.x; idx < 64 * 10; idx += blockDim.x) {
     const int r = idx / 10, c = (idx % 10) * 8;
     *reinterpret_cast<uint4*>(&sW1[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&W1[r * 80 + c]);
     *reinterpret_cast<uint4*>(&sW2[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&W2[r * 80 + c]);
+    *reinterpret_cast<uint4*>(&sN2[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&Wn2[r * 80 + c]);
+  }
+  for (int idx = threadIdx.x; idx < 64 * 18; idx += blockDim.x) {
+    const int r = idx / 18, c = (idx % 18) * 8;
+    *reinterpret_cast<uint4*>(&sN1[r * kNodeLd + c]) = *reinterpret_cast<const uint4*>(&Wn1[r * 144 + c]);
   }
   __syncthreads();
   const int64_t chunks = (n + kFuseNodes - 1) / kFuseNodes;
@@ -549,6 +562,68 @@ k_edge_round_fused(int64_t n, const uint32_t* __restrict__ off, const bf16* __re
       __syncwarp();                           // sM free for the next tile's staging
     }
     close_until(e_end);
+    // node network of the run's nodes (the rows of one MMA tile), as the unfused node layers
+    // compute it: z = relu(W_n1 XN), h_out = h + W_n2 [z, 1]
+    __syncwarp();                             // the run's XN rows, written above, visible
+    const int nrows = (int)(i1 - i0);
+    const bool vg = g < nrows, vh = g + 8 < nrows;
+    const bf16* xn = XN + (i0 + g) * 144;
+    const bf16* xh = xn + 8 * 144;
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 9; ++kk) {
+      const uint32_t a0 = vg ? ld_u32(xn + kk * 16 + 2 * t) : 0u;
+      const uint32_t a1 = vh ? ld_u32(xh + kk * 16 + 2 * t) : 0u;
+      const uint32_t a2 = vg ? ld_u32(xn + kk * 16 + 2 * t + 8) : 0u;
+      const uint32_t a3 = vh ? ld_u32(xh + kk * 16 + 2 * t + 8) : 0u;
+#pragma unroll
+      for (int nt = 0; nt < 8; nt += 2) {
+        uint32_t b0, b1, c0, c1;
+        ldsm_b4<kNodeLd>(sN1, nt, kk * 16, lane, b0, b1, c0, c1);
+        mma16816(acc[nt], a0, a1, a2, a3, b0, b1);
+        mma16816(acc[nt + 1], a0, a1, a2, a3, c0, c1);
+      }
+    }
+    float acc2[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) acc2[nt][0] = acc2[nt][1] = acc2[nt][2] = acc2[nt][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 5; ++kk) {
+      uint32_t a0, a1, a2, a3;
+      if (kk < 4) {
+        const float* lo = acc[2 * kk];
+        const float* hi = acc[2 * kk + 1];
+        a0 = pack2(__float2bfloat16_rn(fmaxf(lo[0], 0.f)), __float2bfloat16_rn(fmaxf(lo[1], 0.f)));
+        a1 = pack2(__float2bfloat16_rn(fmaxf(lo[2], 0.f)), __float2bfloat16_rn(fmaxf(lo[3], 0.f)));
+        a2 = pack2(__float2bfloat16_rn(fmaxf(hi[0], 0.f)), __float2bfloat16_rn(fmaxf(hi[1], 0.f)));
+        a3 = pack2(__float2bfloat16_rn(fmaxf(hi[2], 0.f)), __float2bfloat16_rn(fmaxf(hi[3], 0.f)));
+      } else {
+        a0 = a1 = t == 0 ? pack2(__float2bfloat16_rn(1.0f), __float2bfloat16_rn(0.f)) : 0u;
+        a2 = a3 = 0u;
+      }
+#pragma unroll
+      for (int nt = 0; nt < 8; nt += 2) {
+        uint32_t b0, b1, c0, c1;
+        ldsm_b4(sN2, nt, kk * 16, lane, b0, b1, c0, c1);
+        mma16816(acc2[nt], a0, a1, a2, a3, b0, b1);
+        mma16816(acc2[nt + 1], a0, a1, a2, a3, c0, c1);
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int64_t o = (i0 + g) * F + nt * 8 + 2 * t;
+      if (vg) {
+        const float2 h = *reinterpret_cast<const float2*>(&H[o]);
+        *reinterpret_cast<float2*>(&Hout[o]) = make_float2(h.x + acc2[nt][0], h.y + acc2[nt][1]);
+      }
+      if (vh) {
+        const float2 h = *reinterpret_cast<const float2*>(&H[o + 8 * F]);
+        *reinterpret_cast<float2*>(&Hout[o + 8 * F]) = make_float2(h.x + acc2[nt][2], h.y + acc2[nt][3]);
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -942,19 +1017,24 @@ void forward(sph_handle* h, sph_learned* L, cudaStream_t s, bool train) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFuseWarps * 32, fused_smem());
       const unsigned grid = (unsigned)std::min<int64_t>((chunks + kFuseWarps - 1) / kFuseWarps,
                                                         (int64_t)std::max(per_sm, 1) * sms);
+      // node states ping-pong between H and H0 (H0 is only kept for training's backward)
+      float* hin = (r & 1) ? L->H0 : L->H;
+      float* hout = (r & 1) ? L->H : L->H0;
       if (n > 0)
-        kern<<<grid, kFuseWarps * 32, fused_smem(), s>>>(n, L->off, L->XS, L->enbr, L->H, Wl(L, L_E1), Wl(L, L_E2),
-                                                         inv_nbar, L->XN[r]);
+        kern<<<grid, kFuseWarps * 32, fused_smem(), s>>>(n, L->off, L->XS, L->enbr, hin, Wl(L, L_E1), Wl(L, L_E2),
+                                                         Wl(L, L_N1), Wl(L, L_N2), inv_nbar, L->XN[r], hout);
     } else {
       if (E > 0) k_edge_rows<<<blocks_for(E * 10), 256, 0, s>>>(E, fe, L->XS, L->enbr, L->H, L->XE[r]);
       dense<64>(E, 80, L->XE[r], 80, Wl(L, L_E1), nullptr, 0, 0, 0, L->A1[r], 80, 0, F, 1, nullptr, 0, s);
       dense<64>(E, 80, L->A1[r], 80, Wl(L, L_E2), L->Mbuf, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
       k_segsum<<<blocks_for(n * F), 256, 0, s>>>(n, L->off, L->Mbuf, L->H, inv_nbar, L->XN[r]);
+      dense<64>(n, 144, L->XN[r], 144, Wl(L, L_N1), nullptr, 0, 0, 0, L->A2[r], 80, 0, F, 1, nullptr, 0, s);
+      dense<64>(n, 80, L->A2[r], 80, Wl(L, L_N2), L->H, F, F, 1, nullptr, 0, 0, 0, 0, nullptr, 0, s);
     }
-    dense<64>(n, 144, L->XN[r], 144, Wl(L, L_N1), nullptr, 0, 0, 0, L->A2[r], 80, 0, F, 1, nullptr, 0, s);
-    dense<64>(n, 80, L->A2[r], 80, Wl(L, L_N2), L->H, F, F, 1, nullptr, 0, 0, 0, 0, nullptr, 0, s);
   }
-  k_rows_bf16<<<blocks_for(n * F), 256, 0, s>>>(n, F, L->H, F, L->XD, 80);
+  // the fused rounds leave the final node states in H0 after an odd number of rounds
+  const float* hfin = (fused && (ROUNDS & 1)) ? L->H0 : L->H;
+  k_rows_bf16<<<blocks_for(n * F), 256, 0, s>>>(n, F, hfin, F, L->XD, 80);
   dense<64>(n, 80, L->XD, 80, Wl(L, L_D1), nullptr, 0, 0, 0, L->A3, 80, 0, F, 1, nullptr, 0, s);
   dense<16>(n, 80, L->A3, 80, Wl(L, L_D2), L->Y, 16, 16, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
 }
