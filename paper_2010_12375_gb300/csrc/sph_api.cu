@@ -306,6 +306,9 @@ int ensure_stage(sph_handle* h, size_t elems) {
   return SPH_OK;
 }
 
+constexpr int kUploadChunks = 8;              // host state upload: chunks (and events - 1)
+constexpr int64_t kUploadChunkMin = 1 << 18;  // particles below which one copy is enough
+
 // Bring caller arrays onto the device: device pointers are used as they are,
 // host arrays go through the staging buffer at offset `off`.
 const double* device_view(sph_handle* h, const double* p, size_t elems, size_t off, cudaStream_t s,
@@ -426,7 +429,10 @@ void sph_destroy(sph_handle* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->up_stream) cudaStreamDestroy(h->up_stream);
   for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->up_ev)
     if (e) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   if (h->hglob) cudaFreeHost(h->hglob);
@@ -624,7 +630,34 @@ int sph_set_state(sph_handle* h, const double* pos, const double* vel, const dou
   if (b.n > 0 && (!pos || !vel || !rho)) return fail(h, SPH_E_INVALID, "pos, vel and rho are required");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = (size_t)b.n, d = (size_t)b.dim;
-  if (b.n > 0) {
+  const bool host_all = b.n >= kUploadChunkMin && !is_device_ptr(pos) && !is_device_ptr(vel) &&
+                        !is_device_ptr(rho) && (!drho_dt || !is_device_ptr(drho_dt));
+  if (host_all) {
+    // host arrays: kUploadChunks row chunks, each imported while the next one is copied
+    if (!h->up_stream) {
+      CK(h, cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking));
+      for (auto& e : h->up_ev) CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    double* sp = h->stage;
+    double* sv = sp + n * d;
+    double* sr = sv + n * d;
+    double* sd = drho_dt ? sr + n : nullptr;
+    CK(h, cudaEventRecord(h->up_ev[kUploadChunks], s));   // after the caller's earlier work
+    CK(h, cudaStreamWaitEvent(h->up_stream, h->up_ev[kUploadChunks], 0));
+    for (int c = 0; c < kUploadChunks; ++c) {
+      const size_t r0 = n * c / kUploadChunks, r1 = n * (c + 1) / kUploadChunks;
+      if (r1 == r0) continue;
+      cudaStream_t u = h->up_stream;
+      CK(h, cudaMemcpyAsync(sp + r0 * d, pos + r0 * d, sizeof(double) * (r1 - r0) * d, cudaMemcpyHostToDevice, u));
+      CK(h, cudaMemcpyAsync(sv + r0 * d, vel + r0 * d, sizeof(double) * (r1 - r0) * d, cudaMemcpyHostToDevice, u));
+      CK(h, cudaMemcpyAsync(sr + r0, rho + r0, sizeof(double) * (r1 - r0), cudaMemcpyHostToDevice, u));
+      if (sd) CK(h, cudaMemcpyAsync(sd + r0, drho_dt + r0, sizeof(double) * (r1 - r0), cudaMemcpyHostToDevice, u));
+      CK(h, cudaEventRecord(h->up_ev[c], u));
+      CK(h, cudaStreamWaitEvent(s, h->up_ev[c], 0));
+      sph::launch_import(b, sp, sv, sr, sd, s, (int64_t)r0, (int64_t)r1);
+      ++h->launches;
+    }
+  } else if (b.n > 0) {
     cudaError_t e[4];
     const double* p = device_view(h, pos, n * d, 0, s, &e[0]);
     const double* v = device_view(h, vel, n * d, n * d, s, &e[1]);

@@ -31,6 +31,10 @@ struct sph_handle {
   // kernel timing
   bool timing = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  // chunked host upload of sph_set_state: copies on their own stream, the import of
+  // each chunk on the caller's stream as soon as the chunk has arrived
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_ev[9] = {nullptr};
   double ms[2] = {0.0, 0.0};
   int64_t timed[2] = {0, 0};
   bool cells_valid = false;

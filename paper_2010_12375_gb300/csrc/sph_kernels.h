@@ -65,8 +65,9 @@ void flag_near_wall_cells(const Buffers& b, uint8_t* tmp, cudaStream_t s);
 void launch_iota(int* a, int64_t n, cudaStream_t s);     // a[i] = i
 
 // import / export
+// rows [i0, i1) of the caller's arrays (i1 < 0: to the end)
 void launch_import(const Buffers& b, const double* pos, const double* vel, const double* rho,
-                   const double* drho, cudaStream_t s);
+                   const double* drho, cudaStream_t s, int64_t i0 = 0, int64_t i1 = -1);
 void launch_import_walls(const Buffers& b, const double* pos, const double* nrm, const double* vol,
                          cudaStream_t s);
 void launch_export(const Buffers& b, double* pos, double* vel, double* rho, double* drho,

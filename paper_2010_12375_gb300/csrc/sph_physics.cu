@@ -69,11 +69,11 @@ __device__ __forceinline__ bool block_one_instance(const int* inst_of, int64_t n
 
 // ---------------------------------------------------------------- import / export ----
 template <int D>
-__global__ void k_import(int64_t n, const double* __restrict__ pos, const double* __restrict__ vel,
+__global__ void k_import(int64_t i0, int64_t n, const double* __restrict__ pos, const double* __restrict__ vel,
                          const double* __restrict__ rho, const double* __restrict__ drho,
                          const int* __restrict__ inst_of, const Inst* __restrict__ inst,
                          int4* __restrict__ P, float4* __restrict__ V, Global* g) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // rows [i0, n)
   if (i >= n) return;
   const Inst& I = inst[inst_index(inst_of, i)];
   int q[3] = {0, 0, 0};
@@ -394,9 +394,10 @@ k_viscous(int64_t n, const int4* __restrict__ P, const float4* __restrict__ V,
   } while (0)
 
 void launch_import(const Buffers& b, const double* pos, const double* vel, const double* rho,
-                   const double* drho, cudaStream_t s) {
-  if (b.n == 0) return;
-  SPH_DIM_LAUNCH(b, k_import, grid_for(b.n), kBlock, s, b.n, pos, vel, rho, drho, b.inst_of, b.inst,
+                   const double* drho, cudaStream_t s, int64_t i0, int64_t i1) {
+  if (i1 < 0) i1 = b.n;
+  if (i1 <= i0) return;
+  SPH_DIM_LAUNCH(b, k_import, grid_for(i1 - i0), kBlock, s, i0, i1, pos, vel, rho, drho, b.inst_of, b.inst,
                  b.PS, b.VS, b.glob);
 }
 
