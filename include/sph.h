@@ -188,7 +188,10 @@ int sph_get_state(sph_handle* h, double* pos, double* vel, double* rho, double* 
 
 /* Replace the state (id order, same sizes as sph_create; drho_dt may be NULL = 0)
  * and, if t >= 0, instance 0's simulated time. Call sph_build_cells before
- * the next advection step (sph_step does). */
+ * the next advection step (sph_step does). Host arrays of 262,144 particles or more are
+ * copied in row chunks on a stream the handle owns, ordered after the work already on
+ * `stream`, while `stream` converts each chunk that has arrived. Synchronous: the
+ * caller's arrays may be reused when it returns. */
 int sph_set_state(sph_handle* h, const double* pos, const double* vel, const double* rho,
                   const double* drho_dt, double t, void* stream);
 
