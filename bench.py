@@ -165,8 +165,9 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"3D dam break, bounded CPU sample (dp = 1/{CPU_SAMPLE_N})",
-                   "n_fluid": 2 * CPU_SAMPLE_N ** 3},
+        # the GPU arm's workload; each step times a bounded sample of it (cpu_baseline.sample)
+        "config": {"workload": f"3D dam break, fluid 2x1x1 in a 5.366x5.366x1 tank, dp = 1/{args.n}",
+                   "sample": f"dp = 1/{CPU_SAMPLE_N}, {2 * CPU_SAMPLE_N ** 3} fluid particles per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": cpu_sample_text(args.steps)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
