@@ -319,8 +319,10 @@ k_density(int64_t n, int4* P, const int* __restrict__ inst_of, const Inst* __res
   kahan2(s, nc, make_float2(I.sig_lo, 0.0f), f2(1.0f));
   const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
   const int nq = (nf + 3) >> 2;
+  int4 nxt = nq ? nb4[i] : make_int4(0, 0, 0, 0);
   for (int q = 0; q < nq; ++q) {
-    const int4 cq = nb4[(int64_t)q * n + i];
+    const int4 cq = nxt;
+    if (q + 1 < nq) nxt = nb4[(int64_t)(q + 1) * n + i];   // next quad in flight
     const int sl = q << 2;
     const int j1 = sl + 1 < nf ? cq.y : cq.x, j2 = sl + 2 < nf ? cq.z : cq.x, j3 = sl + 3 < nf ? cq.w : cq.x;
     const int4 a0 = P[cq.x], a1 = P[j1], a2 = P[j2], a3 = P[j3];
