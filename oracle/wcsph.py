@@ -40,6 +40,13 @@ Readings where the paper is silent or inconsistent (the same readings the CUDA p
   R8  Viscous acceleration is fluid-fluid only, with eta = rho0 nu, evaluated once per
       advection step after density re-initialisation and held over its substeps.
   R9  In the second half step the position update uses v^{n+1}.
+  R12 Transport velocity (Eq. transport, flows without free surface), off when p0 = 0: the
+      background-pressure acceleration a_i = -2 sum_j m_j p0/(rho_i rho_j) grad_i W_ij over
+      fluid pairs, with the mid-point geometry and densities of the pressure relaxation, acts
+      on the transport velocity only; the transport velocity starts each substep equal to v,
+      so over the substep it moves the particle by dt^2/2 a_i in addition to v, applied to
+      the mid-point position. p0 is not given in the paper: 2 rho0 c0^2 for the Taylor-Green
+      vortex (the largest value that stayed stable in a sweep at 40^2).
 
 Parity pins: every function here is pinned by the tests in tests/test_oracle_pins.py
 (closed forms, invariants, brute force). None is unpinned.
@@ -111,6 +118,7 @@ class Params:
     periodic: np.ndarray
     free_surface: bool
     sigma0: float = 0.0
+    p_transport: float = 0.0   # R12: background pressure p0 of Eq. transport (0 = off)
 
     @staticmethod
     def from_problem(p) -> "Params":
@@ -122,7 +130,8 @@ class Params:
                      lo=np.asarray(p.lo, dtype=np.float64)[:d].copy(),
                      hi=np.asarray(p.hi, dtype=np.float64)[:d].copy(),
                      periodic=np.asarray(p.periodic)[:d].astype(bool),
-                     free_surface=bool(p.free_surface))
+                     free_surface=bool(p.free_surface),
+                     p_transport=float(getattr(p, "p_transport", 0.0)))
         prm.sigma0 = lattice_sigma0(prm.dp, prm.h, d)
         return prm
 
@@ -426,6 +435,8 @@ def pressure_relaxation(st: State, w: Walls, nb, acc_prior, dt: float, prm: Para
     Eq. verlet-first-mediate: v to the new step. Returns (state, dv/dt).
     With `geometry` (from frozen_geometry) the pair vectors are those of the
     configuration update instead of the mid-point positions (reading R11).
+    With a background pressure p0 > 0 (Eq. transport, reading R12) the mid-point
+    position also takes the transport shift dt^2/2 a_i.
     """
     I, J, IW, KW = nb
     N = st.x.shape[0]
@@ -434,6 +445,7 @@ def pressure_relaxation(st: State, w: Walls, nb, acc_prior, dt: float, prm: Para
     x = st.x + 0.5 * dt * st.v
     p = eos_pressure(rho, prm)
     acc = np.zeros((N, prm.dim))
+    shift = 0.0
     if I.size:
         rij, r, e = _geometry(x[I], x[J], prm) if geometry is None else _from_rij(geometry[0])
         dW = kernel_dW(r, prm.h, prm.dim)
@@ -443,6 +455,10 @@ def pressure_relaxation(st: State, w: Walls, nb, acc_prior, dt: float, prm: Para
         grad = (-e) * dW[:, None]                    # grad_i W_ij = dW/dr r_ij/|r_ij|  (R2)
         Vj = st.m[J] / rho[J]
         acc += _scatter_add(I, (-2.0 * Vj * Ps / rho[I])[:, None] * grad, N)
+        if prm.p_transport > 0.0:
+            # Eq. transport: -2 sum_j m_j p0 / (rho_i rho_j) grad_i W_ij (R12)
+            a_tv = _scatter_add(I, (-2.0 * prm.p_transport * Vj / rho[I])[:, None] * grad, N)
+            shift = 0.5 * dt * dt * a_tv
     if IW.size:
         if geometry is None:
             rfw, r, e = _geometry(x[IW], w.x[KW], prm)
@@ -459,7 +475,7 @@ def pressure_relaxation(st: State, w: Walls, nb, acc_prior, dt: float, prm: Para
         acc += _scatter_add(IW, (-2.0 * w.V[KW] * Ps / rho[IW])[:, None] * grad, N)
     dvdt = acc_prior + g[None, :] + acc
     v = st.v + dt * dvdt
-    out = State(x, v, rho, st.drho.copy(), st.m, st.t)
+    out = State(x + shift, v, rho, st.drho.copy(), st.m, st.t)
     return out, dvdt
 
 

@@ -53,6 +53,7 @@ class Workload:
     wall_vol: np.ndarray         # (Nw,)
     t_end: float = 0.0
     meta: dict = field(default_factory=dict)
+    p_transport: float = 0.0     # background pressure p0 of the transport velocity (0 = off)
 
     @property
     def n_fluid(self) -> int:
@@ -200,11 +201,12 @@ def still_tank(dim=2, H=0.5, width=None, height=None, dp=0.025, g=1.0, rho0=1.0)
     )
 
 
-def taylor_green(n=100, nu=0.01, c0=10.0, rho0=1.0):
+def taylor_green(n=100, nu=0.01, c0=10.0, rho0=1.0, transport=True):
     """2D periodic Taylor-Green vortex on the unit square, n x n lattice, Re = 1/nu.
 
     u = -cos(2 pi x) sin(2 pi y), v = sin(2 pi x) cos(2 pi y), rho = rho0, no gravity,
-    no walls; kinetic energy decays as exp(-16 pi^2 nu t).
+    no walls; kinetic energy decays as exp(-16 pi^2 nu t). A flow without free surface:
+    with `transport` the transport velocity is on with background pressure 2 rho0 c0^2.
     """
     dp = 1.0 / n
     pos = _lattice(np.zeros(2), [n, n], dp)
@@ -223,6 +225,7 @@ def taylor_green(n=100, nu=0.01, c0=10.0, rho0=1.0):
         periodic=per, free_surface=0, pos=pos, vel=vel, rho=np.full(N, rho0),
         mass=np.full(N, rho0 * dp * dp), wall_pos=np.zeros((0, 2)), wall_normal=np.zeros((0, 2)),
         wall_vol=np.zeros(0), t_end=1.0, meta={"U": 1.0, "L": 1.0},
+        p_transport=2.0 * rho0 * c0 ** 2 if transport else 0.0,
     )
 
 

@@ -24,7 +24,7 @@ def _case(case):
     if case == "dam2d":
         prob, vel_amp, rho_amp = wk.dam_break_2d(), 0.3, 0.01
     elif case == "tg":
-        prob, vel_amp, rho_amp = wk.taylor_green(64), 0.05, 0.005
+        prob, vel_amp, rho_amp = wk.taylor_green(64, transport=False), 0.05, 0.005
     elif case == "dam3d":
         prob, vel_amp, rho_amp = wk.dam_break_3d(16), 0.3, 0.01
     else:

@@ -407,6 +407,86 @@ def test_taylor_green_decay_converges_to_closed_form():
     assert errs[1] < errs[0] < 0.06
 
 
+# ------------------------------------------------------------------ transport velocity (R12)
+def _transport_shift(prob, x, v, dt_frac=0.5):
+    """Mid-point shift of one pressure relaxation from the transport velocity alone."""
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    st.x, st.v = x.copy(), v.copy()
+    nb = o.neighbour_sets(st.x, w.x, prm)
+    dt = dt_frac * o.dt_acoustic(st.v, prm)
+    acc0 = np.zeros_like(x)
+    on, _ = o.pressure_relaxation(st, w, nb, acc0, dt, prm)
+    prm_off = o.Params.from_problem(prob)
+    prm_off.p_transport = 0.0
+    off, _ = o.pressure_relaxation(st, w, nb, acc0, dt, prm_off)
+    return on.x - off.x, st.m, prm
+
+
+def test_transport_shift_vanishes_on_a_lattice():
+    # at rest on the lattice sum_j V_j grad W_ij = 0 by symmetry: no transport shift
+    tg = wk.taylor_green(20)
+    shift, _, prm = _transport_shift(tg, tg.pos, np.zeros_like(tg.pos))
+    assert prm.p_transport == 2.0 * prm.rho0 * prm.c0 ** 2
+    assert np.abs(shift).max() < 1e-12 * prm.dp
+
+
+def test_transport_shift_restores_a_displaced_particle():
+    # one particle pushed towards its +x neighbour is moved back (-x): the background
+    # pressure term repels crowded particles (a sign flip would pull them together)
+    tg = wk.taylor_green(20)
+    x = tg.pos.copy()
+    k = 210
+    x[k, 0] += 0.25 * tg.dp
+    shift, _, prm = _transport_shift(tg, x, np.zeros_like(x))
+    assert shift[k, 0] < -1e-6 * prm.dp
+    assert abs(shift[k, 1]) < 1e-9 * prm.dp          # the displacement is along x only
+
+
+def test_transport_shift_keeps_the_centre_of_mass():
+    # pair antisymmetry of -2 m_i m_j p0/(rho_i rho_j) grad_i W_ij: sum m_i shift_i = 0
+    tg = wk.taylor_green(24)
+    rng = np.random.default_rng(3)
+    x = np.mod(tg.pos + rng.uniform(-0.3, 0.3, tg.pos.shape) * tg.dp, 1.0)
+    shift, m, prm = _transport_shift(tg, x, tg.vel)
+    total = np.abs(np.sum(m[:, None] * shift, axis=0)).max()
+    assert np.abs(shift).max() > 1e-6 * prm.dp
+    assert total < 1e-12 * np.sum(m[:, None] * np.abs(shift))
+
+
+@pytest.mark.slow
+def test_taylor_green_with_transport_velocity_converges_to_closed_form():
+    # Eq. transport keeps the vortex regular: the kinetic-energy error against
+    # exp(-16 pi^2 nu t) up to t = 0.5 falls with resolution; without it the vortex
+    # breaks up (tensile instability) and loses most of its energy by t = 0.5
+    errs = []
+    for n in (24, 32, 40):
+        _, series = o.run(wk.taylor_green(n), t_end=0.5)
+        ke = np.array([s["kinetic"] for s in series])
+        t = np.array([s["t"] for s in series])
+        errs.append(np.max(np.abs(ke / ke[0] - np.exp(-16 * np.pi ** 2 * 0.01 * t))))
+    assert errs[2] < errs[1] < errs[0] < 0.16 and errs[2] < 0.1, errs
+    _, series = o.run(wk.taylor_green(32, transport=False), t_end=0.5)
+    ke = np.array([s["kinetic"] for s in series])
+    assert ke[-1] / ke[0] < 0.5 * np.exp(-16 * np.pi ** 2 * 0.01 * series[-1]["t"])
+
+
+def test_planted_transport_sign_flip_is_caught(monkeypatch):
+    orig = o.pressure_relaxation
+
+    def flipped(st, w, nb, acc_prior, dt, prm, geometry=None):
+        on, a = orig(st, w, nb, acc_prior, dt, prm, geometry)
+        p0 = prm.p_transport
+        prm.p_transport = 0.0
+        off, _ = orig(st, w, nb, acc_prior, dt, prm, geometry)
+        prm.p_transport = p0
+        on.x = off.x - (on.x - off.x)
+        return on, a
+    monkeypatch.setattr(o, "pressure_relaxation", flipped)
+    with pytest.raises(AssertionError):
+        test_transport_shift_restores_a_displaced_particle()
+
+
 @pytest.mark.slow
 def test_dam_break_front_and_density_variation():
     prob = wk.dam_break_2d(n_per_H=20)
