@@ -39,8 +39,8 @@ UNIT = "particle-substeps/s"
 # profiles/pressure_relaxation_dam_break_3d.md; it is scaled to the benchmark's particle
 # count (the traffic is per particle: state records plus its neighbour row). Valid only
 # for the kernel sources whose hash is recorded with it.
-TRAFFIC_BYTES_PER_PARTICLE = 391.25
-TRAFFIC_SOURCE_HASH = "c691de2bc1df65bd"
+TRAFFIC_BYTES_PER_PARTICLE = 390.07
+TRAFFIC_SOURCE_HASH = "895398bd41154fbc"
 
 
 def kernel_source_hash():

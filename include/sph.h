@@ -90,6 +90,11 @@ typedef struct {
   int32_t  periodic[3];   /* 1 = periodic axis with period hi - lo (>= 3 cells)             */
   int32_t  capacity;      /* max neighbours (fluid + wall) per particle; 0 = 48 (2D) / 128 (3D) */
   uint32_t flags;         /* SPH_FLAG_* (taken from the first instance)                    */
+  double   p_transport;   /* background pressure p0 of the transport velocity (Eq. transport,
+                             flows without free surface); 0 = off. On: each pressure
+                             relaxation also moves the mid-point position by dt^2/2 a_i,
+                             a_i = -2 sum_j m_j p0 / (rho_i rho_j) grad_i W_ij over fluid
+                             pairs at the mid-point; not with SPH_FLAG_FROZEN_GEOMETRY */
 } sph_params;
 
 /* FP64 conservation and bulk diagnostics of one tank. */

@@ -120,6 +120,9 @@ int check_params(const sph_params* p, std::string* why) {
   if (p->u_ref == 0.0 && !(p->nu > 0.0)) return bad("u_ref = 0 needs nu > 0 to bound Dt_ad");
   if (p->capacity < 0 || p->capacity > 65535) return bad("capacity must be in [0, 65535]");
   if (p->free_surface != 0 && p->free_surface != 1) return bad("free_surface must be 0 or 1");
+  if (!(std::isfinite(p->p_transport) && p->p_transport >= 0.0)) return bad("p_transport must be >= 0");
+  if (p->p_transport > 0.0 && (p->flags & SPH_FLAG_FROZEN_GEOMETRY))
+    return bad("the transport velocity needs the recomputed pair geometry (no SPH_FLAG_FROZEN_GEOMETRY)");
   double period = 0.0;
   for (int a = 0; a < p->dim; ++a) {
     if (!std::isfinite(p->gravity[a])) return bad("gravity must be finite");
@@ -184,6 +187,7 @@ Inst make_inst(const sph_params& p) {
   for (int a = 0; a < 3; ++a) I.g[a] = a < d ? (float)p.gravity[a] : 0.0f;
   I.eta = (float)(p.rho0 * p.nu);
   I.mass = 0.0f;
+  I.p_tv = (float)p.p_transport;
   for (int a = 0; a < 3; ++a) {
     I.ncell[a] = ncell[a];
     I.scell[a] = a < d ? 2 * ncell[a] : 1;
@@ -496,6 +500,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
     if (params[k].nu > 0.0) any_visc = true;
     for (int a = 0; a < dim; ++a)
       if (params[k].periodic[a]) b.any_periodic = true;
+    if (params[k].p_transport > 0.0) b.any_transport = true;
     h->hinst.push_back(I);
   }
   if (n_cells >= (1ll << 32) - 1) return fail(h, SPH_E_INVALID, "too many cells");

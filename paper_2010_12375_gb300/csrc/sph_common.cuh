@@ -41,6 +41,7 @@ struct Inst {
   float g[3];
   float eta;                     // rho0 * nu
   float mass;                    // uniform particle mass
+  float p_tv;                    // background pressure p0 of the transport velocity (0 = off)
   int   ncell[3];                // cells per axis (position frame: q >> bits)
   int   scell[3];                // search cells per axis, 2 ncell (1 on an unused axis)
   int   period[3];               // period in quanta on periodic axes, else 0

@@ -20,6 +20,7 @@ struct Buffers {
   int64_t n = 0, nw = 0, n_cells = 0;
   int n_inst = 1, dim = 2, cap = 0;
   bool any_periodic = false;      // some tank has a periodic axis
+  bool any_transport = false;     // some tank has the transport velocity on
   Inst* inst = nullptr;           // [n_inst]
   Inst inst0{};                   // host copy of instance 0 (kernel argument when n_inst == 1)
   Ctrl* ctrl = nullptr;           // [n_inst]

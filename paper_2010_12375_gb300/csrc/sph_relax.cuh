@@ -136,12 +136,13 @@ struct PrCtx {
   float hdt, dev_i, rho_i, pr_i;
   int px, py, pz;
   float2 sx, sy, sz, nx, ny, nz;      // Kahan sums (per lane) and negated compensations
+  float2 bx, by, bz;                  // transport velocity: sum V_j (dW/dr)/r r_ij (plain sums)
 };
 
 // Two fluid pairs (a, b) of the pressure relaxation: V_j P* (dW/dr)/r r_ij accumulated.
 // FG: the pair vectors and (dW/dr)/r come from the frozen table (ga, gb), else from the
 // mid-point positions.
-template <int D, bool PER, bool FG = false>
+template <int D, bool PER, bool FG = false, bool TV = false>
 __device__ __forceinline__ void pr_fluid2(const Inst& I, PrCtx& C, const int4& pi, const float4& vi, const int4& pa,
                                           const int4& pb, const float4& va, const float4& vb, float2 mj,
                                           float2 DQ, float4 ga = float4(), float4 gb = float4()) {
@@ -175,6 +176,12 @@ __device__ __forceinline__ void pr_fluid2(const Inst& I, PrCtx& C, const int4& p
   kahan2(C.sx, C.nx, f, rx);
   kahan2(C.sy, C.ny, f, ry);
   if (D == 3) kahan2(C.sz, C.nz, f, rz);
+  if (TV) {                                          // Eq. transport: V_j grad_i W_ij
+    const float2 b = mul2(mul2(mj, rcp2(rho_j)), G.fw);
+    C.bx = fma2(b, rx, C.bx);
+    C.by = fma2(b, ry, C.by);
+    if (D == 3) C.bz = fma2(b, rz, C.bz);
+  }
 }
 
 // Two wall pairs of the pressure relaxation (one-sided problem along the wall normal).
@@ -217,7 +224,10 @@ __device__ __forceinline__ void pr_wall2(const Inst& I, PrCtx& C, const int4& pi
 // and the lanes' compensated sums are combined in a fixed order. TPP = 1 is one thread per
 // particle; 2 and 4 trade per-thread work for more threads in flight.
 // FG: pair geometry from the frozen table geo ([slot][n]) instead of the positions.
-template <int D, bool PER, int TPP, int BLK, bool UNI, bool FG>
+// TV: transport velocity (Eq. transport): the mid-point position written for the density
+// relaxation also takes dt^2/2 a_i, a_i = -(2 p0 / rho_i) sum_j V_j grad_i W_ij over the
+// fluid pairs (one thread per particle only).
+template <int D, bool PER, int TPP, int BLK, bool UNI, bool FG, bool TV = false>
 __global__ void __launch_bounds__(BLK, pr_min_blocks(BLK))
 k_pressure_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, const int4* __restrict__ PS,
                       const float4* __restrict__ VS,
@@ -236,8 +246,10 @@ k_pressure_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, 
   const double dtd = ctrl[k].dt;
   if (dtd == 0.0) valid = false;                 // tank idle for this substep
   float v2 = 0.0f;
+  static_assert(!TV || (TPP == 1 && !FG), "transport velocity: one thread per particle, recomputed geometry");
   PrCtx C;
   C.sx = C.sy = C.sz = C.nx = C.ny = C.nz = f2(0.f);
+  C.bx = C.by = C.bz = f2(0.f);
   const Inst& I = UNI ? Ip : inst[k];        // one tank: constants straight from the argument
   const float dt = (float)dtd;
   int4 pi = make_int4(0, 0, 0, 0);
@@ -291,8 +303,8 @@ k_pressure_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, 
         m01 = make_float2(mass[j0], mass[j1]);
         m23 = make_float2(mass[j2], mass[j3]);
       }
-      pr_fluid2<D, PER, FG>(I, C, pi, vi, p0, p1, v0, v1, m01, DQ, g0, g1);
-      pr_fluid2<D, PER, FG>(I, C, pi, vi, p2, p3, v2v, v3, m23, DQ, g2, g3);
+      pr_fluid2<D, PER, FG, TV>(I, C, pi, vi, p0, p1, v0, v1, m01, DQ, g0, g1);
+      pr_fluid2<D, PER, FG, TV>(I, C, pi, vi, p2, p3, v2v, v3, m23, DQ, g2, g3);
       cur = nxt;
     }
     if (nw) {
@@ -337,9 +349,16 @@ k_pressure_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, 
     const float a2 = D == 3 ? ap.z + I.g[2] + sc * az : 0.f;
     const float4 vn = make_float4(vi.x + dt * a0, vi.y + dt * a1, vi.z + dt * a2, vi.w);  // verlet-first-mediate
     const float hdt = C.hdt;
-    int qx = pi.x + __float2int_rn(hdt * vi.x * I.inv_dq);                              // verlet-first-half
-    int qy = pi.y + __float2int_rn(hdt * vi.y * I.inv_dq);
-    int qz = D == 3 ? pi.z + __float2int_rn(hdt * vi.z * I.inv_dq) : 0;
+    float ux = vi.x, uy = vi.y, uz = vi.z;                   // dt/2 times this moves r to n+1/2
+    if (TV) {                                                // + dt^2/2 a_i: dt/2 (v + dt a_i)
+      const float tv = -2.0f * I.p_tv / C.rho_i * dt;
+      ux += tv * (C.bx.x + C.bx.y);
+      uy += tv * (C.by.x + C.by.y);
+      uz += tv * (C.bz.x + C.bz.y);
+    }
+    int qx = pi.x + __float2int_rn(hdt * ux * I.inv_dq);                                // verlet-first-half
+    int qy = pi.y + __float2int_rn(hdt * uy * I.inv_dq);
+    int qz = D == 3 ? pi.z + __float2int_rn(hdt * uz * I.inv_dq) : 0;
     if (PER) {
       qx = wrap_coord(qx, C.px);
       qy = wrap_coord(qy, C.py);
@@ -552,6 +571,17 @@ void launch_pr(int tpp, int block, const Buffers& b, cudaStream_t s) {
     const unsigned g1 = grid_for(b.n, 128);
     if (b.n_inst == 1) k_pressure_relaxation<D, PER, 1, 128, true, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_PR_ARGS);
     else k_pressure_relaxation<D, PER, 1, 128, false, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_PR_ARGS);
+    return;
+  }
+  if (b.any_transport) {     // transport velocity: one thread per particle, the configured block
+    const unsigned g1 = grid_for(b.n, block);
+#define SPH_PR_TV(B) (b.n_inst == 1                                                                \
+      ? k_pressure_relaxation<D, PER, 1, B, true, false, true><<<g1, B, 0, s>>>(b.inst0, nullptr, SPH_PR_ARGS) \
+      : k_pressure_relaxation<D, PER, 1, B, false, false, true><<<g1, B, 0, s>>>(b.inst0, nullptr, SPH_PR_ARGS))
+    if (block == 512) SPH_PR_TV(512);
+    else if (block == 256) SPH_PR_TV(256);
+    else SPH_PR_TV(128);
+#undef SPH_PR_TV
     return;
   }
 #define SPH_PR_T(T) (block == 512 ? SPH_PR(T, 512) : block == 256 ? SPH_PR(T, 256) : SPH_PR(T, 128))

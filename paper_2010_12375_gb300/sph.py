@@ -50,6 +50,7 @@ class SphParams(ctypes.Structure):
         ("u_ref", ctypes.c_double), ("nu", ctypes.c_double),
         ("gravity", ctypes.c_double * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
         ("periodic", ctypes.c_int32 * 3), ("capacity", ctypes.c_int32), ("flags", ctypes.c_uint32),
+        ("p_transport", ctypes.c_double),
     ]
 
 
@@ -190,6 +191,7 @@ def params_from(problem, flags=0, capacity=0) -> SphParams:
         p.hi[a] = float(problem.hi[a])
         p.periodic[a] = int(problem.periodic[a])
     p.capacity = int(capacity)
+    p.p_transport = float(getattr(problem, "p_transport", 0.0))
     p.flags = int(flags)
     return p
 

@@ -344,7 +344,8 @@ def test_dam_break_2d_trajectory_energy_and_front(sph):
 
 
 def test_taylor_green_kinetic_energy(sph):
-    prob = wk.taylor_green(64)
+    # without the transport velocity (the lattice still regular up to t = 0.1)
+    prob = wk.taylor_green(64, transport=False)
     sim = sph.Simulation(prob, flags=sph.SPH_FLAG_GRAPH)
     ts, kes = [], []
     d = sim.diagnostics()
@@ -361,6 +362,44 @@ def test_taylor_green_kinetic_energy(sph):
     assert np.max(np.abs(kes - _interp(np.array(ts), ot, ok))) / ok[0] < 5e-3
     exact = np.exp(-16 * np.pi ** 2 * 0.01 * np.array(ts))
     assert np.max(np.abs(kes / kes[0] - exact)) < 0.06
+
+
+def _tg_kinetic(sph, n, t_end, transport=True):
+    sim = sph.Simulation(wk.taylor_green(n, transport=transport), flags=sph.SPH_FLAG_GRAPH)
+    ts, kes = [], []
+    d = sim.diagnostics()
+    while d["t"] < t_end:
+        ts.append(d["t"]); kes.append(d["kinetic"])
+        sim.step(1)
+        d = sim.diagnostics()
+    ts.append(d["t"]); kes.append(d["kinetic"])
+    sim.close()
+    return np.array(ts), np.array(kes)
+
+
+def test_taylor_green_with_transport_velocity_follows_the_oracle(sph):
+    # the GPU path's transport shift against the oracle's reading R12 over a trajectory
+    ts, kes = _tg_kinetic(sph, 32, 0.3)
+    _, series = o.run(wk.taylor_green(32), t_end=0.3)
+    ot = np.array([s["t"] for s in series])
+    ok = np.array([s["kinetic"] for s in series])
+    err = np.max(np.abs(kes - _interp(ts, ot, ok))) / ok[0]
+    print(f"TG 32^2 with transport velocity, GPU vs oracle to t = 0.3: {err:.2e} of KE(0)")
+    assert err < 5e-3
+
+
+def test_taylor_green_decay_to_t1_converges_with_resolution(sph):
+    # Eq. transport on (background pressure 2 rho0 c0^2): |KE/KE0 - exp(-16 pi^2 nu t)| up
+    # to t = 1 falls from 100^2 to 200^2 to 400^2; without it the vortex breaks up
+    errs = []
+    for n in (100, 200, 400):
+        ts, kes = _tg_kinetic(sph, n, 1.0)
+        assert ts[-1] >= 1.0
+        errs.append(np.max(np.abs(kes / kes[0] - np.exp(-16 * np.pi ** 2 * 0.01 * ts))))
+    print("TG max |KE error| to t = 1 at 100^2, 200^2, 400^2:", ["%.4f" % e for e in errs])
+    assert errs[2] < errs[1] < errs[0] < 0.03 and errs[2] < 0.01, errs
+    ts, kes = _tg_kinetic(sph, 100, 1.0, transport=False)
+    assert np.max(np.abs(kes / kes[0] - np.exp(-16 * np.pi ** 2 * 0.01 * ts))) > 0.2
 
 
 # ------------------------------------------------------------------ edge cases and errors
