@@ -67,6 +67,15 @@ def test_params_check_on_host(lib):
     p = lib.params_from(wk.dam_break_2d())
     p.u_ref = 0.0                                          # Dt_ad unbounded at rest
     assert lib.sph_params_check(p) == lib.SPH_E_INVALID
+    tg = wk.taylor_green(50)
+    assert tg.p_transport > 0.0
+    p = lib.params_from(tg)
+    p.p_transport = -1.0                                   # background pressure below zero
+    assert lib.sph_params_check(p) == lib.SPH_E_INVALID
+    p = lib.params_from(tg, flags=lib.SPH_FLAG_FROZEN_GEOMETRY)
+    assert lib.sph_params_check(p) == lib.SPH_E_INVALID    # transport needs recomputed geometry
+    p = lib.params_from(wk.taylor_green(50, transport=False), flags=lib.SPH_FLAG_FROZEN_GEOMETRY)
+    assert lib.sph_params_check(p) == lib.SPH_OK
 
 
 def test_create_without_gpu_fails_cleanly(lib):
