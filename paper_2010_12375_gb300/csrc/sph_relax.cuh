@@ -26,7 +26,9 @@
 // variants, each with its own register budget); UNI, a single-tank handle whose constant
 // record arrives as the kernel argument; FG, the frozen-geometry reading, where each
 // pair's vector r_i - r_j and (dW/dr)/r come from the table written at the configuration
-// update instead of from the current positions.
+// update instead of from the current positions; TV (pressure relaxation only), the
+// transport velocity of Eq. transport, whose background-pressure term moves the mid-point
+// position by dt^2/2 a_i.
 #pragma once
 
 #include "sph_kernels.h"
