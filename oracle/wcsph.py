@@ -312,23 +312,17 @@ def neighbour_sets_quantised(x: np.ndarray, xw: np.ndarray, prm: Params):
     return I, J, IW, KW
 
 
-def search_shift(bits: int, axis: int) -> int:
-    """Search cells (reading R10): the 2h position cell halved along x (index q >> (bits - 1),
-    about h) and quartered along the other axes (q >> (bits - 2), about h/2)."""
-    return bits - 1 if axis == 0 else bits - 2
-
-
 def cell_permutation(x: np.ndarray, ids: np.ndarray, prm: Params) -> np.ndarray:
-    """Particle ids in (search cell, id) order, search cells flattened with x fastest; the
-    order is the one the cell-linked list of Sec. 6.2 is stored in (reading R10)."""
+    """Particle ids in (search cell, id) order. Search cells halve the position cell on
+    every axis (cell index q >> (bits - 1), about h wide) and are flattened with x fastest;
+    the order is the one the cell-linked list of Sec. 6.2 is stored in (reading R10)."""
     cell, ncell, bits, dq, _ = quantisation(prm)
-    q = quantise(x, prm)
+    c = quantise(x, prm) >> (bits - 1)
     flat = np.zeros(x.shape[0], dtype=np.int64)
     stride = 1
     for a in range(prm.dim):
-        sh = search_shift(bits, a)
-        flat += (q[:, a] >> sh) * stride
-        stride *= ncell[a] << (bits - sh)
+        flat += c[:, a] * stride
+        stride *= 2 * ncell[a]
     order = np.lexsort((ids, flat))
     return ids[order]
 

