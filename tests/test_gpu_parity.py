@@ -310,6 +310,25 @@ def test_batched_instances_match_single_runs(sph):
     multi.close()
 
 
+def test_batched_transport_velocity_tanks_match_single_runs(sph):
+    # the transport-velocity kernel with the tank constants read per particle
+    tanks = [wk.taylor_green(32), wk.taylor_green(40)]
+    multi = sph.Simulation(tanks)
+    multi.step(3)
+    pos_m, vel_m, rho_m, _ = multi.state()
+    off = multi.fluid_offsets
+    for k, t in enumerate(tanks):
+        single = sph.Simulation(t)
+        single.step(3)
+        pos_s, vel_s, rho_s, _ = single.state()
+        sl = slice(off[k], off[k + 1])
+        np.testing.assert_array_equal(pos_m[sl], pos_s)
+        np.testing.assert_array_equal(vel_m[sl], vel_s)
+        np.testing.assert_array_equal(rho_m[sl], rho_s)
+        single.close()
+    multi.close()
+
+
 # ------------------------------------------------------------------ trajectories
 def _interp(t, ts, ys):
     return np.interp(t, ts, ys)
