@@ -19,7 +19,9 @@ def test_reference_arm_prints_one_contract_line():
                 "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
-    assert line["config"]["workload"]
+    # the GPU arm's workload (the 8.04M-particle 3D dam break), each step a bounded sample
+    assert line["config"]["workload"].startswith("3D dam break") and "dp = 1/159" in line["config"]["workload"]
+    assert line["config"]["sample"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
