@@ -40,6 +40,11 @@ Readings where the paper is silent or inconsistent (the same readings the CUDA p
   R8  Viscous acceleration is fluid-fluid only, with eta = rho0 nu, evaluated once per
       advection step after density re-initialisation and held over its substeps.
   R9  In the second half step the position update uses v^{n+1}.
+  R10 Particles are stored in (search cell, id) order, search cells being the 2h position
+      cells halved on every axis and flattened x fastest (Sec. 6.2 fixes no order inside the
+      cell-linked list); neighbour sets are those of the 2h definition.
+  R11 Optional frozen pair geometry: r_i - r_j and (dW/dr)/r of every pair taken at the
+      configuration update and used by every half step of the advection step.
   R12 Transport velocity (Eq. transport, flows without free surface), off when p0 = 0: the
       background-pressure acceleration a_i = -2 sum_j m_j p0/(rho_i rho_j) grad_i W_ij over
       fluid pairs, with the mid-point geometry and densities of the pressure relaxation, acts
