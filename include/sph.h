@@ -9,7 +9,9 @@
  * of the position-based Verlet scheme (Eqs. verlet-first-half,
  * verlet-first-mediate, verlet-first-final with Eq. riemannsph, Eq. eqeos and
  * the one-sided wall problem of Eqs. eqriepartial, eqrienoslip, eqriepright),
- * with a Wendland C2 kernel, dummy-particle walls and gravity.
+ * with a Wendland C2 kernel, dummy-particle walls and gravity; optionally the
+ * transport velocity of Eq. transport (sph_params.p_transport) for flows without
+ * free surface.
  *
  * Conventions shared by every entry point
  *  - Return value: SPH_OK (0) or a negative SPH_E_* code. No call aborts the
