@@ -1,0 +1,94 @@
+"""Plain FP64 CPU oracle of species diffusion on the fluid particles (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may use this
+module. It shares no code with the CUDA library.
+
+The method (paper Sec. "Schemes for thermal and mass diffusion"), in the paper's order:
+
+  * dC/dt = div(D grad C) (Eq. diffusion-eq) with a symmetric positive-definite tensor D,
+    factored D = L L^T (Eq. chol).
+  * The SPH form of the transformed Laplacian (Eq. grad-laplace):
+        dC_i/dt = 2 sum_j (m_j/rho_j) (C_i - C_j) / (L~_ij e_ij)^2 * (1/r_ij) dW/dr_ij,
+    with L~_ij the pair combination of the per-particle factors L~_i, D = L~_i^-1 L~_i^-T.
+  * Time integration by a two-stage second-order Runge-Kutta scheme (Table tab:particle-dynamics:
+    the diffusion process is integrated with RK2).
+
+Readings where the paper is silent or inconsistent (the same readings the CUDA path takes):
+  R13 One diffusion tensor per body. Then every L~_i equals L^-1, the pair combination of two
+      equal factors is that factor (the printed combination L~_i L~_j/(L~_i + L~_j) is read as
+      the harmonic mean, which it is up to the factor 2 that makes equal factors reproduce
+      themselves), and the pair weight is 1/(L^-1 e)^2 = 1/(e^T D^-1 e); for isotropic
+      D = kappa I it is kappa. Volumes are m_j/rho_j of the current state. The species lives
+      on the fluid particles; wall particles carry none and exchange nothing (zero flux
+      through walls). Pairs at zero distance contribute nothing (as reading R6 of the
+      fluid oracle). The kernel-corrected form (Eq. grad-laplace-renormalize) is not taken.
+  R14 RK2 is Heun's form: C* = C^n + dt f(C^n), C^{n+1} = (C^n + C* + dt f(C*))/2. The
+      operator is linear and autonomous, so every two-stage second-order Runge-Kutta scheme
+      gives the same C^{n+1} up to rounding.
+  R15 For anisotropic D the printed operator is not consistent with div(D grad C): its
+      continuum limit applied to a quadratic field with Hessian H is
+      (d/|S|) int_S w(e) e^T H e dS over the unit sphere S (|S| its measure), with
+      w(e) = 1/(e^T D^-1 e); it equals tr(D H) only when D is isotropic. The oracle
+      computes the printed operator; the tests pin it against that closed-form limit.
+
+Parity pins: every function here is pinned by tests/test_diffusion_oracle.py (closed forms,
+the analytic solution of a diffusing band, conservation, brute force). None is unpinned.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import wcsph as o
+
+
+def tensor_inverse(D, dim: int) -> np.ndarray:
+    """D^-1 of a symmetric positive-definite tensor, checked through its Cholesky factor
+    (Eq. chol): L L^T = D with a positive diagonal exists only for SPD D."""
+    D = np.asarray(D, dtype=np.float64).reshape(dim, dim)
+    if not np.allclose(D, D.T, rtol=0.0, atol=0.0):
+        raise ValueError("D must be symmetric")
+    L = np.linalg.cholesky(D)           # raises for a tensor that is not positive definite
+    Linv = np.linalg.inv(L)
+    return Linv.T @ Linv                # (L L^T)^-1 = L^-T L^-1
+
+
+def fluid_pairs(x: np.ndarray, prm: o.Params):
+    """Directed fluid-fluid pairs of the neighbour set |r_i - r_j| < 2h, j != i."""
+    I, J, _, _ = o.neighbour_sets(x, np.zeros((0, prm.dim)), prm)
+    return I, J
+
+
+def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params) -> np.ndarray:
+    """Eq. grad-laplace under R13: dC_i/dt for every fluid particle i."""
+    rij = o.min_image(x[I] - x[J], prm.period)
+    r2 = np.sum(rij * rij, axis=1)
+    r = np.sqrt(r2)
+    ok = r2 > 0.0
+    fw = np.zeros_like(r)
+    fw[ok] = o.kernel_dW(r[ok], prm.h, prm.dim) / r[ok]            # (1/r) dW/dr
+    quad = np.einsum("pa,ab,pb->p", rij, Dinv, rij)                  # r^2 e^T D^-1 e
+    w = np.zeros_like(r)
+    w[ok] = r2[ok] / quad[ok]                                        # 1/(L~ e)^2
+    terms = 2.0 * vol[J] * (C[I] - C[J]) * fw * w
+    out = np.zeros(x.shape[0])
+    np.add.at(out, I, terms)
+    return out
+
+
+def rk2_step(x, C, vol, I, J, Dinv, dt: float, prm: o.Params) -> np.ndarray:
+    """One step of R14 (Heun)."""
+    Cs = C + dt * diffusion_rate(x, C, vol, I, J, Dinv, prm)
+    return 0.5 * (C + Cs + dt * diffusion_rate(x, Cs, vol, I, J, Dinv, prm))
+
+
+def run(x, C, m, rho, D, dt: float, n_steps: int, prm: o.Params) -> np.ndarray:
+    """n_steps RK2 steps of the species C on static particles (positions x, masses m,
+    densities rho)."""
+    x = np.asarray(x, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64).copy()
+    vol = np.asarray(m, dtype=np.float64) / np.asarray(rho, dtype=np.float64)
+    Dinv = tensor_inverse(D, prm.dim)
+    I, J = fluid_pairs(x, prm)
+    for _ in range(int(n_steps)):
+        C = rk2_step(x, C, vol, I, J, Dinv, dt, prm)
+    return C

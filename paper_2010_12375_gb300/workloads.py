@@ -253,6 +253,50 @@ def periodic_box(dim=2, n=24, seed=0, vel_amp=0.3, rho_amp=0.01, jitter=0.1, c0=
     )
 
 
+def diffusion_band(n=100, ny=8, kappa=1.0, a=0.1, D=None):
+    """Band of pollutant diffusing across a static particle body (Sec. mass diffusion,
+    first test): unit-periodic x axis with n lattice columns, ny rows on a periodic y axis
+    of length ny/n, C = 1 where |x - 1/2| < a and 0 elsewhere, diffusion tensor kappa I
+    (or `D`, 3x3 with the leading 2x2 used). meta: C0, D (3x3), dt = 0.1 h^2 / max eig D."""
+    dp = 1.0 / n
+    pos = _lattice(np.zeros(2), [n, ny], dp)
+    C0 = (np.abs(pos[:, 0] - 0.5) < a).astype(np.float64)
+    return _static_body(f"diffusion_band_{n}x{ny}", 2, dp, pos, np.array([1.0, ny * dp, 0.0]),
+                        C0, kappa, D)
+
+
+def diffusion_block_3d(n=200, kappa=1.0, sigma=0.1, D=None):
+    """Gaussian blob C = exp(-|x - c|^2 / (2 sigma^2)) in a static unit-periodic cube of n^3
+    lattice particles (the 3D diffusion workload). meta as diffusion_band."""
+    dp = 1.0 / n
+    pos = _lattice(np.zeros(3), [n, n, n], dp)
+    d2 = np.sum((pos - 0.5) ** 2, axis=1)
+    C0 = np.exp(-d2 / (2.0 * sigma * sigma))
+    return _static_body(f"diffusion_block_3d_{n}", 3, dp, pos, np.ones(3), C0, kappa, D)
+
+
+def _static_body(name, dim, dp, pos, extent, C0, kappa, D):
+    N = pos.shape[0]
+    Dm = np.zeros((3, 3))
+    if D is None:
+        Dm[:dim, :dim] = kappa * np.eye(dim)
+    else:
+        Dm[:dim, :dim] = np.asarray(D, dtype=np.float64)[:dim, :dim]
+    h = H_OVER_DP * dp
+    lam = float(np.max(np.linalg.eigvalsh(Dm[:dim, :dim])))
+    lo = np.zeros(3)
+    hi = np.asarray(extent, dtype=np.float64).copy()
+    per = np.zeros(3, dtype=np.int32)
+    per[:dim] = 1
+    return Workload(
+        name=name, dim=dim, h=h, dp=dp, rho0=1.0, c0=10.0, cfl_ad=0.25, cfl_ac=0.6, u_ref=1.0,
+        nu=0.0, gravity=np.zeros(3), lo=lo, hi=hi, periodic=per, free_surface=0, pos=pos,
+        vel=np.zeros((N, dim)), rho=np.ones(N), mass=np.full(N, dp ** dim),
+        wall_pos=np.zeros((0, dim)), wall_normal=np.zeros((0, dim)), wall_vol=np.zeros(0),
+        meta={"C0": C0, "D": Dm, "dt": 0.1 * h * h / lam},
+    )
+
+
 # ---------------------------------------------------------------------------------------
 # Seeded batched tanks.  splitmix64 (Steele, Lea, Flood 2014) drives the sampling so a
 # given seed always yields the same geometry.

@@ -1,0 +1,184 @@
+"""Pins of the diffusion oracle (oracle/diffusion.py) against what the paper and the
+mathematics fix: closed forms of the operator on quadratic fields, the closed-form
+continuum limit of the printed anisotropic operator (reading R15), conservation, the
+analytic solution of a diffusing band (the paper's first diffusion test, Sec. mass
+diffusion), the amplification polynomial of the two-stage scheme, and brute force."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import diffusion as df
+from oracle import wcsph as o
+from paper_2010_12375_gb300 import workloads as wl
+
+
+def _params(dim, h, dp, lo, hi, periodic):
+    return o.Params(dim=dim, h=h, dp=dp, rho0=1.0, c0=1.0, cfl_ad=0.25, cfl_ac=0.6, u_ref=0.1,
+                    nu=0.0, gravity=np.zeros(dim), lo=np.asarray(lo, float), hi=np.asarray(hi, float),
+                    periodic=np.asarray(periodic, bool), free_surface=False)
+
+
+def _centre_rate(dim, h_over_dp, D, H):
+    """Rate at the centre particle of an unbounded lattice patch for C = x^T H x / 2."""
+    dp = 1.0
+    k = int(math.ceil(2 * h_over_dp)) + 1
+    ax = np.arange(-k, k + 1, dtype=np.float64)
+    X = np.stack([g.ravel() for g in np.meshgrid(*([ax] * dim), indexing="ij")], 1) * dp
+    C = 0.5 * np.einsum("pa,ab,pb->p", X, H, X)
+    i0 = int(np.nonzero(np.all(X == 0, axis=1))[0][0])
+    J = np.array([j for j in range(X.shape[0]) if j != i0])
+    I = np.full(J.size, i0)
+    prm = _params(dim, h_over_dp * dp, dp, -np.full(dim, 100.0), np.full(dim, 100.0), [False] * dim)
+    vol = np.full(X.shape[0], dp ** dim)
+    return df.diffusion_rate(X, C, vol, I, J, df.tensor_inverse(D, dim), prm)[i0]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_quadratic_isotropic_is_the_laplacian(dim):
+    # div(kappa grad C) = kappa tr H exactly for a quadratic field; the lattice sum
+    # converges to it as h/dp grows (1.3: 2.6 %, 4: < 2e-5)
+    kappa = 0.7
+    H = np.diag(np.arange(1.0, dim + 1.0))
+    exact = kappa * np.trace(H)
+    assert abs(_centre_rate(dim, 4.0, kappa * np.eye(dim), H) / exact - 1.0) < 2e-5
+    assert abs(_centre_rate(dim, 1.3, kappa * np.eye(dim), H) / exact - 1.0) < 0.03
+
+
+@pytest.mark.parametrize("H,limit", [
+    # D = diag(4, 1) in 2D: w(theta) = 1/(cos^2/4 + sin^2); (2/2pi) int w e^T H e dtheta
+    # with int cos^2/(A cos^2 + B sin^2) = 2 pi/(A + sqrt(AB)) and the sin^2 analogue
+    (np.diag([2.0, 0.0]), 4.0 / (0.25 + 0.5)),
+    (np.diag([0.0, 2.0]), 4.0 / (1.0 + 0.5)),
+])
+def test_anisotropic_printed_operator_limit(H, limit):
+    # reading R15: the printed operator tends to (d/|S|) int w(e) e^T H e dS, not tr(D H)
+    D = np.diag([4.0, 1.0])
+    got = _centre_rate(2, 4.0, D, H)
+    assert abs(got / limit - 1.0) < 5e-3
+    assert abs(got / np.trace(D @ H) - 1.0) > 0.2                    # not div(D grad C)
+
+
+def _jittered_box(dim, n, seed, periodic=True):
+    rng = np.random.default_rng(seed)
+    dp = 1.0 / n
+    g = np.stack([a.ravel() for a in np.meshgrid(*([np.arange(n) + 0.5] * dim), indexing="ij")], 1) * dp
+    x = g + rng.uniform(-0.2, 0.2, g.shape) * dp
+    x = np.mod(x, 1.0) if periodic else x
+    prm = _params(dim, 1.3 * dp, dp, np.zeros(dim), np.ones(dim), [periodic] * dim)
+    return x, prm, rng
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_conservation_and_constant_field(dim):
+    x, prm, rng = _jittered_box(dim, 12 if dim == 2 else 7, seed=3)
+    n = x.shape[0]
+    vol = prm.dp ** dim * rng.uniform(0.8, 1.2, n)
+    C = rng.uniform(-1.0, 1.0, n)
+    A = rng.normal(size=(dim, dim))
+    D = A @ A.T + dim * np.eye(dim)                 # anisotropic, off-diagonal terms
+    Dinv = df.tensor_inverse(D, dim)
+    I, J = df.fluid_pairs(x, prm)
+    r = df.diffusion_rate(x, C, vol, I, J, Dinv, prm)
+    # antisymmetric pair exchange: sum_i V_i dC_i/dt = 0
+    assert abs(np.sum(vol * r)) < 1e-12 * np.sum(np.abs(vol * r))
+    assert np.all(df.diffusion_rate(x, np.full(n, 2.5), vol, I, J, Dinv, prm) == 0.0)
+
+
+def test_brute_force_double_loop():
+    # every pair term written out with plain loops on a tiny periodic box
+    x, prm, rng = _jittered_box(2, 6, seed=11)
+    n = x.shape[0]
+    vol = prm.dp ** 2 * rng.uniform(0.8, 1.2, n)
+    C = rng.uniform(0.0, 1.0, n)
+    D = np.array([[2.0, 0.6], [0.6, 1.0]])
+    Dinv = np.linalg.inv(D)
+    I, J = df.fluid_pairs(x, prm)
+    got = df.diffusion_rate(x, C, vol, I, J, df.tensor_inverse(D, 2), prm)
+    h = prm.h
+    alpha = 7.0 / (4.0 * math.pi * h * h)
+    want = np.zeros(n)
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            d = x[i] - x[j]
+            d -= np.round(d)                          # unit period
+            r = math.hypot(d[0], d[1])
+            if r >= 2 * h:
+                continue
+            q = r / h
+            dW = alpha / h * (-5.0 * q) * (1 - q / 2) ** 3
+            e = d / r
+            w = 1.0 / float(e @ Dinv @ e)
+            want[i] += 2.0 * vol[j] * (C[i] - C[j]) * w * dW / r
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * np.max(np.abs(want)))
+
+
+def test_band_against_the_analytic_solution():
+    # Sec. mass diffusion, first test: a band of pollutant (C = 1 for |x - 1/2| < a)
+    # diffusing in 1D. On the unit-periodic axis the exact solution is the image sum
+    # C = 1/2 sum_k [erf((a - (x - 1/2 + k))/s) + erf((a + (x - 1/2 + k))/s)], s = sqrt(4 kappa t).
+    w = wl.diffusion_band(n=100, ny=8, kappa=1.0, a=0.1)
+    prm = o.Params.from_problem(w)
+    D = np.asarray(w.meta["D"])[:2, :2]
+    dt = w.meta["dt"]
+    steps = 150
+    C = df.run(w.pos, w.meta["C0"], w.mass, w.rho, D, dt, steps, prm)
+    s = math.sqrt(4.0 * 1.0 * dt * steps)
+    xs = w.pos[:, 0] - 0.5
+    exact = np.zeros_like(xs)
+    for k in range(-2, 3):
+        exact += 0.5 * (np.vectorize(math.erf)((0.1 - (xs + k)) / s) +
+                        np.vectorize(math.erf)((0.1 + (xs + k)) / s))
+    err = np.max(np.abs(C - exact))
+    assert err < 1e-2
+    # a planted factor-2 slip in the operator (kappa/2) is visible at this tolerance
+    half = df.run(w.pos, w.meta["C0"], w.mass, w.rho, 0.5 * D, dt, steps, prm)
+    assert np.max(np.abs(half - exact)) > 3e-2
+
+
+def _sine_mode_rate(n, h_over_dp, kappa):
+    dp = 1.0 / n
+    g = np.stack([a.ravel() for a in np.meshgrid(np.arange(n) * dp, np.arange(n) * dp, indexing="ij")], 1)
+    C0 = np.sin(2 * math.pi * g[:, 0])
+    prm = _params(2, h_over_dp * dp, dp, [0, 0], [1, 1], [True, True])
+    vol = np.full(g.shape[0], dp * dp)
+    I, J = df.fluid_pairs(g, prm)
+    Dinv = df.tensor_inverse(kappa * np.eye(2), 2)
+    r = df.diffusion_rate(g, C0, vol, I, J, Dinv, prm)
+    big = np.abs(C0) > 0.5
+    lam = -r[big] / C0[big]
+    assert np.ptp(lam) < 1e-9 * np.max(lam)          # an eigenvector of the operator
+    return float(lam.mean()), (g, C0, vol, I, J, Dinv, prm)
+
+
+def test_rk2_amplification_of_a_sine_mode():
+    # a sine mode on a periodic lattice is an eigenvector of the linear operator, so one
+    # two-stage second-order step multiplies it by 1 - z + z^2/2 with z = lambda dt
+    kappa, k2 = 0.3, (2 * math.pi) ** 2
+    lam, (g, C0, vol, I, J, Dinv, prm) = _sine_mode_rate(40, 1.3, kappa)
+    assert abs(lam / (kappa * k2) - 1.0) < 0.03
+    dt = 0.1 * prm.h ** 2 / kappa
+    C = C0.copy()
+    for _ in range(5):
+        C = df.rk2_step(g, C, vol, I, J, Dinv, dt, prm)
+    z = lam * dt
+    np.testing.assert_allclose(C, (1 - z + z * z / 2) ** 5 * C0, rtol=0, atol=1e-12)
+
+
+def test_sine_mode_rate_converges_at_second_order():
+    # at fixed h/dp = 3 the rate tends to kappa k^2 with an error of order (k h)^2
+    kappa, k2 = 0.3, (2 * math.pi) ** 2
+    e40 = abs(_sine_mode_rate(40, 3.0, kappa)[0] / (kappa * k2) - 1.0)
+    e80 = abs(_sine_mode_rate(80, 3.0, kappa)[0] / (kappa * k2) - 1.0)
+    assert e40 < 0.02 and 3.5 < e40 / e80 < 4.5
+
+
+def test_tensor_inverse_rejects_bad_tensors():
+    with pytest.raises(ValueError):
+        df.tensor_inverse([[1.0, 0.2], [0.0, 1.0]], 2)          # not symmetric
+    with pytest.raises(np.linalg.LinAlgError):
+        df.tensor_inverse([[1.0, 2.0], [2.0, 1.0]], 2)          # indefinite
+    D = np.array([[3.0, 1.0], [1.0, 2.0]])
+    np.testing.assert_allclose(df.tensor_inverse(D, 2) @ D, np.eye(2), atol=1e-14)
