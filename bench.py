@@ -383,6 +383,9 @@ def run_workload(args):
     if args.workload == "sizes":
         run_sizes(args)
         return
+    if args.workload == "diffusion3d":
+        run_diffusion(args, stream)
+        return
     if args.workload == "batched":
         problems = wk.batched_dam_breaks(256)
         name = "256 independent 2D dam breaks (2k-50k fluid each), one handle"
@@ -460,6 +463,73 @@ def run_sizes(args):
            "dtype": "f32", "data": "synthetic", "loop": "graph",
            "config": {"workload": "3D dam break 2x1x1 in a 5.366x5.366x1 tank, dp = 1/80, 1/126, 1/159"},
            "value": rows[-1]["value"], "sizes": rows}
+    print(json.dumps(out), flush=True)
+
+
+def run_diffusion(args, stream):
+    """Species diffusion (Eq. grad-laplace, two-stage Runge-Kutta) on a static unit-periodic
+    cube of 200^3 = 8.0M lattice particles (isotropic D, Gaussian blob): RK2 steps per second
+    through one sph_diffusion_step call, and the stage kernel against the HBM roofline."""
+    import torch
+    from paper_2010_12375_gb300 import sph, workloads as wk
+    prob = wk.diffusion_block_3d(200, kappa=1.0, sigma=0.1)
+    sim = sph.Simulation(prob, stream=stream)
+    sph.sph_build_cells(sim.handle, stream)
+    sp = sph.sph_species_create(sim.handle, prob.meta["D"], 3)
+    sph.sph_species_set(sim.handle, sp, prob.meta["C0"], stream)
+    dt = prob.meta["dt"]
+    fluid_pairs, _ = sph.sph_pair_count(sim.handle, stream)
+    n = sim.n
+
+    def timed(k):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sph.sph_diffusion_step(sim.handle, sp, dt, k, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    for _ in range(args.warmup):
+        timed(1)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_k = timed(args.steps)
+    ms_2k = timed(2 * args.steps)
+    clk = clocks.stop()
+    sph.sph_species_destroy(sp)
+    sim.close()
+    stage_ms = (ms_2k - ms_k) / (2 * args.steps)        # per stage kernel, gather/scatter removed
+    # algorithmic bytes of one stage: own position record 16, own species 4, row count 4,
+    # species written 4, C^n 4 in the second stage (2 on average), 4 per neighbour index
+    per_particle = 16 + 4 + 4 + 4 + 2
+    alg = n * per_particle + 4 * fluid_pairs
+    peak, src = measured_peaks()
+    achieved = alg / (stage_ms * 1e-3) / 1e9
+    out = {"metric": "particle RK2 diffusion steps/s, 3D periodic block 200^3", "unit": "particle-steps/s",
+           "value": n * args.steps / (ms_k * 1e-3), "ms_per_step": ms_k / args.steps,
+           "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"3D unit-periodic static block, {n} particles (dp = 1/200, h = 1.3 dp), "
+                                  "isotropic D, Gaussian blob sigma = 0.1; inputs larger than L2",
+                      "fluid_pairs": int(fluid_pairs)},
+           "clocks": clk,
+           "gpu_launches": 2 * args.steps + 2,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "k_diffusion_stage", "stage_ms": stage_ms,
+                        "algorithmic_bytes": alg, "peak_source": src}}
+    if not args.no_cpu_baseline:
+        from oracle import diffusion as odf, wcsph as ow
+        small = wk.diffusion_block_3d(24, kappa=1.0, sigma=0.1)
+        t0 = time.perf_counter()
+        odf.run(small.pos, small.meta["C0"], small.mass, small.rho, small.meta["D"], small.meta["dt"], 2,
+                ow.Params.from_problem(small))
+        sec = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": small.n_fluid * 2 / sec, "unit": "particle-steps/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"2 RK2 steps of the same block at 24^3 = {small.n_fluid} particles, "
+                                         "neighbour search included"}
     print(json.dumps(out), flush=True)
 
 
@@ -554,7 +624,7 @@ def main():
                     help="the frozen-pair-geometry reading (pair vectors kept from the configuration update)")
     ap.add_argument("--launch-config", default=None,
                     help="pr_tpp,pr_block,dr_tpp,dr_block: fixed launch variants instead of autotuning")
-    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes"],
+    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes", "diffusion3d"],
                     help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -11,7 +11,8 @@
  * the one-sided wall problem of Eqs. eqriepartial, eqrienoslip, eqriepright),
  * with a Wendland C2 kernel, dummy-particle walls and gravity; optionally the
  * transport velocity of Eq. transport (sph_params.p_transport) for flows without
- * free surface.
+ * free surface. A species carried by the fluid particles diffuses by Eq. grad-laplace
+ * with two-stage Runge-Kutta steps (sph_species_*, sph_diffusion_step).
  *
  * Conventions shared by every entry point
  *  - Return value: SPH_OK (0) or a negative SPH_E_* code. No call aborts the
@@ -307,6 +308,43 @@ int sph_learned_train_step(sph_handle* h, sph_learned* net, const double* target
  * instead. *used_learned = 1 when the network's step was kept. Synchronous. */
 int sph_learned_step(sph_handle* h, sph_learned* net, double max_mean_rho_dev,
                      double max_energy_drift, int32_t* used_learned, void* stream);
+
+/* ---- Species diffusion (Sec. "Schemes for thermal and mass diffusion") ----------------
+ * A species C (concentration or temperature) carried by the fluid particles of a handle
+ * diffuses by dC/dt = div(D grad C) (Eq. diffusion-eq), discretised as Eq. grad-laplace:
+ *   dC_i/dt = 2 sum_j (m_j/rho_j) (C_i - C_j) w(e_ij) (1/r_ij) dW/dr_ij,
+ *   w(e) = 1/(L^-1 e)^2 = 1/(e^T D^-1 e),  D = L L^T (Eq. chol),
+ * over the fluid neighbours of the current neighbour table (wall particles carry no
+ * species: zero flux through walls), with one diffusion tensor D per species object (so
+ * the pair combination of the per-particle factors is the factor itself) and the masses,
+ * densities and positions of the handle's current state. Pairs at zero distance add
+ * nothing. Time integration is the two-stage second-order Runge-Kutta scheme (Heun):
+ *   C* = C + dt f(C),  C <- (C + C* + dt f(C*)) / 2.
+ * For isotropic D = kappa I, w = kappa and the operator is the SPH Laplacian times kappa.
+ * For anisotropic D the printed weight is not consistent with div(D grad C) (its
+ * continuum limit on a quadratic field differs from tr(D H)); it is computed as printed.
+ * The scheme is explicit: dt <= h^2 / (7 lambda_max(D)) is a sufficient stability bound
+ * (Gershgorin on the lattice sum of |dW/dr|/r, about 3.5/h^2 in 2D and 3D).
+ * The species is stored on the device in FP32, by caller row, so sph_step and
+ * sph_build_cells may reorder the particles between diffusion calls. */
+typedef struct sph_species sph_species;
+
+/* D: host, dim x dim row-major, symmetric positive definite (else SPH_E_INVALID). The
+ * object belongs to handle h (same dimension, particle count) and must be destroyed
+ * before it. The species starts at 0. On failure *out may still hold an object that
+ * carries the message (sph_species_last_error); destroy it. */
+int sph_species_create(sph_handle* h, const double* D, sph_species** out);
+void sph_species_destroy(sph_species* sp);
+const char* sph_species_last_error(const sph_species* sp);
+/* C: host or device, n_fluid doubles in caller row order. Synchronous. */
+int sph_species_set(sph_handle* h, sph_species* sp, const double* C, void* stream);
+/* C: host or device, n_fluid doubles in caller row order. Synchronous. */
+int sph_species_get(sph_handle* h, sph_species* sp, double* C, void* stream);
+/* n_steps RK2 steps of size dt (> 0, finite) on the current neighbour table, which
+ * must be valid (sph_build_cells after the last state change; SPH_E_INVALID otherwise).
+ * Positions, velocities and densities are not changed. Asynchronous on stream: two
+ * kernel launches per step plus a gather and a scatter of the species per call. */
+int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_steps, void* stream);
 
 /* Allocation-free diagnostics. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory (code running inside

@@ -38,6 +38,8 @@ EXPORTS = [
     "sph_learned_weight_count", "sph_learned_create", "sph_learned_destroy",
     "sph_learned_last_error", "sph_learned_set_weights", "sph_learned_get_weights",
     "sph_learned_set_fused", "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
+    "sph_species_create", "sph_species_destroy", "sph_species_last_error", "sph_species_set",
+    "sph_species_get", "sph_diffusion_step",
 ]
 
 
@@ -139,6 +141,12 @@ def load():
         "sph_learned_predict": (i32, [P, P, P, P]),
         "sph_learned_train_step": (i32, [P, P, P, dbl, ctypes.POINTER(dbl), P, P]),
         "sph_learned_step": (i32, [P, P, dbl, dbl, ctypes.POINTER(i32), P]),
+        "sph_species_create": (i32, [P, P, ctypes.POINTER(P)]),
+        "sph_species_destroy": (None, [P]),
+        "sph_species_last_error": (ctypes.c_char_p, [P]),
+        "sph_species_set": (i32, [P, P, P, P]),
+        "sph_species_get": (i32, [P, P, P, P]),
+        "sph_diffusion_step": (i32, [P, P, dbl, i32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -471,6 +479,48 @@ def sph_learned_step(h, net, max_mean_rho_dev=0.01, max_energy_drift=0.005, stre
 
 
 # ------------------------------------------------------------------------------ convenience
+# ------------------------------------------------------------------------ species diffusion
+def _scheck(lib, sp, code):
+    if code != SPH_OK:
+        raise SphError(code, lib.sph_species_last_error(sp).decode() if sp else "")
+
+
+def sph_species_create(h, D, dim):
+    """Species object on handle h with diffusion tensor D (dim x dim, SPD)."""
+    lib = load()
+    Dm = np.ascontiguousarray(np.asarray(D, dtype=np.float64)[:dim, :dim])
+    sp = ctypes.c_void_p()
+    code = lib.sph_species_create(h, _ptr(Dm), ctypes.byref(sp))
+    if code != SPH_OK:
+        msg = lib.sph_species_last_error(sp).decode() if sp.value else ""
+        if sp.value:
+            lib.sph_species_destroy(sp)
+        raise SphError(code, msg)
+    return sp
+
+
+def sph_species_destroy(sp):
+    load().sph_species_destroy(sp)
+
+
+def sph_species_set(h, sp, C, stream=None):
+    lib = load()
+    C = _f64(C)
+    _scheck(lib, sp, lib.sph_species_set(h, sp, _ptr(C), _stream(stream)))
+
+
+def sph_species_get(h, sp, n, stream=None, out=None):
+    lib = load()
+    C = np.empty(n, dtype=np.float64) if out is None else out
+    _scheck(lib, sp, lib.sph_species_get(h, sp, _ptr(C), _stream(stream)))
+    return C
+
+
+def sph_diffusion_step(h, sp, dt, n_steps=1, stream=None):
+    lib = load()
+    _scheck(lib, sp, lib.sph_diffusion_step(h, sp, float(dt), int(n_steps), _stream(stream)))
+
+
 class Simulation:
     """One handle over one or more tanks built from workload objects (marshalling only)."""
 
