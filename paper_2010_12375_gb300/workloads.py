@@ -257,7 +257,8 @@ def diffusion_band(n=100, ny=8, kappa=1.0, a=0.1, D=None):
     """Band of pollutant diffusing across a static particle body (Sec. mass diffusion,
     first test): unit-periodic x axis with n lattice columns, ny rows on a periodic y axis
     of length ny/n, C = 1 where |x - 1/2| < a and 0 elsewhere, diffusion tensor kappa I
-    (or `D`, 3x3 with the leading 2x2 used). meta: C0, D (3x3), dt = 0.1 h^2 / max eig D."""
+    (or `D`, 3x3 with the leading 2x2 used). meta: C0, D (3x3), dt = 0.1 h^2 / max eig D.
+    The GPU's position contract has all periodic axes share one period: ny = n there."""
     dp = 1.0 / n
     pos = _lattice(np.zeros(2), [n, ny], dp)
     C0 = (np.abs(pos[:, 0] - 0.5) < a).astype(np.float64)

@@ -71,7 +71,7 @@ def _oracle_run(p, D, C0, dt, steps):
 def _case(name):
     rng = np.random.default_rng(7)
     if name == "band2d":
-        prob = wk.diffusion_band(n=200, ny=40, kappa=1.0, a=0.1)
+        prob = wk.diffusion_band(n=128, ny=128, kappa=1.0, a=0.1)   # periodic axes share one period
         p = _representable_problem(prob)
         C0 = prob.meta["C0"]
         D = prob.meta["D"][:2, :2]
@@ -146,8 +146,8 @@ def test_species_follows_particles_through_resorting(sph):
 
 
 def test_batched_tanks_diffuse_independently(sph):
-    pa = _representable_problem(wk.diffusion_band(n=100, ny=8, kappa=1.0, a=0.1))
-    pb = _representable_problem(wk.diffusion_band(n=64, ny=8, kappa=1.0, a=0.2))
+    pa = _representable_problem(wk.diffusion_band(n=64, ny=64, kappa=1.0, a=0.1))
+    pb = _representable_problem(wk.diffusion_band(n=48, ny=48, kappa=1.0, a=0.2))
     D = np.eye(2)
     dt = 0.1 * min(pa.h, pb.h) ** 2          # the smaller of the two stable steps
     C0 = np.concatenate([pa.meta["C0"], pb.meta["C0"]])
@@ -160,7 +160,7 @@ def test_batched_tanks_diffuse_independently(sph):
 
 def test_edge_cases(sph):
     # zero steps leave C as set; a lone particle has no neighbours; bad arguments fail cleanly
-    prob = _representable_problem(wk.diffusion_band(n=100, ny=8))
+    prob = _representable_problem(wk.diffusion_band(n=32, ny=32))
     sim = sph.Simulation(prob)
     try:
         sp = sph.sph_species_create(sim.handle, np.eye(2), 2)
