@@ -11,11 +11,14 @@
 //   stage 2: C^{n+1} = (C^n + C* + dt f(C*)) / 2      (written over C^n, own index only)
 //
 // One thread per fluid particle walks the fluid part of its neighbour row in the
-// quad-interleaved table, keeping the next index quad in flight, and gathers per neighbour
-// the 16-byte position record (fixed-point position + density deviation, the same record
-// the relaxations read) and the 4-byte species value. Pair vectors are exact integer
-// differences scaled by the position quantum. Wall neighbours are skipped: walls carry no
-// species (zero flux). Pairs at zero distance add nothing.
+// quad-interleaved table, keeping the next index quad in flight. Each call packs, per slot,
+// one 16-byte record R = {qx, qy, qz, bits(C)} (2D: {qx, qy, bits(V), bits(C)}, V = m/rho),
+// so a neighbour costs one 16-byte gather; in 3D the volumes V_j come from a separate
+// array only when they are not all equal within a tank (checked once per call on the
+// device; neighbours never cross tanks, so equal volumes mean V_j = V_i). Stages ping-pong
+// between two record buffers and write only the species word. Pair vectors are exact
+// integer differences scaled by the position quantum. Wall neighbours are skipped: walls
+// carry no species (zero flux). Pairs at zero distance add nothing.
 //
 // Between calls the species is kept by caller row, so the fluid solver may re-sort the
 // particles; each call gathers it into slot order, runs its steps and scatters it back.
@@ -42,13 +45,14 @@ __device__ __forceinline__ float axis_diff(int qi, int qj, int period, float dq)
   return (float)(PER ? wrap_diff(qi - qj, period) : qi - qj) * dq;
 }
 
-// One pair's share of f(C)_i / 2, zero at zero distance and beyond 2h.
+// One pair's share of f(C)_i / 2 without the volume V_j; zero at zero distance and
+// beyond 2h.
 template <int D, bool PER, bool ISO>
-__device__ __forceinline__ float diff_term(const Inst& I, const DiffCoef& K, const int4& pi, float ci,
-                                           const int4& a, float ca, float ma) {
-  const float rx = axis_diff<PER>(pi.x, a.x, I.period[0], I.dq);
-  const float ry = axis_diff<PER>(pi.y, a.y, I.period[1], I.dq);
-  const float rz = D == 3 ? axis_diff<PER>(pi.z, a.z, I.period[2], I.dq) : 0.0f;
+__device__ __forceinline__ float diff_term(const Inst& I, const DiffCoef& K, const int4& ri, float ci,
+                                           const int4& a) {
+  const float rx = axis_diff<PER>(ri.x, a.x, I.period[0], I.dq);
+  const float ry = axis_diff<PER>(ri.y, a.y, I.period[1], I.dq);
+  const float rz = D == 3 ? axis_diff<PER>(ri.z, a.z, I.period[2], I.dq) : 0.0f;
   const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
   const float r = r2 * rsqrtf(r2);
   const float t = fmaxf(fmaf(r, -0.5f * I.inv_h, 1.0f), 0.0f);
@@ -61,22 +65,32 @@ __device__ __forceinline__ float diff_term(const Inst& I, const DiffCoef& K, con
     if (D == 3) qf = fmaf(K.zz * rz, rz, fmaf(2.0f * K.xz * rx, rz, fmaf(2.0f * K.yz * ry, rz, qf)));
     w = __fdividef(r2, qf);                                        // 1/(e^T D^-1 e)
   }
-  const float vj = __fdividef(ma, I.rho0 + i2f(a.w));              // m_j / rho_j
-  const float term = vj * (ci - ca) * fw * w;
+  const float term = (ci - i2f(a.w)) * fw * w;
   return r2 > 0.0f ? term : 0.0f;
+}
+
+// Volume of slot j: packed in the record in 2D, else the tank's common volume (uniform)
+// or the per-slot array.
+template <int D>
+__device__ __forceinline__ float volume_of(const int4& a, int64_t j, float vi, bool uniform,
+                                           const float* __restrict__ vol) {
+  if (D == 2) return i2f(a.z);
+  return uniform ? vi : vol[j];
 }
 
 template <int D, bool PER, bool ISO, bool SECOND>
 __global__ void __launch_bounds__(kDiffBlock)
-k_diffusion_stage(int64_t n, const int4* __restrict__ P, const float* __restrict__ Cin, const float* Cn,
-                  float* Cout, const int* __restrict__ nbr, const uint32_t* __restrict__ nbc,
-                  const int* __restrict__ inst_of, const Inst* __restrict__ inst,
-                  const float* __restrict__ mass, DiffCoef K, float dt) {
+k_diffusion_stage(int64_t n, const int4* __restrict__ Rin, int4* __restrict__ Rout, const int* __restrict__ nbr,
+                  const uint32_t* __restrict__ nbc, const int* __restrict__ inst_of,
+                  const Inst* __restrict__ inst, const float* __restrict__ vol,
+                  const int* __restrict__ nonuniform, DiffCoef K, float dt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Inst& I = inst[inst_of ? inst_of[i] : 0];
-  const int4 pi = P[i];
-  const float ci = Cin[i];
+  const bool uniform = D == 2 || *nonuniform == 0;
+  const int4 ri = Rin[i];
+  const float ci = i2f(ri.w);
+  const float vi = D == 2 ? i2f(ri.z) : vol[i];
   const int nf = (int)(nbc[i] & 0xffffu);
   const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
   const int nq = (nf + 3) >> 2;
@@ -87,36 +101,53 @@ k_diffusion_stage(int64_t n, const int4* __restrict__ P, const float* __restrict
     if (q + 1 < nq) nxt = nb4[(int64_t)(q + 1) * n + i];   // next quad in flight
     const int sl = q << 2;
     const int j1 = sl + 1 < nf ? cq.y : cq.x, j2 = sl + 2 < nf ? cq.z : cq.x, j3 = sl + 3 < nf ? cq.w : cq.x;
-    const int4 a0 = P[cq.x], a1 = P[j1], a2 = P[j2], a3 = P[j3];
-    const float c0 = Cin[cq.x], c1 = Cin[j1], c2 = Cin[j2], c3 = Cin[j3];
-    float m0 = I.mass, m1 = I.mass, m2 = I.mass, m3 = I.mass;
-    if (mass) {
-      m0 = mass[cq.x]; m1 = mass[j1]; m2 = mass[j2]; m3 = mass[j3];
-    }
-    s0 += diff_term<D, PER, ISO>(I, K, pi, ci, a0, c0, m0);
-    const float t1 = diff_term<D, PER, ISO>(I, K, pi, ci, a1, c1, m1);
-    const float t2 = diff_term<D, PER, ISO>(I, K, pi, ci, a2, c2, m2);
-    const float t3 = diff_term<D, PER, ISO>(I, K, pi, ci, a3, c3, m3);
+    const int4 a0 = Rin[cq.x], a1 = Rin[j1], a2 = Rin[j2], a3 = Rin[j3];
+    const float t0 = volume_of<D>(a0, cq.x, vi, uniform, vol) * diff_term<D, PER, ISO>(I, K, ri, ci, a0);
+    const float t1 = volume_of<D>(a1, j1, vi, uniform, vol) * diff_term<D, PER, ISO>(I, K, ri, ci, a1);
+    const float t2 = volume_of<D>(a2, j2, vi, uniform, vol) * diff_term<D, PER, ISO>(I, K, ri, ci, a2);
+    const float t3 = volume_of<D>(a3, j3, vi, uniform, vol) * diff_term<D, PER, ISO>(I, K, ri, ci, a3);
+    s0 += t0;
     s1 += sl + 1 < nf ? t1 : 0.0f;
     s0 += sl + 2 < nf ? t2 : 0.0f;
     s1 += sl + 3 < nf ? t3 : 0.0f;
   }
   const float rate = 2.0f * (s0 + s1);
   const float next = fmaf(dt, rate, ci);
-  Cout[i] = SECOND ? 0.5f * (Cn[i] + next) : next;
+  // stage 2 reads C^n from the output record's own slot (written by no other thread)
+  const float out = SECOND ? 0.5f * (i2f(Rout[i].w) + next) : next;
+  reinterpret_cast<int*>(Rout)[4 * i + 3] = f2i(out);
 }
 
-// Caller row -> slot order and back (b.id[slot] = caller row).
-__global__ void k_species_gather(int64_t n, const int* __restrict__ id, const float* __restrict__ by_row,
-                                 float* __restrict__ by_slot) {
+// Per call: records of both buffers from the fluid state and the species by caller row
+// (b.id[slot] = caller row), the per-slot volumes (3D) and the flag of unequal volumes
+// within a tank.
+template <int D>
+__global__ void k_species_pack(int64_t n, const int4* __restrict__ P, const int* __restrict__ id,
+                               const int* __restrict__ inst_of, const Inst* __restrict__ inst,
+                               const float* __restrict__ mass, const float* __restrict__ by_row,
+                               int4* __restrict__ R0, int4* __restrict__ R1, float* __restrict__ vol,
+                               int* __restrict__ nonuniform) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) by_slot[i] = by_row[id[i]];
+  if (i >= n) return;
+  const Inst& I = inst[inst_of ? inst_of[i] : 0];
+  const int4 p = P[i];
+  const float v = __fdividef(mass ? mass[i] : I.mass, I.rho0 + i2f(p.w));      // m_i / rho_i
+  const int c = f2i(by_row[id[i]]);
+  const int4 r = make_int4(p.x, p.y, D == 2 ? f2i(v) : p.z, c);
+  R0[i] = r;
+  R1[i] = r;
+  if (D == 3) {
+    vol[i] = v;
+    const int64_t f = I.fluid_begin;                                  // the tank's first slot
+    const float vf = __fdividef(mass ? mass[f] : I.mass, I.rho0 + i2f(P[f].w));
+    if (vf != v) atomicOr(nonuniform, 1);
+  }
 }
 
-__global__ void k_species_scatter(int64_t n, const int* __restrict__ id, const float* __restrict__ by_slot,
-                                  float* __restrict__ by_row) {
+__global__ void k_species_unpack(int64_t n, const int* __restrict__ id, const int4* __restrict__ R,
+                                 float* __restrict__ by_row) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) by_row[id[i]] = by_slot[i];
+  if (i < n) by_row[id[i]] = i2f(R[i].w);
 }
 
 __global__ void k_species_import(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
@@ -129,8 +160,8 @@ __global__ void k_species_export(int64_t n, const float* __restrict__ src, doubl
   if (i < n) dst[i] = (double)src[i];
 }
 
-using StageFn = void (*)(int64_t, const int4*, const float*, const float*, float*, const int*,
-                         const uint32_t*, const int*, const Inst*, const float*, DiffCoef, float);
+using StageFn = void (*)(int64_t, const int4*, int4*, const int*, const uint32_t*, const int*, const Inst*,
+                         const float*, const int*, DiffCoef, float);
 
 template <int D, bool PER, bool ISO>
 void pick_stages(StageFn* s1, StageFn* s2) {
@@ -153,8 +184,10 @@ struct sph_species {
   sph::DiffCoef K{};
   bool iso = false;
   float* by_row = nullptr;     // [n] species by caller row (kept between calls)
-  float* ca = nullptr;         // [n] slot order: C^n
-  float* cb = nullptr;         // [n] slot order: C*
+  int4* r0 = nullptr;          // [n] slot records carrying C^n
+  int4* r1 = nullptr;          // [n] slot records carrying C*
+  float* vol = nullptr;        // [n] slot volumes m/rho (3D)
+  int* nonuniform = nullptr;   // [1] volumes differ within a tank (3D)
   double* stage = nullptr;     // [n] doubles for host copies
   std::string err;
 };
@@ -241,8 +274,10 @@ int sph_species_create(sph_handle* h, const double* D, sph_species** out) {
   if (sp->n > 0) {
     const size_t n = (size_t)sp->n;
     if (cudaMalloc(&sp->by_row, sizeof(float) * n) != cudaSuccess ||
-        cudaMalloc(&sp->ca, sizeof(float) * n) != cudaSuccess ||
-        cudaMalloc(&sp->cb, sizeof(float) * n) != cudaSuccess ||
+        cudaMalloc(&sp->r0, sizeof(int4) * n) != cudaSuccess ||
+        cudaMalloc(&sp->r1, sizeof(int4) * n) != cudaSuccess ||
+        cudaMalloc(&sp->vol, sizeof(float) * n) != cudaSuccess ||
+        cudaMalloc(&sp->nonuniform, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&sp->stage, sizeof(double) * n) != cudaSuccess) {
       cudaGetLastError();
       return sfail(sp, SPH_E_OOM, "device allocation of the species failed");
@@ -256,8 +291,10 @@ int sph_species_create(sph_handle* h, const double* D, sph_species** out) {
 void sph_species_destroy(sph_species* sp) {
   if (!sp) return;
   cudaFree(sp->by_row);
-  cudaFree(sp->ca);
-  cudaFree(sp->cb);
+  cudaFree(sp->r0);
+  cudaFree(sp->r1);
+  cudaFree(sp->vol);
+  cudaFree(sp->nonuniform);
   cudaFree(sp->stage);
   delete sp;
 }
@@ -318,14 +355,18 @@ int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_step
   }
   const unsigned grid = sph::diff_grid(b.n);
   const float fdt = (float)dt;
-  sph::k_species_gather<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.id, sp->by_row, sp->ca);
+  if (cudaMemsetAsync(sp->nonuniform, 0, sizeof(int), s) != cudaSuccess)
+    return sfail(sp, SPH_E_CUDA, "diffusion set-up failed");
+  auto pack = b.dim == 2 ? sph::k_species_pack<2> : sph::k_species_pack<3>;
+  pack<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.PS, b.id, b.inst_of, b.inst, b.mass, sp->by_row, sp->r0,
+                                        sp->r1, sp->vol, sp->nonuniform);
   for (int k = 0; k < n_steps; ++k) {
-    s1<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.PS, sp->ca, nullptr, sp->cb, b.nbr, b.nbc, b.inst_of,
-                                         b.inst, b.mass, sp->K, fdt);
-    s2<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.PS, sp->cb, sp->ca, sp->ca, b.nbr, b.nbc, b.inst_of,
-                                         b.inst, b.mass, sp->K, fdt);
+    s1<<<grid, sph::kDiffBlock, 0, s>>>(b.n, sp->r0, sp->r1, b.nbr, b.nbc, b.inst_of, b.inst, sp->vol,
+                                         sp->nonuniform, sp->K, fdt);
+    s2<<<grid, sph::kDiffBlock, 0, s>>>(b.n, sp->r1, sp->r0, b.nbr, b.nbc, b.inst_of, b.inst, sp->vol,
+                                         sp->nonuniform, sp->K, fdt);
   }
-  sph::k_species_scatter<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.id, sp->ca, sp->by_row);
+  sph::k_species_unpack<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.id, sp->r0, sp->by_row);
   h->launches += 2 + 2 * (int64_t)n_steps;
   if (cudaGetLastError() != cudaSuccess) return sfail(sp, SPH_E_CUDA, "diffusion launch failed");
   return SPH_OK;
