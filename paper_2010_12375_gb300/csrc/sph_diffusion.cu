@@ -13,12 +13,15 @@
 // One thread per fluid particle walks the fluid part of its neighbour row in the
 // quad-interleaved table, keeping the next index quad in flight. Each call packs, per slot,
 // one 16-byte record R = {qx, qy, qz, bits(C)} (2D: {qx, qy, bits(V), bits(C)}, V = m/rho),
-// so a neighbour costs one 16-byte gather; in 3D the volumes V_j come from a separate
-// array only when they are not all equal within a tank (checked once per call on the
-// device; neighbours never cross tanks, so equal volumes mean V_j = V_i). Stages ping-pong
-// between two record buffers and write only the species word. Pair vectors are exact
-// integer differences scaled by the position quantum. Wall neighbours are skipped: walls
-// carry no species (zero flux). Pairs at zero distance add nothing.
+// so a neighbour costs one 16-byte gather. Stages ping-pong between two record buffers and
+// write only the species word. The pair arithmetic is issue-bound, so it runs two pairs per
+// packed FP32 instruction; pair coordinates are exact integer differences converted with
+// the magic-number add, wrapped on periodic axes only for particles within the support of
+// a periodic face; and when all volumes of a tank are equal (checked once per call on the
+// device; neighbours never cross tanks, so then V_j = V_i) the volume and the kernel
+// constants leave the pair loop. Otherwise V_j comes from the record (2D) or a per-slot
+// array (3D). Wall neighbours are skipped: walls carry no species (zero flux). Pairs at
+// zero distance add nothing.
 //
 // Between calls the species is kept by caller row, so the fluid solver may re-sort the
 // particles; each call gathers it into slot order, runs its steps and scatters it back.
@@ -40,42 +43,93 @@ struct DiffCoef {
 
 inline unsigned diff_grid(int64_t n) { return (unsigned)((n + kDiffBlock - 1) / kDiffBlock); }
 
+// Exactly converted, packed pair coordinate q_i - q_j for lanes (a, b), in length units.
 template <bool PER>
-__device__ __forceinline__ float axis_diff(int qi, int qj, int period, float dq) {
-  return (float)(PER ? wrap_diff(qi - qj, period) : qi - qj) * dq;
+__device__ __forceinline__ float2 pair_coord2(int qi, int qa, int qb, int period, float2 DQ) {
+  return mul2(add2(make_float2(biased_diff<PER>(qi, qa, period), biased_diff<PER>(qi, qb, period)),
+                   f2(-kMagic)),
+              DQ);
 }
 
-// One pair's share of f(C)_i / 2 without the volume V_j; zero at zero distance and
-// beyond 2h.
+// Two pairs (lanes a, b) of the stage sum without the volumes and without the constant
+// factor dwr_a of (dW/dr)/r (and kappa when isotropic):
+// (C_i - C_j) (1 - q/2)^3 w(e_ij). At zero distance r = 0 * inf is NaN, fmaxf turns the
+// kernel factor into 0 and the pair adds nothing.
 template <int D, bool PER, bool ISO>
-__device__ __forceinline__ float diff_term(const Inst& I, const DiffCoef& K, const int4& ri, float ci,
-                                           const int4& a) {
-  const float rx = axis_diff<PER>(ri.x, a.x, I.period[0], I.dq);
-  const float ry = axis_diff<PER>(ri.y, a.y, I.period[1], I.dq);
-  const float rz = D == 3 ? axis_diff<PER>(ri.z, a.z, I.period[2], I.dq) : 0.0f;
-  const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-  const float r = r2 * rsqrtf(r2);
-  const float t = fmaxf(fmaf(r, -0.5f * I.inv_h, 1.0f), 0.0f);
-  const float fw = I.dwr_a * (t * t * t);                         // (dW/dr)/r, Wendland C2
-  float w;
-  if (ISO) {
-    w = K.kappa;
-  } else {
-    float qf = fmaf(K.xx * rx, rx, fmaf(K.yy * ry, ry, 2.0f * K.xy * rx * ry));
-    if (D == 3) qf = fmaf(K.zz * rz, rz, fmaf(2.0f * K.xz * rx, rz, fmaf(2.0f * K.yz * ry, rz, qf)));
-    w = __fdividef(r2, qf);                                        // 1/(e^T D^-1 e)
+__device__ __forceinline__ float2 diff_terms2(const Inst& I, const DiffCoef& K, const int4& ri, float ci,
+                                              const int4& a, const int4& b) {
+  const float2 DQ = f2(I.dq);
+  const float2 rx = pair_coord2<PER>(ri.x, a.x, b.x, I.period[0], DQ);
+  const float2 ry = pair_coord2<PER>(ri.y, a.y, b.y, I.period[1], DQ);
+  float2 rz = f2(0.0f);
+  float2 r2 = fma2(rx, rx, mul2(ry, ry));
+  if (D == 3) {
+    rz = pair_coord2<PER>(ri.z, a.z, b.z, I.period[2], DQ);
+    r2 = fma2(rz, rz, r2);
   }
-  const float term = (ci - i2f(a.w)) * fw * w;
-  return r2 > 0.0f ? term : 0.0f;
+  const float2 r = mul2(r2, rsqrt2(r2));
+  const float2 t = max2(fma2(r, f2(-0.5f * I.inv_h), f2(1.0f)), 0.0f);
+  float2 k = mul2(mul2(t, t), t);
+  if (!ISO) {
+    float2 qf = fma2(mul2(f2(K.xx), rx), rx, fma2(mul2(f2(K.yy), ry), ry, mul2(mul2(f2(2.0f * K.xy), rx), ry)));
+    if (D == 3)
+      qf = fma2(mul2(f2(K.zz), rz), rz,
+                fma2(mul2(f2(2.0f * K.xz), rx), rz, fma2(mul2(f2(2.0f * K.yz), ry), rz, qf)));
+    k = mul2(k, make_float2(__fdividef(r2.x, fmaxf(qf.x, 1e-30f)),       // 1/(e^T D^-1 e)
+                            __fdividef(r2.y, fmaxf(qf.y, 1e-30f))));
+  }
+  return mul2(sub2(f2(ci), make_float2(i2f(a.w), i2f(b.w))), k);
 }
 
-// Volume of slot j: packed in the record in 2D, else the tank's common volume (uniform)
-// or the per-slot array.
-template <int D>
-__device__ __forceinline__ float volume_of(const int4& a, int64_t j, float vi, bool uniform,
-                                           const float* __restrict__ vol) {
-  if (D == 2) return i2f(a.z);
-  return uniform ? vi : vol[j];
+// Sum over the fluid part of row i of V_j-weighted pair terms (VJ: V_j per pair, from the
+// record in 2D or the volume array in 3D; else the caller multiplies by the common volume).
+template <int D, bool PER, bool ISO, bool VJ>
+__device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Inst& I, const DiffCoef& K,
+                                         const int4& ri, float ci, const int4* __restrict__ R,
+                                         const int4* __restrict__ nb4, const float* __restrict__ vol) {
+  const int nq = (nf + 3) >> 2;
+  float2 s = f2(0.0f);
+  int4 nxt = nq ? nb4[i] : make_int4(0, 0, 0, 0);
+  for (int q = 0; q < nq; ++q) {
+    const int4 cq = nxt;
+    if (q + 1 < nq) nxt = nb4[(int64_t)(q + 1) * n + i];   // next quad in flight
+    const int sl = q << 2;
+    const int j1 = sl + 1 < nf ? cq.y : cq.x, j2 = sl + 2 < nf ? cq.z : cq.x, j3 = sl + 3 < nf ? cq.w : cq.x;
+    const int4 a0 = R[cq.x], a1 = R[j1], a2 = R[j2], a3 = R[j3];
+    float2 w01 = make_float2(1.0f, sl + 1 < nf ? 1.0f : 0.0f);
+    float2 w23 = make_float2(sl + 2 < nf ? 1.0f : 0.0f, sl + 3 < nf ? 1.0f : 0.0f);
+    if (VJ) {
+      if (D == 2) {
+        w01 = mul2(w01, make_float2(i2f(a0.z), i2f(a1.z)));
+        w23 = mul2(w23, make_float2(i2f(a2.z), i2f(a3.z)));
+      } else {
+        w01 = mul2(w01, make_float2(vol[cq.x], vol[j1]));
+        w23 = mul2(w23, make_float2(vol[j2], vol[j3]));
+      }
+    }
+    s = fma2(diff_terms2<D, PER, ISO>(I, K, ri, ci, a0, a1), w01, s);
+    s = fma2(diff_terms2<D, PER, ISO>(I, K, ri, ci, a2, a3), w23, s);
+  }
+  return s.x + s.y;
+}
+
+// Row sum with the periodic wrap only where a neighbour can lie across a periodic
+// boundary: particles farther than the support from every periodic face take the plain
+// differences.
+template <int D, bool PER, bool ISO, bool VJ>
+__device__ __forceinline__ float row_sum_any(int64_t n, int64_t i, int nf, const Inst& I, const DiffCoef& K,
+                                             const int4& ri, float ci, const int4* __restrict__ R,
+                                             const int4* __restrict__ nb4, const float* __restrict__ vol) {
+  if (PER) {
+    const int reach = (int)ceilf(sqrtf((float)I.R2)) + 2;          // support radius in quanta
+    const int q[3] = {ri.x, ri.y, ri.z};
+    bool near_face = false;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (I.period[a]) near_face |= q[a] < reach || q[a] >= I.period[a] - reach;
+    if (near_face) return row_sum<D, true, ISO, VJ>(n, i, nf, I, K, ri, ci, R, nb4, vol);
+  }
+  return row_sum<D, false, ISO, VJ>(n, i, nf, I, K, ri, ci, R, nb4, vol);
 }
 
 template <int D, bool PER, bool ISO, bool SECOND>
@@ -87,31 +141,18 @@ k_diffusion_stage(int64_t n, const int4* __restrict__ Rin, int4* __restrict__ Ro
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Inst& I = inst[inst_of ? inst_of[i] : 0];
-  const bool uniform = D == 2 || *nonuniform == 0;
   const int4 ri = Rin[i];
   const float ci = i2f(ri.w);
-  const float vi = D == 2 ? i2f(ri.z) : vol[i];
   const int nf = (int)(nbc[i] & 0xffffu);
   const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
-  const int nq = (nf + 3) >> 2;
-  float s0 = 0.0f, s1 = 0.0f;
-  int4 nxt = nq ? nb4[i] : make_int4(0, 0, 0, 0);
-  for (int q = 0; q < nq; ++q) {
-    const int4 cq = nxt;
-    if (q + 1 < nq) nxt = nb4[(int64_t)(q + 1) * n + i];   // next quad in flight
-    const int sl = q << 2;
-    const int j1 = sl + 1 < nf ? cq.y : cq.x, j2 = sl + 2 < nf ? cq.z : cq.x, j3 = sl + 3 < nf ? cq.w : cq.x;
-    const int4 a0 = Rin[cq.x], a1 = Rin[j1], a2 = Rin[j2], a3 = Rin[j3];
-    const float t0 = volume_of<D>(a0, cq.x, vi, uniform, vol) * diff_term<D, PER, ISO>(I, K, ri, ci, a0);
-    const float t1 = volume_of<D>(a1, j1, vi, uniform, vol) * diff_term<D, PER, ISO>(I, K, ri, ci, a1);
-    const float t2 = volume_of<D>(a2, j2, vi, uniform, vol) * diff_term<D, PER, ISO>(I, K, ri, ci, a2);
-    const float t3 = volume_of<D>(a3, j3, vi, uniform, vol) * diff_term<D, PER, ISO>(I, K, ri, ci, a3);
-    s0 += t0;
-    s1 += sl + 1 < nf ? t1 : 0.0f;
-    s0 += sl + 2 < nf ? t2 : 0.0f;
-    s1 += sl + 3 < nf ? t3 : 0.0f;
+  float sum;
+  if (*nonuniform == 0) {          // equal volumes within the tank: V_j = V_i
+    const float vi = D == 2 ? i2f(ri.z) : vol[i];
+    sum = vi * row_sum_any<D, PER, ISO, false>(n, i, nf, I, K, ri, ci, Rin, nb4, vol);
+  } else {
+    sum = row_sum_any<D, PER, ISO, true>(n, i, nf, I, K, ri, ci, Rin, nb4, vol);
   }
-  const float rate = 2.0f * (s0 + s1);
+  const float rate = 2.0f * (ISO ? I.dwr_a * K.kappa : I.dwr_a) * sum;
   const float next = fmaf(dt, rate, ci);
   // stage 2 reads C^n from the output record's own slot (written by no other thread)
   const float out = SECOND ? 0.5f * (i2f(Rout[i].w) + next) : next;
@@ -136,12 +177,10 @@ __global__ void k_species_pack(int64_t n, const int4* __restrict__ P, const int*
   const int4 r = make_int4(p.x, p.y, D == 2 ? f2i(v) : p.z, c);
   R0[i] = r;
   R1[i] = r;
-  if (D == 3) {
-    vol[i] = v;
-    const int64_t f = I.fluid_begin;                                  // the tank's first slot
-    const float vf = __fdividef(mass ? mass[f] : I.mass, I.rho0 + i2f(P[f].w));
-    if (vf != v) atomicOr(nonuniform, 1);
-  }
+  if (D == 3) vol[i] = v;
+  const int64_t f = I.fluid_begin;                                    // the tank's first slot
+  const float vf = __fdividef(mass ? mass[f] : I.mass, I.rho0 + i2f(P[f].w));
+  if (vf != v) atomicOr(nonuniform, 1);
 }
 
 __global__ void k_species_unpack(int64_t n, const int* __restrict__ id, const int4* __restrict__ R,
