@@ -43,11 +43,20 @@ TRAFFIC_BYTES_PER_PARTICLE = 390.07
 TRAFFIC_SOURCE_HASH = "895398bd41154fbc"
 
 
-def kernel_source_hash():
-    """Hash of the pressure relaxation's sources with comments and blank lines removed, so
-    the stored traffic figure stays valid across comment edits and lapses on code edits."""
+# DRAM bytes (read + write) per particle of one diffusion stage launch, from the ncu capture
+# of k_diffusion_stage on the 120^3 block (both stages, 652.8 MB per launch at 1.728M
+# particles); traffic is per particle on the lattice, so it scales to the 200^3 block.
+DIFF_TRAFFIC_BYTES_PER_PARTICLE = 377.8
+DIFF_TRAFFIC_SOURCE_HASH = "652b43b7c07ea298"
+DIFF_SOURCES = ("sph_common.cuh", "sph_diffusion.cu")
+
+
+def kernel_source_hash(files=("sph_common.cuh", "sph_relax.cuh", "sph_relax_pr.cu")):
+    """Hash of a kernel's sources with comments and blank lines removed, so a stored
+    traffic figure stays valid across comment edits and lapses on code edits (default:
+    the pressure relaxation)."""
     h = hashlib.sha256()
-    for f in ("sph_common.cuh", "sph_relax.cuh", "sph_relax_pr.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2010_12375_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()
@@ -518,7 +527,9 @@ def run_diffusion(args, stream):
            "clocks": clk,
            "gpu_launches": 2 * args.steps + 2,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak,
+                        "traffic": (DIFF_TRAFFIC_BYTES_PER_PARTICLE * n
+                                    if kernel_source_hash(DIFF_SOURCES) == DIFF_TRAFFIC_SOURCE_HASH else None),
                         "kernel": "k_diffusion_stage", "stage_ms": stage_ms,
                         "algorithmic_bytes": alg, "peak_source": src}}
     if not args.no_cpu_baseline:
