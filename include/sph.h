@@ -12,7 +12,8 @@
  * with a Wendland C2 kernel, dummy-particle walls and gravity; optionally the
  * transport velocity of Eq. transport (sph_params.p_transport) for flows without
  * free surface. A species carried by the fluid particles diffuses by Eq. grad-laplace
- * with two-stage Runge-Kutta steps (sph_species_*, sph_diffusion_step).
+ * with two-stage Runge-Kutta steps (sph_species_*, sph_diffusion_step) and reacts by the
+ * split QSS scheme of the reaction-diffusion models (sph_reaction_step).
  *
  * Conventions shared by every entry point
  *  - Return value: SPH_OK (0) or a negative SPH_E_* code. No call aborts the
@@ -345,6 +346,43 @@ int sph_species_get(sph_handle* h, sph_species* sp, double* C, void* stream);
  * Positions, velocities and densities are not changed. Asynchronous on stream: two
  * kernel launches per step plus a gather and a scatter of the species per call. */
 int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_steps, void* stream);
+
+/* ---- Reaction step of reaction-diffusion (Sec. "SPH method for reaction-diffusion",
+ * "Reaction-by-reaction splitting") ---------------------------------------------------
+ * Operator splitting separates the diffusion of the species V (sph_diffusion_step) from the
+ * per-particle ODE system dV/dt = I(V, w), dw/dt = g(V, w) (Eq. ode-system) with a gating
+ * variable w held by the species object (starts at 0). The caller composes the two, e.g.
+ * alternating sph_diffusion_step and sph_reaction_step with the same dt.
+ *   model SPH_REACTION_FN, FitzHugh-Nagumo (Eq. fhn):
+ *     I = -V (V - a)(V - 1) - w,   g = eps0 (beta V - gamma w - sigma)
+ *   model SPH_REACTION_AP, Aliev-Panfilov (Eq. a-p):
+ *     I = -k V (V - a)(V - 1) - w V,   g = eps (-k V (V - b - 1) - w),
+ *     eps = eps0 + mu1 w / (mu2 + V)
+ * One step of length dt applies R_V(dt/2), R_w(dt/2), R_w(dt/2), R_V(dt/2) (Eq.
+ * ode-spliting-2rd), each reaction advancing one variable with the other fixed by the
+ * quasi-steady-state update y <- y e^(-p dt) + (q/p)(1 - e^(-p dt)) (Eq. ode-qss), with p and
+ * q at the reaction's starting value. The split into production q and loss p y:
+ *   FN  R_V: q = -w, p = (V - a)(V - 1);        R_w: q = eps0 (beta V - sigma), p = eps0 gamma
+ *   AP  R_V: q = 0,  p = k (V - a)(V - 1) + w;  R_w: q = -eps k V (V - b - 1), p = eps
+ * (1 - e^(-p dt))/p is taken as dt when |p dt| < 1e-12. Because p and q are frozen over a
+ * reaction, the step is first-order accurate where p depends on the reacting variable.
+ * Unused parameters of a model are ignored. FP32 on the device. */
+#define SPH_REACTION_FN 1
+#define SPH_REACTION_AP 2
+typedef struct {
+  int32_t model;                  /* SPH_REACTION_FN or SPH_REACTION_AP */
+  double a, b, k, eps0, mu1, mu2, beta, gamma, sigma;
+} sph_reaction;
+
+/* w: host or device, n_fluid doubles in caller row order. Synchronous. */
+int sph_species_set_gate(sph_handle* h, sph_species* sp, const double* w, void* stream);
+/* w: host or device, n_fluid doubles in caller row order. Synchronous. */
+int sph_species_get_gate(sph_handle* h, sph_species* sp, double* w, void* stream);
+/* n_steps splitting steps of size dt (> 0, finite) of every particle's (V, w), V being the
+ * species. No neighbour table needed. Unknown model or non-finite parameters:
+ * SPH_E_INVALID. Asynchronous on stream: one kernel launch per call. */
+int sph_reaction_step(sph_handle* h, sph_species* sp, const sph_reaction* r, double dt, int32_t n_steps,
+                      void* stream);
 
 /* Allocation-free diagnostics. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory (code running inside

@@ -202,6 +202,54 @@ __global__ void k_species_export(int64_t n, const float* __restrict__ src, doubl
   if (i < n) dst[i] = (double)src[i];
 }
 
+// ---- reaction step (Sec. "Reaction-by-reaction splitting") ---------------------------------
+// Per particle: Eq. ode-spliting-2rd applies R_V(dt/2), R_w(dt/2), R_w(dt/2), R_V(dt/2); each
+// reaction writes its right-hand side as q - p y (Eq. ode-new-form) and takes the QSS update
+// of Eq. ode-qss with p and q at the reaction's starting value. Production/loss split:
+//   FitzHugh-Nagumo (Eq. fhn)  R_V: q = -w, p = (V - a)(V - 1);  R_w: q = eps0 (beta V - sigma),
+//                              p = eps0 gamma
+//   Aliev-Panfilov (Eq. a-p)   R_V: q = 0, p = k (V - a)(V - 1) + w;  R_w: q = -eps k V (V - b - 1),
+//                              p = eps = eps0 + mu1 w / (mu2 + V)
+struct ReactCoef {
+  int model;
+  float a, b, k, eps0, mu1, mu2, beta, gamma, sigma;
+};
+
+// y e^(-p dt) + q (1 - e^(-p dt))/p, the fraction taken as dt when |p dt| < 1e-12.
+__device__ __forceinline__ float qss(float y, float q, float p, float dt) {
+  const float x = -p * dt;
+  const float frac = fabsf(x) < 1e-12f ? dt : -expm1f(x) / p;
+  return fmaf(y, expf(x), q * frac);
+}
+
+__device__ __forceinline__ float react_V(float V, float w, const ReactCoef& R, float dt) {
+  if (R.model == 1) return qss(V, -w, (V - R.a) * (V - 1.0f), dt);
+  return qss(V, 0.0f, fmaf(R.k * (V - R.a), V - 1.0f, w), dt);
+}
+
+__device__ __forceinline__ float react_w(float V, float w, const ReactCoef& R, float dt) {
+  if (R.model == 1) return qss(w, R.eps0 * (R.beta * V - R.sigma), R.eps0 * R.gamma, dt);
+  const float eps = R.eps0 + R.mu1 * w / (R.mu2 + V);
+  return qss(w, -eps * R.k * V * (V - R.b - 1.0f), eps, dt);
+}
+
+// All steps of one call in registers: 16 bytes of HBM traffic per particle per call.
+__global__ void k_reaction(int64_t n, float* __restrict__ V, float* __restrict__ w, ReactCoef R, float dt,
+                           int n_steps) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v = V[i], g = w[i];
+  const float h = 0.5f * dt;
+  for (int s = 0; s < n_steps; ++s) {
+    v = react_V(v, g, R, h);
+    g = react_w(v, g, R, h);
+    g = react_w(v, g, R, h);
+    v = react_V(v, g, R, h);
+  }
+  V[i] = v;
+  w[i] = g;
+}
+
 using StageFn = void (*)(int64_t, const int4*, int4*, const int*, const uint32_t*, const int*, const Inst*,
                          const float*, const int*, DiffCoef, float);
 
@@ -226,6 +274,7 @@ struct sph_species {
   sph::DiffCoef K{};
   bool iso = false;
   float* by_row = nullptr;     // [n] species by caller row (kept between calls)
+  float* gate = nullptr;       // [n] gating variable w of the reaction step, by caller row
   int4* r0 = nullptr;          // [n] slot records carrying C^n
   int4* r1 = nullptr;          // [n] slot records carrying C*
   float* vol = nullptr;        // [n] slot volumes m/rho (3D)
@@ -320,11 +369,13 @@ int sph_species_create(sph_handle* h, const double* D, sph_species** out) {
         cudaMalloc(&sp->r1, sizeof(int4) * n) != cudaSuccess ||
         cudaMalloc(&sp->vol, sizeof(float) * n) != cudaSuccess ||
         cudaMalloc(&sp->nonuniform, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&sp->gate, sizeof(float) * n) != cudaSuccess ||
         cudaMalloc(&sp->stage, sizeof(double) * n) != cudaSuccess) {
       cudaGetLastError();
       return sfail(sp, SPH_E_OOM, "device allocation of the species failed");
     }
-    if (cudaMemset(sp->by_row, 0, sizeof(float) * n) != cudaSuccess)
+    if (cudaMemset(sp->by_row, 0, sizeof(float) * n) != cudaSuccess ||
+        cudaMemset(sp->gate, 0, sizeof(float) * n) != cudaSuccess)
       return sfail(sp, SPH_E_CUDA, "clearing the species failed");
   }
   return SPH_OK;
@@ -337,17 +388,22 @@ void sph_species_destroy(sph_species* sp) {
   cudaFree(sp->r1);
   cudaFree(sp->vol);
   cudaFree(sp->nonuniform);
+  cudaFree(sp->gate);
   cudaFree(sp->stage);
   delete sp;
 }
 
 const char* sph_species_last_error(const sph_species* sp) { return sp ? sp->err.c_str() : "null species"; }
 
-int sph_species_set(sph_handle* h, sph_species* sp, const double* C, void* stream) {
+}  // extern "C"
+
+namespace {
+
+int species_upload(sph_handle* h, sph_species* sp, const double* C, float* dst, void* stream) {
   if (!h || !sp) return SPH_E_INVALID;
   if (sp->n != h->b.n || sp->dim != h->b.dim) return sfail(sp, SPH_E_INVALID, "species belongs to another handle");
   if (sp->n == 0) return SPH_OK;
-  if (!C) return sfail(sp, SPH_E_INVALID, "C is required");
+  if (!C) return sfail(sp, SPH_E_INVALID, "the array is required");
   cudaStream_t s = (cudaStream_t)stream;
   const double* src = C;
   if (!device_pointer(C)) {
@@ -355,27 +411,68 @@ int sph_species_set(sph_handle* h, sph_species* sp, const double* C, void* strea
       return sfail(sp, SPH_E_CUDA, "copy of the species failed");
     src = sp->stage;
   }
-  sph::k_species_import<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, s>>>(sp->n, src, sp->by_row);
+  sph::k_species_import<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, s>>>(sp->n, src, dst);
   ++h->launches;
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return sfail(sp, SPH_E_CUDA, "species upload failed");
   return SPH_OK;
 }
 
-int sph_species_get(sph_handle* h, sph_species* sp, double* C, void* stream) {
+int species_download(sph_handle* h, sph_species* sp, const float* src, double* C, void* stream) {
   if (!h || !sp) return SPH_E_INVALID;
   if (sp->n != h->b.n || sp->dim != h->b.dim) return sfail(sp, SPH_E_INVALID, "species belongs to another handle");
   if (sp->n == 0) return SPH_OK;
-  if (!C) return sfail(sp, SPH_E_INVALID, "C is required");
+  if (!C) return sfail(sp, SPH_E_INVALID, "the array is required");
   cudaStream_t s = (cudaStream_t)stream;
   const bool dev = device_pointer(C);
   double* dst = dev ? C : sp->stage;
-  sph::k_species_export<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, s>>>(sp->n, sp->by_row, dst);
+  sph::k_species_export<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, s>>>(sp->n, src, dst);
   ++h->launches;
   if (!dev && cudaMemcpyAsync(C, sp->stage, sizeof(double) * sp->n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return sfail(sp, SPH_E_CUDA, "copy of the species failed");
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return sfail(sp, SPH_E_CUDA, "species download failed");
+  return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sph_species_set(sph_handle* h, sph_species* sp, const double* C, void* stream) {
+  return species_upload(h, sp, C, sp ? sp->by_row : nullptr, stream);
+}
+
+int sph_species_get(sph_handle* h, sph_species* sp, double* C, void* stream) {
+  return species_download(h, sp, sp ? sp->by_row : nullptr, C, stream);
+}
+
+int sph_species_set_gate(sph_handle* h, sph_species* sp, const double* w, void* stream) {
+  return species_upload(h, sp, w, sp ? sp->gate : nullptr, stream);
+}
+
+int sph_species_get_gate(sph_handle* h, sph_species* sp, double* w, void* stream) {
+  return species_download(h, sp, sp ? sp->gate : nullptr, w, stream);
+}
+
+int sph_reaction_step(sph_handle* h, sph_species* sp, const sph_reaction* r, double dt, int32_t n_steps,
+                      void* stream) {
+  if (!h || !sp) return SPH_E_INVALID;
+  if (sp->n != h->b.n || sp->dim != h->b.dim) return sfail(sp, SPH_E_INVALID, "species belongs to another handle");
+  if (!r || (r->model != SPH_REACTION_FN && r->model != SPH_REACTION_AP))
+    return sfail(sp, SPH_E_INVALID, "unknown reaction model");
+  const double vals[] = {r->a, r->b, r->k, r->eps0, r->mu1, r->mu2, r->beta, r->gamma, r->sigma};
+  for (double v : vals)
+    if (!std::isfinite(v)) return sfail(sp, SPH_E_INVALID, "reaction parameters must be finite");
+  if (!(std::isfinite(dt) && dt > 0.0) || n_steps < 0) return sfail(sp, SPH_E_INVALID, "dt must be > 0 and n_steps >= 0");
+  if (sp->n == 0 || n_steps == 0) return SPH_OK;
+  const sph::ReactCoef R{r->model, (float)r->a, (float)r->b, (float)r->k, (float)r->eps0, (float)r->mu1,
+                         (float)r->mu2, (float)r->beta, (float)r->gamma, (float)r->sigma};
+  cudaStream_t s = (cudaStream_t)stream;
+  sph::k_reaction<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, s>>>(sp->n, sp->by_row, sp->gate, R, (float)dt,
+                                                                    n_steps);
+  ++h->launches;
+  if (cudaGetLastError() != cudaSuccess) return sfail(sp, SPH_E_CUDA, "reaction launch failed");
   return SPH_OK;
 }
 

@@ -39,7 +39,8 @@ EXPORTS = [
     "sph_learned_last_error", "sph_learned_set_weights", "sph_learned_get_weights",
     "sph_learned_set_fused", "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
     "sph_species_create", "sph_species_destroy", "sph_species_last_error", "sph_species_set",
-    "sph_species_get", "sph_diffusion_step",
+    "sph_species_get", "sph_diffusion_step", "sph_species_set_gate", "sph_species_get_gate",
+    "sph_reaction_step",
 ]
 
 
@@ -86,6 +87,14 @@ class SphInfo(ctypes.Structure):
 
 
 _lib = None
+
+
+SPH_REACTION_FN, SPH_REACTION_AP = 1, 2
+
+
+class SphReaction(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32)] + [(f, ctypes.c_double) for f in
+                                               ("a", "b", "k", "eps0", "mu1", "mu2", "beta", "gamma", "sigma")]
 
 
 class SphError(RuntimeError):
@@ -147,6 +156,9 @@ def load():
         "sph_species_set": (i32, [P, P, P, P]),
         "sph_species_get": (i32, [P, P, P, P]),
         "sph_diffusion_step": (i32, [P, P, dbl, i32, P]),
+        "sph_species_set_gate": (i32, [P, P, P, P]),
+        "sph_species_get_gate": (i32, [P, P, P, P]),
+        "sph_reaction_step": (i32, [P, P, ctypes.POINTER(SphReaction), dbl, i32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -514,6 +526,34 @@ def sph_species_get(h, sp, n, stream=None, out=None):
     C = np.empty(n, dtype=np.float64) if out is None else out
     _scheck(lib, sp, lib.sph_species_get(h, sp, _ptr(C), _stream(stream)))
     return C
+
+
+def sph_species_set_gate(h, sp, w, stream=None):
+    lib = load()
+    w = _f64(w)
+    _scheck(lib, sp, lib.sph_species_set_gate(h, sp, _ptr(w), _stream(stream)))
+
+
+def sph_species_get_gate(h, sp, n, stream=None, out=None):
+    lib = load()
+    w = np.empty(n, dtype=np.float64) if out is None else out
+    _scheck(lib, sp, lib.sph_species_get_gate(h, sp, _ptr(w), _stream(stream)))
+    return w
+
+
+def reaction_from(model, **params) -> SphReaction:
+    """SphReaction for model SPH_REACTION_FN or SPH_REACTION_AP; other fields default to 0."""
+    r = SphReaction()
+    r.model = int(model)
+    for k, v in params.items():
+        setattr(r, k, float(v))
+    return r
+
+
+def sph_reaction_step(h, sp, reaction, dt, n_steps=1, stream=None):
+    lib = load()
+    _scheck(lib, sp, lib.sph_reaction_step(h, sp, ctypes.byref(reaction), float(dt), int(n_steps),
+                                           _stream(stream)))
 
 
 def sph_diffusion_step(h, sp, dt, n_steps=1, stream=None):
