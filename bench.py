@@ -47,8 +47,10 @@ TRAFFIC_SOURCE_HASH = "895398bd41154fbc"
 # of k_diffusion_stage on the 120^3 block (both stages, 652.8 MB per launch at 1.728M
 # particles); traffic is per particle on the lattice, so it scales to the 200^3 block.
 DIFF_TRAFFIC_BYTES_PER_PARTICLE = 377.8
-DIFF_TRAFFIC_SOURCE_HASH = "652b43b7c07ea298"
-DIFF_SOURCES = ("sph_common.cuh", "sph_diffusion.cu")
+DIFF_TRAFFIC_SOURCE_HASH = "8c0ec31d91465a02"
+# the stage kernel and its device helpers: the rest of the file (pack/unpack, the reaction
+# step, the host API) does not change the captured launches
+DIFF_SOURCES = ("sph_common.cuh", ("sph_diffusion.cu", "float2 pair_coord2(", "Per call: records of both buffers"))
 
 
 def kernel_source_hash(files=("sph_common.cuh", "sph_relax.cuh", "sph_relax_pr.cu")):
@@ -57,10 +59,18 @@ def kernel_source_hash(files=("sph_common.cuh", "sph_relax.cuh", "sph_relax_pr.c
     the pressure relaxation)."""
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_2010_12375_gb300", "csrc", f)) as fh:
+        # a (file, first, last) entry hashes only the lines from the first one containing
+        # `first` up to the first one after it containing `last` (that line excluded)
+        name, first, last = (f, None, None) if isinstance(f, str) else f
+        inside = first is None
+        with open(os.path.join(ROOT, "paper_2010_12375_gb300", "csrc", name)) as fh:
             for line in fh:
+                if not inside and first in line:
+                    inside = True
+                elif inside and last is not None and last in line:
+                    break
                 code = line.split("//", 1)[0].rstrip()
-                if code:
+                if inside and code:
                     h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
