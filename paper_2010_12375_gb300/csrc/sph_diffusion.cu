@@ -1,4 +1,6 @@
-// Species diffusion on the fluid particles (Sec. "Schemes for thermal and mass diffusion").
+// Species diffusion on the fluid particles (Sec. "Schemes for thermal and mass diffusion")
+// and the reaction step of reaction-diffusion (Sec. "Reaction-by-reaction splitting"; its
+// kernel and readings are described where it is defined, below the diffusion kernels).
 //
 //   dC_i/dt = 2 sum_j (m_j/rho_j) (C_i - C_j) w(e_ij) (1/r_ij) dW/dr_ij      (Eq. grad-laplace)
 //   w(e)    = 1/(L^-1 e)^2 = 1/(e^T D^-1 e),  D = L L^T                        (Eq. chol)
@@ -27,7 +29,6 @@
 // particles; each call gathers it into slot order, runs its steps and scatters it back.
 #include <cmath>
 #include <string>
-#include <vector>
 
 #include "sph_handle.h"
 
