@@ -517,6 +517,24 @@ def run_diffusion(args, stream):
     ms_k = timed(args.steps)
     ms_2k = timed(2 * args.steps)
     clk = clocks.stop()
+    # the reaction step (FitzHugh-Nagumo, split QSS) on the same particles: a one-step call
+    # moves 16 bytes per particle (HBM-bound); a 50-step call keeps (V, w) in registers
+    fn = sph.reaction_from(sph.SPH_REACTION_FN, a=0.1, eps0=0.08, beta=1.0, gamma=1.0, sigma=0.0)
+
+    def timed_reaction(k, reps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            sph.sph_reaction_step(sim.handle, sp, fn, 0.01, k, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    for _ in range(args.warmup):
+        timed_reaction(1, 1)
+    r1_ms = timed_reaction(1, 20)
+    r50_ms = timed_reaction(50, 5)
     sph.sph_species_destroy(sp)
     sim.close()
     stage_ms = (ms_2k - ms_k) / (2 * args.steps)        # per stage kernel, gather/scatter removed
@@ -541,7 +559,13 @@ def run_diffusion(args, stream):
                         "traffic": (DIFF_TRAFFIC_BYTES_PER_PARTICLE * n
                                     if kernel_source_hash(DIFF_SOURCES) == DIFF_TRAFFIC_SOURCE_HASH else None),
                         "kernel": "k_diffusion_stage", "stage_ms": stage_ms,
-                        "algorithmic_bytes": alg, "peak_source": src}}
+                        "algorithmic_bytes": alg, "peak_source": src},
+           "reaction": {"kernel": "k_reaction", "model": "FitzHugh-Nagumo",
+                        "one_step_call_ms": r1_ms,
+                        "one_step_call_GBps": 16 * n / (r1_ms * 1e-3) / 1e9,
+                        "one_step_call_frac_of_hbm": 16 * n / (r1_ms * 1e-3) / 1e9 / peak,
+                        "fifty_step_call_ms": r50_ms,
+                        "particle_steps_per_s_at_50": n * 50 / (r50_ms * 1e-3)}}
     if not args.no_cpu_baseline:
         from oracle import diffusion as odf, wcsph as ow
         small = wk.diffusion_block_3d(24, kappa=1.0, sigma=0.1)
