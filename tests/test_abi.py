@@ -86,3 +86,22 @@ def test_create_without_gpu_fails_cleanly(lib):
     with pytest.raises(lib.SphError) as e:
         lib.Simulation(wk.dam_break_2d(n_per_H=5))
     assert e.value.code in (lib.SPH_E_CUDA, lib.SPH_E_OOM)
+
+
+def test_species_and_reaction_entry_points_reject_null_handles(lib):
+    # argument checks run before any CUDA call, so they are testable without a GPU
+    import ctypes
+    L = lib.load()
+    out = ctypes.c_void_p(123)
+    D = (ctypes.c_double * 4)(1.0, 0.0, 0.0, 1.0)
+    assert L.sph_species_create(None, D, ctypes.byref(out)) == lib.SPH_E_INVALID
+    assert out.value is None                                  # cleared on failure
+    assert L.sph_species_create(None, D, None) == lib.SPH_E_INVALID
+    r = lib.reaction_from(lib.SPH_REACTION_FN, a=0.1)
+    assert L.sph_reaction_step(None, None, ctypes.byref(r), 0.1, 1, None) == lib.SPH_E_INVALID
+    assert L.sph_diffusion_step(None, None, 0.1, 1, None) == lib.SPH_E_INVALID
+    buf = (ctypes.c_double * 4)()
+    for fn in (L.sph_species_set, L.sph_species_get, L.sph_species_set_gate, L.sph_species_get_gate):
+        assert fn(None, None, buf, None) == lib.SPH_E_INVALID
+    L.sph_species_destroy(None)                               # a no-op
+    assert L.sph_species_last_error(None) == b"null species"
