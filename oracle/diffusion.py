@@ -22,6 +22,10 @@ Readings where the paper is silent or inconsistent (the same readings the CUDA p
       on the fluid particles; wall particles carry none and exchange nothing (zero flux
       through walls). Pairs at zero distance contribute nothing (as reading R6 of the
       fluid oracle). The kernel-corrected form (Eq. grad-laplace-renormalize) is not taken.
+  R17 Per-particle diffusivity: D_i = s_i D with s_i > 0. Then L~_i = L^-1/sqrt(s_i), the
+      harmonic combination of R13 gives L~_ij = L^-1 2/(sqrt(s_i) + sqrt(s_j)), and the pair
+      weight is ((sqrt(s_i) + sqrt(s_j))/2)^2 / (e^T D^-1 e): the squared mean of the square
+      roots, which equals s at a pair of equal factors.
   R14 RK2 is Heun's form: C* = C^n + dt f(C^n), C^{n+1} = (C^n + C* + dt f(C*))/2. The
       operator is linear and autonomous, so every two-stage second-order Runge-Kutta scheme
       gives the same C^{n+1} up to rounding.
@@ -58,8 +62,19 @@ def fluid_pairs(x: np.ndarray, prm: o.Params):
     return I, J
 
 
-def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params) -> np.ndarray:
-    """Eq. grad-laplace under R13: dC_i/dt for every fluid particle i."""
+def pair_scale(scale, I, J):
+    """R17: pair factor of per-particle diffusivity factors s (D_i = s_i D). With
+    L~_i = L^-1 / sqrt(s_i), the harmonic combination of R13 is L^-1 2/(sqrt(s_i) + sqrt(s_j)),
+    so the pair weight gains ((sqrt(s_i) + sqrt(s_j))/2)^2."""
+    if scale is None:
+        return 1.0
+    r = np.sqrt(np.asarray(scale, dtype=np.float64))
+    return (0.5 * (r[I] + r[J])) ** 2
+
+
+def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params, scale=None) -> np.ndarray:
+    """Eq. grad-laplace under R13 (and R17 with per-particle factors `scale`): dC_i/dt for
+    every fluid particle i."""
     rij = o.min_image(x[I] - x[J], prm.period)
     r2 = np.sum(rij * rij, axis=1)
     r = np.sqrt(r2)
@@ -69,26 +84,26 @@ def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params) -> np.ndarray:
     quad = np.einsum("pa,ab,pb->p", rij, Dinv, rij)                  # r^2 e^T D^-1 e
     w = np.zeros_like(r)
     w[ok] = r2[ok] / quad[ok]                                        # 1/(L~ e)^2
-    terms = 2.0 * vol[J] * (C[I] - C[J]) * fw * w
+    terms = 2.0 * vol[J] * (C[I] - C[J]) * fw * w * pair_scale(scale, I, J)
     out = np.zeros(x.shape[0])
     np.add.at(out, I, terms)
     return out
 
 
-def rk2_step(x, C, vol, I, J, Dinv, dt: float, prm: o.Params) -> np.ndarray:
+def rk2_step(x, C, vol, I, J, Dinv, dt: float, prm: o.Params, scale=None) -> np.ndarray:
     """One step of R14 (Heun)."""
-    Cs = C + dt * diffusion_rate(x, C, vol, I, J, Dinv, prm)
-    return 0.5 * (C + Cs + dt * diffusion_rate(x, Cs, vol, I, J, Dinv, prm))
+    Cs = C + dt * diffusion_rate(x, C, vol, I, J, Dinv, prm, scale)
+    return 0.5 * (C + Cs + dt * diffusion_rate(x, Cs, vol, I, J, Dinv, prm, scale))
 
 
-def run(x, C, m, rho, D, dt: float, n_steps: int, prm: o.Params) -> np.ndarray:
+def run(x, C, m, rho, D, dt: float, n_steps: int, prm: o.Params, scale=None) -> np.ndarray:
     """n_steps RK2 steps of the species C on static particles (positions x, masses m,
-    densities rho)."""
+    densities rho; per-particle diffusivity factors `scale`, R17)."""
     x = np.asarray(x, dtype=np.float64)
     C = np.asarray(C, dtype=np.float64).copy()
     vol = np.asarray(m, dtype=np.float64) / np.asarray(rho, dtype=np.float64)
     Dinv = tensor_inverse(D, prm.dim)
     I, J = fluid_pairs(x, prm)
     for _ in range(int(n_steps)):
-        C = rk2_step(x, C, vol, I, J, Dinv, dt, prm)
+        C = rk2_step(x, C, vol, I, J, Dinv, dt, prm, scale)
     return C

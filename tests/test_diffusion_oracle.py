@@ -182,3 +182,48 @@ def test_tensor_inverse_rejects_bad_tensors():
         df.tensor_inverse([[1.0, 2.0], [2.0, 1.0]], 2)          # indefinite
     D = np.array([[3.0, 1.0], [1.0, 2.0]])
     np.testing.assert_allclose(df.tensor_inverse(D, 2) @ D, np.eye(2), atol=1e-14)
+
+
+def _centre_rate_scaled(h_over_dp, C_of, s_of, x0):
+    """Rate at the lattice point nearest x0 (2D, isotropic D = I) with per-particle
+    factors s(x) and field C(x)."""
+    dp = 1.0
+    k = int(math.ceil(2 * h_over_dp)) + 1
+    ax = np.arange(-k, k + 1, dtype=np.float64)
+    X = np.stack([g.ravel() for g in np.meshgrid(ax, ax, indexing="ij")], 1) * dp + np.asarray(x0)
+    i0 = int(np.argmin(np.sum((X - np.asarray(x0)) ** 2, axis=1)))
+    J = np.array([j for j in range(X.shape[0]) if j != i0])
+    I = np.full(J.size, i0)
+    prm = _params(2, h_over_dp * dp, dp, -np.full(2, 100.0), np.full(2, 100.0), [False, False])
+    vol = np.full(X.shape[0], dp * dp)
+    return df.diffusion_rate(X, C_of(X), vol, I, J, np.eye(2), prm, scale=s_of(X))[i0]
+
+
+def test_per_particle_diffusivity_gives_the_variable_coefficient_operator():
+    # reading R17: with D_i = s_i I the operator tends to div(s grad C) = s lap C + grad s . grad C
+    # C = x^2 + y^2 / 2, s = 2 + 0.05 x + 0.02 y at x0 = (3, -2):
+    # lap C = 3, grad C = (6, -2), grad s = (0.05, 0.02) -> s lap C + grad s . grad C
+    C_of = lambda X: X[:, 0] ** 2 + 0.5 * X[:, 1] ** 2
+    s_of = lambda X: 2.0 + 0.05 * X[:, 0] + 0.02 * X[:, 1]
+    x0 = (3.0, -2.0)
+    exact = (2.0 + 0.15 - 0.04) * 3.0 + (0.05 * 6.0 - 0.02 * 2.0)
+    got = _centre_rate_scaled(4.0, C_of, s_of, x0)
+    assert abs(got / exact - 1.0) < 1e-3
+    # a one-sided factor (s_i alone) drops the grad s . grad C term and fails
+    one_sided = lambda X: np.full(X.shape[0], 2.0 + 0.15 - 0.04)
+    assert abs(_centre_rate_scaled(4.0, C_of, one_sided, x0) / exact - 1.0) > 0.03
+
+
+def test_uniform_factor_scales_the_tensor():
+    x, prm, rng = _jittered_box(2, 10, seed=5)
+    n = x.shape[0]
+    vol = prm.dp ** 2 * rng.uniform(0.9, 1.1, n)
+    C = rng.uniform(0.0, 1.0, n)
+    D = np.array([[1.5, 0.3], [0.3, 0.8]])
+    I, J = df.fluid_pairs(x, prm)
+    a = df.diffusion_rate(x, C, vol, I, J, df.tensor_inverse(2.5 * D, 2), prm)
+    b = df.diffusion_rate(x, C, vol, I, J, df.tensor_inverse(D, 2), prm, scale=np.full(n, 2.5))
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12 * np.max(np.abs(a)))
+    s = rng.uniform(0.5, 2.0, n)                    # conservation with varying factors
+    r = df.diffusion_rate(x, C, vol, I, J, df.tensor_inverse(D, 2), prm, scale=s)
+    assert abs(np.sum(vol * r)) < 1e-12 * np.sum(np.abs(vol * r))
