@@ -341,10 +341,19 @@ const char* sph_species_last_error(const sph_species* sp);
 int sph_species_set(sph_handle* h, sph_species* sp, const double* C, void* stream);
 /* C: host or device, n_fluid doubles in caller row order. Synchronous. */
 int sph_species_get(sph_handle* h, sph_species* sp, double* C, void* stream);
+/* Per-particle diffusivity factors: particle i diffuses with s_i D (s: host or device,
+ * n_fluid doubles in caller row order, each positive and finite, else SPH_E_INVALID and
+ * no factors). The pair combination of Eq. grad-laplace's per-particle factors, read as
+ * the harmonic mean of L~_i = L^-1/sqrt(s_i), weights a pair by
+ * ((sqrt(s_i) + sqrt(s_j))/2)^2. Until called, every factor is 1. Synchronous. */
+int sph_species_set_scale(sph_handle* h, sph_species* sp, const double* s, void* stream);
 /* n_steps RK2 steps of size dt (> 0, finite) on the current neighbour table, which
  * must be valid (sph_build_cells after the last state change; SPH_E_INVALID otherwise).
- * Positions, velocities and densities are not changed. Asynchronous on stream: two
- * kernel launches per step plus a gather and a scatter of the species per call. */
+ * Positions, velocities and densities are not changed. Two kernel launches per step plus
+ * a gather and a scatter of the species per call; the call synchronises stream once,
+ * after the gather, to learn whether volumes and factors are uniform within each tank
+ * (then the stage kernels take them out of the pair loop), and is otherwise
+ * asynchronous. */
 int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_steps, void* stream);
 
 /* ---- Reaction step of reaction-diffusion (Sec. "SPH method for reaction-diffusion",

@@ -82,12 +82,15 @@ __device__ __forceinline__ float2 diff_terms2(const Inst& I, const DiffCoef& K, 
   return mul2(sub2(f2(ci), make_float2(i2f(a.w), i2f(b.w))), k);
 }
 
-// Sum over the fluid part of row i of V_j-weighted pair terms (VJ: V_j per pair, from the
-// record in 2D or the volume array in 3D; else the caller multiplies by the common volume).
+// Sum over the fluid part of row i of weighted pair terms. VJ: each pair weighted by V_j
+// (from the record in 2D or the volume array in 3D) and by ((sqrt s_i + sqrt s_j)/2)^2 of
+// the per-particle diffusivity factors (sq = sqrt s per slot, NULL when none is set); else
+// the caller multiplies by the common volume and factor.
 template <int D, bool PER, bool ISO, bool VJ>
 __device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Inst& I, const DiffCoef& K,
                                          const int4& ri, float ci, const int4* __restrict__ R,
-                                         const int4* __restrict__ nb4, const float* __restrict__ vol) {
+                                         const int4* __restrict__ nb4, const float* __restrict__ vol,
+                                         const float* __restrict__ sq, float sqi) {
   const int nq = (nf + 3) >> 2;
   float2 s = f2(0.0f);
   int4 nxt = nq ? nb4[i] : make_int4(0, 0, 0, 0);
@@ -107,6 +110,12 @@ __device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Ins
         w01 = mul2(w01, make_float2(vol[cq.x], vol[j1]));
         w23 = mul2(w23, make_float2(vol[j2], vol[j3]));
       }
+      if (sq) {
+        const float2 m01 = mul2(add2(f2(sqi), make_float2(sq[cq.x], sq[j1])), f2(0.5f));
+        const float2 m23 = mul2(add2(f2(sqi), make_float2(sq[j2], sq[j3])), f2(0.5f));
+        w01 = mul2(w01, mul2(m01, m01));
+        w23 = mul2(w23, mul2(m23, m23));
+      }
     }
     s = fma2(diff_terms2<D, PER, ISO>(I, K, ri, ci, a0, a1), w01, s);
     s = fma2(diff_terms2<D, PER, ISO>(I, K, ri, ci, a2, a3), w23, s);
@@ -120,7 +129,8 @@ __device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Ins
 template <int D, bool PER, bool ISO, bool VJ>
 __device__ __forceinline__ float row_sum_any(int64_t n, int64_t i, int nf, const Inst& I, const DiffCoef& K,
                                              const int4& ri, float ci, const int4* __restrict__ R,
-                                             const int4* __restrict__ nb4, const float* __restrict__ vol) {
+                                             const int4* __restrict__ nb4, const float* __restrict__ vol,
+                                             const float* __restrict__ sq, float sqi) {
   if (PER) {
     const int reach = (int)ceilf(sqrtf((float)I.R2)) + 2;          // support radius in quanta
     const int q[3] = {ri.x, ri.y, ri.z};
@@ -128,20 +138,23 @@ __device__ __forceinline__ float row_sum_any(int64_t n, int64_t i, int nf, const
 #pragma unroll
     for (int a = 0; a < D; ++a)
       if (I.period[a]) near_face |= q[a] < reach || q[a] >= I.period[a] - reach;
-    if (near_face) return row_sum<D, true, ISO, VJ>(n, i, nf, I, K, ri, ci, R, nb4, vol);
+    if (near_face) return row_sum<D, true, ISO, VJ>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi);
   }
-  return row_sum<D, false, ISO, VJ>(n, i, nf, I, K, ri, ci, R, nb4, vol);
+  return row_sum<D, false, ISO, VJ>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi);
 }
 
-// Five blocks of 256 per SM (48 registers) for the isotropic variants: the stage is
-// latency-bound and runs 8 % faster at 8M particles than with four; the anisotropic
+// Five blocks of 256 per SM (48 registers) for the isotropic uniform variants: the stage
+// is latency-bound and runs 8 % faster at 8M particles than with four; the anisotropic
 // variants keep four, since they would spill at 48 registers.
-template <int D, bool PER, bool ISO, bool SECOND>
-__global__ void __launch_bounds__(kDiffBlock, ISO ? 5 : 4)
+// UNIF: volumes and diffusivity factors are equal within each tank (the host reads the
+// flag the pack kernel computes); the general path weights every pair and keeps four
+// blocks per SM, where its extra per-pair loads fit without spilling.
+template <int D, bool PER, bool ISO, bool SECOND, bool UNIF>
+__global__ void __launch_bounds__(kDiffBlock, ISO && UNIF ? 5 : 4)
 k_diffusion_stage(int64_t n, const int4* __restrict__ Rin, int4* __restrict__ Rout, const int* __restrict__ nbr,
                   const uint32_t* __restrict__ nbc, const int* __restrict__ inst_of,
                   const Inst* __restrict__ inst, const float* __restrict__ vol,
-                  const int* __restrict__ nonuniform, DiffCoef K, float dt) {
+                  const float* __restrict__ sq, DiffCoef K, float dt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Inst& I = inst[inst_of ? inst_of[i] : 0];
@@ -149,12 +162,13 @@ k_diffusion_stage(int64_t n, const int4* __restrict__ Rin, int4* __restrict__ Ro
   const float ci = i2f(ri.w);
   const int nf = (int)(nbc[i] & 0xffffu);
   const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
+  const float sqi = sq ? sq[i] : 1.0f;
   float sum;
-  if (*nonuniform == 0) {          // equal volumes within the tank: V_j = V_i
+  if (UNIF) {                      // equal volumes and factors within the tank: those of i
     const float vi = D == 2 ? i2f(ri.z) : vol[i];
-    sum = vi * row_sum_any<D, PER, ISO, false>(n, i, nf, I, K, ri, ci, Rin, nb4, vol);
+    sum = vi * (sqi * sqi) * row_sum_any<D, PER, ISO, false>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi);
   } else {
-    sum = row_sum_any<D, PER, ISO, true>(n, i, nf, I, K, ri, ci, Rin, nb4, vol);
+    sum = row_sum_any<D, PER, ISO, true>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi);
   }
   const float rate = 2.0f * (ISO ? I.dwr_a * K.kappa : I.dwr_a) * sum;
   const float next = fmaf(dt, rate, ci);
@@ -171,6 +185,7 @@ __global__ void k_species_pack(int64_t n, const int4* __restrict__ P, const int*
                                const int* __restrict__ inst_of, const Inst* __restrict__ inst,
                                const float* __restrict__ mass, const float* __restrict__ by_row,
                                int4* __restrict__ R0, int4* __restrict__ R1, float* __restrict__ vol,
+                               const float* __restrict__ scale_by_row, float* __restrict__ sq,
                                int* __restrict__ nonuniform) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -185,6 +200,17 @@ __global__ void k_species_pack(int64_t n, const int4* __restrict__ P, const int*
   const int64_t f = I.fluid_begin;                                    // the tank's first slot
   const float vf = __fdividef(mass ? mass[f] : I.mass, I.rho0 + i2f(P[f].w));
   if (vf != v) atomicOr(nonuniform, 1);
+  if (scale_by_row) {                                                 // sqrt of s_i, R17
+    const float q = sqrtf(scale_by_row[id[i]]);
+    sq[i] = q;
+    if (sqrtf(scale_by_row[id[f]]) != q) atomicOr(nonuniform, 2);
+  }
+}
+
+// Flags a diffusivity factor that is not a positive finite number.
+__global__ void k_check_scale(int64_t n, const float* __restrict__ s, int* __restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !(s[i] > 0.0f && s[i] <= 3.402823466e38f)) atomicOr(bad, 1);
 }
 
 __global__ void k_species_unpack(int64_t n, const int* __restrict__ id, const int4* __restrict__ R,
@@ -252,18 +278,23 @@ __global__ void k_reaction(int64_t n, float* __restrict__ V, float* __restrict__
 }
 
 using StageFn = void (*)(int64_t, const int4*, int4*, const int*, const uint32_t*, const int*, const Inst*,
-                         const float*, const int*, DiffCoef, float);
+                         const float*, const float*, DiffCoef, float);
 
-template <int D, bool PER, bool ISO>
+template <int D, bool PER, bool ISO, bool UNIF>
 void pick_stages(StageFn* s1, StageFn* s2) {
-  *s1 = k_diffusion_stage<D, PER, ISO, false>;
-  *s2 = k_diffusion_stage<D, PER, ISO, true>;
+  *s1 = k_diffusion_stage<D, PER, ISO, false, UNIF>;
+  *s2 = k_diffusion_stage<D, PER, ISO, true, UNIF>;
 }
 
 template <int D, bool PER>
-void pick_stages(bool iso, StageFn* s1, StageFn* s2) {
-  if (iso) pick_stages<D, PER, true>(s1, s2);
-  else pick_stages<D, PER, false>(s1, s2);
+void pick_stages(bool iso, bool unif, StageFn* s1, StageFn* s2) {
+  if (iso) {
+    if (unif) pick_stages<D, PER, true, true>(s1, s2);
+    else pick_stages<D, PER, true, false>(s1, s2);
+  } else {
+    if (unif) pick_stages<D, PER, false, true>(s1, s2);
+    else pick_stages<D, PER, false, false>(s1, s2);
+  }
 }
 
 }  // namespace
@@ -279,7 +310,9 @@ struct sph_species {
   int4* r0 = nullptr;          // [n] slot records carrying C^n
   int4* r1 = nullptr;          // [n] slot records carrying C*
   float* vol = nullptr;        // [n] slot volumes m/rho (3D)
-  int* nonuniform = nullptr;   // [1] volumes differ within a tank (3D)
+  int* nonuniform = nullptr;   // [1] bit 0: volumes differ within a tank; bit 1: factors do
+  float* scale_by_row = nullptr;  // [n] per-particle diffusivity factors s (NULL: all 1)
+  float* sq = nullptr;         // [n] sqrt(s) per slot (with scale_by_row)
   double* stage = nullptr;     // [n] doubles for host copies
   std::string err;
 };
@@ -390,6 +423,8 @@ void sph_species_destroy(sph_species* sp) {
   cudaFree(sp->vol);
   cudaFree(sp->nonuniform);
   cudaFree(sp->gate);
+  cudaFree(sp->scale_by_row);
+  cudaFree(sp->sq);
   cudaFree(sp->stage);
   delete sp;
 }
@@ -456,6 +491,39 @@ int sph_species_get_gate(sph_handle* h, sph_species* sp, double* w, void* stream
   return species_download(h, sp, sp ? sp->gate : nullptr, w, stream);
 }
 
+int sph_species_set_scale(sph_handle* h, sph_species* sp, const double* s, void* stream) {
+  if (!h || !sp) return SPH_E_INVALID;
+  if (sp->n != h->b.n || sp->dim != h->b.dim) return sfail(sp, SPH_E_INVALID, "species belongs to another handle");
+  if (sp->n == 0) return SPH_OK;
+  if (!sp->scale_by_row) {
+    if (cudaMalloc(&sp->scale_by_row, sizeof(float) * sp->n) != cudaSuccess ||
+        cudaMalloc(&sp->sq, sizeof(float) * sp->n) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(sp->scale_by_row);
+      sp->scale_by_row = nullptr;
+      return sfail(sp, SPH_E_OOM, "device allocation of the diffusivity factors failed");
+    }
+  }
+  int r = species_upload(h, sp, s, sp->scale_by_row, stream);
+  if (r != SPH_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  int bad = 0;
+  if (cudaMemsetAsync(sp->nonuniform, 0, sizeof(int), st) != cudaSuccess) return sfail(sp, SPH_E_CUDA, "check failed");
+  sph::k_check_scale<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, st>>>(sp->n, sp->scale_by_row, sp->nonuniform);
+  ++h->launches;
+  if (cudaMemcpyAsync(&bad, sp->nonuniform, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return sfail(sp, SPH_E_CUDA, "check failed");
+  if (bad) {                       // back to no factors
+    cudaFree(sp->scale_by_row);
+    cudaFree(sp->sq);
+    sp->scale_by_row = nullptr;
+    sp->sq = nullptr;
+    return sfail(sp, SPH_E_INVALID, "diffusivity factors must be positive and finite");
+  }
+  return SPH_OK;
+}
+
 int sph_reaction_step(sph_handle* h, sph_species* sp, const sph_reaction* r, double dt, int32_t n_steps,
                       void* stream) {
   if (!h || !sp) return SPH_E_INVALID;
@@ -485,26 +553,32 @@ int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_step
   const sph::Buffers& b = h->b;
   if (b.n == 0 || n_steps == 0) return SPH_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  sph::StageFn s1, s2;
-  if (b.dim == 2) {
-    if (b.any_periodic) sph::pick_stages<2, true>(sp->iso, &s1, &s2);
-    else sph::pick_stages<2, false>(sp->iso, &s1, &s2);
-  } else {
-    if (b.any_periodic) sph::pick_stages<3, true>(sp->iso, &s1, &s2);
-    else sph::pick_stages<3, false>(sp->iso, &s1, &s2);
-  }
   const unsigned grid = sph::diff_grid(b.n);
   const float fdt = (float)dt;
   if (cudaMemsetAsync(sp->nonuniform, 0, sizeof(int), s) != cudaSuccess)
     return sfail(sp, SPH_E_CUDA, "diffusion set-up failed");
   auto pack = b.dim == 2 ? sph::k_species_pack<2> : sph::k_species_pack<3>;
   pack<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.PS, b.id, b.inst_of, b.inst, b.mass, sp->by_row, sp->r0,
-                                        sp->r1, sp->vol, sp->nonuniform);
+                                        sp->r1, sp->vol, sp->scale_by_row, sp->sq, sp->nonuniform);
+  // the one synchronisation of the call: which stage kernels the volumes and factors allow
+  int nonuniform = 0;
+  if (cudaMemcpyAsync(&nonuniform, sp->nonuniform, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return sfail(sp, SPH_E_CUDA, "diffusion set-up failed");
+  const bool unif = nonuniform == 0;
+  sph::StageFn s1, s2;
+  if (b.dim == 2) {
+    if (b.any_periodic) sph::pick_stages<2, true>(sp->iso, unif, &s1, &s2);
+    else sph::pick_stages<2, false>(sp->iso, unif, &s1, &s2);
+  } else {
+    if (b.any_periodic) sph::pick_stages<3, true>(sp->iso, unif, &s1, &s2);
+    else sph::pick_stages<3, false>(sp->iso, unif, &s1, &s2);
+  }
   for (int k = 0; k < n_steps; ++k) {
     s1<<<grid, sph::kDiffBlock, 0, s>>>(b.n, sp->r0, sp->r1, b.nbr, b.nbc, b.inst_of, b.inst, sp->vol,
-                                         sp->nonuniform, sp->K, fdt);
+                                         sp->sq, sp->K, fdt);
     s2<<<grid, sph::kDiffBlock, 0, s>>>(b.n, sp->r1, sp->r0, b.nbr, b.nbc, b.inst_of, b.inst, sp->vol,
-                                         sp->nonuniform, sp->K, fdt);
+                                         sp->sq, sp->K, fdt);
   }
   sph::k_species_unpack<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.id, sp->r0, sp->by_row);
   h->launches += 2 + 2 * (int64_t)n_steps;

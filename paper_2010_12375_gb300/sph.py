@@ -40,7 +40,7 @@ EXPORTS = [
     "sph_learned_set_fused", "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
     "sph_species_create", "sph_species_destroy", "sph_species_last_error", "sph_species_set",
     "sph_species_get", "sph_diffusion_step", "sph_species_set_gate", "sph_species_get_gate",
-    "sph_reaction_step",
+    "sph_reaction_step", "sph_species_set_scale",
 ]
 
 
@@ -159,6 +159,7 @@ def load():
         "sph_species_set_gate": (i32, [P, P, P, P]),
         "sph_species_get_gate": (i32, [P, P, P, P]),
         "sph_reaction_step": (i32, [P, P, ctypes.POINTER(SphReaction), dbl, i32, P]),
+        "sph_species_set_scale": (i32, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -539,6 +540,13 @@ def sph_species_get_gate(h, sp, n, stream=None, out=None):
     w = np.empty(n, dtype=np.float64) if out is None else out
     _scheck(lib, sp, lib.sph_species_get_gate(h, sp, _ptr(w), _stream(stream)))
     return w
+
+
+def sph_species_set_scale(h, sp, s, stream=None):
+    """Per-particle diffusivity factors (caller row order, positive)."""
+    lib = load()
+    s = _f64(s)
+    _scheck(lib, sp, lib.sph_species_set_scale(h, sp, _ptr(s), _stream(stream)))
 
 
 def reaction_from(model, **params) -> SphReaction:

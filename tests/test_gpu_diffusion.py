@@ -245,3 +245,50 @@ def test_full_size_block_sampled_and_analytic(sph):
     exact = (0.01 / s2) ** 1.5 * np.exp(-r2 / (2 * s2))
     assert np.max(np.abs(C20 - exact)) < 2e-3
     assert abs(np.sum(C20) / np.sum(C0) - 1.0) < 1e-5      # uniform volumes: sum C conserved
+
+
+@pytest.mark.parametrize("name", ["aniso2d", "iso3d", "band2d"])
+def test_per_particle_diffusivity_matches_oracle(sph, name):
+    # reading R17: per-particle factors s_i on the tensor; the band has uniform volumes, so
+    # only the factors take it off the uniform path
+    p, D, C0, dt = _case(name)
+    s = np.random.default_rng(13).uniform(0.5, 2.0, p.n_fluid).astype(np.float32).astype(np.float64)
+    dt = dt / 2.0                                   # s up to 2
+    steps = 10
+    sim = sph.Simulation(p)
+    try:
+        sph.sph_build_cells(sim.handle)
+        sp = sph.sph_species_create(sim.handle, D, sim.dim)
+        try:
+            sph.sph_species_set(sim.handle, sp, C0)
+            sph.sph_species_set_scale(sim.handle, sp, s)
+            sph.sph_diffusion_step(sim.handle, sp, dt, steps)
+            Cg = sph.sph_species_get(sim.handle, sp, sim.n)
+            with pytest.raises(sph.SphError):          # a non-positive factor is rejected
+                sph.sph_species_set_scale(sim.handle, sp, np.where(np.arange(sim.n) == 7, 0.0, 1.0))
+        finally:
+            sph.sph_species_destroy(sp)
+    finally:
+        sim.close()
+    prm = o.Params.from_problem(p)
+    Co = df.run(p.pos, C0, p.mass, p.rho, np.asarray(D)[:p.dim, :p.dim], dt, steps, prm, scale=s)
+    assert np.max(np.abs(Co - C0)) > 1e-3
+    assert np.max(np.abs(Cg - Co)) <= _bound(steps, C0, Co), (name, np.max(np.abs(Cg - Co)))
+
+
+def test_uniform_factor_equals_scaled_tensor(sph):
+    # a factor equal for every particle matches the tensor scaled by it
+    p, D, C0, dt = _case("iso3d")
+    a = _gpu_run(sph, p, 2.0 * np.asarray(D), C0, dt / 2, 6)
+    sim = sph.Simulation(p)
+    try:
+        sph.sph_build_cells(sim.handle)
+        sp = sph.sph_species_create(sim.handle, D, 3)
+        sph.sph_species_set(sim.handle, sp, C0)
+        sph.sph_species_set_scale(sim.handle, sp, np.full(sim.n, 2.0))
+        sph.sph_diffusion_step(sim.handle, sp, dt / 2, 6)
+        b = sph.sph_species_get(sim.handle, sp, sim.n)
+        sph.sph_species_destroy(sp)
+    finally:
+        sim.close()
+    assert np.max(np.abs(a - b)) <= 8 * 6 * 2.0 ** -24 * np.max(np.abs(C0))
