@@ -19,11 +19,12 @@
 // write only the species word. The pair arithmetic is issue-bound, so it runs two pairs per
 // packed FP32 instruction; pair coordinates are exact integer differences converted with
 // the magic-number add, wrapped on periodic axes only for particles within the support of
-// a periodic face; and when all volumes of a tank are equal (checked once per call on the
-// device; neighbours never cross tanks, so then V_j = V_i) the volume and the kernel
-// constants leave the pair loop. Otherwise V_j comes from the record (2D) or a per-slot
-// array (3D). Wall neighbours are skipped: walls carry no species (zero flux). Pairs at
-// zero distance add nothing.
+// a periodic face; and when all volumes and diffusivity factors of a tank are equal
+// (checked once per call by the pack kernel, read by the host, which then launches the
+// uniform instantiation; neighbours never cross tanks, so then V_j = V_i) the volume, the
+// factor and the kernel constants leave the pair loop. Otherwise V_j comes from the record
+// (2D) or a per-slot array (3D) and the factor pair from a per-slot array. Wall neighbours
+// are skipped: walls carry no species (zero flux). Pairs at zero distance add nothing.
 //
 // Between calls the species is kept by caller row, so the fluid solver may re-sort the
 // particles; each call gathers it into slot order, runs its steps and scatters it back.
