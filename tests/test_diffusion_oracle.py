@@ -227,3 +227,15 @@ def test_uniform_factor_scales_the_tensor():
     s = rng.uniform(0.5, 2.0, n)                    # conservation with varying factors
     r = df.diffusion_rate(x, C, vol, I, J, df.tensor_inverse(D, 2), prm, scale=s)
     assert abs(np.sum(vol * r)) < 1e-12 * np.sum(np.abs(vol * r))
+
+
+def test_anisotropic_printed_operator_limit_3d():
+    # reading R15 in 3D: D = diag(4, 4, 1), C = z^2. With mu = cos(theta) and A = 1/4, B = 1,
+    # w = 1/(A (1 - mu^2) + B mu^2) and (3/4pi) int w 2 mu^2 dS = 3 int_-1^1 mu^2/(A + (B-A) mu^2) dmu
+    # = 3 (2 - (2/k) atan k)/(A k^2), k^2 = (B - A)/A; tr(D H) would be 2
+    A, B = 0.25, 1.0
+    k = math.sqrt((B - A) / A)
+    limit = 3.0 * (2.0 - (2.0 / k) * math.atan(k)) / (A * k * k)
+    got = _centre_rate(3, 4.0, np.diag([4.0, 4.0, 1.0]), np.diag([0.0, 0.0, 2.0]))
+    assert abs(got / limit - 1.0) < 2e-3
+    assert abs(got / 2.0 - 1.0) > 0.3
