@@ -317,8 +317,9 @@ int sph_learned_step(sph_handle* h, sph_learned* net, double max_mean_rho_dev,
  *   w(e) = 1/(L^-1 e)^2 = 1/(e^T D^-1 e),  D = L L^T (Eq. chol),
  * over the fluid neighbours of the current neighbour table (wall particles carry no
  * species: zero flux through walls), with one diffusion tensor D per species object (so
- * the pair combination of the per-particle factors is the factor itself) and the masses,
- * densities and positions of the handle's current state. Pairs at zero distance add
+ * the pair combination of the per-particle factors is the factor itself; per-particle
+ * multiples of D: sph_species_set_scale) and the masses, densities and positions of the
+ * handle's current state. Pairs at zero distance add
  * nothing. Time integration is the two-stage second-order Runge-Kutta scheme (Heun):
  *   C* = C + dt f(C),  C <- (C + C* + dt f(C*)) / 2.
  * For isotropic D = kappa I, w = kappa and the operator is the SPH Laplacian times kappa.
