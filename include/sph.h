@@ -376,7 +376,9 @@ int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_step
  *   AP  R_V: q = 0,  p = k (V - a)(V - 1) + w;  R_w: q = -eps k V (V - b - 1), p = eps
  * (1 - e^(-p dt))/p is taken as dt when |p dt| < 1e-12. Because p and q are frozen over a
  * reaction, the step is first-order accurate where p depends on the reacting variable.
- * Unused parameters of a model are ignored. FP32 on the device. */
+ * Unused parameters of a model are ignored. AP needs mu2 + V != 0 (eps is singular there;
+ * the step then produces non-finite values, which the caller sees in sph_species_get).
+ * FP32 on the device. */
 #define SPH_REACTION_FN 1
 #define SPH_REACTION_AP 2
 typedef struct {
