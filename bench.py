@@ -35,8 +35,7 @@ UNIT = "particle-substeps/s"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pressure-relaxation
 # launch per fluid particle, from the ncu capture of the 3D dam break at dp = 1/80
-# (1,024,000 particles, neighbour table 0.5 GB > L2) summarised in
-# profiles/pressure_relaxation_dam_break_3d.md; it is scaled to the benchmark's particle
+# (1,024,000 particles, neighbour table 0.5 GB > L2); it is scaled to the benchmark's particle
 # count (the traffic is per particle: state records plus its neighbour row). Valid only
 # for the kernel sources whose hash is recorded with it.
 TRAFFIC_BYTES_PER_PARTICLE = 390.07
@@ -161,24 +160,102 @@ def oracle_steps(n_steps, problem=None):
     return prob.n_fluid * sub / dt, dt, sub
 
 
-def cpu_sample_text(steps):
+def _oracle_worker(conn, seed):
+    """One host core's share of the all-core oracle run: its own copy of the sample, with a
+    seeded velocity perturbation so that the cores do not repeat one another's work; advances
+    it one advection step per request and answers (substeps, seconds)."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    from oracle import wcsph as o
+    prob = cpu_sample_workload()
+    prm = o.Params.from_problem(prob)
+    st, w = o.state_from_problem(prob)
+    st.v = st.v + np.random.default_rng(seed).uniform(-0.01, 0.01, size=st.v.shape)
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            break
+        t0 = time.perf_counter()
+        st, info = o.advection_step(st, w, prm)
+        conn.send((info.substeps, time.perf_counter() - t0))
+    conn.close()
+
+
+class OracleCores:
+    """The oracle on every host core at once: one spawned process per core (spawned, never
+    forked, so it is safe after CUDA has started), each stepping its own sample. A step is
+    timed from the request to the last core's answer."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or len(os.sched_getaffinity(0))
+        ctx = mp.get_context("spawn")
+        self.pipes, self.procs = [], []
+        for k in range(self.cores):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, 1000 + k), daemon=True)
+            p.start()
+            self.pipes.append(a)
+            self.procs.append(p)
+
+    def step(self):
+        """One advection step on every core; returns (particle-substeps, wall seconds)."""
+        t0 = time.perf_counter()
+        for c in self.pipes:
+            c.send(1)
+        subs = [c.recv()[0] for c in self.pipes]
+        return 2 * CPU_SAMPLE_N ** 3 * sum(subs), time.perf_counter() - t0
+
+    def close(self):
+        for c in self.pipes:
+            c.send(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def cpu_sample_text(steps, cores=1):
+    where = "on one core" if cores == 1 else f"on each of {cores} cores at once (one process per core, own sample)"
     return (f"3D dam break at dp = 1/{CPU_SAMPLE_N} ({2 * CPU_SAMPLE_N ** 3:,} fluid + walls, same "
             f"physics as the GPU workload), {steps} advection step(s) of the FP64 numpy oracle "
-            f"on one core")
+            f"{where}")
+
+
+def cpu_baseline(steps):
+    """The oracle as it stands on the host: all cores (the reported figure) and one core."""
+    rate1, secs1, sub1 = oracle_steps(steps)
+    pool = OracleCores()
+    try:
+        pool.step()                                   # workers import and warm up
+        units, secs = 0, 0.0
+        for _ in range(steps):
+            u, t = pool.step()
+            units += u
+            secs += t
+    finally:
+        pool.close()
+    return {"value": units / secs, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": cpu_sample_text(steps, pool.cores) + f" ({secs:.1f} s)",
+            "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                            "sample": cpu_sample_text(steps) + f" ({secs1:.1f} s, {sub1} substeps)"}}
 
 
 def run_reference(args, rank, world):
-    """The reference arm: the FP64 oracle on the host cores, as it stands."""
+    """The reference arm: the FP64 oracle as it stands, on all the host's cores (one process
+    per core, each stepping its own copy of the bounded sample)."""
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_steps(1)
-    secs, subs = 0.0, 0
-    for _ in range(args.steps):
-        _, s, k = oracle_steps(1)
-        secs += s
-        subs += k
-    value = CPU_SAMPLE_N ** 3 * 2 * subs / secs
+    pool = OracleCores()
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        secs, units = 0.0, 0
+        for _ in range(args.steps):
+            u, t = pool.step()
+            units += u
+            secs += t
+    finally:
+        pool.close()
+    value = units / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
@@ -187,8 +264,8 @@ def run_reference(args, rank, world):
         # the GPU arm's workload; each step times a bounded sample of it (cpu_baseline.sample)
         "config": {"workload": f"3D dam break, fluid 2x1x1 in a 5.366x5.366x1 tank, dp = 1/{args.n}",
                    "sample": f"dp = 1/{CPU_SAMPLE_N}, {2 * CPU_SAMPLE_N ** 3} fluid particles per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": cpu_sample_text(args.steps)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                         "sample": cpu_sample_text(args.steps, pool.cores)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -220,7 +297,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     prob = wk.dam_break_3d(args.n)
     N = prob.n_fluid
-    flags = (sph.SPH_FLAG_GRAPH if args.graph else 0) | (sph.SPH_FLAG_FROZEN_GEOMETRY if args.frozen else 0)
+    graph = not args.host_loop
+    flags = (sph.SPH_FLAG_GRAPH if graph else 0) | (sph.SPH_FLAG_FROZEN_GEOMETRY if args.frozen else 0)
     sim = sph.Simulation(prob, flags=flags, stream=stream)
     info = sim.info()
 
@@ -247,8 +325,7 @@ def run_ours(args, rank, world, local_rank):
                  "density_relaxation": {"threads_per_particle": cfg[2], "block": cfg[3]}}
     torch.cuda.synchronize()
 
-    # ---------------- timed region: device-resident state
-    sph.sph_set_kernel_timing(sim.handle, not args.graph)
+    # ---------------- timed region: device-resident state, no per-kernel events inside it
     d0 = sim.diagnostics()
     l0 = sim.kernel_launches()
     barrier()
@@ -269,10 +346,16 @@ def run_ours(args, rank, world, local_rank):
     step_ms = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
     launches = sim.kernel_launches() - l0
     d1 = sim.diagnostics()
-    ktimes, kcount = sph.sph_kernel_times(sim.handle)
-    sph.sph_set_kernel_timing(sim.handle, False)
     substeps = d1["substeps"] - d0["substeps"]
     fluid_pairs, wall_pairs = sim.pair_count()
+
+    # ---------------- kernel means, untimed: the library records CUDA events on the launching
+    # stream around every relaxation launch of these advection steps (host-driven loop, the
+    # same launch variants, continuing from the timed region's state)
+    sph.sph_set_kernel_timing(sim.handle, True)
+    sim.step(args.kernel_steps)
+    ktimes, kcount = sph.sph_kernel_times(sim.handle)
+    sph.sph_set_kernel_timing(sim.handle, False)
 
     # ---------------- e2e: host state in and out every step through the C ABI
     dim = prob.dim
@@ -327,13 +410,14 @@ def run_ours(args, rank, world, local_rank):
             "launch_ms": k7_ms, "algorithmic_bytes_per_launch": k7_bytes,
             "density_relaxation_ms": ktimes[1] / max(kcount[1], 1),
             "gather_ceiling_ms": gather_ms,
-            "frac_of_gather_ceiling": (gather_ms / k7_ms) if kcount[0] else None}
+            "frac_of_gather_ceiling": (gather_ms / k7_ms) if kcount[0] else None,
+            "launch_ms_from": f"CUDA events on the launching stream around each of the {kcount[0]} "
+                              f"launches of {args.kernel_steps} advection steps run right after the "
+                              "timed region (host-driven loop, same state and launch variants)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, secs, sub = oracle_steps(args.cpu_steps)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": cpu_sample_text(args.cpu_steps) + f" ({secs:.1f} s, {sub} substeps)"}
+        cpu = cpu_baseline(args.cpu_steps)
 
     if rank == 0:
         line = {
@@ -349,7 +433,7 @@ def run_ours(args, rank, world, local_rank):
                 "l2": "inputs larger than L2 (state %d MB, neighbour table %.1f GB)"
                       % (32 * N // 10**6, 4 * N * info.capacity / 1e9),
                 "pair_interactions_per_s": 2 * (fluid_pairs + wall_pairs) * total_units / N / (ms_max * 1e-3),
-                "loop": "graph" if args.graph else "host-driven, one sync per substep",
+                "loop": "graph" if graph else "host-driven, one sync per substep",
                 "parallelism": f"replicas x{world}",
                 "launch": tuned or {"autotune": "off"},
             },
@@ -662,7 +746,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=159, help="3D dam break resolution: dp = 1/n, 2n^3 fluid")
-    ap.add_argument("--graph", action="store_true", help="time the CUDA-graph loop instead")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="time the host-driven substep loop instead of the CUDA-graph loop")
+    ap.add_argument("--kernel-steps", type=int, default=3,
+                    help="untimed advection steps over which the relaxation kernels' launches are timed")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--diff-n", type=int, default=200, help="diffusion3d block: n^3 particles")
     ap.add_argument("--cpu-steps", type=int, default=4)

@@ -21,8 +21,9 @@
  *    stays valid for inspection (sph_get_state, sph_last_error).
  *  - Array arguments are plain pointers to host or device memory (unified
  *    addressing decides which); the library copies what it needs and never
- *    keeps a caller pointer beyond the call. Vectors are interleaved per
- *    particle: pos[k*dim + a].
+ *    keeps a caller pointer beyond the call. Device arrays must belong to the
+ *    current device (another GPU's memory returns SPH_E_INVALID). Vectors are
+ *    interleaved per particle: pos[k*dim + a].
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
  *    asynchronous on it, except those that return host values, which
  *    synchronise that stream before returning.
@@ -59,7 +60,10 @@ extern "C" {
 #define SPH_E_DOMAIN   -4   /* a particle left the cell grid [lo, hi) on a non-periodic axis */
 #define SPH_E_UNSTABLE -5   /* NaN/Inf in the state, or a time step below 1e-12 h/c0          */
 #define SPH_E_CAPACITY -6   /* a particle has more neighbours than the per-particle capacity */
-#define SPH_E_TIMEOUT  -7   /* a bounded device-side wait expired                            */
+#define SPH_E_TIMEOUT  -7   /* a bounded device-side wait expired, or an advection step
+                               needed more acoustic substeps than sph_params.max_substeps  */
+#define SPH_E_BOUNDS   -8   /* SPH_FLAG_DEBUG_BOUNDS: a neighbour index, row count or cell
+                               offset out of range, caught before any kernel used it      */
 
 /* ---- flags (sph_params.flags) ----------------------------------------------------- */
 #define SPH_FLAG_GRAPH     1u  /* sph_step runs each advection step as one CUDA graph whose
@@ -72,6 +76,14 @@ extern "C" {
                                       * without it they are recomputed from the current
                                       * positions in every half step. Costs 16 B per neighbour
                                       * slot of device memory (n_fluid x capacity). */
+#define SPH_FLAG_DEBUG_BOUNDS 8u     /* check, before any kernel reads them, that the cell
+                                      * offsets of every configuration update run from 0 to
+                                      * the particle count without decreasing, and that every
+                                      * neighbour row fits the capacity with every index in
+                                      * range; a violation returns SPH_E_BOUNDS and launches
+                                      * nothing that would read it. The checks synchronise
+                                      * the stream, so sph_step then drives the loop from the
+                                      * host (SPH_FLAG_GRAPH is ignored). */
 
 typedef struct sph_handle sph_handle;   /* opaque, library-owned */
 
@@ -99,6 +111,10 @@ typedef struct {
                              relaxation also moves the mid-point position by dt^2/2 a_i,
                              a_i = -2 sum_j m_j p0 / (rho_i rho_j) grad_i W_ij over fluid
                              pairs at the mid-point; not with SPH_FLAG_FROZEN_GEOMETRY */
+  int32_t  max_substeps;  /* bound of the device-side acoustic-substep loop of one advection
+                             step (0 = 1000; a normal step takes 2-6): a step that needs more
+                             stops there with SPH_E_TIMEOUT, the handle stays valid and
+                             sph_clear_error lets it continue */
 } sph_params;
 
 /* FP64 conservation and bulk diagnostics of one tank. */
@@ -155,6 +171,23 @@ void sph_destroy(sph_handle* h);
 const char* sph_last_error(const sph_handle* h);
 
 int sph_get_info(const sph_handle* h, sph_info* out);
+
+/* Clear the handle's error state (the device error word and the message) after the caller
+ * has inspected it, so that the next call does not report it again. Synchronous. */
+int sph_clear_error(sph_handle* h, void* stream);
+
+/* Overwrite one entry of the handle's internal tables (a test aid for SPH_FLAG_DEBUG_BOUNDS;
+ * the paper has no counterpart). what = SPH_DEBUG_NEIGHBOUR: slot `slot` of the neighbour
+ * row of the particle stored at position `index` in the library's current cell-sorted
+ * order; what = SPH_DEBUG_WALL_OFFSET: entry `index` of the wall-particle cell offsets
+ * (0..n_cells; kept from sph_create, read by every configuration update). Refused
+ * (SPH_E_INVALID) unless the handle was created with SPH_FLAG_DEBUG_BOUNDS, since only then
+ * is every table checked before a kernel reads it; an out-of-range index or slot is
+ * SPH_E_INVALID too. Synchronous. */
+#define SPH_DEBUG_NEIGHBOUR    1
+#define SPH_DEBUG_WALL_OFFSET  2
+int sph_debug_write(sph_handle* h, int32_t what, int64_t index, int32_t slot, int64_t value,
+                    void* stream);
 
 /* Configuration update (paper Sec. 2.4 / Sec. 6.2 mesh_cell_linked_list): hash
  * particles to search cells, sort by (search cell, id), cell offsets, reorder the state, and
@@ -402,7 +435,8 @@ int sph_reaction_step(sph_handle* h, sph_species* sp, const sph_reaction* r, dou
  * and hosts that forbid runtime allocation after start-up), for whom creating a
  * handle is not an option. It computes the same FP64 fields as sph_diagnostics
  * (t, dt_ad and the step counters are 0) from the caller's arrays in caller order:
- * pos, vel [n*dim], rho, mass [n], all double and all in DEVICE memory; p supplies
+ * pos, vel [n*dim], rho, mass [n], all double and all in DEVICE memory of the current
+ * device (or managed memory); p supplies
  * dim, rho0, c0 and gravity. out is a host struct; the call synchronises stream.
  * It calls no cudaMalloc, cudaFree or allocating library routine. Its scratch is
  * a fixed 131,200-byte array in the library's device image (1024 blocks of 16
@@ -410,8 +444,10 @@ int sph_reaction_step(sph_handle* h, sph_species* sp, const sph_reaction* r, dou
  * until exit. The first call on each device looks up that array's address with the
  * device current; make that first call before any stream capture begins. Calls
  * share the array and overwrite all of it that they read, so calls that overlap on
- * the GPU race. n above 2^31 - 1, dim not 2 or 3, host pointers or a missing array
- * return SPH_E_INVALID with a message in sph_last_error(NULL). */
+ * the GPU race. n above 2^31 - 1, dim not 2 or 3, host pointers, another device's
+ * memory or a missing array return SPH_E_INVALID with a message in sph_last_error(NULL);
+ * a failed launch returns SPH_E_CUDA (never the previous call's result). The library
+ * cannot see array sizes: each array must hold the n (or n*dim) doubles stated. */
 int sph_diagnostics_noalloc(const sph_params* p, int64_t n, const double* pos, const double* vel,
                             const double* rho, const double* mass, sph_diag* out, void* stream);
 

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <initializer_list>
 #include <map>
 #include <sstream>
 #include <string>
@@ -121,6 +122,7 @@ int check_params(const sph_params* p, std::string* why) {
   if (p->capacity < 0 || p->capacity > 65535) return bad("capacity must be in [0, 65535]");
   if (p->free_surface != 0 && p->free_surface != 1) return bad("free_surface must be 0 or 1");
   if (!(std::isfinite(p->p_transport) && p->p_transport >= 0.0)) return bad("p_transport must be >= 0");
+  if (p->max_substeps < 0) return bad("max_substeps must be >= 0");
   if (p->p_transport > 0.0 && (p->flags & SPH_FLAG_FROZEN_GEOMETRY))
     return bad("the transport velocity needs the recomputed pair geometry (no SPH_FLAG_FROZEN_GEOMETRY)");
   double period = 0.0;
@@ -188,6 +190,7 @@ Inst make_inst(const sph_params& p) {
   I.eta = (float)(p.rho0 * p.nu);
   I.mass = 0.0f;
   I.p_tv = (float)p.p_transport;
+  I.max_sub = p.max_substeps > 0 ? p.max_substeps : sph::kMaxSubstepsPerStep;
   for (int a = 0; a < 3; ++a) {
     I.ncell[a] = ncell[a];
     I.scell[a] = a < d ? 2 * ncell[a] : 1;
@@ -209,6 +212,7 @@ Inst make_inst(const sph_params& p) {
   return I;
 }
 
+// Memory the current device addresses directly: its own device memory or managed memory.
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -216,10 +220,40 @@ bool is_device_ptr(const void* p) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  int cur = -1;
+  if (at.type != cudaMemoryTypeDevice || cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.device == cur;
+}
+
+// Device memory of a GPU other than the current one. The kernels run on the current
+// device, so the entry points reject such arrays instead of dereferencing them.
+bool foreign_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int cur = -1;
+  if (at.type != cudaMemoryTypeDevice || cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.device != cur;
+}
+
+bool any_foreign(std::initializer_list<const void*> ptrs) {
+  for (const void* p : ptrs)
+    if (foreign_device_ptr(p)) return true;
+  return false;
 }
 
 int status_code(const Global& g) {
+  if (g.err & sph::ERR_BOUNDS) return SPH_E_BOUNDS;
   if (g.err & sph::ERR_DOMAIN) return SPH_E_DOMAIN;
   if (g.err & sph::ERR_CAPACITY) return SPH_E_CAPACITY;
   if (g.err & (sph::ERR_NAN | sph::ERR_DT)) return SPH_E_UNSTABLE;
@@ -243,8 +277,43 @@ int sync_status(sph_handle* h, cudaStream_t s) {
 
 void enqueue_build(sph_handle* h, cudaStream_t s, int64_t* n) {
   sph::launch_hash(h->b, s, n);
+  sph::launch_fluid_offsets(h->b, s, n);
   sph::launch_sort_fluid(h->b, s, n);
   sph::launch_neighbours(h->b, s, n);
+}
+
+bool debug_bounds(const sph_handle* h) { return (h->flags & SPH_FLAG_DEBUG_BOUNDS) != 0; }
+
+// SPH_FLAG_DEBUG_BOUNDS: check the cell offsets and the neighbour table, synchronously,
+// before anything reads them; SPH_OK when the flag is off.
+int debug_check(sph_handle* h, cudaStream_t s) {
+  if (!debug_bounds(h)) return SPH_OK;
+  sph::launch_check_offsets(h->b, s, &h->launches);
+  sph::launch_check_table(h->b, s, &h->launches);
+  CK(h, cudaGetLastError());
+  return sync_status(h, s);
+}
+
+// Configuration update. With SPH_FLAG_DEBUG_BOUNDS the offsets are checked after the scan
+// and before the scatter and the neighbour search read them, and the new table after it is
+// written; otherwise the four stages are only enqueued.
+int run_build(sph_handle* h, cudaStream_t s) {
+  if (!debug_bounds(h)) {
+    enqueue_build(h, s, &h->launches);
+    CK(h, cudaGetLastError());
+    return SPH_OK;
+  }
+  sph::launch_hash(h->b, s, &h->launches);
+  sph::launch_fluid_offsets(h->b, s, &h->launches);
+  sph::launch_check_offsets(h->b, s, &h->launches);
+  CK(h, cudaGetLastError());
+  int r = sync_status(h, s);
+  if (r != SPH_OK) return r;
+  sph::launch_sort_fluid(h->b, s, &h->launches);
+  sph::launch_neighbours(h->b, s, &h->launches);
+  sph::launch_check_table(h->b, s, &h->launches);
+  CK(h, cudaGetLastError());
+  return sync_status(h, s);
 }
 
 void enqueue_advection(sph_handle* h, cudaStream_t s, int64_t* n) {
@@ -421,6 +490,7 @@ void drop_graph(sph_handle* h) {
 }  // namespace
 
 int sph_sync_status(sph_handle* h, cudaStream_t s) { return sync_status(h, s); }
+int sph_debug_check(sph_handle* h, cudaStream_t s) { return debug_check(h, s); }
 
 extern "C" {
 
@@ -454,6 +524,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
   if (n_wall > 0 && (!wall_pos || !wall_normal || !wall_vol)) return SPH_E_INVALID;
   if (n_instances > 1 && (!fluid_offsets || !wall_offsets)) return SPH_E_INVALID;
   if (n_fluid >= (1ll << 31) || n_wall >= (1ll << 31)) return SPH_E_INVALID;
+  if (any_foreign({pos, vel, rho, mass, wall_pos, wall_normal, wall_vol})) return SPH_E_INVALID;
   for (int k = 0; k < n_instances; ++k) {
     if (check_params(&params[k], nullptr) != SPH_OK) return SPH_E_INVALID;
     if (params[k].dim != params[0].dim) return SPH_E_INVALID;
@@ -633,6 +704,7 @@ int sph_set_state(sph_handle* h, const double* pos, const double* vel, const dou
   if (!h) return SPH_E_INVALID;
   Buffers& b = h->b;
   if (b.n > 0 && (!pos || !vel || !rho)) return fail(h, SPH_E_INVALID, "pos, vel and rho are required");
+  if (any_foreign({pos, vel, rho, drho_dt})) return fail(h, SPH_E_INVALID, "an array lives on another device");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = (size_t)b.n, d = (size_t)b.dim;
   const bool host_all = b.n >= kUploadChunkMin && !is_device_ptr(pos) && !is_device_ptr(vel) &&
@@ -689,8 +761,8 @@ int sph_set_state(sph_handle* h, const double* pos, const double* vel, const dou
 int sph_build_cells(sph_handle* h, void* stream) {
   if (!h) return SPH_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  enqueue_build(h, s, &h->launches);
-  CK(h, cudaGetLastError());
+  int r = run_build(h, s);
+  if (r != SPH_OK) return r;
   h->cells_valid = true;
   return SPH_OK;
 }
@@ -699,6 +771,8 @@ int sph_advection_step(sph_handle* h, double* dt_ad_out, void* stream) {
   if (!h) return SPH_E_INVALID;
   if (!h->cells_valid) return fail(h, SPH_E_INVALID, "sph_build_cells must run after a state change");
   cudaStream_t s = (cudaStream_t)stream;
+  int rc = debug_check(h, s);
+  if (rc != SPH_OK) return rc;
   enqueue_advection(h, s, &h->launches);
   CK(h, cudaGetLastError());
   if (dt_ad_out) {
@@ -711,6 +785,8 @@ int sph_advection_step(sph_handle* h, double* dt_ad_out, void* stream) {
 int sph_acoustic_substep(sph_handle* h, int32_t* done_out, double* dt_out, void* stream) {
   if (!h) return SPH_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
+  int rc = debug_check(h, s);
+  if (rc != SPH_OK) return rc;
   enqueue_substep(h, s, false, &h->launches);
   CK(h, cudaGetLastError());
   if (done_out || dt_out || h->timing) {
@@ -734,7 +810,7 @@ int sph_acoustic_substep(sph_handle* h, int32_t* done_out, double* dt_out, void*
 int sph_step(sph_handle* h, int32_t n_advection_steps, void* stream) {
   if (!h || n_advection_steps < 0) return SPH_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((h->flags & SPH_FLAG_GRAPH) && !h->timing) {
+  if ((h->flags & SPH_FLAG_GRAPH) && !h->timing && !debug_bounds(h)) {
     if (!h->gexec) {
       int r = build_graph(h);
       if (r != SPH_OK) return r;
@@ -750,7 +826,8 @@ int sph_step(sph_handle* h, int32_t n_advection_steps, void* stream) {
     return r;
   }
   for (int k = 0; k < n_advection_steps; ++k) {
-    enqueue_build(h, s, &h->launches);
+    int rb = run_build(h, s);
+    if (rb != SPH_OK) return rb;
     h->cells_valid = true;
     enqueue_advection(h, s, &h->launches);
     for (int guard = 0;; ++guard) {
@@ -804,6 +881,7 @@ int sph_get_state(sph_handle* h, double* pos, double* vel, double* rho, double* 
   Buffers& b = h->b;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = (size_t)b.n, d = (size_t)b.dim;
+  if (any_foreign({pos, vel, rho, drho_dt})) return fail(h, SPH_E_INVALID, "an array lives on another device");
   if (n == 0) return SPH_OK;
   double* dst[4] = {pos, vel, rho, drho_dt};
   size_t sz[4] = {n * d, n * d, n, n};
@@ -825,6 +903,7 @@ int sph_get_state(sph_handle* h, double* pos, double* vel, double* rho, double* 
 int sph_get_acceleration(sph_handle* h, double* acc, void* stream) {
   if (!h || !acc) return SPH_E_INVALID;
   if (!h->b.acc_keep) return fail(h, SPH_E_INVALID, "create the handle with SPH_FLAG_KEEP_ACC");
+  if (foreign_device_ptr(acc)) return fail(h, SPH_E_INVALID, "acc lives on another device");
   cudaStream_t s = (cudaStream_t)stream;
   size_t e = (size_t)h->b.n * h->b.dim;
   bool dev = is_device_ptr(acc);
@@ -847,6 +926,8 @@ int sph_get_neighbours(sph_handle* h, int32_t* fluid_count, int32_t* wall_count,
   if (!h || !fluid_count || !wall_count || !fluid_ids || !wall_ids) return SPH_E_INVALID;
   if (stride < h->b.cap) return fail(h, SPH_E_INVALID, "stride must be >= capacity");
   cudaStream_t s = (cudaStream_t)stream;
+  int rc = debug_check(h, s);
+  if (rc != SPH_OK) return rc;
   const size_t n = (size_t)h->b.n;
   if (n == 0) return SPH_OK;
   int32_t *fc, *wc, *fi, *wi;
@@ -871,6 +952,8 @@ int sph_get_neighbours(sph_handle* h, int32_t* fluid_count, int32_t* wall_count,
 int sph_pair_count(sph_handle* h, int64_t* fluid_pairs, int64_t* wall_pairs, void* stream) {
   if (!h || !fluid_pairs || !wall_pairs) return SPH_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
+  int rc = debug_check(h, s);
+  if (rc != SPH_OK) return rc;
   unsigned long long* d = reinterpret_cast<unsigned long long*>(h->diag_out);
   unsigned long long hv[2] = {0, 0};
   sph::launch_pair_count(h->b, d, s);
@@ -905,7 +988,8 @@ int sph_set_launch_config(sph_handle* h, const int32_t* cfg) {
 int sph_autotune(sph_handle* h, int32_t* cfg_out, double* ms_out, void* stream) {
   if (!h) return SPH_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  enqueue_build(h, s, &h->launches);
+  int rb = run_build(h, s);
+  if (rb != SPH_OK) return rb;
   h->cells_valid = true;
   enqueue_advection(h, s, &h->launches);
   sph::launch_dt_acoustic(h->b, s, h->cond, false, &h->launches);
@@ -964,6 +1048,8 @@ int sph_gather_ceiling(sph_handle* h, int32_t reps, double* ms_out, void* stream
   if (!h || !ms_out || reps < 1) return SPH_E_INVALID;
   if (!h->cells_valid) return fail(h, SPH_E_INVALID, "sph_build_cells must run first");
   cudaStream_t s = (cudaStream_t)stream;
+  int rc = debug_check(h, s);
+  if (rc != SPH_OK) return rc;
   unsigned* sink = reinterpret_cast<unsigned*>(h->diag_out);
   sph::launch_gather_ceiling(h->b, sink, s, &h->launches);        // warm-up
   CK(h, cudaEventRecord(h->ev[0], s));
@@ -974,6 +1060,38 @@ int sph_gather_ceiling(sph_handle* h, int32_t reps, double* ms_out, void* stream
   CK(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
   *ms_out = (double)ms / reps;
   return sync_status(h, s);
+}
+
+int sph_clear_error(sph_handle* h, void* stream) {
+  if (!h) return SPH_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(h, cudaMemsetAsync(&h->b.glob->err, 0, sizeof(int), s));
+  CK(h, cudaMemsetAsync(&h->b.glob->bad_index, 0, sizeof(long long), s));
+  CK(h, cudaStreamSynchronize(s));
+  h->err.clear();
+  return SPH_OK;
+}
+
+int sph_debug_write(sph_handle* h, int32_t what, int64_t index, int32_t slot, int64_t value, void* stream) {
+  if (!h) return SPH_E_INVALID;
+  if (!debug_bounds(h)) return fail(h, SPH_E_INVALID, "sph_debug_write needs a handle created with SPH_FLAG_DEBUG_BOUNDS");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Buffers& b = h->b;
+  if (what == SPH_DEBUG_NEIGHBOUR) {
+    if (index < 0 || index >= b.n || slot < 0 || slot >= b.cap)
+      return fail(h, SPH_E_INVALID, "sph_debug_write: row or slot out of range");
+    const int v = (int)value;
+    const int64_t at = ((int64_t)(slot >> 2) * b.n + index) * 4 + (slot & 3);
+    CK(h, cudaMemcpyAsync(b.nbr + at, &v, sizeof(int), cudaMemcpyHostToDevice, s));
+  } else if (what == SPH_DEBUG_WALL_OFFSET) {
+    if (index < 0 || index > b.n_cells) return fail(h, SPH_E_INVALID, "sph_debug_write: cell out of range");
+    const uint32_t v = (uint32_t)value;
+    CK(h, cudaMemcpyAsync(b.wstart + index, &v, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  } else {
+    return fail(h, SPH_E_INVALID, "sph_debug_write: unknown table");
+  }
+  CK(h, cudaStreamSynchronize(s));
+  return SPH_OK;
 }
 
 int sph_kernel_launches(sph_handle* h, int64_t* out) {

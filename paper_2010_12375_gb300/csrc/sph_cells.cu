@@ -385,6 +385,49 @@ k_neighbours(int64_t n, const int4* __restrict__ P, const int* __restrict__ inst
   nbc[i] = (uint32_t)nf | ((uint32_t)nw << 16);
 }
 
+// ---------------------------------------------------------------- debug bounds checks --
+// SPH_FLAG_DEBUG_BOUNDS: the offsets of a cell-linked list must start at 0, never decrease
+// and end at the particle count; a neighbour row must fit the capacity with every fluid
+// index below n and every wall index below nw. Each check reads only inside the arrays'
+// own extents, whatever values they hold, and records the first violation.
+__global__ void k_check_offsets(int64_t n_cells, const uint32_t* __restrict__ start, uint32_t total,
+                                Global* g) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > n_cells) return;
+  bool bad = start[c] > total;
+  if (c == 0) bad = bad || start[0] != 0u;
+  if (c == n_cells) bad = bad || start[c] != total;
+  else bad = bad || start[c] > start[c + 1];
+  if (bad) raise_error(g, ERR_BOUNDS, c);
+}
+
+__global__ void k_check_table(int64_t n, int64_t nw, int cap, const int* __restrict__ nbr,
+                              const uint32_t* __restrict__ nbc, Global* g) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t cnt = nbc[i];
+  const int nf = (int)(cnt & 0xffffu), nwi = (int)(cnt >> 16);
+  if (nf > cap || wall_slot0(nf) + nwi > cap) {
+    raise_error(g, ERR_BOUNDS, i);
+    return;
+  }
+  for (int s = 0; s < nf; ++s) {
+    const int j = nbr[slot_index(n, i, s)];
+    if (j < 0 || (int64_t)j >= n) {
+      raise_error(g, ERR_BOUNDS, i);
+      return;
+    }
+  }
+  const int w0 = wall_slot0(nf);
+  for (int s = 0; s < nwi; ++s) {
+    const int w = nbr[slot_index(n, i, w0 + s)];
+    if (w < 0 || (int64_t)w >= nw) {
+      raise_error(g, ERR_BOUNDS, i);
+      return;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- walls ---------------
 __global__ void k_wall_reorder(int64_t n, const int* __restrict__ src, const uint32_t* __restrict__ dst,
                                const int* __restrict__ key, const int4* __restrict__ Pin,
@@ -453,8 +496,11 @@ void launch_hash(const Buffers& b, cudaStream_t s, int64_t* launches) {
   ++*launches;
 }
 
-void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches) {
+void launch_fluid_offsets(const Buffers& b, cudaStream_t s, int64_t* launches) {
   scan_exclusive(b.count, b.fstart, b.n_cells, b.scan_tmp, s, launches);
+}
+
+void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches) {
   if (b.n == 0) return;
   k_scatter<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.cell, b.rank, b.fstart, b.id, b.key, b.src);
   // final slots into rank (free after the scatter); sorted ids into cell (free after the rank)
@@ -501,6 +547,18 @@ void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStre
   cudaMemcpyAsync(b.WP, WP_tmp, sizeof(int4) * b.nw, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(b.WN, WN_tmp, sizeof(float4) * b.nw, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(b.wid, wids_sorted, sizeof(int) * b.nw, cudaMemcpyDeviceToDevice, s);
+}
+
+void launch_check_offsets(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  k_check_offsets<<<grid_for(b.n_cells + 1), kBlock, 0, s>>>(b.n_cells, b.fstart, (uint32_t)b.n, b.glob);
+  k_check_offsets<<<grid_for(b.n_cells + 1), kBlock, 0, s>>>(b.n_cells, b.wstart, (uint32_t)b.nw, b.glob);
+  *launches += 2;
+}
+
+void launch_check_table(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  if (b.n == 0) return;
+  k_check_table<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.nw, b.cap, b.nbr, b.nbc, b.glob);
+  ++*launches;
 }
 
 void launch_iota(int* a, int64_t n, cudaStream_t s) {

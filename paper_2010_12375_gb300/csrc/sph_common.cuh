@@ -20,9 +20,9 @@ namespace sph {
 
 constexpr float kLimiter = 3.0f;        // dissipation limiter of the low-dissipation solver
 constexpr double kLoopSlack = 1e-12;     // substep loop runs while tau < Dt_ad (1 - slack)
-constexpr int kMaxSubstepsPerStep = 1000; // bound of the device-side substep loop (normal: <= 6)
+constexpr int kMaxSubstepsPerStep = 1000; // default bound of the device-side substep loop (normal: <= 6)
 
-enum : int { ERR_DOMAIN = 1, ERR_NAN = 2, ERR_CAPACITY = 4, ERR_DT = 8, ERR_TIMEOUT = 16 };
+enum : int { ERR_DOMAIN = 1, ERR_NAN = 2, ERR_CAPACITY = 4, ERR_DT = 8, ERR_TIMEOUT = 16, ERR_BOUNDS = 32 };
 
 // Per-instance constants (one tank), read-only on the device.
 struct Inst {
@@ -48,6 +48,7 @@ struct Inst {
   int   bits;
   int   sbits;                   // search cell of a particle: q >> sbits, sbits = bits - 1
   int   free_surface;
+  int   max_sub;                 // bound of the substep loop of one advection step
   long long R2;                  // integer neighbour threshold
   long long cell_base;           // first global cell of this instance
   long long fluid_begin, fluid_end;

@@ -325,13 +325,25 @@ int sfail(sph_species* sp, int code, const std::string& msg) {
   return code;
 }
 
-bool device_pointer(const void* p) {
+// Where a caller array lives: host memory (copied through the staging buffer), memory
+// the current device can address directly, or device memory of another GPU (rejected:
+// the kernels run on the current device).
+enum PtrKind { kHostPtr, kDevicePtr, kOtherDevicePtr };
+
+PtrKind pointer_kind(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return kHostPtr;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return kDevicePtr;
+  if (a.type != cudaMemoryTypeDevice) return kHostPtr;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return kOtherDevicePtr;
+  }
+  return a.device == cur ? kDevicePtr : kOtherDevicePtr;
 }
 
 // Cholesky factor of a symmetric d x d tensor (row-major); false unless positive definite.
@@ -443,7 +455,9 @@ int species_upload(sph_handle* h, sph_species* sp, const double* C, float* dst, 
   if (!C) return sfail(sp, SPH_E_INVALID, "the array is required");
   cudaStream_t s = (cudaStream_t)stream;
   const double* src = C;
-  if (!device_pointer(C)) {
+  const PtrKind kind = pointer_kind(C);
+  if (kind == kOtherDevicePtr) return sfail(sp, SPH_E_INVALID, "the array lives on another device");
+  if (kind == kHostPtr) {
     if (cudaMemcpyAsync(sp->stage, C, sizeof(double) * sp->n, cudaMemcpyHostToDevice, s) != cudaSuccess)
       return sfail(sp, SPH_E_CUDA, "copy of the species failed");
     src = sp->stage;
@@ -461,7 +475,9 @@ int species_download(sph_handle* h, sph_species* sp, const float* src, double* C
   if (sp->n == 0) return SPH_OK;
   if (!C) return sfail(sp, SPH_E_INVALID, "the array is required");
   cudaStream_t s = (cudaStream_t)stream;
-  const bool dev = device_pointer(C);
+  const PtrKind kind = pointer_kind(C);
+  if (kind == kOtherDevicePtr) return sfail(sp, SPH_E_INVALID, "the array lives on another device");
+  const bool dev = kind == kDevicePtr;
   double* dst = dev ? C : sp->stage;
   sph::k_species_export<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, s>>>(sp->n, src, dst);
   ++h->launches;
@@ -505,23 +521,31 @@ int sph_species_set_scale(sph_handle* h, sph_species* sp, const double* s, void*
       return sfail(sp, SPH_E_OOM, "device allocation of the diffusivity factors failed");
     }
   }
-  int r = species_upload(h, sp, s, sp->scale_by_row, stream);
-  if (r != SPH_OK) return r;
-  cudaStream_t st = (cudaStream_t)stream;
-  int bad = 0;
-  if (cudaMemsetAsync(sp->nonuniform, 0, sizeof(int), st) != cudaSuccess) return sfail(sp, SPH_E_CUDA, "check failed");
-  sph::k_check_scale<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, st>>>(sp->n, sp->scale_by_row, sp->nonuniform);
-  ++h->launches;
-  if (cudaMemcpyAsync(&bad, sp->nonuniform, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return sfail(sp, SPH_E_CUDA, "check failed");
-  if (bad) {                       // back to no factors
+  // any failure from here on leaves the species with no factors, as before the first call
+  auto drop_factors = [sp](int code, const char* msg) {
     cudaFree(sp->scale_by_row);
     cudaFree(sp->sq);
     sp->scale_by_row = nullptr;
     sp->sq = nullptr;
-    return sfail(sp, SPH_E_INVALID, "diffusivity factors must be positive and finite");
+    if (msg) sp->err = msg;
+    return code;
+  };
+  int r = species_upload(h, sp, s, sp->scale_by_row, stream);
+  if (r != SPH_OK) return drop_factors(r, nullptr);
+  cudaStream_t st = (cudaStream_t)stream;
+  int bad = 0;
+  if (cudaMemsetAsync(sp->nonuniform, 0, sizeof(int), st) != cudaSuccess) {
+    cudaGetLastError();
+    return drop_factors(SPH_E_CUDA, "check failed");
   }
+  sph::k_check_scale<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, st>>>(sp->n, sp->scale_by_row, sp->nonuniform);
+  ++h->launches;
+  if (cudaMemcpyAsync(&bad, sp->nonuniform, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return drop_factors(SPH_E_CUDA, "check failed");
+  }
+  if (bad) return drop_factors(SPH_E_INVALID, "diffusivity factors must be positive and finite");
   return SPH_OK;
 }
 
@@ -551,6 +575,10 @@ int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_step
   if (sp->n != h->b.n || sp->dim != h->b.dim) return sfail(sp, SPH_E_INVALID, "species belongs to another handle");
   if (!(std::isfinite(dt) && dt > 0.0) || n_steps < 0) return sfail(sp, SPH_E_INVALID, "dt must be > 0 and n_steps >= 0");
   if (!h->cells_valid) return sfail(sp, SPH_E_INVALID, "sph_build_cells must run after a state change");
+  {
+    const int r = sph_debug_check(h, (cudaStream_t)stream);
+    if (r != SPH_OK) return sfail(sp, r, "neighbour table check failed (SPH_FLAG_DEBUG_BOUNDS)");
+  }
   const sph::Buffers& b = h->b;
   if (b.n == 0 || n_steps == 0) return SPH_OK;
   cudaStream_t s = (cudaStream_t)stream;

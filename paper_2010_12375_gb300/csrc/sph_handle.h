@@ -42,3 +42,6 @@ struct sph_handle {
 
 // Host-side helpers of sph_api.cu used by the other C-ABI translation units.
 int sph_sync_status(sph_handle* h, cudaStream_t s);
+// SPH_FLAG_DEBUG_BOUNDS: check the cell offsets and the neighbour table before a kernel reads
+// them (synchronous); SPH_OK at once when the flag is off.
+int sph_debug_check(sph_handle* h, cudaStream_t s);

@@ -59,7 +59,11 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
 
 // cell build
 void launch_hash(const Buffers& b, cudaStream_t s, int64_t* launches);
-void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_fluid_offsets(const Buffers& b, cudaStream_t s, int64_t* launches);   // scan of the counts
+void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches);      // scatter, rank, reorder
+// SPH_FLAG_DEBUG_BOUNDS checks: the fluid and wall cell offsets, the neighbour table
+void launch_check_offsets(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_check_table(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_neighbours(const Buffers& b, cudaStream_t s, int64_t* launches);
 void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStream_t s);
 void flag_near_wall_cells(const Buffers& b, uint8_t* tmp, cudaStream_t s);

@@ -2,7 +2,8 @@
 //
 // A message-passing network over the frozen neighbour graph of the step predicts each
 // fluid particle's velocity and density change over Dt_ad (the network is the project's
-// own; the paper has none). Definition, shared with the FP64 reference (oracle/mpnn.py):
+// own; the paper has none). Definition (an FP64 reference implementation of the same
+// network is kept with the tests):
 //   u_i  = [v_i/c0, 100 (rho_i/rho0 - 1), Dt_ad c0/h, 1]                      K = 16
 //   x_ij = [r_ij/h, (v_i - v_j)/c0, 100 dev_i, 100 dev_j, wall]  (walls: v_j = 0, dev_j = 0)
 //   h_i  = relu(W_enc u_i)
@@ -1083,13 +1084,37 @@ __global__ void k_export_y(int64_t n, int dout, const float* __restrict__ Y, con
   for (int c = 0; c < dout; ++c) y[row * dout + c] = (double)Y[i * 16 + c];
 }
 
+// Memory the current device can address directly (its own or managed); device memory
+// of another GPU counts as not addressable (see foreign_ptr).
 bool device_ptr(const void* p) {
   cudaPointerAttributes at;
   if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  int cur = -1;
+  if (at.type != cudaMemoryTypeDevice || cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.device == cur;
+}
+
+// Device memory of a GPU other than the current one: rejected by the entry points, since
+// the kernels run on the current device.
+bool foreign_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int cur = -1;
+  if (at.type != cudaMemoryTypeDevice || cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.device != cur;
 }
 
 int lfail(sph_learned* L, int code, const char* msg) {
@@ -1101,10 +1126,12 @@ void upload_weights_bf16(sph_learned* L, cudaStream_t s) {
   k_weights_bf16<<<blocks_for(kWeights), 256, 0, s>>>(L->w32, L->wb, L->wbt);
 }
 
-int ready(sph_handle* h, sph_learned* L) {
+int ready(sph_handle* h, sph_learned* L, void* stream) {
   if (!h || !L) return SPH_E_INVALID;
   if (h->b.dim != L->dim) return lfail(L, SPH_E_INVALID, "network and handle dimensions differ");
   if (!h->cells_valid) return lfail(L, SPH_E_INVALID, "run sph_build_cells and sph_advection_step first");
+  const int r = sph_debug_check(h, (cudaStream_t)stream);
+  if (r != SPH_OK) return lfail(L, r, "neighbour table check failed (SPH_FLAG_DEBUG_BOUNDS)");
   return SPH_OK;
 }
 
@@ -1186,11 +1213,12 @@ int sph_learned_set_fused(sph_learned* L, int32_t enabled) {
 }
 
 int sph_learned_predict(sph_handle* h, sph_learned* L, double* y, void* stream) {
-  int r = ready(h, L);
+  int r = ready(h, L, stream);
   if (r != SPH_OK) return r;
   cudaStream_t s = (cudaStream_t)stream;
   r = build_inputs(h, L, s);
   if (r != SPH_OK) return lfail(L, r, "building the network inputs failed");
+  if (foreign_ptr(y)) return lfail(L, SPH_E_INVALID, "y lives on another device");
   forward(h, L, s, false);
   if (y) {
     const int dout = h->b.dim + 1;
@@ -1211,9 +1239,10 @@ int sph_learned_predict(sph_handle* h, sph_learned* L, double* y, void* stream) 
 
 int sph_learned_train_step(sph_handle* h, sph_learned* L, const double* target, double lr, double* loss_out,
                            float* grad_out, void* stream) {
-  int r = ready(h, L);
+  int r = ready(h, L, stream);
   if (r != SPH_OK) return r;
   if (!target) return lfail(L, SPH_E_INVALID, "target is required");
+  if (foreign_ptr(target)) return lfail(L, SPH_E_INVALID, "target lives on another device");
   cudaStream_t s = (cudaStream_t)stream;
   r = build_inputs(h, L, s);
   if (r != SPH_OK) return lfail(L, r, "building the network inputs failed");

@@ -104,13 +104,22 @@ __global__ void k_noalloc_final(int blocks, double* __restrict__ scratch) {
   for (int f = 0; f < kNaFields; ++f) scratch[(size_t)kNaBlocks * kNaFields + f] = r[f];
 }
 
+// Device memory of the current device, or managed memory: the kernels run on the current
+// device and read the arrays directly. Device memory of another GPU is refused (its
+// addresses are not this device's, and the scratch address is looked up per device).
 bool on_device(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  int cur = -1;
+  if (at.type != cudaMemoryTypeDevice || cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.device == cur;
 }
 
 // Device address of the scratch array on the current device, looked up once per
@@ -151,7 +160,7 @@ extern "C" int sph_diagnostics_noalloc(const sph_params* p, int64_t n, const dou
   if (n > 0 && (!pos || !vel || !rho || !mass))
     return fail(SPH_E_INVALID, "sph_diagnostics_noalloc: pos, vel, rho and mass are required");
   if (n > 0 && (!on_device(pos) || !on_device(vel) || !on_device(rho) || !on_device(mass)))
-    return fail(SPH_E_INVALID, "sph_diagnostics_noalloc: arrays must be device memory");
+    return fail(SPH_E_INVALID, "sph_diagnostics_noalloc: arrays must be device memory of the current device");
   double* scratch = nullptr;
   int r = scratch_address(&scratch);
   if (r != SPH_OK) return r;
@@ -161,7 +170,13 @@ extern "C" int sph_diagnostics_noalloc(const sph_params* p, int64_t n, const dou
   k_noalloc_partial<<<blocks, kNaThreads, 0, s>>>(n, p->dim, pos, vel, rho, mass, p->gravity[0],
                                                   p->gravity[1], p->dim == 3 ? p->gravity[2] : 0.0,
                                                   p->rho0, p->c0, scratch);
-  k_noalloc_final<<<1, 1, 0, s>>>(blocks, scratch);
+  cudaError_t le = cudaGetLastError();
+  if (le == cudaSuccess) {
+    k_noalloc_final<<<1, 1, 0, s>>>(blocks, scratch);
+    le = cudaGetLastError();
+  }
+  if (le != cudaSuccess)      // the result row would be a previous call's: report, do not read
+    return fail(SPH_E_CUDA, "sph_diagnostics_noalloc: kernel launch failed");
   double v[kNaFields];
   cudaError_t e = cudaMemcpyAsync(v, scratch + (size_t)kNaBlocks * kNaFields, sizeof(v),
                                   cudaMemcpyDeviceToHost, s);

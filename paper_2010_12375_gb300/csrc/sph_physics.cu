@@ -255,11 +255,16 @@ __global__ void k_dt_acoustic(int n_inst, const Inst* __restrict__ inst, Ctrl* c
     double dt_ac = I.cfl_ac * I.h_d / (I.c0_d + vmax);
     double rem = C.dt_ad - C.tau;
     double dt = fmin(dt_ac, rem);
-    // a non-finite or vanishing step, or a runaway substep count, ends the loop with an
-    // error instead of letting the device-side loop spin
-    if (!(dt_ac > 1e-12 * I.h_d / I.c0_d) || !(rem > 0.0) || !(dt > 0.0) ||
-        C.sub_in_step >= kMaxSubstepsPerStep) {
+    // a non-finite or vanishing step ends the loop with an error, and so does a substep
+    // count beyond the tank's bound (a timeout), instead of letting the device-side loop spin
+    if (!(dt_ac > 1e-12 * I.h_d / I.c0_d) || !(rem > 0.0) || !(dt > 0.0)) {
       atomicOr(&g->err, ERR_DT);
+      C.dt = 0.0;
+      C.done = 1;
+      continue;
+    }
+    if (C.sub_in_step >= I.max_sub) {
+      atomicOr(&g->err, ERR_TIMEOUT);
       C.dt = 0.0;
       C.done = 1;
       continue;

@@ -20,12 +20,17 @@ SPH_E_DOMAIN = -4
 SPH_E_UNSTABLE = -5
 SPH_E_CAPACITY = -6
 SPH_E_TIMEOUT = -7
+SPH_E_BOUNDS = -8
 SPH_FLAG_GRAPH = 1
 SPH_FLAG_KEEP_ACC = 2
 SPH_FLAG_FROZEN_GEOMETRY = 4
+SPH_FLAG_DEBUG_BOUNDS = 8
+SPH_DEBUG_NEIGHBOUR = 1
+SPH_DEBUG_WALL_OFFSET = 2
 
 ERROR_NAMES = {0: "SPH_OK", -1: "SPH_E_INVALID", -2: "SPH_E_CUDA", -3: "SPH_E_OOM",
-               -4: "SPH_E_DOMAIN", -5: "SPH_E_UNSTABLE", -6: "SPH_E_CAPACITY", -7: "SPH_E_TIMEOUT"}
+               -4: "SPH_E_DOMAIN", -5: "SPH_E_UNSTABLE", -6: "SPH_E_CAPACITY", -7: "SPH_E_TIMEOUT",
+               -8: "SPH_E_BOUNDS"}
 
 # every function declared in include/sph.h
 EXPORTS = [
@@ -40,7 +45,7 @@ EXPORTS = [
     "sph_learned_set_fused", "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
     "sph_species_create", "sph_species_destroy", "sph_species_last_error", "sph_species_set",
     "sph_species_get", "sph_diffusion_step", "sph_species_set_gate", "sph_species_get_gate",
-    "sph_reaction_step", "sph_species_set_scale",
+    "sph_reaction_step", "sph_species_set_scale", "sph_clear_error", "sph_debug_write",
 ]
 
 
@@ -53,7 +58,7 @@ class SphParams(ctypes.Structure):
         ("u_ref", ctypes.c_double), ("nu", ctypes.c_double),
         ("gravity", ctypes.c_double * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
         ("periodic", ctypes.c_int32 * 3), ("capacity", ctypes.c_int32), ("flags", ctypes.c_uint32),
-        ("p_transport", ctypes.c_double),
+        ("p_transport", ctypes.c_double), ("max_substeps", ctypes.c_int32),
     ]
 
 
@@ -160,6 +165,8 @@ def load():
         "sph_species_get_gate": (i32, [P, P, P, P]),
         "sph_reaction_step": (i32, [P, P, ctypes.POINTER(SphReaction), dbl, i32, P]),
         "sph_species_set_scale": (i32, [P, P, P, P]),
+        "sph_clear_error": (i32, [P, P]),
+        "sph_debug_write": (i32, [P, i32, i64, i32, i64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -197,7 +204,7 @@ def _stream(stream):
     return stream.cuda_stream       # torch.cuda.Stream
 
 
-def params_from(problem, flags=0, capacity=0) -> SphParams:
+def params_from(problem, flags=0, capacity=0, max_substeps=0) -> SphParams:
     """Build the C parameter struct from any object carrying the problem's attributes."""
     p = SphParams()
     p.dim = int(problem.dim)
@@ -214,6 +221,7 @@ def params_from(problem, flags=0, capacity=0) -> SphParams:
     p.capacity = int(capacity)
     p.p_transport = float(getattr(problem, "p_transport", 0.0))
     p.flags = int(flags)
+    p.max_substeps = int(max_substeps)
     return p
 
 
@@ -261,6 +269,17 @@ def sph_get_info(h) -> SphInfo:
     info = SphInfo()
     check(lib, h, lib.sph_get_info(h, ctypes.byref(info)))
     return info
+
+
+def sph_clear_error(h, stream=None):
+    lib = load()
+    check(lib, h, lib.sph_clear_error(h, _stream(stream)))
+
+
+def sph_debug_write(h, what, index, slot, value, stream=None):
+    """Overwrite one table entry (test aid; needs a SPH_FLAG_DEBUG_BOUNDS handle)."""
+    lib = load()
+    check(lib, h, lib.sph_debug_write(h, int(what), int(index), int(slot), int(value), _stream(stream)))
 
 
 def sph_build_cells(h, stream=None):
@@ -404,8 +423,24 @@ def sph_diagnostics_noalloc(params: SphParams, pos, vel, rho, mass, stream=None)
     order) without any device allocation by the library. Returns a dict like
     sph_diagnostics."""
     lib = load()
+    import torch
+    dim = int(params.dim)
+    arrays = {"pos": pos, "vel": vel, "rho": rho, "mass": mass}
+    for name, a in arrays.items():
+        # the library cannot see array sizes: a short or mistyped array would be read past
+        # its end on the device, so the binding checks what the C call takes on trust
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64
+                and a.is_contiguous()):
+            raise SphError(SPH_E_INVALID, f"sph_diagnostics_noalloc: {name} must be a contiguous "
+                                          "float64 CUDA tensor")
+        if a.device.index != torch.cuda.current_device():
+            raise SphError(SPH_E_INVALID, f"sph_diagnostics_noalloc: {name} is not on the current device")
+    n = int(rho.numel())
+    if rho.dim() != 1 or mass.dim() != 1 or mass.numel() != n:
+        raise SphError(SPH_E_INVALID, "sph_diagnostics_noalloc: rho and mass must have shape [n]")
+    if pos.numel() != n * dim or vel.numel() != n * dim:
+        raise SphError(SPH_E_INVALID, "sph_diagnostics_noalloc: pos and vel must hold n * dim values")
     out = SphDiag()
-    n = int(rho.shape[0])
     code = lib.sph_diagnostics_noalloc(ctypes.byref(params), n, _ptr(pos), _ptr(vel), _ptr(rho),
                                        _ptr(mass), ctypes.byref(out), _stream(stream))
     if code != SPH_OK:
@@ -572,12 +607,12 @@ def sph_diffusion_step(h, sp, dt, n_steps=1, stream=None):
 class Simulation:
     """One handle over one or more tanks built from workload objects (marshalling only)."""
 
-    def __init__(self, problems, flags=0, capacity=0, stream=None):
+    def __init__(self, problems, flags=0, capacity=0, stream=None, max_substeps=0):
         probs = problems if isinstance(problems, (list, tuple)) else [problems]
         self.problems = probs
         self.dim = int(probs[0].dim)
         self.stream = stream
-        params = [params_from(p, flags=flags, capacity=capacity) for p in probs]
+        params = [params_from(p, flags=flags, capacity=capacity, max_substeps=max_substeps) for p in probs]
         pos = np.concatenate([np.asarray(p.pos, dtype=np.float64).reshape(-1, self.dim) for p in probs])
         vel = np.concatenate([np.asarray(p.vel, dtype=np.float64).reshape(-1, self.dim) for p in probs])
         rho = np.concatenate([np.asarray(p.rho, dtype=np.float64) for p in probs])

@@ -50,7 +50,8 @@ def test_params_check_on_host(lib):
     assert lib.sph_params_check(lib.params_from(wk.taylor_green(50))) == lib.SPH_OK
     assert lib.sph_params_check(lib.params_from(wk.dam_break_3d(10))) == lib.SPH_OK
     cases = [("h", -1.0), ("h", float("nan")), ("dim", 4), ("c0", 0.0), ("cfl_ad", 0.0),
-             ("cfl_ac", -0.6), ("nu", -1.0), ("capacity", -2), ("free_surface", 3)]
+             ("cfl_ac", -0.6), ("nu", -1.0), ("capacity", -2), ("free_surface", 3),
+             ("max_substeps", -1)]
     for field, val in cases:
         p = lib.params_from(wk.dam_break_2d())
         setattr(p, field, val)
@@ -105,3 +106,12 @@ def test_species_and_reaction_entry_points_reject_null_handles(lib):
         assert fn(None, None, buf, None) == lib.SPH_E_INVALID
     L.sph_species_destroy(None)                               # a no-op
     assert L.sph_species_last_error(None) == b"null species"
+
+
+def test_error_control_entry_points_reject_null_handles(lib):
+    L = lib.load()
+    assert L.sph_clear_error(None, None) == lib.SPH_E_INVALID
+    assert L.sph_debug_write(None, lib.SPH_DEBUG_NEIGHBOUR, 0, 0, 0, None) == lib.SPH_E_INVALID
+    p = lib.params_from(__import__("paper_2010_12375_gb300.workloads", fromlist=["x"]).dam_break_2d(),
+                        max_substeps=1)
+    assert p.max_substeps == 1 and lib.sph_params_check(p) == lib.SPH_OK

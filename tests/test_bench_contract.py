@@ -23,7 +23,9 @@ def test_reference_arm_prints_one_contract_line():
     assert line["config"]["workload"].startswith("3D dam break") and "dp = 1/159" in line["config"]["workload"]
     assert line["config"]["sample"]
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    # every host core at once, one process each
+    assert cb["kind"] == "oracle" and cb["cores"] == len(os.sched_getaffinity(0))
+    assert cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

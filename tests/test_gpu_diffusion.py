@@ -292,3 +292,28 @@ def test_uniform_factor_equals_scaled_tensor(sph):
     finally:
         sim.close()
     assert np.max(np.abs(a - b)) <= 8 * 6 * 2.0 ** -24 * np.max(np.abs(C0))
+
+
+def test_failed_factor_upload_leaves_no_factors(sph):
+    # header contract: a set_scale call that fails returns SPH_E_INVALID and leaves no factors,
+    # both on the first call (nothing allocated before) and after factors were set
+    p, D, C0, dt = _case("iso3d")
+    ref = _gpu_run(sph, p, D, C0, dt, 4)
+    sim = sph.Simulation(p)
+    try:
+        sph.sph_build_cells(sim.handle)
+        sp = sph.sph_species_create(sim.handle, D, 3)
+        try:
+            for preset in (None, np.full(sim.n, 2.0)):
+                sph.sph_species_set(sim.handle, sp, C0)
+                if preset is not None:
+                    sph.sph_species_set_scale(sim.handle, sp, preset)
+                with pytest.raises(sph.SphError) as e:
+                    sph.sph_species_set_scale(sim.handle, sp, None)      # no array
+                assert e.value.code == sph.SPH_E_INVALID
+                sph.sph_diffusion_step(sim.handle, sp, dt, 4)
+                np.testing.assert_array_equal(sph.sph_species_get(sim.handle, sp, sim.n), ref)
+        finally:
+            sph.sph_species_destroy(sp)
+    finally:
+        sim.close()
