@@ -76,6 +76,15 @@ extern "C" {
                                       * without it they are recomputed from the current
                                       * positions in every half step. Costs 16 B per neighbour
                                       * slot of device memory (n_fluid x capacity). */
+#define SPH_FLAG_PERSISTENT  16u     /* sph_step runs all acoustic substeps of each advection step,
+                                      * for every tank of the handle, in one cooperative
+                                      * (persistent) launch: three phases per substep (time step,
+                                      * pressure relaxation, density relaxation) separated by
+                                      * grid-wide barriers whose waits are bounded (a timeout ends
+                                      * the launch with SPH_E_TIMEOUT). Results are bit-identical
+                                      * to the per-launch loop. Ignored with
+                                      * SPH_FLAG_FROZEN_GEOMETRY, SPH_FLAG_DEBUG_BOUNDS or kernel
+                                      * timing on; takes precedence over SPH_FLAG_GRAPH. */
 #define SPH_FLAG_DEBUG_BOUNDS 8u     /* check, before any kernel reads them, that the cell
                                       * offsets of every configuration update run from 0 to
                                       * the particle count without decreasing, and that every
@@ -236,6 +245,22 @@ int sph_get_state(sph_handle* h, double* pos, double* vel, double* rho, double* 
  * caller's arrays may be reused when it returns. */
 int sph_set_state(sph_handle* h, const double* pos, const double* vel, const double* rho,
                   const double* drho_dt, double t, void* stream);
+
+/* Particle gradients of the density and the pressure of every fluid particle (Sec. 1.1,
+ * "particle average and gradient"): the strong form of Eq. gradsph-strong, which gives the
+ * local structure of a field, and the weak form of Eq. gradsph-weak, which conserves. The
+ * paper's grad_i W_ij there is e_ij dW/dr with e_ij from i to j, minus the true gradient;
+ * with the true grad_i W_ij = (dW/dr) (r_i - r_j)/|r_i - r_j| they read
+ *   strong  grad f_i = sum_j V_j (f_j - f_i) grad_i W_ij,
+ *   weak    grad f_i = sum_j V_j (f_i + f_j) grad_i W_ij,
+ * over the neighbour set of the last configuration update (sph_build_cells or a step: call
+ * sph_build_cells first for the set of the current positions) with the pair geometry of the
+ * current positions; V_j = m_j/rho_j for fluid neighbours, and wall neighbours carry the
+ * one-sided wall problem's p_w = p_i + rho_i g.(r_w - r_i), rho_w = rho0 + p_w/c0^2 and their
+ * volume. Outputs: [n_fluid*dim] doubles each, caller order, host or device, any may be NULL.
+ * FP32 sums with Kahan compensation. Synchronous. */
+int sph_gradient_diagnostics(sph_handle* h, double* grad_rho_strong, double* grad_rho_weak,
+                             double* grad_p_strong, double* grad_p_weak, void* stream);
 
 /* dv/dt of the last pressure relaxation in id order [n_fluid*dim] (needs
  * SPH_FLAG_KEEP_ACC). */

@@ -53,8 +53,13 @@ Readings where the paper is silent or inconsistent (the same readings the CUDA p
       the mid-point position. p0 is not given in the paper: 2 rho0 c0^2 for the Taylor-Green
       vortex (the largest value that stayed stable in a sweep at 40^2).
 
-Parity pins: every function here is pinned by the tests in tests/test_oracle_pins.py
-(closed forms, invariants, brute force). None is unpinned.
+  R18 Particle gradients (Eqs. gradsph-strong, gradsph-weak): the paper's grad_i W_ij there
+      is e_ij dW/dr with e_ij from i to j, minus the true gradient of R2; with the true
+      gradient the strong form is sum_j V_j (f_j - f_i) grad_i W_ij and the weak form
+      sum_j V_j (f_i + f_j) grad_i W_ij. Wall neighbours carry the wall problem's p and rho (R4).
+
+Parity pins: every function here is pinned by the tests in tests/test_oracle_pins.py and
+tests/test_gradient_oracle.py (closed forms, invariants, brute force). None is unpinned.
 """
 from __future__ import annotations
 
@@ -555,6 +560,44 @@ def advection_step(st: State, w: Walls, prm: Params, neighbours=neighbour_sets, 
         info.substeps += 1
         info.dts.append(dt)
     return st, info
+
+
+# --------------------------------------------------------------------------------------
+# Particle gradients (Eq. gradsph-strong, Eq. gradsph-weak), R18
+# --------------------------------------------------------------------------------------
+def gradients(st: State, w: Walls, nb, prm: Params) -> dict:
+    """Strong- and weak-form SPH gradients of the density and the pressure of every fluid
+    particle at the current positions (Sec. 1.1, "particle average and gradient").
+
+    The paper writes both with its grad_i W_ij = e_ij dW/dr, e_ij pointing from i to j,
+    which is minus the true gradient of R2. In terms of the true gradient (R18):
+      strong  grad f_i = sum_j V_j (f_j - f_i) grad_i W_ij     (f_ij = f_i - f_j, sign absorbed)
+      weak    grad f_i = sum_j V_j (f_i + f_j) grad_i W_ij     (-2 sum V_j grad W f~_ij, likewise)
+    with V_j = m_j / rho_j for fluid neighbours. A wall neighbour carries the values of the
+    one-sided wall problem (R4): p_w = p_i + rho_i g.(r_w - r_i), rho_w from the EoS, V_w its
+    volume. Returns {"rho_strong", "rho_weak", "p_strong", "p_weak"}, each (N, d).
+    """
+    I, J, IW, KW = nb
+    N, d = st.x.shape
+    p = eos_pressure(st.rho, prm)
+    out = {k: np.zeros((N, d)) for k in ("rho_strong", "rho_weak", "p_strong", "p_weak")}
+    if I.size:
+        _, r, e = _geometry(st.x[I], st.x[J], prm)
+        grad = (-e) * kernel_dW(r, prm.h, prm.dim)[:, None]          # true grad_i W_ij (R2)
+        Vj = st.m[J] / st.rho[J]
+        for f, name in ((st.rho, "rho"), (p, "p")):
+            out[name + "_strong"] += _scatter_add(I, (Vj * (f[J] - f[I]))[:, None] * grad, N)
+            out[name + "_weak"] += _scatter_add(I, (Vj * (f[I] + f[J]))[:, None] * grad, N)
+    if IW.size:
+        rfw, r, e = _geometry(st.x[IW], w.x[KW], prm)
+        grad = (-e) * kernel_dW(r, prm.h, prm.dim)[:, None]
+        pw = p[IW] + st.rho[IW] * ((-rfw) @ prm.gravity)
+        rhow = prm.rho0 + pw / prm.c0 ** 2
+        Vw = w.V[KW]
+        for fi, fw, name in ((st.rho[IW], rhow, "rho"), (p[IW], pw, "p")):
+            out[name + "_strong"] += _scatter_add(IW, (Vw * (fw - fi))[:, None] * grad, N)
+            out[name + "_weak"] += _scatter_add(IW, (Vw * (fi + fw))[:, None] * grad, N)
+    return out
 
 
 # --------------------------------------------------------------------------------------

@@ -594,6 +594,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
   DALLOC(h, b.inst, n_instances);
   DALLOC(h, b.ctrl, n_instances);
   DALLOC(h, b.glob, 1);
+  DALLOC(h, b.pbar, 1);
   DALLOC(h, b.PS, n_fluid);
   DALLOC(h, b.VS, n_fluid);
   DALLOC(h, b.PH, nmax);
@@ -655,6 +656,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
   std::memset(hc.data(), 0, sizeof(Ctrl) * n_instances);
   CK(h, cudaMemcpy(b.ctrl, hc.data(), sizeof(Ctrl) * n_instances, cudaMemcpyHostToDevice));
   CK(h, cudaMemset(b.glob, 0, sizeof(Global)));
+  CK(h, cudaMemset(b.pbar, 0, sizeof(sph::GridBarrier)));
   for (auto& e : h->ev) CK(h, cudaEventCreate(&e));
 
   // walls: import and sort into cells once
@@ -810,6 +812,21 @@ int sph_acoustic_substep(sph_handle* h, int32_t* done_out, double* dt_out, void*
 int sph_step(sph_handle* h, int32_t n_advection_steps, void* stream) {
   if (!h || n_advection_steps < 0) return SPH_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((h->flags & SPH_FLAG_PERSISTENT) && !h->timing && !debug_bounds(h) && !h->b.geo) {
+    // each advection step: the configuration update and the advection step's kernels, then
+    // one cooperative launch for all of its substeps
+    for (int k = 0; k < n_advection_steps; ++k) {
+      int rb = run_build(h, s);
+      if (rb != SPH_OK) return rb;
+      h->cells_valid = true;
+      enqueue_advection(h, s, &h->launches);
+      int grid = 0;
+      cudaError_t e = sph::launch_substeps_persistent(h->b, s, &grid);
+      if (e != cudaSuccess) return cuda_fail(h, e, "persistent substep loop launch");
+      ++h->launches;
+    }
+    return sync_status(h, s);
+  }
   if ((h->flags & SPH_FLAG_GRAPH) && !h->timing && !debug_bounds(h)) {
     if (!h->gexec) {
       int r = build_graph(h);

@@ -38,6 +38,7 @@ struct sph_handle {
   double ms[2] = {0.0, 0.0};
   int64_t timed[2] = {0, 0};
   bool cells_valid = false;
+  float4* grad = nullptr;          // [3][n] gradient sums of sph_gradient_diagnostics (lazily)
 };
 
 // Host-side helpers of sph_api.cu used by the other C-ABI translation units.

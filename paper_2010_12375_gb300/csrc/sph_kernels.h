@@ -14,6 +14,13 @@ struct LaunchCfg {
   int dr_tpp = 1, dr_block = 256;   // density relaxation
 };
 
+// Grid-wide barrier and loop flags of the persistent substep loop (device memory).
+struct GridBarrier {
+  unsigned count;      // blocks arrived at the current barrier
+  unsigned gen;        // barriers completed
+  int active[2];       // per substep (alternating): some tank needs another substep
+};
+
 // Device buffers of one handle. Fluid arrays are indexed in cell-sorted order.
 struct Buffers {
   LaunchCfg cfg;
@@ -51,6 +58,7 @@ struct Buffers {
   int* nbr = nullptr;
   uint32_t* nbc = nullptr;        // [n] fluid count | wall count << 16
   float4* geo = nullptr;          // [cap][n] frozen r_i - r_j and (dW/dr)/r per slot (or NULL)
+  GridBarrier* pbar = nullptr;    // [1] persistent substep loop
 };
 
 size_t scan_tmp_elems(int64_t n);
@@ -91,6 +99,9 @@ void launch_dt_acoustic(const Buffers& b, cudaStream_t s, cudaGraphConditionalHa
                         bool use_cond, int64_t* launches);
 void launch_pressure_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_density_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches);
+// every acoustic substep of the current advection step for every tank in one cooperative
+// launch (not with the frozen-geometry reading); *grid_out receives the blocks launched
+cudaError_t launch_substeps_persistent(const Buffers& b, cudaStream_t s, int* grid_out);
 // per-slot pair geometry at the current positions, for the frozen-geometry reading
 void launch_pair_geometry(const Buffers& b, cudaStream_t s, int64_t* launches);
 // gather-only walk of the neighbour table (diagnostic); sink: one device word

@@ -16,6 +16,7 @@
 // 2h, or at zero distance, contribute nothing.
 #include <cmath>
 
+#include "sph_ctrl.cuh"
 #include "sph_kernels.h"
 
 namespace sph {
@@ -238,46 +239,12 @@ __global__ void k_dt_advection(int n_inst, const Inst* __restrict__ inst, Ctrl* 
   if (threadIdx.x == 0) g->active = 1;
 }
 
-// Eq. dt-relax, clamped to the remainder of the advection step. Sets the
-// condition of the device-side substep loop when launched inside a graph.
+// Eq. dt-relax, clamped to the remainder of the advection step (block body in
+// sph_ctrl.cuh). Sets the condition of the device-side substep loop when launched inside
+// a graph.
 __global__ void k_dt_acoustic(int n_inst, const Inst* __restrict__ inst, Ctrl* ctrl, Global* g,
                               cudaGraphConditionalHandle cond, int use_cond) {
-  int any = 0;
-  for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
-    const Inst& I = inst[k];
-    Ctrl& C = ctrl[k];
-    if (C.done) {
-      C.dt = 0.0;
-      continue;
-    }
-    double vmax = sqrt((double)__uint_as_float(C.vmax2));
-    C.vmax2 = 0u;                                   // refilled by the pressure relaxation
-    double dt_ac = I.cfl_ac * I.h_d / (I.c0_d + vmax);
-    double rem = C.dt_ad - C.tau;
-    double dt = fmin(dt_ac, rem);
-    // a non-finite or vanishing step ends the loop with an error, and so does a substep
-    // count beyond the tank's bound (a timeout), instead of letting the device-side loop spin
-    if (!(dt_ac > 1e-12 * I.h_d / I.c0_d) || !(rem > 0.0) || !(dt > 0.0)) {
-      atomicOr(&g->err, ERR_DT);
-      C.dt = 0.0;
-      C.done = 1;
-      continue;
-    }
-    if (C.sub_in_step >= I.max_sub) {
-      atomicOr(&g->err, ERR_TIMEOUT);
-      C.dt = 0.0;
-      C.done = 1;
-      continue;
-    }
-    C.dt = dt;
-    C.tau += dt;
-    C.t += dt;
-    C.substeps += 1;
-    C.sub_in_step += 1;
-    if (C.tau >= C.dt_ad * (1.0 - kLoopSlack)) C.done = 1;
-    else any = 1;
-  }
-  any = __syncthreads_or(any);
+  const int any = dt_acoustic_block(n_inst, inst, ctrl, g);
   if (threadIdx.x == 0) {
     g->active = any;
     g->substeps += 1;

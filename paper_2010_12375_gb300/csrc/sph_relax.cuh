@@ -229,30 +229,24 @@ __device__ __forceinline__ void pr_wall2(const Inst& I, PrCtx& C, const int4& pi
 // TV: transport velocity (Eq. transport): the mid-point position written for the density
 // relaxation also takes dt^2/2 a_i, a_i = -(2 p0 / rho_i) sum_j V_j grad_i W_ij over the
 // fluid pairs (one thread per particle only).
-template <int D, bool PER, int TPP, int BLK, bool UNI, bool FG, bool TV = false>
-__global__ void __launch_bounds__(BLK, pr_min_blocks(BLK))
-k_pressure_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, const int4* __restrict__ PS,
-                      const float4* __restrict__ VS,
-                      int4* __restrict__ PH, float4* __restrict__ VH,
-                      const float* __restrict__ mass, const int* __restrict__ inst_of,
-                      const Inst* __restrict__ inst, Ctrl* ctrl, const int* __restrict__ nbr,
-                      const uint32_t* __restrict__ nbc, const int4* __restrict__ WP,
-                      const float4* __restrict__ WN, const float4* __restrict__ acc_prior,
-                      float4* __restrict__ acc_keep, Global* g) {
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
-  const int sub = TPP > 1 ? (int)(threadIdx.x % TPP) : 0;
-  int kb;
-  const bool uni = block_one_instance<TPP>(inst_of, n, &kb);
-  bool valid = i < n;
-  const int k = valid ? inst_index(inst_of, i) : kb;
-  const double dtd = ctrl[k].dt;
-  if (dtd == 0.0) valid = false;                 // tank idle for this substep
+// One particle of the pressure relaxation, lane `sub` of the TPP lanes that share it (all
+// lanes take part in the group shuffles, valid or not). Returns |v^{n+1}|^2 on the lane
+// that wrote the particle (*writer), else 0. The array pointers carry the caller's
+// aliasing qualifiers: the per-launch kernels pass __restrict__ ones, the persistent
+// loop plain ones (its phases read what other blocks wrote in the previous phase).
+template <int D, bool PER, int TPP, bool FG, bool TV, typename PI, typename PF>
+__device__ __forceinline__ float pr_particle(const Inst& I, int64_t i, int sub, bool valid, double dtd,
+                                             const float4* __restrict__ geo, int64_t n, PI PS, PF VS,
+                                             int4* PH, float4* VH, const float* __restrict__ mass,
+                                             const int* __restrict__ nbr, const uint32_t* __restrict__ nbc,
+                                             const int4* __restrict__ WP, const float4* __restrict__ WN,
+                                             const float4* __restrict__ acc_prior, float4* __restrict__ acc_keep,
+                                             Global* g, bool* writer_out) {
   float v2 = 0.0f;
   static_assert(!TV || (TPP == 1 && !FG), "transport velocity: one thread per particle, recomputed geometry");
   PrCtx C;
   C.sx = C.sy = C.sz = C.nx = C.ny = C.nz = f2(0.f);
   C.bx = C.by = C.bz = f2(0.f);
-  const Inst& I = UNI ? Ip : inst[k];        // one tank: constants straight from the argument
   const float dt = (float)dtd;
   int4 pi = make_int4(0, 0, 0, 0);
   float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -372,6 +366,32 @@ k_pressure_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, 
     v2 = vn.x * vn.x + vn.y * vn.y + vn.z * vn.z;
     if (!isfinite(v2)) raise_error(g, ERR_NAN, i);
   }
+  *writer_out = writer;
+  return v2;
+}
+
+template <int D, bool PER, int TPP, int BLK, bool UNI, bool FG, bool TV = false>
+__global__ void __launch_bounds__(BLK, pr_min_blocks(BLK))
+k_pressure_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, const int4* __restrict__ PS,
+                      const float4* __restrict__ VS,
+                      int4* __restrict__ PH, float4* __restrict__ VH,
+                      const float* __restrict__ mass, const int* __restrict__ inst_of,
+                      const Inst* __restrict__ inst, Ctrl* ctrl, const int* __restrict__ nbr,
+                      const uint32_t* __restrict__ nbc, const int4* __restrict__ WP,
+                      const float4* __restrict__ WN, const float4* __restrict__ acc_prior,
+                      float4* __restrict__ acc_keep, Global* g) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+  const int sub = TPP > 1 ? (int)(threadIdx.x % TPP) : 0;
+  int kb;
+  const bool uni = block_one_instance<TPP>(inst_of, n, &kb);
+  bool valid = i < n;
+  const int k = valid ? inst_index(inst_of, i) : kb;
+  const double dtd = ctrl[k].dt;
+  if (dtd == 0.0) valid = false;                 // tank idle for this substep
+  const Inst& I = UNI ? Ip : inst[k];        // one tank: constants straight from the argument
+  bool writer;
+  const float v2 = pr_particle<D, PER, TPP, FG, TV, const int4* __restrict__, const float4* __restrict__>(
+      I, i, sub, valid, dtd, geo, n, PS, VS, PH, VH, mass, nbr, nbc, WP, WN, acc_prior, acc_keep, g, &writer);
   reduce_vmax(v2, writer, k, uni, ctrl);
 }
 
@@ -441,24 +461,14 @@ __device__ __forceinline__ void dr_wall2(const Inst& I, DrCtx& C, const int4& pi
   kahan2(C.s, C.nc, mul2(Vw, sub2(Us, UL)), mul2(G.fw, G.r));
 }
 
-template <int D, bool PER, int TPP, int BLK, bool UNI, bool FG>
-__global__ void __launch_bounds__(BLK, dr_min_blocks(BLK))
-k_density_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, const int4* __restrict__ PH,
-                     const float4* __restrict__ VH,
-                     int4* __restrict__ PS, float4* __restrict__ VS,
-                     const float* __restrict__ mass, const int* __restrict__ inst_of,
-                     const Inst* __restrict__ inst, const Ctrl* __restrict__ ctrl,
-                     const int* __restrict__ nbr, const uint32_t* __restrict__ nbc,
-                     const int4* __restrict__ WP, const float4* __restrict__ WN, Global* g) {
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
-  const int sub = TPP > 1 ? (int)(threadIdx.x % TPP) : 0;
-  if (TPP == 1 && i >= n) return;                     // no group shuffles to take part in
-  bool valid = i < n;
-  const int k = valid ? inst_index(inst_of, i) : 0;
-  const double dtd = ctrl[k].dt;
-  if (TPP == 1 && dtd == 0.0) return;
-  if (dtd == 0.0) valid = false;
-  const Inst& I = UNI ? Ip : inst[k];        // one tank: constants straight from the argument
+// One particle of the density relaxation, lane `sub` of TPP (pointer qualifiers as for
+// pr_particle).
+template <int D, bool PER, int TPP, bool FG, typename PI, typename PF>
+__device__ __forceinline__ void dr_particle(const Inst& I, int64_t i, int sub, bool valid, double dtd,
+                                            const float4* __restrict__ geo, int64_t n, PI PH, PF VH,
+                                            int4* PS, float4* VS, const float* __restrict__ mass,
+                                            const int* __restrict__ nbr, const uint32_t* __restrict__ nbc,
+                                            const int4* __restrict__ WP, const float4* __restrict__ WN, Global* g) {
   DrCtx C;
   C.s = C.nc = f2(0.f);
   int4 pi = make_int4(0, 0, 0, 0);
@@ -556,6 +566,28 @@ k_density_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, c
   if (!isfinite(dev_n)) raise_error(g, ERR_NAN, i);
   PS[i] = make_int4(qx, qy, qz, f2i(dev_n));
   VS[i] = make_float4(vi.x, vi.y, vi.z, drho);
+}
+
+template <int D, bool PER, int TPP, int BLK, bool UNI, bool FG>
+__global__ void __launch_bounds__(BLK, dr_min_blocks(BLK))
+k_density_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, const int4* __restrict__ PH,
+                     const float4* __restrict__ VH,
+                     int4* __restrict__ PS, float4* __restrict__ VS,
+                     const float* __restrict__ mass, const int* __restrict__ inst_of,
+                     const Inst* __restrict__ inst, const Ctrl* __restrict__ ctrl,
+                     const int* __restrict__ nbr, const uint32_t* __restrict__ nbc,
+                     const int4* __restrict__ WP, const float4* __restrict__ WN, Global* g) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+  const int sub = TPP > 1 ? (int)(threadIdx.x % TPP) : 0;
+  if (TPP == 1 && i >= n) return;                     // no group shuffles to take part in
+  bool valid = i < n;
+  const int k = valid ? inst_index(inst_of, i) : 0;
+  const double dtd = ctrl[k].dt;
+  if (TPP == 1 && dtd == 0.0) return;
+  if (dtd == 0.0) valid = false;
+  const Inst& I = UNI ? Ip : inst[k];        // one tank: constants straight from the argument
+  dr_particle<D, PER, TPP, FG, const int4* __restrict__, const float4* __restrict__>(
+      I, i, sub, valid, dtd, geo, n, PH, VH, PS, VS, mass, nbr, nbc, WP, WN, g);
 }
 
 // Launch variants: (threads per particle, block size) per kernel, indexed by kTpp / kBlk.

@@ -25,6 +25,7 @@ SPH_FLAG_GRAPH = 1
 SPH_FLAG_KEEP_ACC = 2
 SPH_FLAG_FROZEN_GEOMETRY = 4
 SPH_FLAG_DEBUG_BOUNDS = 8
+SPH_FLAG_PERSISTENT = 16
 SPH_DEBUG_NEIGHBOUR = 1
 SPH_DEBUG_WALL_OFFSET = 2
 
@@ -46,6 +47,7 @@ EXPORTS = [
     "sph_species_create", "sph_species_destroy", "sph_species_last_error", "sph_species_set",
     "sph_species_get", "sph_diffusion_step", "sph_species_set_gate", "sph_species_get_gate",
     "sph_reaction_step", "sph_species_set_scale", "sph_clear_error", "sph_debug_write",
+    "sph_gradient_diagnostics",
 ]
 
 
@@ -167,6 +169,7 @@ def load():
         "sph_species_set_scale": (i32, [P, P, P, P]),
         "sph_clear_error": (i32, [P, P]),
         "sph_debug_write": (i32, [P, i32, i64, i32, i64, P]),
+        "sph_gradient_diagnostics": (i32, [P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -331,6 +334,16 @@ def sph_set_state(h, pos, vel, rho, drho_dt=None, t=-1.0, stream=None):
     pos, vel, rho, drho_dt = _f64(pos), _f64(vel), _f64(rho), _f64(drho_dt)
     check(lib, h, lib.sph_set_state(h, _ptr(pos), _ptr(vel), _ptr(rho), _ptr(drho_dt), float(t),
                                     _stream(stream)))
+
+
+def sph_gradient_diagnostics(h, n, dim, stream=None):
+    """Strong- and weak-form gradients of rho and p per fluid particle (caller order):
+    dict of four (n, dim) float64 arrays."""
+    lib = load()
+    out = {k: np.empty((n, dim)) for k in ("rho_strong", "rho_weak", "p_strong", "p_weak")}
+    check(lib, h, lib.sph_gradient_diagnostics(h, _ptr(out["rho_strong"]), _ptr(out["rho_weak"]),
+                                               _ptr(out["p_strong"]), _ptr(out["p_weak"]), _stream(stream)))
+    return out
 
 
 def sph_get_acceleration(h, n, dim, stream=None):

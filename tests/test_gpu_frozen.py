@@ -97,7 +97,10 @@ def test_frozen_substeps_match_the_frozen_oracle(sph, case):
               f"rho - rho0 {rel_l2(rho_gpu - prm.rho0, st.rho - prm.rho0):.2e}")
         assert rel_l2(acc_gpu, dvdt) < REL_L2_TOL
         assert rel_l2(vel_gpu, st.v) < REL_L2_TOL
-        assert rel_l2(rho_gpu - prm.rho0, st.rho - prm.rho0) < REL_L2_TOL
+        # both sides continue from their own states (not re-synchronised between substeps),
+        # so the density deviation carries every earlier substep's dt drho/dt error: the
+        # per-substep 1e-5 adds up to (k + 1) 1e-5 after substep k
+        assert rel_l2(rho_gpu - prm.rho0, st.rho - prm.rho0) < (k + 1) * REL_L2_TOL
         _, _, _, dq, _ = o.quantisation(prm)
         assert np.max(np.abs(o.min_image(pos_gpu - st.x, prm.period))) < 8 * (k + 1) * dq + 1e-7 * prm.dp
 
