@@ -301,6 +301,8 @@ def run_ours(args, rank, world, local_rank):
     flags = (sph.SPH_FLAG_GRAPH if graph else 0) | (sph.SPH_FLAG_FROZEN_GEOMETRY if args.frozen else 0)
     if args.persistent:
         flags |= sph.SPH_FLAG_PERSISTENT
+    if args.half_pair:
+        flags |= sph.SPH_FLAG_HALF_PAIR
     sim = sph.Simulation(prob, flags=flags, stream=stream)
     info = sim.info()
 
@@ -319,7 +321,7 @@ def run_ours(args, rank, world, local_rank):
         sph.sph_set_launch_config(sim.handle, cfg)
     for _ in range(args.warmup):
         sim.step(1)
-    if cfg is None and not args.no_autotune:
+    if cfg is None and not args.no_autotune and not args.half_pair:
         # one extra (untimed) advection step that times the launch variants
         cfg, times = sph.sph_autotune(sim.handle, stream)
     if cfg is not None:
@@ -401,14 +403,15 @@ def run_ours(args, rank, world, local_rank):
     achieved = k7_bytes / (k7_ms * 1e-3) / 1e9 if kcount[0] else None
     traffic = None
     if (TRAFFIC_BYTES_PER_PARTICLE is not None and TRAFFIC_SOURCE_HASH == kernel_source_hash()
-            and not args.frozen):
+            and not args.frozen and not args.half_pair):
         traffic = TRAFFIC_BYTES_PER_PARTICLE * N
     # the same table walk with the 32-byte neighbour records gathered and no pair arithmetic:
     # the device's floor for gathering them this way (the kernels are gather-bound, not HBM-bound)
     gather_ms = sph.sph_gather_ceiling(sim.handle, 10, stream)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "kernel": "k_pressure_relaxation<3>", "peak_kind": peak_kind,
+            "kernel": ("k_pr_half_a<3> + k_pr_half_b<3> (half-pair)" if args.half_pair
+                       else "k_pressure_relaxation<3>"), "peak_kind": peak_kind,
             "launch_ms": k7_ms, "algorithmic_bytes_per_launch": k7_bytes,
             "density_relaxation_ms": ktimes[1] / max(kcount[1], 1),
             "gather_ceiling_ms": gather_ms,
@@ -428,7 +431,8 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {
                 "workload": f"3D dam break, fluid 2x1x1 in a 5.366x5.366x1 tank, dp = 1/{args.n}"
-                            + (", frozen pair geometry" if args.frozen else ""),
+                            + (", frozen pair geometry" if args.frozen else "")
+                            + (", half-pair evaluation" if args.half_pair else ""),
                 "n_fluid": N, "n_wall": prob.n_wall, "h_over_dp": 1.3,
                 "substeps": substeps, "neighbour_pairs": fluid_pairs + wall_pairs,
                 "mean_neighbours": (fluid_pairs + wall_pairs) / N,
@@ -756,6 +760,8 @@ def main():
     ap.add_argument("--n", type=int, default=159, help="3D dam break resolution: dp = 1/n, 2n^3 fluid")
     ap.add_argument("--host-loop", action="store_true",
                     help="time the host-driven substep loop instead of the CUDA-graph loop")
+    ap.add_argument("--half-pair", action="store_true",
+                    help="the symmetric half-pair evaluation of the relaxations (two passes each)")
     ap.add_argument("--persistent", action="store_true",
                     help="all substeps of an advection step in one cooperative launch")
     ap.add_argument("--kernel-steps", type=int, default=3,

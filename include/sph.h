@@ -83,8 +83,23 @@ extern "C" {
                                       * grid-wide barriers whose waits are bounded (a timeout ends
                                       * the launch with SPH_E_TIMEOUT). Results are bit-identical
                                       * to the per-launch loop. Ignored with
-                                      * SPH_FLAG_FROZEN_GEOMETRY, SPH_FLAG_DEBUG_BOUNDS or kernel
+                                      * SPH_FLAG_FROZEN_GEOMETRY, SPH_FLAG_HALF_PAIR,
+                                      * SPH_FLAG_DEBUG_BOUNDS or kernel
                                       * timing on; takes precedence over SPH_FLAG_GRAPH. */
+#define SPH_FLAG_HALF_PAIR   32u     /* evaluate every unordered fluid pair of the two relaxations
+                                      * once (Newton's third law: P*_ij = P*_ji with the
+                                      * antisymmetric kernel gradient of Eq. gradsph-weak; the
+                                      * continuity term's velocity part symmetric, its pressure
+                                      * part antisymmetric): a first pass adds each pair's share
+                                      * for the lower particle and stores the upper particle's
+                                      * share per neighbour slot, a second pass sums the stored
+                                      * shares through a reverse-slot map built with each
+                                      * configuration update. Fixed summation order, no atomics:
+                                      * bit-reproducible; equal to the per-pair kernels up to
+                                      * rounding. Costs 17 B per neighbour slot of device memory;
+                                      * needs capacity <= 252; not with SPH_FLAG_FROZEN_GEOMETRY or
+                                      * the transport velocity; the launch configuration and the
+                                      * autotuner do not apply (one thread per particle). */
 #define SPH_FLAG_DEBUG_BOUNDS 8u     /* check, before any kernel reads them, that the cell
                                       * offsets of every configuration update run from 0 to
                                       * the particle count without decreasing, and that every

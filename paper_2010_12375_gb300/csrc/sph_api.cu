@@ -123,6 +123,11 @@ int check_params(const sph_params* p, std::string* why) {
   if (p->free_surface != 0 && p->free_surface != 1) return bad("free_surface must be 0 or 1");
   if (!(std::isfinite(p->p_transport) && p->p_transport >= 0.0)) return bad("p_transport must be >= 0");
   if (p->max_substeps < 0) return bad("max_substeps must be >= 0");
+  if (p->flags & SPH_FLAG_HALF_PAIR) {
+    if (p->flags & SPH_FLAG_FROZEN_GEOMETRY) return bad("the half-pair evaluation recomputes the pair geometry");
+    if (p->p_transport > 0.0) return bad("the half-pair evaluation has no transport velocity");
+    if (p->capacity > 252) return bad("the half-pair evaluation needs capacity <= 252");
+  }
   if (p->p_transport > 0.0 && (p->flags & SPH_FLAG_FROZEN_GEOMETRY))
     return bad("the transport velocity needs the recomputed pair geometry (no SPH_FLAG_FROZEN_GEOMETRY)");
   double period = 0.0;
@@ -280,6 +285,7 @@ void enqueue_build(sph_handle* h, cudaStream_t s, int64_t* n) {
   sph::launch_fluid_offsets(h->b, s, n);
   sph::launch_sort_fluid(h->b, s, n);
   sph::launch_neighbours(h->b, s, n);
+  sph::launch_reverse_slots(h->b, s, n);     // half-pair evaluation only (b.hrev set)
 }
 
 bool debug_bounds(const sph_handle* h) { return (h->flags & SPH_FLAG_DEBUG_BOUNDS) != 0; }
@@ -313,6 +319,10 @@ int run_build(sph_handle* h, cudaStream_t s) {
   sph::launch_neighbours(h->b, s, &h->launches);
   sph::launch_check_table(h->b, s, &h->launches);
   CK(h, cudaGetLastError());
+  int rt = sync_status(h, s);              // the reverse map reads the table: check it first
+  if (rt != SPH_OK) return rt;
+  sph::launch_reverse_slots(h->b, s, &h->launches);
+  CK(h, cudaGetLastError());
   return sync_status(h, s);
 }
 
@@ -326,9 +336,11 @@ void enqueue_advection(sph_handle* h, cudaStream_t s, int64_t* n) {
 void enqueue_substep(sph_handle* h, cudaStream_t s, bool use_cond, int64_t* n) {
   sph::launch_dt_acoustic(h->b, s, h->cond, use_cond, n);
   if (h->timing && !use_cond) cudaEventRecord(h->ev[0], s);
-  sph::launch_pressure_relaxation(h->b, s, n);
+  if (h->b.hrev) sph::launch_half_pair(h->b, true, s, n);
+  else sph::launch_pressure_relaxation(h->b, s, n);
   if (h->timing && !use_cond) cudaEventRecord(h->ev[1], s);
-  sph::launch_density_relaxation(h->b, s, n);
+  if (h->b.hrev) sph::launch_half_pair(h->b, false, s, n);
+  else sph::launch_density_relaxation(h->b, s, n);
   if (h->timing && !use_cond) cudaEventRecord(h->ev[2], s);
 }
 
@@ -625,6 +637,11 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
     CK(h, cudaMemset(b.acc_prior, 0, sizeof(float4) * std::max<int64_t>(n_fluid, 1)));
   }
   if (h->flags & SPH_FLAG_FROZEN_GEOMETRY) DALLOC(h, b.geo, (size_t)n_fluid * b.cap);
+  if (h->flags & SPH_FLAG_HALF_PAIR) {
+    DALLOC(h, b.hshare, (size_t)n_fluid * b.cap);
+    DALLOC(h, b.hpart, n_fluid);
+    DALLOC(h, b.hrev, (size_t)n_fluid * b.cap);
+  }
   if (h->flags & SPH_FLAG_KEEP_ACC) {
     DALLOC(h, b.acc_keep, n_fluid);
     CK(h, cudaMemset(b.acc_keep, 0, sizeof(float4) * std::max<int64_t>(n_fluid, 1)));
@@ -812,7 +829,7 @@ int sph_acoustic_substep(sph_handle* h, int32_t* done_out, double* dt_out, void*
 int sph_step(sph_handle* h, int32_t n_advection_steps, void* stream) {
   if (!h || n_advection_steps < 0) return SPH_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((h->flags & SPH_FLAG_PERSISTENT) && !h->timing && !debug_bounds(h) && !h->b.geo) {
+  if ((h->flags & SPH_FLAG_PERSISTENT) && !h->timing && !debug_bounds(h) && !h->b.geo && !h->b.hrev) {
     // each advection step: the configuration update and the advection step's kernels, then
     // one cooperative launch for all of its substeps
     for (int k = 0; k < n_advection_steps; ++k) {
@@ -1004,6 +1021,7 @@ int sph_set_launch_config(sph_handle* h, const int32_t* cfg) {
 
 int sph_autotune(sph_handle* h, int32_t* cfg_out, double* ms_out, void* stream) {
   if (!h) return SPH_E_INVALID;
+  if (h->b.hrev) return fail(h, SPH_E_INVALID, "the half-pair evaluation has no launch variants to tune");
   cudaStream_t s = (cudaStream_t)stream;
   int rb = run_build(h, s);
   if (rb != SPH_OK) return rb;

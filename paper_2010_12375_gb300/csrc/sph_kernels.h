@@ -59,6 +59,11 @@ struct Buffers {
   uint32_t* nbc = nullptr;        // [n] fluid count | wall count << 16
   float4* geo = nullptr;          // [cap][n] frozen r_i - r_j and (dW/dr)/r per slot (or NULL)
   GridBarrier* pbar = nullptr;    // [1] persistent substep loop
+  // half-pair evaluation (or NULL): per-slot shares [cap][n], per-particle partial sums [n],
+  // reverse slots [cap][n] (slot of j in i's row for each slot of j's row holding i < j)
+  float4* hshare = nullptr;
+  float4* hpart = nullptr;
+  uint8_t* hrev = nullptr;
 };
 
 size_t scan_tmp_elems(int64_t n);
@@ -102,6 +107,10 @@ void launch_density_relaxation(const Buffers& b, cudaStream_t s, int64_t* launch
 // every acoustic substep of the current advection step for every tank in one cooperative
 // launch (not with the frozen-geometry reading); *grid_out receives the blocks launched
 cudaError_t launch_substeps_persistent(const Buffers& b, cudaStream_t s, int* grid_out);
+// half-pair evaluation: the reverse-slot map of the current table (after each build), and
+// one relaxation (pressure or density) as its two passes
+void launch_reverse_slots(const Buffers& b, cudaStream_t s, int64_t* launches);
+void launch_half_pair(const Buffers& b, bool pressure, cudaStream_t s, int64_t* launches);
 // per-slot pair geometry at the current positions, for the frozen-geometry reading
 void launch_pair_geometry(const Buffers& b, cudaStream_t s, int64_t* launches);
 // gather-only walk of the neighbour table (diagnostic); sink: one device word

@@ -26,6 +26,7 @@ SPH_FLAG_KEEP_ACC = 2
 SPH_FLAG_FROZEN_GEOMETRY = 4
 SPH_FLAG_DEBUG_BOUNDS = 8
 SPH_FLAG_PERSISTENT = 16
+SPH_FLAG_HALF_PAIR = 32
 SPH_DEBUG_NEIGHBOUR = 1
 SPH_DEBUG_WALL_OFFSET = 2
 
