@@ -349,3 +349,54 @@ def learned_dam_break(n_fluid=100_000):
     """2D dam break H=1, L=2 at about n_fluid particles (447 x 224 for 1e5)."""
     dp = math.sqrt(2.0 / n_fluid)
     return dam_break(dim=2, H=1.0, L=2.0, dp=dp, name=f"dam_break_2d_learned")
+
+
+def water_column_on_plate(dp=1.0 / 40.0, ratio=2, H=1.0, L=1.0, thickness=0.05, youngs=4.55e4,
+                          poisson=0.3, rho_s=2.7, rho0=1.0, g=1.0, model=1, nu=0.0):
+    """2D water column of height H on an elastic plate spanning a tank of width L (the
+    paper's first FSI test, a hydrostatic column on a plate, at synthetic sizes): fluid on a
+    lattice of spacing dp, side walls of four dummy layers standing on the plate, the plate
+    of the given thickness on a lattice ratio times finer (multi-resolution), clamped where
+    it runs under the side walls (x < 0 or x > L). Solid normals point up into the water.
+    The plate's static mid-span deflection under q = rho0 g H is q L^4 / (384 E' I) for a
+    clamped Euler-Bernoulli beam, E' = E / (1 - nu^2), I = thickness^3 / 12."""
+    nx, ny = int(round(L / dp)), int(round(H / dp))
+    fluid = _lattice(np.zeros(2), [nx, ny], dp)
+    top = 1.5 * H
+    nyw = int(round(top / dp))
+    walls = []
+    for k in range(WALL_LAYERS):
+        ys = (np.arange(nyw) + 0.5) * dp
+        walls.append(np.stack([np.full(nyw, -(k + 0.5) * dp), ys], axis=1))
+        walls.append(np.stack([np.full(nyw, L + (k + 0.5) * dp), ys], axis=1))
+    wpos = np.concatenate(walls)
+    wnrm = np.where(wpos[:, :1] < 0, [[1.0, 0.0]], [[-1.0, 0.0]]).astype(np.float64)
+    ds = dp / ratio
+    clamp = WALL_LAYERS * dp
+    nsx = int(round((L + 2 * clamp) / ds))
+    nsy = max(1, int(round(thickness / ds)))
+    spos = _lattice(np.array([-clamp, -nsy * ds]), [nsx, nsy], ds)
+    c0 = 10.0 * math.sqrt(g * H)
+    grav = np.zeros(3)
+    grav[1] = -g
+    lo = np.array([-clamp - 2 * dp, -nsy * ds - 4 * dp, 0.0])
+    hi = np.array([L + clamp + 2 * dp, top + 4 * dp, 0.0])
+    n = fluid.shape[0]
+    wl = Workload(
+        name=f"water_column_on_plate_{n}_r{ratio}", dim=2, h=H_OVER_DP * dp, dp=dp, rho0=rho0, c0=c0,
+        cfl_ad=0.25, cfl_ac=0.6, u_ref=c0 / 10.0, nu=nu, gravity=grav, lo=lo, hi=hi,
+        periodic=np.zeros(3, dtype=np.int32), free_surface=1,
+        pos=fluid, vel=np.zeros_like(fluid), rho=np.full(n, rho0), mass=np.full(n, rho0 * dp * dp),
+        wall_pos=wpos, wall_normal=wnrm, wall_vol=np.full(wpos.shape[0], dp * dp),
+        t_end=1.0, meta={"H": ny * dp, "L": nx * dp, "g": g, "thickness": nsy * ds, "ratio": ratio},
+    )
+    wl.solid_pos = spos
+    wl.solid_vol = np.full(spos.shape[0], ds * ds)
+    wl.solid_normal = np.tile([0.0, 1.0], (spos.shape[0], 1))
+    wl.solid_fixed = (spos[:, 0] < 0.0) | (spos[:, 0] > nx * dp)
+    wl.solid_h = H_OVER_DP * ds
+    wl.solid_dp = ds
+    wl.solid_rho0, wl.solid_youngs, wl.solid_poisson, wl.solid_model = rho_s, youngs, poisson, model
+    Ep = youngs / (1.0 - poisson ** 2)
+    wl.meta["static_deflection"] = rho0 * g * wl.meta["H"] * wl.meta["L"] ** 4 / (384.0 * Ep * wl.meta["thickness"] ** 3 / 12.0)
+    return wl
