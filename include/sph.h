@@ -469,6 +469,65 @@ int sph_species_get_gate(sph_handle* h, sph_species* sp, double* w, void* stream
 int sph_reaction_step(sph_handle* h, sph_species* sp, const sph_reaction* r, double dt, int32_t n_steps,
                       void* stream);
 
+/* ---- Multi-resolution fluid-structure coupling (Sec. "Multi-resolution FSI coupling") -----
+ * An elastic solid with its own particle spacing and smoothing length h_S, attached to a
+ * single-tank handle, is coupled to the fluid through the fluid's kernel:
+ *  - solid, total Lagrangian (Sec. "Total Lagrangian formulation"): neighbours within 2 h_S in
+ *    the reference configuration, kept for the whole run; the true kernel gradient
+ *    grad0_a W_ab = dW/dr r0_ab/|r0_ab| and the correction matrix
+ *    B0_a = (sum_b V_b (r0_b - r0_a) (x) grad0_a W_ab)^-1 (Eq. sph-correctmatrix), computed once;
+ *    first Piola-Kirchhoff stress P = F S, linear elastic S = lambda tr(E) I + 2 mu E or
+ *    Neo-Hookean S = mu (I - C^-1) + lambda ln J C^-1 (E = (C - I)/2, C = F^T F, J = det F,
+ *    mu = E/(2(1 + nu)), lambda = E nu/((1 + nu)(1 - 2 nu)));
+ *    dv_a/dt = (2/m_a) sum_b V_a V_b (P_a B0_a + P_b B0_b)/2 grad0_a W_ab + g + f_a/m_a
+ *    (Eq. sph-mechanical-mom), f_a the fluid's force on it;
+ *  - solid steps, position-based Verlet (Eqs. verlet-first-half-solid,
+ *    verlet-first-mediate-solid, verlet-first-final-solid): F and r half a step, dv/dt, v, r
+ *    the second half, dF/dt = (sum_b V_b (v_b - v_a) (x) grad0_a W_ab) B0_a, F the second
+ *    half (dF/dt is carried from one step's second half to the next step's first half);
+ *  - per fluid acoustic step dt_F: kappa = [dt_F/dt_S] + 1 solid steps of dt_F/kappa, dt_S =
+ *    0.6 min(h_S/(c_S + |v|max), sqrt(h_S/|dv/dt|max)) (Eq. dts-advection, c_S = sqrt(K/rho0),
+ *    K = lambda + 2 mu/3), with the fluid's force held over them;
+ *  - coupling (fluid kernel h_F): after the fluid's pressure relaxation each fluid particle i
+ *    near the solid gains sum_a -2 V_i V_a pbar grad_i W(r_ia)/m_i (Eq. fs-force-mr-sp),
+ *    pbar = (p_i rho^d + p^d rho_i)/(rho_i + rho^d), the imaginary pressure
+ *    p^d = p_i + rho_i max(0, -(g - a~_a).n_a) ((r_i - r_a).n_a) (Eq. fs-coupling-mr read as the
+ *    hydrostatic extrapolation along the solid's normal n_a, pointing into the fluid),
+ *    rho^d from the EoS, and with viscosity the force of Eq. fs-force-mr-sv with
+ *    v^d = 2 v~_a - v_i; the solid takes the opposite forces; after the density relaxation
+ *    each such fluid particle adds the continuity term of its solid neighbours as moving
+ *    walls (U_L = -n_a.v_i, U_R = -U_L - 2 n_a.v~_a, P_R = p^d). v~_a and a~_a are the solid's
+ *    velocity and acceleration averaged over the previous fluid step's solid steps.
+ *  Solid particles take no part in the fluid's density re-initialisation. Clamped particles
+ *  (fixed[a] != 0) keep their reference position and zero velocity. */
+typedef struct sph_solid sph_solid;
+#define SPH_SOLID_LINEAR       1
+#define SPH_SOLID_NEO_HOOKEAN  2
+typedef struct {
+  int32_t model;           /* SPH_SOLID_LINEAR or SPH_SOLID_NEO_HOOKEAN                     */
+  double  rho0;            /* reference density of the solid                               */
+  double  youngs, poisson; /* Young's modulus E > 0 and Poisson ratio -1 < nu < 0.5         */
+  double  h;               /* the solid's smoothing length h_S (its support is 2 h_S)      */
+} sph_solid_params;
+
+/* Attach a solid of n particles (1..16384) to a single-tank handle (one solid per handle):
+ * pos [n*dim] reference positions inside the handle's cell grid, vol [n] volumes, normal
+ * [n*dim] unit normals of the nearest wetted surface (into the fluid), fixed [n] or NULL;
+ * host or device arrays. The solid starts undeformed and at rest; the handle's next
+ * configuration update (sph_build_cells or a step) includes it, and every later acoustic
+ * substep advances it. On failure *out may still hold an object carrying the message
+ * (sph_solid_last_error); destroy it. */
+int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const double* pos, const double* vol,
+                     const double* normal, const int32_t* fixed, sph_solid** out);
+/* Detach from the handle and free; destroy before the handle. */
+void sph_solid_destroy(sph_solid* s);
+const char* sph_solid_last_error(const sph_solid* s);
+/* The solid's state in its particle order (host or device outputs, any may be NULL): pos,
+ * vel, force (the fluid's force held over the last solid steps) [n*dim], F [n*dim*dim]
+ * row-major; solid_steps (host) the solid steps taken so far. Synchronous. */
+int sph_solid_get_state(sph_handle* h, sph_solid* s, double* pos, double* vel, double* force, double* F,
+                        int64_t* solid_steps, void* stream);
+
 /* Allocation-free diagnostics. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory (code running inside
  * another framework's device memory pool or under a fixed device-memory budget,

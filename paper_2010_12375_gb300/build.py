@@ -12,7 +12,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libsph.so")
-SOURCES = ["sph_cells.cu", "sph_physics.cu", "sph_relax_pr.cu", "sph_relax_dr.cu", "sph_gather.cu", "sph_diag.cu", "sph_noalloc.cu", "sph_learned.cu", "sph_diffusion.cu", "sph_gradient.cu", "sph_persistent.cu", "sph_halfpair.cu", "sph_api.cu"]
+SOURCES = ["sph_cells.cu", "sph_physics.cu", "sph_relax_pr.cu", "sph_relax_dr.cu", "sph_gather.cu", "sph_diag.cu", "sph_noalloc.cu", "sph_learned.cu", "sph_diffusion.cu", "sph_gradient.cu", "sph_persistent.cu", "sph_halfpair.cu", "sph_fsi.cu", "sph_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

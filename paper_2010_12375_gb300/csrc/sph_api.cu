@@ -286,6 +286,7 @@ void enqueue_build(sph_handle* h, cudaStream_t s, int64_t* n) {
   sph::launch_sort_fluid(h->b, s, n);
   sph::launch_neighbours(h->b, s, n);
   sph::launch_reverse_slots(h->b, s, n);     // half-pair evaluation only (b.hrev set)
+  sph_fsi_after_build(h, s, n);              // attached solid only
 }
 
 bool debug_bounds(const sph_handle* h) { return (h->flags & SPH_FLAG_DEBUG_BOUNDS) != 0; }
@@ -322,6 +323,7 @@ int run_build(sph_handle* h, cudaStream_t s) {
   int rt = sync_status(h, s);              // the reverse map reads the table: check it first
   if (rt != SPH_OK) return rt;
   sph::launch_reverse_slots(h->b, s, &h->launches);
+  sph_fsi_after_build(h, s, &h->launches);
   CK(h, cudaGetLastError());
   return sync_status(h, s);
 }
@@ -338,9 +340,11 @@ void enqueue_substep(sph_handle* h, cudaStream_t s, bool use_cond, int64_t* n) {
   if (h->timing && !use_cond) cudaEventRecord(h->ev[0], s);
   if (h->b.hrev) sph::launch_half_pair(h->b, true, s, n);
   else sph::launch_pressure_relaxation(h->b, s, n);
+  sph_fsi_after_pressure(h, s, n);
   if (h->timing && !use_cond) cudaEventRecord(h->ev[1], s);
   if (h->b.hrev) sph::launch_half_pair(h->b, false, s, n);
   else sph::launch_density_relaxation(h->b, s, n);
+  sph_fsi_after_density(h, s, n);
   if (h->timing && !use_cond) cudaEventRecord(h->ev[2], s);
 }
 
@@ -502,6 +506,7 @@ void drop_graph(sph_handle* h) {
 }  // namespace
 
 int sph_sync_status(sph_handle* h, cudaStream_t s) { return sync_status(h, s); }
+void sph_drop_graph(sph_handle* h) { drop_graph(h); }
 int sph_debug_check(sph_handle* h, cudaStream_t s) { return debug_check(h, s); }
 
 extern "C" {
@@ -829,7 +834,7 @@ int sph_acoustic_substep(sph_handle* h, int32_t* done_out, double* dt_out, void*
 int sph_step(sph_handle* h, int32_t n_advection_steps, void* stream) {
   if (!h || n_advection_steps < 0) return SPH_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((h->flags & SPH_FLAG_PERSISTENT) && !h->timing && !debug_bounds(h) && !h->b.geo && !h->b.hrev) {
+  if ((h->flags & SPH_FLAG_PERSISTENT) && !h->timing && !debug_bounds(h) && !h->b.geo && !h->b.hrev && !h->solid) {
     // each advection step: the configuration update and the advection step's kernels, then
     // one cooperative launch for all of its substeps
     for (int k = 0; k < n_advection_steps; ++k) {

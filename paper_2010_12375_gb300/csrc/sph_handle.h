@@ -39,6 +39,7 @@ struct sph_handle {
   int64_t timed[2] = {0, 0};
   bool cells_valid = false;
   float4* grad = nullptr;          // [3][n] gradient sums of sph_gradient_diagnostics (lazily)
+  sph_solid* solid = nullptr;      // attached elastic solid (sph_solid_create), or NULL
 };
 
 // Host-side helpers of sph_api.cu used by the other C-ABI translation units.
@@ -46,3 +47,11 @@ int sph_sync_status(sph_handle* h, cudaStream_t s);
 // SPH_FLAG_DEBUG_BOUNDS: check the cell offsets and the neighbour table before a kernel reads
 // them (synchronous); SPH_OK at once when the flag is off.
 int sph_debug_check(sph_handle* h, cudaStream_t s);
+// Drop the captured graph of an advection step (the loop's kernels changed).
+void sph_drop_graph(sph_handle* h);
+// Fluid-structure coupling hooks of the fluid's loop (sph_fsi.cu), no-ops without a solid:
+// the near-fluid list after a configuration update, the coupling forces after the pressure
+// relaxation, the continuity term and the solid's steps after the density relaxation.
+void sph_fsi_after_build(sph_handle* h, cudaStream_t s, int64_t* launches);
+void sph_fsi_after_pressure(sph_handle* h, cudaStream_t s, int64_t* launches);
+void sph_fsi_after_density(sph_handle* h, cudaStream_t s, int64_t* launches);

@@ -48,7 +48,8 @@ EXPORTS = [
     "sph_species_create", "sph_species_destroy", "sph_species_last_error", "sph_species_set",
     "sph_species_get", "sph_diffusion_step", "sph_species_set_gate", "sph_species_get_gate",
     "sph_reaction_step", "sph_species_set_scale", "sph_clear_error", "sph_debug_write",
-    "sph_gradient_diagnostics",
+    "sph_gradient_diagnostics", "sph_solid_create", "sph_solid_destroy", "sph_solid_last_error",
+    "sph_solid_get_state",
 ]
 
 
@@ -103,6 +104,14 @@ SPH_REACTION_FN, SPH_REACTION_AP = 1, 2
 class SphReaction(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32)] + [(f, ctypes.c_double) for f in
                                                ("a", "b", "k", "eps0", "mu1", "mu2", "beta", "gamma", "sigma")]
+
+
+SPH_SOLID_LINEAR, SPH_SOLID_NEO_HOOKEAN = 1, 2
+
+
+class SphSolidParams(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("rho0", ctypes.c_double), ("youngs", ctypes.c_double),
+                ("poisson", ctypes.c_double), ("h", ctypes.c_double)]
 
 
 class SphError(RuntimeError):
@@ -171,6 +180,10 @@ def load():
         "sph_clear_error": (i32, [P, P]),
         "sph_debug_write": (i32, [P, i32, i64, i32, i64, P]),
         "sph_gradient_diagnostics": (i32, [P, P, P, P, P, P]),
+        "sph_solid_create": (i32, [P, ctypes.POINTER(SphSolidParams), i64, P, P, P, P, ctypes.POINTER(P)]),
+        "sph_solid_destroy": (None, [P]),
+        "sph_solid_last_error": (ctypes.c_char_p, [P]),
+        "sph_solid_get_state": (i32, [P, P, P, P, P, P, ctypes.POINTER(i64), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -695,3 +708,46 @@ class Simulation:
 
     def pair_count(self):
         return sph_pair_count(self.handle, self.stream)
+
+
+# ------------------------------------------------------------------------ fluid-structure
+def sph_solid_create(h, model, rho0, youngs, poisson, h_s, pos, vol, normal, fixed=None):
+    """Attach an elastic solid to handle h; returns the opaque solid."""
+    lib = load()
+    p = SphSolidParams(int(model), float(rho0), float(youngs), float(poisson), float(h_s))
+    pos, vol, normal = _f64(pos), _f64(vol), _f64(normal)
+    fx = None if fixed is None else np.ascontiguousarray(np.asarray(fixed).astype(np.int32))
+    n = int(vol.shape[0])
+    s = ctypes.c_void_p()
+    code = lib.sph_solid_create(h, ctypes.byref(p), n, _ptr(pos), _ptr(vol), _ptr(normal), _ptr(fx), ctypes.byref(s))
+    if code != SPH_OK:
+        msg = lib.sph_solid_last_error(s).decode() if s.value else ""
+        if s.value:
+            lib.sph_solid_destroy(s)
+        raise SphError(code, msg)
+    return s
+
+
+def sph_solid_destroy(s):
+    load().sph_solid_destroy(s)
+
+
+def sph_solid_get_state(h, s, n, dim, stream=None):
+    """Returns dict(pos, vel, force (n, dim), F (n, dim, dim), solid_steps)."""
+    lib = load()
+    out = {"pos": np.empty((n, dim)), "vel": np.empty((n, dim)), "force": np.empty((n, dim)),
+           "F": np.empty((n, dim, dim))}
+    steps = ctypes.c_int64(0)
+    code = lib.sph_solid_get_state(h, s, _ptr(out["pos"]), _ptr(out["vel"]), _ptr(out["force"]), _ptr(out["F"]),
+                                   ctypes.byref(steps), _stream(stream))
+    if code != SPH_OK:
+        raise SphError(code, lib.sph_solid_last_error(s).decode())
+    out["solid_steps"] = int(steps.value)
+    return out
+
+
+def solid_from(sim, problem):
+    """Attach the solid a workload describes (solid_* attributes) to a Simulation."""
+    return sph_solid_create(sim.handle, problem.solid_model, problem.solid_rho0, problem.solid_youngs,
+                            problem.solid_poisson, problem.solid_h, problem.solid_pos, problem.solid_vol,
+                            problem.solid_normal, problem.solid_fixed)
