@@ -496,6 +496,9 @@ def run_workload(args):
     if args.workload == "diffusion3d":
         run_diffusion(args, stream)
         return
+    if args.workload == "fsi":
+        run_fsi(args, stream)
+        return
     if args.workload == "batched":
         problems = wk.batched_dam_breaks(256)
         name = "256 independent 2D dam breaks (2k-50k fluid each), one handle"
@@ -676,6 +679,53 @@ def run_diffusion(args, stream):
     print(json.dumps(out), flush=True)
 
 
+def run_fsi(args, stream):
+    """Multi-resolution fluid-structure coupling: a 2D water column on an elastic plate. The
+    plate's lattice is fixed (spacing 1/160, eight layers across its 0.05 thickness) while the
+    fluid's spacing is ratio times it, ratio 1, 2, 4, with multi time stepping (kappa solid
+    steps per fluid acoustic step), plus ratio 1 with single time stepping (the fluid's step
+    capped at the solid's): the fully resolved reference that the paper's multi-resolution
+    speedups are quoted against. Each run advances the same simulated time in advection steps
+    launched as CUDA graphs and timed with CUDA events."""
+    import torch
+    from paper_2010_12375_gb300 import sph, workloads as wk
+    dps, T = 1.0 / 160.0, args.fsi_time
+    rows = []
+    for ratio, single in ((1, True), (1, False), (2, False), (4, False)):
+        wl = wk.water_column_on_plate(dp=dps * ratio, ratio=ratio)
+        sim = sph.Simulation(wl, flags=sph.SPH_FLAG_GRAPH, stream=stream)
+        solid = sph.solid_from(sim, wl, single_step=single)
+        ns = wl.solid_pos.shape[0]
+        for _ in range(args.warmup):
+            sim.step(1)
+        d0 = sim.diagnostics()
+        steps = max(1, int(math.ceil(T / d0["dt_ad"])))
+        s0 = sph.sph_solid_get_state(sim.handle, solid, ns, 2)["solid_steps"]
+        ms, d0, d1 = _timed_steps(sim, steps, stream)
+        s1 = sph.sph_solid_get_state(sim.handle, solid, ns, 2)["solid_steps"]
+        sim_t = d1["t"] - d0["t"]
+        sub = d1["substeps"] - d0["substeps"]
+        rows.append({"ratio": ratio, "time_stepping": "single" if single else "multi",
+                     "n_fluid": wl.n_fluid, "n_solid": ns, "advection_steps": steps, "fluid_substeps": sub,
+                     "solid_steps": s1 - s0, "simulated_time": sim_t, "gpu_ms": ms,
+                     "gpu_ms_per_unit_time": ms / sim_t,
+                     "fluid_particle_substeps_per_s": wl.n_fluid * sub / (ms * 1e-3),
+                     "solid_particle_steps_per_s": ns * (s1 - s0) / (ms * 1e-3)})
+        sph.sph_solid_destroy(solid)
+        sim.close()
+    ref = rows[0]["gpu_ms_per_unit_time"]
+    for r in rows:
+        r["speedup_vs_single_resolution_single_step"] = ref / r["gpu_ms_per_unit_time"]
+    out = {"metric": "multi-resolution FSI speedup, 2D water column on an elastic plate", "unit": "x",
+           "value": rows[-1]["speedup_vs_single_resolution_single_step"], "higher_is_better": True,
+           "n_gpus": 1, "steps": None, "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "2D water column H = 1 on a clamped elastic plate (span 1, thickness 0.05, "
+                                  "E = 4.55e4, nu = 0.3, rho_s = 2.7), plate spacing 1/160, fluid spacing ratio x it",
+                      "simulated_time_per_run": T},
+           "runs": rows}
+    print(json.dumps(out), flush=True)
+
+
 def run_learned_step(args, stream):
     """Cost of one learned advection step against one plain step on the 2D dam break at
     100,128 particles, with the network's initial weights (no training: timing only)."""
@@ -768,6 +818,7 @@ def main():
                     help="untimed advection steps over which the relaxation kernels' launches are timed")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--diff-n", type=int, default=200, help="diffusion3d block: n^3 particles")
+    ap.add_argument("--fsi-time", type=float, default=0.05, help="fsi: simulated time per run")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -775,7 +826,7 @@ def main():
                     help="the frozen-pair-geometry reading (pair vectors kept from the configuration update)")
     ap.add_argument("--launch-config", default=None,
                     help="pr_tpp,pr_block,dr_tpp,dr_block: fixed launch variants instead of autotuning")
-    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes", "diffusion3d"],
+    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes", "diffusion3d", "fsi"],
                     help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -508,6 +508,10 @@ typedef struct {
   double  rho0;            /* reference density of the solid                               */
   double  youngs, poisson; /* Young's modulus E > 0 and Poisson ratio -1 < nu < 0.5         */
   double  h;               /* the solid's smoothing length h_S (its support is 2 h_S)      */
+  int32_t single_step;     /* 0: multi time stepping (kappa solid steps per fluid acoustic
+                              step); 1: single time stepping, the fluid's acoustic step capped
+                              at the solid's (kappa = 1 after the first step), the reference
+                              the multi-resolution scheme is measured against */
 } sph_solid_params;
 
 /* Attach a solid of n particles (1..16384) to a single-tank handle (one solid per handle):

@@ -11,7 +11,10 @@ namespace sph {
 // vanishing step sets ERR_DT, a substep count beyond the tank's bound ERR_TIMEOUT, and
 // either ends the tank's loop instead of letting a device-side loop spin. Returns, in every
 // thread, whether some tank still needs substeps after this one.
-__device__ __forceinline__ int dt_acoustic_block(int n_inst, const Inst* __restrict__ inst, Ctrl* ctrl, Global* g) {
+// dt_cap (or NULL): per tank, a cap on the acoustic step (0 = none), written by a coupled
+// solid run with single time stepping.
+__device__ __forceinline__ int dt_acoustic_block(int n_inst, const Inst* __restrict__ inst, Ctrl* ctrl, Global* g,
+                                                 const double* dt_cap = nullptr) {
   int any = 0;
   for (int k = threadIdx.x; k < n_inst; k += blockDim.x) {
     const Inst& I = inst[k];
@@ -23,6 +26,7 @@ __device__ __forceinline__ int dt_acoustic_block(int n_inst, const Inst* __restr
     double vmax = sqrt((double)__uint_as_float(C.vmax2));
     C.vmax2 = 0u;                                   // refilled by the pressure relaxation
     double dt_ac = I.cfl_ac * I.h_d / (I.c0_d + vmax);
+    if (dt_cap && dt_cap[k] > 0.0) dt_ac = fmin(dt_ac, dt_cap[k]);
     double rem = C.dt_ad - C.tau;
     double dt = fmin(dt_ac, rem);
     if (!(dt_ac > 1e-12 * I.h_d / I.c0_d) || !(rem > 0.0) || !(dt > 0.0)) {

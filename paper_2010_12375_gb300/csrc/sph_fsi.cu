@@ -51,6 +51,7 @@ inline unsigned fgrid(int64_t n) { return (unsigned)((n + kFBlock - 1) / kFBlock
 
 struct SolidMat {
   int model, dim;
+  int single_step;                        // cap the fluid's next acoustic step at dt_S
   float lam, mu, rho0;
   double h, c;                            // smoothing length and sound speed sqrt(K / rho0)
   float g[3];
@@ -332,29 +333,36 @@ k_fsi_fluid_continuity(const Inst I, const int* __restrict__ n_near_p, const int
 }
 
 // ---------------------------------------------------------------- solid steps ----------
-__device__ __forceinline__ void first_piola(const SolidMat& M, const float F[9], float P[9]) {
+// First Piola-Kirchhoff stress from the displacement gradient H = F - I (what the solid
+// stores: near the reference configuration F - I carries the strain without the
+// cancellation that forming F^T F - I in FP32 would cost). K = C - I = H + H^T + H^T H.
+//   linear:       E = K/2, S = lambda tr(E) I + 2 mu E
+//   Neo-Hookean:  S = mu (I - C^-1) + lambda ln J C^-1 = C^-1 (mu K + lambda ln J I),
+//                 ln J = log1p(det(I + H) - 1) with the determinant expanded in H
+// P = F S = S + H S.
+__device__ __forceinline__ void first_piola(const SolidMat& M, const float H[9], float P[9]) {
   const int d = M.dim;
-  float C[9];
+  float K[9];
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) {
-      float s = 0.f;
-      for (int k = 0; k < d; ++k) s += F[k * d + i] * F[k * d + j];
-      C[i * d + j] = s;
+      float s = H[i * d + j] + H[j * d + i];
+      for (int k = 0; k < d; ++k) s += H[k * d + i] * H[k * d + j];
+      K[i * d + j] = s;
     }
   float S[9];
   if (M.model == SPH_SOLID_LINEAR) {
     float trE = 0.f;
-    for (int i = 0; i < d; ++i) trE += 0.5f * (C[i * d + i] - 1.0f);
-    for (int i = 0; i < d; ++i)
-      for (int j = 0; j < d; ++j) {
-        const float E = 0.5f * (C[i * d + j] - (i == j ? 1.0f : 0.0f));
-        S[i * d + j] = 2.0f * M.mu * E + (i == j ? M.lam * trE : 0.0f);
-      }
+    for (int i = 0; i < d; ++i) trE += 0.5f * K[i * d + i];
+    for (int i = 0; i < d * d; ++i) S[i] = M.mu * K[i];
+    for (int i = 0; i < d; ++i) S[i * d + i] += M.lam * trE;
   } else {
-    float Ci[9], detC;
+    float C[9], Ci[9], detC, Jm1;
+    for (int i = 0; i < d * d; ++i) C[i] = K[i];
+    for (int i = 0; i < d; ++i) C[i * d + i] += 1.0f;
     if (d == 2) {
       detC = C[0] * C[3] - C[1] * C[2];
       Ci[0] = C[3] / detC; Ci[1] = -C[1] / detC; Ci[2] = -C[2] / detC; Ci[3] = C[0] / detC;
+      Jm1 = H[0] + H[3] + (H[0] * H[3] - H[1] * H[2]);
     } else {
       detC = C[0] * (C[4] * C[8] - C[5] * C[7]) - C[1] * (C[3] * C[8] - C[5] * C[6]) + C[2] * (C[3] * C[7] - C[4] * C[6]);
       Ci[0] = (C[4] * C[8] - C[5] * C[7]) / detC; Ci[1] = (C[2] * C[7] - C[1] * C[8]) / detC;
@@ -362,15 +370,27 @@ __device__ __forceinline__ void first_piola(const SolidMat& M, const float F[9],
       Ci[4] = (C[0] * C[8] - C[2] * C[6]) / detC; Ci[5] = (C[2] * C[3] - C[0] * C[5]) / detC;
       Ci[6] = (C[3] * C[7] - C[4] * C[6]) / detC; Ci[7] = (C[1] * C[6] - C[0] * C[7]) / detC;
       Ci[8] = (C[0] * C[4] - C[1] * C[3]) / detC;
+      const float tr = H[0] + H[4] + H[8];
+      const float minors = (H[0] * H[4] - H[1] * H[3]) + (H[0] * H[8] - H[2] * H[6]) + (H[4] * H[8] - H[5] * H[7]);
+      const float detH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                         H[2] * (H[3] * H[7] - H[4] * H[6]);
+      Jm1 = tr + minors + detH;
     }
-    const float lnJ = 0.5f * logf(detC);                 // J^2 = det C
-    for (int i = 0; i < d * d; ++i) S[i] = M.lam * lnJ * Ci[i] - M.mu * Ci[i];
-    for (int i = 0; i < d; ++i) S[i * d + i] += M.mu;
+    const float lnJ = log1pf(Jm1);
+    float A[9];
+    for (int i = 0; i < d * d; ++i) A[i] = M.mu * K[i];
+    for (int i = 0; i < d; ++i) A[i * d + i] += M.lam * lnJ;
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        float s = 0.f;
+        for (int k = 0; k < d; ++k) s += Ci[i * d + k] * A[k * d + j];
+        S[i * d + j] = s;
+      }
   }
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) {
-      float s = 0.f;
-      for (int k = 0; k < d; ++k) s += F[i * d + k] * S[k * d + j];
+      float s = S[i * d + j];
+      for (int k = 0; k < d; ++k) s += H[i * d + k] * S[k * d + j];
       P[i * d + j] = s;
     }
 }
@@ -380,7 +400,7 @@ struct SolidPtrs {
   int4* X;
   float4* V;
   const uint8_t* fixed;
-  float *F, *dFdt, *PB;
+  float *F, *dFdt, *PB;   // F: the displacement gradient H = F - I
   const float* B0;
   const int* nb;
   const int* cnt;
@@ -389,6 +409,7 @@ struct SolidPtrs {
   float4 *acc, *vbar, *abar, *vsum, *asum;
   long long* steps;      // solid steps taken, total
   int* kappa_last;
+  double* dt_cap;        // the fluid's cap (single time stepping), or NULL
 };
 
 // All kappa solid steps of one fluid acoustic step, one block, __syncthreads between the
@@ -544,6 +565,36 @@ k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ct
     S.vbar[a] = make_float4(vs.x * inv, vs.y * inv, vs.z * inv, 0.f);
     S.abar[a] = make_float4(as.x * inv, as.y * inv, as.z * inv, 0.f);
   }
+  if (M.single_step && S.dt_cap) {
+    // single time stepping: the next fluid step takes the solid's step from the state it
+    // starts from (the same dt_S the next call computes first), a hair below it so kappa = 1
+    __syncthreads();
+    vm = 0.f;
+    am = 0.f;
+    for (int64_t a = threadIdx.x; a < ns; a += blockDim.x) {
+      const float4 v = S.V[a], ac = S.acc[a];
+      vm = fmaxf(vm, v.x * v.x + v.y * v.y + v.z * v.z);
+      am = fmaxf(am, ac.x * ac.x + ac.y * ac.y + ac.z * ac.z);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+      am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red_v[threadIdx.x >> 5] = vm;
+      red_a[threadIdx.x >> 5] = am;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        vm = fmaxf(vm, red_v[w]);
+        am = fmaxf(am, red_a[w]);
+      }
+      double dts = M.h / (M.c + sqrt((double)vm));
+      if (am > 0.f) dts = fmin(dts, sqrt(M.h / sqrt((double)am)));
+      S.dt_cap[0] = 0.6 * dts * (1.0 - 1e-9);
+    }
+  }
 }
 
 __global__ void k_solid_export(int64_t ns, int d, const int4* __restrict__ X, const float4* __restrict__ V,
@@ -562,8 +613,8 @@ __global__ void k_solid_export(int64_t ns, int d, const int4* __restrict__ X, co
     if (vel) vel[a * d + k] = vv[k];
     if (frc) frc[a * d + k] = ff[k];
   }
-  if (Fout)
-    for (int k = 0; k < d * d; ++k) Fout[a * d * d + k] = F[(int64_t)k * ns + a];
+  if (Fout)                                // F = I + H
+    for (int k = 0; k < d * d; ++k) Fout[a * d * d + k] = (double)F[(int64_t)k * ns + a] + (k % (d + 1) == 0 ? 1.0 : 0.0);
 }
 
 }  // namespace
@@ -581,7 +632,7 @@ struct sph_solid {
   float4 *V = nullptr, *N = nullptr, *force = nullptr, *acc = nullptr, *vbar = nullptr, *abar = nullptr;
   float4 *vsum = nullptr, *asum = nullptr, *gW = nullptr;
   uint8_t* fixed = nullptr;
-  float *F = nullptr, *dFdt = nullptr, *PB = nullptr, *B0 = nullptr;
+  float *F = nullptr, *dFdt = nullptr, *PB = nullptr, *B0 = nullptr;   // F holds H = F - I
   int *nb = nullptr, *cnt = nullptr, *near = nullptr, *box = nullptr, *dev_err = nullptr, *kappa_last = nullptr;
   int* n_near = nullptr;        // length of the near-fluid list (device)
   long long* steps = nullptr;
@@ -628,6 +679,7 @@ sph::SolidPtrs ptrs(sph_solid* s) {
   P.asum = s->asum;
   P.steps = s->steps;
   P.kappa_last = s->kappa_last;
+  P.dt_cap = s->h ? s->h->b.dt_cap : nullptr;
   return P;
 }
 
@@ -716,6 +768,7 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
   const double nu = p->poisson, E = p->youngs;
   s->mat.model = p->model;
   s->mat.dim = d;
+  s->mat.single_step = p->single_step ? 1 : 0;
   s->mat.mu = (float)(E / (2.0 * (1.0 + nu)));
   const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   s->mat.lam = (float)lam;
@@ -759,13 +812,10 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
   if (!ok) return sfail(s, SPH_E_OOM, "device allocation of the solid failed");
   double *dx0 = nullptr, *dvol = nullptr;
   if (!salloc(s, &dx0, (size_t)n * d) || !salloc(s, &dvol, n)) return sfail(s, SPH_E_OOM, "device allocation failed");
-  std::vector<float> eye(dd * n, 0.f);
-  for (int k = 0; k < d; ++k)
-    for (int64_t a = 0; a < n; ++a) eye[(size_t)(k * d + k) * n + a] = 1.f;
   if (cudaMemcpy(s->X, hX.data(), sizeof(int4) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->N, hN.data(), sizeof(float4) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->fixed, hfx.data(), n, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(s->F, eye.data(), sizeof(float) * dd * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(s->F, 0, sizeof(float) * dd * n) != cudaSuccess ||          // H = F - I = 0
       cudaMemcpy(dx0, hp.data(), sizeof(double) * n * d, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(dvol, hv.data(), sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(s->dFdt, 0, sizeof(float) * dd * n) != cudaSuccess ||
@@ -786,6 +836,14 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
   }
   if (derr & 1) return sfail(s, SPH_E_CAPACITY, "a solid particle has more reference neighbours than the capacity");
   if (derr & 2) return sfail(s, SPH_E_INVALID, "a solid particle's correction matrix is singular (too few neighbours)");
+  if (p->single_step) {
+    double* cap = nullptr;
+    if (!salloc(s, &cap, 1) || cudaMemset(cap, 0, sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return sfail(s, SPH_E_OOM, "device allocation of the step cap failed");
+    }
+    h->b.dt_cap = cap;
+  }
   h->solid = s;
   sph_drop_graph(h);                       // the loop now includes the coupling kernels
   h->cells_valid = false;                  // the near list comes with the next configuration update
@@ -796,6 +854,7 @@ void sph_solid_destroy(sph_solid* s) {
   if (!s) return;
   if (s->h && s->h->solid == s) {
     s->h->solid = nullptr;
+    s->h->b.dt_cap = nullptr;              // freed with the solid's allocations below
     sph_drop_graph(s->h);
   }
   for (void* p : s->allocs) cudaFree(p);

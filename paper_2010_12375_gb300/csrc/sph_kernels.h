@@ -59,6 +59,7 @@ struct Buffers {
   uint32_t* nbc = nullptr;        // [n] fluid count | wall count << 16
   float4* geo = nullptr;          // [cap][n] frozen r_i - r_j and (dW/dr)/r per slot (or NULL)
   GridBarrier* pbar = nullptr;    // [1] persistent substep loop
+  double* dt_cap = nullptr;       // [n_inst] cap on the acoustic step (0 = none), or NULL
   // half-pair evaluation (or NULL): per-slot shares [cap][n], per-particle partial sums [n],
   // reverse slots [cap][n] (slot of j in i's row for each slot of j's row holding i < j)
   float4* hshare = nullptr;

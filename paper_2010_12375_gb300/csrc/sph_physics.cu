@@ -243,8 +243,8 @@ __global__ void k_dt_advection(int n_inst, const Inst* __restrict__ inst, Ctrl* 
 // sph_ctrl.cuh). Sets the condition of the device-side substep loop when launched inside
 // a graph.
 __global__ void k_dt_acoustic(int n_inst, const Inst* __restrict__ inst, Ctrl* ctrl, Global* g,
-                              cudaGraphConditionalHandle cond, int use_cond) {
-  const int any = dt_acoustic_block(n_inst, inst, ctrl, g);
+                              cudaGraphConditionalHandle cond, int use_cond, const double* dt_cap) {
+  const int any = dt_acoustic_block(n_inst, inst, ctrl, g, dt_cap);
   if (threadIdx.x == 0) {
     g->active = any;
     g->substeps += 1;
@@ -437,7 +437,7 @@ void launch_viscous(const Buffers& b, cudaStream_t s, int64_t* launches) {
 
 void launch_dt_acoustic(const Buffers& b, cudaStream_t s, cudaGraphConditionalHandle cond,
                         bool use_cond, int64_t* launches) {
-  k_dt_acoustic<<<1, 256, 0, s>>>(b.n_inst, b.inst, b.ctrl, b.glob, cond, use_cond ? 1 : 0);
+  k_dt_acoustic<<<1, 256, 0, s>>>(b.n_inst, b.inst, b.ctrl, b.glob, cond, use_cond ? 1 : 0, b.dt_cap);
   ++*launches;
 }
 

@@ -111,7 +111,7 @@ SPH_SOLID_LINEAR, SPH_SOLID_NEO_HOOKEAN = 1, 2
 
 class SphSolidParams(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("rho0", ctypes.c_double), ("youngs", ctypes.c_double),
-                ("poisson", ctypes.c_double), ("h", ctypes.c_double)]
+                ("poisson", ctypes.c_double), ("h", ctypes.c_double), ("single_step", ctypes.c_int32)]
 
 
 class SphError(RuntimeError):
@@ -711,10 +711,10 @@ class Simulation:
 
 
 # ------------------------------------------------------------------------ fluid-structure
-def sph_solid_create(h, model, rho0, youngs, poisson, h_s, pos, vol, normal, fixed=None):
+def sph_solid_create(h, model, rho0, youngs, poisson, h_s, pos, vol, normal, fixed=None, single_step=False):
     """Attach an elastic solid to handle h; returns the opaque solid."""
     lib = load()
-    p = SphSolidParams(int(model), float(rho0), float(youngs), float(poisson), float(h_s))
+    p = SphSolidParams(int(model), float(rho0), float(youngs), float(poisson), float(h_s), 1 if single_step else 0)
     pos, vol, normal = _f64(pos), _f64(vol), _f64(normal)
     fx = None if fixed is None else np.ascontiguousarray(np.asarray(fixed).astype(np.int32))
     n = int(vol.shape[0])
@@ -746,8 +746,8 @@ def sph_solid_get_state(h, s, n, dim, stream=None):
     return out
 
 
-def solid_from(sim, problem):
+def solid_from(sim, problem, single_step=False):
     """Attach the solid a workload describes (solid_* attributes) to a Simulation."""
     return sph_solid_create(sim.handle, problem.solid_model, problem.solid_rho0, problem.solid_youngs,
                             problem.solid_poisson, problem.solid_h, problem.solid_pos, problem.solid_vol,
-                            problem.solid_normal, problem.solid_fixed)
+                            problem.solid_normal, problem.solid_fixed, single_step)
