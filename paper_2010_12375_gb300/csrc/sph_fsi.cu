@@ -57,12 +57,17 @@ struct SolidMat {
   float g[3];
 };
 
-// d x d matrices stored element-major: M[(r * d + c) * ns + a]
-__device__ __forceinline__ void load_mat(const float* M, int64_t ns, int64_t a, int d, float m[9]) {
-  for (int k = 0; k < d * d; ++k) m[k] = M[(int64_t)k * ns + a];
+// d x d matrices stored element-major: M[(r * d + c) * ns + a]; D is a compile-time
+// dimension so the small matrices stay in registers
+template <int D>
+__device__ __forceinline__ void load_mat(const float* M, int64_t ns, int64_t a, float m[D * D]) {
+#pragma unroll
+  for (int k = 0; k < D * D; ++k) m[k] = M[(int64_t)k * ns + a];
 }
-__device__ __forceinline__ void store_mat(float* M, int64_t ns, int64_t a, int d, const float m[9]) {
-  for (int k = 0; k < d * d; ++k) M[(int64_t)k * ns + a] = m[k];
+template <int D>
+__device__ __forceinline__ void store_mat(float* M, int64_t ns, int64_t a, const float m[D * D]) {
+#pragma unroll
+  for (int k = 0; k < D * D; ++k) M[(int64_t)k * ns + a] = m[k];
 }
 
 // ---------------------------------------------------------------- reference set-up ------
@@ -340,8 +345,9 @@ k_fsi_fluid_continuity(const Inst I, const int* __restrict__ n_near_p, const int
 //   Neo-Hookean:  S = mu (I - C^-1) + lambda ln J C^-1 = C^-1 (mu K + lambda ln J I),
 //                 ln J = log1p(det(I + H) - 1) with the determinant expanded in H
 // P = F S = S + H S.
-__device__ __forceinline__ void first_piola(const SolidMat& M, const float H[9], float P[9]) {
-  const int d = M.dim;
+template <int D>
+__device__ __forceinline__ void first_piola(const SolidMat& M, const float H[D * D], float P[D * D]) {
+  constexpr int d = D;
   float K[9];
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) {
@@ -414,11 +420,12 @@ struct SolidPtrs {
 
 // All kappa solid steps of one fluid acoustic step, one block, __syncthreads between the
 // three phases of each step.
+template <int D>
 __global__ void __launch_bounds__(kSolidThreads)
 k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ctrl) {
   const double dtF = ctrl[0].dt;
   if (dtF == 0.0) return;
-  const int d = M.dim;
+  constexpr int d = D;
   const int64_t ns = S.ns;
   // Eq. dts-advection from the solid's state at the start of the fluid step (R25)
   __shared__ float red_v[kSolidThreads / 32], red_a[kSolidThreads / 32];
@@ -459,11 +466,11 @@ k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ct
   for (int step = 0; step < kappa; ++step) {
     // phase 1: F to the mid point, r half a step, P B0
     for (int64_t a = threadIdx.x; a < ns; a += blockDim.x) {
-      float F[9], dF[9], B[9], P[9], PB[9];
-      load_mat(S.F, ns, a, d, F);
-      load_mat(S.dFdt, ns, a, d, dF);
+      float F[D * D], dF[D * D], B[D * D], P[D * D], PB[D * D];
+      load_mat<D>(S.F, ns, a, F);
+      load_mat<D>(S.dFdt, ns, a, dF);
       for (int k = 0; k < d * d; ++k) F[k] += hh * dF[k];
-      store_mat(S.F, ns, a, d, F);
+      store_mat<D>(S.F, ns, a, F);
       if (!S.fixed[a]) {
         const float4 v = S.V[a];
         int4 q = S.X[a];
@@ -472,15 +479,15 @@ k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ct
         if (d == 3) q.z += __float2int_rn(hh * v.z * I.inv_dq);
         S.X[a] = q;
       }
-      first_piola(M, F, P);
-      load_mat(S.B0, ns, a, d, B);
+      first_piola<D>(M, F, P);
+      load_mat<D>(S.B0, ns, a, B);
       for (int i = 0; i < d; ++i)
         for (int j = 0; j < d; ++j) {
           float s = 0.f;
           for (int k = 0; k < d; ++k) s += P[i * d + k] * B[k * d + j];
           PB[i * d + j] = s;
         }
-      store_mat(S.PB, ns, a, d, PB);
+      store_mat<D>(S.PB, ns, a, PB);
     }
     __syncthreads();
     // phase 2: dv/dt, v, r the second half
@@ -489,8 +496,8 @@ k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ct
       if (!S.fixed[a]) {
         const float Va = i2f(S.X[a].w);
         const float ma = M.rho0 * Va;
-        float PBa[9];
-        load_mat(S.PB, ns, a, d, PBa);
+        float PBa[D * D];
+        load_mat<D>(S.PB, ns, a, PBa);
         float s[3] = {0, 0, 0}, c[3] = {0, 0, 0};
         const int nc = S.cnt[a];
         for (int t = 0; t < nc; ++t) {
@@ -532,7 +539,7 @@ k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ct
     for (int64_t a = threadIdx.x; a < ns; a += blockDim.x) {
       const float4 va = S.V[a];
       const float vav[3] = {va.x, va.y, va.z};
-      float G[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      float G[D * D] = {};
       const int nc = S.cnt[a];
       for (int t = 0; t < nc; ++t) {
         const int b = S.nb[(int64_t)t * ns + a];
@@ -544,18 +551,18 @@ k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ct
         for (int i = 0; i < d; ++i)
           for (int j = 0; j < d; ++j) G[i * d + j] += Vb * (vbv[i] - vav[i]) * gv[j];
       }
-      float B[9], dF[9], F[9];
-      load_mat(S.B0, ns, a, d, B);
+      float B[D * D], dF[D * D], F[D * D];
+      load_mat<D>(S.B0, ns, a, B);
       for (int i = 0; i < d; ++i)
         for (int j = 0; j < d; ++j) {
           float s = 0.f;
           for (int k = 0; k < d; ++k) s += G[i * d + k] * B[k * d + j];
           dF[i * d + j] = s;
         }
-      store_mat(S.dFdt, ns, a, d, dF);
-      load_mat(S.F, ns, a, d, F);
+      store_mat<D>(S.dFdt, ns, a, dF);
+      load_mat<D>(S.F, ns, a, F);
       for (int k = 0; k < d * d; ++k) F[k] += hh * dF[k];
-      store_mat(S.F, ns, a, d, F);
+      store_mat<D>(S.F, ns, a, F);
     }
     __syncthreads();
   }
@@ -730,7 +737,8 @@ void sph_fsi_after_density(sph_handle* h, cudaStream_t st, int64_t* launches) {
                                                  s->N, s->vbar, s->abar);
     *launches += 1;
   }
-  sph::k_solid_steps<<<1, sph::kSolidThreads, 0, st>>>(b.inst0, s->mat, ptrs(s), b.ctrl);
+  auto ks = b.dim == 2 ? sph::k_solid_steps<2> : sph::k_solid_steps<3>;
+  ks<<<1, sph::kSolidThreads, 0, st>>>(b.inst0, s->mat, ptrs(s), b.ctrl);
   *launches += 1;
 }
 
