@@ -43,10 +43,10 @@ TRAFFIC_SOURCE_HASH = "4ddd8c2047d80b4b"
 
 
 # DRAM bytes (read + write) per particle of one diffusion stage launch, from the ncu capture
-# of k_diffusion_stage on the 120^3 block (both stages, 652.4 and 655.8 MB per launch at 1.728M
+# of k_diffusion_stage on the 120^3 block (both stages, 651.8 and 652.8 MB per launch at 1.728M
 # particles); traffic is per particle on the lattice, so it scales to the 200^3 block.
-DIFF_TRAFFIC_BYTES_PER_PARTICLE = 378.5
-DIFF_TRAFFIC_SOURCE_HASH = "c95b5e4d5b85fc09"
+DIFF_TRAFFIC_BYTES_PER_PARTICLE = 377.5
+DIFF_TRAFFIC_SOURCE_HASH = "333d0b1078cf223d"
 # the stage kernel and its device helpers: the rest of the file (pack/unpack, the reaction
 # step, the host API) does not change the captured launches
 DIFF_SOURCES = ("sph_common.cuh", ("sph_diffusion.cu", "float2 pair_coord2(", "Per call: records of both buffers"))

@@ -116,7 +116,8 @@ __device__ __forceinline__ Geo2 geometry2(float2 rx, float2 ry, float2 rz, float
   float2 r2 = fma2(rx, rx, fma2(ry, ry, fma2(rz, rz, f2(kTinyR2))));
   g.inv_r = rsqrt2(r2);
   g.r = mul2(r2, g.inv_r);
-  float2 t = max2(fma2(g.r, f2(-0.5f * inv_h), f2(1.0f)), 0.0f);   // 1 - q/2, 0 beyond 2h
+  // 1 - q/2 clamped to [0, 1] (0 beyond 2h; r >= 0 keeps it <= 1): one saturating FMA per lane
+  float2 t = make_float2(__saturatef(fmaf(g.r.x, -0.5f * inv_h, 1.0f)), __saturatef(fmaf(g.r.y, -0.5f * inv_h, 1.0f)));
   g.fw = mul2(f2(dwr), mul2(mul2(t, t), t));                       // -5 alpha/h^2 (1-q/2)^3
   return g;
 }
@@ -177,7 +178,7 @@ __device__ __forceinline__ void pr_fluid2(const Inst& I, PrCtx& C, const int4& p
   const float2 rho_j = add2(f2(I.rho0), dev_j);
   // U_L - U_R = (v_j - v_i).r_ij / |r_ij|
   const float2 dU = mul2(fma2(dvx, rx, fma2(dvy, ry, mul2(dvz, rz))), G.inv_r);
-  const float2 beta = min2(mul2(f2(I.kc), max2(dU, 0.0f)), 1.0f);
+  const float2 beta = make_float2(__saturatef(I.kc * dU.x), __saturatef(I.kc * dU.y));   // min(kc max(dU, 0), 1)
   // P* = (p_i + p_j)/2 + (c0/4)(rho_i + rho_j) beta (U_L - U_R)
   const float2 pbar = mul2(f2(I.hc0sq), add2(f2(C.dev_i), dev_j));
   const float2 pstar = fma2(mul2(f2(I.qc0), add2(f2(C.rho_i), rho_j)), mul2(beta, dU), pbar);
@@ -219,7 +220,7 @@ __device__ __forceinline__ void pr_wall2(const Inst& I, PrCtx& C, const int4& pi
   const float2 PR = fma2(f2(-C.rho_i), gr, f2(C.pr_i));
   const float2 rhoR = fma2(PR, f2(I.inv_c0sq), f2(I.rho0));
   const float2 dU = add2(UL, UL);
-  const float2 beta = min2(mul2(f2(I.kc), max2(dU, 0.0f)), 1.0f);
+  const float2 beta = make_float2(__saturatef(I.kc * dU.x), __saturatef(I.kc * dU.y));   // min(kc max(dU, 0), 1)
   const float2 pstar = fma2(mul2(f2(I.qc0), add2(f2(C.rho_i), rhoR)), mul2(beta, dU),
                             mul2(f2(0.5f), add2(f2(C.pr_i), PR)));
   const float2 f = mul2(mul2(Vw, pstar), G.fw);
