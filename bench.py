@@ -38,8 +38,8 @@ UNIT = "particle-substeps/s"
 # (1,024,000 particles, neighbour table 0.5 GB > L2); it is scaled to the benchmark's particle
 # count (the traffic is per particle: state records plus its neighbour row). Valid only
 # for the kernel sources whose hash is recorded with it.
-TRAFFIC_BYTES_PER_PARTICLE = 390.50
-TRAFFIC_SOURCE_HASH = "4ddd8c2047d80b4b"
+TRAFFIC_BYTES_PER_PARTICLE = 389.79
+TRAFFIC_SOURCE_HASH = "af5377473ba40097"
 
 
 # DRAM bytes (read + write) per particle of one diffusion stage launch, from the ncu capture
