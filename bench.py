@@ -693,7 +693,7 @@ def run_fsi(args, stream):
     rows = []
     for ratio, single in ((1, True), (1, False), (2, False), (4, False)):
         wl = wk.water_column_on_plate(dp=dps * ratio, ratio=ratio)
-        sim = sph.Simulation(wl, flags=sph.SPH_FLAG_GRAPH, stream=stream)
+        sim = sph.Simulation(wl, flags=0 if args.host_loop else sph.SPH_FLAG_GRAPH, stream=stream)
         solid = sph.solid_from(sim, wl, single_step=single)
         ns = wl.solid_pos.shape[0]
         for _ in range(args.warmup):

@@ -26,7 +26,7 @@
 //  * after the fluid density relaxation, each near fluid particle adds the continuity term
 //    of its solid neighbours as moving walls (U_L = -n.v_i, U_R = -U_L - 2 n.v~_a, P_R = p^d);
 //  * then kappa = [dt_F/dt_S] + 1 solid steps of dt_F/kappa (dt_S of Eq. dts-advection) with
-//    the fluid force held, in one single-block kernel; v~ and a~ become their averages.
+//    the fluid force held, in one thread-block cluster; v~ and a~ become their averages.
 // The fluid particles near the solid (inside its bounding box widened by 3 h_F) are listed
 // once per configuration update, in storage order.
 #include <algorithm>
@@ -36,6 +36,8 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "sph.h"
 #include "sph_handle.h"
 #include "sph_kernels.h"
@@ -43,11 +45,19 @@
 namespace sph {
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int kFBlock = 128;
-constexpr int kSolidThreads = 1024;       // the solid steps run in one block
+constexpr int kSolidThreads = 1024;       // threads per block of the solid-step cluster
 constexpr int kMaxSolid = 16 * kSolidThreads;
+constexpr int kMaxSolidSteps = 1 << 16;   // solid steps in one fluid step, at most
 
 inline unsigned fgrid(int64_t n) { return (unsigned)((n + kFBlock - 1) / kFBlock); }
+// blocks for a warp per item over up to n items: 16 blocks an SM at most (grid-stride beyond)
+inline unsigned wgrid(int64_t n) {
+  constexpr int w = kFBlock / 32;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + w - 1) / w, 152 * 16));
+}
 
 struct SolidMat {
   int model, dim;
@@ -71,16 +81,31 @@ __device__ __forceinline__ void store_mat(float* M, int64_t ns, int64_t a, const
 }
 
 // ---------------------------------------------------------------- reference set-up ------
+// Neighbour slots as (owning block << 16) | slot in its tile, once the cluster's particles
+// per block P is fixed: the solid steps then address a neighbour's shared memory directly.
+__global__ void k_solid_pack_rows(int64_t ns, int cap, const int* __restrict__ cnt, int P, int* __restrict__ nb) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= ns) return;
+  const int c = min(cnt[a], cap);
+  for (int t = 0; t < c; ++t) {
+    const int b = nb[(int64_t)t * ns + a];
+    nb[(int64_t)t * ns + a] = ((b / P) << 16) | (b % P);
+  }
+}
+
 // One thread per solid particle: its neighbours within 2 h_S in the reference configuration
-// (ascending index), their kernel gradients, and B0 (FP64, then stored in FP32).
+// (ascending index), their kernel gradients times the neighbour's volume gV_ab = V_b grad0_a
+// W_ab, the row sum c_a = sum_b gV_ab, and B0 (all in FP64, then stored in FP32).
 __global__ void k_solid_setup(int64_t ns, int d, double h, const double* __restrict__ x0,
                               const double* __restrict__ vol, int cap, int* __restrict__ nb,
-                              int* __restrict__ cnt, float4* __restrict__ gW, float* __restrict__ B0, int* err) {
+                              int* __restrict__ cnt, float4* __restrict__ gV, float4* __restrict__ cA,
+                              float* __restrict__ B0, int* err) {
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= ns) return;
   const double pi = 3.14159265358979323846;
   const double alpha = d == 2 ? 7.0 / (4.0 * pi * h * h) : 21.0 / (16.0 * pi * h * h * h);
   double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double csum[3] = {0, 0, 0};
   int c = 0;
   for (int64_t b = 0; b < ns; ++b) {
     if (b == a) continue;
@@ -98,12 +123,14 @@ __global__ void k_solid_setup(int64_t ns, int d, double h, const double* __restr
     const double fw = alpha / h * (-5.0 * q) * t * t * t / dist;     // (dW/dr) / r
     double g[3] = {fw * r[0], fw * r[1], fw * r[2]};
     nb[(int64_t)c * ns + a] = (int)b;
-    gW[(int64_t)c * ns + a] = make_float4((float)g[0], (float)g[1], (float)g[2], 0.f);
+    gV[(int64_t)c * ns + a] = make_float4((float)(vol[b] * g[0]), (float)(vol[b] * g[1]), (float)(vol[b] * g[2]), 0.f);
+    for (int k = 0; k < 3; ++k) csum[k] += vol[b] * g[k];
     for (int i = 0; i < d; ++i)
       for (int j = 0; j < d; ++j) M[i * d + j] += vol[b] * (-r[i]) * g[j];   // (r0_b - r0_a) (x) grad
     ++c;
   }
   cnt[a] = c;
+  cA[a] = make_float4((float)csum[0], (float)csum[1], (float)csum[2], 0.f);
   double inv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (d == 2) {
     const double det = M[0] * M[3] - M[1] * M[2];
@@ -229,6 +256,35 @@ __device__ __forceinline__ float3 fsi_force(const FsiPair& P, float dev_i, float
   return f;
 }
 
+// The coupling sums run a warp per particle: each lane takes a strided share of the other
+// side's particles with a compensated running sum, and the warp combines the 32 shares by
+// a fixed shuffle tree of error-free sums, so every result is deterministic. The grids are
+// fixed (a grid-stride loop over warps), since the near list's length is on the device.
+constexpr int kCoupleWarps = kFBlock / 32;
+
+// Error-free sum of two floats (Knuth's two-sum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Running sum with its error term, and the warp-wide combination of 32 such pairs.
+__device__ __forceinline__ void csum_add(float& s, float& e, float x) {
+  float t;
+  two_sum(s, x, s, t);
+  e += t;
+}
+__device__ __forceinline__ float csum_warp(float s, float e) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float so = __shfl_xor_sync(0xffffffffu, s, o), eo = __shfl_xor_sync(0xffffffffu, e, o);
+    float t;
+    two_sum(s, so, s, t);
+    e += eo + t;
+  }
+  return s + e;
+}
+
 template <int D>
 __global__ void __launch_bounds__(kFBlock)
 k_fsi_fluid_pressure(const Inst I, const int* __restrict__ n_near_p, const int* __restrict__ near, const int4* __restrict__ PH,
@@ -236,38 +292,42 @@ k_fsi_fluid_pressure(const Inst I, const int* __restrict__ n_near_p, const int* 
                      const Ctrl* __restrict__ ctrl, int64_t ns, const int4* __restrict__ X,
                      const float4* __restrict__ N, const float4* __restrict__ vbar, const float4* __restrict__ abar,
                      float4* __restrict__ acc_keep) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= *n_near_p) return;
   const double dtd = ctrl[0].dt;
   if (dtd == 0.0) return;
-  const int i = near[k];
-  const int4 qi = PH[i];
-  const float dev_i = i2f(qi.w);
-  const float m_i = mass ? mass[i] : I.mass;
-  const float4 vi = VS[i];
-  float s[3] = {0, 0, 0}, c[3] = {0, 0, 0};
-  for (int64_t a = 0; a < ns; ++a) {
-    const int4 qa = X[a];
-    const FsiPair P = fsi_geometry<D>(qi, qa, I);
-    if (!P.in) continue;
-    const float3 f = fsi_force(P, dev_i, m_i, vi, i2f(qa.w), N[a], vbar[a], abar[a], I);
-    kahan_add(s[0], c[0], f.x / m_i);
-    kahan_add(s[1], c[1], f.y / m_i);
-    if (D == 3) kahan_add(s[2], c[2], f.z / m_i);
-  }
-  const float dt = (float)dtd;
-  const float ax = s[0] - c[0], ay = s[1] - c[1], az = s[2] - c[2];
-  float4 v = VH[i];
-  v.x += dt * ax;
-  v.y += dt * ay;
-  if (D == 3) v.z += dt * az;
-  VH[i] = v;
-  if (acc_keep) {
-    float4 a = acc_keep[i];
-    a.x += ax;
-    a.y += ay;
-    a.z += az;
-    acc_keep[i] = a;
+  const int lane = threadIdx.x & 31;
+  const int n_near = *n_near_p;
+  for (int k = blockIdx.x * kCoupleWarps + (threadIdx.x >> 5); k < n_near; k += gridDim.x * kCoupleWarps) {
+    const int i = near[k];
+    const int4 qi = PH[i];
+    const float dev_i = i2f(qi.w);
+    const float m_i = mass ? mass[i] : I.mass;
+    const float4 vi = VS[i];
+    float s[3] = {0, 0, 0}, e[3] = {0, 0, 0};
+    for (int64_t a = lane; a < ns; a += 32) {
+      const int4 qa = X[a];
+      const FsiPair P = fsi_geometry<D>(qi, qa, I);
+      if (!P.in) continue;
+      const float3 f = fsi_force(P, dev_i, m_i, vi, i2f(qa.w), N[a], vbar[a], abar[a], I);
+      csum_add(s[0], e[0], f.x / m_i);
+      csum_add(s[1], e[1], f.y / m_i);
+      if (D == 3) csum_add(s[2], e[2], f.z / m_i);
+    }
+    const float ax = csum_warp(s[0], e[0]), ay = csum_warp(s[1], e[1]), az = D == 3 ? csum_warp(s[2], e[2]) : 0.f;
+    if (lane == 0) {
+      const float dt = (float)dtd;
+      float4 v = VH[i];
+      v.x += dt * ax;
+      v.y += dt * ay;
+      if (D == 3) v.z += dt * az;
+      VH[i] = v;
+      if (acc_keep) {
+        float4 acc = acc_keep[i];
+        acc.x += ax;
+        acc.y += ay;
+        acc.z += az;
+        acc_keep[i] = acc;
+      }
+    }
   }
 }
 
@@ -277,26 +337,28 @@ k_fsi_solid_force(const Inst I, const int* __restrict__ n_near_p, const int* __r
                   const float4* __restrict__ VS, const float* __restrict__ mass, const Ctrl* __restrict__ ctrl,
                   int64_t ns, const int4* __restrict__ X, const float4* __restrict__ N,
                   const float4* __restrict__ vbar, const float4* __restrict__ abar, float4* __restrict__ force) {
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= ns) return;
   if (ctrl[0].dt == 0.0) return;
-  const int4 qa = X[a];
-  const float V_a = i2f(qa.w);
-  const float4 n = N[a], vb = vbar[a], ab = abar[a];
+  const int lane = threadIdx.x & 31;
   const int n_near = *n_near_p;
-  float s[3] = {0, 0, 0}, c[3] = {0, 0, 0};
-  for (int k = 0; k < n_near; ++k) {
-    const int i = near[k];
-    const int4 qi = PH[i];
-    const FsiPair P = fsi_geometry<D>(qi, qa, I);
-    if (!P.in) continue;
-    const float m_i = mass ? mass[i] : I.mass;
-    const float3 f = fsi_force(P, i2f(qi.w), m_i, VS[i], V_a, n, vb, ab, I);
-    kahan_add(s[0], c[0], -f.x);
-    kahan_add(s[1], c[1], -f.y);
-    if (D == 3) kahan_add(s[2], c[2], -f.z);
+  for (int64_t a = (int64_t)blockIdx.x * kCoupleWarps + (threadIdx.x >> 5); a < ns; a += (int64_t)gridDim.x * kCoupleWarps) {
+    const int4 qa = X[a];
+    const float V_a = i2f(qa.w);
+    const float4 n = N[a], vb = vbar[a], ab = abar[a];
+    float s[3] = {0, 0, 0}, e[3] = {0, 0, 0};
+    for (int k = lane; k < n_near; k += 32) {
+      const int i = near[k];
+      const int4 qi = PH[i];
+      const FsiPair P = fsi_geometry<D>(qi, qa, I);
+      if (!P.in) continue;
+      const float m_i = mass ? mass[i] : I.mass;
+      const float3 f = fsi_force(P, i2f(qi.w), m_i, VS[i], V_a, n, vb, ab, I);
+      csum_add(s[0], e[0], -f.x);
+      csum_add(s[1], e[1], -f.y);
+      if (D == 3) csum_add(s[2], e[2], -f.z);
+    }
+    const float fx = csum_warp(s[0], e[0]), fy = csum_warp(s[1], e[1]), fz = D == 3 ? csum_warp(s[2], e[2]) : 0.f;
+    if (lane == 0) force[a] = make_float4(fx, fy, fz, 0.f);
   }
-  force[a] = make_float4(s[0] - c[0], s[1] - c[1], s[2] - c[2], 0.f);
 }
 
 template <int D>
@@ -305,36 +367,40 @@ k_fsi_fluid_continuity(const Inst I, const int* __restrict__ n_near_p, const int
                        float4* __restrict__ VS, const int4* __restrict__ PH, const Ctrl* __restrict__ ctrl,
                        int64_t ns, const int4* __restrict__ X, const float4* __restrict__ N,
                        const float4* __restrict__ vbar, const float4* __restrict__ abar) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= *n_near_p) return;
   const double dtd = ctrl[0].dt;
   if (dtd == 0.0) return;
-  const int i = near[k];
-  int4 qi = PS[i];                         // r^{n+1}, and the new density deviation in w
-  float4 vi = VS[i];                       // v^{n+1}
-  const float dev_h = i2f(PH[i].w);        // rho_i is the mid-point density, as in the fluid pass
-  const float rho_i = I.rho0 + dev_h;
-  const float p_i = I.c0sq * dev_h;
-  float s = 0.f, c = 0.f;
-  for (int64_t a = 0; a < ns; ++a) {
-    const int4 qa = X[a];
-    const FsiPair P = fsi_geometry<D>(qi, qa, I);
-    if (!P.in) continue;
-    const float4 n = N[a], vb = vbar[a];
-    const float UL = -(n.x * vi.x + n.y * vi.y + n.z * vi.z);
-    const float uw = -(n.x * vb.x + n.y * vb.y + n.z * vb.z);
-    const float UR = -UL + 2.0f * uw;
-    const float PR = imaginary_pressure(p_i, rho_i, P, n, abar[a], I);
-    const float rhoR = I.rho0 + PR * I.inv_c0sq;
-    const float Us = 0.5f * (UL + UR) + (p_i - PR) / ((rho_i + rhoR) * I.c0);   // (P_L - P_R)/(2 rho_bar c0)
-    kahan_add(s, c, 2.0f * rho_i * i2f(qa.w) * (Us - UL) * P.dW);
+  const int lane = threadIdx.x & 31;
+  const int n_near = *n_near_p;
+  for (int k = blockIdx.x * kCoupleWarps + (threadIdx.x >> 5); k < n_near; k += gridDim.x * kCoupleWarps) {
+    const int i = near[k];
+    int4 qi = PS[i];                       // r^{n+1}, and the new density deviation in w
+    float4 vi = VS[i];                     // v^{n+1}
+    const float dev_h = i2f(PH[i].w);      // rho_i is the mid-point density, as in the fluid pass
+    const float rho_i = I.rho0 + dev_h;
+    const float p_i = I.c0sq * dev_h;
+    float s = 0.f, e = 0.f;
+    for (int64_t a = lane; a < ns; a += 32) {
+      const int4 qa = X[a];
+      const FsiPair P = fsi_geometry<D>(qi, qa, I);
+      if (!P.in) continue;
+      const float4 n = N[a], vb = vbar[a];
+      const float UL = -(n.x * vi.x + n.y * vi.y + n.z * vi.z);
+      const float uw = -(n.x * vb.x + n.y * vb.y + n.z * vb.z);
+      const float UR = -UL + 2.0f * uw;
+      const float PR = imaginary_pressure(p_i, rho_i, P, n, abar[a], I);
+      const float rhoR = I.rho0 + PR * I.inv_c0sq;
+      const float Us = 0.5f * (UL + UR) + (p_i - PR) / ((rho_i + rhoR) * I.c0);   // (P_L - P_R)/(2 rho_bar c0)
+      csum_add(s, e, 2.0f * rho_i * i2f(qa.w) * (Us - UL) * P.dW);
+    }
+    const float drho = csum_warp(s, e);
+    if (lane == 0) {
+      const float hdt = 0.5f * (float)dtd;
+      qi.w = f2i(i2f(qi.w) + hdt * drho);
+      vi.w += drho;
+      PS[i] = qi;
+      VS[i] = vi;
+    }
   }
-  const float drho = s - c;
-  const float hdt = 0.5f * (float)dtd;
-  qi.w = f2i(i2f(qi.w) + hdt * drho);
-  vi.w += drho;
-  PS[i] = qi;
-  VS[i] = vi;
 }
 
 // ---------------------------------------------------------------- solid steps ----------
@@ -406,214 +472,462 @@ struct SolidPtrs {
   int4* X;
   float4* V;
   const uint8_t* fixed;
-  float *F, *dFdt, *PB;   // F: the displacement gradient H = F - I
+  const float* vol;      // reference volumes
+  float *F, *dFdt;       // F: the displacement gradient H = F - I
   const float* B0;
-  const int* nb;
+  const int* nb;         // neighbour slots, packed (block << 16) | tile slot
   const int* cnt;
-  const float4* gW;
+  const float4* gV;      // V_b grad0_a W_ab per slot
+  const float4* cA;      // sum_b V_b grad0_a W_ab per particle
   const float4* force;
-  float4 *acc, *vbar, *abar, *vsum, *asum;
+  float4 *acc, *vbar, *abar;
   long long* steps;      // solid steps taken, total
   int* kappa_last;
   double* dt_cap;        // the fluid's cap (single time stepping), or NULL
+  Global* g;             // the handle's error word
+  int lanes;             // lanes per particle in the neighbour sums: 1, 2, 4, 8, 16 or 32
+  int per_block;         // particles owned by each block of the cluster (the last may own fewer)
+  int row;               // slots a particle in the staged rows (the longest reference row)
 };
 
-// All kappa solid steps of one fluid acoustic step, one block, __syncthreads between the
-// three phases of each step.
+// Shared-memory image of the particles one block owns during the solid steps: what the
+// neighbours read (P B0 as D rows of a float4 each -- one float4 in 2D --, and v) and the
+// owner's own state. Bytes per particle: 80 + 16 R + 8 D^2, R = 1 (2D) or 3 (3D).
+__host__ __device__ constexpr int pb_rows(int d) { return d == 2 ? 1 : 3; }
 template <int D>
-__global__ void __launch_bounds__(kSolidThreads)
-k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ctrl) {
-  const double dtF = ctrl[0].dt;
-  if (dtF == 0.0) return;
-  constexpr int d = D;
-  const int64_t ns = S.ns;
-  // Eq. dts-advection from the solid's state at the start of the fluid step (R25)
-  __shared__ float red_v[kSolidThreads / 32], red_a[kSolidThreads / 32];
-  __shared__ int s_kappa;
-  float vm = 0.f, am = 0.f;
-  for (int64_t a = threadIdx.x; a < ns; a += blockDim.x) {
-    const float4 v = S.V[a], ac = S.acc[a];
-    vm = fmaxf(vm, v.x * v.x + v.y * v.y + v.z * v.z);
-    am = fmaxf(am, ac.x * ac.x + ac.y * ac.y + ac.z * ac.z);
-    S.vsum[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-    S.asum[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+struct SolidTile {
+  float4* V;             // published: velocity
+  float4* PB;            // published: P B0, rows [l * R + r]
+  int4* X;               // position (fixed point) and volume bits
+  float4 *acc, *vsum, *asum;
+  float *F, *dF;         // H = F - I and dF/dt, element-major [k * P + l]
+  __device__ SolidTile(void* base, int P) {
+    float4* f4 = reinterpret_cast<float4*>(base);
+    V = f4;
+    PB = f4 + P;
+    X = reinterpret_cast<int4*>(PB + pb_rows(D) * P);
+    acc = reinterpret_cast<float4*>(X + P);
+    vsum = acc + P;
+    asum = vsum + P;
+    F = reinterpret_cast<float*>(asum + P);
+    dF = F + D * D * P;
   }
+};
+__host__ __device__ constexpr int solid_tile_bytes(int d, int P) {
+  return (P * (80 + 16 * pb_rows(d) + 8 * d * d) + 15) / 16 * 16;   // what follows stays 16-byte aligned
+}
+
+// P B0 of tile slot l as a d x d matrix (2D: one float4 holds the four entries)
+template <int D>
+__device__ __forceinline__ void load_pb(const float4* PB, int l, float m[D * D]) {
+  if (D == 2) {
+    const float4 r = PB[l];
+    m[0] = r.x; m[1] = r.y; m[2] = r.z; m[3] = r.w;
+  } else {
+    for (int i = 0; i < D; ++i) {
+      const float4 r = PB[l * 3 + i];
+      m[i * D] = r.x;
+      m[i * D + 1] = r.y;
+      m[i * D + 2] = r.z;
+    }
+  }
+}
+template <int D>
+__device__ __forceinline__ void store_pb(float4* PB, int l, const float m[D * D]) {
+  if (D == 2) PB[l] = make_float4(m[0], m[1], m[2], m[3]);
+  else
+    for (int i = 0; i < D; ++i) PB[l * 3 + i] = make_float4(m[i * D], m[i * D + 1], m[i * D + 2], 0.f);
+}
+
+// Largest |v|^2 and |dv/dt|^2 over the solid, the same in every thread of the cluster:
+// per block through shared memory, then each block reads the others' through distributed
+// shared memory. Ends with a cluster barrier, so the per-block slots can be reused.
+__device__ __forceinline__ void cluster_vmax(cg::cluster_group& cl, float& vm, float& am, float (*red)[kSolidThreads / 32],
+                                             float* blk) {
   for (int o = 16; o > 0; o >>= 1) {
     vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
     am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    red_v[threadIdx.x >> 5] = vm;
-    red_a[threadIdx.x >> 5] = am;
+    red[0][threadIdx.x >> 5] = vm;
+    red[1][threadIdx.x >> 5] = am;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      vm = fmaxf(vm, red_v[w]);
-      am = fmaxf(am, red_a[w]);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      vm = fmaxf(vm, red[0][w]);
+      am = fmaxf(am, red[1][w]);
     }
-    double dts = M.h / (M.c + sqrt((double)vm));
-    if (am > 0.f) dts = fmin(dts, sqrt(M.h / sqrt((double)am)));
-    dts *= 0.6;
-    s_kappa = (int)floor(dtF / dts) + 1;
-    *S.kappa_last = s_kappa;
-    *S.steps += s_kappa;
+    blk[0] = vm;
+    blk[1] = am;
+  }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    for (unsigned r = 0; r < cl.num_blocks(); ++r) {
+      const float* o = cl.map_shared_rank(blk, r);
+      vm = fmaxf(vm, o[0]);
+      am = fmaxf(am, o[1]);
+    }
+    red[0][0] = vm;
+    red[1][0] = am;
+  }
+  cl.sync();                               // every block has read every other block's slots
+  vm = red[0][0];
+  am = red[1][0];
+}
+
+__device__ __forceinline__ bool gt_is_first() { return threadIdx.x == 0 && blockIdx.x == 0; }
+
+// Eq. dts-advection from the largest |v|^2 and |dv/dt|^2 (CFL 0.6).
+__device__ __forceinline__ double solid_dt(const SolidMat& M, float vm, float am) {
+  double dts = M.h / (M.c + sqrt((double)vm));
+  if (am > 0.f) dts = fmin(dts, sqrt(M.h / sqrt((double)am)));
+  return 0.6 * dts;
+}
+
+// The constant data of the solid steps: per-slot neighbour rows (packed owner slots, V_b
+// grad0 W) and per-particle counts, c_a, fluid force, volume, B0 and clamp flags. Read from
+// global memory (particle a, slot t at [t ns + a]), or with CS staged once per launch into
+// the block's shared memory after the tile (tile slot l, slot t at [l row + t]): the cluster
+// barrier's acquire drops L1, so global reads would go to L2 on every phase.
+template <int D, bool CS>
+struct SolidConst {
+  const int* nb;
+  const float4* gV;
+  const int* cnt;
+  const float4 *cA, *force;
+  const float* vol;
+  const float* B0;
+  const uint8_t* fixed;
+  int64_t ss, ps, bs;    // slot stride, particle stride of the rows, element stride of B0
+  __device__ int slot(int64_t p, int t) const { return CS ? nb[t * ss + p * ps] : __ldg(nb + t * ss + p * ps); }
+  __device__ float4 grad(int64_t p, int t) const { return CS ? gV[t * ss + p * ps] : __ldg(gV + t * ss + p * ps); }
+  __device__ int count(int64_t p) const { return CS ? cnt[p] : __ldg(cnt + p); }
+  __device__ float4 csum(int64_t p) const { return CS ? cA[p] : __ldg(cA + p); }
+  __device__ float4 f(int64_t p) const { return CS ? force[p] : __ldg(force + p); }
+  __device__ float v(int64_t p) const { return CS ? vol[p] : __ldg(vol + p); }
+  __device__ float b0(int64_t p, int k) const { return CS ? B0[k * bs + p] : __ldg(B0 + k * bs + p); }
+  __device__ bool clamped(int64_t p) const { return (CS ? fixed[p] : __ldg(fixed + p)) != 0; }
+};
+
+// Shared-memory bytes per particle of the staged constants (row slots a particle): the rows
+// (16 + 4 bytes a slot), c_a and the fluid force (16 each), count and volume (4 each), B0
+// (4 d^2) and the clamp flag (1)
+__host__ __device__ constexpr int solid_const_bytes(int d, int row) { return row * 20 + 40 + 4 * d * d + 1; }
+
+// First half of a solid step for the owned particle at tile slot l, whose F (the H = F - I
+// of the end of the last step) and dF/dt the caller holds: F += dt/2 dF/dt, r += dt/2 v,
+// and P B0 published for the neighbours' stress divergence.
+template <int D, bool CS>
+__device__ __forceinline__ void solid_first_half(const Inst& I, const SolidMat& M, const SolidConst<D, CS>& C,
+                                                 int64_t p, const SolidTile<D>& T, int P, int l, float F[D * D],
+                                                 const float dF[D * D], float hh) {
+  constexpr int d = D;
+  for (int k = 0; k < d * d; ++k) {
+    F[k] += hh * dF[k];
+    T.F[k * P + l] = F[k];
+  }
+  if (!C.clamped(p)) {
+    const float4 v = T.V[l];
+    int4 q = T.X[l];
+    q.x += __float2int_rn(hh * v.x * I.inv_dq);
+    q.y += __float2int_rn(hh * v.y * I.inv_dq);
+    if (d == 3) q.z += __float2int_rn(hh * v.z * I.inv_dq);
+    T.X[l] = q;
+  }
+  float Pk[D * D], B[D * D], PB[D * D];
+  first_piola<D>(M, F, Pk);
+#pragma unroll
+  for (int k = 0; k < d * d; ++k) B[k] = C.b0(p, k);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      float s = 0.f;
+      for (int k = 0; k < d; ++k) s += Pk[i * d + k] * B[k * d + j];
+      PB[i * d + j] = s;
+    }
+  store_pb<D>(T.PB, l, PB);
+}
+
+// All kappa solid steps of one fluid acoustic step in one thread-block cluster (up to 16
+// blocks of 1024 threads), the solid held in the cluster's distributed shared memory: block
+// r owns the particles [r P, (r + 1) P) (internal order: a Morton curve of the reference
+// positions) and keeps their state, and with CS the constant rows too, in its shared
+// memory for the whole launch; global memory is read at the start and written at the end.
+// A neighbour's P B0 and v are read from its owner's shared memory. Each owned particle
+// belongs to a group of `lanes` adjacent lanes: its first lane updates the particle's
+// state, the others take strided shares of its reference neighbours, combined by a shuffle
+// tree (error-free sums for the stress divergence). Two phases a step, each ended by a
+// cluster barrier:
+//   A. dv/dt from the neighbours' P B0, then v and the second half of r;
+//   B. dF/dt = (sum_b V_b (v_b - v_a) (x) grad0 W) B0 from the neighbours' new v, F to the
+//      end of the step, and straight on the next step's first half (F, r, P B0).
+// kappa is computed identically in every block. A step that is not positive and finite, or
+// more than kMaxSolidSteps solid steps in one fluid step, sets ERR_DT and takes no step.
+template <int D, bool CS>
+__global__ void __launch_bounds__(kSolidThreads, 1)
+k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ctrl) {
+  cg::cluster_group cl = cg::this_cluster();
+  const double dtF = ctrl[0].dt;           // the same in every block
+  if (dtF == 0.0) return;
+  if (S.lanes < 1 || S.lanes > 32 || (S.lanes & (S.lanes - 1)) != 0 || S.per_block < 1 ||
+      (int64_t)S.per_block * cl.num_blocks() < S.ns || (CS && S.row < 1)) {   // the host sizes these
+    if (gt_is_first() && S.g) atomicOr(&S.g->err, ERR_BOUNDS);
+    return;
+  }
+  constexpr int d = D;
+  extern __shared__ float4 tile_mem[];
+  const int P = S.per_block;
+  const unsigned rank = cl.block_rank();
+  const SolidTile<D> T(tile_mem, P);
+  const int64_t first = (int64_t)rank * P;
+  const int own = (int)max((int64_t)0, min((int64_t)P, S.ns - first));   // particles this block owns
+  const int L = S.lanes;                   // divides 32: a group never spans two warps
+  const int lane = (int)(threadIdx.x & (unsigned)(L - 1));
+  const int gpb = (int)blockDim.x / L, grp = (int)threadIdx.x / L;
+  __shared__ float red[2][kSolidThreads / 32];
+  __shared__ float blk[2];
+  __shared__ int s_kappa;
+
+  // the constants: global, or staged after the tile
+  SolidConst<D, CS> C;
+  if (CS) {
+    const int row = S.row;
+    char* base = reinterpret_cast<char*>(tile_mem) + solid_tile_bytes(d, P);
+    float4* gVs = reinterpret_cast<float4*>(base);
+    float4* cAs = gVs + (int64_t)P * row;
+    float4* fs = cAs + P;
+    int* nbs = reinterpret_cast<int*>(fs + P);
+    int* cnts = nbs + (int64_t)P * row;
+    float* vols = reinterpret_cast<float*>(cnts + P);
+    float* B0s = vols + P;
+    uint8_t* fxs = reinterpret_cast<uint8_t*>(B0s + d * d * P);
+    for (int l = threadIdx.x; l < own; l += blockDim.x) {
+      const int64_t a = first + l;
+      cnts[l] = min(S.cnt[a], row);
+      cAs[l] = S.cA[a];
+      fs[l] = S.force[a];
+      vols[l] = S.vol[a];
+      fxs[l] = S.fixed[a];
+      for (int k = 0; k < d * d; ++k) B0s[k * P + l] = S.B0[(int64_t)k * S.ns + a];
+    }
+    for (int64_t idx = threadIdx.x; idx < (int64_t)own * row; idx += blockDim.x) {
+      const int t = (int)(idx / own), l = (int)(idx - (int64_t)t * own);
+      const int64_t a = first + l;
+      if (t < S.cnt[a]) {
+        nbs[(int64_t)l * row + t] = S.nb[(int64_t)t * S.ns + a];
+        gVs[(int64_t)l * row + t] = S.gV[(int64_t)t * S.ns + a];
+      }
+    }
+    C = SolidConst<D, CS>{nbs, gVs, cnts, cAs, fs, vols, B0s, fxs, 1, row, P};
+  } else {
+    C = SolidConst<D, CS>{S.nb, S.gV, S.cnt, S.cA, S.force, S.vol, S.B0, S.fixed, S.ns, 1, S.ns};
+  }
+  // index of particle (tile slot l) in the constants
+  auto cp = [&](int l) -> int64_t { return CS ? (int64_t)l : first + l; };
+
+  // the owned particles into shared memory; Eq. dts-advection from the state at the start
+  // of the fluid step (R25)
+  float vm = 0.f, am = 0.f;
+  for (int l = threadIdx.x; l < own; l += blockDim.x) {
+    const int64_t a = first + l;
+    const float4 v = S.V[a], ac = S.acc[a];
+    T.V[l] = v;
+    T.X[l] = S.X[a];
+    T.acc[l] = ac;
+    T.vsum[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+    T.asum[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < d * d; ++k) {
+      T.F[k * P + l] = S.F[(int64_t)k * S.ns + a];
+      T.dF[k * P + l] = S.dFdt[(int64_t)k * S.ns + a];
+    }
+    vm = fmaxf(vm, v.x * v.x + v.y * v.y + v.z * v.z);
+    am = fmaxf(am, ac.x * ac.x + ac.y * ac.y + ac.z * ac.z);
+  }
+  cluster_vmax(cl, vm, am, red, blk);      // also orders the staging above for the whole block
+  if (threadIdx.x == 0) {
+    const double dts = solid_dt(M, vm, am);
+    const double r = dtF / dts;
+    int kappa = 0;
+    if (dts > 0.0 && r < (double)kMaxSolidSteps) kappa = (int)floor(r) + 1;
+    else if (rank == 0 && S.g) atomicOr(&S.g->err, ERR_DT);
+    s_kappa = kappa;
+    if (rank == 0) {
+      *S.kappa_last = kappa;
+      *S.steps += kappa;
+    }
   }
   __syncthreads();
   const int kappa = s_kappa;
+  if (kappa == 0) return;                  // the same decision in every block; nothing written
   const double hd = dtF / kappa;
   const float h = (float)hd, hh = 0.5f * h;
-  for (int step = 0; step < kappa; ++step) {
-    // phase 1: F to the mid point, r half a step, P B0
-    for (int64_t a = threadIdx.x; a < ns; a += blockDim.x) {
-      float F[D * D], dF[D * D], B[D * D], P[D * D], PB[D * D];
-      load_mat<D>(S.F, ns, a, F);
-      load_mat<D>(S.dFdt, ns, a, dF);
-      for (int k = 0; k < d * d; ++k) F[k] += hh * dF[k];
-      store_mat<D>(S.F, ns, a, F);
-      if (!S.fixed[a]) {
-        const float4 v = S.V[a];
-        int4 q = S.X[a];
-        q.x += __float2int_rn(hh * v.x * I.inv_dq);
-        q.y += __float2int_rn(hh * v.y * I.inv_dq);
-        if (d == 3) q.z += __float2int_rn(hh * v.z * I.inv_dq);
-        S.X[a] = q;
-      }
-      first_piola<D>(M, F, P);
-      load_mat<D>(S.B0, ns, a, B);
-      for (int i = 0; i < d; ++i)
-        for (int j = 0; j < d; ++j) {
-          float s = 0.f;
-          for (int k = 0; k < d; ++k) s += P[i * d + k] * B[k * d + j];
-          PB[i * d + j] = s;
-        }
-      store_mat<D>(S.PB, ns, a, PB);
+  for (int l = threadIdx.x; l < own; l += blockDim.x) {
+    float F[D * D], dF[D * D];
+    for (int k = 0; k < d * d; ++k) {
+      F[k] = T.F[k * P + l];
+      dF[k] = T.dF[k * P + l];
     }
-    __syncthreads();
-    // phase 2: dv/dt, v, r the second half
-    for (int64_t a = threadIdx.x; a < ns; a += blockDim.x) {
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!S.fixed[a]) {
-        const float Va = i2f(S.X[a].w);
-        const float ma = M.rho0 * Va;
-        float PBa[D * D];
-        load_mat<D>(S.PB, ns, a, PBa);
-        float s[3] = {0, 0, 0}, c[3] = {0, 0, 0};
-        const int nc = S.cnt[a];
-        for (int t = 0; t < nc; ++t) {
-          const int b = S.nb[(int64_t)t * ns + a];
-          const float4 g = S.gW[(int64_t)t * ns + a];
+    solid_first_half<D, CS>(I, M, C, cp(l), T, P, l, F, dF, hh);
+  }
+  cl.sync();
+  for (int step = 0; step < kappa; ++step) {
+    // A: dv/dt, v, r the second half (passes uniform over the block for the shuffles). With
+    // gV_ab = V_b grad0 W and c_a = sum_b gV_ab, Eq. sph-mechanical-mom's sum
+    // (2 / m_a) sum_b V_a V_b (P_a B0_a + P_b B0_b)/2 grad0 W = (P_a B0_a c_a + sum_b P_b B0_b gV_ab) / rho0.
+    for (int base = 0; base < own; base += gpb) {
+      const int l = base + grp;
+      const bool live = l < own;
+      const int64_t p = cp(l);
+      const bool moves = live && !C.clamped(p);
+      float sx[3] = {0.f, 0.f, 0.f}, ex[3] = {0.f, 0.f, 0.f};
+      if (moves) {
+        const int nc = C.count(p);
+#pragma unroll 2
+        for (int t = lane; t < nc; t += L) {
+          const int pk = C.slot(p, t);
+          const float4 g = C.grad(p, t);
           const float gv[3] = {g.x, g.y, g.z};
-          const float w = Va * i2f(S.X[b].w);
+          float PBb[D * D];
+          load_pb<D>(cl.map_shared_rank(T.PB, (unsigned)(pk >> 16)), pk & 0xffff, PBb);
           for (int i = 0; i < d; ++i) {
-            float x = 0.f;
-            for (int j = 0; j < d; ++j) x += 0.5f * (PBa[i * d + j] + S.PB[(int64_t)(i * d + j) * ns + b]) * gv[j];
-            kahan_add(s[i], c[i], w * x);
+            float x = PBb[i * d] * gv[0];
+            for (int j = 1; j < d; ++j) x = fmaf(PBb[i * d + j], gv[j], x);
+            float e;
+            two_sum(sx[i], x, sx[i], e);
+            ex[i] += e;
           }
         }
-        const float4 f = S.force[a];
-        acc.x = 2.0f * (s[0] - c[0]) / ma + M.g[0] + f.x / ma;
-        acc.y = 2.0f * (s[1] - c[1]) / ma + M.g[1] + f.y / ma;
-        acc.z = d == 3 ? 2.0f * (s[2] - c[2]) / ma + M.g[2] + f.z / ma : 0.f;
-        float4 v = S.V[a];
-        v.x += h * acc.x;
-        v.y += h * acc.y;
-        v.z += h * acc.z;
-        S.V[a] = v;
-        int4 q = S.X[a];
-        q.x += __float2int_rn(hh * v.x * I.inv_dq);
-        q.y += __float2int_rn(hh * v.y * I.inv_dq);
-        if (d == 3) q.z += __float2int_rn(hh * v.z * I.inv_dq);
-        S.X[a] = q;
       }
-      S.acc[a] = acc;
-      const float4 v = S.V[a];
-      float4 vs = S.vsum[a], as = S.asum[a];
-      vs.x += v.x; vs.y += v.y; vs.z += v.z;
-      as.x += acc.x; as.y += acc.y; as.z += acc.z;
-      S.vsum[a] = vs;
-      S.asum[a] = as;
-    }
-    __syncthreads();
-    // phase 3: dF/dt from the new velocities, F the second half
-    for (int64_t a = threadIdx.x; a < ns; a += blockDim.x) {
-      const float4 va = S.V[a];
-      const float vav[3] = {va.x, va.y, va.z};
-      float G[D * D] = {};
-      const int nc = S.cnt[a];
-      for (int t = 0; t < nc; ++t) {
-        const int b = S.nb[(int64_t)t * ns + a];
-        const float4 g = S.gW[(int64_t)t * ns + a];
-        const float gv[3] = {g.x, g.y, g.z};
-        const float4 vb = S.V[b];
-        const float vbv[3] = {vb.x, vb.y, vb.z};
-        const float Vb = i2f(S.X[b].w);
-        for (int i = 0; i < d; ++i)
-          for (int j = 0; j < d; ++j) G[i * d + j] += Vb * (vbv[i] - vav[i]) * gv[j];
-      }
-      float B[D * D], dF[D * D], F[D * D];
-      load_mat<D>(S.B0, ns, a, B);
-      for (int i = 0; i < d; ++i)
-        for (int j = 0; j < d; ++j) {
-          float s = 0.f;
-          for (int k = 0; k < d; ++k) s += G[i * d + k] * B[k * d + j];
-          dF[i * d + j] = s;
+      for (int o = L >> 1; o > 0; o >>= 1)
+        for (int i = 0; i < d; ++i) {
+          const float so = __shfl_xor_sync(0xffffffffu, sx[i], o), eo = __shfl_xor_sync(0xffffffffu, ex[i], o);
+          float e;
+          two_sum(sx[i], so, sx[i], e);
+          ex[i] += eo + e;
         }
-      store_mat<D>(S.dFdt, ns, a, dF);
-      load_mat<D>(S.F, ns, a, F);
-      for (int k = 0; k < d * d; ++k) F[k] += hh * dF[k];
-      store_mat<D>(S.F, ns, a, F);
+      if (live && lane == 0) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 v = T.V[l];
+        if (moves) {
+          float PBa[D * D];
+          load_pb<D>(T.PB, l, PBa);
+          const float4 c4 = C.csum(p);
+          const float cv[3] = {c4.x, c4.y, c4.z};
+          float div[3] = {0.f, 0.f, 0.f};
+          for (int i = 0; i < d; ++i) {
+            float y = ex[i];
+            for (int j = 0; j < d; ++j) y = fmaf(PBa[i * d + j], cv[j], y);
+            div[i] = sx[i] + y;
+          }
+          const float inv_rho0 = 1.0f / M.rho0, inv_m = inv_rho0 / C.v(p);
+          const float4 f = C.f(p);
+          acc.x = div[0] * inv_rho0 + M.g[0] + f.x * inv_m;
+          acc.y = div[1] * inv_rho0 + M.g[1] + f.y * inv_m;
+          acc.z = d == 3 ? div[2] * inv_rho0 + M.g[2] + f.z * inv_m : 0.f;
+          v.x += h * acc.x;
+          v.y += h * acc.y;
+          v.z += h * acc.z;
+          T.V[l] = v;
+          int4 q = T.X[l];
+          q.x += __float2int_rn(hh * v.x * I.inv_dq);
+          q.y += __float2int_rn(hh * v.y * I.inv_dq);
+          if (d == 3) q.z += __float2int_rn(hh * v.z * I.inv_dq);
+          T.X[l] = q;
+        }
+        T.acc[l] = acc;
+        float4 vs = T.vsum[l], as = T.asum[l];
+        vs.x += v.x; vs.y += v.y; vs.z += v.z;
+        as.x += acc.x; as.y += acc.y; as.z += acc.z;
+        T.vsum[l] = vs;
+        T.asum[l] = as;
+      }
     }
-    __syncthreads();
+    cl.sync();                             // v published; every read of P B0 done
+    // B: dF/dt from the new velocities, F the second half, then the next step's first half
+    const bool more = step + 1 < kappa;
+    for (int base = 0; base < own; base += gpb) {
+      const int l = base + grp;
+      const bool live = l < own;
+      const int64_t p = cp(l);
+      float G[D * D] = {};
+      if (live) {
+        const float4 va = T.V[l];
+        const float vav[3] = {va.x, va.y, va.z};
+        const int nc = C.count(p);
+#pragma unroll 2
+        for (int t = lane; t < nc; t += L) {
+          const int pk = C.slot(p, t);
+          const float4 g = C.grad(p, t);
+          const float gv[3] = {g.x, g.y, g.z};
+          const float4 vb = cl.map_shared_rank(T.V, (unsigned)(pk >> 16))[pk & 0xffff];
+          const float dv[3] = {vb.x - vav[0], vb.y - vav[1], vb.z - vav[2]};
+          for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) G[i * d + j] = fmaf(dv[i], gv[j], G[i * d + j]);
+        }
+      }
+      for (int o = L >> 1; o > 0; o >>= 1)
+        for (int k = 0; k < d * d; ++k) G[k] += __shfl_xor_sync(0xffffffffu, G[k], o);
+      if (live && lane == 0) {
+        float B[D * D], dF[D * D], F[D * D];
+#pragma unroll
+        for (int k = 0; k < d * d; ++k) B[k] = C.b0(p, k);
+        for (int i = 0; i < d; ++i)
+          for (int j = 0; j < d; ++j) {
+            float s = 0.f;
+            for (int k = 0; k < d; ++k) s += G[i * d + k] * B[k * d + j];
+            dF[i * d + j] = s;
+          }
+        for (int k = 0; k < d * d; ++k) {
+          T.dF[k * P + l] = dF[k];
+          F[k] = T.F[k * P + l] + hh * dF[k];
+        }
+        if (more) solid_first_half<D, CS>(I, M, C, p, T, P, l, F, dF, hh);
+        else
+          for (int k = 0; k < d * d; ++k) T.F[k * P + l] = F[k];
+      }
+    }
+    cl.sync();                             // P B0 published; every read of v done
   }
+  // the owned particles back to global memory, with the step averages v~ and a~, and (single
+  // time stepping) the next fluid step's cap
   const float inv = 1.0f / (float)kappa;
-  for (int64_t a = threadIdx.x; a < ns; a += blockDim.x) {
-    const float4 vs = S.vsum[a], as = S.asum[a];
+  vm = 0.f;
+  am = 0.f;
+  for (int l = threadIdx.x; l < own; l += blockDim.x) {
+    const int64_t a = first + l;
+    const float4 v = T.V[l], ac = T.acc[l], vs = T.vsum[l], as = T.asum[l];
+    S.V[a] = v;
+    S.X[a] = T.X[l];
+    S.acc[a] = ac;
     S.vbar[a] = make_float4(vs.x * inv, vs.y * inv, vs.z * inv, 0.f);
     S.abar[a] = make_float4(as.x * inv, as.y * inv, as.z * inv, 0.f);
+    for (int k = 0; k < d * d; ++k) {
+      S.F[(int64_t)k * S.ns + a] = T.F[k * P + l];
+      S.dFdt[(int64_t)k * S.ns + a] = T.dF[k * P + l];
+    }
+    vm = fmaxf(vm, v.x * v.x + v.y * v.y + v.z * v.z);
+    am = fmaxf(am, ac.x * ac.x + ac.y * ac.y + ac.z * ac.z);
   }
   if (M.single_step && S.dt_cap) {
     // single time stepping: the next fluid step takes the solid's step from the state it
     // starts from (the same dt_S the next call computes first), a hair below it so kappa = 1
-    __syncthreads();
-    vm = 0.f;
-    am = 0.f;
-    for (int64_t a = threadIdx.x; a < ns; a += blockDim.x) {
-      const float4 v = S.V[a], ac = S.acc[a];
-      vm = fmaxf(vm, v.x * v.x + v.y * v.y + v.z * v.z);
-      am = fmaxf(am, ac.x * ac.x + ac.y * ac.y + ac.z * ac.z);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
-      am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red_v[threadIdx.x >> 5] = vm;
-      red_a[threadIdx.x >> 5] = am;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        vm = fmaxf(vm, red_v[w]);
-        am = fmaxf(am, red_a[w]);
-      }
-      double dts = M.h / (M.c + sqrt((double)vm));
-      if (am > 0.f) dts = fmin(dts, sqrt(M.h / sqrt((double)am)));
-      S.dt_cap[0] = 0.6 * dts * (1.0 - 1e-9);
-    }
+    cluster_vmax(cl, vm, am, red, blk);
+    if (threadIdx.x == 0 && rank == 0) S.dt_cap[0] = solid_dt(M, vm, am) * (1.0 - 1e-9);
   }
 }
 
-__global__ void k_solid_export(int64_t ns, int d, const int4* __restrict__ X, const float4* __restrict__ V,
-                               const float4* __restrict__ force, const float* __restrict__ F, double lo0,
-                               double lo1, double lo2, double dq, double* pos, double* vel, double* frc,
-                               double* Fout) {
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= ns) return;
-  const int4 q = X[a];
+// The solid's state in the caller's order (perm: internal index -> caller's), FP64.
+__global__ void k_solid_export(int64_t ns, int d, const int* __restrict__ perm, const int4* __restrict__ X,
+                               const float4* __restrict__ V, const float4* __restrict__ force,
+                               const float* __restrict__ F, double lo0, double lo1, double lo2, double dq,
+                               double* pos, double* vel, double* frc, double* Fout) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns) return;
+  const int64_t a = perm[i];               // the caller's index of internal particle i
+  const int4 q = X[i];
   const int qv[3] = {q.x, q.y, q.z};
   const double lo[3] = {lo0, lo1, lo2};
-  const float4 v = V[a], f = force[a];
+  const float4 v = V[i], f = force[i];
   const float vv[3] = {v.x, v.y, v.z}, ff[3] = {f.x, f.y, f.z};
   for (int k = 0; k < d; ++k) {
     if (pos) pos[a * d + k] = lo[k] + (double)qv[k] * dq;
@@ -621,7 +935,7 @@ __global__ void k_solid_export(int64_t ns, int d, const int4* __restrict__ X, co
     if (frc) frc[a * d + k] = ff[k];
   }
   if (Fout)                                // F = I + H
-    for (int k = 0; k < d * d; ++k) Fout[a * d * d + k] = (double)F[(int64_t)k * ns + a] + (k % (d + 1) == 0 ? 1.0 : 0.0);
+    for (int k = 0; k < d * d; ++k) Fout[a * d * d + k] = (double)F[(int64_t)k * ns + i] + (k % (d + 1) == 0 ? 1.0 : 0.0);
 }
 
 }  // namespace
@@ -633,16 +947,21 @@ struct sph_solid {
   std::string err;
   int64_t ns = 0;
   int dim = 2, cap = 0;
+  int cluster = 1, lanes = 1, per_block = 1, tile_bytes = 0, row = 1;   // shape of the solid-step launch
+  bool staged = false;          // constant rows staged in shared memory
   sph::SolidMat mat{};
   std::vector<void*> allocs;
   int4* X = nullptr;
   float4 *V = nullptr, *N = nullptr, *force = nullptr, *acc = nullptr, *vbar = nullptr, *abar = nullptr;
-  float4 *vsum = nullptr, *asum = nullptr, *gW = nullptr;
+  float4 *gV = nullptr, *cA = nullptr;
   uint8_t* fixed = nullptr;
-  float *F = nullptr, *dFdt = nullptr, *PB = nullptr, *B0 = nullptr;   // F holds H = F - I
+  float *F = nullptr, *dFdt = nullptr, *B0 = nullptr;   // F holds H = F - I
+  float* vol = nullptr;         // reference volumes
   int *nb = nullptr, *cnt = nullptr, *near = nullptr, *box = nullptr, *dev_err = nullptr, *kappa_last = nullptr;
   int* n_near = nullptr;        // length of the near-fluid list (device)
   long long* steps = nullptr;
+  int* perm = nullptr;          // internal index -> the caller's (device)
+  std::vector<int> perm_host;
   uint32_t *flag = nullptr, *off = nullptr, *scan_tmp = nullptr;
 };
 
@@ -666,28 +985,114 @@ bool salloc(sph_solid* s, T** p, size_t count) {
 }
 
 sph::SolidPtrs ptrs(sph_solid* s) {
-  sph::SolidPtrs P;
+  sph::SolidPtrs P{};
   P.ns = s->ns;
   P.X = s->X;
   P.V = s->V;
   P.fixed = s->fixed;
+  P.vol = s->vol;
   P.F = s->F;
   P.dFdt = s->dFdt;
-  P.PB = s->PB;
   P.B0 = s->B0;
   P.nb = s->nb;
   P.cnt = s->cnt;
-  P.gW = s->gW;
+  P.gV = s->gV;
+  P.cA = s->cA;
   P.force = s->force;
   P.acc = s->acc;
   P.vbar = s->vbar;
   P.abar = s->abar;
-  P.vsum = s->vsum;
-  P.asum = s->asum;
   P.steps = s->steps;
   P.kappa_last = s->kappa_last;
   P.dt_cap = s->h ? s->h->b.dt_cap : nullptr;
+  P.g = s->h ? s->h->b.glob : nullptr;
+  P.lanes = s->lanes;
+  P.per_block = s->per_block;
+  P.row = s->row;
   return P;
+}
+
+const void* solid_kernel(int dim, bool staged) {
+  if (dim == 2) return staged ? (const void*)sph::k_solid_steps<2, true> : (const void*)sph::k_solid_steps<2, false>;
+  return staged ? (const void*)sph::k_solid_steps<3, true> : (const void*)sph::k_solid_steps<3, false>;
+}
+
+// Shape of the solid-step launch: `lanes` per particle from the longest reference row (about
+// six neighbours a lane); a cluster of c blocks, each holding ceil(ns / c) particles in its
+// shared memory, with the constant rows too where they fit. c aims at eight or more busy
+// warps a block, and stays within what the device schedules (16 blocks where non-portable
+// cluster sizes are allowed) and within each block's shared memory. Returns false when no
+// cluster holds the solid.
+bool choose_cluster(sph_solid* s, int max_row) {
+  int L = 1;
+  while (L < 32 && L * 6 < max_row) L <<= 1;
+  s->lanes = L;
+  s->row = std::max(max_row, 1);
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int budget = optin - 1024;         // the kernel's static shared memory and a margin
+  for (int cs = 1; cs >= 0; --cs) {        // constants staged in shared memory where they fit
+    const void* kern = solid_kernel(s->dim, cs != 0);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, budget) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    auto bytes_for = [&](int P) {
+      return (int64_t)sph::solid_tile_bytes(s->dim, P) + (cs ? (int64_t)P * sph::solid_const_bytes(s->dim, s->row) : 0);
+    };
+    const int64_t per = bytes_for(1) + 16;
+    const int64_t c_mem = (s->ns + budget / per - 1) / std::max<int64_t>(budget / per, 1);
+    const int64_t c_busy = (s->ns * L + 255) / 256;
+    const int c0 = (int)std::max<int64_t>(c_mem, std::min<int64_t>(16, c_busy));
+    std::vector<int> order;
+    for (int c = c0; c >= (int)std::max<int64_t>(c_mem, 1); --c) order.push_back(c);
+    for (int c = c0 + 1; c <= 16; ++c) order.push_back(c);
+    for (int c : order) {
+      const int P = (int)((s->ns + c - 1) / c);
+      const int64_t bytes = bytes_for(P);
+      if (bytes > budget) continue;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      cfg.gridDim = dim3((unsigned)c);
+      cfg.blockDim = dim3(sph::kSolidThreads);
+      cfg.dynamicSmemBytes = (size_t)bytes;
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)c;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int active = 0;
+      if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0) {
+        s->cluster = c;
+        s->per_block = P;
+        s->tile_bytes = (int)bytes;
+        s->staged = cs != 0;
+        return true;
+      }
+      cudaGetLastError();
+    }
+  }
+  return false;
+}
+
+void cluster_config(const sph_solid* s, cudaStream_t st, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at) {
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3((unsigned)s->cluster);
+  cfg->blockDim = dim3(sph::kSolidThreads);
+  cfg->dynamicSmemBytes = (size_t)s->tile_bytes;
+  cfg->stream = st;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)s->cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg->attrs = at;
+  cfg->numAttrs = 1;
 }
 
 }  // namespace
@@ -714,12 +1119,12 @@ void sph_fsi_after_pressure(sph_handle* h, cudaStream_t st, int64_t* launches) {
   sph_solid* s = h->solid;
   if (!s || s->ns == 0 || h->b.n == 0) return;
   sph::Buffers& b = h->b;
-  // launched over every fluid slot: threads past the near list's length (on the device) exit
+  // a warp per near fluid particle (the list's length is on the device), a warp per solid particle
   auto fp = b.dim == 2 ? sph::k_fsi_fluid_pressure<2> : sph::k_fsi_fluid_pressure<3>;
-  fp<<<sph::fgrid(b.n), sph::kFBlock, 0, st>>>(b.inst0, s->n_near, s->near, b.PH, b.VH, b.VS, b.mass, b.ctrl, s->ns,
+  fp<<<sph::wgrid(b.n), sph::kFBlock, 0, st>>>(b.inst0, s->n_near, s->near, b.PH, b.VH, b.VS, b.mass, b.ctrl, s->ns,
                                                s->X, s->N, s->vbar, s->abar, b.acc_keep);
   auto sf = b.dim == 2 ? sph::k_fsi_solid_force<2> : sph::k_fsi_solid_force<3>;
-  sf<<<sph::fgrid(s->ns), sph::kFBlock, 0, st>>>(b.inst0, s->n_near, s->near, b.PH, b.VS, b.mass, b.ctrl, s->ns, s->X,
+  sf<<<sph::wgrid(s->ns), sph::kFBlock, 0, st>>>(b.inst0, s->n_near, s->near, b.PH, b.VS, b.mass, b.ctrl, s->ns, s->X,
                                                  s->N, s->vbar, s->abar, s->force);
   sph::Buffers vb = b;                     // |v|max over the corrected new velocities
   vb.VS = b.VH;
@@ -733,12 +1138,16 @@ void sph_fsi_after_density(sph_handle* h, cudaStream_t st, int64_t* launches) {
   sph::Buffers& b = h->b;
   if (b.n > 0) {
     auto fc = b.dim == 2 ? sph::k_fsi_fluid_continuity<2> : sph::k_fsi_fluid_continuity<3>;
-    fc<<<sph::fgrid(b.n), sph::kFBlock, 0, st>>>(b.inst0, s->n_near, s->near, b.PS, b.VS, b.PH, b.ctrl, s->ns, s->X,
+    fc<<<sph::wgrid(b.n), sph::kFBlock, 0, st>>>(b.inst0, s->n_near, s->near, b.PS, b.VS, b.PH, b.ctrl, s->ns, s->X,
                                                  s->N, s->vbar, s->abar);
     *launches += 1;
   }
-  auto ks = b.dim == 2 ? sph::k_solid_steps<2> : sph::k_solid_steps<3>;
-  ks<<<1, sph::kSolidThreads, 0, st>>>(b.inst0, s->mat, ptrs(s), b.ctrl);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  cluster_config(s, st, &cfg, at);
+  auto ks = b.dim == 2 ? (s->staged ? sph::k_solid_steps<2, true> : sph::k_solid_steps<2, false>)
+                       : (s->staged ? sph::k_solid_steps<3, true> : sph::k_solid_steps<3, false>);
+  cudaLaunchKernelEx(&cfg, ks, b.inst0, s->mat, ptrs(s), (const sph::Ctrl*)b.ctrl);
   *launches += 1;
 }
 
@@ -773,6 +1182,45 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
     cudaGetLastError();
     return sfail(s, SPH_E_CUDA, "copy of the solid's arrays failed");
   }
+  // Internal order: the particles sorted along a Morton curve of their reference positions
+  // (cells of the lattice spacing), so that each block of the solid-step cluster owns a
+  // compact patch and most reference neighbours share its shared memory. perm maps an
+  // internal index to the caller's.
+  {
+    const double dps = std::pow(hv[0], 1.0 / d);
+    if (!(dps > 0.0) || !std::isfinite(dps)) return sfail(s, SPH_E_INVALID, "solid volumes must be positive");
+    double lo[3] = {1e300, 1e300, 1e300};
+    for (int64_t a = 0; a < n; ++a)
+      for (int k = 0; k < d; ++k) lo[k] = std::min(lo[k], hp[a * d + k]);
+    std::vector<uint64_t> key((size_t)n);
+    for (int64_t a = 0; a < n; ++a) {
+      uint64_t m = 0;
+      for (int k = 0; k < d; ++k) {
+        const double c = std::floor((hp[a * d + k] - lo[k]) / dps);
+        const uint64_t ci = (uint64_t)std::min(65535.0, std::max(0.0, c));
+        for (int bit = 0; bit < 16; ++bit) m |= ((ci >> bit) & 1u) << (bit * d + k);
+      }
+      key[(size_t)a] = m;
+    }
+    s->perm_host.resize((size_t)n);
+    for (int64_t a = 0; a < n; ++a) s->perm_host[(size_t)a] = (int)a;
+    std::stable_sort(s->perm_host.begin(), s->perm_host.end(), [&](int x, int y) { return key[x] < key[y]; });
+    std::vector<double> p2((size_t)n * d), v2((size_t)n), n2((size_t)n * d);
+    std::vector<int32_t> f2((size_t)n);
+    for (int64_t k2 = 0; k2 < n; ++k2) {
+      const int64_t a = s->perm_host[(size_t)k2];
+      for (int k = 0; k < d; ++k) {
+        p2[k2 * d + k] = hp[a * d + k];
+        n2[k2 * d + k] = hn[a * d + k];
+      }
+      v2[k2] = hv[a];
+      f2[k2] = hf[a];
+    }
+    hp.swap(p2);
+    hv.swap(v2);
+    hn.swap(n2);
+    hf.swap(f2);
+  }
   const double nu = p->poisson, E = p->youngs;
   s->mat.model = p->model;
   s->mat.dim = d;
@@ -792,6 +1240,7 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
   std::vector<int4> hX((size_t)n);
   std::vector<float4> hN((size_t)n);
   std::vector<uint8_t> hfx((size_t)n);
+  std::vector<float> hvol((size_t)n);
   for (int64_t a = 0; a < n; ++a) {
     int q[3] = {0, 0, 0};
     for (int k = 0; k < d; ++k) {
@@ -800,6 +1249,7 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
       q[k] = (int)std::llrint(v);
     }
     float vb = (float)hv[a];
+    hvol[a] = vb;
     int vbits;
     std::memcpy(&vbits, &vb, sizeof(int));
     hX[a] = make_int4(q[0], q[1], q[2], vbits);
@@ -808,13 +1258,13 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
   }
   const size_t dd = (size_t)d * d;
   bool ok = salloc(s, &s->X, n) && salloc(s, &s->V, n) && salloc(s, &s->N, n) && salloc(s, &s->force, n) &&
-            salloc(s, &s->acc, n) && salloc(s, &s->vbar, n) && salloc(s, &s->abar, n) && salloc(s, &s->vsum, n) &&
-            salloc(s, &s->asum, n) && salloc(s, &s->fixed, n) && salloc(s, &s->F, dd * n) &&
-            salloc(s, &s->dFdt, dd * n) && salloc(s, &s->PB, dd * n) && salloc(s, &s->B0, dd * n) &&
-            salloc(s, &s->nb, (size_t)s->cap * n) && salloc(s, &s->cnt, n) && salloc(s, &s->gW, (size_t)s->cap * n) &&
+            salloc(s, &s->acc, n) && salloc(s, &s->vbar, n) && salloc(s, &s->abar, n) &&
+            salloc(s, &s->fixed, n) && salloc(s, &s->vol, n) && salloc(s, &s->F, dd * n) &&
+            salloc(s, &s->dFdt, dd * n) && salloc(s, &s->B0, dd * n) &&
+            salloc(s, &s->nb, (size_t)s->cap * n) && salloc(s, &s->cnt, n) && salloc(s, &s->gV, (size_t)s->cap * n) && salloc(s, &s->cA, n) &&
             salloc(s, &s->box, 6) && salloc(s, &s->dev_err, 1) && salloc(s, &s->kappa_last, 1) &&
             salloc(s, &s->n_near, 1) &&
-            salloc(s, &s->steps, 1) && salloc(s, &s->near, std::max<int64_t>(h->b.n, 1)) &&
+            salloc(s, &s->steps, 1) && salloc(s, &s->perm, n) && salloc(s, &s->near, std::max<int64_t>(h->b.n, 1)) &&
             salloc(s, &s->flag, std::max<int64_t>(h->b.n, 1)) && salloc(s, &s->off, std::max<int64_t>(h->b.n, 1) + 1) &&
             salloc(s, &s->scan_tmp, sph::scan_tmp_elems(std::max<int64_t>(h->b.n, 1)));
   if (!ok) return sfail(s, SPH_E_OOM, "device allocation of the solid failed");
@@ -823,6 +1273,8 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
   if (cudaMemcpy(s->X, hX.data(), sizeof(int4) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->N, hN.data(), sizeof(float4) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(s->fixed, hfx.data(), n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->perm, s->perm_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->vol, hvol.data(), sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(s->F, 0, sizeof(float) * dd * n) != cudaSuccess ||          // H = F - I = 0
       cudaMemcpy(dx0, hp.data(), sizeof(double) * n * d, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(dvol, hv.data(), sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -835,7 +1287,7 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
     cudaGetLastError();
     return sfail(s, SPH_E_CUDA, "initialising the solid failed");
   }
-  sph::k_solid_setup<<<sph::fgrid(n), sph::kFBlock>>>(n, d, p->h, dx0, dvol, s->cap, s->nb, s->cnt, s->gW, s->B0,
+  sph::k_solid_setup<<<sph::fgrid(n), sph::kFBlock>>>(n, d, p->h, dx0, dvol, s->cap, s->nb, s->cnt, s->gV, s->cA, s->B0,
                                                       s->dev_err);
   int derr = 0;
   if (cudaMemcpy(&derr, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -844,6 +1296,18 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
   }
   if (derr & 1) return sfail(s, SPH_E_CAPACITY, "a solid particle has more reference neighbours than the capacity");
   if (derr & 2) return sfail(s, SPH_E_INVALID, "a solid particle's correction matrix is singular (too few neighbours)");
+  std::vector<int> hcnt((size_t)n);
+  if (cudaMemcpy(hcnt.data(), s->cnt, sizeof(int) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return sfail(s, SPH_E_CUDA, "solid set-up failed");
+  }
+  if (!choose_cluster(s, *std::max_element(hcnt.begin(), hcnt.end())))
+    return sfail(s, SPH_E_CAPACITY, "the solid does not fit the shared memory of one thread-block cluster");
+  sph::k_solid_pack_rows<<<sph::fgrid(n), sph::kFBlock>>>(n, s->cap, s->cnt, s->per_block, s->nb);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return sfail(s, SPH_E_CUDA, "solid set-up failed");
+  }
   if (p->single_step) {
     double* cap = nullptr;
     if (!salloc(s, &cap, 1) || cudaMemset(cap, 0, sizeof(double)) != cudaSuccess) {
@@ -886,7 +1350,7 @@ int sph_solid_get_state(sph_handle* h, sph_solid* s, double* pos, double* vel, d
   }
   double* t[4] = {tmp, tmp + n * d, tmp + 2 * n * d, tmp + 3 * n * d};
   const sph::Inst& I = h->b.inst0;
-  sph::k_solid_export<<<sph::fgrid(s->ns), sph::kFBlock, 0, st>>>(s->ns, d, s->X, s->V, s->force, s->F, I.lo[0],
+  sph::k_solid_export<<<sph::fgrid(s->ns), sph::kFBlock, 0, st>>>(s->ns, d, s->perm, s->X, s->V, s->force, s->F, I.lo[0],
                                                                   I.lo[1], I.lo[2], I.dq_d, t[0], t[1], t[2], t[3]);
   int rc = SPH_OK;
   for (int k = 0; k < 4; ++k)

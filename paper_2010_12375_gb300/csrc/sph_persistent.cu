@@ -21,42 +21,13 @@
 #include <algorithm>
 
 #include "sph_ctrl.cuh"
+#include "sph_grid_sync.cuh"
 #include "sph_relax.cuh"
 
 namespace sph {
 namespace {
 
 constexpr int kPBlock = 128;
-constexpr unsigned kBarrierSpinLimit = 1u << 24;   // polls of 64 ns sleeps: about a second
-
-__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, Global* g) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned* genp = &bar->gen;
-    const unsigned my = *genp;               // this barrier cannot complete before we arrive
-    __threadfence();                         // release this block's writes
-    if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      unsigned spins = 0;
-      while (*genp == my) {
-        if (++spins > kBarrierSpinLimit) {
-          atomicOr(&g->err, ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();                         // acquire the other blocks' writes
-  }
-  __syncthreads();
-  return ok != 0;
-}
 
 // |v^{n+1}|^2 maximum per tank: one atomic per warp when its particles share a tank.
 __device__ __forceinline__ void warp_vmax(float v2, bool writer, int k, Ctrl* ctrl) {
