@@ -526,9 +526,12 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
 /* Detach from the handle and free; destroy before the handle. */
 void sph_solid_destroy(sph_solid* s);
 const char* sph_solid_last_error(const sph_solid* s);
-/* The solid's state in its particle order (host or device outputs, any may be NULL): pos,
- * vel, force (the fluid's force held over the last solid steps) [n*dim], F [n*dim*dim]
- * row-major; solid_steps (host) the solid steps taken so far. Synchronous. */
+/* Number of particles of the solid (the n it was created with), or -1 for NULL: the
+ * outputs of sph_solid_get_state hold n*dim (and n*dim*dim) values, dim the handle's. */
+int64_t sph_solid_size(const sph_solid* s);
+/* The solid's state in the caller's particle order (host or device outputs, any may be
+ * NULL): pos, vel, force (the fluid's force held over the last solid steps) [n*dim], F
+ * [n*dim*dim] row-major; solid_steps (host) the solid steps taken so far. Synchronous. */
 int sph_solid_get_state(sph_handle* h, sph_solid* s, double* pos, double* vel, double* force, double* F,
                         int64_t* solid_steps, void* stream);
 

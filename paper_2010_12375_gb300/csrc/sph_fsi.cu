@@ -1335,6 +1335,8 @@ void sph_solid_destroy(sph_solid* s) {
 
 const char* sph_solid_last_error(const sph_solid* s) { return s ? s->err.c_str() : "null solid"; }
 
+int64_t sph_solid_size(const sph_solid* s) { return s ? s->ns : -1; }
+
 int sph_solid_get_state(sph_handle* h, sph_solid* s, double* pos, double* vel, double* force, double* F,
                         int64_t* solid_steps, void* stream) {
   if (!h || !s || s->h != h) return SPH_E_INVALID;

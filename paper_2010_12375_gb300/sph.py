@@ -48,7 +48,7 @@ EXPORTS = [
     "sph_species_create", "sph_species_destroy", "sph_species_last_error", "sph_species_set",
     "sph_species_get", "sph_diffusion_step", "sph_species_set_gate", "sph_species_get_gate",
     "sph_reaction_step", "sph_species_set_scale", "sph_clear_error", "sph_debug_write",
-    "sph_gradient_diagnostics", "sph_solid_create", "sph_solid_destroy", "sph_solid_last_error",
+    "sph_gradient_diagnostics", "sph_solid_create", "sph_solid_destroy", "sph_solid_last_error", "sph_solid_size",
     "sph_solid_get_state",
 ]
 
@@ -183,6 +183,7 @@ def load():
         "sph_solid_create": (i32, [P, ctypes.POINTER(SphSolidParams), i64, P, P, P, P, ctypes.POINTER(P)]),
         "sph_solid_destroy": (None, [P]),
         "sph_solid_last_error": (ctypes.c_char_p, [P]),
+        "sph_solid_size": (i64, [P]),
         "sph_solid_get_state": (i32, [P, P, P, P, P, P, ctypes.POINTER(i64), P]),
     }
     for name, (res, args) in sig.items():
@@ -732,9 +733,18 @@ def sph_solid_destroy(s):
     load().sph_solid_destroy(s)
 
 
-def sph_solid_get_state(h, s, n, dim, stream=None):
-    """Returns dict(pos, vel, force (n, dim), F (n, dim, dim), solid_steps)."""
+def sph_solid_size(s) -> int:
+    return int(load().sph_solid_size(s))
+
+
+def sph_solid_get_state(h, s, n=None, dim=None, stream=None):
+    """Returns dict(pos, vel, force (n, dim), F (n, dim, dim), solid_steps). n and dim are the
+    solid's own (its particle count and the handle's dimension); given ones must match."""
     lib = load()
+    n_s, dim_h = sph_solid_size(s), sph_get_info(h).dim
+    if (n is not None and n != n_s) or (dim is not None and dim != dim_h):
+        raise ValueError(f"the solid has {n_s} particles in {dim_h}D, not {n} in {dim}D")
+    n, dim = n_s, dim_h
     out = {"pos": np.empty((n, dim)), "vel": np.empty((n, dim)), "force": np.empty((n, dim)),
            "F": np.empty((n, dim, dim))}
     steps = ctypes.c_int64(0)

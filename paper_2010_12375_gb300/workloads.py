@@ -351,6 +351,48 @@ def learned_dam_break(n_fluid=100_000):
     return dam_break(dim=2, H=1.0, L=2.0, dp=dp, name=f"dam_break_2d_learned")
 
 
+def water_column_on_plate_3d(dp=1.0 / 16.0, ratio=2, H=0.5, L=0.5, W=0.5, thickness=0.1, youngs=4.55e4,
+                             poisson=0.3, rho_s=2.7, rho0=1.0, g=1.0, model=1, nu=0.0):
+    """3D counterpart of water_column_on_plate: a block of water H high over an L x W plate
+    (y up, gravity along -y), side walls of four dummy layers standing on the plate on all
+    four sides, the plate of the given thickness on a lattice ratio times finer, clamped where
+    it runs under the walls (x or z outside the tank). Solid normals point up into the water."""
+    nx, ny, nz = int(round(L / dp)), int(round(H / dp)), int(round(W / dp))
+    fluid = _lattice(np.zeros(3), [nx, ny, nz], dp)
+    top = 1.5 * H
+    nyw = int(round(top / dp))
+    wpos, wnrm, _ = tank_walls(np.zeros(3), np.array([nx * dp, nyw * dp, nz * dp]), dp)
+    side = (wpos[:, 1] > 0.0) & (wpos[:, 1] < nyw * dp)      # the x and z walls, not floor or lid
+    wpos, wnrm = wpos[side], wnrm[side]
+    ds = dp / ratio
+    clamp = WALL_LAYERS * dp
+    nsx, nsz = int(round((nx * dp + 2 * clamp) / ds)), int(round((nz * dp + 2 * clamp) / ds))
+    nsy = max(1, int(round(thickness / ds)))
+    spos = _lattice(np.array([-clamp, -nsy * ds, -clamp]), [nsx, nsy, nsz], ds)
+    c0 = 10.0 * math.sqrt(g * H)
+    grav = np.zeros(3)
+    grav[1] = -g
+    lo = np.array([-clamp - 2 * dp, -nsy * ds - 4 * dp, -clamp - 2 * dp])
+    hi = np.array([nx * dp + clamp + 2 * dp, top + 4 * dp, nz * dp + clamp + 2 * dp])
+    n = fluid.shape[0]
+    wl = Workload(
+        name=f"water_column_on_plate_3d_{n}_r{ratio}", dim=3, h=H_OVER_DP * dp, dp=dp, rho0=rho0, c0=c0,
+        cfl_ad=0.25, cfl_ac=0.6, u_ref=c0 / 10.0, nu=nu, gravity=grav, lo=lo, hi=hi,
+        periodic=np.zeros(3, dtype=np.int32), free_surface=1,
+        pos=fluid, vel=np.zeros_like(fluid), rho=np.full(n, rho0), mass=np.full(n, rho0 * dp ** 3),
+        wall_pos=wpos, wall_normal=wnrm, wall_vol=np.full(wpos.shape[0], dp ** 3),
+        t_end=1.0, meta={"H": ny * dp, "L": nx * dp, "W": nz * dp, "g": g, "thickness": nsy * ds, "ratio": ratio},
+    )
+    wl.solid_pos = spos
+    wl.solid_vol = np.full(spos.shape[0], ds ** 3)
+    wl.solid_normal = np.tile([0.0, 1.0, 0.0], (spos.shape[0], 1))
+    wl.solid_fixed = (spos[:, 0] < 0.0) | (spos[:, 0] > nx * dp) | (spos[:, 2] < 0.0) | (spos[:, 2] > nz * dp)
+    wl.solid_h = H_OVER_DP * ds
+    wl.solid_dp = ds
+    wl.solid_rho0, wl.solid_youngs, wl.solid_poisson, wl.solid_model = rho_s, youngs, poisson, model
+    return wl
+
+
 def water_column_on_plate(dp=1.0 / 40.0, ratio=2, H=1.0, L=1.0, thickness=0.05, youngs=4.55e4,
                           poisson=0.3, rho_s=2.7, rho0=1.0, g=1.0, model=1, nu=0.0):
     """2D water column of height H on an elastic plate spanning a tank of width L (the

@@ -1,5 +1,6 @@
 """The C ABI without a GPU: the library builds, loads and exports every function that
 include/sph.h declares, and the host-only parameter check behaves."""
+import ctypes
 import os
 import re
 
@@ -115,3 +116,12 @@ def test_error_control_entry_points_reject_null_handles(lib):
     p = lib.params_from(__import__("paper_2010_12375_gb300.workloads", fromlist=["x"]).dam_break_2d(),
                         max_substeps=1)
     assert p.max_substeps == 1 and lib.sph_params_check(p) == lib.SPH_OK
+
+
+def test_solid_entry_points_reject_null_handles(lib):
+    L = lib.load()
+    assert L.sph_solid_size(None) == -1
+    out = ctypes.c_void_p(0)
+    assert L.sph_solid_create(None, None, 0, None, None, None, None, ctypes.byref(out)) == lib.SPH_E_INVALID
+    assert L.sph_solid_get_state(None, None, None, None, None, None, None, None) == lib.SPH_E_INVALID
+    L.sph_solid_destroy(None)                                 # a no-op

@@ -2,11 +2,11 @@
 the multi-resolution coupling, against what fixes them independently:
   * B0 tends to the identity in the interior of a lattice as h/dp grows, and with it F is
     exact for any linear displacement, at every particle, surfaces included;
-  * a rigid rotation gives F = R and zero stress, for both material laws;
+  * a rigid rotation gives F = R and zero stress, for both material laws, in 2D and 3D;
   * the elastic forces are antisymmetric per pair: a free solid's momentum is conserved;
   * a cantilever's first bending frequency against Euler-Bernoulli's closed form;
-  * a hydrostatic column on a rigid plate loads it with the column's weight rho0 g H L, and
-    the fluid takes exactly the opposite momentum;
+  * a hydrostatic column on a rigid plate loads it with the column's weight rho0 g H L
+    (rho0 g H L W in 3D), and the fluid takes exactly the opposite momentum;
   * the viscous coupling slows fluid sliding along a plate (R23);
   * the kappa solid steps cover the fluid step.
 Planted mistakes fail them: no correction matrix, a flipped stress sign, no pressure
@@ -60,6 +60,44 @@ def test_linear_displacement_and_rigid_rotation(model):
         assert np.allclose(f.first_piola(Fs[None], sol.mat)[0], Fs @ S_lin, rtol=1e-12)
     else:    # small strain: Neo-Hookean agrees with the linear law to first order in e
         assert np.allclose(f.first_piola(Fs[None], sol.mat)[0], Fs @ S_lin, rtol=3 * e)
+
+
+@pytest.mark.parametrize("model", [f.LINEAR, f.NEO_HOOKEAN])
+def test_3d_linear_displacement_and_rigid_rotation(model):
+    dp = 0.01
+    x0 = wk._lattice(np.zeros(3), [8, 6, 5], dp)
+    mat = f.Material(rho0=1000.0, youngs=2e6, poisson=0.3, model=model)
+    sol = f.make_solid(x0, np.full(len(x0), dp ** 3), np.tile([0.0, 1.0, 0.0], (len(x0), 1)),
+                       np.zeros(len(x0), bool), mat, 1.3 * dp, np.zeros(3))
+    G = np.array([[0.01, -0.02, 0.004], [0.005, 0.03, -0.01], [-0.003, 0.002, 0.02]])
+    F = f.deformation_gradient_from_displacement(sol, x0 @ G.T)
+    assert np.abs(F - (np.eye(3) + G)).max() < 1e-12          # surfaces and corners included
+    a, b = 0.3, -0.2                                            # a rotation about z, then about x
+    Rz = np.array([[math.cos(a), -math.sin(a), 0.0], [math.sin(a), math.cos(a), 0.0], [0.0, 0.0, 1.0]])
+    Rx = np.array([[1.0, 0.0, 0.0], [0.0, math.cos(b), -math.sin(b)], [0.0, math.sin(b), math.cos(b)]])
+    R = Rx @ Rz
+    sol.F = f.deformation_gradient_from_displacement(sol, x0 @ R.T - x0)
+    assert np.abs(sol.F - R).max() < 1e-12
+    assert np.abs(f.first_piola(sol.F, sol.mat)).max() < 1e-8 * sol.mat.youngs
+    assert np.abs(f.elastic_acceleration(sol)).max() < 1e-8 * sol.mat.youngs / (sol.mat.rho0 * sol.h)
+
+
+def test_3d_hydrostatic_column_loads_the_plate_with_its_weight():
+    # a 0.5 x 0.5 x 0.5 block of water on a plate clamped on four sides: the plate carries
+    # rho0 g H L W (0.978 of it at dp = 1/16, 0.984 at 1/24), straight down, and the fluid
+    # takes exactly the opposite momentum
+    wl = wk.water_column_on_plate_3d()
+    prm = o.Params.from_problem(wl)
+    st, _ = o.state_from_problem(wl)
+    sol = f.solid_from_problem(wl)
+    H, g = wl.meta["H"], wl.meta["g"]
+    rho = prm.rho0 + prm.rho0 * g * (H - st.x[:, 1]) / prm.c0 ** 2
+    acc, force = f.coupling_forces(st.x, rho, st.v, st.m, sol, prm)
+    total, fluid = force.sum(axis=0), np.sum(st.m[:, None] * acc, axis=0)
+    weight = prm.rho0 * g * H * wl.meta["L"] * wl.meta["W"]
+    assert abs(total[0]) < 1e-12 * weight and abs(total[2]) < 1e-12 * weight
+    assert abs(total[1] + weight) < 0.03 * weight, (total, weight)
+    assert np.abs(total + fluid).max() < 1e-12 * weight
 
 
 def test_free_solid_conserves_momentum():
