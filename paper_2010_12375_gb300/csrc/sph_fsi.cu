@@ -256,11 +256,53 @@ __device__ __forceinline__ float3 fsi_force(const FsiPair& P, float dev_i, float
   return f;
 }
 
-// The coupling sums run a warp per particle: each lane takes a strided share of the other
-// side's particles with a compensated running sum, and the warp combines the 32 shares by
-// a fixed shuffle tree of error-free sums, so every result is deterministic. The grids are
-// fixed (a grid-stride loop over warps), since the near list's length is on the device.
+// The coupling sums run a warp per particle. The other side's particles come in chunks of
+// 32 consecutive ones (the solid in its Morton order, the near fluid list in storage order)
+// with the bounding box of their current positions: the warp tests 32 boxes at a time and
+// visits only chunks whose box lies within 2h (the box distance bounds every pair distance
+// from below, so no pair is missed), each lane taking one particle of a visited chunk with
+// a compensated running sum; the warp combines the 32 shares by a fixed shuffle tree of
+// error-free sums, so every result is deterministic. The grids are fixed (a grid-stride loop
+// over warps), since the near list's length is on the device.
 constexpr int kCoupleWarps = kFBlock / 32;
+
+// Bounding box (lo, hi) of the positions of each chunk of 32 consecutive entries of a list
+// (idx[k], or k itself when idx is NULL) of n entries, n on the device when n_dev is given.
+__global__ void __launch_bounds__(kFBlock)
+k_chunk_boxes(int64_t n_host, const int* __restrict__ n_dev, const int* __restrict__ idx, const int4* __restrict__ X,
+              int4* __restrict__ box) {
+  const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+  const int lane = threadIdx.x & 31;
+  for (int64_t c = (int64_t)blockIdx.x * kCoupleWarps + (threadIdx.x >> 5); c * 32 < n;
+       c += (int64_t)gridDim.x * kCoupleWarps) {
+    const int64_t k = c * 32 + lane;
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    if (k < n) {
+      const int4 q = X[idx ? (int64_t)idx[k] : k];
+      lo[0] = hi[0] = q.x;
+      lo[1] = hi[1] = q.y;
+      lo[2] = hi[2] = q.z;
+    }
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
+      hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
+    }
+    if (lane == 0) {
+      box[2 * c] = make_int4(lo[0], lo[1], lo[2], 0);
+      box[2 * c + 1] = make_int4(hi[0], hi[1], hi[2], 0);
+    }
+  }
+}
+
+// Whether a chunk's box comes within the support of q: the squared distance from q to the
+// box (in position quanta) below the pair threshold R2.
+template <int D>
+__device__ __forceinline__ bool box_within(const int4& q, const int4& lo, const int4& hi, long long R2) {
+  const long long dx = max(max((long long)lo.x - q.x, (long long)q.x - hi.x), 0LL);
+  const long long dy = max(max((long long)lo.y - q.y, (long long)q.y - hi.y), 0LL);
+  const long long dz = D == 3 ? max(max((long long)lo.z - q.z, (long long)q.z - hi.z), 0LL) : 0LL;
+  return dx * dx + dy * dy + dz * dz < R2;
+}
 
 // Error-free sum of two floats (Knuth's two-sum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -291,11 +333,12 @@ k_fsi_fluid_pressure(const Inst I, const int* __restrict__ n_near_p, const int* 
                      float4* __restrict__ VH, const float4* __restrict__ VS, const float* __restrict__ mass,
                      const Ctrl* __restrict__ ctrl, int64_t ns, const int4* __restrict__ X,
                      const float4* __restrict__ N, const float4* __restrict__ vbar, const float4* __restrict__ abar,
-                     float4* __restrict__ acc_keep) {
+                     const int4* __restrict__ sbox, float4* __restrict__ acc_keep) {
   const double dtd = ctrl[0].dt;
   if (dtd == 0.0) return;
   const int lane = threadIdx.x & 31;
   const int n_near = *n_near_p;
+  const int64_t nch = (ns + 31) / 32;
   for (int k = blockIdx.x * kCoupleWarps + (threadIdx.x >> 5); k < n_near; k += gridDim.x * kCoupleWarps) {
     const int i = near[k];
     const int4 qi = PH[i];
@@ -303,14 +346,21 @@ k_fsi_fluid_pressure(const Inst I, const int* __restrict__ n_near_p, const int* 
     const float m_i = mass ? mass[i] : I.mass;
     const float4 vi = VS[i];
     float s[3] = {0, 0, 0}, e[3] = {0, 0, 0};
-    for (int64_t a = lane; a < ns; a += 32) {
-      const int4 qa = X[a];
-      const FsiPair P = fsi_geometry<D>(qi, qa, I);
-      if (!P.in) continue;
-      const float3 f = fsi_force(P, dev_i, m_i, vi, i2f(qa.w), N[a], vbar[a], abar[a], I);
-      csum_add(s[0], e[0], f.x / m_i);
-      csum_add(s[1], e[1], f.y / m_i);
-      if (D == 3) csum_add(s[2], e[2], f.z / m_i);
+    for (int64_t c0 = 0; c0 < nch; c0 += 32) {
+      const int64_t c = c0 + lane;
+      unsigned hits = __ballot_sync(0xffffffffu, c < nch && box_within<D>(qi, sbox[2 * c], sbox[2 * c + 1], I.R2));
+      while (hits) {
+        const int64_t a = (c0 + __ffs(hits) - 1) * 32 + lane;
+        hits &= hits - 1;
+        if (a >= ns) continue;
+        const int4 qa = X[a];
+        const FsiPair P = fsi_geometry<D>(qi, qa, I);
+        if (!P.in) continue;
+        const float3 f = fsi_force(P, dev_i, m_i, vi, i2f(qa.w), N[a], vbar[a], abar[a], I);
+        csum_add(s[0], e[0], f.x / m_i);
+        csum_add(s[1], e[1], f.y / m_i);
+        if (D == 3) csum_add(s[2], e[2], f.z / m_i);
+      }
     }
     const float ax = csum_warp(s[0], e[0]), ay = csum_warp(s[1], e[1]), az = D == 3 ? csum_warp(s[2], e[2]) : 0.f;
     if (lane == 0) {
@@ -336,25 +386,34 @@ __global__ void __launch_bounds__(kFBlock)
 k_fsi_solid_force(const Inst I, const int* __restrict__ n_near_p, const int* __restrict__ near, const int4* __restrict__ PH,
                   const float4* __restrict__ VS, const float* __restrict__ mass, const Ctrl* __restrict__ ctrl,
                   int64_t ns, const int4* __restrict__ X, const float4* __restrict__ N,
-                  const float4* __restrict__ vbar, const float4* __restrict__ abar, float4* __restrict__ force) {
+                  const float4* __restrict__ vbar, const float4* __restrict__ abar, const int4* __restrict__ fbox,
+                  float4* __restrict__ force) {
   if (ctrl[0].dt == 0.0) return;
   const int lane = threadIdx.x & 31;
   const int n_near = *n_near_p;
+  const int nch = (n_near + 31) / 32;
   for (int64_t a = (int64_t)blockIdx.x * kCoupleWarps + (threadIdx.x >> 5); a < ns; a += (int64_t)gridDim.x * kCoupleWarps) {
     const int4 qa = X[a];
     const float V_a = i2f(qa.w);
     const float4 n = N[a], vb = vbar[a], ab = abar[a];
     float s[3] = {0, 0, 0}, e[3] = {0, 0, 0};
-    for (int k = lane; k < n_near; k += 32) {
-      const int i = near[k];
-      const int4 qi = PH[i];
-      const FsiPair P = fsi_geometry<D>(qi, qa, I);
-      if (!P.in) continue;
-      const float m_i = mass ? mass[i] : I.mass;
-      const float3 f = fsi_force(P, i2f(qi.w), m_i, VS[i], V_a, n, vb, ab, I);
-      csum_add(s[0], e[0], -f.x);
-      csum_add(s[1], e[1], -f.y);
-      if (D == 3) csum_add(s[2], e[2], -f.z);
+    for (int c0 = 0; c0 < nch; c0 += 32) {
+      const int c = c0 + lane;
+      unsigned hits = __ballot_sync(0xffffffffu, c < nch && box_within<D>(qa, fbox[2 * c], fbox[2 * c + 1], I.R2));
+      while (hits) {
+        const int k = (c0 + __ffs(hits) - 1) * 32 + lane;
+        hits &= hits - 1;
+        if (k >= n_near) continue;
+        const int i = near[k];
+        const int4 qi = PH[i];
+        const FsiPair P = fsi_geometry<D>(qi, qa, I);
+        if (!P.in) continue;
+        const float m_i = mass ? mass[i] : I.mass;
+        const float3 f = fsi_force(P, i2f(qi.w), m_i, VS[i], V_a, n, vb, ab, I);
+        csum_add(s[0], e[0], -f.x);
+        csum_add(s[1], e[1], -f.y);
+        if (D == 3) csum_add(s[2], e[2], -f.z);
+      }
     }
     const float fx = csum_warp(s[0], e[0]), fy = csum_warp(s[1], e[1]), fz = D == 3 ? csum_warp(s[2], e[2]) : 0.f;
     if (lane == 0) force[a] = make_float4(fx, fy, fz, 0.f);
@@ -366,11 +425,12 @@ __global__ void __launch_bounds__(kFBlock)
 k_fsi_fluid_continuity(const Inst I, const int* __restrict__ n_near_p, const int* __restrict__ near, int4* __restrict__ PS,
                        float4* __restrict__ VS, const int4* __restrict__ PH, const Ctrl* __restrict__ ctrl,
                        int64_t ns, const int4* __restrict__ X, const float4* __restrict__ N,
-                       const float4* __restrict__ vbar, const float4* __restrict__ abar) {
+                       const float4* __restrict__ vbar, const float4* __restrict__ abar, const int4* __restrict__ sbox) {
   const double dtd = ctrl[0].dt;
   if (dtd == 0.0) return;
   const int lane = threadIdx.x & 31;
   const int n_near = *n_near_p;
+  const int64_t nch = (ns + 31) / 32;
   for (int k = blockIdx.x * kCoupleWarps + (threadIdx.x >> 5); k < n_near; k += gridDim.x * kCoupleWarps) {
     const int i = near[k];
     int4 qi = PS[i];                       // r^{n+1}, and the new density deviation in w
@@ -379,18 +439,25 @@ k_fsi_fluid_continuity(const Inst I, const int* __restrict__ n_near_p, const int
     const float rho_i = I.rho0 + dev_h;
     const float p_i = I.c0sq * dev_h;
     float s = 0.f, e = 0.f;
-    for (int64_t a = lane; a < ns; a += 32) {
-      const int4 qa = X[a];
-      const FsiPair P = fsi_geometry<D>(qi, qa, I);
-      if (!P.in) continue;
-      const float4 n = N[a], vb = vbar[a];
-      const float UL = -(n.x * vi.x + n.y * vi.y + n.z * vi.z);
-      const float uw = -(n.x * vb.x + n.y * vb.y + n.z * vb.z);
-      const float UR = -UL + 2.0f * uw;
-      const float PR = imaginary_pressure(p_i, rho_i, P, n, abar[a], I);
-      const float rhoR = I.rho0 + PR * I.inv_c0sq;
-      const float Us = 0.5f * (UL + UR) + (p_i - PR) / ((rho_i + rhoR) * I.c0);   // (P_L - P_R)/(2 rho_bar c0)
-      csum_add(s, e, 2.0f * rho_i * i2f(qa.w) * (Us - UL) * P.dW);
+    for (int64_t c0 = 0; c0 < nch; c0 += 32) {
+      const int64_t c = c0 + lane;
+      unsigned hits = __ballot_sync(0xffffffffu, c < nch && box_within<D>(qi, sbox[2 * c], sbox[2 * c + 1], I.R2));
+      while (hits) {
+        const int64_t a = (c0 + __ffs(hits) - 1) * 32 + lane;
+        hits &= hits - 1;
+        if (a >= ns) continue;
+        const int4 qa = X[a];
+        const FsiPair P = fsi_geometry<D>(qi, qa, I);
+        if (!P.in) continue;
+        const float4 n = N[a], vb = vbar[a];
+        const float UL = -(n.x * vi.x + n.y * vi.y + n.z * vi.z);
+        const float uw = -(n.x * vb.x + n.y * vb.y + n.z * vb.z);
+        const float UR = -UL + 2.0f * uw;
+        const float PR = imaginary_pressure(p_i, rho_i, P, n, abar[a], I);
+        const float rhoR = I.rho0 + PR * I.inv_c0sq;
+        const float Us = 0.5f * (UL + UR) + (p_i - PR) / ((rho_i + rhoR) * I.c0);   // (P_L - P_R)/(2 rho_bar c0)
+        csum_add(s, e, 2.0f * rho_i * i2f(qa.w) * (Us - UL) * P.dW);
+      }
     }
     const float drho = csum_warp(s, e);
     if (lane == 0) {
@@ -961,6 +1028,7 @@ struct sph_solid {
   int* n_near = nullptr;        // length of the near-fluid list (device)
   long long* steps = nullptr;
   int* perm = nullptr;          // internal index -> the caller's (device)
+  int4 *sbox = nullptr, *fbox = nullptr;   // chunk boxes: solid, near fluid list
   std::vector<int> perm_host;
   uint32_t *flag = nullptr, *off = nullptr, *scan_tmp = nullptr;
 };
@@ -1119,17 +1187,21 @@ void sph_fsi_after_pressure(sph_handle* h, cudaStream_t st, int64_t* launches) {
   sph_solid* s = h->solid;
   if (!s || s->ns == 0 || h->b.n == 0) return;
   sph::Buffers& b = h->b;
-  // a warp per near fluid particle (the list's length is on the device), a warp per solid particle
+  // chunk boxes of the solid's positions and of the near fluid list's mid-point positions;
+  // then a warp per near fluid particle (the list's length is on the device), a warp per
+  // solid particle
+  sph::k_chunk_boxes<<<sph::wgrid((s->ns + 31) / 32), sph::kFBlock, 0, st>>>(s->ns, nullptr, nullptr, s->X, s->sbox);
+  sph::k_chunk_boxes<<<sph::wgrid((b.n + 31) / 32), sph::kFBlock, 0, st>>>(0, s->n_near, s->near, b.PH, s->fbox);
   auto fp = b.dim == 2 ? sph::k_fsi_fluid_pressure<2> : sph::k_fsi_fluid_pressure<3>;
   fp<<<sph::wgrid(b.n), sph::kFBlock, 0, st>>>(b.inst0, s->n_near, s->near, b.PH, b.VH, b.VS, b.mass, b.ctrl, s->ns,
-                                               s->X, s->N, s->vbar, s->abar, b.acc_keep);
+                                               s->X, s->N, s->vbar, s->abar, s->sbox, b.acc_keep);
   auto sf = b.dim == 2 ? sph::k_fsi_solid_force<2> : sph::k_fsi_solid_force<3>;
   sf<<<sph::wgrid(s->ns), sph::kFBlock, 0, st>>>(b.inst0, s->n_near, s->near, b.PH, b.VS, b.mass, b.ctrl, s->ns, s->X,
-                                                 s->N, s->vbar, s->abar, s->force);
+                                                 s->N, s->vbar, s->abar, s->fbox, s->force);
   sph::Buffers vb = b;                     // |v|max over the corrected new velocities
   vb.VS = b.VH;
   sph::launch_vmax(vb, st, launches);
-  *launches += 2;
+  *launches += 4;
 }
 
 void sph_fsi_after_density(sph_handle* h, cudaStream_t st, int64_t* launches) {
@@ -1139,7 +1211,7 @@ void sph_fsi_after_density(sph_handle* h, cudaStream_t st, int64_t* launches) {
   if (b.n > 0) {
     auto fc = b.dim == 2 ? sph::k_fsi_fluid_continuity<2> : sph::k_fsi_fluid_continuity<3>;
     fc<<<sph::wgrid(b.n), sph::kFBlock, 0, st>>>(b.inst0, s->n_near, s->near, b.PS, b.VS, b.PH, b.ctrl, s->ns, s->X,
-                                                 s->N, s->vbar, s->abar);
+                                                 s->N, s->vbar, s->abar, s->sbox);
     *launches += 1;
   }
   cudaLaunchConfig_t cfg = {};
@@ -1264,7 +1336,8 @@ int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const 
             salloc(s, &s->nb, (size_t)s->cap * n) && salloc(s, &s->cnt, n) && salloc(s, &s->gV, (size_t)s->cap * n) && salloc(s, &s->cA, n) &&
             salloc(s, &s->box, 6) && salloc(s, &s->dev_err, 1) && salloc(s, &s->kappa_last, 1) &&
             salloc(s, &s->n_near, 1) &&
-            salloc(s, &s->steps, 1) && salloc(s, &s->perm, n) && salloc(s, &s->near, std::max<int64_t>(h->b.n, 1)) &&
+            salloc(s, &s->steps, 1) && salloc(s, &s->perm, n) && salloc(s, &s->sbox, 2 * ((n + 31) / 32)) &&
+            salloc(s, &s->fbox, 2 * ((std::max<int64_t>(h->b.n, 1) + 31) / 32)) && salloc(s, &s->near, std::max<int64_t>(h->b.n, 1)) &&
             salloc(s, &s->flag, std::max<int64_t>(h->b.n, 1)) && salloc(s, &s->off, std::max<int64_t>(h->b.n, 1) + 1) &&
             salloc(s, &s->scan_tmp, sph::scan_tmp_elems(std::max<int64_t>(h->b.n, 1)));
   if (!ok) return sfail(s, SPH_E_OOM, "device allocation of the solid failed");
