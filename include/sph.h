@@ -517,10 +517,15 @@ typedef struct {
 /* Attach a solid of n particles (1..16384) to a single-tank handle (one solid per handle):
  * pos [n*dim] reference positions inside the handle's cell grid, vol [n] volumes, normal
  * [n*dim] unit normals of the nearest wetted surface (into the fluid), fixed [n] or NULL;
- * host or device arrays. The solid starts undeformed and at rest; the handle's next
+ * host or device arrays, copied. The solid starts undeformed and at rest; the handle's next
  * configuration update (sph_build_cells or a step) includes it, and every later acoustic
- * substep advances it. On failure *out may still hold an object carrying the message
- * (sph_solid_last_error); destroy it. */
+ * substep advances it. The κ solid steps of a fluid step run in one thread-block cluster of
+ * up to 16 blocks holding the solid in shared memory; internally the particles are kept in
+ * a Morton order of their reference positions (outputs come back in the caller's order).
+ * Errors: SPH_E_INVALID (arguments, a singular correction matrix), SPH_E_DOMAIN (a particle
+ * outside the cell grid), SPH_E_CAPACITY (a reference row longer than the set-up capacity,
+ * or a solid that no cluster's shared memory holds), SPH_E_OOM, SPH_E_CUDA. On failure *out
+ * may still hold an object carrying the message (sph_solid_last_error); destroy it. */
 int sph_solid_create(sph_handle* h, const sph_solid_params* p, int64_t n, const double* pos, const double* vol,
                      const double* normal, const int32_t* fixed, sph_solid** out);
 /* Detach from the handle and free; destroy before the handle. */
