@@ -21,7 +21,7 @@ Readings where the paper is silent or inconsistent (the same readings the CUDA p
       D = kappa I it is kappa. Volumes are m_j/rho_j of the current state. The species lives
       on the fluid particles; wall particles carry none and exchange nothing (zero flux
       through walls). Pairs at zero distance contribute nothing (as reading R6 of the
-      fluid oracle). The kernel-corrected form (Eq. grad-laplace-renormalize) is not taken.
+      fluid oracle). The kernel-corrected form (Eq. grad-laplace-renormalize) is R31.
   R17 Per-particle diffusivity: D_i = s_i D with s_i > 0. Then L~_i = L^-1/sqrt(s_i), the
       harmonic combination of R13 gives L~_ij = L^-1 2/(sqrt(s_i) + sqrt(s_j)), and the pair
       weight is ((sqrt(s_i) + sqrt(s_j))/2)^2 / (e^T D^-1 e): the squared mean of the square
@@ -34,6 +34,17 @@ Readings where the paper is silent or inconsistent (the same readings the CUDA p
       (d/|S|) int_S w(e) e^T H e dS over the unit sphere S (|S| its measure), with
       w(e) = 1/(e^T D^-1 e); it equals tr(D H) only when D is isotropic. The oracle
       computes the printed operator; the tests pin it against that closed-form limit.
+  R31 The kernel-corrected form (Eq. grad-laplace-renormalize) as printed multiplies the
+      matrix B0 by the scalar C and dots it with e.e = 1; read with the correction acting
+      on the pair direction, e^T B0 e, and the two sides averaged: the pair weight of
+      Eq. grad-laplace gains (e^T B0_i e + e^T B0_j e)/2. It reduces to Eq. grad-laplace for
+      B0 = I, keeps both particles' matrices as printed, leaves constant fields at rest and,
+      with a symmetric weight, conserves the species; the literal per-side product
+      (e^T B0_i e C_i - e^T B0_j e C_j) moves a constant field wherever B0 varies. B0_i =
+      (sum_j V_j (r_j - r_i) (x) grad_i W_ij)^-1 (Eq. sph-correctmatrix) over the species'
+      pairs of the current configuration, V_j = m_j/rho_j; where that sum is singular (its
+      determinant below 1e-6 (trace/d)^d, e.g. a particle with fewer than d neighbours
+      spanning space) B0_i = I.
 
 Parity pins: every function here is pinned by tests/test_diffusion_oracle.py (closed forms,
 the analytic solution of a diffusing band, conservation, brute force). None is unpinned.
@@ -72,9 +83,29 @@ def pair_scale(scale, I, J):
     return (0.5 * (r[I] + r[J])) ** 2
 
 
-def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params, scale=None) -> np.ndarray:
-    """Eq. grad-laplace under R13 (and R17 with per-particle factors `scale`): dC_i/dt for
-    every fluid particle i."""
+def correction_matrices(x, vol, I, J, prm: o.Params) -> np.ndarray:
+    """R31: B0_i = (sum_j V_j (r_j - r_i) (x) grad_i W_ij)^-1 (Eq. sph-correctmatrix) over the
+    directed pairs (I, J), the identity where the sum is singular."""
+    n, d = x.shape[0], prm.dim
+    rij = o.min_image(x[I] - x[J], prm.period)
+    r = np.sqrt(np.sum(rij * rij, axis=1))
+    ok = r > 0.0
+    fw = np.zeros_like(r)
+    fw[ok] = o.kernel_dW(r[ok], prm.h, d) / r[ok]                   # grad_i W_ij = fw r_ij
+    outer = (vol[J] * fw)[:, None, None] * (-rij)[:, :, None] * rij[:, None, :]
+    M = np.zeros((n, d, d))
+    np.add.at(M, I, outer)
+    B = np.broadcast_to(np.eye(d), (n, d, d)).copy()
+    tr = np.trace(M, axis1=1, axis2=2) / d
+    good = np.linalg.det(M) > 1e-6 * np.abs(tr) ** d
+    B[good] = np.linalg.inv(M[good])
+    return B
+
+
+def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params, scale=None, B=None) -> np.ndarray:
+    """Eq. grad-laplace under R13 (and R17 with per-particle factors `scale`; with the
+    correction matrices B, Eq. grad-laplace-renormalize under R31): dC_i/dt for every fluid
+    particle i."""
     rij = o.min_image(x[I] - x[J], prm.period)
     r2 = np.sum(rij * rij, axis=1)
     r = np.sqrt(r2)
@@ -84,26 +115,32 @@ def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params, scale=None) -> np.ndarr
     quad = np.einsum("pa,ab,pb->p", rij, Dinv, rij)                  # r^2 e^T D^-1 e
     w = np.zeros_like(r)
     w[ok] = r2[ok] / quad[ok]                                        # 1/(L~ e)^2
+    if B is not None:                                                # R31: (e^T B_i e + e^T B_j e)/2
+        qi = np.einsum("pa,pab,pb->p", rij, B[I], rij)
+        qj = np.einsum("pa,pab,pb->p", rij, B[J], rij)
+        w[ok] = w[ok] * 0.5 * (qi[ok] + qj[ok]) / r2[ok]
     terms = 2.0 * vol[J] * (C[I] - C[J]) * fw * w * pair_scale(scale, I, J)
     out = np.zeros(x.shape[0])
     np.add.at(out, I, terms)
     return out
 
 
-def rk2_step(x, C, vol, I, J, Dinv, dt: float, prm: o.Params, scale=None) -> np.ndarray:
+def rk2_step(x, C, vol, I, J, Dinv, dt: float, prm: o.Params, scale=None, B=None) -> np.ndarray:
     """One step of R14 (Heun)."""
-    Cs = C + dt * diffusion_rate(x, C, vol, I, J, Dinv, prm, scale)
-    return 0.5 * (C + Cs + dt * diffusion_rate(x, Cs, vol, I, J, Dinv, prm, scale))
+    Cs = C + dt * diffusion_rate(x, C, vol, I, J, Dinv, prm, scale, B)
+    return 0.5 * (C + Cs + dt * diffusion_rate(x, Cs, vol, I, J, Dinv, prm, scale, B))
 
 
-def run(x, C, m, rho, D, dt: float, n_steps: int, prm: o.Params, scale=None) -> np.ndarray:
+def run(x, C, m, rho, D, dt: float, n_steps: int, prm: o.Params, scale=None, corrected=False) -> np.ndarray:
     """n_steps RK2 steps of the species C on static particles (positions x, masses m,
-    densities rho; per-particle diffusivity factors `scale`, R17)."""
+    densities rho; per-particle diffusivity factors `scale`, R17; the kernel-corrected form,
+    R31, with `corrected`)."""
     x = np.asarray(x, dtype=np.float64)
     C = np.asarray(C, dtype=np.float64).copy()
     vol = np.asarray(m, dtype=np.float64) / np.asarray(rho, dtype=np.float64)
     Dinv = tensor_inverse(D, prm.dim)
     I, J = fluid_pairs(x, prm)
+    B = correction_matrices(x, vol, I, J, prm) if corrected else None
     for _ in range(int(n_steps)):
-        C = rk2_step(x, C, vol, I, J, Dinv, dt, prm, scale)
+        C = rk2_step(x, C, vol, I, J, Dinv, dt, prm, scale, B)
     return C

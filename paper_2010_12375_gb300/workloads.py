@@ -276,6 +276,21 @@ def diffusion_block_3d(n=200, kappa=1.0, sigma=0.1, D=None):
     return _static_body(f"diffusion_block_3d_{n}", 3, dp, pos, np.ones(3), C0, kappa, D)
 
 
+def diffusion_patch(n=40, kappa=1.0, sigma=0.2, D=None):
+    """Square patch of n x n lattice particles on [0, 1]^2 with free edges (no periodic axis,
+    no walls), so that the kernel correction matrices vary near the edges; Gaussian blob
+    C = exp(-|x - c|^2 / (2 sigma^2)). meta as diffusion_band."""
+    dp = 1.0 / n
+    pos = _lattice(np.zeros(2), [n, n], dp)
+    C0 = np.exp(-np.sum((pos - 0.5) ** 2, axis=1) / (2.0 * sigma * sigma))
+    w = _static_body(f"diffusion_patch_{n}", 2, dp, pos, np.ones(3), C0, kappa, D)
+    w.periodic = np.zeros(3, dtype=np.int32)
+    w.lo = np.array([-4.0 * dp, -4.0 * dp, 0.0])
+    w.hi = np.array([1.0 + 4.0 * dp, 1.0 + 4.0 * dp, 0.0])
+    w.free_surface = 1
+    return w
+
+
 def _static_body(name, dim, dp, pos, extent, C0, kappa, D):
     N = pos.shape[0]
     Dm = np.zeros((3, 3))
