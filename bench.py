@@ -43,10 +43,10 @@ TRAFFIC_SOURCE_HASH = "af5377473ba40097"
 
 
 # DRAM bytes (read + write) per particle of one diffusion stage launch, from the ncu capture
-# of k_diffusion_stage on the 120^3 block (both stages, 651.8 and 652.8 MB per launch at 1.728M
+# of k_diffusion_stage on the 120^3 block (both stages, 652.4 and 652.8 MB per launch at 1.728M
 # particles); traffic is per particle on the lattice, so it scales to the 200^3 block.
-DIFF_TRAFFIC_BYTES_PER_PARTICLE = 377.5
-DIFF_TRAFFIC_SOURCE_HASH = "333d0b1078cf223d"
+DIFF_TRAFFIC_BYTES_PER_PARTICLE = 377.6
+DIFF_TRAFFIC_SOURCE_HASH = "42dfba3e5c8d53e3"
 # the stage kernel and its device helpers: the rest of the file (pack/unpack, the reaction
 # step, the host API) does not change the captured launches
 DIFF_SOURCES = ("sph_common.cuh", ("sph_diffusion.cu", "float2 pair_coord2(", "Per call: records of both buffers"))
@@ -595,6 +595,8 @@ def run_diffusion(args, stream):
     sim = sph.Simulation(prob, stream=stream)
     sph.sph_build_cells(sim.handle, stream)
     sp = sph.sph_species_create(sim.handle, prob.meta["D"], 3)
+    if args.corrected:                      # the kernel-corrected form (Eq. grad-laplace-renormalize)
+        sph.sph_species_set_correction(sim.handle, sp, True)
     sph.sph_species_set(sim.handle, sp, prob.meta["C0"], stream)
     dt = prob.meta["dt"]
     fluid_pairs, _ = sph.sph_pair_count(sim.handle, stream)
@@ -636,11 +638,11 @@ def run_diffusion(args, stream):
     r50_ms = timed_reaction(50, 5)
     sph.sph_species_destroy(sp)
     sim.close()
-    stage_ms = (ms_2k - ms_k) / (2 * args.steps)        # per stage kernel, gather/scatter removed
+    stage_ms = (ms_2k - ms_k) / (2 * args.steps)        # per stage kernel, gather/scatter (and B0) removed
     # algorithmic bytes of one stage: own record 16 (position + species), own volume 4,
     # row count 4, species written 4, C^n 4 in the second stage (2 on average), and 4 per
     # neighbour index; the neighbours' records are re-reads of records counted once
-    per_particle = 16 + 4 + 4 + 4 + 2
+    per_particle = 16 + 4 + 4 + 4 + 2 + (24 if args.corrected else 0)     # + own B0 (6 floats)
     alg = n * per_particle + 4 * fluid_pairs
     peak, src = measured_peaks()
     achieved = alg / (stage_ms * 1e-3) / 1e9
@@ -650,13 +652,15 @@ def run_diffusion(args, stream):
            "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"3D unit-periodic static block, {n} particles (dp = 1/{nd}, h = 1.3 dp), "
                                   "isotropic D, Gaussian blob sigma = 0.1; inputs larger than L2",
-                      "fluid_pairs": int(fluid_pairs)},
+                      "fluid_pairs": int(fluid_pairs),
+                      "form": "kernel-corrected" if args.corrected else "plain"},
            "clocks": clk,
-           "gpu_launches": 2 * args.steps + 2,
+           "gpu_launches": 2 * args.steps + 2 + (1 if args.corrected else 0),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak,
                         "traffic": (DIFF_TRAFFIC_BYTES_PER_PARTICLE * n
-                                    if kernel_source_hash(DIFF_SOURCES) == DIFF_TRAFFIC_SOURCE_HASH else None),
+                                    if kernel_source_hash(DIFF_SOURCES) == DIFF_TRAFFIC_SOURCE_HASH
+                                    and not args.corrected else None),
                         "kernel": "k_diffusion_stage", "stage_ms": stage_ms,
                         "algorithmic_bytes": alg, "peak_source": src},
            "reaction": {"kernel": "k_reaction", "model": "FitzHugh-Nagumo",
@@ -818,6 +822,8 @@ def main():
                     help="untimed advection steps over which the relaxation kernels' launches are timed")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--diff-n", type=int, default=200, help="diffusion3d block: n^3 particles")
+    ap.add_argument("--corrected", action="store_true",
+                    help="diffusion3d: the kernel-corrected form (Eq. grad-laplace-renormalize)")
     ap.add_argument("--fsi-time", type=float, default=0.05, help="fsi: simulated time per run")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -421,6 +421,16 @@ int sph_species_get(sph_handle* h, sph_species* sp, double* C, void* stream);
  * the harmonic mean of L~_i = L^-1/sqrt(s_i), weights a pair by
  * ((sqrt(s_i) + sqrt(s_j))/2)^2. Until called, every factor is 1. Synchronous. */
 int sph_species_set_scale(sph_handle* h, sph_species* sp, const double* s, void* stream);
+/* The kernel-corrected form (Eq. grad-laplace-renormalize) on (on != 0) or off (the
+ * default, Eq. grad-laplace). The printed form multiplies the correction matrix B0 by the
+ * scalar C; it is taken as the pair weight of Eq. grad-laplace times
+ * (e^T B0_i e + e^T B0_j e)/2, which is Eq. grad-laplace for B0 = I, keeps constant fields
+ * at rest and conserves the species. B0_i = (sum_j V_j (r_j - r_i) (x) grad_i W_ij)^-1
+ * (Eq. sph-correctmatrix) over the species' fluid pairs, V_j = m_j/rho_j, is formed once
+ * per sph_diffusion_step call from the current configuration (the identity where that
+ * sum is singular: determinant below 1e-6 (trace/d)^d). SPH_E_OOM if its per-particle
+ * storage cannot be allocated. Host-only; takes effect at the next diffusion step. */
+int sph_species_set_correction(sph_handle* h, sph_species* sp, int32_t on);
 /* n_steps RK2 steps of size dt (> 0, finite) on the current neighbour table, which
  * must be valid (sph_build_cells after the last state change; SPH_E_INVALID otherwise).
  * Positions, velocities and densities are not changed. Two kernel launches per step plus

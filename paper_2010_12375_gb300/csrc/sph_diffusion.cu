@@ -26,6 +26,11 @@
 // (2D) or a per-slot array (3D) and the factor pair from a per-slot array. Wall neighbours
 // are skipped: walls carry no species (zero flux). Pairs at zero distance add nothing.
 //
+// Kernel-corrected form (Eq. grad-laplace-renormalize, read as: the pair weight gains
+// (e^T B0_i e + e^T B0_j e)/2): once per call a kernel forms each slot's symmetric
+// B0_i = (sum_j V_j (r_j - r_i) (x) grad_i W_ij)^-1 over the same fluid pairs (the identity
+// where that sum is singular), and the corrected stage kernels gather B0_j with each record.
+//
 // Between calls the species is kept by caller row, so the fluid solver may re-sort the
 // particles; each call gathers it into slot order, runs its steps and scatters it back.
 #include <cmath>
@@ -57,9 +62,32 @@ __device__ __forceinline__ float2 pair_coord2(int qi, int qa, int qb, int period
 // factor dwr_a of (dW/dr)/r (and kappa when isotropic):
 // (C_i - C_j) (1 - q/2)^3 w(e_ij). At zero distance r = 0 * inf is NaN, fmaxf turns the
 // kernel factor into 0 and the pair adds nothing.
-template <int D, bool PER, bool ISO>
+// Symmetric B0 of a slot: {xx, yy, zz, xy, xz, yz}, stored as one float4 {xx, yy, xy, 0}
+// per slot in 2D and two, {xx, yy, zz, xy} and {xz, yz, 0, 0}, in 3D.
+struct Sym3 {
+  float xx, yy, zz, xy, xz, yz;
+};
+template <int D>
+__device__ __forceinline__ Sym3 load_b0(const float4* __restrict__ Bc, int64_t j) {
+  if (D == 2) {
+    const float4 b = Bc[j];
+    return Sym3{b.x, b.y, 0.0f, b.z, 0.0f, 0.0f};
+  }
+  const float4 b0 = Bc[2 * j], b1 = Bc[2 * j + 1];
+  return Sym3{b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+}
+template <int D>
+__device__ __forceinline__ float2 quad_form2(const Sym3& B, float2 rx, float2 ry, float2 rz) {
+  float2 q = fma2(mul2(f2(B.xx), rx), rx, fma2(mul2(f2(B.yy), ry), ry, mul2(mul2(f2(2.0f * B.xy), rx), ry)));
+  if (D == 3)
+    q = fma2(mul2(f2(B.zz), rz), rz, fma2(mul2(f2(2.0f * B.xz), rx), rz, fma2(mul2(f2(2.0f * B.yz), ry), rz, q)));
+  return q;
+}
+
+template <int D, bool PER, bool ISO, bool CORR = false>
 __device__ __forceinline__ float2 diff_terms2(const Inst& I, const DiffCoef& K, const int4& ri, float ci,
-                                              const int4& a, const int4& b) {
+                                              const int4& a, const int4& b, const Sym3* Bi = nullptr,
+                                              const Sym3* Ba = nullptr, const Sym3* Bb = nullptr) {
   const float2 DQ = f2(I.dq);
   const float2 rx = pair_coord2<PER>(ri.x, a.x, b.x, I.period[0], DQ);
   const float2 ry = pair_coord2<PER>(ri.y, a.y, b.y, I.period[1], DQ);
@@ -80,6 +108,12 @@ __device__ __forceinline__ float2 diff_terms2(const Inst& I, const DiffCoef& K, 
     k = mul2(k, make_float2(__fdividef(r2.x, fmaxf(qf.x, 1e-30f)),       // 1/(e^T D^-1 e)
                             __fdividef(r2.y, fmaxf(qf.y, 1e-30f))));
   }
+  if (CORR) {                        // (e^T B0_i e + e^T B0_j e)/2 = (r^T B0_i r + r^T B0_j r)/(2 r^2)
+    const float2 qi = quad_form2<D>(*Bi, rx, ry, rz);
+    const float2 qab = make_float2(quad_form2<D>(*Ba, rx, ry, rz).x, quad_form2<D>(*Bb, rx, ry, rz).y);
+    const float2 half_inv = make_float2(__fdividef(0.5f, fmaxf(r2.x, 1e-30f)), __fdividef(0.5f, fmaxf(r2.y, 1e-30f)));
+    k = mul2(k, mul2(add2(qi, qab), half_inv));
+  }
   return mul2(sub2(f2(ci), make_float2(i2f(a.w), i2f(b.w))), k);
 }
 
@@ -87,11 +121,12 @@ __device__ __forceinline__ float2 diff_terms2(const Inst& I, const DiffCoef& K, 
 // (from the record in 2D or the volume array in 3D) and by ((sqrt s_i + sqrt s_j)/2)^2 of
 // the per-particle diffusivity factors (sq = sqrt s per slot, NULL when none is set); else
 // the caller multiplies by the common volume and factor.
-template <int D, bool PER, bool ISO, bool VJ>
+template <int D, bool PER, bool ISO, bool VJ, bool CORR>
 __device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Inst& I, const DiffCoef& K,
                                          const int4& ri, float ci, const int4* __restrict__ R,
                                          const int4* __restrict__ nb4, const float* __restrict__ vol,
-                                         const float* __restrict__ sq, float sqi) {
+                                         const float* __restrict__ sq, float sqi, const float4* __restrict__ Bc,
+                                         const Sym3& Bi) {
   const int nq = (nf + 3) >> 2;
   float2 s = f2(0.0f);
   int4 nxt = nq ? nb4[i] : make_int4(0, 0, 0, 0);
@@ -118,8 +153,14 @@ __device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Ins
         w23 = mul2(w23, mul2(m23, m23));
       }
     }
-    s = fma2(diff_terms2<D, PER, ISO>(I, K, ri, ci, a0, a1), w01, s);
-    s = fma2(diff_terms2<D, PER, ISO>(I, K, ri, ci, a2, a3), w23, s);
+    if (CORR) {
+      const Sym3 b0 = load_b0<D>(Bc, cq.x), b1 = load_b0<D>(Bc, j1), b2 = load_b0<D>(Bc, j2), b3 = load_b0<D>(Bc, j3);
+      s = fma2(diff_terms2<D, PER, ISO, true>(I, K, ri, ci, a0, a1, &Bi, &b0, &b1), w01, s);
+      s = fma2(diff_terms2<D, PER, ISO, true>(I, K, ri, ci, a2, a3, &Bi, &b2, &b3), w23, s);
+    } else {
+      s = fma2(diff_terms2<D, PER, ISO>(I, K, ri, ci, a0, a1), w01, s);
+      s = fma2(diff_terms2<D, PER, ISO>(I, K, ri, ci, a2, a3), w23, s);
+    }
   }
   return s.x + s.y;
 }
@@ -127,11 +168,12 @@ __device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Ins
 // Row sum with the periodic wrap only where a neighbour can lie across a periodic
 // boundary: particles farther than the support from every periodic face take the plain
 // differences.
-template <int D, bool PER, bool ISO, bool VJ>
+template <int D, bool PER, bool ISO, bool VJ, bool CORR>
 __device__ __forceinline__ float row_sum_any(int64_t n, int64_t i, int nf, const Inst& I, const DiffCoef& K,
                                              const int4& ri, float ci, const int4* __restrict__ R,
                                              const int4* __restrict__ nb4, const float* __restrict__ vol,
-                                             const float* __restrict__ sq, float sqi) {
+                                             const float* __restrict__ sq, float sqi,
+                                             const float4* __restrict__ Bc, const Sym3& Bi) {
   if (PER) {
     const int reach = (int)ceilf(sqrtf((float)I.R2)) + 2;          // support radius in quanta
     const int q[3] = {ri.x, ri.y, ri.z};
@@ -139,9 +181,9 @@ __device__ __forceinline__ float row_sum_any(int64_t n, int64_t i, int nf, const
 #pragma unroll
     for (int a = 0; a < D; ++a)
       if (I.period[a]) near_face |= q[a] < reach || q[a] >= I.period[a] - reach;
-    if (near_face) return row_sum<D, true, ISO, VJ>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi);
+    if (near_face) return row_sum<D, true, ISO, VJ, CORR>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi, Bc, Bi);
   }
-  return row_sum<D, false, ISO, VJ>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi);
+  return row_sum<D, false, ISO, VJ, CORR>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi, Bc, Bi);
 }
 
 // Five blocks of 256 per SM (48 registers) for the isotropic uniform variants: the stage
@@ -150,12 +192,14 @@ __device__ __forceinline__ float row_sum_any(int64_t n, int64_t i, int nf, const
 // UNIF: volumes and diffusivity factors are equal within each tank (the host reads the
 // flag the pack kernel computes); the general path weights every pair and keeps four
 // blocks per SM, where its extra per-pair loads fit without spilling.
-template <int D, bool PER, bool ISO, bool SECOND, bool UNIF>
-__global__ void __launch_bounds__(kDiffBlock, ISO && UNIF ? 5 : 4)
+// CORR: the kernel-corrected form, B0 per slot in Bc (one 16-byte gather per neighbour in
+// 2D, two in 3D; fewer resident blocks, where the B0 of a quad of neighbours fits).
+template <int D, bool PER, bool ISO, bool SECOND, bool UNIF, bool CORR>
+__global__ void __launch_bounds__(kDiffBlock, CORR ? (D == 3 ? 2 : 3) : (ISO && UNIF ? 5 : 4))
 k_diffusion_stage(int64_t n, const int4* __restrict__ Rin, int4* __restrict__ Rout, const int* __restrict__ nbr,
                   const uint32_t* __restrict__ nbc, const int* __restrict__ inst_of,
                   const Inst* __restrict__ inst, const float* __restrict__ vol,
-                  const float* __restrict__ sq, DiffCoef K, float dt) {
+                  const float* __restrict__ sq, DiffCoef K, float dt, const float4* __restrict__ Bc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Inst& I = inst[inst_of ? inst_of[i] : 0];
@@ -164,12 +208,13 @@ k_diffusion_stage(int64_t n, const int4* __restrict__ Rin, int4* __restrict__ Ro
   const int nf = (int)(nbc[i] & 0xffffu);
   const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
   const float sqi = sq ? sq[i] : 1.0f;
+  const Sym3 Bi = CORR ? load_b0<D>(Bc, i) : Sym3{1.0f, 1.0f, 1.0f, 0.0f, 0.0f, 0.0f};
   float sum;
   if (UNIF) {                      // equal volumes and factors within the tank: those of i
     const float vi = D == 2 ? i2f(ri.z) : vol[i];
-    sum = vi * (sqi * sqi) * row_sum_any<D, PER, ISO, false>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi);
+    sum = vi * (sqi * sqi) * row_sum_any<D, PER, ISO, false, CORR>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi, Bc, Bi);
   } else {
-    sum = row_sum_any<D, PER, ISO, true>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi);
+    sum = row_sum_any<D, PER, ISO, true, CORR>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi, Bc, Bi);
   }
   const float rate = 2.0f * (ISO ? I.dwr_a * K.kappa : I.dwr_a) * sum;
   const float next = fmaf(dt, rate, ci);
@@ -205,6 +250,62 @@ __global__ void k_species_pack(int64_t n, const int4* __restrict__ P, const int*
     const float q = sqrtf(scale_by_row[id[i]]);
     sq[i] = q;
     if (sqrtf(scale_by_row[id[f]]) != q) atomicOr(nonuniform, 2);
+  }
+}
+
+// Per slot: B0_i = (sum_j V_j (r_j - r_i) (x) grad_i W_ij)^-1 over the fluid part of row i
+// (grad_i W_ij = dwr_a (1 - q/2)^3 r_ij, so the sum is -dwr_a sum_j V_j (1 - q/2)^3 r_ij r_ij^T,
+// symmetric), the identity where its determinant is below 1e-6 (trace/d)^d. Pairs at zero
+// distance add nothing.
+template <int D, bool PER>
+__global__ void k_species_correction(int64_t n, const int4* __restrict__ R, const int* __restrict__ nbr,
+                                     const uint32_t* __restrict__ nbc, const int* __restrict__ inst_of,
+                                     const Inst* __restrict__ inst, const float* __restrict__ vol,
+                                     float4* __restrict__ Bc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Inst& I = inst[inst_of ? inst_of[i] : 0];
+  const int4 ri = R[i];
+  const int nf = (int)(nbc[i] & 0xffffu);
+  float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
+  for (int s = 0; s < nf; ++s) {
+    const int j = nbr[(((int64_t)(s >> 2)) * n + i) * 4 + (s & 3)];
+    const int4 rj = R[j];
+    const float rx = (biased_diff<PER>(ri.x, rj.x, I.period[0]) - kMagic) * I.dq;
+    const float ry = (biased_diff<PER>(ri.y, rj.y, I.period[1]) - kMagic) * I.dq;
+    const float rz = D == 3 ? (biased_diff<PER>(ri.z, rj.z, I.period[2]) - kMagic) * I.dq : 0.0f;
+    const float r2 = rx * rx + ry * ry + rz * rz;
+    if (!(r2 > 0.0f)) continue;
+    const float t = fmaxf(fmaf(sqrtf(r2), -0.5f * I.inv_h, 1.0f), 0.0f);
+    const float w = (D == 2 ? i2f(rj.z) : vol[j]) * t * t * t;
+    mxx = fmaf(w * rx, rx, mxx);
+    myy = fmaf(w * ry, ry, myy);
+    mxy = fmaf(w * rx, ry, mxy);
+    if (D == 3) {
+      mzz = fmaf(w * rz, rz, mzz);
+      mxz = fmaf(w * rx, rz, mxz);
+      myz = fmaf(w * ry, rz, myz);
+    }
+  }
+  const float c = -I.dwr_a;                // > 0
+  mxx *= c; myy *= c; mzz *= c; mxy *= c; mxz *= c; myz *= c;
+  if (D == 2) {
+    const float det = mxx * myy - mxy * mxy, tr = 0.5f * (mxx + myy);
+    if (det > 1e-6f * tr * tr)
+      Bc[i] = make_float4(myy / det, mxx / det, -mxy / det, 0.0f);
+    else
+      Bc[i] = make_float4(1.0f, 1.0f, 0.0f, 0.0f);
+  } else {
+    const float cxx = myy * mzz - myz * myz, cyy = mxx * mzz - mxz * mxz, czz = mxx * myy - mxy * mxy;
+    const float cxy = mxz * myz - mxy * mzz, cxz = mxy * myz - mxz * myy, cyz = mxy * mxz - mxx * myz;
+    const float det = mxx * cxx + mxy * cxy + mxz * cxz, tr = (mxx + myy + mzz) / 3.0f;
+    if (det > 1e-6f * tr * tr * tr) {
+      Bc[2 * i] = make_float4(cxx / det, cyy / det, czz / det, cxy / det);
+      Bc[2 * i + 1] = make_float4(cxz / det, cyz / det, 0.0f, 0.0f);
+    } else {
+      Bc[2 * i] = make_float4(1.0f, 1.0f, 1.0f, 0.0f);
+      Bc[2 * i + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
   }
 }
 
@@ -279,22 +380,30 @@ __global__ void k_reaction(int64_t n, float* __restrict__ V, float* __restrict__
 }
 
 using StageFn = void (*)(int64_t, const int4*, int4*, const int*, const uint32_t*, const int*, const Inst*,
-                         const float*, const float*, DiffCoef, float);
+                         const float*, const float*, DiffCoef, float, const float4*);
 
-template <int D, bool PER, bool ISO, bool UNIF>
+template <int D, bool PER, bool ISO, bool UNIF, bool CORR>
 void pick_stages(StageFn* s1, StageFn* s2) {
-  *s1 = k_diffusion_stage<D, PER, ISO, false, UNIF>;
-  *s2 = k_diffusion_stage<D, PER, ISO, true, UNIF>;
+  *s1 = k_diffusion_stage<D, PER, ISO, false, UNIF, CORR>;
+  *s2 = k_diffusion_stage<D, PER, ISO, true, UNIF, CORR>;
 }
 
 template <int D, bool PER>
-void pick_stages(bool iso, bool unif, StageFn* s1, StageFn* s2) {
-  if (iso) {
-    if (unif) pick_stages<D, PER, true, true>(s1, s2);
-    else pick_stages<D, PER, true, false>(s1, s2);
+void pick_stages(bool iso, bool unif, bool corr, StageFn* s1, StageFn* s2) {
+  if (corr) {
+    if (iso) {
+      if (unif) pick_stages<D, PER, true, true, true>(s1, s2);
+      else pick_stages<D, PER, true, false, true>(s1, s2);
+    } else {
+      if (unif) pick_stages<D, PER, false, true, true>(s1, s2);
+      else pick_stages<D, PER, false, false, true>(s1, s2);
+    }
+  } else if (iso) {
+    if (unif) pick_stages<D, PER, true, true, false>(s1, s2);
+    else pick_stages<D, PER, true, false, false>(s1, s2);
   } else {
-    if (unif) pick_stages<D, PER, false, true>(s1, s2);
-    else pick_stages<D, PER, false, false>(s1, s2);
+    if (unif) pick_stages<D, PER, false, true, false>(s1, s2);
+    else pick_stages<D, PER, false, false, false>(s1, s2);
   }
 }
 
@@ -315,6 +424,8 @@ struct sph_species {
   float* scale_by_row = nullptr;  // [n] per-particle diffusivity factors s (NULL: all 1)
   float* sq = nullptr;         // [n] sqrt(s) per slot (with scale_by_row)
   double* stage = nullptr;     // [n] doubles for host copies
+  bool corrected = false;      // the kernel-corrected form (sph_species_set_correction)
+  float4* Bc = nullptr;        // [n] (2D) or [2n] (3D): symmetric B0 per slot, formed per call
   std::string err;
 };
 
@@ -439,6 +550,7 @@ void sph_species_destroy(sph_species* sp) {
   cudaFree(sp->scale_by_row);
   cudaFree(sp->sq);
   cudaFree(sp->stage);
+  cudaFree(sp->Bc);
   delete sp;
 }
 
@@ -549,6 +661,20 @@ int sph_species_set_scale(sph_handle* h, sph_species* sp, const double* s, void*
   return SPH_OK;
 }
 
+int sph_species_set_correction(sph_handle* h, sph_species* sp, int32_t on) {
+  if (!h || !sp) return SPH_E_INVALID;
+  if (sp->n != h->b.n || sp->dim != h->b.dim) return sfail(sp, SPH_E_INVALID, "species belongs to another handle");
+  if (on && !sp->Bc && sp->n > 0) {
+    if (cudaMalloc(&sp->Bc, sizeof(float4) * (size_t)sp->n * (sp->dim == 2 ? 1 : 2)) != cudaSuccess) {
+      cudaGetLastError();
+      sp->Bc = nullptr;
+      return sfail(sp, SPH_E_OOM, "device allocation of the correction matrices failed");
+    }
+  }
+  sp->corrected = on != 0;
+  return SPH_OK;
+}
+
 int sph_reaction_step(sph_handle* h, sph_species* sp, const sph_reaction* r, double dt, int32_t n_steps,
                       void* stream) {
   if (!h || !sp) return SPH_E_INVALID;
@@ -597,17 +723,23 @@ int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_step
   const bool unif = nonuniform == 0;
   sph::StageFn s1, s2;
   if (b.dim == 2) {
-    if (b.any_periodic) sph::pick_stages<2, true>(sp->iso, unif, &s1, &s2);
-    else sph::pick_stages<2, false>(sp->iso, unif, &s1, &s2);
+    if (b.any_periodic) sph::pick_stages<2, true>(sp->iso, unif, sp->corrected, &s1, &s2);
+    else sph::pick_stages<2, false>(sp->iso, unif, sp->corrected, &s1, &s2);
   } else {
-    if (b.any_periodic) sph::pick_stages<3, true>(sp->iso, unif, &s1, &s2);
-    else sph::pick_stages<3, false>(sp->iso, unif, &s1, &s2);
+    if (b.any_periodic) sph::pick_stages<3, true>(sp->iso, unif, sp->corrected, &s1, &s2);
+    else sph::pick_stages<3, false>(sp->iso, unif, sp->corrected, &s1, &s2);
+  }
+  if (sp->corrected) {             // B0 of the current configuration, once per call
+    auto corr = b.dim == 2 ? (b.any_periodic ? sph::k_species_correction<2, true> : sph::k_species_correction<2, false>)
+                           : (b.any_periodic ? sph::k_species_correction<3, true> : sph::k_species_correction<3, false>);
+    corr<<<grid, sph::kDiffBlock, 0, s>>>(b.n, sp->r0, b.nbr, b.nbc, b.inst_of, b.inst, sp->vol, sp->Bc);
+    ++h->launches;
   }
   for (int k = 0; k < n_steps; ++k) {
     s1<<<grid, sph::kDiffBlock, 0, s>>>(b.n, sp->r0, sp->r1, b.nbr, b.nbc, b.inst_of, b.inst, sp->vol,
-                                         sp->sq, sp->K, fdt);
+                                         sp->sq, sp->K, fdt, sp->Bc);
     s2<<<grid, sph::kDiffBlock, 0, s>>>(b.n, sp->r1, sp->r0, b.nbr, b.nbc, b.inst_of, b.inst, sp->vol,
-                                         sp->sq, sp->K, fdt);
+                                         sp->sq, sp->K, fdt, sp->Bc);
   }
   sph::k_species_unpack<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.id, sp->r0, sp->by_row);
   h->launches += 2 + 2 * (int64_t)n_steps;

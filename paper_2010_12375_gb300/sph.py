@@ -47,7 +47,7 @@ EXPORTS = [
     "sph_learned_set_fused", "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
     "sph_species_create", "sph_species_destroy", "sph_species_last_error", "sph_species_set",
     "sph_species_get", "sph_diffusion_step", "sph_species_set_gate", "sph_species_get_gate",
-    "sph_reaction_step", "sph_species_set_scale", "sph_clear_error", "sph_debug_write",
+    "sph_reaction_step", "sph_species_set_scale", "sph_species_set_correction", "sph_clear_error", "sph_debug_write",
     "sph_gradient_diagnostics", "sph_solid_create", "sph_solid_destroy", "sph_solid_last_error", "sph_solid_size",
     "sph_solid_get_state",
 ]
@@ -177,6 +177,7 @@ def load():
         "sph_species_get_gate": (i32, [P, P, P, P]),
         "sph_reaction_step": (i32, [P, P, ctypes.POINTER(SphReaction), dbl, i32, P]),
         "sph_species_set_scale": (i32, [P, P, P, P]),
+        "sph_species_set_correction": (i32, [P, P, i32]),
         "sph_clear_error": (i32, [P, P]),
         "sph_debug_write": (i32, [P, i32, i64, i32, i64, P]),
         "sph_gradient_diagnostics": (i32, [P, P, P, P, P, P]),
@@ -610,6 +611,12 @@ def sph_species_set_scale(h, sp, s, stream=None):
     lib = load()
     s = _f64(s)
     _scheck(lib, sp, lib.sph_species_set_scale(h, sp, _ptr(s), _stream(stream)))
+
+
+def sph_species_set_correction(h, sp, on=True):
+    """The kernel-corrected diffusion form (Eq. grad-laplace-renormalize) on or off."""
+    lib = load()
+    _scheck(lib, sp, lib.sph_species_set_correction(h, sp, 1 if on else 0))
 
 
 def reaction_from(model, **params) -> SphReaction:
