@@ -34,6 +34,13 @@ Readings where the paper is silent or inconsistent (the same readings the CUDA p
       (d/|S|) int_S w(e) e^T H e dS over the unit sphere S (|S| its measure), with
       w(e) = 1/(e^T D^-1 e); it equals tr(D H) only when D is isotropic. The oracle
       computes the printed operator; the tests pin it against that closed-form limit.
+  R32 Per-particle tensors of different shape, D_i = L_i L_i^T (Cholesky, Eq. chol), so
+      L~_i = L_i^-1. The printed combination L~_i L~_j/(L~_i + L~_j), read as the harmonic
+      mean of matrices (as R13 reads it for scalars), is L~_ij = 2 (L~_i^-1 + L~_j^-1)^-1
+      = 2 (L_i + L_j)^-1, and the pair weight 1/(L~_ij e)^2 is r^2 / |M^-1 r|^2 with
+      M = (L_i + L_j)/2. It is R13's 1/(e^T D^-1 e) when every D_i = D and R17's
+      ((sqrt s_i + sqrt s_j)/2)^2 / (e^T D^-1 e) when D_i = s_i D, and it is symmetric in i
+      and j, so the species is conserved.
   R31 The kernel-corrected form (Eq. grad-laplace-renormalize) as printed multiplies the
       matrix B0 by the scalar C and dots it with e.e = 1; read with the correction acting
       on the pair direction, e^T B0 e, and the two sides averaged: the pair weight of
@@ -102,17 +109,31 @@ def correction_matrices(x, vol, I, J, prm: o.Params) -> np.ndarray:
     return B
 
 
-def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params, scale=None, B=None) -> np.ndarray:
-    """Eq. grad-laplace under R13 (and R17 with per-particle factors `scale`; with the
-    correction matrices B, Eq. grad-laplace-renormalize under R31): dC_i/dt for every fluid
-    particle i."""
+def tensor_factors(Dp, dim: int) -> np.ndarray:
+    """R32: the Cholesky factor L_i of every particle's tensor D_i (Dp: (n, dim, dim)),
+    each checked symmetric positive definite."""
+    Dp = np.asarray(Dp, dtype=np.float64).reshape(-1, dim, dim)
+    if not np.array_equal(Dp, np.swapaxes(Dp, 1, 2)):
+        raise ValueError("every D_i must be symmetric")
+    return np.linalg.cholesky(Dp)        # raises unless every D_i is positive definite
+
+
+def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params, scale=None, B=None, Lf=None) -> np.ndarray:
+    """Eq. grad-laplace under R13 (and R17 with per-particle factors `scale`; with
+    per-particle tensor factors Lf (n, d, d), R32, in place of Dinv; with the correction
+    matrices B, Eq. grad-laplace-renormalize under R31): dC_i/dt for every fluid particle i."""
     rij = o.min_image(x[I] - x[J], prm.period)
     r2 = np.sum(rij * rij, axis=1)
     r = np.sqrt(r2)
     ok = r2 > 0.0
     fw = np.zeros_like(r)
     fw[ok] = o.kernel_dW(r[ok], prm.h, prm.dim) / r[ok]            # (1/r) dW/dr
-    quad = np.einsum("pa,ab,pb->p", rij, Dinv, rij)                  # r^2 e^T D^-1 e
+    if Lf is None:
+        quad = np.einsum("pa,ab,pb->p", rij, Dinv, rij)              # r^2 e^T D^-1 e
+    else:                                                            # R32: |M^-1 r|^2, M = (L_i + L_j)/2
+        M = 0.5 * (Lf[I] + Lf[J])
+        y = np.linalg.solve(M, rij[:, :, None])[:, :, 0]
+        quad = np.sum(y * y, axis=1)
     w = np.zeros_like(r)
     w[ok] = r2[ok] / quad[ok]                                        # 1/(L~ e)^2
     if B is not None:                                                # R31: (e^T B_i e + e^T B_j e)/2
@@ -125,22 +146,30 @@ def diffusion_rate(x, C, vol, I, J, Dinv, prm: o.Params, scale=None, B=None) -> 
     return out
 
 
-def rk2_step(x, C, vol, I, J, Dinv, dt: float, prm: o.Params, scale=None, B=None) -> np.ndarray:
+def rk2_step(x, C, vol, I, J, Dinv, dt: float, prm: o.Params, scale=None, B=None, Lf=None) -> np.ndarray:
     """One step of R14 (Heun)."""
-    Cs = C + dt * diffusion_rate(x, C, vol, I, J, Dinv, prm, scale, B)
-    return 0.5 * (C + Cs + dt * diffusion_rate(x, Cs, vol, I, J, Dinv, prm, scale, B))
+    Cs = C + dt * diffusion_rate(x, C, vol, I, J, Dinv, prm, scale, B, Lf)
+    return 0.5 * (C + Cs + dt * diffusion_rate(x, Cs, vol, I, J, Dinv, prm, scale, B, Lf))
 
 
-def run(x, C, m, rho, D, dt: float, n_steps: int, prm: o.Params, scale=None, corrected=False) -> np.ndarray:
+def run(x, C, m, rho, D, dt: float, n_steps: int, prm: o.Params, scale=None, corrected=False,
+        tensors=None) -> np.ndarray:
     """n_steps RK2 steps of the species C on static particles (positions x, masses m,
-    densities rho; per-particle diffusivity factors `scale`, R17; the kernel-corrected form,
-    R31, with `corrected`)."""
+    densities rho; per-particle diffusivity factors `scale`, R17; per-particle tensors
+    `tensors` (n, d, d) in place of D, R32, combined with `scale` as D_i = s_i tensors_i;
+    the kernel-corrected form, R31, with `corrected`)."""
     x = np.asarray(x, dtype=np.float64)
     C = np.asarray(C, dtype=np.float64).copy()
     vol = np.asarray(m, dtype=np.float64) / np.asarray(rho, dtype=np.float64)
     Dinv = tensor_inverse(D, prm.dim)
     I, J = fluid_pairs(x, prm)
     B = correction_matrices(x, vol, I, J, prm) if corrected else None
+    Lf = None
+    if tensors is not None:
+        Lf = tensor_factors(tensors, prm.dim)
+        if scale is not None:
+            Lf = Lf * np.sqrt(np.asarray(scale, dtype=np.float64))[:, None, None]
+            scale = None
     for _ in range(int(n_steps)):
-        C = rk2_step(x, C, vol, I, J, Dinv, dt, prm, scale, B)
+        C = rk2_step(x, C, vol, I, J, Dinv, dt, prm, scale, B, Lf)
     return C

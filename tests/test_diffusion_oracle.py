@@ -323,3 +323,70 @@ def test_corrected_form_planted_mistake_moves_a_constant_field():
     literal = np.zeros(len(x))
     np.add.at(literal, I, 2.0 * vol[J] * (qi - qj) * fw)             # C = 1
     assert np.abs(literal).max() > 100.0
+
+
+# ---- per-particle tensors of different shape (reading R32) -----------------------------------
+
+def _box_operator(n=24, seed=4):
+    w = wl.periodic_box(2, n=n, seed=seed, vel_amp=0.0)
+    prm = o.Params.from_problem(w)
+    x, vol = w.pos, w.mass / w.rho
+    I, J = df.fluid_pairs(x, prm)
+    return w, prm, x, vol, I, J
+
+
+def _random_spd(rng, n, d):
+    A = rng.normal(size=(n, d, d))
+    return A @ np.swapaxes(A, 1, 2) + 0.5 * np.eye(d)
+
+
+def test_equal_tensors_are_the_single_tensor_operator():
+    w, prm, x, vol, I, J = _box_operator()
+    D = np.array([[2.0, 0.6], [0.6, 1.0]])
+    C = np.random.default_rng(1).random(len(x))
+    Lf = df.tensor_factors(np.broadcast_to(D, (len(x), 2, 2)), 2)
+    a = df.diffusion_rate(x, C, vol, I, J, df.tensor_inverse(D, 2), prm)
+    b = df.diffusion_rate(x, C, vol, I, J, None, prm, Lf=Lf)
+    assert np.allclose(b, a, rtol=1e-12, atol=1e-12 * np.abs(a).max())
+
+
+def test_scaled_tensors_are_the_per_particle_factor_operator():
+    # D_i = s_i D gives R17's ((sqrt s_i + sqrt s_j)/2)^2 / (e^T D^-1 e)
+    w, prm, x, vol, I, J = _box_operator()
+    rng = np.random.default_rng(2)
+    D = np.array([[1.5, -0.4], [-0.4, 0.8]])
+    s = rng.uniform(0.5, 2.0, len(x))
+    C = rng.random(len(x))
+    Lf = df.tensor_factors(s[:, None, None] * D, 2)
+    a = df.diffusion_rate(x, C, vol, I, J, df.tensor_inverse(D, 2), prm, scale=s)
+    b = df.diffusion_rate(x, C, vol, I, J, None, prm, Lf=Lf)
+    assert np.allclose(b, a, rtol=1e-11, atol=1e-11 * np.abs(a).max())
+
+
+def test_tensors_of_different_shape_conserve_and_keep_constants():
+    w, prm, x, vol, I, J = _box_operator()
+    rng = np.random.default_rng(3)
+    Lf = df.tensor_factors(_random_spd(rng, len(x), 2), 2)
+    C = rng.random(len(x))
+    L = df.diffusion_rate(x, C, vol, I, J, None, prm, Lf=Lf)
+    assert abs(np.sum(vol * L)) < 1e-12 * np.sum(np.abs(vol * L))
+    assert np.abs(df.diffusion_rate(x, np.ones(len(x)), vol, I, J, None, prm, Lf=Lf)).max() == 0.0
+    with pytest.raises(np.linalg.LinAlgError):                        # not positive definite
+        df.tensor_factors(np.broadcast_to(np.diag([1.0, -1.0]), (3, 2, 2)), 2)
+
+
+def test_tensors_planted_mistake_breaks_conservation():
+    # taking only particle i's factor (M = L_i) makes the pair weight one-sided: the species
+    # is no longer conserved
+    w, prm, x, vol, I, J = _box_operator()
+    rng = np.random.default_rng(3)
+    Lf = df.tensor_factors(_random_spd(rng, len(x), 2), 2)
+    C = rng.random(len(x))
+    rij = o.min_image(x[I] - x[J], prm.period)
+    y = np.linalg.solve(Lf[I], rij[:, :, None])[:, :, 0]
+    r2 = np.sum(rij * rij, axis=1)
+    r = np.sqrt(r2)
+    terms = 2.0 * vol[J] * (C[I] - C[J]) * o.kernel_dW(r, prm.h, 2) / r * r2 / np.sum(y * y, axis=1)
+    L = np.zeros(len(x))
+    np.add.at(L, I, terms)
+    assert abs(np.sum(vol * L)) > 1e-6 * np.sum(np.abs(vol * L))
