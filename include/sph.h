@@ -421,6 +421,15 @@ int sph_species_get(sph_handle* h, sph_species* sp, double* C, void* stream);
  * the harmonic mean of L~_i = L^-1/sqrt(s_i), weights a pair by
  * ((sqrt(s_i) + sqrt(s_j))/2)^2. Until called, every factor is 1. Synchronous. */
 int sph_species_set_scale(sph_handle* h, sph_species* sp, const double* s, void* stream);
+/* Per-particle diffusion tensors of different shape: particle i diffuses with D_i (Dp: host
+ * or device, n_fluid x dim x dim doubles in caller row order, each row-major, finite,
+ * symmetric and positive definite; else SPH_E_INVALID and the species keeps what it had).
+ * D_i = L_i L_i^T (Eq. chol); the printed pair combination of the factors, read as the
+ * harmonic mean of matrices, weights a pair by r^2 / |M^-1 r|^2, M = (L_i + L_j)/2, which is
+ * 1/(e^T D^-1 e) for equal tensors and the sph_species_set_scale weight for D_i = s_i D.
+ * Replaces the species' own tensor until called with Dp = NULL; diffusivity factors set by
+ * sph_species_set_scale multiply on top (D_i = s_i Dp_i). Synchronous. */
+int sph_species_set_tensors(sph_handle* h, sph_species* sp, const double* Dp, void* stream);
 /* The kernel-corrected form (Eq. grad-laplace-renormalize) on (on != 0) or off (the
  * default, Eq. grad-laplace). The printed form multiplies the correction matrix B0 by the
  * scalar C; it is taken as the pair weight of Eq. grad-laplace times

@@ -26,6 +26,12 @@
 // (2D) or a per-slot array (3D) and the factor pair from a per-slot array. Wall neighbours
 // are skipped: walls carry no species (zero flux). Pairs at zero distance add nothing.
 //
+// Per-particle tensors of different shape (D_i = L_i L_i^T, Eq. chol): the printed pair
+// combination read as the harmonic mean of matrices gives the weight r^2 / |M^-1 r|^2 with
+// M = (L_i + L_j)/2 (lower triangular, forward substitution per pair); the factors are
+// formed once per upload (FP64 Cholesky), times sqrt(s_i) with per-particle factors, and
+// gathered per slot like B0 below.
+//
 // Kernel-corrected form (Eq. grad-laplace-renormalize, read as: the pair weight gains
 // (e^T B0_i e + e^T B0_j e)/2): once per call a kernel forms each slot's symmetric
 // B0_i = (sum_j V_j (r_j - r_i) (x) grad_i W_ij)^-1 over the same fluid pairs (the identity
@@ -76,6 +82,35 @@ __device__ __forceinline__ Sym3 load_b0(const float4* __restrict__ Bc, int64_t j
   const float4 b0 = Bc[2 * j], b1 = Bc[2 * j + 1];
   return Sym3{b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
 }
+// Lower-triangular factor of a slot: {l00, l10, l11, l20, l21, l22}, stored as one float4
+// {l00, l10, l11, 0} per slot in 2D and two, {l00, l10, l11, l20} and {l21, l22, 0, 0}, in 3D.
+struct Tri3 {
+  float l00, l10, l11, l20, l21, l22;
+};
+template <int D>
+__device__ __forceinline__ Tri3 load_tri(const float4* __restrict__ Lc, int64_t j) {
+  if (D == 2) {
+    const float4 b = Lc[j];
+    return Tri3{b.x, b.y, b.z, 0.0f, 0.0f, 1.0f};
+  }
+  const float4 b0 = Lc[2 * j], b1 = Lc[2 * j + 1];
+  return Tri3{b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+}
+// |M^-1 r|^2 for one pair, M = (L_i + L_j)/2, by forward substitution
+template <int D>
+__device__ __forceinline__ float tri_solve_sq(const Tri3& Li, const Tri3& Lj, float rx, float ry, float rz) {
+  const float m00 = 0.5f * (Li.l00 + Lj.l00), m10 = 0.5f * (Li.l10 + Lj.l10), m11 = 0.5f * (Li.l11 + Lj.l11);
+  const float y0 = __fdividef(rx, m00);
+  const float y1 = __fdividef(fmaf(-m10, y0, ry), m11);
+  float q = fmaf(y0, y0, y1 * y1);
+  if (D == 3) {
+    const float m20 = 0.5f * (Li.l20 + Lj.l20), m21 = 0.5f * (Li.l21 + Lj.l21), m22 = 0.5f * (Li.l22 + Lj.l22);
+    const float y2 = __fdividef(fmaf(-m21, y1, fmaf(-m20, y0, rz)), m22);
+    q = fmaf(y2, y2, q);
+  }
+  return q;
+}
+
 template <int D>
 __device__ __forceinline__ float2 quad_form2(const Sym3& B, float2 rx, float2 ry, float2 rz) {
   float2 q = fma2(mul2(f2(B.xx), rx), rx, fma2(mul2(f2(B.yy), ry), ry, mul2(mul2(f2(2.0f * B.xy), rx), ry)));
@@ -84,10 +119,13 @@ __device__ __forceinline__ float2 quad_form2(const Sym3& B, float2 rx, float2 ry
   return q;
 }
 
-template <int D, bool PER, bool ISO, bool CORR = false>
+// TEN: per-particle tensors (the weight from the factors Li, La, Lb; ISO and K unused).
+template <int D, bool PER, bool ISO, bool CORR = false, bool TEN = false>
 __device__ __forceinline__ float2 diff_terms2(const Inst& I, const DiffCoef& K, const int4& ri, float ci,
                                               const int4& a, const int4& b, const Sym3* Bi = nullptr,
-                                              const Sym3* Ba = nullptr, const Sym3* Bb = nullptr) {
+                                              const Sym3* Ba = nullptr, const Sym3* Bb = nullptr,
+                                              const Tri3* Li = nullptr, const Tri3* La = nullptr,
+                                              const Tri3* Lb = nullptr) {
   const float2 DQ = f2(I.dq);
   const float2 rx = pair_coord2<PER>(ri.x, a.x, b.x, I.period[0], DQ);
   const float2 ry = pair_coord2<PER>(ri.y, a.y, b.y, I.period[1], DQ);
@@ -100,7 +138,10 @@ __device__ __forceinline__ float2 diff_terms2(const Inst& I, const DiffCoef& K, 
   const float2 r = mul2(r2, rsqrt2(r2));
   const float2 t = max2(fma2(r, f2(-0.5f * I.inv_h), f2(1.0f)), 0.0f);
   float2 k = mul2(mul2(t, t), t);
-  if (!ISO) {
+  if (TEN) {                         // r^2 / |M^-1 r|^2
+    const float qa = tri_solve_sq<D>(*Li, *La, rx.x, ry.x, rz.x), qb = tri_solve_sq<D>(*Li, *Lb, rx.y, ry.y, rz.y);
+    k = mul2(k, make_float2(__fdividef(r2.x, fmaxf(qa, 1e-30f)), __fdividef(r2.y, fmaxf(qb, 1e-30f))));
+  } else if (!ISO) {
     float2 qf = fma2(mul2(f2(K.xx), rx), rx, fma2(mul2(f2(K.yy), ry), ry, mul2(mul2(f2(2.0f * K.xy), rx), ry)));
     if (D == 3)
       qf = fma2(mul2(f2(K.zz), rz), rz,
@@ -121,12 +162,12 @@ __device__ __forceinline__ float2 diff_terms2(const Inst& I, const DiffCoef& K, 
 // (from the record in 2D or the volume array in 3D) and by ((sqrt s_i + sqrt s_j)/2)^2 of
 // the per-particle diffusivity factors (sq = sqrt s per slot, NULL when none is set); else
 // the caller multiplies by the common volume and factor.
-template <int D, bool PER, bool ISO, bool VJ, bool CORR>
+template <int D, bool PER, bool ISO, bool VJ, bool CORR, bool TEN>
 __device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Inst& I, const DiffCoef& K,
                                          const int4& ri, float ci, const int4* __restrict__ R,
                                          const int4* __restrict__ nb4, const float* __restrict__ vol,
                                          const float* __restrict__ sq, float sqi, const float4* __restrict__ Bc,
-                                         const Sym3& Bi) {
+                                         const Sym3& Bi, const float4* __restrict__ Lc, const Tri3& Li) {
   const int nq = (nf + 3) >> 2;
   float2 s = f2(0.0f);
   int4 nxt = nq ? nb4[i] : make_int4(0, 0, 0, 0);
@@ -153,7 +194,17 @@ __device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Ins
         w23 = mul2(w23, mul2(m23, m23));
       }
     }
-    if (CORR) {
+    if (TEN) {
+      const Tri3 l0 = load_tri<D>(Lc, cq.x), l1 = load_tri<D>(Lc, j1), l2 = load_tri<D>(Lc, j2), l3 = load_tri<D>(Lc, j3);
+      if (CORR) {
+        const Sym3 b0 = load_b0<D>(Bc, cq.x), b1 = load_b0<D>(Bc, j1), b2 = load_b0<D>(Bc, j2), b3 = load_b0<D>(Bc, j3);
+        s = fma2(diff_terms2<D, PER, ISO, true, true>(I, K, ri, ci, a0, a1, &Bi, &b0, &b1, &Li, &l0, &l1), w01, s);
+        s = fma2(diff_terms2<D, PER, ISO, true, true>(I, K, ri, ci, a2, a3, &Bi, &b2, &b3, &Li, &l2, &l3), w23, s);
+      } else {
+        s = fma2(diff_terms2<D, PER, ISO, false, true>(I, K, ri, ci, a0, a1, nullptr, nullptr, nullptr, &Li, &l0, &l1), w01, s);
+        s = fma2(diff_terms2<D, PER, ISO, false, true>(I, K, ri, ci, a2, a3, nullptr, nullptr, nullptr, &Li, &l2, &l3), w23, s);
+      }
+    } else if (CORR) {
       const Sym3 b0 = load_b0<D>(Bc, cq.x), b1 = load_b0<D>(Bc, j1), b2 = load_b0<D>(Bc, j2), b3 = load_b0<D>(Bc, j3);
       s = fma2(diff_terms2<D, PER, ISO, true>(I, K, ri, ci, a0, a1, &Bi, &b0, &b1), w01, s);
       s = fma2(diff_terms2<D, PER, ISO, true>(I, K, ri, ci, a2, a3, &Bi, &b2, &b3), w23, s);
@@ -168,12 +219,13 @@ __device__ __forceinline__ float row_sum(int64_t n, int64_t i, int nf, const Ins
 // Row sum with the periodic wrap only where a neighbour can lie across a periodic
 // boundary: particles farther than the support from every periodic face take the plain
 // differences.
-template <int D, bool PER, bool ISO, bool VJ, bool CORR>
+template <int D, bool PER, bool ISO, bool VJ, bool CORR, bool TEN>
 __device__ __forceinline__ float row_sum_any(int64_t n, int64_t i, int nf, const Inst& I, const DiffCoef& K,
                                              const int4& ri, float ci, const int4* __restrict__ R,
                                              const int4* __restrict__ nb4, const float* __restrict__ vol,
                                              const float* __restrict__ sq, float sqi,
-                                             const float4* __restrict__ Bc, const Sym3& Bi) {
+                                             const float4* __restrict__ Bc, const Sym3& Bi,
+                                             const float4* __restrict__ Lc, const Tri3& Li) {
   if (PER) {
     const int reach = (int)ceilf(sqrtf((float)I.R2)) + 2;          // support radius in quanta
     const int q[3] = {ri.x, ri.y, ri.z};
@@ -181,9 +233,10 @@ __device__ __forceinline__ float row_sum_any(int64_t n, int64_t i, int nf, const
 #pragma unroll
     for (int a = 0; a < D; ++a)
       if (I.period[a]) near_face |= q[a] < reach || q[a] >= I.period[a] - reach;
-    if (near_face) return row_sum<D, true, ISO, VJ, CORR>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi, Bc, Bi);
+    if (near_face)
+      return row_sum<D, true, ISO, VJ, CORR, TEN>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi, Bc, Bi, Lc, Li);
   }
-  return row_sum<D, false, ISO, VJ, CORR>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi, Bc, Bi);
+  return row_sum<D, false, ISO, VJ, CORR, TEN>(n, i, nf, I, K, ri, ci, R, nb4, vol, sq, sqi, Bc, Bi, Lc, Li);
 }
 
 // Five blocks of 256 per SM (48 registers) for the isotropic uniform variants: the stage
@@ -193,13 +246,16 @@ __device__ __forceinline__ float row_sum_any(int64_t n, int64_t i, int nf, const
 // flag the pack kernel computes); the general path weights every pair and keeps four
 // blocks per SM, where its extra per-pair loads fit without spilling.
 // CORR: the kernel-corrected form, B0 per slot in Bc (one 16-byte gather per neighbour in
-// 2D, two in 3D; fewer resident blocks, where the B0 of a quad of neighbours fits).
-template <int D, bool PER, bool ISO, bool SECOND, bool UNIF, bool CORR>
-__global__ void __launch_bounds__(kDiffBlock, CORR ? (D == 3 ? 2 : 3) : (ISO && UNIF ? 5 : 4))
+// 2D, two in 3D; fewer resident blocks, where the B0 of a quad of neighbours fits). TEN:
+// per-particle tensors, factors per slot in Lc (the same gathers again), on the weighted
+// path with the diffusivity factors folded into the factors (sq NULL).
+template <int D, bool PER, bool ISO, bool SECOND, bool UNIF, bool CORR, bool TEN>
+__global__ void __launch_bounds__(kDiffBlock, (CORR || TEN) ? ((D == 3 || (CORR && TEN)) ? 2 : 3) : (ISO && UNIF ? 5 : 4))
 k_diffusion_stage(int64_t n, const int4* __restrict__ Rin, int4* __restrict__ Rout, const int* __restrict__ nbr,
                   const uint32_t* __restrict__ nbc, const int* __restrict__ inst_of,
                   const Inst* __restrict__ inst, const float* __restrict__ vol,
-                  const float* __restrict__ sq, DiffCoef K, float dt, const float4* __restrict__ Bc) {
+                  const float* __restrict__ sq, DiffCoef K, float dt, const float4* __restrict__ Bc,
+                  const float4* __restrict__ Lc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Inst& I = inst[inst_of ? inst_of[i] : 0];
@@ -209,12 +265,14 @@ k_diffusion_stage(int64_t n, const int4* __restrict__ Rin, int4* __restrict__ Ro
   const int4* __restrict__ nb4 = reinterpret_cast<const int4*>(nbr);
   const float sqi = sq ? sq[i] : 1.0f;
   const Sym3 Bi = CORR ? load_b0<D>(Bc, i) : Sym3{1.0f, 1.0f, 1.0f, 0.0f, 0.0f, 0.0f};
+  const Tri3 Li = TEN ? load_tri<D>(Lc, i) : Tri3{1.0f, 0.0f, 1.0f, 0.0f, 0.0f, 1.0f};
   float sum;
   if (UNIF) {                      // equal volumes and factors within the tank: those of i
     const float vi = D == 2 ? i2f(ri.z) : vol[i];
-    sum = vi * (sqi * sqi) * row_sum_any<D, PER, ISO, false, CORR>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi, Bc, Bi);
+    sum = vi * (sqi * sqi) *
+          row_sum_any<D, PER, ISO, false, CORR, TEN>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi, Bc, Bi, Lc, Li);
   } else {
-    sum = row_sum_any<D, PER, ISO, true, CORR>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi, Bc, Bi);
+    sum = row_sum_any<D, PER, ISO, true, CORR, TEN>(n, i, nf, I, K, ri, ci, Rin, nb4, vol, sq, sqi, Bc, Bi, Lc, Li);
   }
   const float rate = 2.0f * (ISO ? I.dwr_a * K.kappa : I.dwr_a) * sum;
   const float next = fmaf(dt, rate, ci);
@@ -309,6 +367,60 @@ __global__ void k_species_correction(int64_t n, const int4* __restrict__ R, cons
   }
 }
 
+// Per caller row: the lower-triangular Cholesky factor of D_i (row-major d x d doubles), in
+// FP64, stored {l00, l10, l11, l20, l21, l22}; flags a tensor that is not finite, symmetric
+// and positive definite.
+__global__ void k_species_factor(int64_t n, int d, const double* __restrict__ Dp, float* __restrict__ Lrow,
+                                 int* __restrict__ bad) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const double* A = Dp + r * d * d;
+  double L[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  bool ok = true;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (!isfinite(A[i * d + j]) || A[i * d + j] != A[j * d + i]) ok = false;
+  for (int i = 0; i < d && ok; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double v = A[i * d + j];
+      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+      if (i == j) {
+        if (!(v > 0.0)) {
+          ok = false;
+          break;
+        }
+        L[i][i] = sqrt(v);
+      } else {
+        L[i][j] = v / L[j][j];
+      }
+    }
+  if (!ok) {
+    atomicOr(bad, 1);
+    return;
+  }
+  float* o = Lrow + 6 * r;
+  o[0] = (float)L[0][0]; o[1] = (float)L[1][0]; o[2] = (float)L[1][1];
+  o[3] = (float)L[2][0]; o[4] = (float)L[2][1]; o[5] = (float)(d == 3 ? L[2][2] : 1.0);
+}
+
+// Per slot: the factor of the slot's caller row, times sqrt(s) when diffusivity factors are
+// set (D_i = s_i D'_i), into the slot layout of load_tri.
+template <int D>
+__global__ void k_species_pack_tensors(int64_t n, const int* __restrict__ id, const float* __restrict__ Lrow,
+                                       const float* __restrict__ scale_by_row, float4* __restrict__ Lc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t r = id[i];
+  const float* l = Lrow + 6 * r;
+  const float q = scale_by_row ? sqrtf(scale_by_row[r]) : 1.0f;
+  if (D == 2) {
+    Lc[i] = make_float4(q * l[0], q * l[1], q * l[2], 0.0f);
+  } else {
+    Lc[2 * i] = make_float4(q * l[0], q * l[1], q * l[2], q * l[3]);
+    Lc[2 * i + 1] = make_float4(q * l[4], q * l[5], 0.0f, 0.0f);
+  }
+}
+
 // Flags a diffusivity factor that is not a positive finite number.
 __global__ void k_check_scale(int64_t n, const float* __restrict__ s, int* __restrict__ bad) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -380,17 +492,20 @@ __global__ void k_reaction(int64_t n, float* __restrict__ V, float* __restrict__
 }
 
 using StageFn = void (*)(int64_t, const int4*, int4*, const int*, const uint32_t*, const int*, const Inst*,
-                         const float*, const float*, DiffCoef, float, const float4*);
+                         const float*, const float*, DiffCoef, float, const float4*, const float4*);
 
-template <int D, bool PER, bool ISO, bool UNIF, bool CORR>
+template <int D, bool PER, bool ISO, bool UNIF, bool CORR, bool TEN = false>
 void pick_stages(StageFn* s1, StageFn* s2) {
-  *s1 = k_diffusion_stage<D, PER, ISO, false, UNIF, CORR>;
-  *s2 = k_diffusion_stage<D, PER, ISO, true, UNIF, CORR>;
+  *s1 = k_diffusion_stage<D, PER, ISO, false, UNIF, CORR, TEN>;
+  *s2 = k_diffusion_stage<D, PER, ISO, true, UNIF, CORR, TEN>;
 }
 
 template <int D, bool PER>
-void pick_stages(bool iso, bool unif, bool corr, StageFn* s1, StageFn* s2) {
-  if (corr) {
+void pick_stages(bool iso, bool unif, bool corr, bool ten, StageFn* s1, StageFn* s2) {
+  if (ten) {                       // per-particle tensors: the weighted path
+    if (corr) pick_stages<D, PER, false, false, true, true>(s1, s2);
+    else pick_stages<D, PER, false, false, false, true>(s1, s2);
+  } else if (corr) {
     if (iso) {
       if (unif) pick_stages<D, PER, true, true, true>(s1, s2);
       else pick_stages<D, PER, true, false, true>(s1, s2);
@@ -426,6 +541,8 @@ struct sph_species {
   double* stage = nullptr;     // [n] doubles for host copies
   bool corrected = false;      // the kernel-corrected form (sph_species_set_correction)
   float4* Bc = nullptr;        // [n] (2D) or [2n] (3D): symmetric B0 per slot, formed per call
+  float* Lrow = nullptr;       // [6n] per-particle tensor factors by caller row (NULL: none)
+  float4* Lc = nullptr;        // [n] (2D) or [2n] (3D): the factors per slot, packed per call
   std::string err;
 };
 
@@ -551,6 +668,8 @@ void sph_species_destroy(sph_species* sp) {
   cudaFree(sp->sq);
   cudaFree(sp->stage);
   cudaFree(sp->Bc);
+  cudaFree(sp->Lrow);
+  cudaFree(sp->Lc);
   delete sp;
 }
 
@@ -661,6 +780,60 @@ int sph_species_set_scale(sph_handle* h, sph_species* sp, const double* s, void*
   return SPH_OK;
 }
 
+int sph_species_set_tensors(sph_handle* h, sph_species* sp, const double* Dp, void* stream) {
+  if (!h || !sp) return SPH_E_INVALID;
+  if (sp->n != h->b.n || sp->dim != h->b.dim) return sfail(sp, SPH_E_INVALID, "species belongs to another handle");
+  if (!Dp) {                       // back to the species' own tensor
+    cudaFree(sp->Lrow);
+    cudaFree(sp->Lc);
+    sp->Lrow = nullptr;
+    sp->Lc = nullptr;
+    return SPH_OK;
+  }
+  if (sp->n == 0) return SPH_OK;
+  const PtrKind kind = pointer_kind(Dp);
+  if (kind == kOtherDevicePtr) return sfail(sp, SPH_E_INVALID, "the array lives on another device");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = sp->dim;
+  const size_t n = (size_t)sp->n, nd = n * d * d;
+  float* Lrow = nullptr;
+  float4* Lc = nullptr;
+  double* staged = nullptr;
+  auto cleanup = [&](int code, const char* msg) {
+    cudaGetLastError();
+    cudaFree(Lrow);
+    cudaFree(Lc);
+    cudaFree(staged);
+    return sfail(sp, code, msg);
+  };
+  if (cudaMalloc(&Lrow, sizeof(float) * 6 * n) != cudaSuccess ||
+      cudaMalloc(&Lc, sizeof(float4) * n * (d == 2 ? 1 : 2)) != cudaSuccess)
+    return cleanup(SPH_E_OOM, "device allocation of the tensor factors failed");
+  const double* src = Dp;
+  if (kind == kHostPtr) {
+    if (cudaMalloc(&staged, sizeof(double) * nd) != cudaSuccess)
+      return cleanup(SPH_E_OOM, "staging allocation of the tensors failed");
+    if (cudaMemcpyAsync(staged, Dp, sizeof(double) * nd, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return cleanup(SPH_E_CUDA, "copy of the tensors failed");
+    src = staged;
+  }
+  int bad = 0;
+  if (cudaMemsetAsync(sp->nonuniform, 0, sizeof(int), st) != cudaSuccess)
+    return cleanup(SPH_E_CUDA, "tensor set-up failed");
+  sph::k_species_factor<<<sph::diff_grid(sp->n), sph::kDiffBlock, 0, st>>>(sp->n, d, src, Lrow, sp->nonuniform);
+  ++h->launches;
+  if (cudaMemcpyAsync(&bad, sp->nonuniform, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return cleanup(SPH_E_CUDA, "tensor set-up failed");
+  if (bad) return cleanup(SPH_E_INVALID, "every D_i must be finite, symmetric and positive definite");
+  cudaFree(staged);
+  cudaFree(sp->Lrow);
+  cudaFree(sp->Lc);
+  sp->Lrow = Lrow;
+  sp->Lc = Lc;
+  return SPH_OK;
+}
+
 int sph_species_set_correction(sph_handle* h, sph_species* sp, int32_t on) {
   if (!h || !sp) return SPH_E_INVALID;
   if (sp->n != h->b.n || sp->dim != h->b.dim) return sfail(sp, SPH_E_INVALID, "species belongs to another handle");
@@ -720,15 +893,22 @@ int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_step
   if (cudaMemcpyAsync(&nonuniform, sp->nonuniform, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return sfail(sp, SPH_E_CUDA, "diffusion set-up failed");
-  const bool unif = nonuniform == 0;
+  const bool ten = sp->Lrow != nullptr;
+  const bool unif = nonuniform == 0 && !ten;
   sph::StageFn s1, s2;
   if (b.dim == 2) {
-    if (b.any_periodic) sph::pick_stages<2, true>(sp->iso, unif, sp->corrected, &s1, &s2);
-    else sph::pick_stages<2, false>(sp->iso, unif, sp->corrected, &s1, &s2);
+    if (b.any_periodic) sph::pick_stages<2, true>(sp->iso, unif, sp->corrected, ten, &s1, &s2);
+    else sph::pick_stages<2, false>(sp->iso, unif, sp->corrected, ten, &s1, &s2);
   } else {
-    if (b.any_periodic) sph::pick_stages<3, true>(sp->iso, unif, sp->corrected, &s1, &s2);
-    else sph::pick_stages<3, false>(sp->iso, unif, sp->corrected, &s1, &s2);
+    if (b.any_periodic) sph::pick_stages<3, true>(sp->iso, unif, sp->corrected, ten, &s1, &s2);
+    else sph::pick_stages<3, false>(sp->iso, unif, sp->corrected, ten, &s1, &s2);
   }
+  if (ten) {                       // the tensor factors per slot (sqrt(s) folded in)
+    auto pt = b.dim == 2 ? sph::k_species_pack_tensors<2> : sph::k_species_pack_tensors<3>;
+    pt<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.id, sp->Lrow, sp->scale_by_row, sp->Lc);
+    ++h->launches;
+  }
+  const float* sq_stage = ten ? nullptr : sp->sq;
   if (sp->corrected) {             // B0 of the current configuration, once per call
     auto corr = b.dim == 2 ? (b.any_periodic ? sph::k_species_correction<2, true> : sph::k_species_correction<2, false>)
                            : (b.any_periodic ? sph::k_species_correction<3, true> : sph::k_species_correction<3, false>);
@@ -737,9 +917,9 @@ int sph_diffusion_step(sph_handle* h, sph_species* sp, double dt, int32_t n_step
   }
   for (int k = 0; k < n_steps; ++k) {
     s1<<<grid, sph::kDiffBlock, 0, s>>>(b.n, sp->r0, sp->r1, b.nbr, b.nbc, b.inst_of, b.inst, sp->vol,
-                                         sp->sq, sp->K, fdt, sp->Bc);
+                                         sq_stage, sp->K, fdt, sp->Bc, sp->Lc);
     s2<<<grid, sph::kDiffBlock, 0, s>>>(b.n, sp->r1, sp->r0, b.nbr, b.nbc, b.inst_of, b.inst, sp->vol,
-                                         sp->sq, sp->K, fdt, sp->Bc);
+                                         sq_stage, sp->K, fdt, sp->Bc, sp->Lc);
   }
   sph::k_species_unpack<<<grid, sph::kDiffBlock, 0, s>>>(b.n, b.id, sp->r0, sp->by_row);
   h->launches += 2 + 2 * (int64_t)n_steps;

@@ -47,7 +47,7 @@ EXPORTS = [
     "sph_learned_set_fused", "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
     "sph_species_create", "sph_species_destroy", "sph_species_last_error", "sph_species_set",
     "sph_species_get", "sph_diffusion_step", "sph_species_set_gate", "sph_species_get_gate",
-    "sph_reaction_step", "sph_species_set_scale", "sph_species_set_correction", "sph_clear_error", "sph_debug_write",
+    "sph_reaction_step", "sph_species_set_scale", "sph_species_set_correction", "sph_species_set_tensors", "sph_clear_error", "sph_debug_write",
     "sph_gradient_diagnostics", "sph_solid_create", "sph_solid_destroy", "sph_solid_last_error", "sph_solid_size",
     "sph_solid_get_state",
 ]
@@ -178,6 +178,7 @@ def load():
         "sph_reaction_step": (i32, [P, P, ctypes.POINTER(SphReaction), dbl, i32, P]),
         "sph_species_set_scale": (i32, [P, P, P, P]),
         "sph_species_set_correction": (i32, [P, P, i32]),
+        "sph_species_set_tensors": (i32, [P, P, P, P]),
         "sph_clear_error": (i32, [P, P]),
         "sph_debug_write": (i32, [P, i32, i64, i32, i64, P]),
         "sph_gradient_diagnostics": (i32, [P, P, P, P, P, P]),
@@ -611,6 +612,17 @@ def sph_species_set_scale(h, sp, s, stream=None):
     lib = load()
     s = _f64(s)
     _scheck(lib, sp, lib.sph_species_set_scale(h, sp, _ptr(s), _stream(stream)))
+
+
+def sph_species_set_tensors(h, sp, Dp, stream=None):
+    """Per-particle diffusion tensors (n, dim, dim) in caller row order, or None to return to
+    the species' own tensor."""
+    lib = load()
+    if Dp is None:
+        _scheck(lib, sp, lib.sph_species_set_tensors(h, sp, None, _stream(stream)))
+        return
+    Dp = _f64(Dp)
+    _scheck(lib, sp, lib.sph_species_set_tensors(h, sp, _ptr(Dp), _stream(stream)))
 
 
 def sph_species_set_correction(h, sp, on=True):

@@ -103,6 +103,7 @@ def test_species_and_reaction_entry_points_reject_null_handles(lib):
     assert L.sph_reaction_step(None, None, ctypes.byref(r), 0.1, 1, None) == lib.SPH_E_INVALID
     assert L.sph_diffusion_step(None, None, 0.1, 1, None) == lib.SPH_E_INVALID
     assert L.sph_species_set_correction(None, None, 1) == lib.SPH_E_INVALID
+    assert L.sph_species_set_tensors(None, None, None, None) == lib.SPH_E_INVALID
     buf = (ctypes.c_double * 4)()
     for fn in (L.sph_species_set, L.sph_species_get, L.sph_species_set_gate, L.sph_species_get_gate):
         assert fn(None, None, buf, None) == lib.SPH_E_INVALID

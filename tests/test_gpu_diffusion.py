@@ -315,6 +315,77 @@ def test_corrected_diffusion_matches_oracle(sph, name):
     assert err <= _bound(steps, C0, Co), (name, err)
 
 
+@pytest.mark.parametrize("name,scale,corrected", [("aniso2d", False, False), ("iso3d", False, False),
+                                                  ("aniso2d", True, False), ("patch2d", False, True),
+                                                  ("aniso3d", True, True)])
+def test_per_particle_tensors_match_oracle(sph, name, scale, corrected):
+    # reading R32: every particle its own SPD tensor, alone, with diffusivity factors on top
+    # (D_i = s_i Dp_i) and with the kernel-corrected form
+    if name == "patch2d":
+        p = _representable_problem(wk.diffusion_patch(48), mass_jitter=0.1, seed=2)
+        C0 = np.asarray(np.random.default_rng(11).uniform(0.0, 1.0, p.n_fluid), np.float32).astype(np.float64)
+    else:
+        p, _, C0, _ = _case(name)
+    rng = np.random.default_rng(21)
+    d = p.dim
+    A = rng.normal(size=(p.n_fluid, d, d))
+    Dp = 0.3 * (A @ np.swapaxes(A, 1, 2)) + 0.5 * np.eye(d)
+    Dp = 0.5 * (Dp + np.swapaxes(Dp, 1, 2))
+    s = rng.uniform(0.5, 2.0, p.n_fluid).astype(np.float32).astype(np.float64) if scale else None
+    lam = max(float(np.max(np.linalg.eigvalsh(Dp))) * (2.0 if scale else 1.0), 1e-12)
+    dt = 0.1 * p.h ** 2 / lam
+    steps = 10
+    sim = sph.Simulation(p)
+    try:
+        sph.sph_build_cells(sim.handle)
+        sp = sph.sph_species_create(sim.handle, np.eye(d), sim.dim)
+        try:
+            sph.sph_species_set_tensors(sim.handle, sp, Dp)
+            if s is not None:
+                sph.sph_species_set_scale(sim.handle, sp, s)
+            if corrected:
+                sph.sph_species_set_correction(sim.handle, sp, True)
+            bad = Dp.copy()
+            bad[3] = -np.eye(d)
+            with pytest.raises(sph.SphError):          # not positive definite: refused, tensors kept
+                sph.sph_species_set_tensors(sim.handle, sp, bad)
+            sph.sph_species_set(sim.handle, sp, C0)
+            sph.sph_diffusion_step(sim.handle, sp, dt, steps)
+            Cg = sph.sph_species_get(sim.handle, sp, sim.n)
+        finally:
+            sph.sph_species_destroy(sp)
+    finally:
+        sim.close()
+    prm = o.Params.from_problem(p)
+    Co = df.run(p.pos, C0, p.mass, p.rho, np.eye(d), dt, steps, prm, scale=s, corrected=corrected, tensors=Dp)
+    err = np.max(np.abs(Cg - Co))
+    print(f"{name} scale {scale} corrected {corrected}: tensors vs oracle {err:.2e} (bound {_bound(steps, C0, Co):.2e})")
+    assert np.max(np.abs(Co - C0)) > 1e-3
+    assert err <= _bound(steps, C0, Co), (name, err)
+
+
+def test_clearing_tensors_returns_to_the_species_tensor(sph):
+    p, D, C0, dt = _case("aniso2d")
+    sim = sph.Simulation(p)
+    try:
+        sph.sph_build_cells(sim.handle)
+        out = []
+        for with_tensors in (False, True):
+            sp = sph.sph_species_create(sim.handle, D, sim.dim)
+            try:
+                if with_tensors:
+                    sph.sph_species_set_tensors(sim.handle, sp, np.broadcast_to(2.0 * np.eye(2), (p.n_fluid, 2, 2)))
+                    sph.sph_species_set_tensors(sim.handle, sp, None)
+                sph.sph_species_set(sim.handle, sp, C0)
+                sph.sph_diffusion_step(sim.handle, sp, dt, 5)
+                out.append(sph.sph_species_get(sim.handle, sp, sim.n))
+            finally:
+                sph.sph_species_destroy(sp)
+    finally:
+        sim.close()
+    assert np.array_equal(out[0], out[1])
+
+
 def test_uniform_factor_equals_scaled_tensor(sph):
     # a factor equal for every particle matches the tensor scaled by it
     p, D, C0, dt = _case("iso3d")
