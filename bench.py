@@ -43,10 +43,10 @@ TRAFFIC_SOURCE_HASH = "af5377473ba40097"
 
 
 # DRAM bytes (read + write) per particle of one diffusion stage launch, from the ncu capture
-# of k_diffusion_stage on the 120^3 block (both stages, 652.4 and 652.8 MB per launch at 1.728M
+# of k_diffusion_stage on the 120^3 block (both stages, 652.2 and 652.5 MB per launch at 1.728M
 # particles); traffic is per particle on the lattice, so it scales to the 200^3 block.
-DIFF_TRAFFIC_BYTES_PER_PARTICLE = 377.6
-DIFF_TRAFFIC_SOURCE_HASH = "42dfba3e5c8d53e3"
+DIFF_TRAFFIC_BYTES_PER_PARTICLE = 377.5
+DIFF_TRAFFIC_SOURCE_HASH = "36a9a20bee506b41"
 # the stage kernel and its device helpers: the rest of the file (pack/unpack, the reaction
 # step, the host API) does not change the captured launches
 DIFF_SOURCES = ("sph_common.cuh", ("sph_diffusion.cu", "float2 pair_coord2(", "Per call: records of both buffers"))
