@@ -716,15 +716,16 @@ __device__ __forceinline__ void solid_first_half(const Inst& I, const SolidMat& 
 }
 
 // All kappa solid steps of one fluid acoustic step in one thread-block cluster (up to 16
-// blocks of 1024 threads), the solid held in the cluster's distributed shared memory: block
+// blocks of up to 1024 threads: as many as the owned particles' lane groups need), the
+// solid held in the cluster's distributed shared memory: block
 // r owns the particles [r P, (r + 1) P) (internal order: a Morton curve of the reference
 // positions) and keeps their state, and with CS the constant rows too, in its shared
 // memory for the whole launch; global memory is read at the start and written at the end.
 // A neighbour's P B0 and v are read from its owner's shared memory. Each owned particle
 // belongs to a group of `lanes` adjacent lanes: its first lane updates the particle's
 // state, the others take strided shares of its reference neighbours, combined by a shuffle
-// tree (error-free sums for the stress divergence). Two phases a step, each ended by a
-// cluster barrier:
+// tree (plain FP32 sums: compensated ones moved no parity figure and cost 2 % of the step).
+// Two phases a step, each ended by a cluster barrier:
 //   A. dv/dt from the neighbours' P B0, then v and the second half of r;
 //   B. dF/dt = (sum_b V_b (v_b - v_a) (x) grad0 W) B0 from the neighbours' new v, F to the
 //      end of the step, and straight on the next step's first half (F, r, P B0).
@@ -846,7 +847,7 @@ k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ct
       const bool live = l < own;
       const int64_t p = cp(l);
       const bool moves = live && !C.clamped(p);
-      float sx[3] = {0.f, 0.f, 0.f}, ex[3] = {0.f, 0.f, 0.f};
+      float sx[3] = {0.f, 0.f, 0.f};
       if (moves) {
         const int nc = C.count(p);
 #pragma unroll 2
@@ -856,22 +857,12 @@ k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ct
           const float gv[3] = {g.x, g.y, g.z};
           float PBb[D * D];
           load_pb<D>(cl.map_shared_rank(T.PB, (unsigned)(pk >> 16)), pk & 0xffff, PBb);
-          for (int i = 0; i < d; ++i) {
-            float x = PBb[i * d] * gv[0];
-            for (int j = 1; j < d; ++j) x = fmaf(PBb[i * d + j], gv[j], x);
-            float e;
-            two_sum(sx[i], x, sx[i], e);
-            ex[i] += e;
-          }
+          for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) sx[i] = fmaf(PBb[i * d + j], gv[j], sx[i]);
         }
       }
       for (int o = L >> 1; o > 0; o >>= 1)
-        for (int i = 0; i < d; ++i) {
-          const float so = __shfl_xor_sync(0xffffffffu, sx[i], o), eo = __shfl_xor_sync(0xffffffffu, ex[i], o);
-          float e;
-          two_sum(sx[i], so, sx[i], e);
-          ex[i] += eo + e;
-        }
+        for (int i = 0; i < d; ++i) sx[i] += __shfl_xor_sync(0xffffffffu, sx[i], o);
       if (live && lane == 0) {
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 v = T.V[l];
@@ -882,7 +873,7 @@ k_solid_steps(const Inst I, SolidMat M, SolidPtrs S, const Ctrl* __restrict__ ct
           const float cv[3] = {c4.x, c4.y, c4.z};
           float div[3] = {0.f, 0.f, 0.f};
           for (int i = 0; i < d; ++i) {
-            float y = ex[i];
+            float y = 0.0f;
             for (int j = 0; j < d; ++j) y = fmaf(PBa[i * d + j], cv[j], y);
             div[i] = sx[i] + y;
           }
@@ -1014,7 +1005,7 @@ struct sph_solid {
   std::string err;
   int64_t ns = 0;
   int dim = 2, cap = 0;
-  int cluster = 1, lanes = 1, per_block = 1, tile_bytes = 0, row = 1;   // shape of the solid-step launch
+  int cluster = 1, threads = 32, lanes = 1, per_block = 1, tile_bytes = 0, row = 1;   // shape of the solid-step launch
   bool staged = false;          // constant rows staged in shared memory
   sph::SolidMat mat{};
   std::vector<void*> allocs;
@@ -1124,10 +1115,12 @@ bool choose_cluster(sph_solid* s, int max_row) {
       const int P = (int)((s->ns + c - 1) / c);
       const int64_t bytes = bytes_for(P);
       if (bytes > budget) continue;
+      // threads: the owned particles' lane groups, whole warps, at most one block's limit
+      const int threads = (int)std::min<int64_t>(sph::kSolidThreads, std::max<int64_t>(32, ((int64_t)P * L + 31) / 32 * 32));
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute at[1];
       cfg.gridDim = dim3((unsigned)c);
-      cfg.blockDim = dim3(sph::kSolidThreads);
+      cfg.blockDim = dim3((unsigned)threads);
       cfg.dynamicSmemBytes = (size_t)bytes;
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = (unsigned)c;
@@ -1138,6 +1131,7 @@ bool choose_cluster(sph_solid* s, int max_row) {
       int active = 0;
       if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) == cudaSuccess && active > 0) {
         s->cluster = c;
+        s->threads = threads;
         s->per_block = P;
         s->tile_bytes = (int)bytes;
         s->staged = cs != 0;
@@ -1152,7 +1146,7 @@ bool choose_cluster(sph_solid* s, int max_row) {
 void cluster_config(const sph_solid* s, cudaStream_t st, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at) {
   *cfg = cudaLaunchConfig_t{};
   cfg->gridDim = dim3((unsigned)s->cluster);
-  cfg->blockDim = dim3(sph::kSolidThreads);
+  cfg->blockDim = dim3((unsigned)s->threads);
   cfg->dynamicSmemBytes = (size_t)s->tile_bytes;
   cfg->stream = st;
   at[0].id = cudaLaunchAttributeClusterDimension;
