@@ -40,6 +40,9 @@ UNIT = "particle-substeps/s"
 # for the kernel sources whose hash is recorded with it.
 TRAFFIC_BYTES_PER_PARTICLE = 389.79
 TRAFFIC_SOURCE_HASH = "af5377473ba40097"
+# Pipe utilisation of the same kernel from the same full capture (% of peak while active):
+# the FP32 FMA pipe (scalar and packed FP32 FMA/MUL/ADD) and the L1 data pipe that bounds it
+PR_PIPES = {"fp32_fma_pipe": 0.527, "l1_data_pipe": 0.847, "issue_active": 0.556}
 
 
 # DRAM bytes (read + write) per particle of one diffusion stage launch, from the ncu capture
@@ -416,6 +419,8 @@ def run_ours(args, rank, world, local_rank):
             "density_relaxation_ms": ktimes[1] / max(kcount[1], 1),
             "gather_ceiling_ms": gather_ms,
             "frac_of_gather_ceiling": (gather_ms / k7_ms) if kcount[0] else None,
+            "pipes": (dict(PR_PIPES, source="ncu --set full of this kernel at n = 80 (1.02M fluid)")
+                      if traffic is not None else None),
             "launch_ms_from": f"CUDA events on the launching stream around each of the {kcount[0]} "
                               f"launches of {args.kernel_steps} advection steps run right after the "
                               "timed region (host-driven loop, same state and launch variants)"}
