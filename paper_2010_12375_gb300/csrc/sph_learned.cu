@@ -14,9 +14,12 @@
 //   targets [(dv_i - g Dt_ad)/V_S, 100 drho_i/rho0], V_S = |g| Dt_ad (U_ref when g = 0),
 //   loss = mean squared error.
 // Every product rounds its operands to bfloat16 and accumulates in FP32 on the tensor
-// cores (mma.sync m16n8k16). These layers are skinny (64 outputs, K <= 144: ~34 FLOP per
-// byte moved, far below the tensor-core ridge of ~285), so they are bound by HBM and the
-// warp-level MMA is not their limiter. Weight gradients are summed per block and then over
+// cores: the layer-by-layer path (training, and inference when the fused rounds are off)
+// on the fifth-generation tensor cores (tcgen05, 128-row tiles, accumulators in TMEM; see
+// sph_tc.cuh), the fused inference rounds with warp-level mma.sync m16n8k16 (both sum each
+// 16-wide K step in the same order, so the two paths agree bit for bit). These layers are
+// skinny (64 outputs, K <= 144: ~34 FLOP per byte moved, far below the tensor-core ridge of
+// ~285), so unfused they are bound by HBM, not by the MMA. Weight gradients are summed per block and then over
 // blocks in a fixed order and node-embedding gradients of the neighbour gather are summed
 // per node over its reverse edges in edge order, so a training step is deterministic (only
 // the reported loss value is accumulated with atomics).
@@ -31,6 +34,7 @@
 #include "sph.h"
 #include "sph_handle.h"
 #include "sph_kernels.h"
+#include "sph_tc.cuh"
 
 using bf16 = __nv_bfloat16;
 
@@ -73,14 +77,22 @@ __device__ __forceinline__ void mma16816(float* c, uint32_t a0, uint32_t a1, uin
 }
 
 // ------------------------------------------------------------------ dense forward
-// Y = X W^T for M rows. X bf16 [M x K] (row stride ldx), W bf16 [NO x K] row-major. Epilogue
-// per element (m, n < NO): y = acc; y = 0 where mask[m, n] <= 0 (ReLU backward) if mask;
+// Y = X W^T for M rows on the fifth-generation tensor cores (sph_tc.cuh). Each CTA (one
+// warpgroup of 128 threads) keeps W [NO x K] in shared memory in the core-matrix layout and
+// walks 128-row tiles (grid-stride): the tile's rows are copied into the A operand, one
+// thread issues the K/16 MMAs into TMEM, and each warp then reads its 32 rows' accumulators
+// (TMEM lane = row) 16 columns at a time for the epilogue. Epilogue per element
+// (m, n < NO): y = acc; y = 0 where mask[m, n] <= 0 (ReLU backward) if mask;
 // y = max(y, 0) if relu; out_f32[m, n] = y (or += y with accum) for n < nf_store;
-// out_b[m, col0 + n] = bf16(y) for n < nb_store.
-// Each block keeps W in shared memory and walks row tiles of 64 (grid-stride), the next
-// tile's rows streaming in with 16-byte cp.async copies while the current one is
-// multiplied. K, ldx, ldf, ldo, ldm, col0, nf_store and nb_store are multiples of 8 / 2
-// (checked by the host wrapper), so rows move in 16-byte pieces and results in pairs.
+// out_b[m, col0 + n] = bf16(y) for n < nb_store. Copies are shaped for the memory system:
+// a quarter-warp moves one core matrix (8 rows x 16 bytes: one 128-byte shared-memory
+// wavefront, two full global sectors per row pair of pieces), and each warp stages its
+// 32 x 16 block of results in shared memory to store them as 64-byte row segments.
+// K is a multiple of 16, ldx, ldo, col0 and nb_store multiples of 8, ldf and nf_store of 4,
+// ldm of 2 (checked by the host wrapper). A wait for the tensor core that runs out sets
+// ERR_TIMEOUT in *err and the CTA stops.
+constexpr int kDenseStageLd = 17;           // staged row stride (floats): conflict-free columns
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
   const int n = valid ? 16 : 0;                       // 0: fill the 16 bytes with zeros
@@ -89,85 +101,140 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// 16-byte pieces of an R-row operand, [R x K] row-major in global memory (row stride ld
+// elements), into the core-matrix layout: piece (row, kc) by lane (row % 8) + 8 (kc % 4) of a
+// warp-sized block of 8 rows x 4 pieces. Rows at or past rows_valid are zero. ASYNC: by
+// cp.async (zero-filled past rows_valid), completed by the caller's cp_async_wait_all.
+template <bool ASYNC>
+__device__ __forceinline__ void load_operand(unsigned char* dst, int R, int K, const bf16* __restrict__ src,
+                                             int64_t ld, int64_t rows_valid) {
+  const int KC = K / 8, KB = (KC + 3) / 4;           // pieces per row, 4-piece groups
+  const int blocks = (R / 8) * KB;
+  const int lane = threadIdx.x & 31;
+  for (int blk = threadIdx.x >> 5; blk < blocks; blk += blockDim.x >> 5) {
+    const int r = (blk / KB) * 8 + (lane & 7), kc = (blk % KB) * 4 + (lane >> 3);
+    if (kc >= KC) continue;
+    const bool valid = r < rows_valid;
+    unsigned char* d = dst + tc::core_offset(R, r, kc * 8);
+    if (ASYNC) {
+      cp_async16(d, src + (valid ? (int64_t)r * ld : 0) + kc * 8, valid);
+    } else {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (valid) v = *reinterpret_cast<const uint4*>(src + (int64_t)r * ld + kc * 8);
+      *reinterpret_cast<uint4*>(d) = v;
+    }
+  }
+}
+
 template <int NO>
 __global__ void __launch_bounds__(128)
 k_dense(int64_t M, int K, const bf16* __restrict__ X, int ldx, const bf16* __restrict__ W,
         float* __restrict__ out_f32, int ldf, int nf_store, int accum, bf16* __restrict__ out_b, int ldo,
-        int col0, int nb_store, int relu, const bf16* __restrict__ mask, int ldm) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int LD = K + 8;                       // padded row: conflict-free fragment loads
-  bf16* sW = reinterpret_cast<bf16*>(smem_raw);
-  bf16* const sX0 = sW + NO * LD;            // two row-tile buffers of kTile x LD
-  const int64_t tiles = (M + kTile - 1) / kTile;
-  const int chunks = K / 8;                   // 16-byte pieces per row
-  auto load_tile = [&](int64_t tile, bf16* dst) {
-    const int64_t m0 = tile * kTile;
-    for (int idx = threadIdx.x; idx < kTile * chunks; idx += blockDim.x) {
-      const int r = idx / chunks, c = (idx % chunks) * 8;
-      const int64_t m = m0 + r;
-      cp_async16(dst + r * LD + c, X + (m < M ? m : 0) * ldx + c, m < M);
-    }
-    cp_async_commit();
-  };
-  int64_t tile = blockIdx.x;
-  if (tile < tiles) load_tile(tile, sX0);
-  for (int idx = threadIdx.x; idx < NO * chunks; idx += blockDim.x) {
-    const int r = idx / chunks, c = (idx % chunks) * 8;
-    *reinterpret_cast<uint4*>(&sW[r * LD + c]) = *reinterpret_cast<const uint4*>(&W[r * K + c]);
+        int col0, int nb_store, int relu, const bf16* __restrict__ mask, int ldm, int* __restrict__ err) {
+  constexpr int COLS = tc::tmem_cols(NO);
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float stage[4][32 * kDenseStageLd];      // per warp: 32 rows x 16 results
+  unsigned char* sB = tc_smem;                        // NO x K
+  unsigned char* sA0 = tc_smem + NO * K * 2;          // two 128 x K row tiles
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  load_operand<false>(sB, NO, K, W, K, NO);
+  if (threadIdx.x == 0) tc::mbar_init(&bar);
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t b_addr = tc::smem_u32(sB);
+  const int64_t tiles = (M + 127) / 128;
+  float* st = stage[warp];
+  uint32_t phase = 0;
+  if (blockIdx.x < tiles) {                           // the first tile streams in
+    const int64_t m0 = (int64_t)blockIdx.x * 128;
+    load_operand<true>(sA0, 128, K, X + m0 * ldx, ldx, M - m0);
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  for (int buf = 0; tile < tiles; tile += gridDim.x, buf ^= 1) {
+  cp_async_commit();
+  int buf = 0;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, buf ^= 1) {
+    const int64_t m0 = tile * 128;
+    unsigned char* sA = sA0 + buf * 128 * K * 2;
     cp_async_wait_all();
-    __syncthreads();                          // this tile (and W) in place; the other buffer free
-    if (tile + gridDim.x < tiles) load_tile(tile + gridDim.x, sX0 + (buf ^ 1) * kTile * LD);
-    const bf16* sX = sX0 + buf * kTile * LD;
-    float acc[NO / 8][4];
-#pragma unroll
-    for (int nt = 0; nt < NO / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    const bf16* xr0 = sX + (warp * 16 + g) * LD;
-    const bf16* xr1 = xr0 + 8 * LD;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-      const uint32_t a0 = ld_u32(xr0 + k0 + 2 * t), a1 = ld_u32(xr1 + k0 + 2 * t);
-      const uint32_t a2 = ld_u32(xr0 + k0 + 2 * t + 8), a3 = ld_u32(xr1 + k0 + 2 * t + 8);
-#pragma unroll
-      for (int nt = 0; nt < NO / 8; ++nt) {
-        const bf16* wr = sW + (nt * 8 + g) * LD + k0 + 2 * t;
-        mma16816(acc[nt], a0, a1, a2, a3, ld_u32(wr), ld_u32(wr + 8));
-      }
+    tc::fence_to_async();
+    __syncthreads();                                  // this tile in place; the other buffer free
+    const int64_t next = tile + gridDim.x;
+    if (next < tiles)                                 // the next tile streams in meanwhile
+      load_operand<true>(sA0 + (buf ^ 1) * 128 * K * 2, 128, K, X + next * 128 * ldx, ldx, M - next * 128);
+    cp_async_commit();
+    if (threadIdx.x == 0) {
+      tc::fence_after_sync();
+      tc::mma_tile<NO>(tmem, tc::smem_u32(sA), b_addr, K, false, &bar);
     }
-    const int64_t m0 = tile * kTile;
+    const bool done = tc::mbar_wait(&bar, phase);
+    phase ^= 1u;
+    if (!__syncthreads_and(done)) {                   // the same decision in every thread
+      if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+      break;
+    }
+    tc::fence_after_sync();
+    const int64_t mw = m0 + warp * 32;                // this warp's first row
+    const int64_t my = mw + lane;                     // the row whose accumulators this lane reads
+#pragma unroll 1
+    for (int c0 = 0; c0 < NO; c0 += 16) {
+      float y[16];
+      tc::tmem_ld16(tc::tmem_addr(tmem, warp, c0), y);
+      if (mask && my < M) {
 #pragma unroll
-    for (int nt = 0; nt < NO / 8; ++nt)
+        for (int q = 0; q < 16; q += 2) {
+          const uint32_t mk = ld_u32(&mask[my * ldm + c0 + q]);
+          if (!(__bfloat162float(__ushort_as_bfloat16((unsigned short)(mk & 0xffffu))) > 0.f)) y[q] = 0.f;
+          if (!(__bfloat162float(__ushort_as_bfloat16((unsigned short)(mk >> 16))) > 0.f)) y[q + 1] = 0.f;
+        }
+      }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t m = m0 + warp * 16 + g + 8 * h;
-        if (m >= M) continue;
-        const int n = nt * 8 + 2 * t;         // this thread's pair of columns (n, n + 1)
-        float y0 = acc[nt][2 * h], y1 = acc[nt][2 * h + 1];
-        if (mask) {
-          const uint32_t mk = ld_u32(&mask[m * ldm + n]);
-          y0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk & 0xffffu))) > 0.f ? y0 : 0.f;
-          y1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk >> 16))) > 0.f ? y1 : 0.f;
-        }
-        if (relu) {
-          y0 = fmaxf(y0, 0.f);
-          y1 = fmaxf(y1, 0.f);
-        }
-        if (out_f32 && n < nf_store) {
-          float2* o = reinterpret_cast<float2*>(&out_f32[m * ldf + n]);
-          if (accum) {
-            const float2 p = *o;
-            *o = make_float2(p.x + y0, p.y + y1);
-          } else {
-            *o = make_float2(y0, y1);
+      for (int q = 0; q < 16; ++q) st[lane * kDenseStageLd + q] = relu ? fmaxf(y[q], 0.f) : y[q];
+      __syncwarp();
+      if (out_f32 && c0 < nf_store) {                 // 8 rows x 4 float4 pieces per pass
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) {
+          const int r = pass * 8 + (lane >> 2), c = (lane & 3) * 4;
+          const int64_t m = mw + r;
+          if (m < M && c0 + c < nf_store) {
+            const float* v = st + r * kDenseStageLd + c;
+            float4 o = make_float4(v[0], v[1], v[2], v[3]);
+            float4* dst = reinterpret_cast<float4*>(&out_f32[m * ldf + c0 + c]);
+            if (accum) {
+              const float4 p = *dst;
+              o = make_float4(p.x + o.x, p.y + o.y, p.z + o.z, p.w + o.w);
+            }
+            *dst = o;
           }
         }
-        if (out_b && n < nb_store)
-          *reinterpret_cast<uint32_t*>(&out_b[m * ldo + col0 + n]) =
-              pack2(__float2bfloat16_rn(y0), __float2bfloat16_rn(y1));
       }
+      if (out_b && c0 < nb_store) {                   // 16 rows x 2 pieces of 8 bf16 per pass
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          const int r = pass * 16 + (lane >> 1), c = (lane & 1) * 8;
+          const int64_t m = mw + r;
+          if (m < M && c0 + c < nb_store) {
+            const float* v = st + r * kDenseStageLd + c;
+            uint4 o;
+            o.x = pack2(__float2bfloat16_rn(v[0]), __float2bfloat16_rn(v[1]));
+            o.y = pack2(__float2bfloat16_rn(v[2]), __float2bfloat16_rn(v[3]));
+            o.z = pack2(__float2bfloat16_rn(v[4]), __float2bfloat16_rn(v[5]));
+            o.w = pack2(__float2bfloat16_rn(v[6]), __float2bfloat16_rn(v[7]));
+            *reinterpret_cast<uint4*>(&out_b[m * ldo + col0 + c0 + c]) = o;
+          }
+        }
+      }
+      __syncwarp();                                   // the staging block is reused next
+    }
+    tc::fence_before_sync();
+    __syncthreads();                                  // TMEM read and the A tile free before the next
   }
-  cp_async_wait_all();                        // no copy left in flight at exit
+  cp_async_wait_all();                                // no copy left in flight at exit
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, COLS);
 }
 
 // ------------------------------------------------------------------ weight gradient
@@ -792,14 +859,22 @@ __global__ void k_learned_clock(int n_inst, Ctrl* ctrl) {
 }
 
 template <int NO>
-size_t dense_smem(int K) { return (size_t)(NO + 2 * kTile) * (K + 8) * sizeof(bf16); }
+size_t dense_smem(int K) {
+  // W and two A tiles; at least enough that no more CTAs share an SM than its 512 TMEM
+  // columns hold, so a TMEM allocation never waits
+  const size_t need = (size_t)(2 * 128 + NO) * K * sizeof(bf16);
+  const size_t per_sm = 233472;                               // shared memory of an SM
+  const size_t floor = per_sm / (size_t)(512 / tc::tmem_cols(NO) + 1) + 1;
+  return std::max(need, floor);
+}
 
 template <int NO>
 size_t dw_smem(int K) { return (size_t)kTile * ((NO + 8) + (K + 8)) * sizeof(bf16); }
 
 template <int NO>
 void set_smem_attrs() {
-  cudaFuncSetAttribute(k_dense<NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem<NO>(144));
+  cudaFuncSetAttribute(k_dense<NO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)std::max(dense_smem<NO>(144), dense_smem<NO>(16)));
 }
 
 template <int NO>
@@ -822,6 +897,7 @@ struct sph_learned {
   bf16* wbt = nullptr;
   int64_t adam_t = 0;
   bool fused = true;                         // fused edge rounds for inference
+  int* tc_err = nullptr;                     // the handle's device error word (tensor-core waits)
   // workspace
   int64_t cap_n = 0, cap_e = 0;
   uint32_t* cnt = nullptr;
@@ -932,18 +1008,19 @@ int ensure_workspace(sph_learned* L, int64_t n, int64_t E) {
 
 template <int NO>
 void dense(int64_t M, int K, const bf16* X, int ldx, const bf16* W, float* of, int ldf, int nf, int accum,
-           bf16* ob, int ldo, int col0, int nb, int relu, const bf16* mask, int ldm, cudaStream_t s) {
+           bf16* ob, int ldo, int col0, int nb, int relu, const bf16* mask, int ldm, int* err, cudaStream_t s) {
   if (M == 0) return;
-  // rows move as 16-byte pieces and results as pairs: strides and column ranges must allow it
-  if (K % 8 || ldx % 8 || (of && (ldf % 2 || nf % 2)) || (ob && (ldo % 2 || col0 % 2 || nb % 2)) ||
+  // K in MMA steps of 16; rows move as 16-byte pieces, results as 16-byte pieces: strides
+  // and column ranges must allow it
+  if (K % 16 || K > 144 || ldx % 8 || (of && (ldf % 4 || nf % 4)) || (ob && (ldo % 8 || col0 % 8 || nb % 8)) ||
       (mask && ldm % 2)) {
     std::fprintf(stderr, "sph_learned: dense layer with unaligned shape\n");
     return;
   }
-  const int64_t tiles = (M + kTile - 1) / kTile;
-  const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 4);
+  const int64_t tiles = (M + 127) / 128;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 8);
   k_dense<NO><<<grid, 128, dense_smem<NO>(K), s>>>(M, K, X, ldx, W, of, ldf, nf, accum, ob, ldo, col0, nb, relu,
-                                                   mask, ldm);
+                                                   mask, ldm, err);
 }
 
 // grad[layer] += dY^T X over M rows
@@ -1001,12 +1078,13 @@ int build_inputs(sph_handle* h, sph_learned* L, cudaStream_t s) {
 // train: keep every round's edge rows and activations for the backward pass; otherwise
 // (inference) the edge network of each round runs fused when the network allows it.
 void forward(sph_handle* h, sph_learned* L, cudaStream_t s, bool train) {
+  L->tc_err = &h->b.glob->err;
   const int64_t n = h->b.n, E = L->E;
   const int d = h->b.dim, fe = 2 * d + 3;
   const float inv_nbar = 1.0f / nbar(d);
   const bool fused = L->fused && !train;
   // encoder: H = relu(U W_enc^T); H0 keeps h0 for the encoder's backward
-  dense<64>(n, 16, L->U, 16, Wl(L, L_ENC), L->H, F, F, 0, nullptr, 0, 0, 0, 1, nullptr, 0, s);
+  dense<64>(n, 16, L->U, 16, Wl(L, L_ENC), L->H, F, F, 0, nullptr, 0, 0, 0, 1, nullptr, 0, L->tc_err, s);
   if (train) cudaMemcpyAsync(L->H0, L->H, sizeof(float) * n * F, cudaMemcpyDeviceToDevice, s);
   for (int r = 0; r < ROUNDS; ++r) {
     if (fused) {
@@ -1026,21 +1104,22 @@ void forward(sph_handle* h, sph_learned* L, cudaStream_t s, bool train) {
                                                          Wl(L, L_N1), Wl(L, L_N2), inv_nbar, L->XN[r], hout);
     } else {
       if (E > 0) k_edge_rows<<<blocks_for(E * 10), 256, 0, s>>>(E, fe, L->XS, L->enbr, L->H, L->XE[r]);
-      dense<64>(E, 80, L->XE[r], 80, Wl(L, L_E1), nullptr, 0, 0, 0, L->A1[r], 80, 0, F, 1, nullptr, 0, s);
-      dense<64>(E, 80, L->A1[r], 80, Wl(L, L_E2), L->Mbuf, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+      dense<64>(E, 80, L->XE[r], 80, Wl(L, L_E1), nullptr, 0, 0, 0, L->A1[r], 80, 0, F, 1, nullptr, 0, L->tc_err, s);
+      dense<64>(E, 80, L->A1[r], 80, Wl(L, L_E2), L->Mbuf, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
       k_segsum<<<blocks_for(n * F), 256, 0, s>>>(n, L->off, L->Mbuf, L->H, inv_nbar, L->XN[r]);
-      dense<64>(n, 144, L->XN[r], 144, Wl(L, L_N1), nullptr, 0, 0, 0, L->A2[r], 80, 0, F, 1, nullptr, 0, s);
-      dense<64>(n, 80, L->A2[r], 80, Wl(L, L_N2), L->H, F, F, 1, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+      dense<64>(n, 144, L->XN[r], 144, Wl(L, L_N1), nullptr, 0, 0, 0, L->A2[r], 80, 0, F, 1, nullptr, 0, L->tc_err, s);
+      dense<64>(n, 80, L->A2[r], 80, Wl(L, L_N2), L->H, F, F, 1, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
     }
   }
   // the fused rounds leave the final node states in H0 after an odd number of rounds
   const float* hfin = (fused && (ROUNDS & 1)) ? L->H0 : L->H;
   k_rows_bf16<<<blocks_for(n * F), 256, 0, s>>>(n, F, hfin, F, L->XD, 80);
-  dense<64>(n, 80, L->XD, 80, Wl(L, L_D1), nullptr, 0, 0, 0, L->A3, 80, 0, F, 1, nullptr, 0, s);
-  dense<16>(n, 80, L->A3, 80, Wl(L, L_D2), L->Y, 16, 16, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+  dense<64>(n, 80, L->XD, 80, Wl(L, L_D1), nullptr, 0, 0, 0, L->A3, 80, 0, F, 1, nullptr, 0, L->tc_err, s);
+  dense<16>(n, 80, L->A3, 80, Wl(L, L_D2), L->Y, 16, 16, 0, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
 }
 
 void backward(sph_handle* h, sph_learned* L, cudaStream_t s) {
+  L->tc_err = &h->b.glob->err;
   const int64_t n = h->b.n, E = L->E;
   const int d = h->b.dim, fe = 2 * d + 3;
   const float inv_nbar = 1.0f / nbar(d);
@@ -1048,23 +1127,23 @@ void backward(sph_handle* h, sph_learned* L, cudaStream_t s) {
   if (E > 0) k_reverse_edges<<<blocks_for(E), 256, 0, s>>>(E, L->esrc, L->enbr, L->off, L->erev);
   // decoder
   dense_dw<16>(L, L_D2, n, 80, L->dYb, 16, L->A3, 80, s);
-  dense<80>(n, 16, L->dYb, 16, WTl(L, L_D2), nullptr, 0, 0, 0, L->dZn, F, 0, F, 0, L->A3, 80, s);
+  dense<80>(n, 16, L->dYb, 16, WTl(L, L_D2), nullptr, 0, 0, 0, L->dZn, F, 0, F, 0, L->A3, 80, L->tc_err, s);
   dense_dw<64>(L, L_D1, n, 80, L->dZn, F, L->XD, 80, s);
-  dense<80>(n, 64, L->dZn, F, WTl(L, L_D1), L->dH, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+  dense<80>(n, 64, L->dZn, F, WTl(L, L_D1), L->dH, F, F, 0, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
   for (int r = ROUNDS - 1; r >= 0; --r) {
     // h_new = h + W_n2 [relu(W_n1 XN), 1]
     k_rows_bf16<<<blocks_for(n * F), 256, 0, s>>>(n, F, L->dH, F, L->dZn, F);
     dense_dw<64>(L, L_N2, n, 80, L->dZn, F, L->A2[r], 80, s);
     bf16* dZ2 = L->dZe;   // reuse the edge buffer (E >= n)
-    dense<80>(n, 64, L->dZn, F, WTl(L, L_N2), nullptr, 0, 0, 0, dZ2, F, 0, F, 0, L->A2[r], 80, s);
+    dense<80>(n, 64, L->dZn, F, WTl(L, L_N2), nullptr, 0, 0, 0, dZ2, F, 0, F, 0, L->A2[r], 80, L->tc_err, s);
     dense_dw<64>(L, L_N1, n, 144, dZ2, F, L->XN[r], 144, s);
-    dense<144>(n, 64, dZ2, F, WTl(L, L_N1), L->dXN, 144, 144, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+    dense<144>(n, 64, dZ2, F, WTl(L, L_N1), L->dXN, 144, 144, 0, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
     k_node_back<<<blocks_for(n * F), 256, 0, s>>>(n, L->dXN, L->dH);
     if (E > 0) k_edge_back<<<blocks_for(E * F), 256, 0, s>>>(E, L->esrc, L->dXN, inv_nbar, L->dM);
     dense_dw<64>(L, L_E2, E, 80, L->dM, F, L->A1[r], 80, s);
-    dense<80>(E, 64, L->dM, F, WTl(L, L_E2), nullptr, 0, 0, 0, L->dZe, F, 0, F, 0, L->A1[r], 80, s);
+    dense<80>(E, 64, L->dM, F, WTl(L, L_E2), nullptr, 0, 0, 0, L->dZe, F, 0, F, 0, L->A1[r], 80, L->tc_err, s);
     dense_dw<64>(L, L_E1, E, 80, L->dZe, F, L->XE[r], 80, s);
-    dense<80>(E, 64, L->dZe, F, WTl(L, L_E1), L->dXE, 80, 80, 0, nullptr, 0, 0, 0, 0, nullptr, 0, s);
+    dense<80>(E, 64, L->dZe, F, WTl(L, L_E1), L->dXE, 80, 80, 0, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
     if (E > 0) k_gather_dh<<<blocks_for(n * F), 256, 0, s>>>(n, fe, L->off, L->enbr, L->erev, L->dXE, L->dH);
   }
   k_relu_back<<<blocks_for(n * F), 256, 0, s>>>(n, L->dH, L->H0, L->dZn);
