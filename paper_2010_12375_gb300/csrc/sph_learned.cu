@@ -425,252 +425,274 @@ __global__ void k_segsum(int64_t n, const uint32_t* __restrict__ off, const floa
   XN[i * 144 + F + f] = __float2bfloat16_rn(s * inv_nbar);
 }
 
-// ------------------------------------------------------------------ fused edge round (tcgen05)
-// Round input row templates: T[j] is edge row [XS | bf16(h_j) | 1 | 0...] of any edge whose
-// neighbour is fluid node j, with zeros where the static features go; T[n] serves wall
-// neighbours (h = 0). An edge row is its neighbour's template with the static features
-// merged into the first one or two 16-byte pieces. The same launch writes the h part of
-// the round's node rows, XN[i][0, 64) = bf16(h_i). One thread per 16-byte piece.
-template <int FE>
-__global__ void k_node_templates(int64_t n, const float* __restrict__ H, bf16* __restrict__ T,
-                                 bf16* __restrict__ XN) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  __align__(16) bf16 v[8];
-  if (idx < (n + 1) * 10) {
-    const int64_t j = idx / 10;
-    const int c0 = (int)(idx - j * 10) * 8;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int c = c0 + k;
-      float x = 0.f;
-      if (c >= FE && c < FE + F) x = j < n ? H[j * F + (c - FE)] : 0.f;
-      else if (c == FE + F) x = 1.0f;
-      v[k] = __float2bfloat16_rn(x);
-    }
-    *reinterpret_cast<uint4*>(T + j * 80 + c0) = *reinterpret_cast<const uint4*>(v);
-  } else if (idx < (n + 1) * 10 + n * 8) {
-    const int64_t q = idx - (n + 1) * 10, i = q / 8;
-    const int c0 = (int)(q - i * 8) * 8;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = __float2bfloat16_rn(H[i * F + c0 + k]);
-    *reinterpret_cast<uint4*>(XN + i * 144 + c0) = *reinterpret_cast<const uint4*>(v);
-  }
+// Edge network of one round, fused for inference. Each warp takes a run of kFuseNodes
+// nodes and walks their edges in 16-row tiles. The next tile's h_j rows and static edge
+// features are loaded (whole rows, 16-byte pieces) while the current tile is multiplied,
+// and the neighbour indices one tile ahead of that. A tile's A fragments are read from a
+// per-warp staging copy of those rows, column by column as k_edge_rows lays a round input
+// row out (static features, bf16(h_j) or zero for a wall, the bias 1, zero padding). Both
+// edge layers run on the tensor cores (mma.sync m16n8k16, k-steps in k_dense's order; the
+// first layer's accumulators become the second layer's A fragments after k_dense's ReLU
+// and bfloat16 rounding), and the messages are added per node in edge order as k_segsum
+// does. After its edges, the run's node rows go through the node network (both node
+// layers, the update added to h) into the other node-state buffer. XN and the new node
+// states are therefore bit-identical to the unfused path's, and no per-edge row,
+// activation or message goes to memory.
+constexpr int kFuseWarps = 8;
+constexpr int kFuseNodes = 8;
+constexpr int kFuseLd = 88;                   // padded weight row of 80 bf16
+constexpr int kStageLd = 68;                  // staged h row: 64 floats + pad (16-byte rows)
+constexpr int kStageWords = 16 * kStageLd + 16 * 8;   // h rows, then the static features (bf16 pairs)
+constexpr int kMsgLd = 72;                    // message row stride: conflict-free float2 stores
+
+static_assert(16 * kMsgLd <= kStageWords, "messages must fit the staging area");
+
+constexpr int kNodeLd = 152;                  // padded weight row of 144 bf16 (node layer 1)
+
+inline size_t fused_smem() {
+  return (size_t)(3 * 64 * kFuseLd + 64 * kNodeLd) * sizeof(bf16) + (size_t)kFuseWarps * kStageWords * sizeof(float);
 }
 
-// Edge network of one round for inference, on the fifth-generation tensor cores. Each CTA
-// (one warpgroup) takes runs of `run` consecutive nodes and walks their edges in 128-row
-// tiles: the tile's rows are assembled in shared memory (the neighbours' templates by
-// cp.async, the static features merged into the first pieces by plain stores), layer 1
-// multiplies them into TMEM columns [0, 64), each thread turns its row's accumulators into
-// bf16(relu(z)) as layer 2's A operand (with the constant bias column; it reuses the tile's
-// row buffer, free once layer 1 has read it), layer 2 multiplies into columns [64, 128), and
-// the messages are staged 16 columns at a time and added per node in edge order (a node
-// whose edges continue into the next tile carries its partial sums), exactly as k_segsum
-// adds them; closed nodes write XN[i][64, 128) = bf16(a_i). The next tile's rows stream into
-// the other row buffer meanwhile. Every product, rounding and sum is the unfused path's, so
-// XN is bit-identical to it; the node layers then run as the unfused path's dense layers.
-// A wait for the tensor core that runs out sets ERR_TIMEOUT in *err and the CTA stops.
-constexpr int kRunMax = 128;                  // nodes in a run, at most
+// column of slot q (0..19) of a lane with quad index t: k-step q / 4, position q % 4 in
+// {0, 1, 8, 9}
+__device__ __forceinline__ int fuse_col(int q, int t) { return (q >> 2) * 16 + 2 * t + (q & 1) + ((q >> 1) & 1) * 8; }
 
-inline size_t edge_tc_smem() {
-  return (size_t)(2 * 64 * 80 + 2 * 128 * 80) * sizeof(bf16) + 128 * kDenseStageLd * sizeof(float) +
-         2 * 64 * sizeof(float) + (kRunMax + 1) * 4 * sizeof(int) + (kRunMax + 1) * sizeof(uint32_t);
+// B fragments of two n-tiles (nt, nt + 1) at k-step k0 from a row-major [n][kFuseLd] weight
+// copy: lane i addresses row i % 8 of 8x8 matrix i / 8 (matrices: (nt, k0), (nt, k0 + 8),
+// (nt + 1, k0), (nt + 1, k0 + 8)), and receives row lane / 4, columns 2 (lane % 4), +1 of
+// each, which is the m16n8k16 B fragment.
+template <int LD = kFuseLd>
+__device__ __forceinline__ void ldsm_b4(const bf16* W, int nt, int k0, int lane, uint32_t& b0, uint32_t& b1,
+                                        uint32_t& c0, uint32_t& c1) {
+  const int m = lane >> 3;
+  const bf16* p = W + ((nt + (m >> 1)) * 8 + (lane & 7)) * LD + k0 + (m & 1) * 8;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(b0), "=r"(b1), "=r"(c0), "=r"(c1)
+               : "r"(a));
 }
 
-// rows of tile [e0, te) into row buffer A: pieces 2..9 of each neighbour's template by
-// cp.async (zero past te), committed; pieces 0 and 1 of row `tid` returned merged
+// bf16 of column c of a staged row: static feature, h value, bias or zero padding
 template <int FE>
-__device__ __forceinline__ void edge_rows_async(unsigned char* A, uint32_t e0, uint32_t te, int64_t n,
-                                                const int* __restrict__ enbr, const bf16* __restrict__ T,
-                                                const bf16* __restrict__ XS, uint4& q0, uint4& q1) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int blk = warp; blk < 32; blk += 4) {          // 16 row groups x 2 groups of 4 pieces
-    const int r = (blk >> 1) * 8 + (lane & 7), p = 2 + (blk & 1) * 4 + (lane >> 3);
-    const uint32_t e = e0 + (uint32_t)r;
-    const bool valid = e < te;
-    int j = valid ? __ldg(&enbr[e]) : 0;
-    if (j < 0) j = (int)n;                            // walls: the zero template
-    cp_async16(A + tc::core_offset(128, r, p * 8), T + (valid ? (int64_t)j * 80 + p * 8 : 0), valid);
-  }
-  cp_async_commit();
-  const uint32_t e = e0 + threadIdx.x;
-  q0 = make_uint4(0u, 0u, 0u, 0u);
-  q1 = q0;
-  if (e < te) {
-    int j = __ldg(&enbr[e]);
-    if (j < 0) j = (int)n;
-    const uint4* tj = reinterpret_cast<const uint4*>(T + (int64_t)j * 80);
-    const uint4* xs = reinterpret_cast<const uint4*>(XS + (int64_t)e * 16);
-    q0 = __ldg(tj);
-    q1 = __ldg(tj + 1);
-    const uint4 x0 = __ldg(xs), x1 = __ldg(xs + 1);
-    bf16* a = reinterpret_cast<bf16*>(&q0);
-    bf16* b = reinterpret_cast<bf16*>(&q1);
-    const bf16* xa = reinterpret_cast<const bf16*>(&x0);
-    const bf16* xb = reinterpret_cast<const bf16*>(&x1);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (k < FE) a[k] = xa[k];
-      if (8 + k < FE) b[k] = xb[k];
-    }
-  }
+__device__ __forceinline__ bf16 fuse_elem(const float* __restrict__ hrow, const bf16* __restrict__ xrow, int c,
+                                          bool valid) {
+  if (c < FE) return xrow[c];
+  if (c < FE + F) return __float2bfloat16_rn(hrow[c - FE]);
+  return __float2bfloat16_rn(valid && c == FE + F ? 1.0f : 0.f);
 }
 
 template <int FE>
-__global__ void __launch_bounds__(128)
-k_edge_round_tc(int64_t n, int run, const uint32_t* __restrict__ off, const bf16* __restrict__ XS,
-                const int* __restrict__ enbr, const bf16* __restrict__ T, const bf16* __restrict__ W1,
-                const bf16* __restrict__ W2, float inv_nbar, bf16* __restrict__ XN, int* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char tc_smem[];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ uint32_t tmem_slot;
-  __shared__ int list_len, carry_open;
-  unsigned char* sW1 = tc_smem;                       // 64 x 80
-  unsigned char* sW2 = sW1 + 64 * 80 * 2;             // 64 x 80
-  unsigned char* sRows = sW2 + 64 * 80 * 2;           // two 128 x 80 row buffers
-  float* stage = reinterpret_cast<float*>(sRows + 2 * 128 * 80 * 2);   // 128 x 16 messages
-  float* carry_in = stage + 128 * kDenseStageLd;      // partial sums of the node carried into the tile
-  float* carry_out = carry_in + 64;                   // ... and of the node it leaves open
-  int* lnode = reinterpret_cast<int*>(carry_out + 64);   // per node of the tile: id, first row, end row, closes
-  int* lbeg = lnode + (kRunMax + 1);
-  int* lend = lbeg + (kRunMax + 1);
-  int* lclose = lend + (kRunMax + 1);
-  uint32_t* soff = reinterpret_cast<uint32_t*>(lclose + (kRunMax + 1));   // the run's edge offsets
-  const int warp = threadIdx.x >> 5, tid = threadIdx.x;
-  load_operand<false>(sW1, 64, 80, W1, 80, 64);
-  load_operand<false>(sW2, 64, 80, W2, 80, 64);
-  if (tid == 0) {
-    tc::mbar_init(&bar[0]);
-    tc::mbar_init(&bar[1]);
+__global__ void __launch_bounds__(kFuseWarps * 32, 2)
+k_edge_round_fused(int64_t n, const uint32_t* __restrict__ off, const bf16* __restrict__ XS,
+                   const int* __restrict__ enbr, const float* __restrict__ H, const bf16* __restrict__ W1,
+                   const bf16* __restrict__ W2, const bf16* __restrict__ Wn1, const bf16* __restrict__ Wn2,
+                   float inv_nbar, bf16* __restrict__ XN, float* __restrict__ Hout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  bf16* sW1 = reinterpret_cast<bf16*>(smem_raw);
+  bf16* sW2 = sW1 + 64 * kFuseLd;
+  bf16* sN2 = sW2 + 64 * kFuseLd;             // node layer 2, rows of kFuseLd
+  bf16* sN1 = sN2 + 64 * kFuseLd;             // node layer 1, rows of kNodeLd
+  float* stage = reinterpret_cast<float*>(sN1 + 64 * kNodeLd) + warp * kStageWords;   // h rows
+  bf16* xstage = reinterpret_cast<bf16*>(stage + 16 * kStageLd);                       // [16][16]
+  float* sM = stage;                          // the messages reuse the staging rows (16 x kMsgLd)
+  for (int idx = threadIdx.x; idx < 64 * 10; idx += blockDim.x) {
+    const int r = idx / 10, c = (idx % 10) * 8;
+    *reinterpret_cast<uint4*>(&sW1[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&W1[r * 80 + c]);
+    *reinterpret_cast<uint4*>(&sW2[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&W2[r * 80 + c]);
+    *reinterpret_cast<uint4*>(&sN2[r * kFuseLd + c]) = *reinterpret_cast<const uint4*>(&Wn2[r * 80 + c]);
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_slot, 128);
-  tc::fence_before_sync();
+  for (int idx = threadIdx.x; idx < 64 * 18; idx += blockDim.x) {
+    const int r = idx / 18, c = (idx % 18) * 8;
+    *reinterpret_cast<uint4*>(&sN1[r * kNodeLd + c]) = *reinterpret_cast<const uint4*>(&Wn1[r * 144 + c]);
+  }
   __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = tmem_slot;
-  __align__(16) bf16 one[8];                          // layer 2's constant columns: 1 at 64, 0 after
+  const int64_t chunks = (n + kFuseNodes - 1) / kFuseNodes;
+  for (int64_t ch = (int64_t)blockIdx.x * kFuseWarps + warp; ch < chunks; ch += (int64_t)gridDim.x * kFuseWarps) {
+    const int64_t i0 = ch * kFuseNodes, i1 = min(i0 + (int64_t)kFuseNodes, n);
+    const uint32_t e_begin = off[i0], e_end = off[i1];
+    int64_t cur = i0;                         // node whose sum is open
+    uint32_t cur_end = off[cur + 1];
+    float s0 = 0.f, s1 = 0.f;                 // this lane's columns 2 lane, 2 lane + 1
+    // close every node whose edges end at or before edge e (edgeless nodes included)
+    auto close_until = [&](uint32_t e) {
+      while (cur < i1 && cur_end <= e) {
+        const int f = 2 * lane;
+        const float2 hv = *reinterpret_cast<const float2*>(&H[cur * F + f]);
+        *reinterpret_cast<uint32_t*>(&XN[cur * 144 + f]) = pack2(__float2bfloat16_rn(hv.x), __float2bfloat16_rn(hv.y));
+        *reinterpret_cast<uint32_t*>(&XN[cur * 144 + F + f]) =
+            pack2(__float2bfloat16_rn(s0 * inv_nbar), __float2bfloat16_rn(s1 * inv_nbar));
+        s0 = s1 = 0.f;
+        ++cur;
+        if (cur < i1) cur_end = off[cur + 1];
+      }
+    };
+    close_until(e_begin);
+    // neighbour index of row `lane` (lanes 0..15) of the tile at t0, -1 past the end
+    auto idx_of = [&](uint32_t t0) { return lane < 16 && t0 + lane < e_end ? __ldg(&enbr[t0 + lane]) : -1; };
+    // the tile's rows: piece p of lane l is row 2p + l / 16, floats 4 (l % 16) .. + 3
+    float4 hq[8];
+    uint4 xq;
+    auto load_tile = [&](uint32_t t0, int jrow) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) one[k] = __float2bfloat16_rn(k == 0 ? 1.0f : 0.0f);
-  uint32_t phase = 0;                                 // both barriers complete once per tile
-  bool ok = true;
-  const int64_t runs = (n + run - 1) / run;
-  for (int64_t rr = blockIdx.x; rr < runs && ok; rr += gridDim.x) {
-    const int64_t i0 = rr * run, i1 = min(i0 + (int64_t)run, n);
-    const int nodes = (int)(i1 - i0);
-    for (int t = tid; t <= nodes; t += 128) soff[t] = off[i0 + t];
-    __syncthreads();
-    const uint32_t E0 = soff[0], E1 = soff[nodes];
-    int cur = 0;                                      // first node of the run not yet closed
-    if (tid == 0) carry_open = 0;
-    int buf = 0;
-    uint4 q0, q1;
-    if (E0 < E1) edge_rows_async<FE>(sRows, E0, min(E0 + 128u, E1), n, enbr, T, XS, q0, q1);
-    for (uint32_t e0 = E0; e0 < E1; e0 += 128, buf ^= 1) {
-      const uint32_t te = min(e0 + 128u, E1);
-      unsigned char* A = sRows + buf * 128 * 80 * 2;
-      *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, 0)) = q0;
-      *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, 8)) = q1;
-      // the tile's node list (thread 0): from cur, the nodes whose edges start before te (an
-      // edgeless node closes where it sits in edge order; those after the run's last edge
-      // close after its last tile)
-      if (tid == 0) {
-        int len = 0;
-        for (int k = cur; k < nodes && len <= kRunMax; ++k) {
-          const uint32_t kb = soff[k], ke = soff[k + 1];
-          if (kb >= te) break;
-          lnode[len] = k;
-          lbeg[len] = (int)(max(kb, e0) - e0);
-          lend[len] = (int)(min(ke, te) - e0);
-          lclose[len] = ke <= te ? 1 : 0;
-          ++len;
-          if (ke > te) break;                         // continues into the next tile
+      for (int p = 0; p < 8; ++p) {
+        const int row = 2 * p + (lane >> 4);
+        const int j = __shfl_sync(0xffffffffu, jrow, row);
+        hq[p] = (t0 + row < e_end && j >= 0) ? __ldg(reinterpret_cast<const float4*>(&H[(int64_t)j * F]) + (lane & 15))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const int xrow = lane >> 1;
+      xq = t0 + xrow < e_end ? __ldg(reinterpret_cast<const uint4*>(&XS[((int64_t)t0 + xrow) * 16]) + (lane & 1))
+                             : make_uint4(0u, 0u, 0u, 0u);
+    };
+    load_tile(e_begin, idx_of(e_begin));
+    int jn = idx_of(e_begin + 16);
+    for (uint32_t t0 = e_begin; t0 < e_end; t0 += 16) {
+      // stage the current tile's rows and read this lane's A fragments of the first layer
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+        *reinterpret_cast<float4*>(&stage[(2 * p + (lane >> 4)) * kStageLd + 4 * (lane & 15)]) = hq[p];
+      *reinterpret_cast<uint4*>(&xstage[(lane >> 1) * 16 + 8 * (lane & 1)]) = xq;
+      __syncwarp();
+      const bool va = t0 + g < e_end, vb = t0 + g + 8 < e_end;
+      const float* ha = stage + g * kStageLd;
+      const float* hb = ha + 8 * kStageLd;
+      const bf16* xa = xstage + g * 16;
+      const bf16* xb = xa + 8 * 16;
+      uint32_t A[5][4];
+#pragma unroll
+      for (int kk = 0; kk < 5; ++kk) {
+        const int c = kk * 16 + 2 * t;
+        A[kk][0] = pack2(fuse_elem<FE>(ha, xa, c, va), fuse_elem<FE>(ha, xa, c + 1, va));
+        A[kk][1] = pack2(fuse_elem<FE>(hb, xb, c, vb), fuse_elem<FE>(hb, xb, c + 1, vb));
+        A[kk][2] = pack2(fuse_elem<FE>(ha, xa, c + 8, va), fuse_elem<FE>(ha, xa, c + 9, va));
+        A[kk][3] = pack2(fuse_elem<FE>(hb, xb, c + 8, vb), fuse_elem<FE>(hb, xb, c + 9, vb));
+      }
+      __syncwarp();                           // staging read: free for the messages
+      // next tile's rows in flight during this tile's products
+      const uint32_t t1 = t0 + 16;
+      if (t1 < e_end) {
+        load_tile(t1, jn);
+        jn = idx_of(t1 + 16);
+      }
+      float acc[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 5; ++kk)
+#pragma unroll
+        for (int nt = 0; nt < 8; nt += 2) {
+          uint32_t b0, b1, c0, c1;
+          ldsm_b4(sW1, nt, kk * 16, lane, b0, b1, c0, c1);
+          mma16816(acc[nt], A[kk][0], A[kk][1], A[kk][2], A[kk][3], b0, b1);
+          mma16816(acc[nt + 1], A[kk][0], A[kk][1], A[kk][2], A[kk][3], c0, c1);
         }
-        list_len = len;
-      }
-      cp_async_wait_all();
-      tc::fence_to_async();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after_sync();
-        tc::mma_tile<64>(tmem, tc::smem_u32(A), tc::smem_u32(sW1), 80, false, &bar[0]);
-      }
-      // the next tile's rows stream into the other buffer meanwhile (its last reader, the
-      // previous tile's layer 2, has finished)
-      const uint32_t e1 = e0 + 128;
-      if (e1 < E1) edge_rows_async<FE>(sRows + (buf ^ 1) * 128 * 80 * 2, e1, min(e1 + 128u, E1), n, enbr, T, XS, q0, q1);
-      bool done = tc::mbar_wait(&bar[0], phase);
-      if (!__syncthreads_and(done)) {
-        if (tid == 0) atomicOr(err, ERR_TIMEOUT);
-        ok = false;
-        break;
-      }
-      tc::fence_after_sync();
-      // layer 2's A, in this tile's row buffer: bf16(relu(z)) of this thread's row, 1, 0...
-#pragma unroll 1
-      for (int c0 = 0; c0 < 64; c0 += 16) {
-        float z[16];
-        tc::tmem_ld16(tc::tmem_addr(tmem, warp, c0), z);
-        __align__(16) bf16 v[16];
+      // second layer: A = [bf16(relu(z)) | 1 | 0...], z's fragments reused in place
+      float acc2[8][4];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = __float2bfloat16_rn(fmaxf(z[q], 0.f));
-        *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, c0)) = *reinterpret_cast<const uint4*>(v);
-        *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, c0 + 8)) = *reinterpret_cast<const uint4*>(v + 8);
-      }
-      *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, 64)) = *reinterpret_cast<const uint4*>(one);
-      *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, 72)) = make_uint4(0u, 0u, 0u, 0u);
-      tc::fence_to_async();
-      tc::fence_before_sync();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after_sync();
-        tc::mma_tile<64>(tmem + 64, tc::smem_u32(A), tc::smem_u32(sW2), 80, false, &bar[1]);
-      }
-      done = tc::mbar_wait(&bar[1], phase);
-      phase ^= 1u;
-      if (!__syncthreads_and(done)) {
-        if (tid == 0) atomicOr(err, ERR_TIMEOUT);
-        ok = false;
-        break;
-      }
-      tc::fence_after_sync();
-      // messages, 16 columns at a time: staged, then summed per node in edge order
-      const int len = list_len;
-#pragma unroll 1
-      for (int c0 = 0; c0 < 64; c0 += 16) {
-        float m[16];
-        tc::tmem_ld16(tc::tmem_addr(tmem + 64, warp, c0), m);
+      for (int nt = 0; nt < 8; ++nt) acc2[nt][0] = acc2[nt][1] = acc2[nt][2] = acc2[nt][3] = 0.f;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) stage[tid * kDenseStageLd + q] = m[q];
-        __syncthreads();
-        for (int pair = tid; pair < len * 16; pair += 128) {
-          const int li = pair >> 4, q = pair & 15;
-          float sum = (li == 0 && carry_open) ? carry_in[c0 + q] : 0.f;
-          const int rb = lbeg[li], re = lend[li];
-#pragma unroll 4
-          for (int r = rb; r < re; ++r) sum += stage[r * kDenseStageLd + q];
-          if (lclose[li])
-            XN[(i0 + lnode[li]) * 144 + F + c0 + q] = __float2bfloat16_rn(sum * inv_nbar);
-          else
-            carry_out[c0 + q] = sum;
+      for (int kk = 0; kk < 5; ++kk) {
+        uint32_t a0, a1, a2, a3;
+        if (kk < 4) {
+          const float* lo = acc[2 * kk];
+          const float* hi = acc[2 * kk + 1];
+          a0 = pack2(__float2bfloat16_rn(fmaxf(lo[0], 0.f)), __float2bfloat16_rn(fmaxf(lo[1], 0.f)));
+          a1 = pack2(__float2bfloat16_rn(fmaxf(lo[2], 0.f)), __float2bfloat16_rn(fmaxf(lo[3], 0.f)));
+          a2 = pack2(__float2bfloat16_rn(fmaxf(hi[0], 0.f)), __float2bfloat16_rn(fmaxf(hi[1], 0.f)));
+          a3 = pack2(__float2bfloat16_rn(fmaxf(hi[2], 0.f)), __float2bfloat16_rn(fmaxf(hi[3], 0.f)));
+        } else {                              // columns 64..79: the bias column, then zeros
+          a0 = a1 = t == 0 ? pack2(__float2bfloat16_rn(1.0f), __float2bfloat16_rn(0.f)) : 0u;
+          a2 = a3 = 0u;
         }
-        __syncthreads();
+#pragma unroll
+        for (int nt = 0; nt < 8; nt += 2) {
+          uint32_t b0, b1, c0, c1;
+          ldsm_b4(sW2, nt, kk * 16, lane, b0, b1, c0, c1);
+          mma16816(acc2[nt], a0, a1, a2, a3, b0, b1);
+          mma16816(acc2[nt + 1], a0, a1, a2, a3, c0, c1);
+        }
       }
-      if (tid < 64) carry_in[tid] = carry_out[tid];   // read only after the barrier below
-      if (tid == 0) carry_open = (len > 0 && !lclose[len - 1]) ? 1 : 0;
-      if (len > 0) cur = lnode[len - 1] + (lclose[len - 1] ? 1 : 0);
-      tc::fence_before_sync();
-      __syncthreads();
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        *reinterpret_cast<float2*>(&sM[g * kMsgLd + c]) = make_float2(acc2[nt][0], acc2[nt][1]);
+        *reinterpret_cast<float2*>(&sM[(g + 8) * kMsgLd + c]) = make_float2(acc2[nt][2], acc2[nt][3]);
+      }
+      __syncwarp();
+      const int rows = (int)min(16u, e_end - t0);
+      for (int r = 0; r < rows; ++r) {
+        close_until(t0 + (uint32_t)r);
+        const float2 m = *reinterpret_cast<const float2*>(&sM[r * kMsgLd + 2 * lane]);
+        s0 += m.x;
+        s1 += m.y;
+      }
+      __syncwarp();                           // sM free for the next tile's staging
     }
-    if (!ok) break;
-    // nodes left (edgeless ones after the run's last edge): a = 0
-    for (int k = cur + tid / 64; k < nodes; k += 2)
-      XN[(i0 + k) * 144 + F + (tid & 63)] = __float2bfloat16_rn(0.f * inv_nbar);
-    __syncthreads();
+    close_until(e_end);
+    // node network of the run's nodes (the rows of one MMA tile), as the unfused node layers
+    // compute it: z = relu(W_n1 XN), h_out = h + W_n2 [z, 1]
+    __syncwarp();                             // the run's XN rows, written above, visible
+    const int nrows = (int)(i1 - i0);
+    const bool vg = g < nrows, vh = g + 8 < nrows;
+    const bf16* xn = XN + (i0 + g) * 144;
+    const bf16* xh = xn + 8 * 144;
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 9; ++kk) {
+      const uint32_t a0 = vg ? ld_u32(xn + kk * 16 + 2 * t) : 0u;
+      const uint32_t a1 = vh ? ld_u32(xh + kk * 16 + 2 * t) : 0u;
+      const uint32_t a2 = vg ? ld_u32(xn + kk * 16 + 2 * t + 8) : 0u;
+      const uint32_t a3 = vh ? ld_u32(xh + kk * 16 + 2 * t + 8) : 0u;
+#pragma unroll
+      for (int nt = 0; nt < 8; nt += 2) {
+        uint32_t b0, b1, c0, c1;
+        ldsm_b4<kNodeLd>(sN1, nt, kk * 16, lane, b0, b1, c0, c1);
+        mma16816(acc[nt], a0, a1, a2, a3, b0, b1);
+        mma16816(acc[nt + 1], a0, a1, a2, a3, c0, c1);
+      }
+    }
+    float acc2[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) acc2[nt][0] = acc2[nt][1] = acc2[nt][2] = acc2[nt][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 5; ++kk) {
+      uint32_t a0, a1, a2, a3;
+      if (kk < 4) {
+        const float* lo = acc[2 * kk];
+        const float* hi = acc[2 * kk + 1];
+        a0 = pack2(__float2bfloat16_rn(fmaxf(lo[0], 0.f)), __float2bfloat16_rn(fmaxf(lo[1], 0.f)));
+        a1 = pack2(__float2bfloat16_rn(fmaxf(lo[2], 0.f)), __float2bfloat16_rn(fmaxf(lo[3], 0.f)));
+        a2 = pack2(__float2bfloat16_rn(fmaxf(hi[0], 0.f)), __float2bfloat16_rn(fmaxf(hi[1], 0.f)));
+        a3 = pack2(__float2bfloat16_rn(fmaxf(hi[2], 0.f)), __float2bfloat16_rn(fmaxf(hi[3], 0.f)));
+      } else {
+        a0 = a1 = t == 0 ? pack2(__float2bfloat16_rn(1.0f), __float2bfloat16_rn(0.f)) : 0u;
+        a2 = a3 = 0u;
+      }
+#pragma unroll
+      for (int nt = 0; nt < 8; nt += 2) {
+        uint32_t b0, b1, c0, c1;
+        ldsm_b4(sN2, nt, kk * 16, lane, b0, b1, c0, c1);
+        mma16816(acc2[nt], a0, a1, a2, a3, b0, b1);
+        mma16816(acc2[nt + 1], a0, a1, a2, a3, c0, c1);
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int64_t o = (i0 + g) * F + nt * 8 + 2 * t;
+      if (vg) {
+        const float2 h = *reinterpret_cast<const float2*>(&H[o]);
+        *reinterpret_cast<float2*>(&Hout[o]) = make_float2(h.x + acc2[nt][0], h.y + acc2[nt][1]);
+      }
+      if (vh) {
+        const float2 h = *reinterpret_cast<const float2*>(&H[o + 8 * F]);
+        *reinterpret_cast<float2*>(&Hout[o + 8 * F]) = make_float2(h.x + acc2[nt][2], h.y + acc2[nt][3]);
+      }
+    }
+    __syncwarp();
   }
-  cp_async_wait_all();
-  tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, 128);
 }
 
 __global__ void k_rows_bf16(int64_t n, int cols, const float* __restrict__ src, int lds, bf16* __restrict__ dst,
@@ -893,7 +915,6 @@ struct sph_learned {
   float* Mbuf = nullptr;
   float* H = nullptr;
   float* H0 = nullptr;
-  bf16* T = nullptr;                         // [n + 1][80] round input row templates (fused rounds)
   bf16* XD = nullptr;
   bf16* A3 = nullptr;
   float* Y = nullptr;
@@ -950,7 +971,7 @@ int ensure_workspace(sph_learned* L, int64_t n, int64_t E) {
   bool ok = nalloc(L, &L->cnt, n) && nalloc(L, &L->off, n + 1) &&
             nalloc(L, &L->scan_tmp, sph::scan_tmp_elems(n)) && nalloc(L, &L->esrc, E) && nalloc(L, &L->enbr, E) && nalloc(L, &L->XS, E * 16) && nalloc(L, &L->erev, E) &&
             nalloc(L, &L->U, n * 16) && nalloc(L, &L->Mbuf, E * F) && nalloc(L, &L->H, n * F) &&
-            nalloc(L, &L->H0, n * F) && nalloc(L, &L->T, (n + 1) * 80) && nalloc(L, &L->XD, n * 80) && nalloc(L, &L->A3, n * 80) &&
+            nalloc(L, &L->H0, n * F) && nalloc(L, &L->XD, n * 80) && nalloc(L, &L->A3, n * 80) &&
             nalloc(L, &L->Y, n * 16) && nalloc(L, &L->dH, n * F) && nalloc(L, &L->dXN, n * 144) &&
             nalloc(L, &L->dYb, n * 16) && nalloc(L, &L->dZn, n * F) && nalloc(L, &L->dM, E * F) &&
             nalloc(L, &L->dZe, std::max(E, n) * F) && nalloc(L, &L->dXE, E * 80) && nalloc(L, &L->loss, 1) &&
@@ -1067,19 +1088,20 @@ void forward(sph_handle* h, sph_learned* L, cudaStream_t s, bool train) {
   if (train) cudaMemcpyAsync(L->H0, L->H, sizeof(float) * n * F, cudaMemcpyDeviceToDevice, s);
   for (int r = 0; r < ROUNDS; ++r) {
     if (fused) {
-      // the round's node templates, the edge network on the tensor cores, then the node layers
-      auto tmpl = d == 2 ? k_node_templates<7> : k_node_templates<9>;
-      tmpl<<<blocks_for((n + 1) * 10 + n * 8), 256, 0, s>>>(n, L->H, L->T, L->XN[r]);
-      if (n > 0) {
-        const int run = d == 2 ? 64 : 16;               // about 1,280 edges a run
-        const int64_t runs = (n + run - 1) / run;
-        auto kern = d == 2 ? k_edge_round_tc<7> : k_edge_round_tc<9>;
-        const unsigned grid = (unsigned)std::min<int64_t>(runs, 152 * 3);
-        kern<<<grid, 128, edge_tc_smem(), s>>>(n, run, L->off, L->XS, L->enbr, L->T, Wl(L, L_E1), Wl(L, L_E2),
-                                               inv_nbar, L->XN[r], L->tc_err);
-      }
-      dense<64>(n, 144, L->XN[r], 144, Wl(L, L_N1), nullptr, 0, 0, 0, L->A2[r], 80, 0, F, 1, nullptr, 0, L->tc_err, s);
-      dense<64>(n, 80, L->A2[r], 80, Wl(L, L_N2), L->H, F, F, 1, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
+      const int64_t chunks = (n + kFuseNodes - 1) / kFuseNodes;
+      int per_sm = 1, sms = 1, dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      auto kern = d == 2 ? k_edge_round_fused<7> : k_edge_round_fused<9>;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFuseWarps * 32, fused_smem());
+      const unsigned grid = (unsigned)std::min<int64_t>((chunks + kFuseWarps - 1) / kFuseWarps,
+                                                        (int64_t)std::max(per_sm, 1) * sms);
+      // node states ping-pong between H and H0 (H0 is only kept for training's backward)
+      float* hin = (r & 1) ? L->H0 : L->H;
+      float* hout = (r & 1) ? L->H : L->H0;
+      if (n > 0)
+        kern<<<grid, kFuseWarps * 32, fused_smem(), s>>>(n, L->off, L->XS, L->enbr, hin, Wl(L, L_E1), Wl(L, L_E2),
+                                                         Wl(L, L_N1), Wl(L, L_N2), inv_nbar, L->XN[r], hout);
     } else {
       if (E > 0) k_edge_rows<<<blocks_for(E * 10), 256, 0, s>>>(E, fe, L->XS, L->enbr, L->H, L->XE[r]);
       dense<64>(E, 80, L->XE[r], 80, Wl(L, L_E1), nullptr, 0, 0, 0, L->A1[r], 80, 0, F, 1, nullptr, 0, L->tc_err, s);
@@ -1089,7 +1111,9 @@ void forward(sph_handle* h, sph_learned* L, cudaStream_t s, bool train) {
       dense<64>(n, 80, L->A2[r], 80, Wl(L, L_N2), L->H, F, F, 1, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
     }
   }
-  k_rows_bf16<<<blocks_for(n * F), 256, 0, s>>>(n, F, L->H, F, L->XD, 80);
+  // the fused rounds leave the final node states in H0 after an odd number of rounds
+  const float* hfin = (fused && (ROUNDS & 1)) ? L->H0 : L->H;
+  k_rows_bf16<<<blocks_for(n * F), 256, 0, s>>>(n, F, hfin, F, L->XD, 80);
   dense<64>(n, 80, L->XD, 80, Wl(L, L_D1), nullptr, 0, 0, 0, L->A3, 80, 0, F, 1, nullptr, 0, L->tc_err, s);
   dense<16>(n, 80, L->A3, 80, Wl(L, L_D2), L->Y, 16, 16, 0, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
 }
@@ -1216,8 +1240,8 @@ int sph_learned_create(int32_t dim, const float* weights, sph_learned** out) {
   if (!nalloc(L, &L->w32, kWeights) || !nalloc(L, &L->m, kWeights) || !nalloc(L, &L->v, kWeights) ||
       !nalloc(L, &L->grad, kWeights) || !nalloc(L, &L->wb, kWeights) || !nalloc(L, &L->wbt, kWeights))
     return lfail(L, SPH_E_OOM, "device allocation of the weights failed");
-  cudaFuncSetAttribute(k_edge_round_tc<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)edge_tc_smem());
-  cudaFuncSetAttribute(k_edge_round_tc<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)edge_tc_smem());
+  cudaFuncSetAttribute(k_edge_round_fused<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem());
+  cudaFuncSetAttribute(k_edge_round_fused<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem());
   set_smem_attrs<16>();
   set_smem_attrs<64>();
   set_smem_attrs<80>();
