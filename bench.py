@@ -77,6 +77,9 @@ def kernel_source_hash(files=("sph_common.cuh", "sph_relax.cuh", "sph_relax_pr.c
     return h.hexdigest()[:16]
 
 
+NOMINAL_HBM_GBS = 7900.0    # GB300 HBM3e, nominal (context beside the measured copy peak)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -413,6 +416,8 @@ def run_ours(args, rank, world, local_rank):
     gather_ms = sph.sph_gather_ceiling(sim.handle, 10, stream)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "nominal_peak": NOMINAL_HBM_GBS,
+            "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
             "kernel": ("k_pr_half_a<3> + k_pr_half_b<3> (half-pair)" if args.half_pair
                        else "k_pressure_relaxation<3>"), "peak_kind": peak_kind,
             "launch_ms": k7_ms, "algorithmic_bytes_per_launch": k7_bytes,
