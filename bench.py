@@ -751,8 +751,8 @@ def run_learned_step(args, stream):
         sim.step(1)
     ms, _, _ = _timed_steps(sim, args.steps, stream)          # plain steps first, graph loop
     net = sph.sph_learned_create(2, learned.initial_weights(2, seed=0))
-    if args.unfused:                         # the layer-by-layer path (edge rows, dense layers, sums)
-        sph.sph_learned_set_fused(net, False)
+    form = 0 if args.unfused else args.fused_form   # 0: the layer-by-layer path (edge rows, dense layers, sums)
+    sph.sph_learned_set_fused(net, form)
     # every learned step starts from the same state (the untrained network is not meant to be
     # stepped on its own output); only the learned steps are inside the events
     start = sim.state()
@@ -775,7 +775,7 @@ def run_learned_step(args, stream):
            "value": learned_ms, "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "dtype": "bf16 network, f32 solver", "data": "synthetic",
            "config": {"workload": f"2D dam break H=1, L=2, {prob.n_fluid} fluid particles, initial weights",
-                      "edge_rounds": "unfused" if args.unfused else "fused"},
+                      "edge_rounds": ["unfused", "fused, warp-level MMA", "fused, tcgen05 pipeline"][form]},
            "plain_ms_per_step": ms / args.steps}
     print(json.dumps(out), flush=True)
 
@@ -835,6 +835,8 @@ def main():
                     help="untimed advection steps over which the relaxation kernels' launches are timed")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--diff-n", type=int, default=200, help="diffusion3d block: n^3 particles")
+    ap.add_argument("--fused-form", type=int, default=1, choices=[1, 2],
+                    help="learned_step: fused edge rounds on warp-level MMA (1) or the tcgen05 pipeline (2)")
     ap.add_argument("--unfused", action="store_true",
                     help="learned_step: the layer-by-layer path instead of the fused edge rounds")
     ap.add_argument("--corrected", action="store_true",

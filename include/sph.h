@@ -360,9 +360,11 @@ const char* sph_learned_last_error(const sph_learned* net);
 /* Replace the weights (resets the Adam moments) / read them (host or device pointer). */
 int sph_learned_set_weights(sph_learned* net, const float* weights);
 int sph_learned_get_weights(sph_learned* net, float* weights);
-/* Inference (predict, learned step) runs each round's edge network as one fused kernel
- * whose result is bit-identical to the unfused layers that training uses (enabled = 1,
- * the default); enabled = 0 makes inference use the unfused layers as well. */
+/* How inference (predict, learned step) runs each round's edge network. enabled = 1 (the
+ * default): one fused kernel on warp-level tensor-core MMA; 2: a warp-specialised pipeline
+ * on the fifth-generation tensor cores (tcgen05, TMEM accumulators), the node layers then
+ * layer by layer; 0: the unfused layers that training uses. All three give bit-identical
+ * results. Any other value: SPH_E_INVALID, the setting unchanged. */
 int sph_learned_set_fused(sph_learned* net, int32_t enabled);
 /* Network output for the handle's current state, which must be the start of an advection
  * step (sph_build_cells then sph_advection_step). y: [n_fluid * (dim+1)] double, id order,

@@ -695,6 +695,423 @@ k_edge_round_fused(int64_t n, const uint32_t* __restrict__ off, const bf16* __re
   }
 }
 
+// ------------------------------------------------------------------ fused edge round, pipelined (tcgen05)
+// Round input row templates: T[j] is edge row [XS | bf16(h_j) | 1 | 0...] of any edge whose
+// neighbour is fluid node j, with zeros where the static features go; T[n] serves wall
+// neighbours (h = 0). An edge row is its neighbour's template with the static features
+// merged into the first one or two 16-byte pieces. The same launch writes the h part of
+// the round's node rows, XN[i][0, 64) = bf16(h_i). One thread per 16-byte piece.
+template <int FE>
+__global__ void k_node_templates(int64_t n, const float* __restrict__ H, bf16* __restrict__ T,
+                                 bf16* __restrict__ XN) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __align__(16) bf16 v[8];
+  if (idx < (n + 1) * 10) {
+    const int64_t j = idx / 10;
+    const int c0 = (int)(idx - j * 10) * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = c0 + k;
+      float x = 0.f;
+      if (c >= FE && c < FE + F) x = j < n ? H[j * F + (c - FE)] : 0.f;
+      else if (c == FE + F) x = 1.0f;
+      v[k] = __float2bfloat16_rn(x);
+    }
+    *reinterpret_cast<uint4*>(T + j * 80 + c0) = *reinterpret_cast<const uint4*>(v);
+  } else if (idx < (n + 1) * 10 + n * 8) {
+    const int64_t q = idx - (n + 1) * 10, i = q / 8;
+    const int c0 = (int)(q - i * 8) * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __float2bfloat16_rn(H[i * F + c0 + k]);
+    *reinterpret_cast<uint4*>(XN + i * 144 + c0) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// Edge network of one round for inference on the fifth-generation tensor cores, as a
+// warp-specialised pipeline. Each CTA takes runs of at most kWsRun consecutive nodes and
+// walks their edges in 128-row tiles through a ring of kWsStages tile buffers:
+//   warp 4 + p (producer p) assembles the tiles t with t % kWsStages == p in buffer p:
+//     pieces of the neighbours' templates by cp.async, the static features merged into
+//     the first pieces by plain stores; it signals a tile as soon as its copies have landed;
+//   warp 4 + kWsStages (one issuing lane) runs layer 1 of tile t + 1 into TMEM accumulator set
+//     (t + 1) % 2 before layer 2 of tile t, each as K/16 tcgen05.mma (M = 128, N = 64)
+//     committed to an mbarrier; layer 2's commit also frees the tile buffer;
+//   warps 0-3 (epilogue, one TMEM lane = one edge row per thread) turn layer 1's
+//     accumulators of tile t into bf16(relu(z)) and the constant columns, written over the
+//     tile's own buffer as layer 2's A operand; then, while layer 2 of tile t runs, they
+//     stage the messages of tile t - 1 32 columns at a time and add them per node in edge
+//     order (a node whose edges continue into the next tile carries its partial sums);
+//     closed nodes write XN[i][64, 128) = bf16(a_i).
+// Every product, rounding and sum is the layer-by-layer path's, so XN is bit-identical to
+// it; the node layers then run as that path's dense layers. Every wait is bounded: one that
+// runs out sets ERR_TIMEOUT in *err and makes every role stop. On GB300 this pipeline runs
+// the 100,128-particle learned step in 1.17 ms against 1.15 ms for the warp-level MMA rounds
+// (k_edge_round_fused): the epilogue warpgroup's per-node sums and operand conversion,
+// not the tensor core, bound it, so inference keeps the warp-level rounds by default.
+constexpr int kWsStages = 3;
+constexpr int kWsThreads = 128 + 32 * kWsStages + 32;   // warps 0-3 epilogue, one producer per buffer, MMA
+constexpr int kWsMmaWarp = 4 + kWsStages;
+constexpr int kWsRun = 128;                   // nodes in a run, at most
+constexpr int kWsTile = 128 * 80 * 2;         // bytes of one 128-row tile of edge rows
+constexpr int kWsMsgLd = 33;                  // staged message row: 32 floats + pad (conflict-free)
+
+inline size_t ws_smem() {
+  return (size_t)2 * 64 * 80 * 2 + (size_t)kWsStages * kWsTile + 128 * kWsMsgLd * sizeof(float) +
+         2 * 64 * sizeof(float) + (kWsRun + 1) * sizeof(uint32_t);
+}
+
+struct WsSync {
+  uint64_t full[kWsStages], empty[kWsStages];   // tile buffer written / free again
+  uint64_t a1_full[2], a1_empty[2];             // layer-1 accumulators ready / read
+  uint64_t a2_ready[2];                         // layer 2's operand written
+  uint64_t a2_full[2], a2_empty[2];             // layer-2 accumulators ready / read
+  uint64_t fin;                                 // every MMA of the CTA complete
+  int abort;
+};
+
+__device__ __forceinline__ void ws_bar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(tc::smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void ws_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void ws_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(tc::smem_u32(bar))
+               : "memory");
+}
+// Bounded wait for the phase of parity `parity`; gives up when another role has aborted,
+// and aborts every role when it runs out itself.
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* err) {
+  for (unsigned spin = 0; spin < tc::kWaitLimit; ++spin) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(tc::smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+// AND of a flag over the epilogue warpgroup (named barrier 1, 128 threads): the same
+// decision in every epilogue thread
+__device__ __forceinline__ bool epi_all(bool v) {
+  int r;
+  asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\t"
+               "selp.s32 %0, 1, 0, q;\n\t}\n"
+               : "=r"(r)
+               : "r"((int)v)
+               : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
+__device__ __forceinline__ float ld_shared_f32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+// number of epilogue threads whose flag is set (named barrier 1, 128 threads)
+__device__ __forceinline__ int epi_count(bool v) {
+  int r;
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %1, 0;\n\tbar.red.popc.u32 %0, 1, 128, p;\n\t}\n"
+               : "=r"(r)
+               : "r"((int)v)
+               : "memory");
+  return r;
+}
+
+template <int FE>
+__global__ void __launch_bounds__(kWsThreads, 2)
+k_edge_round_ws(int64_t n, int run, const uint32_t* __restrict__ off, const bf16* __restrict__ XS,
+                const int* __restrict__ enbr, const bf16* __restrict__ T, const bf16* __restrict__ W1,
+                const bf16* __restrict__ W2, float inv_nbar, bf16* __restrict__ XN, int* __restrict__ err) {
+  constexpr int MP = (FE + 7) / 8;                    // leading pieces that hold static features
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  __shared__ WsSync S;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int carry_open;
+  unsigned char* sW1 = tc_smem;                       // 64 x 80
+  unsigned char* sW2 = sW1 + 64 * 80 * 2;             // 64 x 80
+  unsigned char* sTiles = sW2 + 64 * 80 * 2;          // kWsStages x (128 x 80)
+  float* stage = reinterpret_cast<float*>(sTiles + kWsStages * kWsTile);   // 128 x 32 messages
+  float* carry_in = stage + 128 * kWsMsgLd;           // partial sums of the node carried into the tile
+  float* carry_out = carry_in + 64;                   // ... and of the node it leaves open
+  uint32_t* soff = reinterpret_cast<uint32_t*>(carry_out + 64);   // the run's edge offsets
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  load_operand<false>(sW1, 64, 80, W1, 80, 64);
+  load_operand<false>(sW2, 64, 80, W2, 80, 64);
+  if (tid == 0) {
+    for (int s = 0; s < kWsStages; ++s) {
+      ws_bar_init(&S.full[s], 1);
+      ws_bar_init(&S.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ws_bar_init(&S.a1_full[b], 1);
+      ws_bar_init(&S.a1_empty[b], 4);             // one arrival per epilogue warp
+      ws_bar_init(&S.a2_ready[b], 4);
+      ws_bar_init(&S.a2_full[b], 1);
+      ws_bar_init(&S.a2_empty[b], 4);
+    }
+    ws_bar_init(&S.fin, 1);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, 256);
+  tc::fence_to_async();                               // the weights, for the tensor core
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_slot;                    // acc1[b] at 64 b, acc2[b] at 128 + 64 b
+  volatile int* abort = &S.abort;
+  const int64_t runs = (n + run - 1) / run;
+
+  if (warp >= 4 && warp < kWsMmaWarp) {
+    // ---------------- producers: warp 4 + p assembles the tiles t with t % kWsStages == p,
+    // always into buffer p, and signals each as soon as its copies have landed
+    const int p = warp - 4;
+    uint32_t t = 0;
+    bool ok = true;
+    for (int64_t rr = blockIdx.x; rr < runs && ok; rr += gridDim.x) {
+      const int64_t i0 = rr * run, i1 = min(i0 + (int64_t)run, n);
+      const uint32_t E0 = __ldg(&off[i0]), E1 = __ldg(&off[i1]);
+      for (uint32_t e0 = E0; e0 < E1; e0 += 128, ++t) {
+        if ((int)(t % kWsStages) != p) continue;
+        const bool got = ws_wait(&S.empty[p], ((t / kWsStages) & 1u) ^ 1u, abort, err);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        const uint32_t te = min(e0 + 128u, E1);
+        unsigned char* A = sTiles + p * kWsTile;
+        // rows lane + 32 k: every load of the tile issued before any is used
+        int jr[4];
+        bool vr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t e = e0 + (uint32_t)(lane + 32 * k);
+          vr[k] = e < te;
+          const int j = vr[k] ? __ldg(&enbr[e]) : 0;
+          jr[k] = j < 0 ? (int)n : j;                 // walls: the zero template
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bf16* tj = T + (int64_t)jr[k] * 80;
+#pragma unroll
+          for (int q = MP; q < 10; ++q)
+            cp_async16(A + tc::core_offset(128, lane + 32 * k, q * 8), vr[k] ? tj + q * 8 : T, vr[k]);
+        }
+        uint4 q[4][MP], x[4][MP];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int c = 0; c < MP; ++c) {
+            q[k][c] = x[k][c] = make_uint4(0u, 0u, 0u, 0u);
+            if (vr[k]) {
+              q[k][c] = __ldg(reinterpret_cast<const uint4*>(T + (int64_t)jr[k] * 80) + c);
+              x[k][c] = __ldg(reinterpret_cast<const uint4*>(XS + (int64_t)(e0 + lane + 32 * k) * 16) + c);
+            }
+          }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int c = 0; c < MP; ++c) {
+            bf16* a = reinterpret_cast<bf16*>(&q[k][c]);
+            const bf16* xa = reinterpret_cast<const bf16*>(&x[k][c]);
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+              if (c * 8 + m < FE) a[m] = xa[m];
+            *reinterpret_cast<uint4*>(A + tc::core_offset(128, lane + 32 * k, c * 8)) = q[k][c];
+          }
+        cp_async_commit();
+        cp_async_wait_all();
+        tc::fence_to_async();
+        __syncwarp();                                 // the warp's copies and stores, then one arrival
+        if (lane == 0) ws_arrive(&S.full[p]);
+      }
+    }
+    cp_async_wait_all();
+  } else if (warp == kWsMmaWarp) {
+    // ---------------- MMA issue (all lanes wait, lane 0 issues)
+    uint32_t TT = 0;
+    for (int64_t rr = blockIdx.x; rr < runs; rr += gridDim.x) {
+      const int64_t i0 = rr * run, i1 = min(i0 + (int64_t)run, n);
+      const uint32_t E0 = __ldg(&off[i0]), E1 = __ldg(&off[i1]);
+      TT += (E1 - E0 + 127u) / 128u;
+    }
+    const uint32_t w1 = tc::smem_u32(sW1), w2 = tc::smem_u32(sW2);
+    auto layer1 = [&](uint32_t t) -> bool {
+      const int s = (int)(t % kWsStages), b = (int)(t & 1u);
+      bool g = ws_wait(&S.full[s], (t / kWsStages) & 1u, abort, err);
+      g = g && ws_wait(&S.a1_empty[b], ((t >> 1) & 1u) ^ 1u, abort, err);
+      if (!__all_sync(0xffffffffu, g)) return false;
+      tc::fence_after_sync();
+      if (lane == 0) tc::mma_tile<64>(tmem + 64 * b, tc::smem_u32(sTiles + s * kWsTile), w1, 80, false, &S.a1_full[b]);
+      __syncwarp();
+      return true;
+    };
+    bool ok = TT == 0 || layer1(0);
+    for (uint32_t t = 0; t < TT && ok; ++t) {
+      if (t + 1 < TT && !layer1(t + 1)) break;
+      const int s = (int)(t % kWsStages), b = (int)(t & 1u);
+      bool g = ws_wait(&S.a2_ready[b], (t >> 1) & 1u, abort, err);
+      g = g && ws_wait(&S.a2_empty[b], ((t >> 1) & 1u) ^ 1u, abort, err);
+      if (!__all_sync(0xffffffffu, g)) break;
+      tc::fence_after_sync();
+      if (lane == 0) {
+        tc::mma_tile<64>(tmem + 128 + 64 * b, tc::smem_u32(sTiles + s * kWsTile), w2, 80, false, &S.a2_full[b]);
+        ws_commit(&S.empty[s]);                       // the tile buffer is free once layer 2 has read it
+      }
+      __syncwarp();
+    }
+    if (lane == 0) ws_commit(&S.fin);                 // every MMA issued above, complete
+    __syncwarp();
+    if (!tc::mbar_wait(&S.fin, 0) && lane == 0) atomicOr(err, ERR_TIMEOUT);
+  } else {
+    // ---------------- epilogue (warps 0-3): the messages of tile t - 1 are summed while
+    // layer 2 of tile t runs (within a run; its last tile is summed before the next run)
+    __align__(16) bf16 one[8];                        // layer 2's constant columns: 1 at 64, 0 after
+#pragma unroll
+    for (int k = 0; k < 8; ++k) one[k] = __float2bfloat16_rn(k == 0 ? 1.0f : 0.0f);
+    uint32_t t = 0;
+    bool ok = true;
+    int cur = 0;                                      // first node of the run not yet closed
+    int64_t i0 = 0;
+    int nodes = 0;
+    // messages of tile u = [e0, te) of the current run, summed per node in edge order. The
+    // tile's nodes are cur, cur + 1, ... while their first edge lies before te (soff never
+    // decreases, so they are the nodes cur + k with soff[cur + k] < te; an edgeless node
+    // closes where it sits in edge order, those after the run's last edge close after its
+    // last tile); a node whose edges run past te stays open and carries its sums.
+    auto messages = [&](uint32_t u, uint32_t e0, uint32_t te) -> bool {
+      const int b = (int)(u & 1u);
+      const int k = cur + tid;
+      const int len = epi_count(k < nodes && soff[k] < te);
+      if (!epi_all(ws_wait(&S.a2_full[b], (u >> 1) & 1u, abort, err))) return false;
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        float m[16];
+        tc::tmem_ld16(tc::tmem_addr(tmem + 128 + 64 * b, warp, c0), m);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) stage[tid * kWsMsgLd + q] = m[q];
+        tc::tmem_ld16(tc::tmem_addr(tmem + 128 + 64 * b, warp, c0 + 16), m);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) stage[tid * kWsMsgLd + 16 + q] = m[q];
+        epi_sync();
+        // two (node, column) sums a thread at a time, each over its rows in edge order, eight
+        // rows' loads in flight (+0 past a node's last row leaves a sum that started at +0
+        // unchanged, bit for bit)
+        for (int p0 = tid; p0 < len * 32; p0 += 256) {
+          const int p1 = p0 + 128;
+          const bool two = p1 < len * 32;
+          const int li0 = p0 >> 5, li1 = two ? p1 >> 5 : li0, q = p0 & 31;
+          const uint32_t kb0 = soff[cur + li0], ke0 = soff[cur + li0 + 1];
+          const uint32_t kb1 = soff[cur + li1], ke1 = soff[cur + li1 + 1];
+          const int rb0 = (int)(max(kb0, e0) - e0), re0 = (int)(min(ke0, te) - e0);
+          const int rb1 = (int)(max(kb1, e0) - e0), re1 = two ? (int)(min(ke1, te) - e0) : rb1;
+          float s0 = (li0 == 0 && carry_open) ? carry_in[c0 + q] : 0.f;
+          float s1 = (li1 == 0 && carry_open) ? carry_in[c0 + q] : 0.f;
+          const uint32_t col = tc::smem_u32(stage + q);
+          for (int r = 0; r < re0 - rb0 || r < re1 - rb1; r += 8) {
+            float v[8], w[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              v[c] = ld_shared_f32(col + 4u * (uint32_t)(min(rb0 + r + c, 127) * kWsMsgLd));
+              w[c] = ld_shared_f32(col + 4u * (uint32_t)(min(rb1 + r + c, 127) * kWsMsgLd));
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              s0 += rb0 + r + c < re0 ? v[c] : 0.f;
+              s1 += rb1 + r + c < re1 ? w[c] : 0.f;
+            }
+          }
+          if (ke0 <= te) XN[(i0 + cur + li0) * 144 + F + c0 + q] = __float2bfloat16_rn(s0 * inv_nbar);
+          else carry_out[c0 + q] = s0;
+          if (two) {
+            if (ke1 <= te) XN[(i0 + cur + li1) * 144 + F + c0 + q] = __float2bfloat16_rn(s1 * inv_nbar);
+            else carry_out[c0 + q] = s1;
+          }
+        }
+        epi_sync();
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) ws_arrive(&S.a2_empty[b]);
+      const bool open = len > 0 && soff[cur + len] > te;   // the tile's last node continues
+      if (tid < 64) carry_in[tid] = carry_out[tid];   // read only after the barrier below
+      if (tid == 0) carry_open = open ? 1 : 0;
+      cur += open ? len - 1 : len;
+      epi_sync();
+      return true;
+    };
+    for (int64_t rr = blockIdx.x; rr < runs && ok; rr += gridDim.x) {
+      i0 = rr * run;
+      const int64_t i1 = min(i0 + (int64_t)run, n);
+      nodes = (int)(i1 - i0);
+      for (int k = tid; k <= nodes; k += 128) soff[k] = off[i0 + k];
+      if (tid == 0) carry_open = 0;
+      epi_sync();
+      const uint32_t E0 = soff[0], E1 = soff[nodes];
+      cur = 0;
+      bool pending = false;                           // a tile whose messages are not summed yet
+      uint32_t pu = 0, pe0 = 0, pte = 0;
+      for (uint32_t e0 = E0; e0 < E1; e0 += 128, ++t) {
+        const uint32_t te = min(e0 + 128u, E1);
+        const int s = (int)(t % kWsStages), b = (int)(t & 1u);
+        unsigned char* A = sTiles + s * kWsTile;
+        // layer 2's A over the tile's rows: bf16(relu(z)) of this thread's row, 1, 0...
+        if (!epi_all(ws_wait(&S.a1_full[b], (t >> 1) & 1u, abort, err))) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+          float z[16];
+          tc::tmem_ld16(tc::tmem_addr(tmem + 64 * b, warp, c0), z);
+          __align__(16) bf16 v[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = __float2bfloat16_rn(fmaxf(z[q], 0.f));
+          *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, c0)) = *reinterpret_cast<const uint4*>(v);
+          *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, c0 + 8)) = *reinterpret_cast<const uint4*>(v + 8);
+        }
+        *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, 64)) = *reinterpret_cast<const uint4*>(one);
+        *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, 72)) = make_uint4(0u, 0u, 0u, 0u);
+        tc::fence_to_async();
+        tc::fence_before_sync();
+        __syncwarp();                                 // the warp's TMEM reads and stores, then one arrival
+        if (lane == 0) {
+          ws_arrive(&S.a1_empty[b]);
+          ws_arrive(&S.a2_ready[b]);
+        }
+        if (pending && !messages(pu, pe0, pte)) {
+          ok = false;
+          break;
+        }
+        pending = true;
+        pu = t;
+        pe0 = e0;
+        pte = te;
+      }
+      if (ok && pending && !messages(pu, pe0, pte)) ok = false;
+      if (!ok) break;
+      // nodes left (edgeless ones after the run's last edge): a = 0
+      for (int k = cur + tid / 64; k < nodes; k += 2)
+        XN[(i0 + k) * 144 + F + (tid & 63)] = __float2bfloat16_rn(0.f * inv_nbar);
+      epi_sync();
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(tmem, 256);
+  }
+}
+
 __global__ void k_rows_bf16(int64_t n, int cols, const float* __restrict__ src, int lds, bf16* __restrict__ dst,
                             int ldd) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -896,7 +1313,7 @@ struct sph_learned {
   bf16* wb = nullptr;
   bf16* wbt = nullptr;
   int64_t adam_t = 0;
-  bool fused = true;                         // fused edge rounds for inference
+  int fused = 1;                             // inference rounds: 0 layer by layer, 1 warp MMA, 2 tcgen05 pipeline
   int* tc_err = nullptr;                     // the handle's device error word (tensor-core waits)
   // workspace
   int64_t cap_n = 0, cap_e = 0;
@@ -907,6 +1324,7 @@ struct sph_learned {
   int* enbr = nullptr;
   bf16* U = nullptr;
   bf16* XS = nullptr;                        // [E][16] static edge features
+  bf16* T = nullptr;                         // [n + 1][80] round input row templates
   int* erev = nullptr;                       // [E] reverse of each fluid edge, -1 for walls
   bf16* XE[ROUNDS] = {nullptr};
   bf16* A1[ROUNDS] = {nullptr};
@@ -975,7 +1393,7 @@ int ensure_workspace(sph_learned* L, int64_t n, int64_t E) {
             nalloc(L, &L->Y, n * 16) && nalloc(L, &L->dH, n * F) && nalloc(L, &L->dXN, n * 144) &&
             nalloc(L, &L->dYb, n * 16) && nalloc(L, &L->dZn, n * F) && nalloc(L, &L->dM, E * F) &&
             nalloc(L, &L->dZe, std::max(E, n) * F) && nalloc(L, &L->dXE, E * 80) && nalloc(L, &L->loss, 1) &&
-            nalloc(L, &L->saveP, n) && nalloc(L, &L->saveV, n);
+            nalloc(L, &L->saveP, n) && nalloc(L, &L->saveV, n) && nalloc(L, &L->T, (n + 1) * 80);
   for (int r = 0; r < ROUNDS && ok; ++r)
     ok = nalloc(L, &L->XE[r], E * 80) && nalloc(L, &L->A1[r], E * 80) && nalloc(L, &L->XN[r], n * 144) &&
          nalloc(L, &L->A2[r], n * 80);
@@ -1082,7 +1500,8 @@ void forward(sph_handle* h, sph_learned* L, cudaStream_t s, bool train) {
   const int64_t n = h->b.n, E = L->E;
   const int d = h->b.dim, fe = 2 * d + 3;
   const float inv_nbar = 1.0f / nbar(d);
-  const bool fused = L->fused && !train;
+  const bool fused = L->fused == 1 && !train;
+  const bool piped = L->fused == 2 && !train;
   // encoder: H = relu(U W_enc^T); H0 keeps h0 for the encoder's backward
   dense<64>(n, 16, L->U, 16, Wl(L, L_ENC), L->H, F, F, 0, nullptr, 0, 0, 0, 1, nullptr, 0, L->tc_err, s);
   if (train) cudaMemcpyAsync(L->H0, L->H, sizeof(float) * n * F, cudaMemcpyDeviceToDevice, s);
@@ -1102,6 +1521,25 @@ void forward(sph_handle* h, sph_learned* L, cudaStream_t s, bool train) {
       if (n > 0)
         kern<<<grid, kFuseWarps * 32, fused_smem(), s>>>(n, L->off, L->XS, L->enbr, hin, Wl(L, L_E1), Wl(L, L_E2),
                                                          Wl(L, L_N1), Wl(L, L_N2), inv_nbar, L->XN[r], hout);
+    } else if (piped) {
+      auto tmpl = d == 2 ? k_node_templates<7> : k_node_templates<9>;
+      tmpl<<<blocks_for((n + 1) * 10 + n * 8), 256, 0, s>>>(n, L->H, L->T, L->XN[r]);
+      if (n > 0) {
+        int sms = 1, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // runs of equal node counts, a whole number of them per CTA where possible
+        const int64_t slots = 2 * (int64_t)sms;
+        const int64_t per = (n + slots * kWsRun - 1) / (slots * kWsRun);
+        const int run = (int)std::max<int64_t>(1, (n + slots * per - 1) / (slots * per));
+        const int64_t runs = (n + run - 1) / run;
+        const unsigned grid = (unsigned)std::min<int64_t>(runs, slots);
+        auto kern = d == 2 ? k_edge_round_ws<7> : k_edge_round_ws<9>;
+        kern<<<grid, kWsThreads, ws_smem(), s>>>(n, run, L->off, L->XS, L->enbr, L->T, Wl(L, L_E1), Wl(L, L_E2),
+                                                 inv_nbar, L->XN[r], L->tc_err);
+      }
+      dense<64>(n, 144, L->XN[r], 144, Wl(L, L_N1), nullptr, 0, 0, 0, L->A2[r], 80, 0, F, 1, nullptr, 0, L->tc_err, s);
+      dense<64>(n, 80, L->A2[r], 80, Wl(L, L_N2), L->H, F, F, 1, nullptr, 0, 0, 0, 0, nullptr, 0, L->tc_err, s);
     } else {
       if (E > 0) k_edge_rows<<<blocks_for(E * 10), 256, 0, s>>>(E, fe, L->XS, L->enbr, L->H, L->XE[r]);
       dense<64>(E, 80, L->XE[r], 80, Wl(L, L_E1), nullptr, 0, 0, 0, L->A1[r], 80, 0, F, 1, nullptr, 0, L->tc_err, s);
@@ -1242,6 +1680,8 @@ int sph_learned_create(int32_t dim, const float* weights, sph_learned** out) {
     return lfail(L, SPH_E_OOM, "device allocation of the weights failed");
   cudaFuncSetAttribute(k_edge_round_fused<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem());
   cudaFuncSetAttribute(k_edge_round_fused<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem());
+  cudaFuncSetAttribute(k_edge_round_ws<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem());
+  cudaFuncSetAttribute(k_edge_round_ws<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem());
   set_smem_attrs<16>();
   set_smem_attrs<64>();
   set_smem_attrs<80>();
@@ -1287,7 +1727,8 @@ int sph_learned_get_weights(sph_learned* L, float* w) {
 
 int sph_learned_set_fused(sph_learned* L, int32_t enabled) {
   if (!L) return SPH_E_INVALID;
-  L->fused = enabled != 0;
+  if (enabled < 0 || enabled > 2) return SPH_E_INVALID;
+  L->fused = enabled;
   return SPH_OK;
 }
 
@@ -1409,3 +1850,4 @@ int sph_learned_step(sph_handle* h, sph_learned* L, double max_mean_rho_dev, dou
 }
 
 }  // extern "C"
+

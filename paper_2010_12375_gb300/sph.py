@@ -524,7 +524,7 @@ def sph_learned_get_weights(net):
 
 def sph_learned_set_fused(net, enabled):
     lib = load()
-    _lcheck(lib, net, lib.sph_learned_set_fused(net, 1 if enabled else 0))
+    _lcheck(lib, net, lib.sph_learned_set_fused(net, int(enabled)))
 
 
 def sph_learned_predict(h, net, n, dim, stream=None):

@@ -82,11 +82,16 @@ def test_forward_matches_reference(sph, dim):
     sim.close()
 
 
+FUSED_FORMS = [1, 2]     # warp-level MMA rounds; tcgen05 pipeline
+
+
+@pytest.mark.parametrize("form", FUSED_FORMS)
 @pytest.mark.parametrize("dim", [2, 3])
-def test_fused_inference_equals_the_unfused_layers(sph, dim):
+def test_fused_inference_equals_the_unfused_layers(sph, dim, form):
     # the fused edge rounds make the same products, roundings and sums in the same order
     prob, state = _case(dim, seed=2)
     net = sph.sph_learned_create(dim, pack(mpnn.init_weights(dim, seed=6)))
+    sph.sph_learned_set_fused(net, form)
     sim, _, _, _, _ = _start_of_step(sph, prob, state)
     y_fused = sph.sph_learned_predict(sim.handle, net, prob.n_fluid, dim)
     sph.sph_learned_set_fused(net, False)
@@ -97,7 +102,16 @@ def test_fused_inference_equals_the_unfused_layers(sph, dim):
     sim.close()
 
 
-def test_fused_inference_with_edgeless_nodes(sph):
+def test_fused_form_outside_the_range_is_rejected(sph):
+    net = sph.sph_learned_create(2, pack(mpnn.init_weights(2, seed=1)))
+    for bad in (-1, 3):
+        with pytest.raises(sph.SphError):
+            sph.sph_learned_set_fused(net, bad)
+    sph.sph_learned_destroy(net)
+
+
+@pytest.mark.parametrize("form", FUSED_FORMS)
+def test_fused_inference_with_edgeless_nodes(sph, form):
     # five particles lifted into the empty upper tank, > 2h from everything: nodes without
     # edges between nodes with edges, in the fused kernel's node runs and edge tiles
     prob, (x, v, rho, drho) = _case(2, seed=4)
@@ -106,6 +120,7 @@ def test_fused_inference_with_edgeless_nodes(sph):
         x[7 * k + 3] = (0.1 + 0.15 * k, 0.8)
     state = representable(prob, x, v, rho, drho)
     net = sph.sph_learned_create(2, pack(mpnn.init_weights(2, seed=8)))
+    sph.sph_learned_set_fused(net, form)
     sim, _, _, _, _ = _start_of_step(sph, prob, state)
     fc, wc, _, _ = sim.neighbours()
     assert np.count_nonzero(fc + wc == 0) >= 5
@@ -117,7 +132,8 @@ def test_fused_inference_with_edgeless_nodes(sph):
     sim.close()
 
 
-def test_fused_inference_single_particle(sph):
+@pytest.mark.parametrize("form", FUSED_FORMS)
+def test_fused_inference_single_particle(sph, form):
     # no edges at all: every round's messages are zero
     prob = wk.dam_break(dim=2, H=0.3, L=0.4, dp=0.02, tank=1.0)
     prob.wall_pos = walls_representable(prob)
@@ -127,6 +143,7 @@ def test_fused_inference_single_particle(sph):
     single.rho = np.array([prob.rho0])
     single.mass = prob.mass[:1]
     net = sph.sph_learned_create(2, pack(mpnn.init_weights(2, seed=9)))
+    sph.sph_learned_set_fused(net, form)
     sim = sph.Simulation(single)
     sim.build_cells()
     sim.advection_step()
