@@ -509,6 +509,9 @@ def run_workload(args):
     if args.workload == "fsi":
         run_fsi(args, stream)
         return
+    if args.workload == "gradients":
+        run_gradients(args, stream)
+        return
     if args.workload == "batched":
         problems = wk.batched_dam_breaks(256)
         name = "256 independent 2D dam breaks (2k-50k fluid each), one handle"
@@ -592,6 +595,60 @@ def run_sizes(args):
            "config": {"workload": "3D dam break 2x1x1 in a 5.366x5.366x1 tank, dp = 1/80, 1/126, 1/159"},
            "value": rows[-1]["value"], "sizes": rows}
     print(json.dumps(out), flush=True)
+
+
+def run_gradients(args, stream):
+    """Strong- and weak-form particle gradients of rho and p (sph_gradient_diagnostics) on the
+    3D dam break after a few advection steps: one call computes all four per fluid particle
+    (the three compensated vector sums over its neighbour row) and exports the weak-form
+    pressure gradient to a device array in caller order (FP64)."""
+    import torch
+    from paper_2010_12375_gb300 import sph, workloads as wk
+    prob = wk.dam_break_3d(args.n)
+    sim = sph.Simulation(prob, flags=sph.SPH_FLAG_GRAPH, stream=stream)
+    for _ in range(3):
+        sim.step(1)
+    sph.sph_build_cells(sim.handle, stream)
+    n = sim.n
+    fluid_pairs, wall_pairs = sph.sph_pair_count(sim.handle, stream)
+    out = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    lib = sph.load()
+
+    def call():
+        sph.check(lib, sim.handle, lib.sph_gradient_diagnostics(sim.handle, None, None, None, sph._ptr(out),
+                                                                 sph._stream(stream)))
+
+    for _ in range(args.warmup):
+        call()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        call()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # algorithmic bytes of one call: the gradient pass reads the particle's 16-byte record,
+    # its count and 4 bytes per neighbour index (neighbour records counted once) and writes
+    # three 16-byte sums; the export reads them and the id and writes 3 doubles
+    nbar = (fluid_pairs + wall_pairs) / n
+    per_particle = 16 + 4 + 4 * nbar + 48 + (48 + 4 + 24)
+    peak, peak_kind = measured_peaks()
+    achieved = per_particle * n / (ms * 1e-3) / 1e9
+    sim.close()
+    print(json.dumps({
+        "metric": "particle gradient diagnostics, 3D dam break", "value": n / (ms * 1e-3),
+        "unit": "particles/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_call": ms, "dtype": "f32 sums, f64 export", "data": "synthetic",
+        "config": {"workload": f"3D dam break, dp = 1/{args.n}, {n} fluid particles, n_bar = {nbar:.1f}",
+                   "fields": "grad rho and grad p, strong and weak (one call), weak grad p exported"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_particle": per_particle},
+        "clocks": clk}), flush=True)
 
 
 def run_diffusion(args, stream):
@@ -849,7 +906,7 @@ def main():
                     help="the frozen-pair-geometry reading (pair vectors kept from the configuration update)")
     ap.add_argument("--launch-config", default=None,
                     help="pr_tpp,pr_block,dr_tpp,dr_block: fixed launch variants instead of autotuning")
-    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes", "diffusion3d", "fsi"],
+    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes", "diffusion3d", "fsi", "gradients"],
                     help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()
     if args.warmup < 3:
