@@ -87,11 +87,19 @@ __device__ __forceinline__ void mma16816(float* c, uint32_t a0, uint32_t a1, uin
 // out_b[m, col0 + n] = bf16(y) for n < nb_store. Copies are shaped for the memory system:
 // a quarter-warp moves one core matrix (8 rows x 16 bytes: one 128-byte shared-memory
 // wavefront, two full global sectors per row pair of pieces), and each warp stages its
-// 32 x 16 block of results in shared memory to store them as 64-byte row segments.
+// 32 x 16 block of results in shared memory (in the tile the tensor core has just read, so
+// the staging costs no shared memory of its own) to store them as 64-byte row segments.
 // K is a multiple of 16, ldx, ldo, col0 and nb_store multiples of 8, ldf and nf_store of 4,
 // ldm of 2 (checked by the host wrapper). A wait for the tensor core that runs out sets
 // ERR_TIMEOUT in *err and the CTA stops.
 constexpr int kDenseStageLd = 17;           // staged row stride (floats): conflict-free columns
+
+// shared memory of k_dense: W, then two row tiles of 128 x K, each large enough to serve as
+// the four warps' staging blocks once the tensor core has read it
+__host__ __device__ constexpr int dense_w_bytes(int NO, int K) { return (NO * K * 2 + 127) / 128 * 128; }
+__host__ __device__ constexpr int dense_tile_bytes(int K) {
+  return ((128 * K * 2 > 4 * 32 * kDenseStageLd * 4 ? 128 * K * 2 : 4 * 32 * kDenseStageLd * 4) + 127) / 128 * 128;
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
@@ -135,9 +143,9 @@ k_dense(int64_t M, int K, const bf16* __restrict__ X, int ldx, const bf16* __res
   extern __shared__ __align__(128) unsigned char tc_smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ float stage[4][32 * kDenseStageLd];      // per warp: 32 rows x 16 results
   unsigned char* sB = tc_smem;                        // NO x K
-  unsigned char* sA0 = tc_smem + NO * K * 2;          // two 128 x K row tiles
+  const int tile_bytes = dense_tile_bytes(K);
+  unsigned char* sA0 = tc_smem + dense_w_bytes(NO, K);   // two 128 x K row tiles
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_operand<false>(sB, NO, K, W, K, NO);
   if (threadIdx.x == 0) tc::mbar_init(&bar);
@@ -148,7 +156,6 @@ k_dense(int64_t M, int K, const bf16* __restrict__ X, int ldx, const bf16* __res
   const uint32_t tmem = tmem_slot;
   const uint32_t b_addr = tc::smem_u32(sB);
   const int64_t tiles = (M + 127) / 128;
-  float* st = stage[warp];
   uint32_t phase = 0;
   if (blockIdx.x < tiles) {                           // the first tile streams in
     const int64_t m0 = (int64_t)blockIdx.x * 128;
@@ -156,15 +163,16 @@ k_dense(int64_t M, int K, const bf16* __restrict__ X, int ldx, const bf16* __res
   }
   cp_async_commit();
   int buf = 0;
+  float* st = nullptr;                                // this warp's staging block, in the tile just multiplied
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, buf ^= 1) {
     const int64_t m0 = tile * 128;
-    unsigned char* sA = sA0 + buf * 128 * K * 2;
+    unsigned char* sA = sA0 + buf * tile_bytes;
     cp_async_wait_all();
     tc::fence_to_async();
     __syncthreads();                                  // this tile in place; the other buffer free
     const int64_t next = tile + gridDim.x;
     if (next < tiles)                                 // the next tile streams in meanwhile
-      load_operand<true>(sA0 + (buf ^ 1) * 128 * K * 2, 128, K, X + next * 128 * ldx, ldx, M - next * 128);
+      load_operand<true>(sA0 + (buf ^ 1) * tile_bytes, 128, K, X + next * 128 * ldx, ldx, M - next * 128);
     cp_async_commit();
     if (threadIdx.x == 0) {
       tc::fence_after_sync();
@@ -177,6 +185,7 @@ k_dense(int64_t M, int K, const bf16* __restrict__ X, int ldx, const bf16* __res
       break;
     }
     tc::fence_after_sync();
+    st = reinterpret_cast<float*>(sA) + warp * 32 * kDenseStageLd;   // the tensor core is done with the tile
     const int64_t mw = m0 + warp * 32;                // this warp's first row
     const int64_t my = mw + lane;                     // the row whose accumulators this lane reads
 #pragma unroll 1
@@ -1279,7 +1288,7 @@ template <int NO>
 size_t dense_smem(int K) {
   // W and two A tiles; at least enough that no more CTAs share an SM than its 512 TMEM
   // columns hold, so a TMEM allocation never waits
-  const size_t need = (size_t)(2 * 128 + NO) * K * sizeof(bf16);
+  const size_t need = (size_t)dense_w_bytes(NO, K) + 2 * (size_t)dense_tile_bytes(K);
   const size_t per_sm = 233472;                               // shared memory of an SM
   const size_t floor = per_sm / (size_t)(512 / tc::tmem_cols(NO) + 1) + 1;
   return std::max(need, floor);

@@ -102,6 +102,27 @@ def test_fused_inference_equals_the_unfused_layers(sph, dim, form):
     sim.close()
 
 
+def test_all_forms_agree_bit_for_bit_at_100k_particles(sph):
+    # 2M edges: every dense-layer CTA walks several 128-row tiles (both tile buffers), and the
+    # fused kernels run many node runs per CTA; the three forms must agree exactly
+    from paper_2010_12375_gb300 import learned
+    prob = wk.learned_dam_break()
+    sim = sph.Simulation(prob, flags=sph.SPH_FLAG_GRAPH)
+    sim.step(2)
+    sim.build_cells()
+    sim.advection_step()
+    net = sph.sph_learned_create(2, learned.initial_weights(2, seed=0))
+    ys = []
+    for form in (0, 1, 2):
+        sph.sph_learned_set_fused(net, form)
+        ys.append(sph.sph_learned_predict(sim.handle, net, prob.n_fluid, 2))
+    assert np.all(np.isfinite(ys[0])) and np.abs(ys[0]).max() > 0
+    np.testing.assert_array_equal(ys[1], ys[0])
+    np.testing.assert_array_equal(ys[2], ys[0])
+    sph.sph_learned_destroy(net)
+    sim.close()
+
+
 def test_fused_form_outside_the_range_is_rejected(sph):
     net = sph.sph_learned_create(2, pack(mpnn.init_weights(2, seed=1)))
     for bad in (-1, 3):
