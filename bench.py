@@ -407,6 +407,11 @@ def run_ours(args, rank, world, local_rank):
         # the frozen reading also streams one 16-byte pair record per neighbour slot
         k7_bytes += 16 * (fluid_pairs + wall_pairs)
     achieved = k7_bytes / (k7_ms * 1e-3) / 1e9 if kcount[0] else None
+    k8_bytes = N * (28 + 20 + 4) + 4 * (fluid_pairs + wall_pairs)
+    if args.frozen:
+        k8_bytes += 16 * (fluid_pairs + wall_pairs)
+    k8_ms = ktimes[1] / max(kcount[1], 1)
+    k8_achieved = (k8_bytes / (k8_ms * 1e-3) / 1e9) if (kcount[1] and not args.half_pair) else None
     traffic = None
     if (TRAFFIC_BYTES_PER_PARTICLE is not None and TRAFFIC_SOURCE_HASH == kernel_source_hash()
             and not args.frozen and not args.half_pair):
@@ -422,6 +427,10 @@ def run_ours(args, rank, world, local_rank):
                        else "k_pressure_relaxation<3>"), "peak_kind": peak_kind,
             "launch_ms": k7_ms, "algorithmic_bytes_per_launch": k7_bytes,
             "density_relaxation_ms": ktimes[1] / max(kcount[1], 1),
+            # the density relaxation against the same peak: state read 28 B + write 20 B per
+            # particle, count 4 B, 4 B per neighbour index
+            "density_relaxation": ({"algorithmic_bytes_per_launch": k8_bytes, "achieved": k8_achieved,
+                                    "frac": k8_achieved / peak, "unit": "GB/s"} if k8_achieved else None),
             "gather_ceiling_ms": gather_ms,
             "frac_of_gather_ceiling": (gather_ms / k7_ms) if kcount[0] else None,
             "pipes": (dict(PR_PIPES, source="ncu --set full of this kernel at n = 80 (1.02M fluid)")
