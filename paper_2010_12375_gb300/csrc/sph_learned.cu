@@ -765,8 +765,11 @@ constexpr int kWsTile = 128 * 80 * 2;         // bytes of one 128-row tile of ed
 constexpr int kWsMsgLd = 33;                  // staged message row: 32 floats + pad (conflict-free)
 
 inline size_t ws_smem() {
-  return (size_t)2 * 64 * 80 * 2 + (size_t)kWsStages * kWsTile + 128 * kWsMsgLd * sizeof(float) +
-         2 * 64 * sizeof(float) + (kWsRun + 1) * sizeof(uint32_t);
+  // at least a third of an SM's shared memory, so that no more than two CTAs (256 TMEM
+  // columns each) share an SM and a TMEM allocation never waits
+  const size_t need = (size_t)2 * 64 * 80 * 2 + (size_t)kWsStages * kWsTile + 128 * kWsMsgLd * sizeof(float) +
+                      2 * 64 * sizeof(float) + (kWsRun + 1) * sizeof(uint32_t);
+  return std::max(need, (size_t)233472 / 3 + 1);
 }
 
 struct WsSync {
