@@ -762,7 +762,7 @@ constexpr int kWsThreads = 128 + 32 * kWsStages + 32;   // warps 0-3 epilogue, o
 constexpr int kWsMmaWarp = 4 + kWsStages;
 constexpr int kWsRun = 128;                   // nodes in a run, at most
 constexpr int kWsTile = 128 * 80 * 2;         // bytes of one 128-row tile of edge rows
-constexpr int kWsMsgLd = 33;                  // staged message row: 32 floats + pad (conflict-free)
+constexpr int kWsMsgLd = 36;                  // staged message row: 32 floats + pad (16-byte rows, conflict-free)
 
 inline size_t ws_smem() {
   // at least a third of an SM's shared memory, so that no more than two CTAs (256 TMEM
@@ -1008,10 +1008,12 @@ k_edge_round_ws(int64_t n, int run, const uint32_t* __restrict__ off, const bf16
         float m[16];
         tc::tmem_ld16(tc::tmem_addr(tmem + 128 + 64 * b, warp, c0), m);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) stage[tid * kWsMsgLd + q] = m[q];
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4*>(&stage[tid * kWsMsgLd + q]) = make_float4(m[q], m[q + 1], m[q + 2], m[q + 3]);
         tc::tmem_ld16(tc::tmem_addr(tmem + 128 + 64 * b, warp, c0 + 16), m);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) stage[tid * kWsMsgLd + 16 + q] = m[q];
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4*>(&stage[tid * kWsMsgLd + 16 + q]) = make_float4(m[q], m[q + 1], m[q + 2], m[q + 3]);
         epi_sync();
         // two (node, column) sums a thread at a time, each over its rows in edge order, eight
         // rows' loads in flight (+0 past a node's last row leaves a sum that started at +0
@@ -1084,11 +1086,11 @@ k_edge_round_ws(int64_t n, int run, const uint32_t* __restrict__ off, const bf16
         for (int c0 = 0; c0 < 64; c0 += 16) {
           float z[16];
           tc::tmem_ld16(tc::tmem_addr(tmem + 64 * b, warp, c0), z);
-          __align__(16) bf16 v[16];
+          __align__(16) __nv_bfloat162 v[8];         // pairs rounded by one packed conversion each
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = __float2bfloat16_rn(fmaxf(z[q], 0.f));
+          for (int q = 0; q < 8; ++q) v[q] = __floats2bfloat162_rn(fmaxf(z[2 * q], 0.f), fmaxf(z[2 * q + 1], 0.f));
           *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, c0)) = *reinterpret_cast<const uint4*>(v);
-          *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, c0 + 8)) = *reinterpret_cast<const uint4*>(v + 8);
+          *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, c0 + 8)) = *reinterpret_cast<const uint4*>(v + 4);
         }
         *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, 64)) = *reinterpret_cast<const uint4*>(one);
         *reinterpret_cast<uint4*>(A + tc::core_offset(128, tid, 72)) = make_uint4(0u, 0u, 0u, 0u);
