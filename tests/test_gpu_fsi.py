@@ -103,6 +103,36 @@ def _coupled_substep_against_oracle(sph, wl, prm, label):
     assert np.max(np.abs(disp_g - disp_o)) < 2 * kappa * dq + 1e-6 * np.max(np.abs(disp_o))
 
 
+def _fluid_above(wl, gap):
+    """The workload with only the fluid lying more than `gap` above the plate's top."""
+    keep = wl.pos[:, 1] > np.max(wl.solid_pos[:, 1]) + gap
+    out = copy.copy(wl)
+    out.pos, out.vel, out.rho, out.mass = wl.pos[keep], wl.vel[keep], wl.rho[keep], wl.mass[keep]
+    return out
+
+
+def test_solid_out_of_the_fluids_reach(sph):
+    # degenerate coupling: no fluid particle within reach of the plate (the gap is four
+    # fluid smoothing lengths, twice the support): no coupling pair anywhere, the plate
+    # moves under gravity alone, and the fluid steps exactly as it does without a solid
+    wl, prm = _prepared(2)
+    wl = _fluid_above(wl, 4 * wl.h)
+    _coupled_substep_against_oracle(sph, wl, prm, "fluid out of reach")
+    runs = []
+    for with_solid in (True, False):
+        sim = sph.Simulation(wl, flags=sph.SPH_FLAG_GRAPH)
+        solid = sph.solid_from(sim, wl) if with_solid else None
+        sim.step(3)
+        runs.append(sim.state())
+        if with_solid:
+            sg = sph.sph_solid_get_state(sim.handle, solid)
+            assert np.all(sg["force"] == 0.0) and sg["solid_steps"] > 0
+            sph.sph_solid_destroy(solid)
+        sim.close()
+    for a, b in zip(runs[0], runs[1]):
+        np.testing.assert_array_equal(a, b)
+
+
 @pytest.mark.slow
 def test_plate_deflection_follows_the_oracle():
     pytest.importorskip("scipy")
