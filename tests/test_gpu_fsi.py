@@ -170,6 +170,11 @@ def test_solid_refuses_bad_arguments(sph):
     with pytest.raises(sph.SphError):                      # Poisson ratio out of range
         sph.sph_solid_create(sim.handle, 1, 2.7, 4.5e4, 0.5, wl.solid_h, wl.solid_pos, wl.solid_vol,
                              wl.solid_normal, wl.solid_fixed)
+    for count in (0, 16385):                               # particle count outside [1, 16384]
+        idx = np.arange(count) % wl.solid_pos.shape[0]
+        with pytest.raises(sph.SphError):
+            sph.sph_solid_create(sim.handle, 1, 2.7, 4.5e4, 0.3, wl.solid_h, wl.solid_pos[idx], wl.solid_vol[idx],
+                                 wl.solid_normal[idx], None if wl.solid_fixed is None else wl.solid_fixed[idx])
     s1 = sph.solid_from(sim, wl)
     with pytest.raises(sph.SphError):                      # one solid per handle
         sph.solid_from(sim, wl)
