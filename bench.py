@@ -521,6 +521,9 @@ def run_workload(args):
     if args.workload == "gradients":
         run_gradients(args, stream)
         return
+    if args.workload == "beam":
+        run_beam(args, stream)
+        return
     if args.workload == "batched":
         problems = wk.batched_dam_breaks(256)
         name = "256 independent 2D dam breaks (2k-50k fluid each), one handle"
@@ -604,6 +607,65 @@ def run_sizes(args):
            "config": {"workload": "3D dam break 2x1x1 in a 5.366x5.366x1 tank, dp = 1/80, 1/126, 1/159"},
            "value": rows[-1]["value"], "sizes": rows}
     print(json.dumps(out), flush=True)
+
+
+def run_beam(args, stream):
+    """The paper's oscillating beam with the solid alone: a 2D cantilever 0.2 long and 0.02
+    thick (10 particles across, 1,040 particles) loaded suddenly by its own weight. One run
+    samples the tip after every fluid substep (host loop) for the first bending period against
+    the clamped-free Euler-Bernoulli period; a second run times 1.5 s of simulated time through
+    the CUDA-graph loop: solid particle-steps per second."""
+    import torch
+    from paper_2010_12375_gb300 import sph, workloads as wk
+    wl = wk.cantilever_beam(ds=0.002)
+    T = 1.5
+    x0 = wl.solid_pos
+    tip = int(np.argmax(x0[:, 0] + 1e-6 * x0[:, 1]))
+    sim = sph.Simulation(wl, stream=stream)
+    solid = sph.solid_from(sim, wl)
+    t, ts, ys, n_adv = 0.0, [], [], 0
+    while t < T:
+        sim.build_cells()
+        sim.advection_step()
+        n_adv += 1
+        done = False
+        while not done:
+            done, dt = sim.acoustic_substep()
+            t += dt
+            ts.append(t)
+            ys.append(sph.sph_solid_get_state(sim.handle, solid)["pos"][tip, 1] - x0[tip, 1])
+    sph.sph_solid_destroy(solid)
+    sim.close()
+    ts, ys = np.asarray(ts), np.asarray(ys) - np.mean(ys)
+    i = np.nonzero((ys[:-1] < 0.0) & (ys[1:] >= 0.0))[0]
+    cr = ts[i] - ys[i] * (ts[i + 1] - ts[i]) / (ys[i + 1] - ys[i])
+    period = (cr[-1] - cr[0]) / (len(cr) - 1)
+    sim = sph.Simulation(wl, flags=sph.SPH_FLAG_GRAPH, stream=stream)
+    solid = sph.solid_from(sim, wl)
+    sim.step(args.warmup)
+    s0 = sph.sph_solid_get_state(sim.handle, solid)["solid_steps"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = n_adv                                      # the advection steps of the sampled run
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    sim.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    n_solid_steps = sph.sph_solid_get_state(sim.handle, solid)["solid_steps"] - s0
+    sph.sph_solid_destroy(solid)
+    sim.close()
+    ns = x0.shape[0]
+    print(json.dumps({
+        "metric": "oscillating cantilever, solid alone: solid particle-steps/s", "value": ns * n_solid_steps / (ms * 1e-3),
+        "unit": "particle-steps/s", "higher_is_better": True, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"2D cantilever 0.2 x 0.02, {ns} particles (10 across), E = 2e6, nu = 0.3, rho = 1000, "
+                               f"loaded by its weight (g = 1) from rest",
+                   "simulated_s": T},
+        "us_per_solid_step": 1e3 * ms / max(n_solid_steps, 1), "solid_steps": int(n_solid_steps),
+        "first_period_s": period, "period_euler_bernoulli_s": wl.meta["period_eb"],
+        "period_ratio": period / wl.meta["period_eb"]}), flush=True)
 
 
 def run_gradients(args, stream):
@@ -915,7 +977,7 @@ def main():
                     help="the frozen-pair-geometry reading (pair vectors kept from the configuration update)")
     ap.add_argument("--launch-config", default=None,
                     help="pr_tpp,pr_block,dr_tpp,dr_block: fixed launch variants instead of autotuning")
-    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes", "diffusion3d", "fsi", "gradients"],
+    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes", "diffusion3d", "fsi", "gradients", "beam"],
                     help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -164,6 +164,76 @@ def test_plate_deflection_follows_the_oracle():
     assert err < 5e-3
 
 
+def _up_crossing_period(ts, ys):
+    """Period of an oscillation from the upward crossings of its mean (linear interpolation
+    between samples; crossings of one direction only, so an offset of the mean cancels)."""
+    ts, ys = np.asarray(ts), np.asarray(ys) - np.mean(ys)
+    i = np.nonzero((ys[:-1] < 0.0) & (ys[1:] >= 0.0))[0]
+    cr = ts[i] - ys[i] * (ts[i + 1] - ts[i]) / (ys[i + 1] - ys[i])
+    return (cr[-1] - cr[0]) / (len(cr) - 1), len(cr)
+
+
+def _beam_tip_gpu(sph, wl, T):
+    """The solid alone, stepped through the library's substep loop (no fluid): tip deflection
+    after every fluid substep (each holding kappa solid steps)."""
+    sim = sph.Simulation(wl)
+    solid = sph.solid_from(sim, wl)
+    x0 = wl.solid_pos
+    tip = int(np.argmax(x0[:, 0] + 1e-6 * x0[:, 1]))
+    t, ts, ys, steps = 0.0, [], [], 0
+    while t < T:
+        sim.build_cells()
+        sim.advection_step()
+        done = False
+        while not done:
+            done, dt = sim.acoustic_substep()
+            t += dt
+            sg = sph.sph_solid_get_state(sim.handle, solid)
+            ts.append(t)
+            ys.append(sg["pos"][tip, 1] - x0[tip, 1])
+            steps = sg["solid_steps"]                 # solid steps since the solid was attached
+    sph.sph_solid_destroy(solid)
+    sim.close()
+    return np.asarray(ts), np.asarray(ys), steps
+
+
+def _beam_tip_oracle(wl, T):
+    sol = f.solid_from_problem(wl)
+    x0 = wl.solid_pos
+    tip = int(np.argmax(x0[:, 0] + 1e-6 * x0[:, 1]))
+    t, ts, ys = 0.0, [], []
+    while t < T:
+        dt = 0.8 * f.solid_dt(sol)
+        f.solid_step(sol, dt)
+        t += dt
+        ts.append(t)
+        ys.append(sol.x[tip, 1] - x0[tip, 1])
+    return np.asarray(ts), np.asarray(ys)
+
+
+def test_cantilever_oscillates_at_its_first_bending_frequency(sph):
+    # the paper's oscillating beam with the solid alone: a cantilever 0.2 long and 0.02 thick
+    # loaded suddenly by its weight. At 5 particles across its period matches the oracle's
+    # (the same discretisation in FP64); at 10 across it approaches the clamped-free
+    # Euler-Bernoulli period from above (the oracle pins the same convergence)
+    T = 1.5
+    coarse = wk.cantilever_beam(ds=0.004)
+    tg, yg, _ = _beam_tip_gpu(sph, coarse, T)
+    to, yo = _beam_tip_oracle(coarse, T)
+    pg, ng = _up_crossing_period(tg, yg)
+    po, no = _up_crossing_period(to, yo)
+    fine = wk.cantilever_beam(ds=0.002)
+    tf, yf, steps = _beam_tip_gpu(sph, fine, T)
+    pf, nf = _up_crossing_period(tf, yf)
+    eb = fine.meta["period_eb"]
+    print(f"cantilever period: 5 across GPU {pg:.5f} s ({ng} crossings) oracle {po:.5f} s ({no}); "
+          f"10 across GPU {pf:.5f} s = {pf / eb:.4f} x Euler-Bernoulli ({eb:.5f} s), {steps} solid steps; "
+          f"tip amplitude {np.ptp(yf):.3e} (static deflection x2 {3 * fine.meta['g'] * fine.solid_rho0 * 0.2 ** 4 / (fine.solid_youngs / 0.91 * 0.02 ** 2):.3e})")
+    assert ng >= 3 and no >= 3 and nf >= 3
+    assert abs(pg / po - 1.0) < 5e-3
+    assert 1.0 < pf / eb < 1.09 and abs(pf / eb - 1.0) < abs(pg / eb - 1.0)
+
+
 def test_solid_refuses_bad_arguments(sph):
     wl, _ = _prepared(2)
     sim = sph.Simulation(wl)
