@@ -448,6 +448,42 @@ def cantilever_beam(ds=0.002, L=0.2, thickness=0.02, youngs=2e6, poisson=0.3, rh
     return wl
 
 
+def cantilever_beam_3d(ds=0.004, L=0.2, thickness=0.02, youngs=2e6, poisson=0.3, rho_s=1000.0, g=1.0, model=1,
+                       fluid_dp=0.008, c0=2.0):
+    """3D cantilever of length L and a square cross-section thickness x thickness on a lattice
+    of spacing ds, clamped over 3 h_S at its root (x < 0), the solid alone, loaded suddenly
+    by its own weight along -y (as cantilever_beam). For a slender beam of square section the
+    clamped-free Euler-Bernoulli period uses E itself (uniaxial stress) and I / A =
+    thickness^2 / 12 (meta["period_eb"])."""
+    clamp = 3 * H_OVER_DP * ds
+    nx, ny = int(round((L + clamp) / ds)), max(1, int(round(thickness / ds)))
+    spos = _lattice(np.array([-clamp, 0.0, 0.0]), [nx, ny, ny], ds)
+    grav = np.zeros(3)
+    grav[1] = -g
+    margin = 0.25 * L
+    lo = np.array([-clamp - margin, -margin, -margin])
+    hi = np.array([L + margin, ny * ds + margin, ny * ds + margin])
+    empty = np.zeros((0, 3))
+    wl = Workload(
+        name=f"cantilever_beam_3d_{spos.shape[0]}", dim=3, h=H_OVER_DP * fluid_dp, dp=fluid_dp, rho0=1.0, c0=c0,
+        cfl_ad=0.25, cfl_ac=0.6, u_ref=c0 / 10.0, nu=0.0, gravity=grav, lo=lo, hi=hi,
+        periodic=np.zeros(3, dtype=np.int32), free_surface=1,
+        pos=empty, vel=empty.copy(), rho=np.zeros(0), mass=np.zeros(0),
+        wall_pos=empty.copy(), wall_normal=empty.copy(), wall_vol=np.zeros(0),
+        t_end=1.0, meta={"L": L, "thickness": ny * ds, "g": g},
+    )
+    wl.solid_pos = spos
+    wl.solid_vol = np.full(spos.shape[0], ds ** 3)
+    wl.solid_normal = np.tile([0.0, 1.0, 0.0], (spos.shape[0], 1))
+    wl.solid_fixed = spos[:, 0] < 0.0
+    wl.solid_h = H_OVER_DP * ds
+    wl.solid_dp = ds
+    wl.solid_rho0, wl.solid_youngs, wl.solid_poisson, wl.solid_model = rho_s, youngs, poisson, model
+    t = ny * ds
+    wl.meta["period_eb"] = 2.0 * math.pi / (1.875 ** 2 * math.sqrt(youngs * t ** 2 / 12.0 / (rho_s * L ** 4)))
+    return wl
+
+
 def water_column_on_plate(dp=1.0 / 40.0, ratio=2, H=1.0, L=1.0, thickness=0.05, youngs=4.55e4,
                           poisson=0.3, rho_s=2.7, rho0=1.0, g=1.0, model=1, nu=0.0):
     """2D water column of height H on an elastic plate spanning a tank of width L (the

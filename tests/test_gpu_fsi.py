@@ -234,6 +234,23 @@ def test_cantilever_oscillates_at_its_first_bending_frequency(sph):
     assert 1.0 < pf / eb < 1.09 and abs(pf / eb - 1.0) < abs(pg / eb - 1.0)
 
 
+def test_3d_cantilever_period_converges_to_euler_bernoulli(sph):
+    # a 3D cantilever of square section (5 and 10 particles across, 1,350 and 10,400
+    # particles; the finer one reads its constant rows from global memory), loaded by its
+    # weight: the first bending period approaches the Euler-Bernoulli period from above
+    T = 1.5
+    ratios = []
+    for ds in (0.004, 0.002):
+        wl = wk.cantilever_beam_3d(ds=ds)
+        ts, ys, steps = _beam_tip_gpu(sph, wl, T)
+        p, n = _up_crossing_period(ts, ys)
+        assert n >= 3
+        ratios.append(p / wl.meta["period_eb"])
+        print(f"3D cantilever, {wl.solid_pos.shape[0]} particles: period {p:.5f} s = {ratios[-1]:.4f} x "
+              f"Euler-Bernoulli, {steps} solid steps")
+    assert 1.0 < ratios[1] < ratios[0] and ratios[1] < 1.1
+
+
 def test_solid_refuses_bad_arguments(sph):
     wl, _ = _prepared(2)
     sim = sph.Simulation(wl)
