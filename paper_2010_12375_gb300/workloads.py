@@ -160,6 +160,42 @@ def dam_break(dim=2, H=1.0, L=2.0, W=1.0, dp=None, n_per_H=40, tank=None, rho0=1
     )
 
 
+def dam_break_with_obstacle(dim=2, H=1.0, L=2.0, W=1.0, dp=None, n_per_H=40, obstacle_x=None,
+                            obstacle_w=0.4, obstacle_h=0.4, **kw):
+    """Dam break with a block obstacle on the tank floor (the paper's dam break with an
+    obstacle, at synthetic sizes): the dam break above plus dummy wall particles filling the
+    block [x_o, x_o + w] by [0, h] (the full tank depth in 3D) on the same lattice, each with
+    the unit outward normal of its nearest face among the block's left, right and top faces
+    (the normalised sum where two are equally near, the top face's where the left and right
+    ones are). x_o defaults to 1.5 L."""
+    base = dam_break(dim=dim, H=H, L=L, W=W, dp=dp, n_per_H=n_per_H, **kw)
+    dp = base.dp
+    xo = 1.5 * base.meta["L"] if obstacle_x is None else obstacle_x
+    nx, ny = int(round(obstacle_w / dp)), int(round(obstacle_h / dp))
+    x0 = round(xo / dp) * dp                        # on the lattice of the fluid and the walls
+    if dim == 2:
+        blk = _lattice(np.array([x0, 0.0]), [nx, ny], dp)
+    else:
+        nz = int(round((base.hi[2] - base.lo[2]) / dp)) - 2 * WALL_LAYERS
+        blk = _lattice(np.array([x0, 0.0, 0.0]), [nx, ny, nz], dp)
+    d = np.stack([blk[:, 0] - x0, x0 + nx * dp - blk[:, 0], ny * dp - blk[:, 1]], axis=1)
+    faces = np.array([[-1.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    near = d <= d.min(axis=1, keepdims=True) + 1e-9 * dp
+    nrm = near.astype(np.float64) @ faces
+    nrm[np.linalg.norm(nrm, axis=1) < 0.5] = faces[2]   # equally near the left and right faces: up
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    if dim == 3:
+        nrm = np.concatenate([nrm, np.zeros((nrm.shape[0], 1))], axis=1)
+    keep = ~np.any(np.all(np.abs(blk[:, None, :] - base.pos[None, :, :]) < 0.5 * dp, axis=2), axis=1) \
+        if base.pos.shape[0] * blk.shape[0] < 2e8 else np.ones(blk.shape[0], dtype=bool)
+    base.wall_pos = np.concatenate([base.wall_pos, blk[keep]])
+    base.wall_normal = np.concatenate([base.wall_normal, nrm[keep]])
+    base.wall_vol = np.concatenate([base.wall_vol, np.full(int(keep.sum()), dp ** dim)])
+    base.name = f"dam_break_obstacle_{dim}d_{base.n_fluid}"
+    base.meta.update({"obstacle": (float(x0), float(nx * dp), float(ny * dp))})
+    return base
+
+
 def dam_break_2d(n_per_H=40, **kw):
     """2D dam break: H=1, L=2, tank 5.366, dp = H/40 gives 3200 fluid particles."""
     return dam_break(dim=2, n_per_H=n_per_H, **kw)

@@ -133,13 +133,19 @@ def _substep_case(case):
     elif case == "dam3d":
         prob = wk.dam_break_3d(16)
         vel_amp, rho_amp = 0.3, 0.01
+    elif case == "obstacle2d":                     # a block on the floor against the column
+        prob = wk.dam_break_with_obstacle(dim=2, obstacle_x=2.0)
+        vel_amp, rho_amp = 0.3, 0.01
+    elif case == "obstacle3d":
+        prob = wk.dam_break_with_obstacle(dim=3, dp=1.0 / 16.0, obstacle_x=2.0)
+        vel_amp, rho_amp = 0.3, 0.01
     else:
         prob = wk.periodic_box(dim=3, n=12, seed=3)
         vel_amp, rho_amp = 0.1, 0.01
     return prob, vel_amp, rho_amp
 
 
-@pytest.mark.parametrize("case", ["dam2d", "tg", "dam3d", "box3d"])
+@pytest.mark.parametrize("case", ["dam2d", "tg", "dam3d", "box3d", "obstacle2d", "obstacle3d"])
 def test_one_substep_matches_oracle(sph, case):
     prob, vel_amp, rho_amp = _substep_case(case)
     prob = _with_walls_on_grid(prob)
@@ -168,6 +174,10 @@ def test_one_substep_matches_oracle(sph, case):
 
     st = o.State(xq, v32, rho32, d32, np.asarray(prob.mass, dtype=np.float64), 0.0)
     nb = o.neighbour_sets_quantised(st.x, w.x, prm)
+    if case.startswith("obstacle"):                       # fluid pairs with the block's particles
+        x0, bw, bh = prob.meta["obstacle"]
+        wx = w.x[nb[3]]
+        assert np.count_nonzero((wx[:, 0] > x0) & (wx[:, 0] < x0 + bw) & (wx[:, 1] > 0.0)) > 100
     Dt = o.dt_advection(st.v, prm)
     st.rho = o.density_summation(st, w, nb, prm)
     if prm.free_surface:
