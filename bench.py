@@ -524,6 +524,9 @@ def run_workload(args):
     if args.workload == "beam":
         run_beam(args, stream)
         return
+    if args.workload == "gate":
+        run_gate(args, stream)
+        return
     if args.workload == "batched":
         problems = wk.batched_dam_breaks(256)
         name = "256 independent 2D dam breaks (2k-50k fluid each), one handle"
@@ -607,6 +610,45 @@ def run_sizes(args):
            "config": {"workload": "3D dam break 2x1x1 in a 5.366x5.366x1 tank, dp = 1/80, 1/126, 1/159"},
            "value": rows[-1]["value"], "sizes": rows}
     print(json.dumps(out), flush=True)
+
+
+def run_gate(args, stream):
+    """Dam break through an elastic gate (2,240 fluid particles, a 268-particle Neo-Hookean
+    gate on a lattice twice as fine), 0.4 s of simulated time through the CUDA-graph loop: GPU
+    time per simulated second and the gate's free end (opening along x, lift along y) every
+    0.05 s, sampled between advection steps outside the timed spans."""
+    import torch
+    from paper_2010_12375_gb300 import sph, workloads as wk
+    wl = wk.elastic_gate()
+    tip = int(np.argmin(wl.solid_pos[:, 1] - 1e-6 * wl.solid_pos[:, 0]))
+    sim = sph.Simulation(wl, flags=sph.SPH_FLAG_GRAPH, stream=stream)
+    solid = sph.solid_from(sim, wl)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, t, mark, steps, trace = 0.0, 0.0, 0.05, 0, []
+    while t < wl.t_end:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sim.step(1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms += ev0.elapsed_time(ev1)
+        steps += 1
+        t = sim.diagnostics()["t"]
+        if t >= mark - 1e-12:
+            p = sph.sph_solid_get_state(sim.handle, solid)["pos"][tip] - wl.solid_pos[tip]
+            trace.append({"t": round(t, 4), "opening": float(p[0]), "lift": float(p[1])})
+            mark += 0.05
+    sg = sph.sph_solid_get_state(sim.handle, solid)
+    sph.sph_solid_destroy(solid)
+    sim.close()
+    print(json.dumps({
+        "metric": "dam break through an elastic gate: GPU ms per simulated second", "value": ms / t, "unit": "ms/s",
+        "higher_is_better": False, "n_gpus": 1, "steps": steps, "warmup": 0, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"water column {wl.meta['A']} x {wl.meta['H']}, {wl.n_fluid} fluid particles; "
+                               f"Neo-Hookean gate {wl.meta['thickness']} x {wl.meta['gate_h']}, "
+                               f"{wl.solid_pos.shape[0]} particles (ratio {wl.meta['ratio']})",
+                   "simulated_s": t},
+        "solid_steps": int(sg["solid_steps"]), "free_end": trace}), flush=True)
 
 
 def run_beam(args, stream):
@@ -977,7 +1019,7 @@ def main():
                     help="the frozen-pair-geometry reading (pair vectors kept from the configuration update)")
     ap.add_argument("--launch-config", default=None,
                     help="pr_tpp,pr_block,dr_tpp,dr_block: fixed launch variants instead of autotuning")
-    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes", "diffusion3d", "fsi", "gradients", "beam"],
+    ap.add_argument("--workload", default="dam3d", choices=["dam3d", "batched", "dam2d", "tg", "learned", "learned_step", "sizes", "diffusion3d", "fsi", "gradients", "beam", "gate"],
                     help="dam3d is the benchmark line; the others print secondary lines")
     args = ap.parse_args()
     if args.warmup < 3:

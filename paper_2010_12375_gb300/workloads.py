@@ -520,6 +520,64 @@ def cantilever_beam_3d(ds=0.004, L=0.2, thickness=0.02, youngs=2e6, poisson=0.3,
     return wl
 
 
+def elastic_gate(dp=0.0025, ratio=2, A=0.1, H=0.14, gate_h=0.079, gate_t=0.005, tank_w=0.4, youngs=12e6,
+                 poisson=0.4, rho_s=1100.0, rho0=1000.0, g=9.81, model=2):
+    """Dam break through an elastic gate (the paper's FSI case after Antoci et al., at synthetic
+    sizes): a water column A wide and H high at rest against a rigid wall that ends gate_h above
+    the floor; below it an elastic gate of thickness gate_t closes the opening, clamped where it
+    runs into the rigid wall (over three solid smoothing lengths) and free at its lower end, just
+    above the floor. The fluid on a lattice of spacing dp, the gate on one ratio times finer;
+    a floor running on to the right so that the water leaves under the opening gate. Solid
+    normals point into the water (-x). The rigid wall is four dummy layers thick, above the
+    gate's clamped part, its normals pointing into the water as well (the case is meant for
+    the gate's opening, before water reaches the wall's far side)."""
+    nx, ny = int(round(A / dp)), int(round(H / dp))
+    fluid = _lattice(np.zeros(2), [nx, ny], dp)
+    top = H + 8 * dp
+    wpos, wnrm, wvol = tank_walls(np.zeros(2), np.array([tank_w, top]), dp)
+    keep = wpos[:, 1] < top                            # an open top: no ceiling layers
+    wpos, wnrm, wvol = wpos[keep], wnrm[keep], wvol[keep]
+    ds = dp / ratio
+    clamp = 3 * H_OVER_DP * ds
+    nsx = max(1, int(round(gate_t / ds)))
+    gy0 = 0.5 * ds                                     # the free end, half a spacing above the floor
+    nsy = int(round((gate_h + clamp - gy0) / ds))
+    spos = _lattice(np.array([nx * dp, gy0]), [nsx, nsy], ds)
+    fixed = spos[:, 1] > gate_h
+    # the rigid wall above the gate's clamped part (which closes the span between gate_h and
+    # the wall): four layers from the gate's left face on
+    wy0 = gate_h + clamp
+    nwy = int(round((top - wy0) / dp))
+    rig = _lattice(np.array([nx * dp, wy0]), [WALL_LAYERS, nwy], dp)
+    rn = np.tile([-1.0, 0.0], (rig.shape[0], 1))
+    wpos = np.concatenate([wpos, rig])
+    wnrm = np.concatenate([wnrm, rn])
+    wvol = np.concatenate([wvol, np.full(rig.shape[0], dp * dp)])
+    c0 = 10.0 * math.sqrt(g * H)
+    grav = np.zeros(3)
+    grav[1] = -g
+    lo = np.array([-WALL_LAYERS * dp, -WALL_LAYERS * dp, 0.0])
+    hi = np.array([tank_w + WALL_LAYERS * dp, top + 4 * dp, 0.0])
+    n = fluid.shape[0]
+    wl = Workload(
+        name=f"elastic_gate_{n}_r{ratio}", dim=2, h=H_OVER_DP * dp, dp=dp, rho0=rho0, c0=c0,
+        cfl_ad=0.25, cfl_ac=0.6, u_ref=c0 / 10.0, nu=0.0, gravity=grav, lo=lo, hi=hi,
+        periodic=np.zeros(3, dtype=np.int32), free_surface=1,
+        pos=fluid, vel=np.zeros_like(fluid), rho=np.full(n, rho0), mass=np.full(n, rho0 * dp * dp),
+        wall_pos=wpos, wall_normal=wnrm, wall_vol=wvol,
+        t_end=0.4, meta={"H": ny * dp, "L": nx * dp, "A": nx * dp, "g": g, "gate_h": gate_h,
+                         "thickness": nsx * ds, "ratio": ratio},
+    )
+    wl.solid_pos = spos
+    wl.solid_vol = np.full(spos.shape[0], ds * ds)
+    wl.solid_normal = np.tile([-1.0, 0.0], (spos.shape[0], 1))
+    wl.solid_fixed = fixed
+    wl.solid_h = H_OVER_DP * ds
+    wl.solid_dp = ds
+    wl.solid_rho0, wl.solid_youngs, wl.solid_poisson, wl.solid_model = rho_s, youngs, poisson, model
+    return wl
+
+
 def water_column_on_plate(dp=1.0 / 40.0, ratio=2, H=1.0, L=1.0, thickness=0.05, youngs=4.55e4,
                           poisson=0.3, rho_s=2.7, rho0=1.0, g=1.0, model=1, nu=0.0):
     """2D water column of height H on an elastic plate spanning a tank of width L (the

@@ -103,6 +103,41 @@ def _coupled_substep_against_oracle(sph, wl, prm, label):
     assert np.max(np.abs(disp_g - disp_o)) < 2 * kappa * dq + 1e-6 * np.max(np.abs(disp_o))
 
 
+def test_elastic_gate_substep_matches_the_oracle(sph):
+    # the dam break through an elastic gate: a Neo-Hookean gate clamped at its top holds the
+    # column from below a rigid wall
+    wl, prm = _prepared(2, wl=wk.elastic_gate())
+    _coupled_substep_against_oracle(sph, wl, prm, "elastic gate")
+
+
+def test_elastic_gate_opening_follows_the_oracle():
+    # the gate's free end over the first 0.03 s (the water starts to push it open)
+    from paper_2010_12375_gb300 import sph as s
+    s.load()
+    wl, prm = _prepared(2, wl=wk.elastic_gate())
+    tip = int(np.argmin(wl.solid_pos[:, 1] - 1e-6 * wl.solid_pos[:, 0]))   # lowest, rightmost
+    sim = s.Simulation(wl, flags=s.SPH_FLAG_GRAPH)
+    solid = s.solid_from(sim, wl)
+    tg, xg = [0.0], [0.0]
+    while tg[-1] < 0.03:
+        sim.step(1)
+        tg.append(sim.diagnostics()["t"])
+        xg.append(s.sph_solid_get_state(sim.handle, solid)["pos"][tip, 0] - wl.solid_pos[tip, 0])
+    s.sph_solid_destroy(solid)
+    sim.close()
+    st, w = o.state_from_problem(wl)
+    sol = _oracle_solid(wl)
+    to, xo = [0.0], [0.0]
+    while to[-1] < 0.03:
+        st, _, _ = f.advection_step(st, w, prm, sol)
+        to.append(st.t)
+        xo.append(sol.x[tip, 0] - sol.x0[tip, 0])
+    tg, xg, to, xo = map(np.asarray, (tg, xg, to, xo))
+    err = np.max(np.abs(xg - np.interp(tg, to, xo))) / np.max(np.abs(xo))
+    print(f"gate's free end: opening {xo.max():.3e} at t = {to[-1]:.3f}, GPU vs oracle {err:.2e} of it")
+    assert xo.max() > 0.0 and err < 5e-3
+
+
 def _fluid_above(wl, gap):
     """The workload with only the fluid lying more than `gap` above the plate's top."""
     keep = wl.pos[:, 1] > np.max(wl.solid_pos[:, 1]) + gap
