@@ -533,7 +533,7 @@ def elastic_gate(dp=0.0025, ratio=2, A=0.1, H=0.14, gate_h=0.079, gate_t=0.005, 
     the gate's opening, before water reaches the wall's far side)."""
     nx, ny = int(round(A / dp)), int(round(H / dp))
     fluid = _lattice(np.zeros(2), [nx, ny], dp)
-    top = H + 8 * dp
+    top = 3.0 * H                                      # walls high enough for the splash
     wpos, wnrm, wvol = tank_walls(np.zeros(2), np.array([tank_w, top]), dp)
     keep = wpos[:, 1] < top                            # an open top: no ceiling layers
     wpos, wnrm, wvol = wpos[keep], wnrm[keep], wvol[keep]
