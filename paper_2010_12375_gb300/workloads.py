@@ -327,6 +327,35 @@ def diffusion_patch(n=40, kappa=1.0, sigma=0.2, D=None):
     return w
 
 
+def excitable_sheet(n=200, dp=0.5, cross_field=True):
+    """Square sheet of n x n lattice particles of spacing dp with free edges, for the
+    Aliev-Panfilov model with unit diffusivity (the paper's spiral-wave test, at synthetic
+    sizes and in the model's own units). cross_field: the lower-left quarter excited
+    (V = 1) and the upper-left quarter refractory (w = 2), so that the front leaving the
+    excited quarter has a free end beside refractory tissue and curls into a spiral;
+    otherwise a strip along the left edge is excited, and the planar wave it starts leaves
+    the sheet. meta: C0 = V, w0, dt (inside the explicit diffusion limit), the model
+    parameters (k = 8, a = 0.15, b = 0.15, eps0 = 0.002, mu1 = 0.2, mu2 = 0.3)."""
+    pos = _lattice(np.zeros(2), [n, n], dp)
+    L = n * dp
+    if cross_field:
+        V0 = np.where((pos[:, 0] < L / 2) & (pos[:, 1] < L / 2), 1.0, 0.0)
+        w0 = np.where((pos[:, 0] < L / 2) & (pos[:, 1] >= L / 2), 2.0, 0.0)
+    else:
+        V0 = np.where(pos[:, 0] < 0.05 * L, 1.0, 0.0)
+        w0 = np.zeros(pos.shape[0])
+    w = _static_body(f"excitable_sheet_{n}", 2, dp, pos, np.ones(3), V0, 1.0, None)
+    w.periodic = np.zeros(3, dtype=np.int32)
+    w.lo = np.array([-4.0 * dp, -4.0 * dp, 0.0])
+    w.hi = np.array([L + 4.0 * dp, L + 4.0 * dp, 0.0])
+    w.free_surface = 1
+    w.meta["w0"] = w0
+    w.meta["dt"] = 0.02
+    w.meta["L"] = L
+    w.meta["ap"] = dict(k=8.0, a=0.15, b=0.15, eps0=0.002, mu1=0.2, mu2=0.3)
+    return w
+
+
 def _static_body(name, dim, dp, pos, extent, C0, kappa, D):
     N = pos.shape[0]
     Dm = np.zeros((3, 3))

@@ -100,6 +100,46 @@ def test_reaction_diffusion_alternated_matches_oracle(sph):
     assert np.max(np.abs(Vg - V)) < 1e-5 and np.max(np.abs(wg - w)) < 1e-5
 
 
+def _excite(sph, prob, T):
+    """Aliev-Panfilov on the sheet: a diffusion step and a reaction step of dt, alternated, to
+    time T; returns V at the end and the active fraction (V > 0.5) every 50 time units."""
+    sim = sph.Simulation(prob)
+    sph.sph_build_cells(sim.handle)
+    sp = sph.sph_species_create(sim.handle, prob.meta["D"], 2)
+    trace = []
+    try:
+        sph.sph_species_set(sim.handle, sp, prob.meta["C0"])
+        sph.sph_species_set_gate(sim.handle, sp, prob.meta["w0"])
+        r = sph.reaction_from(sph.SPH_REACTION_AP, **prob.meta["ap"])
+        dt = prob.meta["dt"]
+        per = int(round(50.0 / dt))
+        for k in range(int(round(T / dt))):
+            sph.sph_diffusion_step(sim.handle, sp, dt, 1)
+            sph.sph_reaction_step(sim.handle, sp, r, dt, 1)
+            if (k + 1) % per == 0:
+                trace.append(float(np.mean(sph.sph_species_get(sim.handle, sp, sim.n) > 0.5)))
+        V = sph.sph_species_get(sim.handle, sp, sim.n)
+    finally:
+        sph.sph_species_destroy(sp)
+        sim.close()
+    return V, trace
+
+
+def test_spiral_wave_sustains_itself_and_a_planar_wave_leaves(sph):
+    # the paper's spiral-wave test in the Aliev-Panfilov model's units: from a cross-field
+    # start (excited lower-left quarter, refractory upper-left quarter) the front's free end
+    # curls into a spiral that keeps a steady share of the sheet excited, while a planar wave
+    # started at the left edge crosses the sheet and leaves it at rest
+    T = 300.0
+    V_spiral, tr_spiral = _excite(sph, wk.excitable_sheet(200, 0.5, cross_field=True), T)
+    V_plane, tr_plane = _excite(sph, wk.excitable_sheet(200, 0.5, cross_field=False), T)
+    print("active fraction every 50 units, spiral:", [f"{a:.3f}" for a in tr_spiral],
+          "planar:", [f"{a:.3f}" for a in tr_plane])
+    assert np.all(np.isfinite(V_spiral)) and np.all(np.isfinite(V_plane))
+    assert min(tr_spiral[1:]) > 0.1 and max(tr_spiral) < 0.6
+    assert tr_plane[-1] < 0.01 and max(tr_plane) > 0.05
+
+
 def test_reaction_edge_cases(sph):
     prob, sim, sp = _setup(sph, n=16)
     try:
