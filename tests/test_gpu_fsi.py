@@ -5,7 +5,12 @@ the plate's lattice two or four times finer than the fluid's.
 One coupled acoustic substep from the same representable state: fluid dv/dt, v, rho - rho0
 and d rho/dt within 1e-5 relative L2 (the per-substep bar), the solid's kappa equal and its
 velocity after the kappa steps within 1e-5; positions are compared through the displacement.
-Over a trajectory the plate's mid-span deflection stays within 0.5 % of its extreme."""
+Over a trajectory the plate's mid-span deflection stays within 0.5 % of its extreme.
+
+Also the paper's other solid cases at synthetic sizes: the dam break through an elastic gate
+(one substep, and the gate's opening over 0.03 s against the oracle), the cantilever with the
+solid alone (its first bending period against the oracle's and the Euler-Bernoulli period,
+2D and 3D), and the degenerate cases (a plate beyond the fluid's reach, bad arguments)."""
 import copy
 
 import numpy as np

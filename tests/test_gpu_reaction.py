@@ -1,6 +1,7 @@
 """GPU parity of the reaction step of reaction-diffusion (Eq. ode-spliting-2rd with the QSS
 update of Eq. ode-qss; FitzHugh-Nagumo Eq. fhn and Aliev-Panfilov Eq. a-p) through the C ABI
-against the FP64 oracle (oracle/reaction.py), and of diffusion and reaction alternated.
+against the FP64 oracle (oracle/reaction.py), and of diffusion and reaction alternated; and
+the paper's spiral-wave test (a self-sustaining spiral against a planar wave that leaves).
 
 Tolerance. The GPU holds V and w in FP32 and evaluates expf/expm1f in FP32: each of the four
 reactions per step carries a few roundings of relative size 2^-24 on values of order 1, so
