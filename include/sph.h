@@ -301,6 +301,15 @@ int sph_pair_count(sph_handle* h, int64_t* fluid_pairs, int64_t* wall_pairs, voi
  * neighbour row and add their sums in a fixed order); block 128, 256 or 512. Set
  * returns SPH_E_INVALID for other values. Handles created with SPH_FLAG_FROZEN_GEOMETRY
  * run one thread per particle in 128-thread blocks whatever the configuration says. */
+/* Replace the gravity (the body force per unit mass, Eq. governingeq's g) of tank `instance`
+ * (0-based; every tank when instance < 0) for every later call that advances the state, for
+ * instance to follow a tank's translation in its own frame, g_eff(t) = g - a_tank(t). It
+ * also enters the wall problem's P_R (Eq. eqriepright) and an attached solid's momentum
+ * (the solid feels the same frame). A captured advection-step graph is rebuilt at its next
+ * use. g: host array of 3 doubles (components beyond dim ignored). SPH_E_INVALID for a bad
+ * instance or a non-finite component, the gravity unchanged. Synchronous. */
+int sph_set_gravity(sph_handle* h, int32_t instance, const double* g, void* stream);
+
 int sph_get_launch_config(const sph_handle* h, int32_t* cfg);
 int sph_set_launch_config(sph_handle* h, const int32_t* cfg);
 

@@ -1013,6 +1013,30 @@ int sph_get_launch_config(const sph_handle* h, int32_t* cfg) {
   return SPH_OK;
 }
 
+int sph_set_gravity(sph_handle* h, int32_t instance, const double* g, void* stream) {
+  if (!h) return SPH_E_INVALID;
+  if (!g) return fail(h, SPH_E_INVALID, "g is required");
+  const int n_inst = h->b.n_inst, d = h->b.dim;
+  if (instance >= n_inst) return fail(h, SPH_E_INVALID, "no such tank");
+  for (int a = 0; a < d; ++a)
+    if (!std::isfinite(g[a])) return fail(h, SPH_E_INVALID, "gravity must be finite");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k0 = instance < 0 ? 0 : instance, k1 = instance < 0 ? n_inst : instance + 1;
+  for (int k = k0; k < k1; ++k) {
+    for (int a = 0; a < 3; ++a) {
+      h->params[k].gravity[a] = a < d ? g[a] : 0.0;
+      h->hinst[k].g[a] = a < d ? (float)g[a] : 0.0f;
+    }
+    // the device copy, in stream order with the work already queued
+    CK(h, cudaMemcpyAsync(h->b.inst + k, &h->hinst[k], sizeof(Inst), cudaMemcpyHostToDevice, s));
+  }
+  h->b.inst0 = h->hinst[0];
+  if (k0 == 0) sph_fsi_set_gravity(h, h->params[0].gravity);   // a solid lives in tank 0
+  drop_graph(h);
+  CK(h, cudaStreamSynchronize(s));                 // the host copies above are read now
+  return SPH_OK;
+}
+
 int sph_set_launch_config(sph_handle* h, const int32_t* cfg) {
   if (!h || !cfg) return SPH_E_INVALID;
   std::ostringstream o;

@@ -1177,6 +1177,12 @@ void sph_fsi_after_build(sph_handle* h, cudaStream_t st, int64_t* launches) {
   *launches += 1;
 }
 
+void sph_fsi_set_gravity(sph_handle* h, const double* g) {
+  sph_solid* s = h->solid;
+  if (!s) return;
+  for (int a = 0; a < 3; ++a) s->mat.g[a] = a < s->dim ? (float)g[a] : 0.f;
+}
+
 void sph_fsi_after_pressure(sph_handle* h, cudaStream_t st, int64_t* launches) {
   sph_solid* s = h->solid;
   if (!s || s->ns == 0 || h->b.n == 0) return;

@@ -55,3 +55,4 @@ void sph_drop_graph(sph_handle* h);
 void sph_fsi_after_build(sph_handle* h, cudaStream_t s, int64_t* launches);
 void sph_fsi_after_pressure(sph_handle* h, cudaStream_t s, int64_t* launches);
 void sph_fsi_after_density(sph_handle* h, cudaStream_t s, int64_t* launches);
+void sph_fsi_set_gravity(sph_handle* h, const double* g);   // the attached solid's gravity, if any

@@ -41,7 +41,7 @@ EXPORTS = [
     "sph_diagnostics", "sph_get_state", "sph_set_state", "sph_get_acceleration",
     "sph_get_permutation", "sph_get_neighbours", "sph_pair_count", "sph_kernel_launches",
     "sph_set_kernel_timing", "sph_kernel_times", "sph_diagnostics_noalloc",
-    "sph_get_launch_config", "sph_set_launch_config", "sph_autotune", "sph_gather_ceiling",
+    "sph_get_launch_config", "sph_set_launch_config", "sph_autotune", "sph_gather_ceiling", "sph_set_gravity",
     "sph_learned_weight_count", "sph_learned_create", "sph_learned_destroy",
     "sph_learned_last_error", "sph_learned_set_weights", "sph_learned_get_weights",
     "sph_learned_set_fused", "sph_learned_predict", "sph_learned_train_step", "sph_learned_step",
@@ -138,6 +138,7 @@ def load():
         "sph_last_error": (ctypes.c_char_p, [P]),
         "sph_get_info": (i32, [P, ctypes.POINTER(SphInfo)]),
         "sph_build_cells": (i32, [P, P]),
+        "sph_set_gravity": (i32, [P, i32, P, P]),
         "sph_advection_step": (i32, [P, ctypes.POINTER(dbl), P]),
         "sph_acoustic_substep": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(dbl), P]),
         "sph_step": (i32, [P, i32, P]),
@@ -438,6 +439,14 @@ def sph_autotune(h, stream=None):
     ms = (ctypes.c_double * 18)()
     check(lib, h, lib.sph_autotune(h, cfg, ms, _stream(stream)))
     return list(cfg), np.array(ms[:]).reshape(2, 3, 3)
+
+
+def sph_set_gravity(h, g, instance=-1, stream=None):
+    """Replace the gravity of one tank (every tank when instance < 0), e.g. g - a_tank(t)."""
+    lib = load()
+    gv = np.zeros(3, dtype=np.float64)
+    gv[:len(g)] = np.asarray(g, dtype=np.float64)
+    check(lib, h, lib.sph_set_gravity(h, int(instance), _ptr(gv), _stream(stream)))
 
 
 def sph_gather_ceiling(h, reps=10, stream=None) -> float:

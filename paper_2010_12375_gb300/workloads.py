@@ -196,6 +196,33 @@ def dam_break_with_obstacle(dim=2, H=1.0, L=2.0, W=1.0, dp=None, n_per_H=40, obs
     return base
 
 
+def sloshing_tank(L=1.0, d=0.5, dp=0.01, g=9.81, rho0=1.0):
+    """2D rectangular tank of width L filled to depth d at rest, walls twice as high: the
+    sloshing test in the tank's own frame, where a translation of the tank with acceleration
+    a(t) acts as the extra body force -a(t) (sph_set_gravity). meta["period_1"] is the
+    linear first sloshing mode's period, 2 pi / sqrt(g k tanh(k d)) with k = pi / L."""
+    nx, ny = int(round(L / dp)), int(round(d / dp))
+    fluid = _lattice(np.zeros(2), [nx, ny], dp)
+    inner_hi = np.array([nx * dp, 2.0 * d])
+    wpos, wnrm, wvol = tank_walls(np.zeros(2), inner_hi, dp)
+    c0 = 10.0 * math.sqrt(g * d)
+    grav = np.zeros(3)
+    grav[1] = -g
+    lo = np.array([-WALL_LAYERS * dp, -WALL_LAYERS * dp, 0.0])
+    hi = np.array([inner_hi[0] + WALL_LAYERS * dp, inner_hi[1] + WALL_LAYERS * dp, 0.0])
+    n = fluid.shape[0]
+    k = math.pi / (nx * dp)
+    return Workload(
+        name=f"sloshing_tank_{n}", dim=2, h=H_OVER_DP * dp, dp=dp, rho0=rho0, c0=c0, cfl_ad=0.25,
+        cfl_ac=0.6, u_ref=c0 / 10.0, nu=0.0, gravity=grav, lo=lo, hi=hi,
+        periodic=np.zeros(3, dtype=np.int32), free_surface=1,
+        pos=fluid, vel=np.zeros_like(fluid), rho=np.full(n, rho0), mass=np.full(n, rho0 * dp * dp),
+        wall_pos=wpos, wall_normal=wnrm, wall_vol=wvol, t_end=5.0,
+        meta={"L": nx * dp, "d": ny * dp, "g": g,
+              "period_1": 2.0 * math.pi / math.sqrt(g * k * math.tanh(k * ny * dp))},
+    )
+
+
 def dam_break_2d(n_per_H=40, **kw):
     """2D dam break: H=1, L=2, tank 5.366, dp = H/40 gives 3200 fluid particles."""
     return dam_break(dim=2, n_per_H=n_per_H, **kw)

@@ -114,6 +114,8 @@ def test_species_and_reaction_entry_points_reject_null_handles(lib):
 def test_error_control_entry_points_reject_null_handles(lib):
     L = lib.load()
     assert L.sph_clear_error(None, None) == lib.SPH_E_INVALID
+    g = (ctypes.c_double * 3)(0.0, -1.0, 0.0)
+    assert L.sph_set_gravity(None, -1, g, None) == lib.SPH_E_INVALID
     assert L.sph_debug_write(None, lib.SPH_DEBUG_NEIGHBOUR, 0, 0, 0, None) == lib.SPH_E_INVALID
     p = lib.params_from(__import__("paper_2010_12375_gb300.workloads", fromlist=["x"]).dam_break_2d(),
                         max_substeps=1)
