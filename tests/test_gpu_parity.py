@@ -396,6 +396,37 @@ def test_batched_instances_match_single_runs(sph):
     multi.close()
 
 
+def test_set_gravity_of_one_batched_tank(sph):
+    # in a batched handle the new gravity of tank 1 acts on tank 1 alone: tanks 0 and 2 end
+    # bit for bit as in a run without the change, tank 1 as a single tank created with it
+    tanks = wk.batched_dam_breaks(n_instances=3, n_min=300, n_max=1200)
+    g_new = np.array([0.2, -1.1, 0.0])
+    base = sph.Simulation(tanks)
+    base.step(4)
+    ref = base.state()
+    base.close()
+    multi = sph.Simulation(tanks)
+    sph.sph_set_gravity(multi.handle, g_new, instance=1)
+    multi.step(4)
+    got = multi.state()
+    off = multi.fluid_offsets
+    multi.close()
+    t1 = copy.copy(tanks[1])
+    t1.gravity = g_new.copy()
+    single = sph.Simulation(t1)
+    single.step(4)
+    one = single.state()
+    single.close()
+    for k in (0, 2):
+        sl = slice(off[k], off[k + 1])
+        for u, v in zip(got, ref):
+            np.testing.assert_array_equal(u[sl], v[sl])
+    sl = slice(off[1], off[2])
+    for u, v in zip(got, one):
+        np.testing.assert_array_equal(u[sl], v)
+    assert not np.array_equal(got[1][sl], ref[1][sl])
+
+
 def test_batched_tanks_match_the_oracle_tank_by_tank(sph):
     """One substep of the batched form on 16 tanks of the 256-tank set (the smallest, the
     largest and 14 between them in particle count: 2k-50k fluid each, uneven), from a
