@@ -35,14 +35,17 @@ UNIT = "particle-substeps/s"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pressure-relaxation
 # launch per fluid particle, from the ncu capture of the 3D dam break at dp = 1/80
-# (1,024,000 particles, neighbour table 0.5 GB > L2); it is scaled to the benchmark's particle
-# count (the traffic is per particle: state records plus its neighbour row). Valid only
-# for the kernel sources whose hash is recorded with it.
-TRAFFIC_BYTES_PER_PARTICLE = 389.79
-TRAFFIC_SOURCE_HASH = "af5377473ba40097"
+# (1,024,000 particles, neighbour table 0.5 GB > L2) in the row-task launch form; it is
+# scaled to the benchmark's particle count (the traffic is per particle: state records plus
+# its neighbour row). Valid only for the kernel sources whose hash is recorded with it, in
+# the launch form it was captured in.
+TRAFFIC_BYTES_PER_PARTICLE = 389.20
+TRAFFIC_SOURCE_HASH = "5995834dfa8dd7a9"
+TRAFFIC_ROW_FORM = True         # captured launch form: row tasks (True) or one thread a particle
+ROW_BLOCK = 896                 # block of the row-task launch form
 # Pipe utilisation of the same kernel from the same full capture (% of peak while active):
 # the FP32 FMA pipe (scalar and packed FP32 FMA/MUL/ADD) and the L1 data pipe that bounds it
-PR_PIPES = {"fp32_fma_pipe": 0.527, "l1_data_pipe": 0.847, "issue_active": 0.556}
+PR_PIPES = {"fp32_fma_pipe": 0.570, "l1_data_pipe": 0.869, "issue_active": 0.605}
 
 
 # DRAM bytes (read + write) per particle of one diffusion stage launch, from the ncu capture
@@ -331,8 +334,12 @@ def run_ours(args, rank, world, local_rank):
         # one extra (untimed) advection step that times the launch variants
         cfg, times = sph.sph_autotune(sim.handle, stream)
     if cfg is not None:
-        tuned = {"pressure_relaxation": {"threads_per_particle": cfg[0], "block": cfg[1]},
-                 "density_relaxation": {"threads_per_particle": cfg[2], "block": cfg[3]}}
+        def form(t, blk):
+            d = {"threads_per_particle": t, "block": blk}
+            if blk == ROW_BLOCK:
+                d["form"] = "row tasks (one resident block of 28 warps an SM, 32-particle row pieces)"
+            return d
+        tuned = {"pressure_relaxation": form(cfg[0], cfg[1]), "density_relaxation": form(cfg[2], cfg[3])}
     torch.cuda.synchronize()
 
     # ---------------- timed region: device-resident state, no per-kernel events inside it
@@ -413,8 +420,9 @@ def run_ours(args, rank, world, local_rank):
     k8_ms = ktimes[1] / max(kcount[1], 1)
     k8_achieved = (k8_bytes / (k8_ms * 1e-3) / 1e9) if (kcount[1] and not args.half_pair) else None
     traffic = None
+    pr_rows = sph.sph_get_launch_config(sim.handle)[1] == ROW_BLOCK and not args.frozen
     if (TRAFFIC_BYTES_PER_PARTICLE is not None and TRAFFIC_SOURCE_HASH == kernel_source_hash()
-            and not args.frozen and not args.half_pair):
+            and pr_rows == TRAFFIC_ROW_FORM and not args.frozen and not args.half_pair):
         traffic = TRAFFIC_BYTES_PER_PARTICLE * N
     # the same table walk with the 32-byte neighbour records gathered and no pair arithmetic:
     # the device's floor for gathering them this way (the kernels are gather-bound, not HBM-bound)
@@ -424,7 +432,8 @@ def run_ours(args, rank, world, local_rank):
             "nominal_peak": NOMINAL_HBM_GBS,
             "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
             "kernel": ("k_pr_half_a<3> + k_pr_half_b<3> (half-pair)" if args.half_pair
-                       else "k_pressure_relaxation<3>"), "peak_kind": peak_kind,
+                       else "k_pressure_relaxation_rows<3>" if pr_rows else "k_pressure_relaxation<3>"),
+            "peak_kind": peak_kind,
             "launch_ms": k7_ms, "algorithmic_bytes_per_launch": k7_bytes,
             "density_relaxation_ms": ktimes[1] / max(kcount[1], 1),
             # the density relaxation against the same peak: state read 28 B + write 20 B per

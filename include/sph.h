@@ -295,12 +295,6 @@ int sph_get_neighbours(sph_handle* h, int32_t* fluid_count, int32_t* wall_count,
  * sph_build_cells (host outputs; synchronous). */
 int sph_pair_count(sph_handle* h, int64_t* fluid_pairs, int64_t* wall_pairs, void* stream);
 
-/* Launch configuration of the two acoustic-substep kernels: cfg[0] threads per particle
- * and cfg[1] block size of the pressure relaxation, cfg[2], cfg[3] the same for the
- * density relaxation. Threads per particle 1, 2 or 4 (the lanes of a particle split its
- * neighbour row and add their sums in a fixed order); block 128, 256 or 512. Set
- * returns SPH_E_INVALID for other values. Handles created with SPH_FLAG_FROZEN_GEOMETRY
- * run one thread per particle in 128-thread blocks whatever the configuration says. */
 /* Replace the gravity (the body force per unit mass, Eq. governingeq's g) of tank `instance`
  * (0-based; every tank when instance < 0) for every later call that advances the state, for
  * instance to follow a tank's translation in its own frame, g_eff(t) = g - a_tank(t). It
@@ -310,16 +304,29 @@ int sph_pair_count(sph_handle* h, int64_t* fluid_pairs, int64_t* wall_pairs, voi
  * instance or a non-finite component, the gravity unchanged. Synchronous. */
 int sph_set_gravity(sph_handle* h, int32_t instance, const double* g, void* stream);
 
+/* Launch configuration of the two acoustic-substep kernels: cfg[0] threads per particle
+ * and cfg[1] block size of the pressure relaxation, cfg[2], cfg[3] the same for the
+ * density relaxation. Threads per particle 1, 2 or 4 (the lanes of a particle split its
+ * neighbour row and add their sums in a fixed order); block 128, 256 or 512; or, on a
+ * handle of one tank, threads per particle 1 with block 896, the row-task form: one
+ * resident block of 28 warps an SM, each warp taking the next 32 particles of one
+ * search-cell row (the cells along x at fixed y, z) from its block's queue, the blocks
+ * advancing through the cell order side by side; it computes each particle as the other
+ * one-thread-per-particle variants do, so their results are identical bit for bit. Set
+ * returns SPH_E_INVALID for other values. Handles created with SPH_FLAG_FROZEN_GEOMETRY
+ * run one thread per particle in 128-thread blocks whatever the configuration says. */
 int sph_get_launch_config(const sph_handle* h, int32_t* cfg);
 int sph_set_launch_config(sph_handle* h, const int32_t* cfg);
 
-/* Autotuner: runs one advection step, timing every launch variant (3 x 3 per kernel)
- * of the two relaxation kernels on its first substep (each variant recomputes the same
- * substep; the chosen one writes the result), keeps the fastest, and records it in the
- * cache file $SPH_AUTOTUNE_CACHE (default $HOME/.cache/sph_gb300_autotune.json) under
- * (GPU name, dim, particle-count power of two, batched or single). sph_create applies a
- * cached entry for the same key. cfg_out (may be NULL) receives the chosen cfg;
- * ms_out (may be NULL) the mean launch times [kernel][tpp index][block index] (18).
+/* Autotuner: runs one advection step, timing every launch variant of the two relaxation
+ * kernels (3 x 3 threads-per-particle x block variants, and the row-task form on a handle
+ * of one tank) on its first substep (each variant recomputes the same substep; the chosen
+ * one writes the result), keeps the fastest, and records it in the cache file
+ * $SPH_AUTOTUNE_CACHE (default $HOME/.cache/sph_gb300_autotune.json) under (GPU name, dim,
+ * particle-count power of two, batched or single). sph_create applies a cached entry for
+ * the same key. cfg_out (may be NULL) receives the chosen cfg; ms_out (may be NULL) 20
+ * mean launch times, ms_out[10 kernel + 3 tpp_index + block_index] for the 3 x 3
+ * variants and ms_out[10 kernel + 9] for the row-task form (-1 where it does not apply).
  * Synchronous. */
 int sph_autotune(sph_handle* h, int32_t* cfg_out, double* ms_out, void* stream);
 

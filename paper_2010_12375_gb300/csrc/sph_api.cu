@@ -280,11 +280,22 @@ int sync_status(sph_handle* h, cudaStream_t s) {
   return code;
 }
 
+// The row pieces of the row-task form, built with the cells when a relaxation uses it
+// (otherwise at that relaxation's first launch after the build).
+void enqueue_row_tasks(sph_handle* h, cudaStream_t s, int64_t* n) {
+  const sph::LaunchCfg& c = h->b.cfg;
+  if (h->b.row_task && !h->b.geo && (sph::row_form(c.pr_block) || sph::row_form(c.dr_block))) {
+    sph::launch_row_tasks(h->b, s, n);
+    h->rows_valid = true;
+  }
+}
+
 void enqueue_build(sph_handle* h, cudaStream_t s, int64_t* n) {
   sph::launch_hash(h->b, s, n);
   sph::launch_fluid_offsets(h->b, s, n);
   sph::launch_sort_fluid(h->b, s, n);
   sph::launch_neighbours(h->b, s, n);
+  enqueue_row_tasks(h, s, n);
   sph::launch_reverse_slots(h->b, s, n);     // half-pair evaluation only (b.hrev set)
   sph_fsi_after_build(h, s, n);              // attached solid only
 }
@@ -319,6 +330,7 @@ int run_build(sph_handle* h, cudaStream_t s) {
   sph::launch_sort_fluid(h->b, s, &h->launches);
   sph::launch_neighbours(h->b, s, &h->launches);
   sph::launch_check_table(h->b, s, &h->launches);
+  enqueue_row_tasks(h, s, &h->launches);
   CK(h, cudaGetLastError());
   int rt = sync_status(h, s);              // the reverse map reads the table: check it first
   if (rt != SPH_OK) return rt;
@@ -414,6 +426,8 @@ const double* device_view(sph_handle* h, const double* p, size_t elems, size_t o
 // small JSON file: $SPH_AUTOTUNE_CACHE, else $HOME/.cache/sph_gb300_autotune.json.
 const int kTppChoices[3] = {1, 2, 4};
 const int kBlockChoices[3] = {128, 256, 512};
+// per kernel: the 3 x 3 (threads per particle, block) variants, then the row-task form
+constexpr int kAutotuneVariants = 10;
 
 std::string autotune_path() {
   const char* env = std::getenv("SPH_AUTOTUNE_CACHE");
@@ -477,12 +491,15 @@ void write_autotune_cache(const std::map<std::string, std::string>& m) {
   std::rename((path + ".tmp").c_str(), path.c_str());
 }
 
-bool parse_cfg(const std::string& v, sph::LaunchCfg* c) {
+// "pr_tpp,pr_block,dr_tpp,dr_block"; the row-task form (block kRowBlock, one thread per
+// particle) only for a handle of one tank.
+bool parse_cfg(const std::string& v, sph::LaunchCfg* c, bool single) {
   int a[4];
   if (std::sscanf(v.c_str(), "%d,%d,%d,%d", &a[0], &a[1], &a[2], &a[3]) != 4) return false;
   auto ok_t = [](int t) { return t == 1 || t == 2 || t == 4; };
   auto ok_b = [](int b) { return b == 128 || b == 256 || b == 512; };
-  if (!ok_t(a[0]) || !ok_b(a[1]) || !ok_t(a[2]) || !ok_b(a[3])) return false;
+  auto ok = [&](int t, int b) { return ok_t(t) && (ok_b(b) || (single && t == 1 && sph::row_form(b))); };
+  if (!ok(a[0], a[1]) || !ok(a[2], a[3])) return false;
   c->pr_tpp = a[0];
   c->pr_block = a[1];
   c->dr_tpp = a[2];
@@ -626,6 +643,21 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
   DALLOC(h, b.wstart, n_cells + 1);
   DALLOC(h, b.wnear, n_cells);
   DALLOC(h, b.scan_tmp, sph::scan_tmp_elems(n_cells));
+  if (n_instances == 1 && n_fluid > 0) {      // row pieces of the row-task form
+    const Inst& I0 = h->hinst[0];
+    b.n_rows = (int64_t)I0.scell[1] * I0.scell[2];
+    b.row_task_cap = (n_fluid + 31) / 32 + b.n_rows;   // sum over rows of ceil(len / 32)
+    DALLOC(h, b.row_task, (size_t)b.row_task_cap);
+    DALLOC(h, b.row_cnt, (size_t)b.n_rows);
+    DALLOC(h, b.row_off, (size_t)b.n_rows + 1);
+    DALLOC(h, b.row_tmp, sph::scan_tmp_elems(b.n_rows));
+  }
+  b.rows_valid = &h->rows_valid;
+  {
+    int dev = 0;
+    CK(h, cudaGetDevice(&dev));
+    CK(h, cudaDeviceGetAttribute(&b.n_sm, cudaDevAttrMultiProcessorCount, dev));
+  }
   DALLOC(h, b.WP, n_wall);
   DALLOC(h, b.WN, n_wall);
   DALLOC(h, b.wid, n_wall);
@@ -697,7 +729,7 @@ int sph_create(const sph_params* params, int32_t n_instances, const int64_t* flu
   {
     const auto cache = read_autotune_cache();
     const auto it = cache.find(autotune_key(h));
-    if (it != cache.end()) parse_cfg(it->second, &b.cfg);
+    if (it != cache.end()) parse_cfg(it->second, &b.cfg, n_instances == 1);
   }
   CK(h, cudaGetLastError());
   int r = sph_set_state(h, pos, vel, rho, nullptr, 0.0, stream);
@@ -1042,7 +1074,9 @@ int sph_set_launch_config(sph_handle* h, const int32_t* cfg) {
   std::ostringstream o;
   o << cfg[0] << "," << cfg[1] << "," << cfg[2] << "," << cfg[3];
   sph::LaunchCfg c;
-  if (!parse_cfg(o.str(), &c)) return fail(h, SPH_E_INVALID, "threads per particle must be 1, 2 or 4 and blocks 128, 256 or 512");
+  if (!parse_cfg(o.str(), &c, h->b.n_inst == 1))
+    return fail(h, SPH_E_INVALID, "threads per particle must be 1, 2 or 4 and blocks 128, 256 or 512, or 1 and 896 "
+                                  "(row tasks, one tank)");
   h->b.cfg = c;
   drop_graph(h);
   return SPH_OK;
@@ -1059,32 +1093,42 @@ int sph_autotune(sph_handle* h, int32_t* cfg_out, double* ms_out, void* stream) 
   sph::launch_dt_acoustic(h->b, s, h->cond, false, &h->launches);
   cudaEvent_t e0 = h->ev[0], e1 = h->ev[1];
   const int reps = 3;
+  // the row-task form is a tenth variant of each kernel on handles of one tank
+  const bool rows = h->b.row_task && !h->b.geo;
+  if (rows && !h->rows_valid) {
+    sph::launch_row_tasks(h->b, s, &h->launches);
+    h->rows_valid = true;
+  }
   // repeated launches of either kernel are idempotent: same inputs, same outputs
   for (int kernel = 0; kernel < 2; ++kernel) {
     float best = 1e30f;
     sph::LaunchCfg best_cfg = h->b.cfg;
-    for (int t : kTppChoices)
-      for (int blk : kBlockChoices) {
-        sph::LaunchCfg c = h->b.cfg;
-        if (kernel == 0) { c.pr_tpp = t; c.pr_block = blk; } else { c.dr_tpp = t; c.dr_block = blk; }
-        sph::Buffers bb = h->b;
-        bb.cfg = c;
-        CK(h, cudaEventRecord(e0, s));
-        for (int r = 0; r < reps; ++r) {
-          if (kernel == 0) sph::launch_pressure_relaxation(bb, s, &h->launches);
-          else sph::launch_density_relaxation(bb, s, &h->launches);
-        }
-        CK(h, cudaEventRecord(e1, s));
-        CK(h, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(h, cudaEventElapsedTime(&ms, e0, e1));
-        ms /= reps;
-        if (ms_out) ms_out[kernel * 9 + (t == 1 ? 0 : t == 2 ? 1 : 2) * 3 + (blk == 128 ? 0 : blk == 256 ? 1 : 2)] = ms;
-        if (ms < best) {
-          best = ms;
-          best_cfg = c;
-        }
+    for (int v = 0; v < kAutotuneVariants; ++v) {
+      const int t = v < 9 ? kTppChoices[v / 3] : 1, blk = v < 9 ? kBlockChoices[v % 3] : sph::kRowBlock;
+      if (v == 9 && !rows) {
+        if (ms_out) ms_out[kernel * kAutotuneVariants + v] = -1.0;   // not available
+        continue;
       }
+      sph::LaunchCfg c = h->b.cfg;
+      if (kernel == 0) { c.pr_tpp = t; c.pr_block = blk; } else { c.dr_tpp = t; c.dr_block = blk; }
+      sph::Buffers bb = h->b;
+      bb.cfg = c;
+      CK(h, cudaEventRecord(e0, s));
+      for (int r = 0; r < reps; ++r) {
+        if (kernel == 0) sph::launch_pressure_relaxation(bb, s, &h->launches);
+        else sph::launch_density_relaxation(bb, s, &h->launches);
+      }
+      CK(h, cudaEventRecord(e1, s));
+      CK(h, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(h, cudaEventElapsedTime(&ms, e0, e1));
+      ms /= reps;
+      if (ms_out) ms_out[kernel * kAutotuneVariants + v] = ms;
+      if (ms < best) {
+        best = ms;
+        best_cfg = c;
+      }
+    }
     h->b.cfg = best_cfg;
     // the stored result comes from the chosen variant
     if (kernel == 0) sph::launch_pressure_relaxation(h->b, s, &h->launches);

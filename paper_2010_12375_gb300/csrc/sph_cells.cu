@@ -484,6 +484,33 @@ __global__ void k_dilate_axis(int64_t n_cells, int axis, const Inst* __restrict_
   out[c] = v;
 }
 
+// Row pieces of the row-task form (one tank): row r = cy + scell[1] cz holds the search
+// cells (0..scell[0]-1, cy, cz), whose particles are contiguous in the cell order.
+__global__ void k_row_count(const Inst I, int64_t n_rows, const uint32_t* __restrict__ fstart,
+                            uint32_t* __restrict__ cnt) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const long long c0 = I.cell_base + (long long)r * I.scell[0];
+  const uint32_t len = fstart[c0 + I.scell[0]] - fstart[c0];
+  cnt[r] = (len + 31u) >> 5;
+}
+
+__global__ void k_row_fill(const Inst I, int64_t n_rows, const uint32_t* __restrict__ fstart,
+                           const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
+                           int2* __restrict__ task, int64_t cap) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const long long c0 = I.cell_base + (long long)r * I.scell[0];
+  const int first = (int)fstart[c0];
+  const int len = (int)(fstart[c0 + I.scell[0]] - fstart[c0]);
+  const int k_end = (int)cnt[r];
+  for (int k = 0; k < k_end; ++k) {
+    const int64_t t = (int64_t)off[r] + k;
+    if (t >= cap) return;            // not reached: cap >= n/32 + rows bounds the pieces
+    task[t] = make_int2(first + 32 * k, min(32, len - 32 * k));
+  }
+}
+
 }  // namespace
 
 void launch_hash(const Buffers& b, cudaStream_t s, int64_t* launches) {
@@ -501,6 +528,7 @@ void launch_fluid_offsets(const Buffers& b, cudaStream_t s, int64_t* launches) {
 }
 
 void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  if (b.rows_valid) *b.rows_valid = false;     // the row pieces follow the new order
   if (b.n == 0) return;
   k_scatter<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.cell, b.rank, b.fstart, b.id, b.key, b.src);
   // final slots into rank (free after the scatter); sorted ids into cell (free after the rank)
@@ -521,6 +549,16 @@ void launch_neighbours(const Buffers& b, cudaStream_t s, int64_t* launches) {
   kern<<<grid_for(b.n), kBlock, 0, s>>>(b.n, b.PS, b.inst_of, b.inst, b.fstart, wp, b.wstart, b.wnear,
                                         b.cap, b.nbr, b.nbc, b.glob);
   ++*launches;
+}
+
+void launch_row_tasks(const Buffers& b, cudaStream_t s, int64_t* launches) {
+  if (!b.row_task || b.n_rows == 0) return;
+  const unsigned g = grid_for(b.n_rows);
+  k_row_count<<<g, kBlock, 0, s>>>(b.inst0, b.n_rows, b.fstart, b.row_cnt);
+  scan_exclusive(b.row_cnt, b.row_off, b.n_rows, b.row_tmp, s, launches);
+  k_row_fill<<<g, kBlock, 0, s>>>(b.inst0, b.n_rows, b.fstart, b.row_cnt, b.row_off, b.row_task,
+                                  b.row_task_cap);
+  *launches += 2;
 }
 
 // Walls are static: sort them into cells once. Uses the fluid build scratch

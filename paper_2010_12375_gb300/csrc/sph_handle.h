@@ -38,6 +38,7 @@ struct sph_handle {
   double ms[2] = {0.0, 0.0};
   int64_t timed[2] = {0, 0};
   bool cells_valid = false;
+  bool rows_valid = false;         // row pieces match the current cell order (row-task form)
   float4* grad = nullptr;          // [3][n] gradient sums of sph_gradient_diagnostics (lazily)
   sph_solid* solid = nullptr;      // attached elastic solid (sph_solid_create), or NULL
 };

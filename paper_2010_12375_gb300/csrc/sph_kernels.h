@@ -8,7 +8,11 @@
 namespace sph {
 
 // Launch configuration of the acoustic-substep kernels (chosen by the autotuner):
-// threads per particle (1, 2, 4) and block size (128, 256, 512).
+// threads per particle (1, 2, 4) and block size (128, 256, 512), or the row-task form
+// (one thread per particle, block kRowBlock): one resident block of kRowWarps warps an SM,
+// each warp taking 32-particle pieces of one search-cell row from its block's queue.
+constexpr int kRowWarps = 28;
+constexpr int kRowBlock = kRowWarps * 32;
 struct LaunchCfg {
   int pr_tpp = 1, pr_block = 256;   // pressure relaxation
   int dr_tpp = 1, dr_block = 256;   // density relaxation
@@ -65,6 +69,15 @@ struct Buffers {
   float4* hshare = nullptr;
   float4* hpart = nullptr;
   uint8_t* hrev = nullptr;
+  // row tasks of the row-task launch form (one tank only; NULL otherwise): the pieces
+  // (first slot, count <= 32) of every search-cell row along x, row after row
+  int2* row_task = nullptr;       // [row_task_cap]
+  uint32_t* row_cnt = nullptr;    // [n_rows] pieces of each row
+  uint32_t* row_off = nullptr;    // [n_rows + 1] exclusive scan; row_off[n_rows] = pieces
+  uint32_t* row_tmp = nullptr;    // scan scratch
+  int64_t n_rows = 0, row_task_cap = 0;
+  bool* rows_valid = nullptr;     // host flag: the pieces match the current cell order
+  int n_sm = 0;                   // SMs of the device (grid of the row-task form)
 };
 
 size_t scan_tmp_elems(int64_t n);
@@ -79,6 +92,10 @@ void launch_sort_fluid(const Buffers& b, cudaStream_t s, int64_t* launches);    
 void launch_check_offsets(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_check_table(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_neighbours(const Buffers& b, cudaStream_t s, int64_t* launches);
+// the row pieces of the row-task form from the current fluid cell offsets (one tank)
+void launch_row_tasks(const Buffers& b, cudaStream_t s, int64_t* launches);
+// whether a configured block selects the row-task form
+inline bool row_form(int block) { return block == kRowBlock; }
 void sort_walls(Buffers& b, int4* WP_tmp, float4* WN_tmp, int* wid_tmp, cudaStream_t s);
 void flag_near_wall_cells(const Buffers& b, uint8_t* tmp, cudaStream_t s);
 void launch_iota(int* a, int64_t n, cudaStream_t s);     // a[i] = i

@@ -598,6 +598,89 @@ k_density_relaxation(const Inst Ip, const float4* __restrict__ geo, int64_t n, c
       I, i, sub, valid, dtd, geo, n, PH, VH, PS, VS, mass, nbr, nbc, WP, WN, g);
 }
 
+// ---------------------------------------------------------------- row-task form ---
+// One resident block of kRowWarps warps an SM, one thread per particle. Each warp takes
+// the next piece (32 consecutive particles of one search-cell row, `row_task`) from its
+// block's queue: block b works through the runs of kRowWarps consecutive pieces numbered
+// b, b + gridDim.x, b + 2 gridDim.x, ..., so the blocks move through the cell order side by
+// side (the rows in flight share their neighbours in L1 and L2) and a warp that finishes
+// early takes the next piece instead of waiting for the rest of its block. The particle
+// arithmetic is that of the one-thread-per-particle kernels: results equal theirs bit for bit.
+__device__ __forceinline__ bool next_row_piece(int* queue, int lane, long long pieces, long long* t_out) {
+  int q = 0;
+  if (lane == 0) q = atomicAdd(queue, 1);
+  q = __shfl_sync(0xffffffffu, q, 0);
+  const long long t = ((long long)blockIdx.x + (long long)gridDim.x * (q / kRowWarps)) * kRowWarps + q % kRowWarps;
+  *t_out = t;
+  return t < pieces;
+}
+
+template <int D, bool PER, bool TV>
+__global__ void __launch_bounds__(kRowBlock, 1)
+k_pressure_relaxation_rows(const Inst I, int64_t n, const int4* __restrict__ PS, const float4* __restrict__ VS,
+                           int4* __restrict__ PH, float4* __restrict__ VH, const float* __restrict__ mass,
+                           Ctrl* ctrl, const int* __restrict__ nbr, const uint32_t* __restrict__ nbc,
+                           const int4* __restrict__ WP, const float4* __restrict__ WN,
+                           const float4* __restrict__ acc_prior, float4* __restrict__ acc_keep, Global* g,
+                           const int2* __restrict__ row_task, const uint32_t* __restrict__ row_total,
+                           int64_t row_task_cap) {
+  __shared__ int queue;
+  __shared__ float red[kRowWarps];
+  if (threadIdx.x == 0) queue = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long pieces = min((long long)*row_total, (long long)row_task_cap);
+  const double dtd = ctrl[0].dt;
+  float m = 0.0f;
+  long long t;
+  if (dtd != 0.0) {                              // 0: the tank is idle for this substep
+    while (next_row_piece(&queue, lane, pieces, &t)) {
+      const int2 piece = row_task[t];
+      const bool valid = lane < piece.y;
+      bool writer;
+      const float v2 = pr_particle<D, PER, 1, false, TV, const int4* __restrict__, const float4* __restrict__>(
+          I, valid ? (int64_t)piece.x + lane : 0, 0, valid, dtd, nullptr, n, PS, VS, PH, VH, mass, nbr, nbc,
+          WP, WN, acc_prior, acc_keep, g, &writer);
+      if (writer) m = fmaxf(m, v2);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < kRowWarps ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(&ctrl[0].vmax2, __float_as_uint(m));
+  }
+}
+
+template <int D, bool PER>
+__global__ void __launch_bounds__(kRowBlock, 1)
+k_density_relaxation_rows(const Inst I, int64_t n, const int4* __restrict__ PH, const float4* __restrict__ VH,
+                          int4* __restrict__ PS, float4* __restrict__ VS, const float* __restrict__ mass,
+                          const Ctrl* __restrict__ ctrl, const int* __restrict__ nbr,
+                          const uint32_t* __restrict__ nbc, const int4* __restrict__ WP,
+                          const float4* __restrict__ WN, Global* g, const int2* __restrict__ row_task,
+                          const uint32_t* __restrict__ row_total, int64_t row_task_cap) {
+  __shared__ int queue;
+  if (threadIdx.x == 0) queue = 0;
+  __syncthreads();
+  const double dtd = ctrl[0].dt;
+  if (dtd == 0.0) return;
+  const int lane = threadIdx.x & 31;
+  const long long pieces = min((long long)*row_total, (long long)row_task_cap);
+  long long t;
+  while (next_row_piece(&queue, lane, pieces, &t)) {
+    const int2 piece = row_task[t];
+    const bool valid = lane < piece.y;
+    dr_particle<D, PER, 1, false, const int4* __restrict__, const float4* __restrict__>(
+        I, valid ? (int64_t)piece.x + lane : 0, 0, valid, dtd, nullptr, n, PH, VH, PS, VS, mass, nbr, nbc,
+        WP, WN, g);
+  }
+}
+
 // Launch variants: (threads per particle, block size) per kernel, indexed by kTpp / kBlk.
 template <int D, bool PER>
 void launch_pr(int tpp, int block, const Buffers& b, cudaStream_t s) {
@@ -613,6 +696,16 @@ void launch_pr(int tpp, int block, const Buffers& b, cudaStream_t s) {
     const unsigned g1 = grid_for(b.n, 128);
     if (b.n_inst == 1) k_pressure_relaxation<D, PER, 1, 128, true, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_PR_ARGS);
     else k_pressure_relaxation<D, PER, 1, 128, false, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_PR_ARGS);
+    return;
+  }
+  if (row_form(block)) {     // row-task form (one tank; the caller has built the pieces)
+#define SPH_PR_ROWS(TV) k_pressure_relaxation_rows<D, PER, TV><<<b.n_sm, kRowBlock, 0, s>>>(                     \
+      b.inst0, b.n, (const int4*)b.PS, (const float4*)b.VS, b.PH, b.VH, (const float*)b.mass, b.ctrl,          \
+      (const int*)b.nbr, (const uint32_t*)b.nbc, (const int4*)b.WP, (const float4*)b.WN,                        \
+      (const float4*)b.acc_prior, b.acc_keep, b.glob, b.row_task, b.row_off + b.n_rows, b.row_task_cap)
+    if (b.any_transport) SPH_PR_ROWS(true);
+    else SPH_PR_ROWS(false);
+#undef SPH_PR_ROWS
     return;
   }
   if (b.any_transport) {     // transport velocity: one thread per particle, the configured block
@@ -648,6 +741,13 @@ void launch_dr(int tpp, int block, const Buffers& b, cudaStream_t s) {
     const unsigned g1 = grid_for(b.n, 128);
     if (b.n_inst == 1) k_density_relaxation<D, PER, 1, 128, true, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_DR_ARGS);
     else k_density_relaxation<D, PER, 1, 128, false, true><<<g1, 128, 0, s>>>(b.inst0, b.geo, SPH_DR_ARGS);
+    return;
+  }
+  if (row_form(block)) {     // row-task form (one tank; the caller has built the pieces)
+    k_density_relaxation_rows<D, PER><<<b.n_sm, kRowBlock, 0, s>>>(
+        b.inst0, b.n, (const int4*)b.PH, (const float4*)b.VH, b.PS, b.VS, (const float*)b.mass,
+        (const Ctrl*)b.ctrl, (const int*)b.nbr, (const uint32_t*)b.nbc, (const int4*)b.WP, (const float4*)b.WN,
+        b.glob, b.row_task, b.row_off + b.n_rows, b.row_task_cap);
     return;
   }
 #define SPH_DR_T(T) (block == 512 ? SPH_DR(T, 512) : block == 256 ? SPH_DR(T, 256) : SPH_DR(T, 128))

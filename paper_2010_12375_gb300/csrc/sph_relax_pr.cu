@@ -81,7 +81,16 @@ void launch_pair_geometry(const Buffers& b, cudaStream_t s, int64_t* launches) {
 
 void launch_pressure_relaxation(const Buffers& b, cudaStream_t s, int64_t* launches) {
   if (b.n == 0) return;
-  const int tpp = b.cfg.pr_tpp, block = b.cfg.pr_block;
+  const int tpp = b.cfg.pr_tpp;
+  int block = b.cfg.pr_block;
+  if (row_form(block)) {
+    if (!b.row_task || b.geo) {
+      block = 128;                        // row pieces exist for one tank only
+    } else if (!*b.rows_valid) {           // first row-task launch since the cells changed
+      launch_row_tasks(b, s, launches);
+      *b.rows_valid = true;
+    }
+  }
   if (b.dim == 2) {
     if (b.any_periodic) launch_pr<2, true>(tpp, block, b, s);
     else launch_pr<2, false>(tpp, block, b, s);

@@ -433,12 +433,13 @@ def sph_set_launch_config(h, cfg):
 
 def sph_autotune(h, stream=None):
     """Tune the relaxation kernels' launch variants during one advection step; returns
-    (cfg, times[kernel][tpp][block] in ms)."""
+    (cfg, times in ms: [kernel][variant], variants 0-8 = 3 tpp_index + block_index, 9 = the
+    row-task form, -1 where it does not apply)."""
     lib = load()
     cfg = (ctypes.c_int32 * 4)()
-    ms = (ctypes.c_double * 18)()
+    ms = (ctypes.c_double * 20)()
     check(lib, h, lib.sph_autotune(h, cfg, ms, _stream(stream)))
-    return list(cfg), np.array(ms[:]).reshape(2, 3, 3)
+    return list(cfg), np.array(ms[:]).reshape(2, 10)
 
 
 def sph_set_gravity(h, g, instance=-1, stream=None):

@@ -706,7 +706,7 @@ def test_full_size_3d_first_substep_sampled(sph):
 
 
 # ------------------------------------------------------------------ launch variants / autotuner
-@pytest.mark.parametrize("cfg", [[2, 128, 4, 512], [4, 512, 2, 128], [1, 512, 1, 128]])
+@pytest.mark.parametrize("cfg", [[2, 128, 4, 512], [4, 512, 2, 128], [1, 512, 1, 128], [1, 896, 1, 896]])
 @pytest.mark.parametrize("case", ["dam3d", "tg"])
 def test_launch_variants_match_oracle(sph, case, cfg):
     prob, vel_amp, rho_amp = _substep_case(case)
@@ -747,10 +747,46 @@ def test_launch_variants_match_oracle(sph, case, cfg):
 
 def test_invalid_launch_config_is_rejected(sph):
     sim = sph.Simulation(wk.dam_break_2d(n_per_H=10))
+    for bad in ([3, 256, 1, 256], [2, 896, 1, 128], [1, 128, 4, 896], [1, 1024, 1, 128]):
+        with pytest.raises(sph.SphError) as e:
+            sph.sph_set_launch_config(sim.handle, bad)
+        assert e.value.code == sph.SPH_E_INVALID
+    assert sph.sph_get_launch_config(sim.handle) != [2, 896, 1, 128]
+    sim.close()
+    # the row-task form walks the rows of one tank: a batched handle refuses it
+    tanks = [wk.dam_break_2d(n_per_H=10), wk.dam_break_2d(n_per_H=12)]
+    sim = sph.Simulation(tanks)
     with pytest.raises(sph.SphError) as e:
-        sph.sph_set_launch_config(sim.handle, [3, 256, 1, 256])
+        sph.sph_set_launch_config(sim.handle, [1, 896, 1, 128])
     assert e.value.code == sph.SPH_E_INVALID
     sim.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("case", ["dam3d", "dam2d", "tg_tv"])
+def test_row_task_form_equals_the_per_particle_kernels(sph, case, graph):
+    # the row-task form assigns particles to warps by search-cell row and to blocks by a
+    # queue, with the per-particle kernels' arithmetic: every state bit and the substep
+    # count agree with the one-thread-per-particle launches over several advection steps
+    # (cell rebuilds, ragged rows, a free surface; the transport velocity on the periodic
+    # Taylor-Green square)
+    if case == "dam3d":
+        prob = wk.dam_break_3d(14)
+    elif case == "dam2d":
+        prob = wk.dam_break_2d(n_per_H=30)
+    else:
+        prob = wk.taylor_green(n=60, transport=True)
+    out = []
+    for cfg in ([1, 128, 1, 128], [1, 896, 1, 896], [1, 896, 1, 256]):
+        sim = sph.Simulation(prob, flags=sph.SPH_FLAG_GRAPH if graph else 0)
+        sph.sph_set_launch_config(sim.handle, cfg)
+        sim.step(4)
+        out.append((sim.state(), sim.diagnostics()["substeps"]))
+        sim.close()
+    for st, nsub in out[1:]:
+        assert nsub == out[0][1]
+        for u, v in zip(st, out[0][0]):
+            np.testing.assert_array_equal(u, v)
 
 
 def test_autotune_chooses_caches_and_equals_a_plain_step(sph, tmp_path, monkeypatch):
@@ -758,9 +794,12 @@ def test_autotune_chooses_caches_and_equals_a_plain_step(sph, tmp_path, monkeypa
     prob = wk.dam_break_3d(24)
     a = sph.Simulation(prob)
     cfg, times = sph.sph_autotune(a.handle)
-    assert cfg[0] in (1, 2, 4) and cfg[1] in (128, 256, 512)
-    assert np.all(times > 0)
-    assert abs(times[0].min() - times[0][[1, 2, 4].index(cfg[0])][[128, 256, 512].index(cfg[1])]) < 1e-12
+    assert (cfg[0] in (1, 2, 4) and cfg[1] in (128, 256, 512)) or cfg[:2] == [1, 896]
+    assert np.all(times > 0)                 # one tank: the row-task form is timed too
+    for k in range(2):
+        t, blk = cfg[2 * k], cfg[2 * k + 1]
+        v = 9 if blk == 896 else 3 * [1, 2, 4].index(t) + [128, 256, 512].index(blk)
+        assert abs(times[k].min() - times[k][v]) < 1e-12
     text = (tmp_path / "tune.json").read_text()
     assert "|d3|" in text and ",".join(map(str, cfg)) in text
     # a new handle for the same problem size picks the cached choice up
