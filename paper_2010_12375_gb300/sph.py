@@ -217,6 +217,43 @@ def _f64(a):
     return a.to(torch.float64).contiguous()
 
 
+def _count(a):
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _sized(a, count, what):
+    """The C side reads exactly `count` values of a caller array (it cannot check): reject
+    any other size, and a CUDA tensor on another device, before the call."""
+    if a is None:
+        return a
+    if _count(a) != count:
+        raise SphError(SPH_E_INVALID, f"{what}: {count} values expected, {_count(a)} given")
+    if not isinstance(a, np.ndarray) and a.is_cuda:
+        import torch
+        if a.device.index != torch.cuda.current_device():
+            raise SphError(SPH_E_INVALID, f"{what}: the tensor is not on the current device")
+    return a
+
+
+def _out(a, count, what):
+    """A caller's output array: `count` float64 values, contiguous (the C side writes them)."""
+    ok = (a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]) if isinstance(a, np.ndarray) else \
+        (str(a.dtype) == "torch.float64" and a.is_contiguous())
+    if not ok:
+        raise SphError(SPH_E_INVALID, f"{what}: a contiguous float64 array is expected")
+    return _sized(a, count, what)
+
+
+def _handle_shape(h, n=None, dim=None, what="array"):
+    """(fluid particles, dim) of handle h; given n or dim must match them."""
+    info = sph_get_info(h)
+    nh, dh = int(info.n_fluid), int(info.dim)
+    if (n is not None and int(n) != nh) or (dim is not None and int(dim) != dh):
+        raise SphError(SPH_E_INVALID, f"{what}: the handle holds {nh} fluid particles in {dh}D, "
+                                      f"not {n} in {dim}D")
+    return nh, dh
+
+
 def _stream(stream):
     if stream is None:
         return None
@@ -265,6 +302,11 @@ def sph_create(params, pos, vel, rho, mass, wall_pos, wall_normal, wall_vol,
     arr = (SphParams * len(plist))(*plist)
     pos, vel, rho, mass = _f64(pos), _f64(vel), _f64(rho), _f64(mass)
     wall_pos, wall_normal, wall_vol = _f64(wall_pos), _f64(wall_normal), _f64(wall_vol)
+    dim = int(plist[0].dim)
+    n_, nw_ = _count(rho), _count(wall_vol)
+    for a, c, w in ((pos, n_ * dim, "pos"), (vel, n_ * dim, "vel"), (mass, n_, "mass"),
+                    (wall_pos, nw_ * dim, "wall_pos"), (wall_normal, nw_ * dim, "wall_normal")):
+        _sized(a, c, "sph_create: " + w)
     fo = None if fluid_offsets is None else np.ascontiguousarray(fluid_offsets, dtype=np.int64)
     wo = None if wall_offsets is None else np.ascontiguousarray(wall_offsets, dtype=np.int64)
     n = int(rho.shape[0])
@@ -341,8 +383,11 @@ def sph_diagnostics(h, n_instances=1, stream=None):
 def sph_get_state(h, n, dim, stream=None, out=None):
     """Returns (pos, vel, rho, drho_dt) float64 numpy arrays in id order (or fills `out`)."""
     lib = load()
+    n, dim = _handle_shape(h, n, dim, "sph_get_state")
     if out is None:
         out = (np.empty((n, dim)), np.empty((n, dim)), np.empty(n), np.empty(n))
+    for a, c, w in zip(out, (n * dim, n * dim, n, n), ("pos", "vel", "rho", "drho_dt")):
+        _out(a, c, "sph_get_state: " + w)
     check(lib, h, lib.sph_get_state(h, *[_ptr(a) for a in out], _stream(stream)))
     return out
 
@@ -350,6 +395,9 @@ def sph_get_state(h, n, dim, stream=None, out=None):
 def sph_set_state(h, pos, vel, rho, drho_dt=None, t=-1.0, stream=None):
     lib = load()
     pos, vel, rho, drho_dt = _f64(pos), _f64(vel), _f64(rho), _f64(drho_dt)
+    n, dim = _handle_shape(h)
+    for a, c, w in ((pos, n * dim, "pos"), (vel, n * dim, "vel"), (rho, n, "rho"), (drho_dt, n, "drho_dt")):
+        _sized(a, c, "sph_set_state: " + w)
     check(lib, h, lib.sph_set_state(h, _ptr(pos), _ptr(vel), _ptr(rho), _ptr(drho_dt), float(t),
                                     _stream(stream)))
 
@@ -358,6 +406,7 @@ def sph_gradient_diagnostics(h, n, dim, stream=None):
     """Strong- and weak-form gradients of rho and p per fluid particle (caller order):
     dict of four (n, dim) float64 arrays."""
     lib = load()
+    n, dim = _handle_shape(h, n, dim, "sph_gradient_diagnostics")
     out = {k: np.empty((n, dim)) for k in ("rho_strong", "rho_weak", "p_strong", "p_weak")}
     check(lib, h, lib.sph_gradient_diagnostics(h, _ptr(out["rho_strong"]), _ptr(out["rho_weak"]),
                                                _ptr(out["p_strong"]), _ptr(out["p_weak"]), _stream(stream)))
@@ -366,6 +415,7 @@ def sph_gradient_diagnostics(h, n, dim, stream=None):
 
 def sph_get_acceleration(h, n, dim, stream=None):
     lib = load()
+    n, dim = _handle_shape(h, n, dim, "sph_get_acceleration")
     acc = np.empty((n, dim))
     check(lib, h, lib.sph_get_acceleration(h, _ptr(acc), _stream(stream)))
     return acc
@@ -373,6 +423,7 @@ def sph_get_acceleration(h, n, dim, stream=None):
 
 def sph_get_permutation(h, n, stream=None):
     lib = load()
+    n, _ = _handle_shape(h, n, None, "sph_get_permutation")
     ids = np.empty(n, dtype=np.int32)
     check(lib, h, lib.sph_get_permutation(h, _ptr(ids), _stream(stream)))
     return ids
@@ -381,6 +432,7 @@ def sph_get_permutation(h, n, stream=None):
 def sph_get_neighbours(h, n, stride, stream=None):
     """Returns (fluid_count, wall_count, fluid_ids[n, stride], wall_ids[n, stride])."""
     lib = load()
+    n, _ = _handle_shape(h, n, None, "sph_get_neighbours")
     fc = np.empty(n, dtype=np.int32)
     wc = np.empty(n, dtype=np.int32)
     fi = np.empty((n, stride), dtype=np.int32)
@@ -505,6 +557,7 @@ def sph_learned_weight_count() -> int:
 def sph_learned_create(dim, weights=None):
     lib = load()
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+    _sized(w, sph_learned_weight_count(), "sph_learned_create: weights")
     net = ctypes.c_void_p()
     code = lib.sph_learned_create(int(dim), _ptr(w), ctypes.byref(net))
     if code != SPH_OK:
@@ -521,7 +574,8 @@ def sph_learned_destroy(net):
 
 def sph_learned_set_weights(net, weights):
     lib = load()
-    w = np.ascontiguousarray(weights, dtype=np.float32)
+    w = _sized(np.ascontiguousarray(weights, dtype=np.float32), sph_learned_weight_count(),
+               "sph_learned_set_weights")
     _lcheck(lib, net, lib.sph_learned_set_weights(net, _ptr(w)))
 
 
@@ -539,6 +593,7 @@ def sph_learned_set_fused(net, enabled):
 
 def sph_learned_predict(h, net, n, dim, stream=None):
     lib = load()
+    n, dim = _handle_shape(h, n, dim, "sph_learned_predict")
     y = np.empty((n, dim + 1))
     _lcheck(lib, net, lib.sph_learned_predict(h, net, _ptr(y), _stream(stream)))
     return y
@@ -547,7 +602,8 @@ def sph_learned_predict(h, net, n, dim, stream=None):
 def sph_learned_train_step(h, net, target, lr, want_grad=False, stream=None):
     """Returns (loss, gradient or None)."""
     lib = load()
-    t = _f64(target)
+    n, dim = _handle_shape(h)
+    t = _sized(_f64(target), n * (dim + 1), "sph_learned_train_step: target")
     loss = ctypes.c_double(0.0)
     g = np.empty(sph_learned_weight_count(), dtype=np.float32) if want_grad else None
     _lcheck(lib, net, lib.sph_learned_train_step(h, net, _ptr(t), float(lr), ctypes.byref(loss), _ptr(g),
@@ -593,26 +649,28 @@ def sph_species_destroy(sp):
 
 def sph_species_set(h, sp, C, stream=None):
     lib = load()
-    C = _f64(C)
+    C = _sized(_f64(C), _handle_shape(h)[0], "sph_species_set")
     _scheck(lib, sp, lib.sph_species_set(h, sp, _ptr(C), _stream(stream)))
 
 
 def sph_species_get(h, sp, n, stream=None, out=None):
     lib = load()
-    C = np.empty(n, dtype=np.float64) if out is None else out
+    n, _ = _handle_shape(h, n, None, "sph_species_get")
+    C = np.empty(n, dtype=np.float64) if out is None else _out(out, n, "sph_species_get")
     _scheck(lib, sp, lib.sph_species_get(h, sp, _ptr(C), _stream(stream)))
     return C
 
 
 def sph_species_set_gate(h, sp, w, stream=None):
     lib = load()
-    w = _f64(w)
+    w = _sized(_f64(w), _handle_shape(h)[0], "sph_species_set_gate")
     _scheck(lib, sp, lib.sph_species_set_gate(h, sp, _ptr(w), _stream(stream)))
 
 
 def sph_species_get_gate(h, sp, n, stream=None, out=None):
     lib = load()
-    w = np.empty(n, dtype=np.float64) if out is None else out
+    n, _ = _handle_shape(h, n, None, "sph_species_get_gate")
+    w = np.empty(n, dtype=np.float64) if out is None else _out(out, n, "sph_species_get_gate")
     _scheck(lib, sp, lib.sph_species_get_gate(h, sp, _ptr(w), _stream(stream)))
     return w
 
@@ -620,7 +678,7 @@ def sph_species_get_gate(h, sp, n, stream=None, out=None):
 def sph_species_set_scale(h, sp, s, stream=None):
     """Per-particle diffusivity factors (caller row order, positive)."""
     lib = load()
-    s = _f64(s)
+    s = _sized(_f64(s), _handle_shape(h)[0], "sph_species_set_scale")
     _scheck(lib, sp, lib.sph_species_set_scale(h, sp, _ptr(s), _stream(stream)))
 
 
@@ -631,7 +689,8 @@ def sph_species_set_tensors(h, sp, Dp, stream=None):
     if Dp is None:
         _scheck(lib, sp, lib.sph_species_set_tensors(h, sp, None, _stream(stream)))
         return
-    Dp = _f64(Dp)
+    n, dim = _handle_shape(h)
+    Dp = _sized(_f64(Dp), n * dim * dim, "sph_species_set_tensors")
     _scheck(lib, sp, lib.sph_species_set_tensors(h, sp, _ptr(Dp), _stream(stream)))
 
 
@@ -748,6 +807,9 @@ def sph_solid_create(h, model, rho0, youngs, poisson, h_s, pos, vol, normal, fix
     pos, vol, normal = _f64(pos), _f64(vol), _f64(normal)
     fx = None if fixed is None else np.ascontiguousarray(np.asarray(fixed).astype(np.int32))
     n = int(vol.shape[0])
+    dim = sph_get_info(h).dim
+    for a, c, w in ((pos, n * dim, "pos"), (normal, n * dim, "normal"), (fx, n, "fixed")):
+        _sized(a, c, "sph_solid_create: " + w)
     s = ctypes.c_void_p()
     code = lib.sph_solid_create(h, ctypes.byref(p), n, _ptr(pos), _ptr(vol), _ptr(normal), _ptr(fx), ctypes.byref(s))
     if code != SPH_OK:

@@ -129,3 +129,27 @@ def test_solid_entry_points_reject_null_handles(lib):
     assert L.sph_solid_create(None, None, 0, None, None, None, None, ctypes.byref(out)) == lib.SPH_E_INVALID
     assert L.sph_solid_get_state(None, None, None, None, None, None, None, None) == lib.SPH_E_INVALID
     L.sph_solid_destroy(None)                                 # a no-op
+
+
+def test_binding_rejects_caller_arrays_of_the_wrong_size(lib):
+    # the C side reads or writes exactly the counts a handle implies and cannot check them:
+    # the binding refuses any other size, dtype or layout before the call
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    assert lib._sized(None, 5, "x") is None
+    assert lib._sized(np.zeros((2, 3)), 6, "x").shape == (2, 3)
+    assert lib._sized(torch.zeros(6), 6, "x").numel() == 6
+    for bad in (np.zeros(5), np.zeros(7), torch.zeros(2, 2)):
+        with pytest.raises(lib.SphError) as e:
+            lib._sized(bad, 6, "pos")
+        assert e.value.code == lib.SPH_E_INVALID
+    assert lib._out(np.zeros(4), 4, "rho").size == 4
+    assert lib._out(torch.zeros(4, dtype=torch.float64), 4, "rho").numel() == 4
+    for bad in (np.zeros(4, dtype=np.float32), np.zeros((4, 2))[:, 0], torch.zeros(4), np.zeros(3)):
+        with pytest.raises(lib.SphError) as e:
+            lib._out(bad, 4, "rho")
+        assert e.value.code == lib.SPH_E_INVALID
+    # the learned network's weight vector has a fixed length
+    with pytest.raises(lib.SphError) as e:
+        lib.sph_learned_create(2, np.zeros(lib.sph_learned_weight_count() - 1))
+    assert e.value.code == lib.SPH_E_INVALID

@@ -829,3 +829,24 @@ def test_gather_ceiling_runs_and_changes_nothing(sph):
     with pytest.raises(sph.SphError):
         sph.sph_gather_ceiling(sim.handle, 3)
     sim.close()
+
+
+def test_binding_checks_array_sizes_against_the_handle(sph):
+    # caller arrays must hold what the handle implies (the C side reads exactly that); a
+    # refused call leaves the state as it was
+    sim = sph.Simulation(wk.dam_break_2d(n_per_H=10))
+    n, dim = sim.n, sim.dim
+    x, v, rho, _ = sim.state()
+    for args in ((x, v, rho[:-1]), (x[:-1], v, rho), (x, np.zeros((n, 3)), rho)):
+        with pytest.raises(sph.SphError) as e:
+            sph.sph_set_state(sim.handle, *args)
+        assert e.value.code == sph.SPH_E_INVALID
+    for call in (lambda: sph.sph_get_state(sim.handle, n - 1, dim),
+                 lambda: sph.sph_get_acceleration(sim.handle, n, 3),
+                 lambda: sph.sph_get_state(sim.handle, n, dim, out=(x, v, rho, np.zeros(n, np.float32)))):
+        with pytest.raises(sph.SphError) as e:
+            call()
+        assert e.value.code == sph.SPH_E_INVALID
+    for a, b in zip(sim.state(), (x, v, rho)):
+        np.testing.assert_array_equal(a, b)
+    sim.close()
