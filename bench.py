@@ -441,6 +441,7 @@ def run_ours(args, rank, world, local_rank):
             "density_relaxation": ({"algorithmic_bytes_per_launch": k8_bytes, "achieved": k8_achieved,
                                     "frac": k8_achieved / peak, "unit": "GB/s"} if k8_achieved else None),
             "gather_ceiling_ms": gather_ms,
+            "gather_ceiling_form": "row tasks" if pr_rows else "one thread a particle, 128-thread blocks",
             "frac_of_gather_ceiling": (gather_ms / k7_ms) if kcount[0] else None,
             "pipes": (dict(PR_PIPES, source="ncu --set full of this kernel at n = 80 (1.02M fluid)")
                       if traffic is not None else None),

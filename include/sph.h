@@ -332,8 +332,9 @@ int sph_autotune(sph_handle* h, int32_t* cfg_out, double* ms_out, void* stream);
 
 /* Gather ceiling (a measurement aid; the paper has no counterpart): times `reps` launches
  * of a kernel that walks the current neighbour table the way the pressure relaxation does
- * (one thread per particle, 16-byte index quads, the 32-byte position + velocity record
- * of every fluid neighbour and the wall records gathered) with no pair arithmetic, and
+ * (one thread per particle in its configured launch form, per-particle blocks or row tasks,
+ * 16-byte index quads, the 32-byte position + velocity record of every fluid neighbour and
+ * the wall records gathered) with no pair arithmetic, and
  * writes the mean launch time in ms to *ms_out (host). No state is changed. Needs a
  * neighbour table (sph_build_cells or a step first: SPH_E_INVALID otherwise); reps >= 1.
  * Synchronous. */

@@ -131,8 +131,10 @@ void launch_reverse_slots(const Buffers& b, cudaStream_t s, int64_t* launches);
 void launch_half_pair(const Buffers& b, bool pressure, cudaStream_t s, int64_t* launches);
 // per-slot pair geometry at the current positions, for the frozen-geometry reading
 void launch_pair_geometry(const Buffers& b, cudaStream_t s, int64_t* launches);
-// gather-only walk of the neighbour table (diagnostic); sink: one device word
+// gather-only walk of the neighbour table (diagnostic), in the pressure relaxation's launch
+// form (gather_rows: the row-task form); sink: one device word
 void launch_gather_ceiling(const Buffers& b, unsigned* sink, cudaStream_t s, int64_t* launches);
+bool gather_rows(const Buffers& b);
 
 // diagnostics: out[n_inst * kDiagFields] doubles on the device
 constexpr int kDiagFields = 16;

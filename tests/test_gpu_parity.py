@@ -814,9 +814,12 @@ def test_autotune_chooses_caches_and_equals_a_plain_step(sph, tmp_path, monkeypa
     b.close()
 
 
-def test_gather_ceiling_runs_and_changes_nothing(sph):
+@pytest.mark.parametrize("cfg", [[1, 128, 1, 128], [1, 896, 1, 896]])
+def test_gather_ceiling_runs_and_changes_nothing(sph, cfg):
+    # the walk runs in the pressure relaxation's launch form (per particle or row tasks)
     prob = wk.dam_break_3d(24)
     sim = sph.Simulation(prob)
+    sph.sph_set_launch_config(sim.handle, cfg)
     sim.step(1)
     before = sim.state()
     sim.build_cells()
