@@ -32,6 +32,11 @@
 // update instead of from the current positions; TV (pressure relaxation only), the
 // transport velocity of Eq. transport, whose background-pressure term moves the mid-point
 // position by dt^2/2 a_i.
+//
+// Launch forms: the per-particle kernels above map thread i of the grid to particle i;
+// k_pressure_relaxation_rows / k_density_relaxation_rows (the row-task form, one tank)
+// run the same per-particle code in one resident block an SM whose warps take 32-particle
+// pieces of the search-cell rows from a queue (see the row-task section below).
 #pragma once
 
 #include "sph_kernels.h"
